@@ -1,0 +1,128 @@
+"""Pins of the oracle's policy forward, sampling and quantisation emulation."""
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+import oracle as O
+from paper_2304_12152_gb300 import synth
+
+
+def _torch_forward(c, z, ws, bs):
+    """Independent FP64 forward with torch's conv2d (a library primitive)."""
+    x = torch.from_numpy(np.stack([c.astype(np.float64), z]))[None]
+    for l, (w, b) in enumerate(zip(ws, bs)):
+        x = F.conv2d(x, torch.from_numpy(w.astype(np.float64)), torch.from_numpy(b.astype(np.float64)), padding=1)
+        if l < len(ws) - 1:
+            x = torch.relu(x)
+    return x[0].numpy()
+
+
+@pytest.mark.parametrize("chs,hw", [((2, 4, 3, 1), (5, 5)), ((2, 8, 8, 1), (17, 23)), ((2, 6, 6, 4), (9, 12))])
+def test_forward_matches_torch_conv_chain(chs, hw):
+    h, w = hw
+    c = synth.contone_image(h, w, seed=1)
+    ws, _ = synth.he_normal_policy(chs, seed=2)
+    bs = synth.random_biases(chs, seed=3)
+    logits, probs, _ = O.forward(c, ws, bs, noise_seed=11, image=2)
+    z = O.uniform_map(11, 2, 0, h, w)
+    ref = _torch_forward(c, z, ws, bs)
+    np.testing.assert_allclose(logits, ref, rtol=1e-12, atol=1e-12)
+    if chs[-1] == 1:
+        np.testing.assert_allclose(probs[0], 1 / (1 + np.exp(-ref[0])), rtol=1e-12)
+    else:
+        e = np.exp(ref - ref.max(0))
+        np.testing.assert_allclose(probs, e / e.sum(0), rtol=1e-12)
+
+
+def test_forward_hand_unrolled_tiny():
+    # 1 hidden channel, 2 layers on a 3x3 image written out by hand
+    c = np.arange(9, dtype=np.float32).reshape(3, 3) / 10
+    w1 = np.zeros((1, 2, 3, 3), np.float32); w1[0, 0, 1, 1] = 1.0; w1[0, 0, 0, 0] = -0.5
+    w2 = np.zeros((1, 1, 3, 3), np.float32); w2[0, 0, 1, 2] = 2.0
+    b1 = np.array([0.1], np.float32); b2 = np.array([-0.3], np.float32)
+    logits, _, _ = O.forward(c, [w1, w2], [b1, b2], noise_seed=0)
+    cd = c.astype(np.float64)
+    a = np.zeros((3, 3))
+    for y in range(3):
+        for x in range(3):
+            v = 0.1 + cd[y, x]
+            if y >= 1 and x >= 1:
+                v += -0.5 * cd[y - 1, x - 1]
+            a[y, x] = max(float(np.float32(0.1)) - 0.1 + v, 0.0)
+    expect = np.full((3, 3), float(np.float32(-0.3)))
+    for y in range(3):
+        for x in range(2):
+            expect[y, x] += 2.0 * a[y, x + 1]
+    np.testing.assert_allclose(logits[0], expect, atol=1e-7)
+
+
+def test_crop_equals_full_image():
+    """Fully convolutional: any crop (with the halo handled inside) equals the same pixels
+    of the whole-image evaluation, including at the image borders."""
+    chs = (2, 6, 6, 6, 1)
+    c = synth.contone_image(40, 37, seed=4)
+    ws, bs = synth.he_normal_policy(chs, seed=5)
+    full, _, _ = O.forward(c, ws, bs, noise_seed=9, image=1)
+    for (y0, x0, rh, rw) in [(0, 0, 7, 9), (10, 12, 8, 5), (33, 30, 7, 7), (0, 20, 40, 3)]:
+        part, _, _ = O.forward(c, ws, bs, noise_seed=9, image=1, region=(y0, x0, rh, rw))
+        np.testing.assert_allclose(part[0], full[0, y0:y0 + rh, x0:x0 + rw], rtol=1e-13, atol=1e-13)
+
+
+def test_bf16_rounding_matches_torch():
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.normal(0, 1, 2000), rng.normal(0, 1e-3, 500), [1.00390625, 1.01171875, -3.0, 0.0]])
+    ref = torch.from_numpy(xs.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([O.round_bf16(float(np.float32(x))) for x in xs])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_e4m3_rounding_matches_torch():
+    rng = np.random.default_rng(1)
+    xs = np.concatenate([rng.normal(0, 30, 2000), rng.normal(0, 0.01, 500), [448.0, 500.0, -1e4, 2 ** -9, 3 * 2 ** -10]])
+    xs32 = xs.astype(np.float32)
+    # torch's float8_e4m3fn cast is round-to-nearest-even; saturate first (torch does not saturate)
+    ref = torch.from_numpy(np.clip(xs32, -448, 448)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    got = np.array([O.round_e4m3(float(x)) for x in xs32])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_quantised_forms_stay_close():
+    chs = (2, 16, 16, 16, 1)
+    c = synth.contone_image(20, 20, seed=6)
+    ws, bs = synth.he_normal_policy(chs, seed=7)
+    _, p, _ = O.forward(c, ws, bs, noise_seed=1)
+    _, pb, _ = O.forward(c, ws, bs, noise_seed=1, quant=1)
+    assert 0 < np.abs(pb - p).max() < 2e-2
+    _, p8, _ = O.forward(c, ws, bs, noise_seed=1, quant=2, act_scale=[1.0, 4 / 448, 4 / 448, 1.0])
+    assert 0 < np.abs(p8 - p).max() < 1e-1
+
+
+def test_sampling_rules():
+    h, w = 16, 16
+    p = np.linspace(0, 1, h * w).reshape(1, h, w)
+    p[0, 3, 3] = 0.5
+    bits, u = O.sample(p, h, w, (0, 0, h, w), mode=0, seed=0)
+    assert set(np.unique(bits)) <= {0, 1}
+    np.testing.assert_array_equal(bits, (p[0] > 0.5).astype(np.uint8))
+    assert bits[3, 3] == 0                                   # tie p = 0.5 -> 0
+    bits, u = O.sample(p, h, w, (0, 0, h, w), mode=1, seed=5)
+    np.testing.assert_array_equal(u, O.uniform_map(5, 0, 1, h, w))
+    np.testing.assert_array_equal(bits, (u < p[0]).astype(np.uint8))
+    # Bernoulli frequencies follow p
+    pp = np.full((1, 128, 128), 0.3)
+    b, _ = O.sample(pp, 128, 128, (0, 0, 128, 128), 1, 9)
+    assert abs(b.mean() - 0.3) < 5 * np.sqrt(0.21 / b.size)
+
+
+def test_softmax_levels_sampling():
+    K, h, w = 4, 64, 64
+    rng = np.random.default_rng(3)
+    lg = rng.normal(size=(K, h, w))
+    q = np.exp(lg) / np.exp(lg).sum(0)
+    lev, u = O.sample(q, h, w, (0, 0, h, w), 1, 2)
+    cdf = np.cumsum(q, 0)
+    ref = np.argmax(u[None] < cdf, axis=0)
+    np.testing.assert_array_equal(lev, ref)
+    lev0, _ = O.sample(q, h, w, (0, 0, h, w), 0, 2)
+    np.testing.assert_array_equal(lev0, np.argmax(q, 0))
