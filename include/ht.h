@@ -1,0 +1,229 @@
+/*
+ * ht.h -- C ABI of the GB300 halftoning library (libht.so).
+ *
+ * The library implements the data-parallel hot path of "Efficient Halftoning
+ * via Deep Reinforcement Learning" (arXiv 2304.12152):
+ *   - one-shot halftone generation (Algorithm 1, TEST step): a fully
+ *     convolutional policy maps the state s = concat(c, z) (Sec. III, "State")
+ *     to per-pixel action probabilities pi_a(h_a = 1) (Eq. independent), which
+ *     are thresholded at 0.5 or Bernoulli-sampled and bit-packed;
+ *   - the training-time reward R = -MSE(HVS(h), HVS(c)) + w_s CSSIM(h, c)
+ *     (Eq. reward, Eq. final_reward, Eq. cssim), the per-pixel toggle deltas of
+ *     the local-expectation gradient (Eq. le, Eq. marl, Sec. III-C) and the
+ *     anisotropy-suppressing loss on the power spectrum (Eqs. psd, rapsd,
+ *     anis, as; Sec. IV);
+ *   - one training iteration's forward and backward (Algorithm 1, TRAIN step).
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented "device" must point into memory of the current CUDA
+ *     device; "host" pointers are read before the call returns.  The caller
+ *     owns every buffer it passes; the library owns ht_policy / ht_train
+ *     objects and the device workspaces inside them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated; argument
+ *     errors are detected on the host before any launch and return
+ *     HT_ERR_INVALID_ARG / HT_ERR_UNSUPPORTED with nothing launched.
+ *   - A kernel whose bounded internal wait expires records HT_ERR_TIMEOUT in
+ *     a device flag; ht_sync() reports it (and any CUDA error).
+ *   - ht_last_error() returns a thread-local description of the last failure.
+ *
+ * Data layouts:
+ *   - contone image: float32 in [0, 1], row-major [h][pitch] (pitch >= w, in
+ *     elements), device memory.
+ *   - halftone (sigmoid head): 1 bit per pixel, LSB-first in uint32 words,
+ *     row-major with ht_bits_row_words(w, 1) words per row; bit (x % 32) of
+ *     word (y * words + x / 32) is h at (y, x).  K-level head: 2 bits per pixel
+ *     (levels 0..3), 16 pixels per word, bits 2(x % 16)..2(x % 16)+1.  Padding
+ *     bits past w are zero.
+ *   - probability map (optional): float32 [K][h][w] (K = 1 for sigmoid).
+ *   - weights: canonical float32 OIHW per layer, layers concatenated, 3x3
+ *     kernels; biases float32, concatenated.
+ *
+ * Random numbers: the noise channel z and the Bernoulli uniforms u come from
+ * Philox4x32-10 (Salmon et al., SC'11) with key (seed lo32, seed hi32),
+ * counter (g / 4, image, stream, 0) and output lane g % 4, where g = y*w + x
+ * and image is the position in the call's image array; stream 0 = z,
+ * stream 1 + s = Bernoulli sample s; u = (x >> 8) * 2^-24.
+ */
+#ifndef HT_H_
+#define HT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HT_MAX_LAYERS 16
+#define HT_MAX_CHANNELS 64
+
+typedef enum {
+    HT_OK = 0,
+    HT_ERR_INVALID_ARG = 1,
+    HT_ERR_UNSUPPORTED = 2,
+    HT_ERR_OOM = 3,
+    HT_ERR_CUDA = 4,
+    HT_ERR_TIMEOUT = 5
+} ht_status;
+
+typedef enum { HT_FP32 = 0, HT_BF16 = 1, HT_FP8_E4M3 = 2 } ht_precision;
+typedef enum { HT_HEAD_SIGMOID = 0, HT_HEAD_SOFTMAX = 1 } ht_head;
+typedef enum { HT_MODE_THRESHOLD = 0, HT_MODE_BERNOULLI = 1 } ht_mode;
+
+/* Policy network (Sec. III "Agents"; Sec. VI-A): n_layers 3x3 convolutions,
+ * stride 1, zero padding 1, ReLU between layers, channels[0] == 2 (c and z),
+ * channels[n_layers] == 1 with head SIGMOID or == 4 with head SOFTMAX
+ * (4 output levels {0, 1/3, 2/3, 1}, Sec. VI-E).  Hidden widths <= 64.
+ * precision: FP32 = plain CUDA-core form; BF16 / FP8_E4M3 = tensor-core form
+ * (hidden widths must then all be 64; FP32 accumulation). */
+typedef struct {
+    int n_layers;
+    int channels[HT_MAX_LAYERS + 1];
+    int head;
+    int precision;
+} ht_policy_desc;
+
+typedef struct {
+    const float *contone; /* device, [h][pitch] */
+    int h, w, pitch;
+} ht_image;
+
+typedef struct ht_policy ht_policy;
+
+/* Create a policy on the current device from host weights / biases (see the
+ * layout above).  Copies and packs them; the caller keeps ownership of its
+ * arrays.  Errors: INVALID_ARG (shape), UNSUPPORTED (precision / widths),
+ * OOM, CUDA. */
+ht_status ht_create_policy(const ht_policy_desc *desc, const float *weights_host,
+                           const float *biases_host, ht_policy **out);
+ht_status ht_destroy_policy(ht_policy *p);
+
+/* Replace the weights from device float32 arrays (same layout) and repack them
+ * on `stream` (used after each optimiser step in training). */
+ht_status ht_policy_set_weights(ht_policy *p, const float *weights_dev, const float *biases_dev,
+                                void *stream);
+
+/* FP8 form only: per-layer static activation scales (host, n_layers values;
+ * entry l scales the input activations of layer l, entries 0 and n_layers-1
+ * are ignored).  Each hidden layer's input a is stored as e4m3(a / s_l). */
+ht_status ht_policy_set_act_scales(ht_policy *p, const float *scales_host, int n);
+
+/* Total parameter count and FLOPs per output pixel (2 x MACs). */
+int64_t ht_policy_num_params(const ht_policy *p);
+int64_t ht_policy_flops_per_px(const ht_policy *p);
+
+/* uint32 words per halftone row for width w and the given head. */
+int ht_bits_row_words(int w, int head);
+
+/* One-shot halftoning (Algorithm 1, TEST step; Eq. independent).
+ * imgs: host array of n image descriptors (device pixel pointers).
+ * mode: HT_MODE_THRESHOLD (h = [p > 0.5]; softmax head: argmax) or
+ *       HT_MODE_BERNOULLI (h = [u < p]; softmax head: smallest k with
+ *       u < sum_{j<=k} q_j), u from Philox stream 1 with `seed`; z always
+ *       from stream 0 with `seed`.
+ * out_bits: host array of n device pointers, each h * ht_bits_row_words words.
+ * out_prob: NULL or host array of n device pointers (NULL entries allowed),
+ *           each float [K][h][w].
+ * Images may differ in size (1 <= h, w <= 16384). */
+ht_status ht_halftone(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
+                      uint32_t *const *out_bits, float *const *out_prob, void *stream);
+
+/* Reward options (Eq. final_reward, Sec. V): HVS = normalised Gaussian
+ * (sigma_hvs, 2r+1 taps; the Gaussian sigma-2 filter of Sec. VI-B stands in
+ * for the Nasanen model), SSIM window = normalised Gaussian (sigma_ssim,
+ * 2r+1 taps), contrast k, weight w_s, SSIM constants c1, c2, radius r (<= 7).
+ * All windows are "valid" (Sec. VI-A): outputs on (h-2r) x (w-2r). */
+typedef struct {
+    float sigma_hvs, sigma_ssim, k_contrast, w_s, c1, c2;
+    int radius;
+} ht_reward_opts;
+
+/* Fill opts with the paper's defaults: 2.0, 1.5, 2, 0.06, 1e-4, 9e-4, 5. */
+void ht_reward_opts_default(ht_reward_opts *opts);
+
+/* Reward of n (contone, halftone) pairs (binary halftones only).
+ * out: device array of 4*n doubles: MSE, SSIM (mean map), CSSIM, R per image.
+ * Requires h, w >= 2r + 1. */
+ht_status ht_reward(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts *opts,
+                    double *out, void *stream);
+
+/* Toggle deltas of the local-expectation gradient (Eq. le, Sec. III-C):
+ * dR[a] = R(h with h_a = 1) - R(h with h_a = 0) for every pixel a.
+ * dR: host array of n device pointers, each float [h][w]. */
+ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, int n,
+                          const ht_reward_opts *opts, float *const *dR, void *stream);
+
+/* Anisotropy-suppressing loss of n_patches probability maps q (device float
+ * [n_patches][n][n], n a power of two in [8, 1024]) (Eqs. psd, as; Sec. IV).
+ * mode 0: sum over rings (width 1, DC excluded) of squared deviations from
+ *         the ring mean (Eq. as);
+ * mode 1: mean over n_rad radial bins of the variance over n_ang angular bins
+ *         of the bin means divided by the squared ring mean.
+ * out_loss: device, n_patches doubles.  grad: NULL or device float
+ * [n_patches][n][n], receives dL/dq. */
+ht_status ht_anisotropy_loss(const float *q, int n_patches, int n, int mode, int n_rad, int n_ang,
+                             double *out_loss, float *grad, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Training (Algorithm 1, TRAIN step).                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int max_crops;        /* B: crops per step */
+    int crop_h, crop_w;   /* crop size (all crops the same size) */
+    int n_gray;           /* constant-gray patches per step (Sec. IV), may be 0 */
+    int gray_n;           /* gray patch side (power of two) */
+    int n_samples;        /* S: Bernoulli samples per crop */
+    int las_mode;         /* 0 = Eq. (as), 1 = binned form */
+    int n_rad, n_ang;     /* binned form */
+    float w_a;            /* anisotropy weight (paper: 0.002) */
+    ht_reward_opts reward;
+} ht_train_desc;
+
+typedef struct ht_train ht_train;
+
+ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out);
+ht_status ht_train_destroy(ht_train *t);
+
+/* Forward part of one iteration: policy forward on the crops and the gray
+ * patches (levels: host array of n_gray floats), S samples per crop, reward and
+ * toggle deltas per sample, L_MARL (Eq. marl, averaged over crops and samples)
+ * and w_a * L_AS (averaged over patches).  Keeps what the backward needs.
+ * losses_host (host, 4 doubles, written after the call synchronises `stream`):
+ * L_total, L_MARL, L_AS, mean reward R. */
+ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const float *gray_levels,
+                            uint64_t seed, double *losses_host, void *stream);
+
+/* Backward of the last forward: dL_total/dW and dL_total/db (device float
+ * arrays in the canonical layout, overwritten). */
+ht_status ht_train_step_bwd(ht_train *t, float *grad_w, float *grad_b, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Kernel timing (library's own instrumentation).                            */
+/* Between ht_profile_begin and ht_profile_end every hot kernel launch is    */
+/* bracketed by CUDA events on the stream it is launched on; end             */
+/* synchronises the device and returns per-kernel launch counts and summed    */
+/* device time.  out: host array of max entries; *n_out = entries written.   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} ht_kernel_stat;
+
+ht_status ht_profile_begin(void);
+ht_status ht_profile_end(ht_kernel_stat *out, int max, int *n_out);
+
+/* Synchronise `stream` and report device-side errors (timeouts, faults). */
+ht_status ht_sync(void *stream);
+
+/* Thread-local description of the last error ("" if none). */
+const char *ht_last_error(void);
+
+/* Library version string. */
+const char *ht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HT_H_ */

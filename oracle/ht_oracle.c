@@ -515,7 +515,9 @@ int or_toggle_delta(const float *c, int cpitch, const uint8_t *hb, int hpitch, i
 /*     A(rho) = 1/(n_rho - 1) sum (P(f) - Pbar_rho)^2 / Pbar_rho^2             */
 /*   Binned form (32 radial x 16 angular bins): radial bin floor(32 r/(n/2))   */
 /*   for 0 < r < n/2; angular bin floor(16 theta/pi), theta = atan2(u, v) mod  */
-/*   pi.  Per radial bin: a_k = mean of P over angular bin k, m = mean of P    */
+/*   pi (a direction exactly on a bin edge -- 0, 45, 90, 135 degrees -- is in  */
+/*   the bin it opens).  Per radial bin: a_k = mean of P over angular bin k,   */
+/*   m = mean of P                                                            */
 /*   over the whole radial bin, K = number of non-empty angular bins;          */
 /*     A_bin(rho) = 1/(K-1) sum_k (a_k - m)^2 / m^2 ;                          */
 /*     L_bin = mean over radial bins with K >= 2 of A_bin.                     */
@@ -632,11 +634,20 @@ int or_anisotropy_loss(const double *q, int n, int mode, int n_rad, int n_ang,
                 if (r <= 0.0 || r >= half) continue;
                 int br = (int)floor(r / half * n_rad);
                 if (br >= n_rad) br = n_rad - 1;
-                double th = atan2((double)u, (double)v);
-                if (th < 0) th += M_PI;
-                if (th >= M_PI) th -= M_PI;
-                int bt = (int)floor(th / M_PI * n_ang);
-                if (bt >= n_ang) bt = n_ang - 1;
+                int bt;
+                if ((n_ang % 4) == 0 && (u == 0 || v == 0 || u == v || u == -v)) {
+                    /* directions on a bin edge (0, 45, 90, 135 degrees) open their bin */
+                    if (u == 0) bt = 0;
+                    else if (v == 0) bt = n_ang / 2;
+                    else if (u == v) bt = n_ang / 4;
+                    else bt = 3 * n_ang / 4;
+                } else {
+                    double th = atan2((double)u, (double)v);
+                    if (th < 0) th += M_PI;
+                    if (th >= M_PI) th -= M_PI;
+                    bt = (int)floor(th / M_PI * n_ang);
+                    if (bt >= n_ang) bt = n_ang - 1;
+                }
                 bidx[k] = br * n_ang + bt;
                 bsum[br * n_ang + bt] += P[k];
                 bcnt[br * n_ang + bt] += 1;

@@ -1,0 +1,184 @@
+"""Python binding of the halftoning library: argument marshalling only.
+
+Every step of the path runs in libht.so's CUDA kernels; torch provides device
+memory and the current stream.  Function names follow include/ht.h.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import check
+
+
+def _stream(stream: Optional[torch.cuda.Stream] = None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _images(contones: Sequence[torch.Tensor]):
+    arr = (N.Image * len(contones))()
+    for i, c in enumerate(contones):
+        if not (c.is_cuda and c.dtype == torch.float32 and c.dim() == 2 and c.stride(1) == 1):
+            raise ValueError("contone images must be 2-D float32 CUDA tensors with unit column stride")
+        arr[i] = N.Image(c.data_ptr(), c.shape[0], c.shape[1], c.stride(0))
+    return arr
+
+
+def _ptrs(ts: Sequence[Optional[torch.Tensor]]):
+    return (C.c_void_p * len(ts))(*[(t.data_ptr() if t is not None else None) for t in ts])
+
+
+def bits_row_words(w: int, head: int = N.HT_HEAD_SIGMOID) -> int:
+    return N.load().ht_bits_row_words(w, head)
+
+
+def reward_opts(**kw) -> N.RewardOpts:
+    o = N.RewardOpts()
+    N.load().ht_reward_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Policy:
+    """ht_policy: owns packed weights and the forward workspace."""
+
+    def __init__(self, channels: Sequence[int], weights: Sequence[np.ndarray], biases: Sequence[np.ndarray],
+                 head: int = N.HT_HEAD_SIGMOID, precision: int = N.HT_FP32):
+        L = N.load()
+        d = N.PolicyDesc()
+        d.n_layers = len(channels) - 1
+        for i, c in enumerate(channels):
+            d.channels[i] = int(c)
+        d.head, d.precision = head, precision
+        w = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).ravel() for x in weights]))
+        b = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).ravel() for x in biases]))
+        h = C.c_void_p()
+        check(L.ht_create_policy(C.byref(d), w.ctypes.data, b.ctypes.data, C.byref(h)))
+        self._h = h
+        self.channels = tuple(int(c) for c in channels)
+        self.head, self.precision = head, precision
+        self.K = self.channels[-1]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.load().ht_destroy_policy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def num_params(self) -> int:
+        return N.load().ht_policy_num_params(self._h)
+
+    def flops_per_px(self) -> int:
+        return N.load().ht_policy_flops_per_px(self._h)
+
+    def set_act_scales(self, scales: Sequence[float]) -> None:
+        a = np.ascontiguousarray(scales, np.float32)
+        check(N.load().ht_policy_set_act_scales(self._h, a.ctypes.data, a.size))
+
+    def set_weights(self, w_dev: torch.Tensor, b_dev: torch.Tensor, stream=None) -> None:
+        check(N.load().ht_policy_set_weights(self._h, w_dev.data_ptr(), b_dev.data_ptr(), _stream(stream)))
+
+    def alloc_bits(self, h: int, w: int, device="cuda") -> torch.Tensor:
+        words = bits_row_words(w, self.head)
+        return torch.empty((h, words), dtype=torch.int32, device=device)
+
+    def halftone_into(self, contones: Sequence[torch.Tensor], bits: Sequence[torch.Tensor], mode: int, seed: int,
+                      probs: Optional[Sequence[Optional[torch.Tensor]]] = None, stream=None) -> None:
+        imgs = _images(contones)
+        check(N.load().ht_halftone(self._h, imgs, len(contones), mode, seed, _ptrs(bits),
+                                   _ptrs(probs) if probs is not None else None, _stream(stream)))
+
+    def halftone(self, contones: Sequence[torch.Tensor], mode: int = N.HT_MODE_THRESHOLD, seed: int = 0,
+                 want_prob: bool = False, stream=None):
+        bits = [self.alloc_bits(c.shape[0], c.shape[1], c.device) for c in contones]
+        probs = None
+        if want_prob:
+            probs = [torch.empty((self.K, c.shape[0], c.shape[1]), dtype=torch.float32, device=c.device)
+                     for c in contones]
+        self.halftone_into(contones, bits, mode, seed, probs, stream)
+        return bits, probs
+
+
+def reward(contones: Sequence[torch.Tensor], bits: Sequence[torch.Tensor], opts: Optional[N.RewardOpts] = None,
+           out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    o = opts or reward_opts()
+    if out is None:
+        out = torch.empty((len(contones), 4), dtype=torch.float64, device=contones[0].device)
+    check(N.load().ht_reward(_images(contones), _ptrs(bits), len(contones), C.byref(o), out.data_ptr(),
+                             _stream(stream)))
+    return out
+
+
+def toggle_delta(contones: Sequence[torch.Tensor], bits: Sequence[torch.Tensor],
+                 opts: Optional[N.RewardOpts] = None, stream=None) -> List[torch.Tensor]:
+    o = opts or reward_opts()
+    dR = [torch.empty_like(c) for c in contones]
+    check(N.load().ht_toggle_delta(_images(contones), _ptrs(bits), len(contones), C.byref(o), _ptrs(dR),
+                                   _stream(stream)))
+    return dR
+
+
+def anisotropy_loss(q: torch.Tensor, mode: int = 0, n_rad: int = 32, n_ang: int = 16, grad: bool = False,
+                    stream=None) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+    if q.dim() == 2:
+        q = q[None]
+    q = q.contiguous()
+    P, n, _ = q.shape
+    loss = torch.empty(P, dtype=torch.float64, device=q.device)
+    g = torch.empty_like(q) if grad else None
+    check(N.load().ht_anisotropy_loss(q.data_ptr(), P, n, mode, n_rad, n_ang, loss.data_ptr(),
+                                      g.data_ptr() if g is not None else None, _stream(stream)))
+    return loss, g
+
+
+def profile_begin() -> None:
+    check(N.load().ht_profile_begin())
+
+
+def profile_end() -> dict:
+    """{kernel name: (launches, total device ms)} since profile_begin (synchronises)."""
+    arr = (N.KernelStat * 32)()
+    n = C.c_int(0)
+    check(N.load().ht_profile_end(arr, 32, C.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def sync(stream=None) -> None:
+    check(N.load().ht_sync(_stream(stream)))
+
+
+def unpack_bits(bits: torch.Tensor, h: int, w: int, head: int = N.HT_HEAD_SIGMOID) -> np.ndarray:
+    """Host-side view of a packed halftone as uint8 levels [h][w] (tests and tools)."""
+    b = bits.detach().cpu().numpy().view(np.uint32)
+    if head == N.HT_HEAD_SIGMOID:
+        x = np.arange(w)
+        return ((b[:, x // 32] >> (x % 32).astype(np.uint32)) & 1).astype(np.uint8)
+    x = np.arange(w)
+    return ((b[:, x // 16] >> (2 * (x % 16)).astype(np.uint32)) & 3).astype(np.uint8)
+
+
+def pack_bits(levels: np.ndarray, head: int = N.HT_HEAD_SIGMOID) -> np.ndarray:
+    """Inverse of unpack_bits (host), returns int32 words [h][words]."""
+    h, w = levels.shape
+    per = 32 if head == N.HT_HEAD_SIGMOID else 16
+    shift = 1 if head == N.HT_HEAD_SIGMOID else 2
+    words = (w + per - 1) // per
+    out = np.zeros((h, words), dtype=np.uint64)
+    for x in range(w):
+        out[:, x // per] |= levels[:, x].astype(np.uint64) << np.uint64(shift * (x % per))
+    return out.astype(np.uint32).view(np.int32)

@@ -1,0 +1,409 @@
+// api.cu -- the C ABI declared in include/ht.h: argument validation, object
+// lifetime, workspaces and dispatch to the kernels of the other sources.
+#include <stdarg.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "ht_internal.cuh"
+
+namespace {
+thread_local char g_err[1024] = "";
+std::mutex g_flag_mu;
+int *g_flags[64] = {nullptr};   // per-device error flag (device memory)
+}  // namespace
+
+void ht_set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int *ht_device_error_flag()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(g_flag_mu);
+    if (!g_flags[dev]) {
+        int *p = nullptr;
+        if (cudaMalloc((void **)&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+        g_flags[dev] = p;
+    }
+    return g_flags[dev];
+}
+
+namespace {
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_ev_pool;
+const char *const g_kernel_names[HTK_COUNT] = {"k_first_tc",   "k_conv_tc_bf16", "k_conv_tc_fp8", "k_head_tc",
+                                               "k_conv3x3_fp32", "k_head_fp32",  "k_reward",      "k_toggle_delta",
+                                               "k_spectrum",   "k_train"};
+
+cudaEvent_t pool_event()
+{
+    if (!g_ev_pool.empty()) {
+        cudaEvent_t e = g_ev_pool.back();
+        g_ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+void ht_prof_start(int kid, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!g_prof_on) return;
+    ProfRec r;
+    r.kid = kid;
+    r.a = pool_event();
+    r.b = pool_event();
+    cudaEventRecord(r.a, s);
+    g_prof.push_back(r);
+}
+
+void ht_prof_stop(cudaStream_t s)
+{
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!g_prof_on || g_prof.empty()) return;
+    cudaEventRecord(g_prof.back().b, s);
+}
+
+extern "C" {
+
+ht_status ht_profile_begin(void)
+{
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    for (auto &r : g_prof) {
+        g_ev_pool.push_back(r.a);
+        g_ev_pool.push_back(r.b);
+    }
+    g_prof.clear();
+    g_prof_on = true;
+    return HT_OK;
+}
+
+ht_status ht_profile_end(ht_kernel_stat *out, int max, int *n_out)
+{
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof_on = false;
+    HT_CUDA_TRY(cudaDeviceSynchronize());
+    int64_t cnt[HTK_COUNT] = {0};
+    double ms[HTK_COUNT] = {0};
+    for (auto &r : g_prof) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            cnt[r.kid] += 1;
+            ms[r.kid] += t;
+        }
+        g_ev_pool.push_back(r.a);
+        g_ev_pool.push_back(r.b);
+    }
+    g_prof.clear();
+    int n = 0;
+    for (int k = 0; k < HTK_COUNT; ++k) {
+        if (!cnt[k]) continue;
+        if (out && n < max) {
+            memset(out[n].name, 0, sizeof(out[n].name));
+            strncpy(out[n].name, g_kernel_names[k], sizeof(out[n].name) - 1);
+            out[n].launches = cnt[k];
+            out[n].total_ms = ms[k];
+        }
+        ++n;
+    }
+    if (n_out) *n_out = n < max ? n : max;
+    return HT_OK;
+}
+
+const char *ht_last_error(void) { return g_err; }
+const char *ht_version(void) { return "ht 0.1 (sm_103a)"; }
+
+int ht_bits_row_words(int w, int head)
+{
+    if (w <= 0) return 0;
+    return head == HT_HEAD_SOFTMAX ? (w + 15) / 16 : (w + 31) / 32;
+}
+
+void ht_reward_opts_default(ht_reward_opts *o)
+{
+    if (!o) return;
+    o->sigma_hvs = 2.0f;
+    o->sigma_ssim = 1.5f;
+    o->k_contrast = 2.0f;
+    o->w_s = 0.06f;
+    o->c1 = 0.01f * 0.01f;
+    o->c2 = 0.03f * 0.03f;
+    o->radius = 5;
+}
+
+static ht_status validate_desc(const ht_policy_desc *d)
+{
+    HT_CHECK_ARG(d != nullptr, "null policy descriptor");
+    HT_CHECK_ARG(d->n_layers >= 2 && d->n_layers <= HT_MAX_LAYERS, "n_layers must be in [2, %d]", HT_MAX_LAYERS);
+    HT_CHECK_ARG(d->channels[0] == 2, "channels[0] must be 2 (contone and noise)");
+    for (int l = 1; l < d->n_layers; ++l)
+        HT_CHECK_ARG(d->channels[l] >= 1 && d->channels[l] <= HT_MAX_CHANNELS, "hidden width %d out of range",
+                     d->channels[l]);
+    if (d->head == HT_HEAD_SIGMOID) {
+        HT_CHECK_ARG(d->channels[d->n_layers] == 1, "sigmoid head needs 1 output channel");
+    } else if (d->head == HT_HEAD_SOFTMAX) {
+        HT_CHECK_ARG(d->channels[d->n_layers] == 4, "softmax head needs 4 output channels");
+    } else {
+        HT_CHECK_ARG(false, "unknown head %d", d->head);
+    }
+    HT_CHECK_ARG(d->precision == HT_FP32 || d->precision == HT_BF16 || d->precision == HT_FP8_E4M3,
+                 "unknown precision %d", d->precision);
+    if (d->precision != HT_FP32) {
+        if (d->n_layers < 3) {
+            ht_set_error("tensor-core forms need at least one 64 -> 64 layer");
+            return HT_ERR_UNSUPPORTED;
+        }
+        for (int l = 1; l < d->n_layers; ++l)
+            if (d->channels[l] != 64) {
+                ht_set_error("tensor-core forms need every hidden width = 64");
+                return HT_ERR_UNSUPPORTED;
+            }
+    }
+    return HT_OK;
+}
+
+ht_status ht_create_policy(const ht_policy_desc *desc, const float *weights_host, const float *biases_host,
+                           ht_policy **out)
+{
+    HT_CHECK_ARG(out != nullptr, "null output pointer");
+    *out = nullptr;
+    ht_status st = validate_desc(desc);
+    if (st != HT_OK) return st;
+    HT_CHECK_ARG(weights_host && biases_host, "weights and biases are required");
+    ht_policy *p = new ht_policy();
+    p->L = desc->n_layers;
+    memcpy(p->ch, desc->channels, sizeof(p->ch));
+    p->head = desc->head;
+    p->K = desc->channels[desc->n_layers];
+    p->prec = desc->precision;
+    cudaGetDevice(&p->device);
+    p->n_w = p->n_b = 0;
+    for (int l = 0; l < p->L; ++l) {
+        p->w_off[l] = p->n_w;
+        p->b_off[l] = p->n_b;
+        p->n_w += (int64_t)p->ch[l + 1] * p->ch[l] * 9;
+        p->n_b += p->ch[l + 1];
+        p->act_scale[l] = 1.f;
+    }
+    cudaError_t e = cudaMalloc((void **)&p->d_w, sizeof(float) * p->n_w);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_b, sizeof(float) * p->n_b);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_w, weights_host, sizeof(float) * p->n_w, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_b, biases_host, sizeof(float) * p->n_b, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        ht_set_error("policy upload: %s", cudaGetErrorString(e));
+        ht_destroy_policy(p);
+        return e == cudaErrorMemoryAllocation ? HT_ERR_OOM : HT_ERR_CUDA;
+    }
+    if (p->prec != HT_FP32) {
+        st = ht_pack_tc_weights(p, 0);
+        if (st != HT_OK) {
+            ht_destroy_policy(p);
+            return st;
+        }
+    }
+    *out = p;
+    return HT_OK;
+}
+
+ht_status ht_destroy_policy(ht_policy *p)
+{
+    if (!p) return HT_OK;
+    cudaFree(p->d_w);
+    cudaFree(p->d_b);
+    cudaFree(p->d_wpack);
+    cudaFree(p->d_wscale);
+    cudaFree(p->d_ws);
+    delete p;
+    return HT_OK;
+}
+
+ht_status ht_policy_set_weights(ht_policy *p, const float *weights_dev, const float *biases_dev, void *stream)
+{
+    HT_CHECK_ARG(p && weights_dev && biases_dev, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    HT_CUDA_TRY(cudaMemcpyAsync(p->d_w, weights_dev, sizeof(float) * p->n_w, cudaMemcpyDeviceToDevice, s));
+    HT_CUDA_TRY(cudaMemcpyAsync(p->d_b, biases_dev, sizeof(float) * p->n_b, cudaMemcpyDeviceToDevice, s));
+    if (p->prec != HT_FP32) return ht_pack_tc_weights(p, s);
+    return HT_OK;
+}
+
+ht_status ht_policy_set_act_scales(ht_policy *p, const float *scales_host, int n)
+{
+    HT_CHECK_ARG(p && scales_host, "null argument");
+    HT_CHECK_ARG(n == p->L, "expected %d scales", p->L);
+    for (int l = 0; l < n; ++l) {
+        HT_CHECK_ARG(scales_host[l] > 0.f && isfinite(scales_host[l]), "scale %d must be positive", l);
+        p->act_scale[l] = scales_host[l];
+    }
+    return HT_OK;
+}
+
+int64_t ht_policy_num_params(const ht_policy *p) { return p ? p->n_w + p->n_b : 0; }
+
+int64_t ht_policy_flops_per_px(const ht_policy *p)
+{
+    if (!p) return 0;
+    int64_t f = 0;
+    for (int l = 0; l < p->L; ++l) f += 2 * 9 * (int64_t)p->ch[l] * p->ch[l + 1];
+    return f;
+}
+
+}  // extern "C"
+
+ht_status ht_policy_ensure_ws(ht_policy *p, size_t bytes)
+{
+    if (bytes <= p->ws_bytes) return HT_OK;
+    if (p->d_ws) {
+        HT_CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(p->d_ws);
+        p->d_ws = nullptr;
+        p->ws_bytes = 0;
+    }
+    HT_CUDA_TRY(cudaMalloc(&p->d_ws, bytes));
+    p->ws_bytes = bytes;
+    return HT_OK;
+}
+
+extern "C" {
+
+static ht_status validate_images(const ht_image *imgs, int n, int min_side)
+{
+    HT_CHECK_ARG(imgs != nullptr && n >= 1, "need at least one image");
+    for (int i = 0; i < n; ++i) {
+        HT_CHECK_ARG(imgs[i].contone != nullptr, "image %d: null contone", i);
+        HT_CHECK_ARG(imgs[i].h >= min_side && imgs[i].w >= min_side && imgs[i].h <= 16384 && imgs[i].w <= 16384,
+                     "image %d: size %dx%d outside [%d, 16384]", i, imgs[i].h, imgs[i].w, min_side);
+        HT_CHECK_ARG(imgs[i].pitch >= imgs[i].w, "image %d: pitch < width", i);
+    }
+    return HT_OK;
+}
+
+ht_status ht_halftone(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed, uint32_t *const *out_bits,
+                      float *const *out_prob, void *stream)
+{
+    HT_CHECK_ARG(p != nullptr, "null policy");
+    ht_status st = validate_images(imgs, n, 1);
+    if (st != HT_OK) return st;
+    HT_CHECK_ARG(mode == HT_MODE_THRESHOLD || mode == HT_MODE_BERNOULLI, "unknown mode %d", mode);
+    HT_CHECK_ARG(out_bits != nullptr, "null output array");
+    for (int i = 0; i < n; ++i) HT_CHECK_ARG(out_bits[i] != nullptr, "image %d: null bits pointer", i);
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t b = p->prec == HT_FP32 ? ht_fp32_ws_bytes(p, imgs[i].h, imgs[i].w)
+                                            : ht_tc_ws_bytes(p, imgs[i].h, imgs[i].w);
+        need = b > need ? b : need;
+    }
+    st = ht_policy_ensure_ws(p, need);
+    if (st != HT_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        float *prob = out_prob ? out_prob[i] : nullptr;
+        if (p->prec == HT_FP32) {
+            const size_t half = ht_fp32_ws_bytes(p, imgs[i].h, imgs[i].w) / 2;
+            st = ht_run_fp32(p, imgs[i], (uint32_t)i, mode, seed, out_bits[i], prob, (float *)p->d_ws,
+                             (float *)((char *)p->d_ws + half), s);
+        } else {
+            st = ht_run_tc(p, imgs[i], (uint32_t)i, mode, seed, out_bits[i], prob, s);
+        }
+        if (st != HT_OK) return st;
+    }
+    return HT_OK;
+}
+
+static ht_status validate_opts(const ht_reward_opts *o)
+{
+    HT_CHECK_ARG(o != nullptr, "null reward options");
+    HT_CHECK_ARG(o->radius >= 1 && o->radius <= 7, "radius must be in [1, 7]");
+    HT_CHECK_ARG(o->sigma_hvs > 0 && o->sigma_ssim > 0, "window sigmas must be positive");
+    return HT_OK;
+}
+
+ht_status ht_reward(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts *opts, double *out,
+                    void *stream)
+{
+    ht_status st = validate_opts(opts);
+    if (st != HT_OK) return st;
+    st = validate_images(c, n, 2 * opts->radius + 1);
+    if (st != HT_OK) return st;
+    HT_CHECK_ARG(bits && out, "null argument");
+    for (int i = 0; i < n; ++i) HT_CHECK_ARG(bits[i] != nullptr, "image %d: null bits", i);
+    return ht_reward_launch(c, bits, n, *opts, out, (cudaStream_t)stream);
+}
+
+ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts *opts,
+                          float *const *dR, void *stream)
+{
+    ht_status st = validate_opts(opts);
+    if (st != HT_OK) return st;
+    st = validate_images(c, n, 2 * opts->radius + 1);
+    if (st != HT_OK) return st;
+    HT_CHECK_ARG(bits && dR, "null argument");
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        HT_CHECK_ARG(bits[i] && dR[i], "image %d: null pointer", i);
+        const size_t f = ht_toggle_scratch_floats(c[i].h, c[i].w, opts->radius);
+        need = f > need ? f : need;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float *scratch = nullptr;
+    HT_CUDA_TRY(cudaMallocAsync((void **)&scratch, need * sizeof(float), s));
+    st = ht_toggle_launch(c, bits, n, *opts, dR, scratch, need, s);
+    cudaFreeAsync(scratch, s);
+    return st;
+}
+
+ht_status ht_anisotropy_loss(const float *q, int n_patches, int n, int mode, int n_rad, int n_ang, double *out_loss,
+                             float *grad, void *stream)
+{
+    HT_CHECK_ARG(q && out_loss, "null argument");
+    HT_CHECK_ARG(n_patches >= 1, "need at least one patch");
+    HT_CHECK_ARG(n >= 8 && n <= 1024 && (n & (n - 1)) == 0, "n must be a power of two in [8, 1024]");
+    HT_CHECK_ARG(mode == 0 || mode == 1, "mode must be 0 or 1");
+    if (mode == 1) HT_CHECK_ARG(n_rad >= 1 && n_rad <= 256 && n_ang >= 2 && n_ang <= 64, "bad bin counts");
+    else {
+        n_rad = 1;
+        n_ang = 1;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = ht_las_scratch_bytes(n_patches, n, n_rad, n_ang);
+    void *scratch = nullptr;
+    HT_CUDA_TRY(cudaMallocAsync(&scratch, bytes, s));
+    ht_status st = ht_las_launch(q, n_patches, n, mode, n_rad, n_ang, out_loss, grad, scratch, bytes, s);
+    cudaFreeAsync(scratch, s);
+    return st;
+}
+
+ht_status ht_sync(void *stream)
+{
+    HT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    int *flag = ht_device_error_flag();
+    if (!flag) return HT_ERR_CUDA;
+    int v = 0;
+    HT_CUDA_TRY(cudaMemcpy(&v, flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        cudaMemset(flag, 0, sizeof(int));
+        ht_set_error("device-side wait expired (error %d)", v);
+        return (ht_status)v;
+    }
+    return HT_OK;
+}
+
+}  // extern "C"

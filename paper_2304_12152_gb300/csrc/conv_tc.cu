@@ -1,0 +1,816 @@
+// conv_tc.cu -- tensor-core form of the policy forward on sm_103a.
+//
+// Policy (Sec. III "State"/"Agents", Sec. VI-A): 3x3 convolutions, zero
+// padding 1, ReLU between layers, sigmoid / softmax head.  Three kernels:
+//
+//  k_first_tc  layer 1 (2 -> 64): too thin for the tensor pipe (K = 18); FP32
+//              CUDA-core FMAs, the noise channel z drawn in-kernel from Philox
+//              stream 0, ReLU, stored in the chunk-planar layout below.
+//  k_conv_tc   every 64 -> 64 layer: implicit GEMM on tcgen05.  One MMA tile is
+//              128 consecutive output pixels of one row (M = 128) x 64 output
+//              channels (N = 64); K runs over the 9 taps x 64 input channels.
+//              Input rows are staged by TMA into a ring of shared-memory slots
+//              (one image row of 130 pixels incl. the halo per slot); every tap
+//              is a *shifted descriptor* into the staged rows, so no im2col
+//              copy exists.  Weights stay resident in shared memory; the FP32
+//              accumulator lives in TMEM (two 64-column buffers so the
+//              epilogue of row i overlaps the MMAs of row i+1).  Epilogue:
+//              tcgen05.ld -> (dequant) + bias -> ReLU -> bf16 / e4m3 -> global.
+//  k_head_tc   last layer (64 -> K) + sigmoid/softmax + Philox sampling +
+//              bit packing (shared head epilogue).
+//
+// Activation layout in HBM ("chunk-planar"): [chunk][H][W][16 bytes], a chunk
+// being 8 bf16 channels (8 chunks) or 16 e4m3 channels (4 chunks).  A TMA box
+// {16 B, 130 px, 1 row, all chunks} lands in shared memory exactly in the
+// canonical no-swizzle K-major core-matrix layout that tcgen05 descriptors
+// read: pixels at a 16-byte stride (SBO = 128 B per 8-pixel core matrix),
+// chunks 130 * 16 B apart (LBO).  A one-pixel shift of the A operand is a
+// 16-byte shift of the descriptor start address.
+//
+// Warp roles (192 threads, one persistent CTA per SM): warp 0 = TMA producer
+// (and TMEM owner), warp 1 = MMA issuer, warps 2-5 = epilogue (TMEM lane
+// quarters 2, 3, 0, 1).  Every mbarrier wait is bounded (globaltimer); on
+// expiry the kernel records HT_ERR_TIMEOUT, drains its own copies and MMAs,
+// frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "head.cuh"
+
+namespace {
+
+constexpr int TILE_M = 128;                // output pixels per MMA tile (one row segment)
+constexpr int ROW_PX = TILE_M + 2;         // staged pixels per input row (halo of 1 each side)
+constexpr int NSLOT = 6;                   // input-row ring depth
+constexpr int NTHREADS = 192;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;   // 2 s per wait
+
+template <bool FP8>
+struct Cfg {
+    static constexpr int EB = FP8 ? 1 : 2;                    // bytes per element
+    static constexpr int CPC = 16 / EB;                        // channels per 16-byte chunk
+    static constexpr int NCHUNK = 64 / CPC;                    // chunks per pixel (8 / 4)
+    static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;    // 16640 / 8320
+    static constexpr int W_BYTES = 9 * NCHUNK * 64 * 16;       // 73728 / 36864
+    static constexpr int KSTEPS = NCHUNK / 2;                  // MMAs per tap (K = 16 / 32)
+    static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 1024 /*barriers, bias, scales*/;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait.  Returns false on timeout (which it records) or when another
+// role has already aborted (unless ignore_abort).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, bool ignore_abort = false)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31u) == 0) {
+            if (!ignore_abort && *abort_flag) return false;
+            if (globaltimer_ns() - t0 > kTimeoutNs || it > (1u << 28)) {
+                *abort_flag = 1;
+                atomicExch(err, (int)HT_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: canonical K-major layout without swizzle.
+// start >> 4 in [0,14), LBO >> 4 in [16,30), SBO >> 4 in [32,46), version 1 at
+// bit 46, base offset 0, swizzle 0.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: D = F32 (bit 4), A/B format at bits 7/10 (BF16 = 1
+// for kind::f16, E4M3 = 0 for kind::f8f6f4), both K-major, N >> 3 at bit 17,
+// M >> 4 at bit 24.
+template <bool FP8>
+__host__ __device__ constexpr uint32_t idesc_m128_n64()
+{
+    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d)
+{
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return (lo & 0xFFFFu) | (hi << 16);
+}
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Stores 64 channel values of one pixel into the chunk-planar layout.
+// out_fp8: e4m3(bf16(v) * inv_scale) (16 channels per chunk), else bf16 (8 per chunk).
+__device__ __forceinline__ void store_pixel(const float *v, void *out, int out_fp8, float inv_scale, int H, int W,
+                                            int y, int x)
+{
+    if (out_fp8) {
+        uint8_t *o = (uint8_t *)out;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint4 q;
+            q.x = pack_e4m3x4(bf16_round(v[16 * c + 0]) * inv_scale, bf16_round(v[16 * c + 1]) * inv_scale,
+                              bf16_round(v[16 * c + 2]) * inv_scale, bf16_round(v[16 * c + 3]) * inv_scale);
+            q.y = pack_e4m3x4(bf16_round(v[16 * c + 4]) * inv_scale, bf16_round(v[16 * c + 5]) * inv_scale,
+                              bf16_round(v[16 * c + 6]) * inv_scale, bf16_round(v[16 * c + 7]) * inv_scale);
+            q.z = pack_e4m3x4(bf16_round(v[16 * c + 8]) * inv_scale, bf16_round(v[16 * c + 9]) * inv_scale,
+                              bf16_round(v[16 * c + 10]) * inv_scale, bf16_round(v[16 * c + 11]) * inv_scale);
+            q.w = pack_e4m3x4(bf16_round(v[16 * c + 12]) * inv_scale, bf16_round(v[16 * c + 13]) * inv_scale,
+                              bf16_round(v[16 * c + 14]) * inv_scale, bf16_round(v[16 * c + 15]) * inv_scale);
+            *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = q;
+        }
+    } else {
+        uint8_t *o = (uint8_t *)out;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uint4 q;
+            q.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+            q.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+            q.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+            q.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+            *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = q;
+        }
+    }
+}
+
+struct ConvParams {
+    const void *wpack;       // packed weights of this layer ([tap][chunk][n][16 B])
+    const float *bias;       // [64]
+    const float *wscale;     // FP8: per-output-channel weight scale, else null
+    float in_scale;          // FP8: scale of the input activations
+    float out_inv_scale;     // FP8 output: 1 / scale of the next layer's input
+    int out_fp8;
+    void *out;               // chunk-planar output
+    int H, W, n_xtiles, rows_per_unit, n_units;
+    int *err;
+};
+
+// ---------------------------------------------------------------------------
+// 64 -> 64 layer on tcgen05
+// ---------------------------------------------------------------------------
+template <bool FP8>
+__global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap, const ConvParams P)
+{
+    using C = Cfg<FP8>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *s_w = smem;
+    uint8_t *s_rows = smem + C::W_BYTES;
+    uint64_t *bars = (uint64_t *)(s_rows + NSLOT * C::SLOT_BYTES);
+    uint64_t *full = bars, *empty = bars + NSLOT, *wbar = bars + 2 * NSLOT, *accf = wbar + 1, *acce = accf + 2,
+             *drain = acce + 2;
+    uint32_t *s_tmem = (uint32_t *)(drain + 1);
+    volatile int *s_abort = (volatile int *)(s_tmem + 1);
+    float *s_scale = (float *)(s_tmem + 2);      // 64 (dequant scale)
+    float *s_bias = s_scale + 64;                 // 64
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSLOT; ++i) {
+            mbar_init(smem_u32(&full[i]), 1);
+            mbar_init(smem_u32(&empty[i]), 1);
+        }
+        mbar_init(smem_u32(wbar), 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&accf[i]), 1);
+            mbar_init(smem_u32(&acce[i]), 4);
+        }
+        mbar_init(smem_u32(drain), 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 64) {
+        s_bias[threadIdx.x] = P.bias[threadIdx.x];
+        s_scale[threadIdx.x] = FP8 ? P.in_scale * P.wscale[threadIdx.x] : 1.f;
+    }
+    if (warp == 0) tmem_alloc(smem_u32(s_tmem), 128);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *s_tmem;
+
+    if (warp == 0) {
+        // ------------------------- TMA producer -------------------------
+        if (lane == 0) {
+            int last_issued[NSLOT];
+            for (int i = 0; i < NSLOT; ++i) last_issued[i] = -1;
+            mbar_arrive_expect_tx(smem_u32(wbar), C::W_BYTES);
+            bulk_g2s(smem_u32(s_w), P.wpack, C::W_BYTES, smem_u32(wbar));
+            uint32_t li = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
+                const int xt = u % P.n_xtiles, ys = u / P.n_xtiles;
+                const int y0 = ys * P.rows_per_unit;
+                const int y1 = min(P.H, y0 + P.rows_per_unit);
+                const int x0 = xt * TILE_M;
+                for (int r = 0; r < (y1 - y0) + 2; ++r, ++li) {
+                    const int slot = (int)(li % NSLOT);
+                    const uint32_t ph = (li / NSLOT) & 1u;
+                    if (!mbar_wait(smem_u32(&empty[slot]), ph ^ 1u, s_abort, P.err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(smem_u32(&full[slot]), C::SLOT_BYTES);
+                    tma_load_4d(smem_u32(s_rows + slot * C::SLOT_BYTES), &tmap, 0, x0 - 1, y0 - 1 + r, 0,
+                                smem_u32(&full[slot]));
+                    last_issued[slot] = (int)li;
+                }
+            }
+            // drain: every issued copy must have landed before the CTA exits
+            for (int s = 0; s < NSLOT; ++s)
+                if (last_issued[s] >= 0)
+                    mbar_wait(smem_u32(&full[s]), ((uint32_t)last_issued[s] / NSLOT) & 1u, s_abort, P.err, true);
+            mbar_wait(smem_u32(wbar), 0, s_abort, P.err, true);
+        }
+    } else if (warp == 1) {
+        // ------------------------- MMA issuer -------------------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_m128_n64<FP8>();
+            const uint32_t w_addr = smem_u32(s_w), rows_addr = smem_u32(s_rows);
+            bool ok = mbar_wait(smem_u32(wbar), 0, s_abort, P.err);
+            uint32_t ci = 0, ai = 0;
+            for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
+                const int ys = u / P.n_xtiles;
+                const int y0 = ys * P.rows_per_unit;
+                const int nrows = min(P.H, y0 + P.rows_per_unit) - y0;
+                for (int i = 0; i < nrows && ok; ++i) {
+                    for (int j = 0; j < 3 && ok; ++j) {
+                        const uint32_t q = ci + i + j;
+                        ok = mbar_wait(smem_u32(&full[q % NSLOT]), (q / NSLOT) & 1u, s_abort, P.err);
+                    }
+                    const uint32_t a = ai & 1u;
+                    if (ok) ok = mbar_wait(smem_u32(&acce[a]), ((ai >> 1) & 1u) ^ 1u, s_abort, P.err);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + a * 64u;
+#pragma unroll 1
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const uint32_t slot_addr = rows_addr + ((ci + i + dy) % NSLOT) * C::SLOT_BYTES;
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll
+                            for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                                const uint64_t adesc = sdesc(slot_addr + (2 * ks * ROW_PX + dx) * 16, ROW_PX * 16, 128);
+                                const uint64_t bdesc = sdesc(w_addr + ((dy * 3 + dx) * C::NCHUNK + 2 * ks) * 1024, 1024, 128);
+                                mma_ss<FP8>(d, adesc, bdesc, idesc, (dy | dx | ks) != 0);
+                            }
+                        }
+                    }
+                    mma_commit(smem_u32(&accf[a]));
+                    mma_commit(smem_u32(&empty[(ci + i) % NSLOT]));
+                    ++ai;
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&empty[(ci + nrows) % NSLOT]));
+                mma_commit(smem_u32(&empty[(ci + nrows + 1) % NSLOT]));
+                ci += nrows + 2;
+            }
+            // drain: all issued MMAs complete before TMEM is released
+            mma_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0, s_abort, P.err, true);
+        }
+    } else {
+        // ------------------------- epilogue -------------------------
+        const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
+        const int px = quarter * 32 + lane;           // pixel within the tile
+        uint32_t ai = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
+            const int xt = u % P.n_xtiles, ys = u / P.n_xtiles;
+            const int y0 = ys * P.rows_per_unit;
+            const int nrows = min(P.H, y0 + P.rows_per_unit) - y0;
+            const int x = xt * TILE_M + px;
+            for (int i = 0; i < nrows; ++i, ++ai) {
+                const uint32_t a = ai & 1u;
+                int got = 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&accf[a]), (ai >> 1) & 1u, s_abort, P.err) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                float v[64];
+                const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + a * 64u;
+                tmem_ld16(taddr + 0, v + 0);
+                tmem_ld16(taddr + 16, v + 16);
+                tmem_ld16(taddr + 32, v + 32);
+                tmem_ld16(taddr + 48, v + 48);
+                tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acce[a]));
+                if (x < P.W) {
+#pragma unroll
+                    for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], s_scale[n], s_bias[n]), 0.f);
+                    store_pixel(v, P.out, P.out_fp8, P.out_inv_scale, P.H, P.W, y0 + i, x);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 128);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Layer 1 (2 -> 64) on CUDA cores; writes the chunk-planar layout.
+// Tile: 128 pixels x 4 rows, one thread per column.
+// ---------------------------------------------------------------------------
+constexpr int FT_X = 128, FT_Y = 4;
+
+__global__ void __launch_bounds__(FT_X) k_first_tc(const float *__restrict__ contone, int cpitch, int H, int W,
+                                                   uint64_t seed, uint32_t image, const float *__restrict__ w1,
+                                                   const float *__restrict__ b1, void *out, int out_fp8,
+                                                   float out_inv_scale)
+{
+    __shared__ float s_c[FT_Y + 2][FT_X + 2];
+    __shared__ float s_z[FT_Y + 2][FT_X + 2];
+    __shared__ float4 s_w[18][16];               // [tap*2 + ci][o/4]
+    __shared__ float4 s_b[16];
+    const int x0 = blockIdx.x * FT_X, y0 = blockIdx.y * FT_Y;
+    for (int i = threadIdx.x; i < (FT_Y + 2) * (FT_X + 2); i += FT_X) {
+        const int yy = i / (FT_X + 2), xx = i % (FT_X + 2);
+        const int gy = y0 + yy - 1, gx = x0 + xx - 1;
+        float c = 0.f, z = 0.f;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+            c = contone[(size_t)gy * cpitch + gx];
+            z = ht_uniform24(seed, image, 0u, (uint64_t)gy * W + gx);
+        }
+        s_c[yy][xx] = c;
+        s_z[yy][xx] = z;
+    }
+    for (int i = threadIdx.x; i < 18 * 64; i += FT_X) {
+        const int k = i / 64, o = i % 64;           // k = tap*2 + ci
+        const int tap = k >> 1, ci = k & 1;
+        reinterpret_cast<float *>(&s_w[k][0])[o] = w1[((size_t)o * 2 + ci) * 9 + tap];
+    }
+    if (threadIdx.x < 64) reinterpret_cast<float *>(s_b)[threadIdx.x] = b1[threadIdx.x];
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    if (x >= W) return;
+    for (int r = 0; r < FT_Y; ++r) {
+        const int y = y0 + r;
+        if (y >= H) break;
+        float in[18];
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            in[2 * tap] = s_c[r + tap / 3][threadIdx.x + tap % 3];
+            in[2 * tap + 1] = s_z[r + tap / 3][threadIdx.x + tap % 3];
+        }
+        float v[64];
+#pragma unroll
+        for (int o4 = 0; o4 < 16; ++o4) {
+            float4 a = s_b[o4];
+#pragma unroll
+            for (int k = 0; k < 18; ++k) {
+                const float4 wv = s_w[k][o4];
+                a.x = fmaf(in[k], wv.x, a.x);
+                a.y = fmaf(in[k], wv.y, a.y);
+                a.z = fmaf(in[k], wv.z, a.z);
+                a.w = fmaf(in[k], wv.w, a.w);
+            }
+            v[4 * o4 + 0] = fmaxf(a.x, 0.f);
+            v[4 * o4 + 1] = fmaxf(a.y, 0.f);
+            v[4 * o4 + 2] = fmaxf(a.z, 0.f);
+            v[4 * o4 + 3] = fmaxf(a.w, 0.f);
+        }
+        store_pixel(v, out, out_fp8, out_inv_scale, H, W, y, x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Last layer (64 -> K) + head on CUDA cores, reading bf16 chunk-planar input.
+// Tile 32 x 8 pixels; one warp per tile row (the bit-packing granule).
+// ---------------------------------------------------------------------------
+constexpr int HT_X = 32, HT_Y = 8;
+
+template <int K>
+__global__ void __launch_bounds__(HT_X *HT_Y) k_head_tc(const uint8_t *__restrict__ act, int H, int W,
+                                                        const float *__restrict__ wl, const float *__restrict__ bl,
+                                                        int head, int mode, uint64_t seed, uint32_t image,
+                                                        uint32_t *bits, int words, float *prob)
+{
+    extern __shared__ uint4 s_dyn[];
+    uint4 *s_a = s_dyn;                                               // [8][HT_Y+2][HT_X+2]
+    float *s_w = (float *)(s_a + 8 * (HT_Y + 2) * (HT_X + 2));       // [9][64][K]
+    const int x0 = blockIdx.x * HT_X, y0 = blockIdx.y * HT_Y;
+    const int tid = threadIdx.y * HT_X + threadIdx.x;
+    for (int i = tid; i < 8 * (HT_Y + 2) * (HT_X + 2); i += HT_X * HT_Y) {
+        const int c = i / ((HT_Y + 2) * (HT_X + 2)), rem = i % ((HT_Y + 2) * (HT_X + 2));
+        const int yy = rem / (HT_X + 2), xx = rem % (HT_X + 2);
+        const int gy = y0 + yy - 1, gx = x0 + xx - 1;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            v = *reinterpret_cast<const uint4 *>(act + (((size_t)c * H + gy) * W + gx) * 16);
+        s_a[i] = v;
+    }
+    for (int i = tid; i < 9 * 64 * K; i += HT_X * HT_Y) {
+        const int tap = i / (64 * K), rem = i % (64 * K), c = rem / K, k = rem % K;
+        s_w[i] = wl[((size_t)k * 64 + c) * 9 + tap];
+    }
+    __syncthreads();
+    float z[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < K; ++k) z[k] = bl[k];
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int yy = threadIdx.y + tap / 3, xx = threadIdx.x + tap % 3;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint4 q = s_a[(c * (HT_Y + 2) + yy) * (HT_X + 2) + xx];
+            const uint32_t wds[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float lo = __uint_as_float(wds[j] << 16), hi = __uint_as_float(wds[j] & 0xFFFF0000u);
+                const float *wp = s_w + (tap * 64 + c * 8 + 2 * j) * K;
+#pragma unroll
+                for (int k = 0; k < K; ++k) z[k] = fmaf(lo, wp[k], fmaf(hi, wp[K + k], z[k]));
+            }
+        }
+    }
+    ht_head_emit(z, K, head, mode, seed, image, x0, y0 + threadIdx.y, H, W, bits, words, prob);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 4-D map over a chunk-planar activation: dims {16 B, W, H, chunks}.
+ht_status make_act_map(CUtensorMap *m, const void *base, int H, int W, bool fp8)
+{
+    auto enc = get_encode();
+    if (!enc) {
+        ht_set_error("cuTensorMapEncodeTiled unavailable");
+        return HT_ERR_CUDA;
+    }
+    const int cpc = fp8 ? 16 : 8, nchunk = fp8 ? 4 : 8;
+    cuuint64_t dims[4] = {(cuuint64_t)cpc, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nchunk};
+    cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
+    cuuint32_t box[4] = {(cuuint32_t)cpc, (cuuint32_t)ROW_PX, 1, (cuuint32_t)nchunk};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        ht_set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return HT_ERR_CUDA;
+    }
+    return HT_OK;
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// rows per work unit: balances the persistent grid against the halo re-read
+int pick_rows_per_unit(int H, int n_xtiles, int sms)
+{
+    int best = 16;
+    double best_cost = 1e30;
+    for (int r = 4; r <= 64; r += 2) {
+        const long units = (long)n_xtiles * ((H + r - 1) / r);
+        const long rounds = (units + sms - 1) / sms;
+        const double cost = (double)rounds * (r + 2);      // critical-path row loads
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = r;
+        }
+    }
+    return best;
+}
+
+template <bool FP8>
+ht_status launch_conv(const CUtensorMap &m, const ConvParams &P, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FP8>::SMEM));
+        attr_set = true;
+    }
+    const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
+    ht_prof_start(FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
+    k_conv_tc<FP8><<<grid, NTHREADS, Cfg<FP8>::SMEM, s>>>(m, P);
+    ht_prof_stop(s);
+    HT_LAUNCH_CHECK();
+    return HT_OK;
+}
+
+uint16_t f32_to_bf16_rne(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// round-to-nearest-even to OCP E4M3 (saturating), returns the encoded byte
+uint8_t f64_to_e4m3_rne(double x)
+{
+    const uint8_t sign = x < 0 ? 0x80 : 0;
+    double ax = fabs(x);
+    if (ax == 0.0) return sign;
+    double q;
+    if (ax < ldexp(1.0, -6)) {
+        q = ldexp(1.0, -9);
+    } else {
+        int e;
+        frexp(ax, &e);
+        q = ldexp(1.0, e - 4);
+    }
+    double r = nearbyint(ax / q) * q;
+    if (r > 448.0) r = 448.0;
+    if (r < ldexp(1.0, -6)) {                      // subnormal (or rounded up to the min normal below)
+        const int m = (int)nearbyint(r / ldexp(1.0, -9));
+        if (m < 8) return sign | (uint8_t)m;
+    }
+    int e;
+    const double fr = frexp(r, &e);                // r = fr * 2^e, fr in [0.5, 1)
+    const int exp_field = e - 1 + 7;
+    const int mant = (int)nearbyint((fr * 2.0 - 1.0) * 8.0);
+    return sign | (uint8_t)(exp_field << 3) | (uint8_t)mant;
+}
+
+}  // namespace
+
+ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
+{
+    const bool fp8 = (p->prec == HT_FP8_E4M3);
+    const int cpc = fp8 ? 16 : 8, nchunk = fp8 ? 4 : 8;
+    const size_t layer_bytes = (size_t)9 * nchunk * 64 * 16;
+    const int n_inner = p->L - 2;
+    p->wpack_layer_bytes = layer_bytes;
+    if (!p->d_wpack) HT_CUDA_TRY(cudaMalloc(&p->d_wpack, layer_bytes * n_inner));
+    if (fp8 && !p->d_wscale) HT_CUDA_TRY(cudaMalloc((void **)&p->d_wscale, sizeof(float) * 64 * n_inner));
+    // pull the current fp32 weights of the inner layers to the host
+    const size_t nw = (size_t)64 * 64 * 9;
+    float *hw = (float *)malloc(sizeof(float) * nw * n_inner);
+    uint8_t *hp = (uint8_t *)malloc(layer_bytes * n_inner);
+    float *hs = (float *)malloc(sizeof(float) * 64 * n_inner);
+    if (!hw || !hp || !hs) {
+        free(hw);
+        free(hp);
+        free(hs);
+        return HT_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpyAsync(hw, p->d_w + p->w_off[1], sizeof(float) * nw * n_inner, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free(hw);
+        free(hp);
+        free(hs);
+        HT_CUDA_TRY(e);
+    }
+    for (int l = 0; l < n_inner; ++l) {
+        const float *W = hw + nw * l;     // [n][c][3][3]
+        uint8_t *dst = hp + layer_bytes * l;
+        for (int n = 0; n < 64; ++n) {
+            double sc = 1.0;
+            if (fp8) {
+                double amax = 0.0;
+                for (int k = 0; k < 64 * 9; ++k) amax = fmax(amax, fabs((double)W[(size_t)n * 576 + k]));
+                sc = amax > 0.0 ? amax / 448.0 : 1.0;
+                hs[64 * l + n] = (float)sc;
+            }
+            for (int tap = 0; tap < 9; ++tap)
+                for (int c = 0; c < 64; ++c) {
+                    const float wv = W[((size_t)n * 64 + c) * 9 + tap];
+                    const size_t off = (((size_t)tap * nchunk + c / cpc) * 64 + n) * 16;
+                    if (fp8) {
+                        dst[off + (c % cpc)] = f64_to_e4m3_rne((double)wv / sc);
+                    } else {
+                        const uint16_t b = f32_to_bf16_rne(wv);
+                        memcpy(dst + off + 2 * (c % cpc), &b, 2);
+                    }
+                }
+        }
+    }
+    e = cudaMemcpyAsync(p->d_wpack, hp, layer_bytes * n_inner, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && fp8) e = cudaMemcpyAsync(p->d_wscale, hs, sizeof(float) * 64 * n_inner, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    free(hw);
+    free(hp);
+    free(hs);
+    HT_CUDA_TRY(e);
+    return HT_OK;
+}
+
+size_t ht_tc_ws_bytes(const ht_policy *p, int h, int w)
+{
+    const size_t eb = p->prec == HT_FP8_E4M3 ? 1 : 2;
+    // two ping-pong buffers; the bf16 one feeding the head is always 2 B/channel
+    return 2 * (size_t)h * w * 64 * 2 + 0 * eb + 256;
+}
+
+ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int mode, uint64_t seed,
+                    uint32_t *bits, float *prob, cudaStream_t s)
+{
+    const int H = img.h, W = img.w;
+    const bool fp8 = (p->prec == HT_FP8_E4M3);
+    uint8_t *buf[2];
+    buf[0] = (uint8_t *)p->d_ws;
+    buf[1] = buf[0] + (size_t)H * W * 64 * 2;
+    const int n_inner = p->L - 2;
+    int *err = ht_device_error_flag();
+    if (!err) return HT_ERR_CUDA;
+
+    // layer 1: output feeds inner layer 1 (e4m3 in the FP8 form)
+    {
+        const dim3 grid((W + FT_X - 1) / FT_X, (H + FT_Y - 1) / FT_Y);
+        const bool o8 = fp8 && n_inner > 0;
+        ht_prof_start(HTK_FIRST_TC, s);
+        k_first_tc<<<grid, FT_X, 0, s>>>(img.contone, img.pitch, H, W, seed, image_index, p->d_w + p->w_off[0],
+                                         p->d_b + p->b_off[0], buf[0], o8 ? 1 : 0,
+                                         o8 ? 1.f / p->act_scale[1] : 1.f);
+        ht_prof_stop(s);
+        HT_LAUNCH_CHECK();
+    }
+    const int n_xtiles = (W + TILE_M - 1) / TILE_M;
+    const int rpu = pick_rows_per_unit(H, n_xtiles, num_sms());
+    int cur = 0;
+    for (int l = 1; l <= n_inner; ++l) {
+        const bool in8 = fp8;
+        const bool out8 = fp8 && (l < n_inner);
+        CUtensorMap m;
+        ht_status st = make_act_map(&m, buf[cur], H, W, in8);
+        if (st != HT_OK) return st;
+        ConvParams P;
+        P.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (l - 1);
+        P.bias = p->d_b + p->b_off[l];
+        P.wscale = fp8 ? p->d_wscale + 64 * (l - 1) : nullptr;
+        P.in_scale = fp8 ? p->act_scale[l] : 1.f;
+        P.out_inv_scale = out8 ? 1.f / p->act_scale[l + 1] : 1.f;
+        P.out_fp8 = out8 ? 1 : 0;
+        P.out = buf[cur ^ 1];
+        P.H = H;
+        P.W = W;
+        P.n_xtiles = n_xtiles;
+        P.rows_per_unit = rpu;
+        P.n_units = n_xtiles * ((H + rpu - 1) / rpu);
+        P.err = err;
+        st = fp8 ? launch_conv<true>(m, P, s) : launch_conv<false>(m, P, s);
+        if (st != HT_OK) return st;
+        cur ^= 1;
+    }
+    // head
+    {
+        static bool attr = false;
+        const size_t smem = sizeof(uint4) * 8 * (HT_Y + 2) * (HT_X + 2) + sizeof(float) * 9 * 64 * 4;
+        if (!attr) {
+            HT_CUDA_TRY(cudaFuncSetAttribute(k_head_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            HT_CUDA_TRY(cudaFuncSetAttribute(k_head_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+        const dim3 grid((W + HT_X - 1) / HT_X, (H + HT_Y - 1) / HT_Y);
+        const int words = ht_bits_row_words(W, p->head);
+        const float *wl = p->d_w + p->w_off[p->L - 1], *bl = p->d_b + p->b_off[p->L - 1];
+        ht_prof_start(HTK_HEAD_TC, s);
+        if (p->K == 1)
+            k_head_tc<1><<<grid, dim3(HT_X, HT_Y), smem, s>>>(buf[cur], H, W, wl, bl, p->head, mode, seed,
+                                                              image_index, bits, words, prob);
+        else
+            k_head_tc<4><<<grid, dim3(HT_X, HT_Y), smem, s>>>(buf[cur], H, W, wl, bl, p->head, mode, seed,
+                                                              image_index, bits, words, prob);
+        ht_prof_stop(s);
+        HT_LAUNCH_CHECK();
+    }
+    return HT_OK;
+}

@@ -1,0 +1,129 @@
+// ht_internal.cuh -- internal declarations shared by the library's CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "ht.h"
+
+// ---------------------------------------------------------------------------
+// Error plumbing
+// ---------------------------------------------------------------------------
+void ht_set_error(const char *fmt, ...);
+
+#define HT_CHECK_ARG(cond, ...)                 \
+    do {                                        \
+        if (!(cond)) {                          \
+            ht_set_error(__VA_ARGS__);          \
+            return HT_ERR_INVALID_ARG;          \
+        }                                       \
+    } while (0)
+
+#define HT_CUDA_TRY(expr)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            ht_set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? HT_ERR_OOM : HT_ERR_CUDA;          \
+        }                                                                              \
+    } while (0)
+
+#define HT_LAUNCH_CHECK()                                                              \
+    do {                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess) {                                                       \
+            ht_set_error("%s:%d: launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+            return HT_ERR_CUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
+// Device-side error flag (one per device context): kernels whose bounded wait
+// expires store HT_ERR_TIMEOUT here; ht_sync() reads and clears it.
+int *ht_device_error_flag();
+
+// Kernel timing hooks (no-ops unless ht_profile_begin was called).
+enum ht_kernel_id { HTK_FIRST_TC = 0, HTK_CONV_TC_BF16, HTK_CONV_TC_FP8, HTK_HEAD_TC, HTK_CONV_FP32, HTK_HEAD_FP32,
+                    HTK_REWARD, HTK_TOGGLE, HTK_SPECTRUM, HTK_TRAIN, HTK_COUNT };
+void ht_prof_start(int kid, cudaStream_t s);
+void ht_prof_stop(cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Key (seed lo, seed hi),
+// counter (g >> 2, image, stream, 0), output lane g & 3; u = (x >> 8) * 2^-24.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 ht_philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float ht_uniform24(uint64_t seed, uint32_t image, uint32_t stream, uint64_t g)
+{
+    const uint4 r = ht_philox4x32_10(make_uint4((uint32_t)(g >> 2), image, stream, 0u),
+                                     make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const uint32_t lane = (uint32_t)g & 3u;
+    const uint32_t x = lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
+    return (float)(x >> 8) * (1.0f / 16777216.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Policy object
+// ---------------------------------------------------------------------------
+struct ht_policy {
+    int L;                          // conv layers
+    int ch[HT_MAX_LAYERS + 1];
+    int head, K, prec;
+    int device;
+    int64_t n_w, n_b;
+    int64_t w_off[HT_MAX_LAYERS + 1], b_off[HT_MAX_LAYERS + 1];
+    float *d_w = nullptr;           // canonical fp32 OIHW, all layers
+    float *d_b = nullptr;
+    // tensor-core form: packed inner-layer weights ([tap][c8][n][8] per layer)
+    void *d_wpack = nullptr;
+    size_t wpack_layer_bytes = 0;
+    float *d_wscale = nullptr;      // FP8: per (layer, out channel) dequant scale
+    float act_scale[HT_MAX_LAYERS];
+    // per-call workspace (grown on demand; library owned)
+    void *d_ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+ht_status ht_policy_ensure_ws(ht_policy *p, size_t bytes);
+ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Launchers (one per source file)
+// ---------------------------------------------------------------------------
+// plain FP32 form, one image
+ht_status ht_run_fp32(ht_policy *p, const ht_image &img, uint32_t image_index, int mode, uint64_t seed,
+                      uint32_t *bits, float *prob, float *act_a, float *act_b, cudaStream_t s);
+size_t ht_fp32_ws_bytes(const ht_policy *p, int h, int w);
+
+// tensor-core form, one image
+ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int mode, uint64_t seed,
+                    uint32_t *bits, float *prob, cudaStream_t s);
+size_t ht_tc_ws_bytes(const ht_policy *p, int h, int w);
+
+// reward / toggle deltas
+ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
+                           double *out, cudaStream_t s);
+ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
+                           float *const *dR, float *scratch, size_t scratch_floats, cudaStream_t s);
+size_t ht_toggle_scratch_floats(int h, int w, int r);
+
+// spectrum
+ht_status ht_las_launch(const float *q, int n_patches, int n, int mode, int n_rad, int n_ang, double *out_loss,
+                        float *grad, void *scratch, size_t scratch_bytes, cudaStream_t s);
+size_t ht_las_scratch_bytes(int n_patches, int n, int n_rad, int n_ang);

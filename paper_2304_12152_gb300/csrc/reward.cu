@@ -1,0 +1,332 @@
+// reward.cu -- reward R = -MSE(HVS(h), HVS(c)) + w_s CSSIM(h, c) and the toggle
+// deltas of the local-expectation gradient.
+//
+// Reward (Eq. reward, Eq. final_reward, Eq. cssim and the contrast map of
+// Sec. V): every window is a normalised Gaussian, applied "valid" (no padding,
+// Sec. VI-A).  A 2-D normalised Gaussian is the outer product of the
+// normalised 1-D Gaussian, so each window sum runs as a row pass then a column
+// pass over a shared-memory tile.  Five window sums per output:
+//   HVS(h - c)      -> e = HVS(h) - HVS(c)
+//   W(h)            -> mu_h; var_h = mu_h - mu_h^2 (h is binary, h^2 = h)
+//   W(c'), W(c'^2)  -> mu_c, var_c   (c' = c - c_ref, c_ref a per-tile constant
+//                                     that removes the cancellation in E[c^2]-mu^2)
+//   W(h c')         -> cov = E[h c'] - mu_h mu_c'
+// SSIM_j = (2 mu_h mu_c + C1)(2 cov + C2) / ((mu_h^2 + mu_c^2 + C1)(var_h + var_c + C2)),
+// sigma_j = k sqrt(var_c), CSSIM term = sigma_j SSIM_j + 1 - sigma_j.
+// Per-image sums are reduced in FP64 (warp shuffles, then one atomic per block).
+//
+// Toggle deltas (Eq. le, Eq. marl; Sec. III-C): flipping pixel a by
+// delta = 1 - 2 h_a only changes the window sums of the outputs j whose window
+// contains a, by delta * g(a - j) (HVS) and delta * w(a - j) (SSIM window):
+//   e_j'    = e_j + delta g
+//   mu_h'   = mu_h + delta w,   var_h' = mu_h' - mu_h'^2
+//   cov'    = cov + delta w (c_a - mu_c)
+// so dR_a = R(h_a = 1) - R(h_a = 0) = (1/M) sum_j [ -(2 g e_j + delta g^2)
+//            + delta w_s sigma_j (SSIM_j' - SSIM_j) ]  (exact, no approximation).
+#include "ht_internal.cuh"
+
+namespace {
+
+constexpr int MAXR = 7;
+constexpr int RT = 32;                 // reward tile: 32 x 32 valid outputs
+constexpr int NQ = 5;
+
+struct Win {
+    float g[2 * MAXR + 1];             // HVS 1-D taps (normalised)
+    float w[2 * MAXR + 1];             // SSIM window 1-D taps (normalised)
+    int r;
+    float c1, c2, k, ws;
+};
+
+__device__ __forceinline__ float hbit(const uint32_t *bits, int words, int y, int x)
+{
+    return (float)((bits[(size_t)y * words + (x >> 5)] >> (x & 31)) & 1u);
+}
+
+// Computes the five window sums for a 32x32 tile of valid outputs.  Returns,
+// for the calling thread's outputs (rows ty, ty+8, ty+16, ty+24; column tx),
+// the per-output quantities through the callback-free arrays.
+struct Moments {
+    float e, muh, muc, varc, cov;
+};
+
+__device__ void tile_moments(const float *__restrict__ c, int cpitch, const uint32_t *__restrict__ bits, int words,
+                             int H, int W, const Win &wn, int vy0, int vx0, float (*s_h)[RT + 2 * MAXR],
+                             float (*s_c)[RT + 2 * MAXR], float (*s_row)[RT + 2 * MAXR][RT], Moments out[4],
+                             bool valid[4])
+{
+    const int r = wn.r, span = RT + 2 * r;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const float cref = c[(size_t)min(vy0 + r, H - 1) * cpitch + min(vx0 + r, W - 1)];
+    for (int i = tid; i < span * span; i += 256) {
+        const int yy = i / span, xx = i % span;
+        const int gy = vy0 + yy, gx = vx0 + xx;       // image coords of tile input
+        float hv = 0.f, cv = 0.f;
+        if (gy < H && gx < W) {
+            hv = hbit(bits, words, gy, gx);
+            cv = c[(size_t)gy * cpitch + gx] - cref;
+        }
+        s_h[yy][xx] = hv;
+        s_c[yy][xx] = cv;
+    }
+    __syncthreads();
+    // row pass: s_row[q][yy][x] for yy in [0, span), x in [0, 32)
+    for (int yy = ty; yy < span; yy += 8) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+        for (int k = 0; k <= 2 * r; ++k) {
+            const float hv = s_h[yy][tx + k], cv = s_c[yy][tx + k];
+            a0 = fmaf(wn.g[k], hv - (cv + cref), a0);   // h - c (cv holds c - c_ref)
+            a1 = fmaf(wn.w[k], hv, a1);
+            a2 = fmaf(wn.w[k], cv, a2);
+            a3 = fmaf(wn.w[k], cv * cv, a3);
+            a4 = fmaf(wn.w[k], hv * cv, a4);
+        }
+        s_row[0][yy][tx] = a0;
+        s_row[1][yy][tx] = a1;
+        s_row[2][yy][tx] = a2;
+        s_row[3][yy][tx] = a3;
+        s_row[4][yy][tx] = a4;
+    }
+    __syncthreads();
+    const int VH = H - 2 * r, VW = W - 2 * r;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int oy = ty + 8 * t;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+        for (int k = 0; k <= 2 * r; ++k) {
+            a0 = fmaf(wn.g[k], s_row[0][oy + k][tx], a0);
+            a1 = fmaf(wn.w[k], s_row[1][oy + k][tx], a1);
+            a2 = fmaf(wn.w[k], s_row[2][oy + k][tx], a2);
+            a3 = fmaf(wn.w[k], s_row[3][oy + k][tx], a3);
+            a4 = fmaf(wn.w[k], s_row[4][oy + k][tx], a4);
+        }
+        Moments m;
+        m.e = a0;
+        m.muh = a1;
+        m.muc = a2 + cref;
+        m.varc = fmaxf(a3 - a2 * a2, 0.f);
+        m.cov = a4 - a1 * a2;
+        out[t] = m;
+        valid[t] = (vy0 + oy < VH) && (vx0 + tx < VW);
+    }
+}
+
+__device__ __forceinline__ float ssim_of(float muh, float muc, float varh, float varc, float cov, float c1, float c2)
+{
+    return ((2.f * muh * muc + c1) * (2.f * cov + c2)) / ((muh * muh + muc * muc + c1) * (varh + varc + c2));
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256)
+k_reward_tiles(const float *__restrict__ c, int cpitch, const uint32_t *__restrict__ bits, int words, int H, int W,
+               Win wn, double *__restrict__ acc /* 3 doubles */)
+{
+    __shared__ float s_h[RT + 2 * MAXR][RT + 2 * MAXR];
+    __shared__ float s_c[RT + 2 * MAXR][RT + 2 * MAXR];
+    __shared__ float s_row[NQ][RT + 2 * MAXR][RT];
+    __shared__ double s_red[3][8];
+    Moments m[4];
+    bool valid[4];
+    tile_moments(c, cpitch, bits, words, H, W, wn, blockIdx.y * RT, blockIdx.x * RT, s_h, s_c, s_row, m, valid);
+    double se = 0.0, ss = 0.0, sc = 0.0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (!valid[t]) continue;
+        const float varh = m[t].muh - m[t].muh * m[t].muh;
+        const float s = ssim_of(m[t].muh, m[t].muc, varh, m[t].varc, m[t].cov, wn.c1, wn.c2);
+        const float sig = wn.k * sqrtf(m[t].varc);
+        se += (double)m[t].e * (double)m[t].e;
+        ss += (double)s;
+        sc += (double)(sig * s + (1.f - sig));
+    }
+    se = warp_sum(se);
+    ss = warp_sum(ss);
+    sc = warp_sum(sc);
+    const int warp = threadIdx.y, lane = threadIdx.x;
+    if (lane == 0) {
+        s_red[0][warp] = se;
+        s_red[1][warp] = ss;
+        s_red[2][warp] = sc;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < 3) {
+        double v = 0.0;
+        for (int i = 0; i < 8; ++i) v += s_red[lane][i];
+        atomicAdd(&acc[lane], v);
+    }
+}
+
+__global__ void k_reward_finalize(const double *__restrict__ acc, int n, const double *__restrict__ inv_m, float ws,
+                                  double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double mse = acc[3 * i] * inv_m[i], ssim = acc[3 * i + 1] * inv_m[i], cssim = acc[3 * i + 2] * inv_m[i];
+    out[4 * i + 0] = mse;
+    out[4 * i + 1] = ssim;
+    out[4 * i + 2] = cssim;
+    out[4 * i + 3] = -mse + (double)ws * cssim;
+}
+
+// Per-output maps for the toggle deltas, valid coords [VH][VW]:
+// 0 e, 1 mu_h, 2 mu_c, 3 var_c + C2, 4 cov, 5 sigma, 6 SSIM.
+constexpr int NMAP = 7;
+
+__global__ void __launch_bounds__(256)
+k_moment_maps(const float *__restrict__ c, int cpitch, const uint32_t *__restrict__ bits, int words, int H, int W,
+              Win wn, float *__restrict__ maps)
+{
+    __shared__ float s_h[RT + 2 * MAXR][RT + 2 * MAXR];
+    __shared__ float s_c[RT + 2 * MAXR][RT + 2 * MAXR];
+    __shared__ float s_row[NQ][RT + 2 * MAXR][RT];
+    Moments m[4];
+    bool valid[4];
+    const int vy0 = blockIdx.y * RT, vx0 = blockIdx.x * RT;
+    tile_moments(c, cpitch, bits, words, H, W, wn, vy0, vx0, s_h, s_c, s_row, m, valid);
+    const int VH = H - 2 * wn.r, VW = W - 2 * wn.r;
+    const size_t plane = (size_t)VH * VW;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (!valid[t]) continue;
+        const size_t k = (size_t)(vy0 + threadIdx.y + 8 * t) * VW + vx0 + threadIdx.x;
+        const float varh = m[t].muh - m[t].muh * m[t].muh;
+        maps[0 * plane + k] = m[t].e;
+        maps[1 * plane + k] = m[t].muh;
+        maps[2 * plane + k] = m[t].muc;
+        maps[3 * plane + k] = m[t].varc + wn.c2;
+        maps[4 * plane + k] = m[t].cov;
+        maps[5 * plane + k] = wn.k * sqrtf(m[t].varc);
+        maps[6 * plane + k] = ssim_of(m[t].muh, m[t].muc, varh, m[t].varc, m[t].cov, wn.c1, wn.c2);
+    }
+}
+
+constexpr int DTX = 32, DTY = 8;
+
+__global__ void __launch_bounds__(DTX *DTY)
+k_toggle_delta(const float *__restrict__ c, int cpitch, const uint32_t *__restrict__ bits, int words, int H, int W,
+               Win wn, const float *__restrict__ maps, float *__restrict__ dR)
+{
+    constexpr int SH = DTY + 2 * MAXR, SW = DTX + 2 * MAXR;
+    __shared__ float s_m[NMAP][SH][SW];
+    const int r = wn.r;
+    const int VH = H - 2 * r, VW = W - 2 * r;
+    const size_t plane = (size_t)VH * VW;
+    const int ay0 = blockIdx.y * DTY, ax0 = blockIdx.x * DTX;
+    const int tid = threadIdx.y * DTX + threadIdx.x;
+    // stage maps for output positions j in [a0 - r, a0 + tile + r) (image coords)
+    for (int i = tid; i < NMAP * SH * SW; i += DTX * DTY) {
+        const int q = i / (SH * SW), rem = i % (SH * SW);
+        const int yy = rem / SW, xx = rem % SW;
+        const int jy = ay0 - r + yy, jx = ax0 - r + xx;       // image coords of output j
+        float v = 0.f;
+        if (jy >= r && jy < H - r && jx >= r && jx < W - r) v = maps[q * plane + (size_t)(jy - r) * VW + (jx - r)];
+        s_m[q][yy][xx] = v;
+    }
+    __syncthreads();
+    const int ay = ay0 + threadIdx.y, ax = ax0 + threadIdx.x;
+    if (ay >= H || ax >= W) return;
+    const float ha = hbit(bits, words, ay, ax);
+    const float ca = c[(size_t)ay * cpitch + ax];
+    const float delta = 1.f - 2.f * ha;
+    float acc = 0.f;
+    for (int dy = -r; dy <= r; ++dy) {
+        const int jy = ay + dy;
+        if (jy < r || jy >= H - r) continue;
+        const float gy = wn.g[dy + r], wy = wn.w[dy + r];
+        for (int dx = -r; dx <= r; ++dx) {
+            const int jx = ax + dx;
+            if (jx < r || jx >= W - r) continue;
+            const int sy = threadIdx.y + r + dy, sx = threadIdx.x + r + dx;
+            const float g = gy * wn.g[dx + r];
+            const float w = wy * wn.w[dx + r];
+            const float e = s_m[0][sy][sx], muh = s_m[1][sy][sx], muc = s_m[2][sy][sx];
+            const float varc2 = s_m[3][sy][sx], cov = s_m[4][sy][sx], sig = s_m[5][sy][sx], ss = s_m[6][sy][sx];
+            const float muh2 = muh + delta * w;
+            const float varh2 = muh2 - muh2 * muh2;
+            const float cov2 = cov + delta * w * (ca - muc);
+            const float s2 = ((2.f * muh2 * muc + wn.c1) * (2.f * cov2 + wn.c2)) /
+                             ((muh2 * muh2 + muc * muc + wn.c1) * (varh2 + varc2));
+            acc += -(2.f * g * e + delta * g * g) + delta * wn.ws * sig * (s2 - ss);
+        }
+    }
+    dR[(size_t)ay * W + ax] = acc / ((float)VH * (float)VW);
+}
+
+Win make_win(const ht_reward_opts &o)
+{
+    Win wn;
+    wn.r = o.radius;
+    double sg = 0, sw = 0, g[2 * MAXR + 1], w[2 * MAXR + 1];
+    for (int i = -o.radius; i <= o.radius; ++i) {
+        g[i + o.radius] = exp(-(double)(i * i) / (2.0 * o.sigma_hvs * o.sigma_hvs));
+        w[i + o.radius] = exp(-(double)(i * i) / (2.0 * o.sigma_ssim * o.sigma_ssim));
+        sg += g[i + o.radius];
+        sw += w[i + o.radius];
+    }
+    for (int i = 0; i < 2 * MAXR + 1; ++i) {
+        wn.g[i] = i <= 2 * o.radius ? (float)(g[i] / sg) : 0.f;
+        wn.w[i] = i <= 2 * o.radius ? (float)(w[i] / sw) : 0.f;
+    }
+    wn.c1 = o.c1;
+    wn.c2 = o.c2;
+    wn.k = o.k_contrast;
+    wn.ws = o.w_s;
+    return wn;
+}
+
+}  // namespace
+
+ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
+                           double *out, cudaStream_t s)
+{
+    const Win wn = make_win(o);
+    // scratch: 3 accumulators + 1/M per image, staged in `out`'s stream via a small allocation
+    double *acc = nullptr;
+    HT_CUDA_TRY(cudaMallocAsync((void **)&acc, sizeof(double) * 4 * n, s));
+    HT_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * n, s));
+    double *inv_m_h = (double *)malloc(sizeof(double) * n);
+    for (int i = 0; i < n; ++i) inv_m_h[i] = 1.0 / ((double)(c[i].h - 2 * o.radius) * (double)(c[i].w - 2 * o.radius));
+    cudaError_t ce = cudaMemcpyAsync(acc + 3 * n, inv_m_h, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    free(inv_m_h);
+    HT_CUDA_TRY(ce);
+    for (int i = 0; i < n; ++i) {
+        const int VH = c[i].h - 2 * o.radius, VW = c[i].w - 2 * o.radius;
+        const dim3 grid((VW + RT - 1) / RT, (VH + RT - 1) / RT);
+        k_reward_tiles<<<grid, dim3(32, 8), 0, s>>>(c[i].contone, c[i].pitch, bits[i], ht_bits_row_words(c[i].w, 0),
+                                                    c[i].h, c[i].w, wn, acc + 3 * i);
+        HT_LAUNCH_CHECK();
+    }
+    k_reward_finalize<<<(n + 127) / 128, 128, 0, s>>>(acc, n, acc + 3 * n, o.w_s, out);
+    HT_LAUNCH_CHECK();
+    HT_CUDA_TRY(cudaFreeAsync(acc, s));
+    return HT_OK;
+}
+
+ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
+                           float *const *dR, float *scratch, size_t scratch_floats, cudaStream_t s)
+{
+    const Win wn = make_win(o);
+    for (int i = 0; i < n; ++i) {
+        const int H = c[i].h, W = c[i].w, VH = H - 2 * o.radius, VW = W - 2 * o.radius;
+        if ((size_t)NMAP * VH * VW > scratch_floats) {
+            ht_set_error("toggle-delta scratch too small");
+            return HT_ERR_INVALID_ARG;
+        }
+        const int words = ht_bits_row_words(W, 0);
+        k_moment_maps<<<dim3((VW + RT - 1) / RT, (VH + RT - 1) / RT), dim3(32, 8), 0, s>>>(
+            c[i].contone, c[i].pitch, bits[i], words, H, W, wn, scratch);
+        HT_LAUNCH_CHECK();
+        k_toggle_delta<<<dim3((W + DTX - 1) / DTX, (H + DTY - 1) / DTY), dim3(DTX, DTY), 0, s>>>(
+            c[i].contone, c[i].pitch, bits[i], words, H, W, wn, scratch, dR[i]);
+        HT_LAUNCH_CHECK();
+    }
+    return HT_OK;
+}
+
+size_t ht_toggle_scratch_floats(int h, int w, int r) { return (size_t)NMAP * (h - 2 * r) * (w - 2 * r); }

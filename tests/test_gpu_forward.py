@@ -1,0 +1,157 @@
+"""GPU parity of the policy forward + head (both forms) against the FP64 oracle.
+
+Rules: FP32 form -- actions equal the oracle's on every pixel the oracle decides by
+more than 1e-4 (|p - u| > 1e-4), probabilities within 2e-5.  BF16 form -- the same bit
+rule against the oracle emulating the BF16 rounding points (residual mismatches
+counted, at most 1e-3 of the decided pixels).  Probabilities: against the
+BF16-emulating oracle 99.9% within 1e-4 (only accumulation order differs; an
+activation that lands on a bf16 rounding boundary can flip one ulp and move p by up to
+a few 1e-3); against the pure FP64 oracle 99.9% within 2e-3 and all within 6e-3 (seven
+bf16 rounding stages of unit roundoff 2^-9 move a logit of magnitude ~2 by up to
+~1e-2, i.e. p by up to ~3e-3)."""
+
+BF16_Q_P999, BF16_Q_MAX = 1e-4, 4e-3
+BF16_X_P999, BF16_X_MAX = 2e-3, 6e-3
+
+
+def _p999(d):
+    return float(np.quantile(np.abs(d), 0.999))
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2304_12152_gb300 import _native as N
+from paper_2304_12152_gb300 import api, synth
+
+from _cases import compare_levels, decided_mask
+
+pytestmark = pytest.mark.gpu
+
+
+def _policy(chs, seed, prec, head=0, bias_seed=None):
+    ws, bs = synth.he_normal_policy(chs, seed)
+    if bias_seed is not None:
+        bs = synth.random_biases(chs, bias_seed)
+    return ws, bs, api.Policy(chs, ws, bs, head=head, precision=prec)
+
+
+def _run(pol, imgs, mode, seed):
+    cs = [torch.from_numpy(c).cuda() for c in imgs]
+    bits, probs = pol.halftone(cs, mode=mode, seed=seed, want_prob=True)
+    api.sync()
+    lev = [api.unpack_bits(b, c.shape[0], c.shape[1], pol.head) for b, c in zip(bits, imgs)]
+    return lev, [p.cpu().numpy().astype(np.float64) for p in probs], bits
+
+
+def _oracle(imgs, ws, bs, mode, seed, quant=0, region=None, image_ids=None):
+    out = []
+    for i, c in enumerate(imgs):
+        h, w = c.shape
+        reg = region if region is not None else (0, 0, h, w)
+        idx = image_ids[i] if image_ids is not None else i
+        lg, p, _ = O.forward(c, ws, bs, noise_seed=seed, image=idx, quant=quant, region=reg)
+        lev, u = O.sample(p, h, w, reg, mode, seed, idx)
+        out.append((p, lev, u))
+    return out
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp32_small_net_256(mode):
+    """Plain FP32 form, 6-layer 32-wide net, one 256x256 generator image (seed 0)."""
+    chs = synth.NET_SMALL
+    ws, bs, pol = _policy(chs, 0, N.HT_FP32)
+    img = [synth.contone_image(256, 256, seed=0)]
+    lev, probs, _ = _run(pol, img, mode, seed=0)
+    (p_or, lev_or, u), = _oracle(img, ws, bs, mode, 0)
+    assert np.abs(probs[0] - p_or).max() < 2e-5
+    dec = decided_mask(p_or, u, mode)
+    n, bad = compare_levels(lev[0], lev_or, dec)
+    assert n > 0.99 * lev_or.size and bad == 0
+    assert set(np.unique(lev[0])) <= {0, 1}
+
+
+def test_fp32_ragged_batch_bernoulli():
+    """Several images of uneven, non-multiple-of-tile sizes in one call; Philox image index =
+    position in the call; biases non-zero."""
+    chs = (2, 12, 20, 1)
+    ws, bs, pol = _policy(chs, 3, N.HT_FP32, bias_seed=4)
+    shapes = [(1, 1), (5, 300), (37, 53), (70, 33), (33, 64)]
+    imgs = [synth.contone_image(h, w, seed=5, index=i) for i, (h, w) in enumerate(shapes)]
+    lev, probs, bits = _run(pol, imgs, 1, seed=77)
+    ref = _oracle(imgs, ws, bs, 1, 77)
+    for i, (p_or, lev_or, u) in enumerate(ref):
+        assert np.abs(probs[i] - p_or).max() < 2e-5
+        n, bad = compare_levels(lev[i], lev_or, decided_mask(p_or, u, 1))
+        assert bad == 0, (shapes[i], bad)
+        # padding bits past w are zero
+        w = shapes[i][1]
+        if w % 32:
+            tail = (bits[i][:, -1].cpu().numpy().view(np.uint32) >> np.uint32(w % 32))
+            assert np.all(tail == 0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp32_softmax_head(mode):
+    chs = (2, 16, 16, 4)
+    ws, bs, pol = _policy(chs, 6, N.HT_FP32, head=N.HT_HEAD_SOFTMAX, bias_seed=7)
+    imgs = [synth.contone_image(45, 70, seed=8)]
+    lev, probs, _ = _run(pol, imgs, mode, seed=2)
+    (p_or, lev_or, u), = _oracle(imgs, ws, bs, mode, 2)
+    assert np.abs(probs[0] - p_or).max() < 2e-5
+    n, bad = compare_levels(lev[0], lev_or, decided_mask(p_or, u, mode))
+    assert bad == 0 and n > 0.99 * lev_or.size
+    assert set(np.unique(lev[0])) <= {0, 1, 2, 3}
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_bf16_wide_net_tiles_and_tails(mode):
+    """Tensor-core BF16 form, 8-layer 64-wide net; widths span several 128-pixel tiles with
+    ragged tails, heights several row units."""
+    chs = synth.NET_WIDE
+    ws, bs, pol = _policy(chs, 1, N.HT_BF16, bias_seed=2)
+    shapes = [(96, 200), (67, 261), (5, 129), (1, 1)]
+    imgs = [synth.contone_image(h, w, seed=1, index=i) for i, (h, w) in enumerate(shapes)]
+    lev, probs, _ = _run(pol, imgs, mode, seed=1)
+    ref_q = _oracle(imgs, ws, bs, mode, 1, quant=1)
+    ref_x = _oracle(imgs, ws, bs, mode, 1, quant=0)
+    tot_n = tot_bad = 0
+    for i in range(len(imgs)):
+        p_q, lev_q, u = ref_q[i]
+        p_x = ref_x[i][0]
+        assert np.abs(probs[i] - p_q).max() < BF16_Q_MAX and _p999(probs[i] - p_q) < BF16_Q_P999
+        assert np.abs(probs[i] - p_x).max() < BF16_X_MAX and _p999(probs[i] - p_x) < BF16_X_P999
+        n, bad = compare_levels(lev[i], lev_q, decided_mask(p_q, u, mode))
+        tot_n += n
+        tot_bad += bad
+    assert tot_bad <= max(1, 1e-3 * tot_n), (tot_bad, tot_n)
+
+
+def test_bf16_full_size_sampled():
+    """8 x 2048x2048 in one call (the benchmark's launch configuration, Bernoulli seed 1);
+    corners and an interior crop of every image against the oracle evaluated on the crop
+    with its halo."""
+    chs = synth.NET_WIDE
+    ws, bs, pol = _policy(chs, 1, N.HT_BF16)
+    imgs = [synth.contone_image(2048, 2048, seed=1, index=i) for i in range(8)]
+    lev, probs, _ = _run(pol, imgs, 1, seed=1)
+    rng = np.random.default_rng(0)
+    tot_n = tot_bad = 0
+    worst = 0.0
+    diffs = []
+    for i in range(8):
+        y, x = rng.integers(32, 2048 - 64, size=2)
+        regions = [(0, 0, 24, 24), (2048 - 24, 2048 - 40, 24, 40), (int(y), int(x), 24, 24)]
+        if i % 4 == 0:
+            regions = regions[:2]
+        for reg in regions:
+            y0, x0, rh, rw = reg
+            (p_q, lev_q, u), = _oracle([imgs[i]], ws, bs, 1, 1, quant=1, region=reg, image_ids=[i])
+            pg = probs[i][:, y0:y0 + rh, x0:x0 + rw]
+            worst = max(worst, float(np.abs(pg - p_q).max()))
+            diffs.append((pg - p_q).ravel())
+            n, bad = compare_levels(lev[i][y0:y0 + rh, x0:x0 + rw], lev_q, decided_mask(p_q, u, 1))
+            tot_n += n
+            tot_bad += bad
+    assert worst < BF16_Q_MAX and _p999(np.concatenate(diffs)) < BF16_Q_P999
+    assert tot_bad <= max(1, 1e-3 * tot_n), (tot_bad, tot_n)

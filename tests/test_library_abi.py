@@ -1,0 +1,74 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/ht.h declares; host-side argument checks need no GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2304_12152_gb300 import _native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ht.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ht_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    L = N.load()
+    decl = _declared()
+    assert len(decl) >= 15
+    missing = [s for s in decl if not hasattr(L, s)]
+    assert not missing, missing
+    assert set(decl) == set(N.EXPORTS)
+
+
+def test_host_only_calls():
+    L = N.load()
+    assert L.ht_version().startswith(b"ht ")
+    assert L.ht_bits_row_words(1, 0) == 1 and L.ht_bits_row_words(33, 0) == 2 and L.ht_bits_row_words(17, 1) == 2
+    o = N.RewardOpts()
+    L.ht_reward_opts_default(C.byref(o))
+    assert o.radius == 5 and abs(o.w_s - 0.06) < 1e-7 and abs(o.sigma_hvs - 2.0) < 1e-7
+
+
+@pytest.mark.parametrize("chs,head,prec,status", [
+    ((2, 4, 1), 0, N.HT_FP32, None),             # valid (would need a GPU) -> skipped below
+    ((3, 4, 1), 0, N.HT_FP32, N.HT_ERR_INVALID_ARG),
+    ((2, 4, 2), 0, N.HT_FP32, N.HT_ERR_INVALID_ARG),
+    ((2, 4, 1), 1, N.HT_FP32, N.HT_ERR_INVALID_ARG),
+    ((2, 65, 1), 0, N.HT_FP32, N.HT_ERR_INVALID_ARG),
+    ((2, 32, 32, 1), 0, N.HT_BF16, N.HT_ERR_UNSUPPORTED),
+    ((2, 64, 1), 0, N.HT_BF16, N.HT_ERR_UNSUPPORTED),
+])
+def test_policy_descriptor_validation(chs, head, prec, status):
+    if status is None:
+        pytest.skip("valid descriptor needs a device")
+    L = N.load()
+    d = N.PolicyDesc()
+    d.n_layers = len(chs) - 1
+    for i, c in enumerate(chs):
+        d.channels[i] = c
+    d.head, d.precision = head, prec
+    w = (C.c_float * 100000)()
+    h = C.c_void_p()
+    assert L.ht_create_policy(C.byref(d), w, w, C.byref(h)) == status
+    assert not h.value
+    assert len(L.ht_last_error()) > 0
+
+
+def test_argument_errors_before_launch():
+    L = N.load()
+    o = N.RewardOpts()
+    L.ht_reward_opts_default(C.byref(o))
+    img = (N.Image * 1)(N.Image(None, 8, 8, 8))
+    assert L.ht_reward(img, None, 1, C.byref(o), None, None) == N.HT_ERR_INVALID_ARG
+    assert L.ht_anisotropy_loss(None, 1, 16, 0, 0, 0, None, None, None) == N.HT_ERR_INVALID_ARG
+    q = C.c_void_p(16)
+    assert L.ht_anisotropy_loss(q, 1, 12, 0, 0, 0, q, None, None) == N.HT_ERR_INVALID_ARG
+    o.radius = 9
+    img2 = (N.Image * 1)(N.Image(16, 20, 20, 20))
+    assert L.ht_reward(img2, q, 1, C.byref(o), q, None) == N.HT_ERR_INVALID_ARG
