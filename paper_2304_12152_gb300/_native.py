@@ -60,12 +60,15 @@ def lib_path() -> str:
 
 
 def load(build_if_missing: bool = True):
-    """Load libht.so (building it first if asked and needed)."""
+    """Load libht.so (building it first if asked and needed).  HT_LIB_PATH selects
+    a library built elsewhere (e.g. with other compile-time tile parameters)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        path = os.environ.get("HT_LIB_PATH") or _build.LIB
+        if not os.path.exists(path) and path != _build.LIB:
+            raise RuntimeError(f"HT_LIB_PATH={path} does not exist")
         if not os.path.exists(path):
             if not build_if_missing:
                 raise RuntimeError(f"libht.so not built ({path}); run paper_2304_12152_gb300.build.build()")

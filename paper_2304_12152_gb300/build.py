@@ -29,8 +29,8 @@ def _deps_mtime() -> float:
     return max((os.path.getmtime(f) for f in files), default=0.0)
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra, build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _deps_mtime()):
         return obj
     tmp = obj + f".{os.getpid()}.tmp"
@@ -44,24 +44,28 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, defines=(), build_dir: str = BUILD) -> str:
+    """Compile and link; `defines` (e.g. ["HT_CONV_RIL=4"]) go to every translation
+    unit, `build_dir` receives the objects and libht.so."""
+    os.makedirs(build_dir, exist_ok=True)
+    lib = os.path.join(build_dir, "libht.so")
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     if force:
-        for f in glob.glob(os.path.join(BUILD, "*.o")):
+        for f in glob.glob(os.path.join(build_dir, "*.o")):
             os.remove(f)
-    extra = ["-Xptxas", "-v"] if verbose else []
+    extra = (["-Xptxas", "-v"] if verbose else []) + [f"-D{d}" for d in defines]
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
-        return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
+    if os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs):
+        return lib
+    LIB_ = lib
+    tmp = LIB_ + f".{os.getpid()}.tmp"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, LIB_)
+    return LIB_
 
 
 if __name__ == "__main__":

@@ -10,6 +10,8 @@
 //
 // This is the unfused reference form that the tensor-core path is timed
 // against; it is deliberately straightforward (SMEM-tiled direct convolution).
+#include <string.h>
+
 #include "head.cuh"
 
 namespace {
@@ -32,7 +34,7 @@ struct HeadArgs {
 __global__ void __launch_bounds__(TX *TY)
 k_conv3x3_fp32(const float *__restrict__ in, const float *__restrict__ contone, int cpitch,
                const float *__restrict__ w, const float *__restrict__ b, int Cin, int Cout, int H, int W,
-               float *__restrict__ out, HeadArgs ha)
+               float *__restrict__ out, HeadArgs ha, const float *__restrict__ mask)
 {
     __shared__ float s_in[CI_CHUNK][TY + 2][TX + 2];
     __shared__ float s_w[CI_CHUNK][9][CO_T];
@@ -88,9 +90,20 @@ k_conv3x3_fp32(const float *__restrict__ in, const float *__restrict__ contone, 
     const bool inside = (x < W) && (y < H);
     if (ha.head < 0) {
         if (inside) {
+            if (mask) {
+                // data-gradient pass: no bias; gradient masked by the ReLU of the layer's input
 #pragma unroll
-            for (int j = 0; j < CO_T; ++j)
-                if (co0 + j < Cout) out[(size_t)(co0 + j) * plane + (size_t)y * W + x] = fmaxf(acc[j] + b[co0 + j], 0.f);
+                for (int j = 0; j < CO_T; ++j)
+                    if (co0 + j < Cout) {
+                        const size_t k = (size_t)(co0 + j) * plane + (size_t)y * W + x;
+                        out[k] = mask[k] > 0.f ? acc[j] : 0.f;
+                    }
+            } else {
+#pragma unroll
+                for (int j = 0; j < CO_T; ++j)
+                    if (co0 + j < Cout)
+                        out[(size_t)(co0 + j) * plane + (size_t)y * W + x] = fmaxf(acc[j] + b[co0 + j], 0.f);
+            }
         }
         return;
     }
@@ -135,10 +148,60 @@ ht_status ht_run_fp32(ht_policy *p, const ht_image &img, uint32_t image_index, i
         ht_prof_start(last ? HTK_HEAD_FP32 : HTK_CONV_FP32, s);
         k_conv3x3_fp32<<<grid, block, 0, s>>>(in, l == 0 ? img.contone : nullptr, img.pitch,
                                               p->d_w + p->w_off[l], p->d_b + p->b_off[l], Cin, Cout, H, W,
-                                              out, ha);
+                                              out, ha, nullptr);
         ht_prof_stop(s);
         HT_LAUNCH_CHECK();
         in = out;
     }
+    return HT_OK;
+}
+
+// Forward of the FP32 form that keeps every hidden activation (training):
+// acts[l] receives layer l's output [ch[l+1]][H][W] for l < L-1; the head
+// writes the probability map `prob` and threshold actions into `bits`.
+ht_status ht_fwd_fp32_save(ht_policy *p, const ht_image &img, uint32_t image_index, uint64_t seed,
+                           float *const *acts, float *prob, uint32_t *bits, cudaStream_t s)
+{
+    const int H = img.h, W = img.w;
+    const dim3 block(TX, TY);
+    const float *in = nullptr;
+    for (int l = 0; l < p->L; ++l) {
+        const int Cin = p->ch[l], Cout = p->ch[l + 1];
+        const bool last = (l == p->L - 1);
+        HeadArgs ha;
+        ha.head = last ? p->head : -1;
+        ha.K = p->K;
+        ha.mode = HT_MODE_THRESHOLD;
+        ha.seed = seed;
+        ha.image = image_index;
+        ha.bits = bits;
+        ha.words = ht_bits_row_words(W, p->head);
+        ha.prob = prob;
+        const dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, last ? 1 : (Cout + CO_T - 1) / CO_T);
+        float *out = last ? nullptr : acts[l];
+        ht_prof_start(HTK_TRAIN, s);
+        k_conv3x3_fp32<<<grid, block, 0, s>>>(in, l == 0 ? img.contone : nullptr, img.pitch,
+                                              p->d_w + p->w_off[l], p->d_b + p->b_off[l], Cin, Cout, H, W,
+                                              out, ha, nullptr);
+        ht_prof_stop(s);
+        HT_LAUNCH_CHECK();
+        in = out;
+    }
+    return HT_OK;
+}
+
+// Data gradient of one layer: g_in = conv(g_out, W flipped and transposed),
+// masked by (act_in > 0).  wt: [Cin][Cout][3][3] flipped weights.
+ht_status ht_dgrad_fp32(const float *g_out, const float *wt, int Cout, int Cin, int H, int W, const float *act_in,
+                        float *g_in, cudaStream_t s)
+{
+    HeadArgs ha;
+    memset(&ha, 0, sizeof(ha));
+    ha.head = -1;
+    const dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, (Cin + CO_T - 1) / CO_T);
+    ht_prof_start(HTK_TRAIN, s);
+    k_conv3x3_fp32<<<grid, dim3(TX, TY), 0, s>>>(g_out, nullptr, 0, wt, nullptr, Cout, Cin, H, W, g_in, ha, act_in);
+    ht_prof_stop(s);
+    HT_LAUNCH_CHECK();
     return HT_OK;
 }

@@ -32,16 +32,18 @@
 // quarters 2, 3, 0, 1).  Every mbarrier wait is bounded (globaltimer); on
 // expiry the kernel records HT_ERR_TIMEOUT, drains its own copies and MMAs,
 // frees TMEM and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include "head.cuh"
 
 namespace {
 
+#ifndef HT_CONV_NSLOT
+#define HT_CONV_NSLOT 6
+#endif
 constexpr int TILE_M = 128;                // output pixels per MMA tile (one row segment)
 constexpr int ROW_PX = TILE_M + 2;         // staged pixels per input row (halo of 1 each side)
-constexpr int NSLOT = 6;                   // input-row ring depth
+constexpr int RU = 8;                      // output rows per work unit = TMEM accumulator blocks (8 x 64 cols)
+constexpr int NSLOT = HT_CONV_NSLOT;       // input-row ring depth (lookahead of the copy engine)
+constexpr int TMEM_COLS = 512;
 constexpr int NTHREADS = 192;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;   // 2 s per wait
 
@@ -51,7 +53,7 @@ struct Cfg {
     static constexpr int CPC = 16 / EB;                        // channels per 16-byte chunk
     static constexpr int NCHUNK = 64 / CPC;                    // chunks per pixel (8 / 4)
     static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;    // 16640 / 8320
-    static constexpr int W_BYTES = 9 * NCHUNK * 64 * 16;       // 73728 / 36864
+    static constexpr int W_BYTES = 9 * NCHUNK * 64 * 16;       // 73728 / 36864 ([dx][chunk][3 dy][64 n][16 B])
     static constexpr int KSTEPS = NCHUNK / 2;                  // MMAs per tap (K = 16 / 32)
     static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 1024 /*barriers, bias, scales*/;
 };
@@ -112,16 +114,6 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_fla
     }
 }
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                            uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -156,9 +148,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 // for kind::f16, E4M3 = 0 for kind::f8f6f4), both K-major, N >> 3 at bit 17,
 // M >> 4 at bit 24.
 template <bool FP8>
-__host__ __device__ constexpr uint32_t idesc_m128_n64()
+__host__ __device__ constexpr uint32_t idesc_m128(uint32_t n)
 {
-    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
 template <bool FP8>
@@ -197,6 +189,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr)
+{
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
 {
@@ -246,6 +248,7 @@ __device__ __forceinline__ void store_pixel(const float *v, void *out, int out_f
 }
 
 struct ConvParams {
+    const uint8_t *in;       // chunk-planar input activations
     const void *wpack;       // packed weights of this layer ([tap][chunk][n][16 B])
     const float *bias;       // [64]
     const float *wscale;     // FP8: per-output-channel weight scale, else null
@@ -260,8 +263,21 @@ struct ConvParams {
 // ---------------------------------------------------------------------------
 // 64 -> 64 layer on tcgen05
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// 64 -> 64 layer on tcgen05
+//
+// Work unit = RU (8) consecutive output rows x one 128-pixel column tile.  Its
+// RU + 2 input rows are staged one after another; each staged input row r is
+// multiplied, for every dx and K step, against the three kernel rows stacked
+// along N ([dy=2 | dy=1 | dy=0], N = 192): the three 64-column slices of the
+// product are exactly the contributions of row r to output rows r-1, r, r+1,
+// and they land in those rows' TMEM accumulator blocks, which sit side by side
+// (block j = output row y0 + j).  Edge input rows use N = 64 / 128.  Every
+// accumulator block is zeroed by the epilogue after it is drained, so all MMAs
+// accumulate.  Per output row: 12-15 MMAs of N = 192 instead of 36 of N = 64.
+// ---------------------------------------------------------------------------
 template <bool FP8>
-__global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap, const ConvParams P)
+__global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 {
     using C = Cfg<FP8>;
     extern __shared__ uint8_t smem_raw[];
@@ -269,11 +285,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const __grid_constant__
     uint8_t *s_w = smem;
     uint8_t *s_rows = smem + C::W_BYTES;
     uint64_t *bars = (uint64_t *)(s_rows + NSLOT * C::SLOT_BYTES);
-    uint64_t *full = bars, *empty = bars + NSLOT, *wbar = bars + 2 * NSLOT, *accf = wbar + 1, *acce = accf + 2,
-             *drain = acce + 2;
+    uint64_t *full = bars, *empty = bars + NSLOT, *wbar = bars + 2 * NSLOT, *bfull = wbar + 1, *bfree = bfull + RU,
+             *drain = bfree + RU;
     uint32_t *s_tmem = (uint32_t *)(drain + 1);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
-    float *s_scale = (float *)(s_tmem + 2);      // 64 (dequant scale)
+    float *s_scale = (float *)(s_tmem + 4);      // 64 (dequant scale), 16-byte aligned
     float *s_bias = s_scale + 64;                 // 64
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -284,9 +300,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const __grid_constant__
             mbar_init(smem_u32(&empty[i]), 1);
         }
         mbar_init(smem_u32(wbar), 1);
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(smem_u32(&accf[i]), 1);
-            mbar_init(smem_u32(&acce[i]), 4);
+        for (int i = 0; i < RU; ++i) {
+            mbar_init(smem_u32(&bfull[i]), 1);
+            mbar_init(smem_u32(&bfree[i]), 4);
         }
         mbar_init(smem_u32(drain), 1);
         *s_abort = 0;
@@ -296,107 +312,160 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const __grid_constant__
         s_bias[threadIdx.x] = P.bias[threadIdx.x];
         s_scale[threadIdx.x] = FP8 ? P.in_scale * P.wscale[threadIdx.x] : 1.f;
     }
-    if (warp == 0) tmem_alloc(smem_u32(s_tmem), 128);
+    if (warp == 0) tmem_alloc(smem_u32(s_tmem), TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *s_tmem;
 
     if (warp == 0) {
-        // ------------------------- TMA producer -------------------------
+        // ------------------------- producer -------------------------
+        // One input row = NCHUNK contiguous runs of ROW_PX * 16 bytes in HBM (one
+        // per channel chunk).  In-image pixels arrive by bulk async copies
+        // (complete_tx on the slot's barrier); halo pixels outside the image are
+        // zero-filled by the warp with shared stores, made visible to the
+        // tensor core's async proxy by a proxy fence before the barrier arrive.
+        int last_issued[NSLOT];
+        for (int i = 0; i < NSLOT; ++i) last_issued[i] = -1;
         if (lane == 0) {
-            int last_issued[NSLOT];
-            for (int i = 0; i < NSLOT; ++i) last_issued[i] = -1;
             mbar_arrive_expect_tx(smem_u32(wbar), C::W_BYTES);
             bulk_g2s(smem_u32(s_w), P.wpack, C::W_BYTES, smem_u32(wbar));
-            uint32_t li = 0;
-            bool ok = true;
-            for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
-                const int xt = u % P.n_xtiles, ys = u / P.n_xtiles;
-                const int y0 = ys * P.rows_per_unit;
-                const int y1 = min(P.H, y0 + P.rows_per_unit);
-                const int x0 = xt * TILE_M;
-                for (int r = 0; r < (y1 - y0) + 2; ++r, ++li) {
-                    const int slot = (int)(li % NSLOT);
-                    const uint32_t ph = (li / NSLOT) & 1u;
-                    if (!mbar_wait(smem_u32(&empty[slot]), ph ^ 1u, s_abort, P.err)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_expect_tx(smem_u32(&full[slot]), C::SLOT_BYTES);
-                    tma_load_4d(smem_u32(s_rows + slot * C::SLOT_BYTES), &tmap, 0, x0 - 1, y0 - 1 + r, 0,
-                                smem_u32(&full[slot]));
-                    last_issued[slot] = (int)li;
+        }
+        uint32_t li = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
+            const int xt = u % P.n_xtiles, ys = u / P.n_xtiles;
+            const int y0 = ys * RU;
+            const int y1 = min(P.H, y0 + RU);
+            const int x0 = xt * TILE_M;
+            const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, P.W);   // in-image pixel range
+            for (int r = 0; r < (y1 - y0) + 2; ++r, ++li) {
+                const int slot = (int)(li % NSLOT);
+                const uint32_t ph = (li / NSLOT) & 1u;
+                int got = 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&empty[slot]), ph ^ 1u, s_abort, P.err) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, got, 0)) {
+                    ok = false;
+                    break;
                 }
+                uint8_t *dst = s_rows + slot * C::SLOT_BYTES;
+                const int yy = y0 - 1 + r;
+                const bool row_in = (yy >= 0 && yy < P.H);
+                bool zeroed = false;
+                if (!row_in) {
+                    for (int k = lane; k < C::NCHUNK * ROW_PX; k += 32)
+                        *reinterpret_cast<uint4 *>(dst + (size_t)k * 16) = make_uint4(0, 0, 0, 0);
+                    zeroed = true;
+                } else if (lo > x0 - 1 || hi < x0 - 1 + ROW_PX) {
+                    const int nl = lo - (x0 - 1), nr = (x0 - 1 + ROW_PX) - hi;
+                    for (int k = lane; k < C::NCHUNK * (nl + nr); k += 32) {
+                        const int c = k / (nl + nr), j = k % (nl + nr);
+                        const int px = j < nl ? j : (hi - (x0 - 1)) + (j - nl);
+                        *reinterpret_cast<uint4 *>(dst + ((size_t)c * ROW_PX + px) * 16) = make_uint4(0, 0, 0, 0);
+                    }
+                    zeroed = true;
+                }
+                if (zeroed) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    const uint32_t run = (uint32_t)(hi - lo) * 16u;
+                    if (row_in && hi > lo) {
+                        mbar_arrive_expect_tx(smem_u32(&full[slot]), run * C::NCHUNK);
+                        for (int c = 0; c < C::NCHUNK; ++c)
+                            bulk_g2s(smem_u32(dst + ((size_t)c * ROW_PX + (lo - (x0 - 1))) * 16),
+                                     P.in + (((size_t)c * P.H + yy) * P.W + lo) * 16, run, smem_u32(&full[slot]));
+                    } else {
+                        mbar_arrive(smem_u32(&full[slot]));
+                    }
+                }
+                last_issued[slot] = (int)li;
             }
-            // drain: every issued copy must have landed before the CTA exits
-            for (int s = 0; s < NSLOT; ++s)
-                if (last_issued[s] >= 0)
-                    mbar_wait(smem_u32(&full[s]), ((uint32_t)last_issued[s] / NSLOT) & 1u, s_abort, P.err, true);
+        }
+        // drain: every issued copy must have landed before the CTA exits
+        if (lane == 0) {
+            for (int s2 = 0; s2 < NSLOT; ++s2)
+                if (last_issued[s2] >= 0)
+                    mbar_wait(smem_u32(&full[s2]), ((uint32_t)last_issued[s2] / NSLOT) & 1u, s_abort, P.err, true);
             mbar_wait(smem_u32(wbar), 0, s_abort, P.err, true);
         }
+        __syncwarp();
     } else if (warp == 1) {
         // ------------------------- MMA issuer -------------------------
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_m128_n64<FP8>();
-            const uint32_t w_addr = smem_u32(s_w), rows_addr = smem_u32(s_rows);
-            bool ok = mbar_wait(smem_u32(wbar), 0, s_abort, P.err);
-            uint32_t ci = 0, ai = 0;
-            for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
-                const int ys = u / P.n_xtiles;
-                const int y0 = ys * P.rows_per_unit;
-                const int nrows = min(P.H, y0 + P.rows_per_unit) - y0;
-                for (int i = 0; i < nrows && ok; ++i) {
-                    for (int j = 0; j < 3 && ok; ++j) {
-                        const uint32_t q = ci + i + j;
-                        ok = mbar_wait(smem_u32(&full[q % NSLOT]), (q / NSLOT) & 1u, s_abort, P.err);
-                    }
-                    const uint32_t a = ai & 1u;
-                    if (ok) ok = mbar_wait(smem_u32(&acce[a]), ((ai >> 1) & 1u) ^ 1u, s_abort, P.err);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t d = tmem_base + a * 64u;
-#pragma unroll 1
-                    for (int dy = 0; dy < 3; ++dy) {
-                        const uint32_t slot_addr = rows_addr + ((ci + i + dy) % NSLOT) * C::SLOT_BYTES;
-#pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
-#pragma unroll
-                            for (int ks = 0; ks < C::KSTEPS; ++ks) {
-                                const uint64_t adesc = sdesc(slot_addr + (2 * ks * ROW_PX + dx) * 16, ROW_PX * 16, 128);
-                                const uint64_t bdesc = sdesc(w_addr + ((dy * 3 + dx) * C::NCHUNK + 2 * ks) * 1024, 1024, 128);
-                                mma_ss<FP8>(d, adesc, bdesc, idesc, (dy | dx | ks) != 0);
-                            }
-                        }
-                    }
-                    mma_commit(smem_u32(&accf[a]));
-                    mma_commit(smem_u32(&empty[(ci + i) % NSLOT]));
-                    ++ai;
-                }
+        // Warp-uniform schedule; lane 0 waits (result broadcast) and issues.
+        // Descriptors = base descriptor + compile-time / small offsets added to
+        // the 14-bit start-address field (addresses stay below 256 KB).
+        const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
+        const uint64_t b_base = sdesc(smem_u32(s_w), 3 * 1024, 128);
+        auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
+            int got = 0;
+            if (lane == 0) got = mbar_wait(bar, par, s_abort, P.err) ? 1 : 0;
+            return __shfl_sync(0xffffffffu, got, 0) != 0;
+        };
+        bool ok = wait1(smem_u32(wbar), 0);
+        uint32_t q = 0, uit = 0;
+        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
+            const int ys = u / P.n_xtiles;
+            const int y0 = ys * RU;
+            const int nrows = min(P.H, y0 + RU) - y0;
+            for (int k = 0; k < nrows + 2 && ok; ++k, ++q) {
+                ok = wait1(smem_u32(&full[q % NSLOT]), (q / NSLOT) & 1u);
+                if (ok && k < nrows) ok = wait1(smem_u32(&bfree[k]), uit & 1u);   // block k enters use
                 if (!ok) break;
-                mma_commit(smem_u32(&empty[(ci + nrows) % NSLOT]));
-                mma_commit(smem_u32(&empty[(ci + nrows + 1) % NSLOT]));
-                ci += nrows + 2;
+                tc_fence_after();
+                if (lane == 0) {
+                    const int jlo = max(0, k - 2), jhi = min(nrows - 1, k);
+                    const uint32_t n = (uint32_t)(jhi - jlo + 1) * 64u;
+                    const uint32_t idesc = idesc_m128<FP8>(n);
+                    const uint32_t sb = (uint32_t)(2 - k + jlo);                       // first stacked dy block
+                    const uint32_t d = tmem_base + (uint32_t)jlo * 64u;
+                    const uint64_t a_q = a_base + (uint64_t)(((q % NSLOT) * (uint32_t)C::SLOT_BYTES) >> 4);
+                    const uint64_t b_q = b_base + (uint64_t)((sb * 1024u) >> 4);
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                        for (int ks = 0; ks < C::KSTEPS; ++ks)
+                            mma_ss<FP8>(d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
+                                        b_q + (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * 1024) >> 4), idesc, 1u);
+                    mma_commit(smem_u32(&empty[q % NSLOT]));
+                    if (k >= 2) mma_commit(smem_u32(&bfull[k - 2]));     // output row k-2 complete
+                }
+                __syncwarp();
             }
-            // drain: all issued MMAs complete before TMEM is released
+            if (!ok) break;
+            // keep every block's barrier phases in step for short units
+            if (lane == 0)
+                for (int j = nrows; j < RU; ++j) mma_commit(smem_u32(&bfull[j]));
+            __syncwarp();
+        }
+        // drain: all issued MMAs complete before TMEM is released
+        if (lane == 0) {
             mma_commit(smem_u32(drain));
             mbar_wait(smem_u32(drain), 0, s_abort, P.err, true);
         }
+        __syncwarp();
     } else {
         // ------------------------- epilogue -------------------------
         const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
         const int px = quarter * 32 + lane;           // pixel within the tile
-        uint32_t ai = 0;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        // accumulators start at zero (TMEM is undefined after allocation)
+        for (int j = 0; j < RU; ++j)
+            for (int c = 0; c < 64; c += 16) tmem_zero16(lane_base + j * 64 + c);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+            for (int j = 0; j < RU; ++j) mbar_arrive(smem_u32(&bfree[j]));
+        uint32_t uit = 0;
         bool ok = true;
-        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
+        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
             const int xt = u % P.n_xtiles, ys = u / P.n_xtiles;
-            const int y0 = ys * P.rows_per_unit;
-            const int nrows = min(P.H, y0 + P.rows_per_unit) - y0;
+            const int y0 = ys * RU;
+            const int nrows = min(P.H, y0 + RU) - y0;
             const int x = xt * TILE_M + px;
-            for (int i = 0; i < nrows; ++i, ++ai) {
-                const uint32_t a = ai & 1u;
+            for (int j = 0; j < RU; ++j) {
                 int got = 0;
-                if (lane == 0) got = mbar_wait(smem_u32(&accf[a]), (ai >> 1) & 1u, s_abort, P.err) ? 1 : 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&bfull[j]), uit & 1u, s_abort, P.err) ? 1 : 0;
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
@@ -404,19 +473,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const __grid_constant__
                 }
                 tc_fence_after();
                 float v[64];
-                const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + a * 64u;
-                tmem_ld16(taddr + 0, v + 0);
-                tmem_ld16(taddr + 16, v + 16);
-                tmem_ld16(taddr + 32, v + 32);
-                tmem_ld16(taddr + 48, v + 48);
-                tmem_wait_ld();
+                if (j < nrows) {
+                    const uint32_t taddr = lane_base + j * 64u;
+                    tmem_ld16(taddr + 0, v + 0);
+                    tmem_ld16(taddr + 16, v + 16);
+                    tmem_ld16(taddr + 32, v + 32);
+                    tmem_ld16(taddr + 48, v + 48);
+                    tmem_wait_ld();
+                    for (int c = 0; c < 64; c += 16) tmem_zero16(taddr + c);
+                    tmem_wait_st();
+                }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&acce[a]));
-                if (x < P.W) {
+                if (lane == 0) mbar_arrive(smem_u32(&bfree[j]));
+                if (j < nrows && x < P.W) {
 #pragma unroll
-                    for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], s_scale[n], s_bias[n]), 0.f);
-                    store_pixel(v, P.out, P.out_fp8, P.out_inv_scale, P.H, P.W, y0 + i, x);
+                    for (int n4 = 0; n4 < 16; ++n4) {
+                        const float4 sc = reinterpret_cast<const float4 *>(s_scale)[n4];
+                        const float4 bi = reinterpret_cast<const float4 *>(s_bias)[n4];
+                        v[4 * n4 + 0] = fmaxf(fmaf(v[4 * n4 + 0], sc.x, bi.x), 0.f);
+                        v[4 * n4 + 1] = fmaxf(fmaf(v[4 * n4 + 1], sc.y, bi.y), 0.f);
+                        v[4 * n4 + 2] = fmaxf(fmaf(v[4 * n4 + 2], sc.z, bi.z), 0.f);
+                        v[4 * n4 + 3] = fmaxf(fmaf(v[4 * n4 + 3], sc.w, bi.w), 0.f);
+                    }
+                    store_pixel(v, P.out, P.out_fp8, P.out_inv_scale, P.H, P.W, y0 + j, x);
                 }
             }
         }
@@ -426,7 +506,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const __grid_constant__
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, 128);
+        tmem_dealloc(tmem_base, TMEM_COLS);
     }
 }
 
@@ -552,43 +632,6 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_tc(const uint8_t *__restric
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-PFN_cuTensorMapEncodeTiled_v12000 get_encode()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
-}
-
-// 4-D map over a chunk-planar activation: dims {16 B, W, H, chunks}.
-ht_status make_act_map(CUtensorMap *m, const void *base, int H, int W, bool fp8)
-{
-    auto enc = get_encode();
-    if (!enc) {
-        ht_set_error("cuTensorMapEncodeTiled unavailable");
-        return HT_ERR_CUDA;
-    }
-    const int cpc = fp8 ? 16 : 8, nchunk = fp8 ? 4 : 8;
-    cuuint64_t dims[4] = {(cuuint64_t)cpc, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nchunk};
-    cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
-    cuuint32_t box[4] = {(cuuint32_t)cpc, (cuuint32_t)ROW_PX, 1, (cuuint32_t)nchunk};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        ht_set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-        return HT_ERR_CUDA;
-    }
-    return HT_OK;
-}
-
 int num_sms()
 {
     static int n = 0;
@@ -601,25 +644,8 @@ int num_sms()
     return n;
 }
 
-// rows per work unit: balances the persistent grid against the halo re-read
-int pick_rows_per_unit(int H, int n_xtiles, int sms)
-{
-    int best = 16;
-    double best_cost = 1e30;
-    for (int r = 4; r <= 64; r += 2) {
-        const long units = (long)n_xtiles * ((H + r - 1) / r);
-        const long rounds = (units + sms - 1) / sms;
-        const double cost = (double)rounds * (r + 2);      // critical-path row loads
-        if (cost < best_cost) {
-            best_cost = cost;
-            best = r;
-        }
-    }
-    return best;
-}
-
 template <bool FP8>
-ht_status launch_conv(const CUtensorMap &m, const ConvParams &P, cudaStream_t s)
+ht_status launch_conv(const ConvParams &P, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
@@ -628,7 +654,7 @@ ht_status launch_conv(const CUtensorMap &m, const ConvParams &P, cudaStream_t s)
     }
     const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
     ht_prof_start(FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
-    k_conv_tc<FP8><<<grid, NTHREADS, Cfg<FP8>::SMEM, s>>>(m, P);
+    k_conv_tc<FP8><<<grid, NTHREADS, Cfg<FP8>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -713,7 +739,8 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
             for (int tap = 0; tap < 9; ++tap)
                 for (int c = 0; c < 64; ++c) {
                     const float wv = W[((size_t)n * 64 + c) * 9 + tap];
-                    const size_t off = (((size_t)tap * nchunk + c / cpc) * 64 + n) * 16;
+                    const int dy = tap / 3, dx = tap % 3;
+                    const size_t off = ((((size_t)dx * nchunk + c / cpc) * 3 + (2 - dy)) * 64 + n) * 16;
                     if (fp8) {
                         dst[off + (c % cpc)] = f64_to_e4m3_rne((double)wv / sc);
                     } else {
@@ -764,15 +791,12 @@ ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int
         HT_LAUNCH_CHECK();
     }
     const int n_xtiles = (W + TILE_M - 1) / TILE_M;
-    const int rpu = pick_rows_per_unit(H, n_xtiles, num_sms());
+    const int rpu = RU;
     int cur = 0;
     for (int l = 1; l <= n_inner; ++l) {
-        const bool in8 = fp8;
         const bool out8 = fp8 && (l < n_inner);
-        CUtensorMap m;
-        ht_status st = make_act_map(&m, buf[cur], H, W, in8);
-        if (st != HT_OK) return st;
         ConvParams P;
+        P.in = buf[cur];
         P.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (l - 1);
         P.bias = p->d_b + p->b_off[l];
         P.wscale = fp8 ? p->d_wscale + 64 * (l - 1) : nullptr;
@@ -786,7 +810,7 @@ ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int
         P.rows_per_unit = rpu;
         P.n_units = n_xtiles * ((H + rpu - 1) / rpu);
         P.err = err;
-        st = fp8 ? launch_conv<true>(m, P, s) : launch_conv<false>(m, P, s);
+        const ht_status st = fp8 ? launch_conv<true>(P, s) : launch_conv<false>(P, s);
         if (st != HT_OK) return st;
         cur ^= 1;
     }

@@ -110,6 +110,10 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s);
 ht_status ht_run_fp32(ht_policy *p, const ht_image &img, uint32_t image_index, int mode, uint64_t seed,
                       uint32_t *bits, float *prob, float *act_a, float *act_b, cudaStream_t s);
 size_t ht_fp32_ws_bytes(const ht_policy *p, int h, int w);
+ht_status ht_fwd_fp32_save(ht_policy *p, const ht_image &img, uint32_t image_index, uint64_t seed,
+                           float *const *acts, float *prob, uint32_t *bits, cudaStream_t s);
+ht_status ht_dgrad_fp32(const float *g_out, const float *wt, int Cout, int Cin, int H, int W, const float *act_in,
+                        float *g_in, cudaStream_t s);
 
 // tensor-core form, one image
 ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int mode, uint64_t seed,
