@@ -44,7 +44,7 @@ constexpr int ROW_PX = TILE_M + 2;         // staged pixels per input row (halo 
 constexpr int RU = 8;                      // output rows per work unit = TMEM accumulator blocks (8 x 64 cols)
 constexpr int NSLOT = HT_CONV_NSLOT;       // input-row ring depth (lookahead of the copy engine)
 constexpr int TMEM_COLS = 512;
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 320;                // producer, MMA issuer, 8 epilogue warps
 constexpr unsigned long long kTimeoutNs = 2000000000ull;   // 2 s per wait
 
 template <bool FP8>
@@ -55,7 +55,7 @@ struct Cfg {
     static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;    // 16640 / 8320
     static constexpr int W_BYTES = 9 * NCHUNK * 64 * 16;       // 73728 / 36864 ([dx][chunk][3 dy][64 n][16 B])
     static constexpr int KSTEPS = NCHUNK / 2;                  // MMAs per tap (K = 16 / 32)
-    static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 1024 /*barriers, bias, scales*/;
+    static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 4096 /*barriers, bias, scales, head*/;
 };
 
 // ---------------------------------------------------------------------------
@@ -247,15 +247,45 @@ __device__ __forceinline__ void store_pixel(const float *v, void *out, int out_f
     }
 }
 
+// Stores channels 32*half .. 32*half+31 of one pixel (chunk-planar layout).
+__device__ __forceinline__ void store_channels32(const float *v, int half, void *out, int out_fp8, float inv_scale,
+                                                 int H, int W, int y, int x)
+{
+    uint8_t *o = (uint8_t *)out;
+    if (out_fp8) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float q[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) q[i] = bf16_round(v[16 * c + i]) * inv_scale;
+            const uint4 u = make_uint4(pack_e4m3x4(q[0], q[1], q[2], q[3]), pack_e4m3x4(q[4], q[5], q[6], q[7]),
+                                       pack_e4m3x4(q[8], q[9], q[10], q[11]), pack_e4m3x4(q[12], q[13], q[14], q[15]));
+            *reinterpret_cast<uint4 *>(o + (((size_t)(2 * half + c) * H + y) * W + x) * 16) = u;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint4 u = make_uint4(pack_bf16x2(v[8 * c + 0], v[8 * c + 1]), pack_bf16x2(v[8 * c + 2], v[8 * c + 3]),
+                                       pack_bf16x2(v[8 * c + 4], v[8 * c + 5]), pack_bf16x2(v[8 * c + 6], v[8 * c + 7]));
+            *reinterpret_cast<uint4 *>(o + (((size_t)(4 * half + c) * H + y) * W + x) * 16) = u;
+        }
+    }
+}
+
 struct ConvParams {
     const uint8_t *in;       // chunk-planar input activations
-    const void *wpack;       // packed weights of this layer ([tap][chunk][n][16 B])
-    const float *bias;       // [64]
-    const float *wscale;     // FP8: per-output-channel weight scale, else null
-    float in_scale;          // FP8: scale of the input activations
+    const void *wpack;       // packed weights of this layer ([dx][chunk][3 dy][n][16 B])
+    // per-output-channel epilogue constants, read straight from the kernel's
+    // constant bank: acc * scale[n] + bias[n] (scale = input scale x weight
+    // scale in the FP8 form, 1 otherwise)
+    float scale[64];
+    float bias[64];
+    float head_w[9 * 64];    // fused 1-logit head: last-layer weights [tap][channel]
     float out_inv_scale;     // FP8 output: 1 / scale of the next layer's input
     int out_fp8;
     void *out;               // chunk-planar output
+    float *partials;         // non-null on the last hidden layer of a 1-logit head: receives the 9 per-tap dot
+                             // products of the head, [9][H][W], instead of the activations
     int H, W, n_xtiles, rows_per_unit, n_units;
     int *err;
 };
@@ -276,7 +306,7 @@ struct ConvParams {
 // accumulator block is zeroed by the epilogue after it is drained, so all MMAs
 // accumulate.  Per output row: 12-15 MMAs of N = 192 instead of 36 of N = 64.
 // ---------------------------------------------------------------------------
-template <bool FP8>
+template <bool FP8, bool HEAD>
 __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 {
     using C = Cfg<FP8>;
@@ -289,8 +319,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
              *drain = bfree + RU;
     uint32_t *s_tmem = (uint32_t *)(drain + 1);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
-    float *s_scale = (float *)(s_tmem + 4);      // 64 (dequant scale), 16-byte aligned
-    float *s_bias = s_scale + 64;                 // 64
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -307,10 +335,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         mbar_init(smem_u32(drain), 1);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (threadIdx.x < 64) {
-        s_bias[threadIdx.x] = P.bias[threadIdx.x];
-        s_scale[threadIdx.x] = FP8 ? P.in_scale * P.wscale[threadIdx.x] : 1.f;
     }
     if (warp == 0) tmem_alloc(smem_u32(s_tmem), TMEM_COLS);
     tc_fence_before();
@@ -445,17 +469,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         __syncwarp();
     } else {
         // ------------------------- epilogue -------------------------
+        // Eight warps: two per TMEM lane quarter; group g drains blocks j = g, g+2, ...
         const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
+        const int grp = (warp - 2) >> 2;              // 0 or 1
         const int px = quarter * 32 + lane;           // pixel within the tile
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         // accumulators start at zero (TMEM is undefined after allocation)
-        for (int j = 0; j < RU; ++j)
+        for (int j = grp; j < RU; j += 2)
             for (int c = 0; c < 64; c += 16) tmem_zero16(lane_base + j * 64 + c);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0)
-            for (int j = 0; j < RU; ++j) mbar_arrive(smem_u32(&bfree[j]));
+            for (int j = grp; j < RU; j += 2) mbar_arrive(smem_u32(&bfree[j]));
         uint32_t uit = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
@@ -463,7 +489,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
             const int y0 = ys * RU;
             const int nrows = min(P.H, y0 + RU) - y0;
             const int x = xt * TILE_M + px;
-            for (int j = 0; j < RU; ++j) {
+            for (int j = grp; j < RU; j += 2) {
                 int got = 0;
                 if (lane == 0) got = mbar_wait(smem_u32(&bfull[j]), uit & 1u, s_abort, P.err) ? 1 : 0;
                 got = __shfl_sync(0xffffffffu, got, 0);
@@ -488,15 +514,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 if (lane == 0) mbar_arrive(smem_u32(&bfree[j]));
                 if (j < nrows && x < P.W) {
 #pragma unroll
-                    for (int n4 = 0; n4 < 16; ++n4) {
-                        const float4 sc = reinterpret_cast<const float4 *>(s_scale)[n4];
-                        const float4 bi = reinterpret_cast<const float4 *>(s_bias)[n4];
-                        v[4 * n4 + 0] = fmaxf(fmaf(v[4 * n4 + 0], sc.x, bi.x), 0.f);
-                        v[4 * n4 + 1] = fmaxf(fmaf(v[4 * n4 + 1], sc.y, bi.y), 0.f);
-                        v[4 * n4 + 2] = fmaxf(fmaf(v[4 * n4 + 2], sc.z, bi.z), 0.f);
-                        v[4 * n4 + 3] = fmaxf(fmaf(v[4 * n4 + 3], sc.w, bi.w), 0.f);
+                    for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], P.scale[n], P.bias[n]), 0.f);
+                    if constexpr (HEAD) {
+                        // fused 64 -> 1 head: per-tap dot products of the bf16-rounded activations
+                        const size_t plane = (size_t)P.H * P.W, o = (size_t)(y0 + j) * P.W + x;
+                        float acc[9];
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+#pragma unroll
+                        for (int n = 0; n < 64; ++n) {
+                            const float a = bf16_round(v[n]);
+#pragma unroll
+                            for (int t = 0; t < 9; ++t) acc[t] = fmaf(a, P.head_w[t * 64 + n], acc[t]);   // nine chains
+                        }
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) P.partials[t * plane + o] = acc[t];
+                    } else {
+                        store_pixel(v, P.out, P.out_fp8, P.out_inv_scale, P.H, P.W, y0 + j, x);
                     }
-                    store_pixel(v, P.out, P.out_fp8, P.out_inv_scale, P.H, P.W, y0 + j, x);
                 }
             }
         }
@@ -511,68 +546,177 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 }
 
 // ---------------------------------------------------------------------------
-// Layer 1 (2 -> 64) on CUDA cores; writes the chunk-planar layout.
-// Tile: 128 pixels x 4 rows, one thread per column.
+// Layer 1 (2 -> 64) on tcgen05.  K would be 9 taps x 2 channels = 18, too thin
+// and too precise for one bf16 product, so every input v and weight w is split
+// into bf16 hi + lo parts and each product is taken as v_hi w_hi + v_hi w_lo +
+// v_lo w_hi (the dropped v_lo w_lo term is ~2^-16 relative): K = 9 x 6 = 54,
+// padded to 64.  One CTA = 128 pixels x F1_ROWS rows; per row the threads build
+// the A tile (im2col of c and z in the canonical no-swizzle layout), one thread
+// issues 4 MMAs (M = 128, N = 64, K = 16) into TMEM, and the epilogue applies
+// bias and ReLU and stores the chunk-planar activations.  Several CTAs share
+// an SM, so one CTA's MMA overlaps another's A build and stores.
 // ---------------------------------------------------------------------------
-constexpr int FT_X = 128, FT_Y = 4;
+constexpr int F1_ROWS = 16;
+constexpr int F1_SMEM = 1024 + 2 * 8 * 128 * 16 + 8 * 64 * 16 + 2 * (F1_ROWS + 2) * (TILE_M + 2) * 4 + 64 * 4 + 64;
 
-__global__ void __launch_bounds__(FT_X) k_first_tc(const float *__restrict__ contone, int cpitch, int H, int W,
-                                                   uint64_t seed, uint32_t image, const float *__restrict__ w1,
-                                                   const float *__restrict__ b1, void *out, int out_fp8,
-                                                   float out_inv_scale)
+__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo)
 {
-    __shared__ float s_c[FT_Y + 2][FT_X + 2];
-    __shared__ float s_z[FT_Y + 2][FT_X + 2];
-    __shared__ float4 s_w[18][16];               // [tap*2 + ci][o/4]
-    __shared__ float4 s_b[16];
-    const int x0 = blockIdx.x * FT_X, y0 = blockIdx.y * FT_Y;
-    for (int i = threadIdx.x; i < (FT_Y + 2) * (FT_X + 2); i += FT_X) {
-        const int yy = i / (FT_X + 2), xx = i % (FT_X + 2);
+    hi = bf16_round(v);
+    lo = bf16_round(v - hi);
+}
+
+// A row of one pixel: per tap (c_hi, c_hi, c_lo, z_hi, z_hi, z_lo), then zeros,
+// stored as 8 chunks of 8 bf16 in the canonical no-swizzle layout.  Two threads
+// per pixel: half 0 writes chunks 0-3 (taps 0-4 and the first word of tap 5),
+// half 1 chunks 4-7.
+__device__ __forceinline__ void build_first_a(uint8_t *s_a, const float (*s_c)[TILE_M + 2],
+                                              const float (*s_z)[TILE_M + 2], int r, int px, int half)
+{
+    uint32_t w[32];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        if (half == 0 ? tap > 5 : tap < 5) continue;
+        float ch, cl, zh, zl;
+        split_bf16(s_c[r + tap / 3][px + tap % 3], ch, cl);
+        split_bf16(s_z[r + tap / 3][px + tap % 3], zh, zl);
+        w[3 * tap + 0] = pack_bf16x2(ch, ch);
+        w[3 * tap + 1] = pack_bf16x2(cl, zh);
+        w[3 * tap + 2] = pack_bf16x2(zh, zl);
+    }
+#pragma unroll
+    for (int k = 27; k < 32; ++k) w[k] = 0u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if ((c >> 2) != half) continue;
+        *reinterpret_cast<uint4 *>(s_a + ((size_t)c * 128 + px) * 16) =
+            make_uint4(w[4 * c + 0], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_first_mma(const float *__restrict__ contone, int cpitch, int H, int W,
+                                                   uint64_t seed, uint32_t image, const uint8_t *__restrict__ w1pack,
+                                                   const float *__restrict__ b1, void *out, int out_fp8,
+                                                   float out_inv_scale, int *err)
+{
+    extern __shared__ uint8_t f1_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)f1_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *s_a = base;                                        // 2 x [8 chunks][128 px][16 B]
+    uint8_t *s_b = s_a + 2 * 8 * 128 * 16;                      // [8 chunks][64 n][16 B]
+    float (*s_c)[TILE_M + 2] = (float (*)[TILE_M + 2])(s_b + 8 * 64 * 16);
+    float (*s_z)[TILE_M + 2] = s_c + (F1_ROWS + 2);
+    float *s_bias = (float *)(s_z + (F1_ROWS + 2));
+    uint64_t *s_bar = (uint64_t *)(s_bias + 64);                // 2
+    uint32_t *s_tmem = (uint32_t *)(s_bar + 2);
+    volatile int *s_abort = (volatile int *)(s_tmem + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int x0 = blockIdx.x * TILE_M, y0 = blockIdx.y * F1_ROWS;
+    const int nrows = min(F1_ROWS, H - y0);
+
+    for (int i = tid; i < (F1_ROWS + 2) * (TILE_M + 2); i += 256) {
+        const int yy = i / (TILE_M + 2), xx = i % (TILE_M + 2);
         const int gy = y0 + yy - 1, gx = x0 + xx - 1;
-        float c = 0.f, z = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            c = contone[(size_t)gy * cpitch + gx];
-            z = ht_uniform24(seed, image, 0u, (uint64_t)gy * W + gx);
-        }
+        float c = 0.f;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) c = contone[(size_t)gy * cpitch + gx];
         s_c[yy][xx] = c;
-        s_z[yy][xx] = z;
+        s_z[yy][xx] = 0.f;
     }
-    for (int i = threadIdx.x; i < 18 * 64; i += FT_X) {
-        const int k = i / 64, o = i % 64;           // k = tap*2 + ci
-        const int tap = k >> 1, ci = k & 1;
-        reinterpret_cast<float *>(&s_w[k][0])[o] = w1[((size_t)o * 2 + ci) * 9 + tap];
-    }
-    if (threadIdx.x < 64) reinterpret_cast<float *>(s_b)[threadIdx.x] = b1[threadIdx.x];
     __syncthreads();
-    const int x = x0 + threadIdx.x;
-    if (x >= W) return;
-    for (int r = 0; r < FT_Y; ++r) {
-        const int y = y0 + r;
-        if (y >= H) break;
-        float in[18];
+    // noise channel: one Philox4x32-10 call per aligned group of 4 pixel indices g
+    {
+        constexpr int GPR = (TILE_M + 2 + 3) / 4 + 1;          // groups touching one staged row
+        const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+        for (int i = tid; i < (F1_ROWS + 2) * GPR; i += 256) {
+            const int yy = i / GPR, k = i % GPR;
+            const int gy = y0 + yy - 1;
+            if (gy < 0 || gy >= H) continue;
+            const int gxa = max(x0 - 1, 0), gxb = min(x0 - 1 + TILE_M + 2, W);   // in-image staged columns
+            const uint64_t g0 = (uint64_t)gy * W + gxa, g1 = (uint64_t)gy * W + gxb;
+            const uint64_t gq = (g0 >> 2) + (uint64_t)k;                         // counter of this group
+            if ((gq << 2) >= g1) continue;
+            const uint4 r = ht_philox4x32_10(make_uint4((uint32_t)gq, image, 0u, 0u), key);
+            const uint32_t lanes[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            in[2 * tap] = s_c[r + tap / 3][threadIdx.x + tap % 3];
-            in[2 * tap + 1] = s_z[r + tap / 3][threadIdx.x + tap % 3];
-        }
-        float v[64];
-#pragma unroll
-        for (int o4 = 0; o4 < 16; ++o4) {
-            float4 a = s_b[o4];
-#pragma unroll
-            for (int k = 0; k < 18; ++k) {
-                const float4 wv = s_w[k][o4];
-                a.x = fmaf(in[k], wv.x, a.x);
-                a.y = fmaf(in[k], wv.y, a.y);
-                a.z = fmaf(in[k], wv.z, a.z);
-                a.w = fmaf(in[k], wv.w, a.w);
+            for (int l = 0; l < 4; ++l) {
+                const uint64_t g = (gq << 2) + l;
+                if (g < g0 || g >= g1) continue;
+                const int gx = (int)(g - (uint64_t)gy * W);
+                s_z[yy][gx - (x0 - 1)] = (float)(lanes[l] >> 8) * (1.0f / 16777216.0f);
             }
-            v[4 * o4 + 0] = fmaxf(a.x, 0.f);
-            v[4 * o4 + 1] = fmaxf(a.y, 0.f);
-            v[4 * o4 + 2] = fmaxf(a.z, 0.f);
-            v[4 * o4 + 3] = fmaxf(a.w, 0.f);
         }
-        store_pixel(v, out, out_fp8, out_inv_scale, H, W, y, x);
+    }
+    for (int i = tid; i < 8 * 64; i += 256)
+        reinterpret_cast<uint4 *>(s_b)[i] = reinterpret_cast<const uint4 *>(w1pack)[i];
+    if (tid < 64) s_bias[tid] = b1[tid];
+    if (tid == 0) {
+        mbar_init(smem_u32(&s_bar[0]), 1);
+        mbar_init(smem_u32(&s_bar[1]), 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(s_tmem), 128);
+    __syncthreads();
+    build_first_a(s_a, s_c, s_z, 0, tid & 127, tid >> 7);       // row 0 into buffer 0
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    const uint64_t a_desc = sdesc(smem_u32(s_a), 128 * 16, 128);
+    const uint64_t b_desc = sdesc(smem_u32(s_b), 64 * 16, 128);
+    constexpr uint32_t idesc = idesc_m128<false>(64);
+    auto issue = [&](int r) {      // 4 MMAs of row r (A buffer r&1) into accumulator r&1
+        const uint32_t buf = (uint32_t)r & 1u;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+            mma_ss<false>(tmem + buf * 64u,
+                          a_desc + (uint64_t)(((buf * 8 * 128 * 16) + 2 * ks * 128 * 16) >> 4),
+                          b_desc + (uint64_t)((2 * ks * 64 * 16) >> 4), idesc, ks > 0);
+        mma_commit(smem_u32(&s_bar[buf]));
+    };
+    if (tid == 0) issue(0);
+
+    bool ok = true;
+    int issued = 1;
+    for (int r = 0; r < nrows && ok; ++r) {
+        if (r + 1 < nrows) {
+            // row r+1 into the other buffer; its previous reader (row r-1) completed
+            build_first_a(s_a + ((r + 1) & 1) * (8 * 128 * 16), s_c, s_z, r + 1, tid & 127, tid >> 7);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) issue(r + 1);
+            ++issued;
+        }
+        ok = mbar_wait(smem_u32(&s_bar[r & 1]), ((uint32_t)r >> 1) & 1u, s_abort, err);
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) break;
+        tc_fence_after();
+        // warps q and q+4 share TMEM lane quarter q; each takes 32 of the 64 channels
+        const int quarter = warp & 3, chalf = warp >> 2;
+        float v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r & 1) * 64u + chalf * 32u;
+        tmem_ld16(taddr + 0, v + 0);
+        tmem_ld16(taddr + 16, v + 16);
+        tmem_wait_ld();
+        tc_fence_before();
+        const int x = x0 + quarter * 32 + lane;
+        if (x < W) {
+#pragma unroll
+            for (int n = 0; n < 32; ++n) v[n] = fmaxf(v[n] + s_bias[chalf * 32 + n], 0.f);
+            store_channels32(v, chalf, out, out_fp8, out_inv_scale, H, W, y0 + r, x);
+        }
+        __syncthreads();       // accumulator r&1 drained before row r+2 reuses it
+    }
+    if (!ok && tid == 0) {
+        // drain the commits still in flight before TMEM is released
+        for (int k = 0; k < issued; ++k) mbar_wait(smem_u32(&s_bar[k & 1]), ((uint32_t)k >> 1) & 1u, s_abort, err, true);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 128);
     }
 }
 
@@ -630,6 +774,27 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_tc(const uint8_t *__restric
 }
 
 // ---------------------------------------------------------------------------
+// 1-logit head from the per-tap partials written by the last conv layer:
+// z(y,x) = b + sum_{dy,dx} d_{dy,dx}(y+dy-1, x+dx-1) (zero outside the image).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const float *__restrict__ part, int H, int W, float bias,
+                                                              int mode, uint64_t seed, uint32_t image, uint32_t *bits,
+                                                              int words, float *prob)
+{
+    const int x0 = blockIdx.x * HT_X, y = blockIdx.y * HT_Y + threadIdx.y, x = x0 + threadIdx.x;
+    const size_t plane = (size_t)H * W;
+    float z = bias;
+    if (y < H && x < W) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) z += __ldg(part + t * plane + (size_t)yy * W + xx);
+        }
+    }
+    ht_head_emit(&z, 1, HT_HEAD_SIGMOID, mode, seed, image, x0, y, H, W, bits, words, prob);
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 int num_sms()
@@ -644,17 +809,18 @@ int num_sms()
     return n;
 }
 
-template <bool FP8>
+template <bool FP8, bool HEAD>
 ht_status launch_conv(const ConvParams &P, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FP8>::SMEM));
+        HT_CUDA_TRY(
+            cudaFuncSetAttribute(k_conv_tc<FP8, HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FP8>::SMEM));
         attr_set = true;
     }
     const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
     ht_prof_start(FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
-    k_conv_tc<FP8><<<grid, NTHREADS, Cfg<FP8>::SMEM, s>>>(P);
+    k_conv_tc<FP8, HEAD><<<grid, NTHREADS, Cfg<FP8>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -750,6 +916,56 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
                 }
         }
     }
+    {
+        // layer 1: [kchunk 8][n 64][8 bf16], k = 6 tap + j with (w_hi(c), w_lo(c), w_hi(c), w_hi(z), w_lo(z), w_hi(z))
+        float w0[64 * 2 * 9];
+        e = cudaMemcpyAsync(w0, p->d_w + p->w_off[0], sizeof(w0), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        uint16_t pk[8 * 64 * 8];
+        memset(pk, 0, sizeof(pk));
+        for (int n = 0; n < 64; ++n)
+            for (int tap = 0; tap < 9; ++tap)
+                for (int ci = 0; ci < 2; ++ci) {
+                    const float w = w0[(n * 2 + ci) * 9 + tap];
+                    const uint16_t hi = f32_to_bf16_rne(w);
+                    uint32_t hb32 = (uint32_t)hi << 16;
+                    float hf;
+                    memcpy(&hf, &hb32, 4);
+                    const uint16_t lo = f32_to_bf16_rne(w - hf);
+                    const uint16_t trip[3] = {hi, lo, hi};
+                    for (int j = 0; j < 3; ++j) {
+                        const int k = 6 * tap + 3 * ci + j;
+                        pk[((k / 8) * 64 + n) * 8 + (k % 8)] = trip[j];
+                    }
+                }
+        if (e == cudaSuccess && !p->d_w1pack) e = cudaMalloc(&p->d_w1pack, sizeof(pk));
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_w1pack, pk, sizeof(pk), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free(hw);
+            free(hp);
+            free(hs);
+            HT_CUDA_TRY(e);
+        }
+    }
+    // biases and (1-logit head) last-layer weights, host side, for the kernel parameters
+    e = cudaMemcpyAsync(p->h_b, p->d_b, sizeof(float) * p->n_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && p->K == 1)
+        e = cudaMemcpyAsync(p->h_headw, p->d_w + p->w_off[p->L - 1], sizeof(float) * 64 * 9, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free(hw);
+        free(hp);
+        free(hs);
+        HT_CUDA_TRY(e);
+    }
+    if (p->K == 1) {
+        float tmp[9 * 64];
+        memcpy(tmp, p->h_headw, sizeof(tmp));                 // [c][tap] -> [tap][c]
+        for (int c = 0; c < 64; ++c)
+            for (int t = 0; t < 9; ++t) p->h_headw[t * 64 + c] = tmp[c * 9 + t];
+        p->head_bias = p->h_b[p->b_off[p->L - 1]];
+    }
+    if (fp8) memcpy(p->h_wscale, hs, sizeof(float) * 64 * n_inner);
     e = cudaMemcpyAsync(p->d_wpack, hp, layer_bytes * n_inner, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && fp8) e = cudaMemcpyAsync(p->d_wscale, hs, sizeof(float) * 64 * n_inner, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -781,12 +997,18 @@ ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int
 
     // layer 1: output feeds inner layer 1 (e4m3 in the FP8 form)
     {
-        const dim3 grid((W + FT_X - 1) / FT_X, (H + FT_Y - 1) / FT_Y);
+        const dim3 grid((W + TILE_M - 1) / TILE_M, (H + F1_ROWS - 1) / F1_ROWS);
         const bool o8 = fp8 && n_inner > 0;
+        static bool attr1 = false;
+        if (!attr1) {
+            HT_CUDA_TRY(cudaFuncSetAttribute(k_first_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, F1_SMEM));
+            HT_CUDA_TRY(cudaFuncSetAttribute(k_first_mma, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            attr1 = true;
+        }
         ht_prof_start(HTK_FIRST_TC, s);
-        k_first_tc<<<grid, FT_X, 0, s>>>(img.contone, img.pitch, H, W, seed, image_index, p->d_w + p->w_off[0],
-                                         p->d_b + p->b_off[0], buf[0], o8 ? 1 : 0,
-                                         o8 ? 1.f / p->act_scale[1] : 1.f);
+        k_first_mma<<<grid, 256, F1_SMEM, s>>>(img.contone, img.pitch, H, W, seed, image_index,
+                                         (const uint8_t *)p->d_w1pack, p->d_b + p->b_off[0], buf[0], o8 ? 1 : 0,
+                                         o8 ? 1.f / p->act_scale[1] : 1.f, err);
         ht_prof_stop(s);
         HT_LAUNCH_CHECK();
     }
@@ -798,19 +1020,24 @@ ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int
         ConvParams P;
         P.in = buf[cur];
         P.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (l - 1);
-        P.bias = p->d_b + p->b_off[l];
-        P.wscale = fp8 ? p->d_wscale + 64 * (l - 1) : nullptr;
-        P.in_scale = fp8 ? p->act_scale[l] : 1.f;
+        for (int n = 0; n < 64; ++n) {
+            P.bias[n] = p->h_b[p->b_off[l] + n];
+            P.scale[n] = fp8 ? p->act_scale[l] * p->h_wscale[64 * (l - 1) + n] : 1.f;
+        }
         P.out_inv_scale = out8 ? 1.f / p->act_scale[l + 1] : 1.f;
         P.out_fp8 = out8 ? 1 : 0;
         P.out = buf[cur ^ 1];
+        const bool fuse_head = (l == n_inner) && p->K == 1;
+        if (fuse_head) memcpy(P.head_w, p->h_headw, sizeof(P.head_w));
+        P.partials = fuse_head ? (float *)buf[cur ^ 1] : nullptr;
         P.H = H;
         P.W = W;
         P.n_xtiles = n_xtiles;
         P.rows_per_unit = rpu;
         P.n_units = n_xtiles * ((H + rpu - 1) / rpu);
         P.err = err;
-        const ht_status st = fp8 ? launch_conv<true>(P, s) : launch_conv<false>(P, s);
+        const ht_status st = fp8 ? (fuse_head ? launch_conv<true, true>(P, s) : launch_conv<true, false>(P, s))
+                                 : (fuse_head ? launch_conv<false, true>(P, s) : launch_conv<false, false>(P, s));
         if (st != HT_OK) return st;
         cur ^= 1;
     }
@@ -819,7 +1046,6 @@ ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int
         static bool attr = false;
         const size_t smem = sizeof(uint4) * 8 * (HT_Y + 2) * (HT_X + 2) + sizeof(float) * 9 * 64 * 4;
         if (!attr) {
-            HT_CUDA_TRY(cudaFuncSetAttribute(k_head_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             HT_CUDA_TRY(cudaFuncSetAttribute(k_head_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr = true;
         }
@@ -828,8 +1054,8 @@ ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int
         const float *wl = p->d_w + p->w_off[p->L - 1], *bl = p->d_b + p->b_off[p->L - 1];
         ht_prof_start(HTK_HEAD_TC, s);
         if (p->K == 1)
-            k_head_tc<1><<<grid, dim3(HT_X, HT_Y), smem, s>>>(buf[cur], H, W, wl, bl, p->head, mode, seed,
-                                                              image_index, bits, words, prob);
+            k_head_partials<<<grid, dim3(HT_X, HT_Y), 0, s>>>((const float *)buf[cur], H, W, p->head_bias, mode,
+                                                               seed, image_index, bits, words, prob);
         else
             k_head_tc<4><<<grid, dim3(HT_X, HT_Y), smem, s>>>(buf[cur], H, W, wl, bl, p->head, mode, seed,
                                                               image_index, bits, words, prob);

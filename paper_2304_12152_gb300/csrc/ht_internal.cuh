@@ -95,6 +95,13 @@ struct ht_policy {
     size_t wpack_layer_bytes = 0;
     float *d_wscale = nullptr;      // FP8: per (layer, out channel) dequant scale
     float act_scale[HT_MAX_LAYERS];
+    // host copies of the small per-channel constants the tensor-core kernels take as
+    // kernel parameters (refreshed by every repack)
+    float h_b[HT_MAX_LAYERS * HT_MAX_CHANNELS + 4];
+    float h_wscale[HT_MAX_LAYERS * 64];
+    float h_headw[9 * 64];          // 1-logit head: last-layer weights as [9 taps][64]
+    void *d_w1pack = nullptr;       // layer 1 for the tensor cores: bf16 hi/lo split, [kchunk][n][8]
+    float head_bias = 0.f;
     // per-call workspace (grown on demand; library owned)
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
