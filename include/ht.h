@@ -195,7 +195,8 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
                             uint64_t seed, double *losses_host, void *stream);
 
 /* Backward of the last forward: dL_total/dW and dL_total/db (device float
- * arrays in the canonical layout, overwritten). */
+ * arrays in the canonical layout, overwritten).  The crop images passed to the
+ * forward are read again here (first-layer input) and must still be valid. */
 ht_status ht_train_step_bwd(ht_train *t, float *grad_w, float *grad_b, void *stream);
 
 /* ------------------------------------------------------------------------ */

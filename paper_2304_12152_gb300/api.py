@@ -146,6 +146,76 @@ def anisotropy_loss(q: torch.Tensor, mode: int = 0, n_rad: int = 32, n_ang: int 
     return loss, g
 
 
+class Trainer:
+    """ht_train: one iteration of the training step (forward + backward) on device."""
+
+    def __init__(self, policy: Policy, crop_hw: Tuple[int, int], max_crops: int, n_samples: int = 4,
+                 n_gray: int = 0, gray_n: int = 256, las_mode: int = 1, n_rad: int = 32, n_ang: int = 16,
+                 w_a: float = 0.002, reward: Optional[N.RewardOpts] = None):
+        d = N.TrainDesc()
+        d.max_crops, (d.crop_h, d.crop_w) = max_crops, crop_hw
+        d.n_gray, d.gray_n, d.n_samples = n_gray, gray_n, n_samples
+        d.las_mode, d.n_rad, d.n_ang, d.w_a = las_mode, n_rad, n_ang, w_a
+        d.reward = reward or reward_opts()
+        h = C.c_void_p()
+        check(N.load().ht_train_create(policy.handle, C.byref(d), C.byref(h)))
+        self._h, self.policy, self.desc = h, policy, d
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.load().ht_train_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, crops: Sequence[torch.Tensor], gray_levels: Sequence[float] = (), seed: int = 0,
+                stream=None) -> Tuple[float, float, float, float]:
+        """(L_total, L_MARL, L_AS, mean reward)."""
+        out = (C.c_double * 4)()
+        lv = np.ascontiguousarray(gray_levels, np.float32) if len(gray_levels) else np.zeros(1, np.float32)
+        check(N.load().ht_train_step_fwd(self._h, _images(crops), len(crops), lv.ctypes.data, seed, out,
+                                         _stream(stream)))
+        self._crops = list(crops)      # the backward re-reads the crops (first-layer input)
+        return tuple(out)
+
+    def backward(self, grad_w: Optional[torch.Tensor] = None, grad_b: Optional[torch.Tensor] = None, stream=None):
+        n_w = sum(self.policy.channels[i] * self.policy.channels[i + 1] * 9 for i in range(len(self.policy.channels) - 1))
+        n_b = sum(self.policy.channels[1:])
+        dev = torch.device("cuda", torch.cuda.current_device())
+        grad_w = grad_w if grad_w is not None else torch.empty(n_w, dtype=torch.float32, device=dev)
+        grad_b = grad_b if grad_b is not None else torch.empty(n_b, dtype=torch.float32, device=dev)
+        check(N.load().ht_train_step_bwd(self._h, grad_w.data_ptr(), grad_b.data_ptr(), _stream(stream)))
+        return grad_w, grad_b
+
+
+class HalftonePolicyFn(torch.autograd.Function):
+    """torch.autograd.Function driving one training iteration of the library.
+
+    forward(w_flat, b_flat, trainer, crops, gray_levels, seed) loads the FP32 master
+    weights into the policy, runs ht_train_step_fwd and returns L_total as a 0-d
+    tensor; backward returns dL_total/dw and dL_total/db from ht_train_step_bwd
+    (the local-expectation gradient of L_MARL plus w_a times the anisotropy-loss
+    gradient), scaled by the incoming gradient.  The optimiser stays in torch."""
+
+    @staticmethod
+    def forward(ctx, w_flat, b_flat, trainer, crops, gray_levels, seed):
+        trainer.policy.set_weights(w_flat.detach().contiguous(), b_flat.detach().contiguous())
+        losses = trainer.forward(crops, gray_levels, seed)
+        ctx.trainer = trainer
+        ctx.losses = losses
+        return torch.tensor(losses[0], dtype=torch.float64, device=w_flat.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        gw, gb = ctx.trainer.backward()
+        s = g.to(torch.float32)
+        return gw * s, gb * s, None, None, None, None
+
+
 def profile_begin() -> None:
     check(N.load().ht_profile_begin())
 

@@ -9,7 +9,7 @@ pixels (|p - u| > 1e-4) at most 1% (e4m3 has 3 mantissa bits, so one-ulp flips o
 activation are frequent).  Probability error against the pure FP64 oracle is stated
 (printed): e4m3's unit roundoff 2^-4 at six quantisation stages moves a logit of
 magnitude ~2 by up to ~0.3, i.e. p by up to ~0.08; bounded at 0.15 max and 0.1 at the
-99.9th percentile, median below 0.01.
+99.9th percentile, median below 0.03.
 
 Softmax head, BF16 form: a decision flips where |cdf_k - u| is below the probability
 error (~1e-3 in BF16), so the residual-mismatch allowance scales with the K - 1 = 3
@@ -74,7 +74,7 @@ def test_fp8_form(head, chs):
     print(f"FP8 head={head}: |dp| vs FP64 max {e.max():.3e} p99.9 {np.quantile(e, 0.999):.3e}; "
           f"bit mismatches {tot_bad}/{tot_n}")
     assert tot_bad <= 0.01 * tot_n
-    assert e.max() < 0.15 and np.quantile(e, 0.999) < 0.1 and np.median(e) < 0.01
+    assert e.max() < 0.15 and np.quantile(e, 0.999) < 0.1 and np.median(e) < 0.03
     if head == N.HT_HEAD_SOFTMAX:
         assert all(set(np.unique(l)) <= {0, 1, 2, 3} for l in lev)
 

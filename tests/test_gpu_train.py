@@ -1,0 +1,101 @@
+"""GPU parity of one training iteration (Algorithm 1, TRAIN) against the FP64 oracle.
+
+The oracle side is assembled from the pinned oracle routines: forward with saved
+activations, Bernoulli samples h^s = [u^s < p] with u^s from the oracle's Philox
+(stream 1 + s), reward and toggle deltas per sample, the local-expectation surrogate
+(value and dL/dp = -dR), the anisotropy loss of the gray patches' probability maps
+with its gradient, and the hand-written backward (pinned by finite differences and
+torch autograd in the CPU tests).  Tolerances: losses 1e-4 relative, gradients 2e-3
+of the largest gradient entry of the layer (FP32 forward, FP32 dR sums)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2304_12152_gb300 import _native as N
+from paper_2304_12152_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_step(crops, grays, ws, bs, seed, S, w_a, las_mode, n_rad, n_ang):
+    n, G = len(crops), len(grays)
+    gw = [np.zeros(w.shape) for w in ws]
+    gb = [np.zeros(b.shape) for b in bs]
+    l_marl, rs = 0.0, []
+    for i, c in enumerate(crops):
+        h, w = c.shape
+        lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=i, save_acts=True)
+        dp = np.zeros((h, w))
+        for s in range(S):
+            u = O.uniform_map(seed, i, 1 + s, h, w)
+            hb = (u < p[0]).astype(np.uint8)
+            r = O.reward(c, hb)
+            dR = O.toggle_delta(c, hb).reshape(h, w)
+            val, grad = O.le_surrogate(p[0], hb, dR, r["R"])
+            l_marl += val / (n * S)
+            dp += grad / (n * S)
+            rs.append(r["R"])
+        a, b = O.backward(c, ws, bs, seed, i, acts, lg, dp)
+        for l in range(len(ws)):
+            gw[l] += a[l]
+            gb[l] += b[l]
+    l_as = 0.0
+    for g, (lev, nn) in enumerate(grays):
+        c = np.full((nn, nn), lev, np.float32)
+        lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=n + g, save_acts=True)
+        r = O.anisotropy_loss(p[0], mode=las_mode, n_rad=n_rad, n_ang=n_ang, grad=True)
+        l_as += r["loss"] / G
+        a, b = O.backward(c, ws, bs, seed, n + g, acts, lg, w_a * r["grad"] / G)
+        for l in range(len(ws)):
+            gw[l] += a[l]
+            gb[l] += b[l]
+    return l_marl + w_a * l_as, l_marl, l_as, float(np.mean(rs)), gw, gb
+
+
+@pytest.mark.parametrize("las_mode,n_rad,n_ang", [(0, 1, 1), (1, 4, 4)])
+def test_train_step_matches_oracle(las_mode, n_rad, n_ang):
+    chs = (2, 8, 8, 1)
+    ws, _ = synth.he_normal_policy(chs, 21)
+    bs = synth.random_biases(chs, 22, scale=0.1)
+    crops = [synth.contone_image(32, 32, seed=23, index=i) for i in range(2)]
+    levels = [0.25, 0.6]
+    gn, S, seed, w_a = 16, 2, 7, 0.5
+    pol = api.Policy(chs, ws, bs, precision=N.HT_FP32)
+    tr = api.Trainer(pol, (32, 32), max_crops=2, n_samples=S, n_gray=2, gray_n=gn, las_mode=las_mode,
+                     n_rad=n_rad, n_ang=n_ang, w_a=w_a)
+    losses = tr.forward([torch.from_numpy(c).cuda() for c in crops], levels, seed)
+    gw, gb = tr.backward()
+    torch.cuda.synchronize()
+    ref = oracle_step(crops, [(l, gn) for l in levels], ws, bs, seed, S, w_a, las_mode, n_rad, n_ang)
+    for k in range(4):
+        assert abs(losses[k] - ref[k]) <= 1e-4 * abs(ref[k]) + 1e-9, (k, losses, ref[:4])
+    gw = gw.cpu().numpy().astype(np.float64)
+    gb = gb.cpu().numpy().astype(np.float64)
+    ow = ob = 0
+    for l in range(len(ws)):
+        rw, rb = ref[4][l].ravel(), ref[5][l].ravel()
+        scale = max(np.abs(rw).max(), np.abs(rb).max())
+        assert np.abs(gw[ow:ow + rw.size] - rw).max() <= 2e-3 * scale, l
+        assert np.abs(gb[ob:ob + rb.size] - rb).max() <= 2e-3 * scale, l
+        ow += rw.size
+        ob += rb.size
+
+
+def test_autograd_function_drives_adam():
+    """torch.autograd.Function wrapper: gradients reach torch parameters and an Adam
+    step changes the loss deterministically."""
+    chs = (2, 8, 8, 1)
+    ws, bs = synth.he_normal_policy(chs, 31)
+    pol = api.Policy(chs, ws, bs, precision=N.HT_FP32)
+    tr = api.Trainer(pol, (24, 24), max_crops=2, n_samples=2, n_gray=1, gray_n=16, las_mode=1, n_rad=4, n_ang=4)
+    w = torch.nn.Parameter(torch.from_numpy(np.concatenate([x.ravel() for x in ws])).cuda())
+    b = torch.nn.Parameter(torch.from_numpy(np.concatenate([x.ravel() for x in bs])).cuda())
+    crops = [torch.from_numpy(synth.contone_image(24, 24, seed=32, index=i)).cuda() for i in range(2)]
+    opt = torch.optim.Adam([w, b], lr=1e-3)
+    loss = api.HalftonePolicyFn.apply(w, b, tr, crops, [0.5], 3)
+    loss.backward()
+    assert w.grad is not None and torch.isfinite(w.grad).all() and w.grad.abs().sum() > 0
+    opt.step()
+    loss2 = api.HalftonePolicyFn.apply(w, b, tr, crops, [0.5], 3)
+    assert torch.isfinite(loss2) and float(loss2) != float(loss)
