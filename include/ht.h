@@ -148,6 +148,25 @@ void ht_reward_opts_default(ht_reward_opts *opts);
 ht_status ht_reward(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts *opts,
                     double *out, void *stream);
 
+/* Allocation-free variant of ht_reward (the paper has no counterpart; it is a
+ * service for callers that must not allocate device memory while they run, for
+ * example a host application whose own allocator has reserved all the device
+ * memory it may use, or a streaming loop that cannot accept the device-wide
+ * synchronisation cudaMalloc / cudaFree may imply).  Same arguments, results
+ * and tolerances as ht_reward, but it calls no cudaMalloc, cudaFree or other
+ * allocating routine: its FP64 per-image accumulators live in a file-scope
+ * device array of 3 * HT_REWARD_NOALLOC_MAX_IMAGES doubles (24 KiB), held by
+ * every GPU that loads the library until the process exits.
+ *   - n must be <= HT_REWARD_NOALLOC_MAX_IMAGES, else HT_ERR_INVALID_ARG.
+ *   - The first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *     first call before any stream capture.
+ *   - Every call clears and reuses the same array: calls whose work overlaps on
+ *     the GPU (e.g. on unordered streams) race and give wrong results. */
+#define HT_REWARD_NOALLOC_MAX_IMAGES 1024
+ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const *bits, int n,
+                            const ht_reward_opts *opts, double *out, void *stream);
+
 /* Toggle deltas of the local-expectation gradient (Eq. le, Sec. III-C):
  * dR[a] = R(h with h_a = 1) - R(h with h_a = 0) for every pixel a.
  * dR: host array of n device pointers, each float [h][w]. */

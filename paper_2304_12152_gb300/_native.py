@@ -21,7 +21,7 @@ HT_MODE_THRESHOLD, HT_MODE_BERNOULLI = 0, 1
 EXPORTS = (
     "ht_create_policy", "ht_destroy_policy", "ht_policy_set_weights", "ht_policy_set_act_scales",
     "ht_policy_num_params", "ht_policy_flops_per_px", "ht_bits_row_words", "ht_halftone",
-    "ht_reward_opts_default", "ht_reward", "ht_toggle_delta", "ht_anisotropy_loss",
+    "ht_reward_opts_default", "ht_reward", "ht_reward_noalloc", "ht_toggle_delta", "ht_anisotropy_loss",
     "ht_train_create", "ht_train_destroy", "ht_train_step_fwd", "ht_train_step_bwd",
     "ht_profile_begin", "ht_profile_end", "ht_sync", "ht_last_error", "ht_version",
 )
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
         L.ht_reward_opts_default.argtypes = [P(RewardOpts)]
         L.ht_reward_opts_default.restype = None
         L.ht_reward.argtypes = [P(Image), vp, i, P(RewardOpts), vp, vp]
+        L.ht_reward_noalloc.argtypes = [P(Image), vp, i, P(RewardOpts), vp, vp]
         L.ht_toggle_delta.argtypes = [P(Image), vp, i, P(RewardOpts), vp, vp]
         L.ht_anisotropy_loss.argtypes = [vp, i, i, i, i, i, vp, vp, vp]
         L.ht_train_create.argtypes = [vp, P(TrainDesc), P(vp)]

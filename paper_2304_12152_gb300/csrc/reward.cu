@@ -23,6 +23,8 @@
 //   cov'    = cov + delta w (c_a - mu_c)
 // so dR_a = R(h_a = 1) - R(h_a = 0) = (1/M) sum_j [ -(2 g e_j + delta g^2)
 //            + delta w_s sigma_j (SSIM_j' - SSIM_j) ]  (exact, no approximation).
+#include <mutex>
+
 #include "ht_internal.cuh"
 
 namespace {
@@ -330,3 +332,103 @@ ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, int n
 }
 
 size_t ht_toggle_scratch_floats(int h, int w, int r) { return (size_t)NMAP * (h - 2 * r) * (w - 2 * r); }
+
+// ---------------------------------------------------------------------------
+// Allocation-free reward.
+//
+// Some callers of this library must not allocate device memory while they run:
+// a host application whose allocator has reserved the device memory it is
+// allowed to use (a further cudaMalloc would fail or push it over its budget),
+// or a streaming loop that cannot accept the device-wide synchronisation that
+// cudaMalloc / cudaFree may imply.  ht_reward needs a few doubles of scratch per
+// image (FP64 accumulators); ht_reward_noalloc keeps them in the file-scope
+// device array below instead, which every GPU that loads the library holds
+// until the process exits.
+//
+// Host code only sees the array's host-side stand-in; its device address is
+// looked up once per device with cudaGetSymbolAddress (with that device
+// current) on the first call, and cached.  All calls share the array: the
+// accumulators are cleared at the start of every call, and calls whose work
+// overlaps on the GPU (different streams, no ordering) race on it.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_reward_noalloc_acc[3 * HT_REWARD_NOALLOC_MAX_IMAGES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[64] = {nullptr};
+
+struct InvM64 {
+    double v[64];
+};
+
+// out[4 i + ...] for images base .. base + count - 1 (count <= 64)
+__global__ void k_reward_finalize_noalloc(const double *__restrict__ acc, int count, InvM64 inv_m, float ws,
+                                          double *__restrict__ out)
+{
+    const int i = threadIdx.x;
+    if (i >= count) return;
+    const double m = inv_m.v[i];
+    const double mse = acc[3 * i] * m, ssim = acc[3 * i + 1] * m, cssim = acc[3 * i + 2] * m;
+    out[4 * i + 0] = mse;
+    out[4 * i + 1] = ssim;
+    out[4 * i + 2] = cssim;
+    out[4 * i + 3] = -mse + (double)ws * cssim;
+}
+
+}  // namespace
+
+extern "C" ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const *bits, int n,
+                                       const ht_reward_opts *opts, double *out, void *stream)
+{
+    HT_CHECK_ARG(opts != nullptr, "null reward options");
+    HT_CHECK_ARG(opts->radius >= 1 && opts->radius <= 7, "radius must be in [1, 7]");
+    HT_CHECK_ARG(opts->sigma_hvs > 0 && opts->sigma_ssim > 0, "window sigmas must be positive");
+    HT_CHECK_ARG(c != nullptr && n >= 1, "need at least one image");
+    HT_CHECK_ARG(n <= HT_REWARD_NOALLOC_MAX_IMAGES, "ht_reward_noalloc takes at most %d images per call (got %d)",
+                 HT_REWARD_NOALLOC_MAX_IMAGES, n);
+    HT_CHECK_ARG(bits && out, "null argument");
+    const int r = opts->radius;
+    for (int i = 0; i < n; ++i) {
+        HT_CHECK_ARG(c[i].contone && bits[i], "image %d: null pointer", i);
+        HT_CHECK_ARG(c[i].h >= 2 * r + 1 && c[i].w >= 2 * r + 1 && c[i].h <= 16384 && c[i].w <= 16384,
+                     "image %d: size %dx%d outside [%d, 16384]", i, c[i].h, c[i].w, 2 * r + 1);
+        HT_CHECK_ARG(c[i].pitch >= c[i].w, "image %d: pitch < width", i);
+    }
+    int dev = 0;
+    HT_CUDA_TRY(cudaGetDevice(&dev));
+    HT_CHECK_ARG(dev >= 0 && dev < 64, "device index %d out of range", dev);
+    double *acc = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *addr = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&addr, g_reward_noalloc_acc);
+            if (e != cudaSuccess || addr == nullptr) {
+                ht_set_error("cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+                return HT_ERR_CUDA;
+            }
+            g_noalloc_addr[dev] = (double *)addr;
+        }
+        acc = g_noalloc_addr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Win wn = make_win(*opts);
+    HT_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)n, s));
+    for (int i = 0; i < n; ++i) {
+        const int VH = c[i].h - 2 * r, VW = c[i].w - 2 * r;
+        const dim3 grid((VW + RT - 1) / RT, (VH + RT - 1) / RT);
+        k_reward_tiles<<<grid, dim3(32, 8), 0, s>>>(c[i].contone, c[i].pitch, bits[i], ht_bits_row_words(c[i].w, 0),
+                                                    c[i].h, c[i].w, wn, acc + 3 * i);
+        HT_LAUNCH_CHECK();
+    }
+    for (int base = 0; base < n; base += 64) {
+        const int count = n - base < 64 ? n - base : 64;
+        InvM64 im;
+        for (int k = 0; k < count; ++k)
+            im.v[k] = 1.0 / ((double)(c[base + k].h - 2 * r) * (double)(c[base + k].w - 2 * r));
+        k_reward_finalize_noalloc<<<1, 64, 0, s>>>(acc + 3 * base, count, im, opts->w_s, out + 4 * (size_t)base);
+        HT_LAUNCH_CHECK();
+    }
+    return HT_OK;
+}
