@@ -108,22 +108,17 @@ def dist_info():
     return rank, world, local
 
 
-def workload_images(args, rank):
-    from paper_2304_12152_gb300 import synth
-    shapes = [(args.size, args.size)] * args.batch
-    # every rank its own images (replicas): the generator index carries the rank
-    return [synth.contone_image(h, w, seed=1, index=rank * 1000 + i) for i, (h, w) in enumerate(shapes)]
-
-
-def cpu_oracle_sample(img, ws, bs, side, seed, image_id=0):
-    """FP64 oracle (BF16-emulating) forward + Bernoulli actions on a side x side crop."""
+def cpu_oracle_sample(img, ws, bs, side, seed, image_id=0, quant=1, mode=1, scales=None):
+    """FP64 oracle (optionally emulating the reduced-precision rounding) forward and
+    actions on a side x side centre crop."""
     import oracle as O
     h, w = img.shape
+    side = min(side, h, w)
     y0, x0 = (h - side) // 2, (w - side) // 2
     reg = (y0, x0, side, side)
     t0 = time.perf_counter()
-    _, p, _ = O.forward(img, ws, bs, noise_seed=seed, image=image_id, quant=1, region=reg)
-    lev, u = O.sample(p, h, w, reg, 1, seed, image_id)
+    _, p, _ = O.forward(img, ws, bs, noise_seed=seed, image=image_id, quant=quant, act_scale=scales, region=reg)
+    lev, u = O.sample(p, h, w, reg, mode, seed, image_id)
     dt = time.perf_counter() - t0
     return dt, reg, p, lev, u
 
@@ -150,7 +145,7 @@ def run_reference(args):
         "impl": "reference", "metric": "halftone Mpixels/s", "value": v, "unit": "Mpx/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"printer {args.batch}x{args.size}x{args.size}, 2->64x7->1 policy, Bernoulli seed 1",
+        "config": {"workload": f"printer {args.batch}x{args.size}x{args.size}, 2->64x7->1 policy, BF16, Bernoulli seed 1, 1-bit packed",
                    "sample": f"{side}x{side} centre crop of image 0 per step"},
         "cpu_baseline": {"value": v, "unit": "Mpx/s", "cores": O.num_threads(), "kind": "oracle",
                          "sample": f"{side}x{side} crop per step, BF16-emulating FP64 forward + sampling"},
@@ -159,15 +154,43 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+WORKLOADS = {
+    # name: (description, precision, head, net, mode, seed)
+    "printer": ("printer {b}x{h}x{w}, 2->64x7->1 policy, BF16, Bernoulli seed 1, 1-bit packed", "bf16", 0, "wide", 1, 1),
+    "multitone": ("multitone 4x4096x4096, 2->64x7->4 softmax head (levels 0,1/3,2/3,1), FP8 E4M3, Philox seed 2",
+                  "fp8", 1, "wide4", 1, 2),
+    "uneven": ("uneven batch of 64 images, sizes log-uniform 200x300..4096x3072 (seed 4), BF16, Bernoulli seed 4",
+               "bf16", 0, "wide", 1, 4),
+    "small": ("one 256x256 image (seed 0), 2->32x5->1 policy, plain FP32, threshold 0.5", "fp32", 0, "small", 0, 0),
+}
+
+
+def build_inputs(args, rank):
+    from paper_2304_12152_gb300 import synth
+    if args.workload == "printer":
+        shapes = [(args.size, args.size)] * args.batch
+        seed = 1
+    elif args.workload == "multitone":
+        shapes = [(4096, 4096)] * 4
+        seed = 2
+    elif args.workload == "uneven":
+        shapes = synth.uneven_shapes(64, seed=4)
+        seed = 4
+    else:
+        shapes = [(256, 256)]
+        seed = 0
+    return [synth.contone_image(h, w, seed=seed, index=rank * 1000 + i) for i, (h, w) in enumerate(shapes)], shapes
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="printer", choices=sorted(list(WORKLOADS) + ["train"]))
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--size", type=int, default=2048)
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--ref-side", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -177,6 +200,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "train":
+        return run_train(args)
 
     import numpy as np
     import torch
@@ -190,19 +215,23 @@ def main():
     from paper_2304_12152_gb300 import _native as N
     from paper_2304_12152_gb300 import api, synth
 
-    chs = synth.NET_WIDE
+    desc, precision, head, netname, mode, seed = WORKLOADS[args.workload]
+    chs = {"wide": synth.NET_WIDE, "wide4": synth.NET_WIDE_K4, "small": synth.NET_SMALL}[netname]
     ws, bs = synth.he_normal_policy(chs, 1)
-    prec = N.HT_BF16 if args.precision == "bf16" else N.HT_FP32
-    pol = api.Policy(chs, ws, bs, precision=prec)
-    imgs_np = workload_images(args, rank)
+    prec = {"bf16": N.HT_BF16, "fp8": N.HT_FP8_E4M3, "fp32": N.HT_FP32}[precision]
+    pol = api.Policy(chs, ws, bs, head=head, precision=prec)
     dev = torch.device("cuda", local)
+    if prec == N.HT_FP8_E4M3:
+        calib = torch.from_numpy(synth.contone_image(256, 256, seed=99)).to(dev)
+        pol.calibrate(calib, seed=99)
+    imgs_np, shapes = build_inputs(args, rank)
     cs = [torch.from_numpy(c).to(dev) for c in imgs_np]
     bits = [pol.alloc_bits(c.shape[0], c.shape[1], dev) for c in cs]
     px_per_step = sum(c.numel() for c in cs)
     stream = torch.cuda.current_stream()
 
     def step():
-        pol.halftone_into(cs, bits, N.HT_MODE_BERNOULLI, 1)
+        pol.halftone_into(cs, bits, mode, seed)
 
     def barrier():
         if world > 1:
@@ -233,8 +262,7 @@ def main():
     prof = api.profile_end()
     barrier()
     api.sync()
-    ms = ev0.elapsed_time(ev1)
-    ms = max_over_ranks(ms)
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
     ms_step = ms / args.steps
     value = world * px_per_step / (ms_step * 1e-3) / 1e6
 
@@ -267,13 +295,13 @@ def main():
     # ---------------- plain FP32 form of the same net ----------------
     fp32 = None
     if prec != N.HT_FP32 and args.fp32_steps > 0:
-        pol32 = api.Policy(chs, ws, bs, precision=N.HT_FP32)
-        pol32.halftone_into(cs, bits, N.HT_MODE_BERNOULLI, 1)
+        pol32 = api.Policy(chs, ws, bs, head=head, precision=N.HT_FP32)
+        pol32.halftone_into(cs, bits, mode, seed)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.fp32_steps):
-            pol32.halftone_into(cs, bits, N.HT_MODE_BERNOULLI, 1)
+            pol32.halftone_into(cs, bits, mode, seed)
         f1.record(stream)
         torch.cuda.synchronize()
         fms = max_over_ranks(f0.elapsed_time(f1)) / args.fp32_steps
@@ -286,18 +314,32 @@ def main():
     # ---------------- roofline of the dominant kernel ----------------
     pk, src = peaks()
     roof = None
-    kname = "k_conv_tc_bf16" if prec != N.HT_FP32 else "k_conv3x3_fp32"
+    kname = {N.HT_BF16: "k_conv_tc_bf16", N.HT_FP8_E4M3: "k_conv_tc_fp8", N.HT_FP32: "k_conv3x3_fp32"}[prec]
     if kname in prof:
         launches, tot = prof[kname]
         per_launch_ms = tot / launches
-        flops_launch = 2 * 9 * 64 * 64 * (px_per_step / args.batch)   # one 64->64 layer on one image
+        cmid = chs[1]
+        n_mid = len(chs) - 3 if prec != N.HT_FP32 else len(chs) - 2
+        # one launch = one C -> C layer over one image: layers x pixels / launches
+        flops_launch = 2 * 9 * cmid * cmid * px_per_step * args.steps * n_mid / launches
         achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
-        peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
-        roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "per_launch_ms": per_launch_ms,
-                "peak_source": f"{src} bf16 dense, sustained"}
-    kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, sum(x[1] for x in prof.values()))}
-               for k, v in prof.items()}
+        if prec == N.HT_FP32:
+            roof = {"bound": "alu", "kernel": kname, "achieved": achieved,
+                    "peak": fp32_alu_peak(clk.summary()), "unit": "TFLOP/s", "traffic": None,
+                    "per_launch_ms": per_launch_ms,
+                    "peak_source": "SM count x 128 FP32 FMA/clk x 2 x median SM clock under load"}
+            roof["frac"] = achieved / roof["peak"]
+        else:
+            peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+            psrc = f"{src} bf16 dense, sustained"
+            if prec == N.HT_FP8_E4M3:
+                peak *= 2.0
+                psrc = f"{src} bf16 dense sustained x 2 (nominal fp8/bf16 ratio 4.5/2.25)"
+            roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": conv_traffic(args, kname, px_per_step, launches / args.steps),
+                    "per_launch_ms": per_launch_ms, "peak_source": psrc}
+    tot_ms = max(1e-9, sum(x[1] for x in prof.values()))
+    kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / tot_ms} for k, v in prof.items()}
     gpu_launches = sum(v[0] for v in prof.values())
 
     # ---------------- CPU oracle baseline on a bounded sample ----------------
@@ -305,40 +347,118 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
         O.build()
-        side = 64
-        dt, *_ = cpu_oracle_sample(imgs_np[0], ws, bs, side, 1)
-        side = int(min(1024, max(64, side * math.sqrt(15.0 / max(dt, 1e-3)))))
+        quant = {N.HT_BF16: 1, N.HT_FP8_E4M3: 2, N.HT_FP32: 0}[prec]
+        side = 32
+        dt, *_ = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None)
+        side = int(min(min(imgs_np[0].shape), 1024, max(32, side * math.sqrt(15.0 / max(dt, 1e-3)))))
         side -= side % 8
-        dt, reg, p, lev_or, u = cpu_oracle_sample(imgs_np[0], ws, bs, side, 1)
-        y0, x0, rh, rw = reg
-        lev_gpu = api.unpack_bits(bits[0], args.size, args.size)[y0:y0 + rh, x0:x0 + rw]
-        decided = np.abs(p[0] - u) > 1e-4
-        mism = int(((lev_gpu != lev_or) & decided).sum())
+        dt, reg, p, lev_or, u = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None)
         cpu = {"value": side * side / dt / 1e6, "unit": "Mpx/s", "cores": O.num_threads(), "kind": "oracle",
-               "sample": f"{side}x{side} centre crop of image 0 (+8 px halo), BF16-emulating FP64 forward + "
-                         f"Bernoulli actions", "seconds": dt,
-               "bit_match": {"decided": int(decided.sum()), "mismatch": mism,
-                             "rate": 1.0 - mism / max(1, int(decided.sum())), "margin": 1e-4}}
+               "sample": f"{side}x{side} centre crop of image 0 (+halo), FP64 forward"
+                         f"{' emulating the ' + precision.upper() + ' rounding' if quant else ''} + actions",
+               "seconds": dt}
+        if quant != 2:   # FP8 scales come from the library's calibration: no bit comparison
+            y0, x0, rh, rw = reg
+            lev_gpu = api.unpack_bits(bits[0], imgs_np[0].shape[0], imgs_np[0].shape[1], head)[y0:y0 + rh, x0:x0 + rw]
+            if p.shape[0] == 1:
+                decided = np.abs(p[0] - u) > 1e-4
+            else:
+                cdf = np.cumsum(p, 0)
+                decided = np.all(np.abs(cdf - u[None]) > 1e-4, 0) if mode == 1 else np.ones_like(u, bool)
+            mism = int(((lev_gpu != lev_or) & decided).sum())
+            cpu["bit_match"] = {"decided": int(decided.sum()), "mismatch": mism,
+                                "rate": 1.0 - mism / max(1, int(decided.sum())), "margin": 1e-4}
 
     if rank == 0:
+        wdesc = desc.format(b=args.batch, h=args.size, w=args.size)
         line = {
             "metric": "halftone Mpixels/s", "value": value, "unit": "Mpx/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec != N.HT_FP32 else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": precision if precision != "fp8" else "e4m3",
             "data": "synthetic",
-            "config": {"workload": f"printer {args.batch}x{args.size}x{args.size}, 2->64x7->1 policy, "
-                                   f"Bernoulli seed 1, 1-bit packed", "batch": args.batch,
-                       "image": [args.size, args.size], "parallelism": f"replicas x{world}",
-                       "l2": "inputs and activations larger than L2"},
+            "config": {"workload": wdesc, "images": len(shapes), "pixels_per_step": px_per_step,
+                       "parallelism": f"replicas x{world}", "l2": "inputs and activations larger than L2"},
             "e2e": {"value": e2e_val, "unit": "Mpx/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms},
             "roofline": roof, "fp32_plain": fp32, "cpu_baseline": cpu, "kernels": kernels,
             "gpu_launches": gpu_launches, "clocks": clk.summary(),
         }
+        if args.workload == "uneven":
+            line["config"]["shapes"] = shapes
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def fp32_alu_peak(clocks):
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def conv_traffic(args, kname, px_per_step, launches_per_step):
+    """DRAM bytes per launch of the conv kernel, from the committed ncu summary when its
+    recorded source hash matches the current kernel source (else null)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2304_12152_gb300", "csrc", "conv_tc.cu")
+    summ = os.path.join(ROOT, "profiles", "k_conv_tc_bf16_2048.md")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        txt = open(summ).read()
+    except OSError:
+        return None
+    import re
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    b = re.search(r"dram_bytes_per_px_per_layer:\s*([0-9.]+)", txt)
+    if not m or not b or m.group(1) != h or kname != "k_conv_tc_bf16":
+        return None
+    # one launch = one 64 -> 64 layer over one image (six layers per image)
+    return float(b.group(1)) * px_per_step * 6.0 / launches_per_step
+
+
+def run_train(args):
+    """Training step (Algorithm 1 TRAIN) timing: 16 crops 256x256 + 4 gray patches, S = 4."""
+    import torch
+    from paper_2304_12152_gb300 import _native as N
+    from paper_2304_12152_gb300 import api, synth
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    chs = synth.NET_WIDE
+    ws, bs = synth.he_normal_policy(chs, 3)
+    pol = api.Policy(chs, ws, bs, precision=N.HT_FP32)
+    tr = api.Trainer(pol, (256, 256), max_crops=16, n_samples=4, n_gray=4, gray_n=256, las_mode=1, n_rad=32,
+                     n_ang=16, w_a=0.002)
+    crops = [torch.from_numpy(synth.contone_image(256, 256, seed=3, index=i)).cuda() for i in range(16)]
+    levels = [0.1, 0.25, 0.5, 0.75]
+    gw = torch.empty(pol.num_params() - sum(chs[1:]), device="cuda")
+    gb = torch.empty(sum(chs[1:]), device="cuda")
+    for _ in range(args.warmup):
+        tr.forward(crops, levels, 1)
+        tr.backward(gw, gb)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    api.profile_begin()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for k in range(args.steps):
+            losses = tr.forward(crops, levels, 1 + k)
+            tr.backward(gw, gb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    prof = api.profile_end()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({
+        "metric": "training step time", "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "train: 16 crops 256x256 + 4 gray 256x256 {0.1,0.25,0.5,0.75}, S=4, "
+                               "2->64x7->1, w_s 0.06, w_a 0.002, 32x16-bin anisotropy loss"},
+        "losses": {"total": losses[0], "marl": losses[1], "las": losses[2], "mean_R": losses[3]},
+        "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
+        "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk.summary()}), flush=True)
 
 
 if __name__ == "__main__":

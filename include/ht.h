@@ -109,6 +109,13 @@ ht_status ht_policy_set_weights(ht_policy *p, const float *weights_dev, const fl
  * are ignored).  Each hidden layer's input a is stored as e4m3(a / s_l). */
 ht_status ht_policy_set_act_scales(ht_policy *p, const float *scales_host, int n);
 
+/* FP8 form: derive the static activation scales from one calibration image
+ * (device contone, Philox noise with `seed`): an FP32 forward records each
+ * hidden layer's largest activation a_max and sets its consumer's scale to the
+ * power of two 2^ceil(log2(a_max / 448)) (448 = largest e4m3 value), then
+ * repacks.  Synchronises `stream`; allocates a temporary activation buffer. */
+ht_status ht_policy_calibrate(ht_policy *p, const ht_image *img, uint64_t seed, void *stream);
+
 /* Total parameter count and FLOPs per output pixel (2 x MACs). */
 int64_t ht_policy_num_params(const ht_policy *p);
 int64_t ht_policy_flops_per_px(const ht_policy *p);

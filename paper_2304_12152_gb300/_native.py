@@ -20,6 +20,7 @@ HT_MODE_THRESHOLD, HT_MODE_BERNOULLI = 0, 1
 # Every entry point declared in include/ht.h.
 EXPORTS = (
     "ht_create_policy", "ht_destroy_policy", "ht_policy_set_weights", "ht_policy_set_act_scales",
+    "ht_policy_calibrate",
     "ht_policy_num_params", "ht_policy_flops_per_px", "ht_bits_row_words", "ht_halftone",
     "ht_reward_opts_default", "ht_reward", "ht_reward_noalloc", "ht_toggle_delta", "ht_anisotropy_loss",
     "ht_train_create", "ht_train_destroy", "ht_train_step_fwd", "ht_train_step_bwd",
@@ -80,6 +81,7 @@ def load(build_if_missing: bool = True):
         L.ht_destroy_policy.argtypes = [vp]
         L.ht_policy_set_weights.argtypes = [vp, vp, vp, vp]
         L.ht_policy_set_act_scales.argtypes = [vp, vp, i]
+        L.ht_policy_calibrate.argtypes = [vp, P(Image), u64, vp]
         L.ht_policy_num_params.argtypes = [vp]
         L.ht_policy_num_params.restype = i64
         L.ht_policy_flops_per_px.argtypes = [vp]

@@ -90,6 +90,10 @@ class Policy:
         a = np.ascontiguousarray(scales, np.float32)
         check(N.load().ht_policy_set_act_scales(self._h, a.ctypes.data, a.size))
 
+    def calibrate(self, contone: torch.Tensor, seed: int = 99, stream=None) -> None:
+        """FP8 form: static activation scales from one calibration image (ht_policy_calibrate)."""
+        check(N.load().ht_policy_calibrate(self._h, _images([contone]), seed, _stream(stream)))
+
     def set_weights(self, w_dev: torch.Tensor, b_dev: torch.Tensor, stream=None) -> None:
         check(N.load().ht_policy_set_weights(self._h, w_dev.data_ptr(), b_dev.data_ptr(), _stream(stream)))
 

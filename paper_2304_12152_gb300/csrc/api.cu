@@ -257,6 +257,76 @@ ht_status ht_policy_set_act_scales(ht_policy *p, const float *scales_host, int n
     return HT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+__global__ void k_absmax(const float *__restrict__ a, size_t n, unsigned int *__restrict__ out)
+{
+    float m = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(a[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));   // non-negative floats order as uints
+}
+}  // namespace
+
+extern "C" {
+
+ht_status ht_policy_calibrate(ht_policy *p, const ht_image *img, uint64_t seed, void *stream)
+{
+    HT_CHECK_ARG(p && img && img->contone, "null argument");
+    HT_CHECK_ARG(img->h >= 1 && img->w >= 1 && img->pitch >= img->w, "bad calibration image");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t px = (size_t)img->h * img->w;
+    size_t tot = 0;
+    for (int l = 1; l < p->L; ++l) tot += (size_t)p->ch[l] * px;
+    float *acts = nullptr, *prob = nullptr;
+    uint32_t *bits = nullptr;
+    unsigned int *amax = nullptr;
+    cudaError_t e = cudaMalloc((void **)&acts, sizeof(float) * tot);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&prob, sizeof(float) * px * p->K);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&bits, sizeof(uint32_t) * img->h * ht_bits_row_words(img->w, p->head));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&amax, sizeof(unsigned int) * HT_MAX_LAYERS);
+    ht_status st = e == cudaSuccess ? HT_OK : HT_ERR_OOM;
+    unsigned int h_amax[HT_MAX_LAYERS] = {0};
+    if (st == HT_OK) {
+        float *ap[HT_MAX_LAYERS];
+        size_t off = 0;
+        for (int l = 0; l + 1 < p->L; ++l) {
+            ap[l] = acts + off;
+            off += (size_t)p->ch[l + 1] * px;
+        }
+        st = ht_fwd_fp32_save(p, *img, 0u, seed, ap, prob, bits, s);
+        if (st == HT_OK && cudaMemsetAsync(amax, 0, sizeof(unsigned int) * HT_MAX_LAYERS, s) != cudaSuccess)
+            st = HT_ERR_CUDA;
+        for (int l = 0; st == HT_OK && l + 1 < p->L; ++l) {
+            k_absmax<<<256, 256, 0, s>>>(ap[l], (size_t)p->ch[l + 1] * px, amax + l);
+            if (cudaGetLastError() != cudaSuccess) st = HT_ERR_CUDA;
+        }
+        if (st == HT_OK && (cudaMemcpyAsync(h_amax, amax, sizeof(h_amax), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                            cudaStreamSynchronize(s) != cudaSuccess))
+            st = HT_ERR_CUDA;
+    }
+    cudaFree(acts);
+    cudaFree(prob);
+    cudaFree(bits);
+    cudaFree(amax);
+    if (st != HT_OK) {
+        ht_set_error("calibration failed");
+        return st;
+    }
+    // activation l (output of layer l) is the input of layer l + 1
+    for (int l = 0; l + 1 < p->L; ++l) {
+        float a;
+        memcpy(&a, &h_amax[l], 4);
+        const double r = (a > 0.f ? a : 1e-6f) / 448.0;
+        p->act_scale[l + 1] = (float)ldexp(1.0, (int)ceil(log2(r)));
+    }
+    if (p->prec != HT_FP32) return ht_pack_tc_weights(p, s);
+    return HT_OK;
+}
+
 int64_t ht_policy_num_params(const ht_policy *p) { return p ? p->n_w + p->n_b : 0; }
 
 int64_t ht_policy_flops_per_px(const ht_policy *p)

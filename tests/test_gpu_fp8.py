@@ -92,3 +92,20 @@ def test_bf16_softmax_head(mode):
     n, bad = compare_levels(lev[0], ref, decided_mask(pq, u, mode))
     assert bad <= max(1, 3e-3 * n)
     assert np.abs(probs[0] - px).max() < 6e-3
+
+
+def test_library_calibration_matches_oracle_scales():
+    """ht_policy_calibrate (FP32 forward + per-layer abs-max, power-of-two scales) gives the
+    same halftone as scales derived with the oracle on the same calibration image."""
+    chs = synth.NET_WIDE
+    ws, _ = synth.he_normal_policy(chs, 2)
+    bs = synth.random_biases(chs, 5)
+    sc = calibrate(ws, bs, chs)
+    a = api.Policy(chs, ws, bs, precision=N.HT_FP8_E4M3)
+    a.set_act_scales(sc)
+    b = api.Policy(chs, ws, bs, precision=N.HT_FP8_E4M3)
+    b.calibrate(torch.from_numpy(synth.contone_image(64, 64, seed=99)).cuda(), seed=99)
+    imgs = [synth.contone_image(40, 140, seed=6)]
+    la, _ = _run(a, imgs, 1, seed=3)
+    lb, _ = _run(b, imgs, 1, seed=3)
+    np.testing.assert_array_equal(la[0], lb[0])
