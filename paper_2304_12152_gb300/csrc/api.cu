@@ -377,23 +377,23 @@ ht_status ht_halftone(ht_policy *p, const ht_image *imgs, int n, int mode, uint6
     HT_CHECK_ARG(out_bits != nullptr, "null output array");
     for (int i = 0; i < n; ++i) HT_CHECK_ARG(out_bits[i] != nullptr, "image %d: null bits pointer", i);
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->prec != HT_FP32) {
+        st = ht_policy_ensure_ws(p, ht_tc_batch_ws_bytes(p, imgs, n));
+        if (st != HT_OK) return st;
+        return ht_run_tc_batch(p, imgs, n, mode, seed, out_bits, out_prob, s);
+    }
     size_t need = 0;
     for (int i = 0; i < n; ++i) {
-        const size_t b = p->prec == HT_FP32 ? ht_fp32_ws_bytes(p, imgs[i].h, imgs[i].w)
-                                            : ht_tc_ws_bytes(p, imgs[i].h, imgs[i].w);
+        const size_t b = ht_fp32_ws_bytes(p, imgs[i].h, imgs[i].w);
         need = b > need ? b : need;
     }
     st = ht_policy_ensure_ws(p, need);
     if (st != HT_OK) return st;
     for (int i = 0; i < n; ++i) {
         float *prob = out_prob ? out_prob[i] : nullptr;
-        if (p->prec == HT_FP32) {
-            const size_t half = ht_fp32_ws_bytes(p, imgs[i].h, imgs[i].w) / 2;
-            st = ht_run_fp32(p, imgs[i], (uint32_t)i, mode, seed, out_bits[i], prob, (float *)p->d_ws,
-                             (float *)((char *)p->d_ws + half), s);
-        } else {
-            st = ht_run_tc(p, imgs[i], (uint32_t)i, mode, seed, out_bits[i], prob, s);
-        }
+        const size_t half = ht_fp32_ws_bytes(p, imgs[i].h, imgs[i].w) / 2;
+        st = ht_run_fp32(p, imgs[i], (uint32_t)i, mode, seed, out_bits[i], prob, (float *)p->d_ws,
+                         (float *)((char *)p->d_ws + half), s);
         if (st != HT_OK) return st;
     }
     return HT_OK;

@@ -32,6 +32,10 @@
 // quarters 2, 3, 0, 1).  Every mbarrier wait is bounded (globaltimer); on
 // expiry the kernel records HT_ERR_TIMEOUT, drains its own copies and MMAs,
 // frees TMEM and returns.
+#include <stdlib.h>
+
+#include <vector>
+
 #include "head.cuh"
 
 namespace {
@@ -272,8 +276,45 @@ __device__ __forceinline__ void store_channels32(const float *v, int half, void 
     }
 }
 
+// One image of a batched call.  Every kernel of the tensor-core form walks a
+// flattened index space (conv units, layer-1 tiles, head tiles) over all images
+// of the call and finds its image through the *_begin prefix sums.
+struct ImgDesc {
+    const float *contone;
+    uint8_t *act[2];          // ping-pong chunk-planar activation buffers
+    uint32_t *bits;
+    float *prob;              // nullable
+    int cpitch, H, W, words;
+    uint32_t image;           // Philox image index (position in the call)
+    int xtiles;               // ceil(W / 128)
+    int unit_begin;           // first conv unit (xtiles * ceil(H / RU) units per image)
+    int f1_begin;             // first layer-1 tile (xtiles * ceil(H / F1_ROWS))
+    int hd_begin;             // first head tile (ceil(W / 32) * ceil(H / 8))
+};
+
+// largest i with begin(i) <= u (images sorted by their begin offsets)
+template <typename F>
+__device__ __forceinline__ int find_image(int n, int u, F begin)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin(mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct UnitInfo {
+    const uint8_t *in;
+    uint8_t *out;
+    int H, W, x0, y0, nrows;
+};
+
 struct ConvParams {
-    const uint8_t *in;       // chunk-planar input activations
+    const ImgDesc *imgs;     // device table of the call's images
+    int n_imgs, n_units;
+    int in_buf;              // activations are read from act[in_buf], written to act[in_buf ^ 1]
     const void *wpack;       // packed weights of this layer ([dx][chunk][3 dy][n][16 B])
     // per-output-channel epilogue constants, read straight from the kernel's
     // constant bank: acc * scale[n] + bias[n] (scale = input scale x weight
@@ -283,12 +324,26 @@ struct ConvParams {
     float head_w[9 * 64];    // fused 1-logit head: last-layer weights [tap][channel]
     float out_inv_scale;     // FP8 output: 1 / scale of the next layer's input
     int out_fp8;
-    void *out;               // chunk-planar output
-    float *partials;         // non-null on the last hidden layer of a 1-logit head: receives the 9 per-tap dot
-                             // products of the head, [9][H][W], instead of the activations
-    int H, W, n_xtiles, rows_per_unit, n_units;
     int *err;
 };
+
+template <int RUx>
+__device__ __forceinline__ UnitInfo unit_info(const ConvParams &P, int u)
+{
+    const int im = find_image(P.n_imgs, u, [&](int i) { return __ldg(&P.imgs[i].unit_begin); });
+    const ImgDesc *D = P.imgs + im;
+    const int lu = u - __ldg(&D->unit_begin);
+    const int xt = __ldg(&D->xtiles);
+    UnitInfo ui;
+    ui.H = __ldg(&D->H);
+    ui.W = __ldg(&D->W);
+    ui.x0 = (lu % xt) * TILE_M;
+    ui.y0 = (lu / xt) * RUx;
+    ui.nrows = min(ui.H, ui.y0 + RUx) - ui.y0;
+    ui.in = (const uint8_t *)D->act[P.in_buf];
+    ui.out = D->act[P.in_buf ^ 1];
+    return ui;
+}
 
 // ---------------------------------------------------------------------------
 // 64 -> 64 layer on tcgen05
@@ -358,11 +413,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         uint32_t li = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
-            const int xt = u % P.n_xtiles, ys = u / P.n_xtiles;
-            const int y0 = ys * RU;
-            const int y1 = min(P.H, y0 + RU);
-            const int x0 = xt * TILE_M;
-            const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, P.W);   // in-image pixel range
+            const UnitInfo ui = unit_info<RU>(P, u);
+            const int y0 = ui.y0, y1 = ui.y0 + ui.nrows, x0 = ui.x0;
+            const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, ui.W);   // in-image pixel range
             for (int r = 0; r < (y1 - y0) + 2; ++r, ++li) {
                 const int slot = (int)(li % NSLOT);
                 const uint32_t ph = (li / NSLOT) & 1u;
@@ -374,7 +427,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 }
                 uint8_t *dst = s_rows + slot * C::SLOT_BYTES;
                 const int yy = y0 - 1 + r;
-                const bool row_in = (yy >= 0 && yy < P.H);
+                const bool row_in = (yy >= 0 && yy < ui.H);
                 bool zeroed = false;
                 if (!row_in) {
                     for (int k = lane; k < C::NCHUNK * ROW_PX; k += 32)
@@ -397,7 +450,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         mbar_arrive_expect_tx(smem_u32(&full[slot]), run * C::NCHUNK);
                         for (int c = 0; c < C::NCHUNK; ++c)
                             bulk_g2s(smem_u32(dst + ((size_t)c * ROW_PX + (lo - (x0 - 1))) * 16),
-                                     P.in + (((size_t)c * P.H + yy) * P.W + lo) * 16, run, smem_u32(&full[slot]));
+                                     ui.in + (((size_t)c * ui.H + yy) * ui.W + lo) * 16, run, smem_u32(&full[slot]));
                     } else {
                         mbar_arrive(smem_u32(&full[slot]));
                     }
@@ -428,9 +481,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         bool ok = wait1(smem_u32(wbar), 0);
         uint32_t q = 0, uit = 0;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
-            const int ys = u / P.n_xtiles;
-            const int y0 = ys * RU;
-            const int nrows = min(P.H, y0 + RU) - y0;
+            const int nrows = unit_info<RU>(P, u).nrows;
             for (int k = 0; k < nrows + 2 && ok; ++k, ++q) {
                 ok = wait1(smem_u32(&full[q % NSLOT]), (q / NSLOT) & 1u);
                 if (ok && k < nrows) ok = wait1(smem_u32(&bfree[k]), uit & 1u);   // block k enters use
@@ -485,10 +536,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         uint32_t uit = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
-            const int xt = u % P.n_xtiles, ys = u / P.n_xtiles;
-            const int y0 = ys * RU;
-            const int nrows = min(P.H, y0 + RU) - y0;
-            const int x = xt * TILE_M + px;
+            const UnitInfo ui = unit_info<RU>(P, u);
+            const int y0 = ui.y0, nrows = ui.nrows;
+            const int x = ui.x0 + px;
             for (int j = grp; j < RU; j += 2) {
                 int got = 0;
                 if (lane == 0) got = mbar_wait(smem_u32(&bfull[j]), uit & 1u, s_abort, P.err) ? 1 : 0;
@@ -512,12 +562,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&bfree[j]));
-                if (j < nrows && x < P.W) {
+                if (j < nrows && x < ui.W) {
 #pragma unroll
                     for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], P.scale[n], P.bias[n]), 0.f);
                     if constexpr (HEAD) {
                         // fused 64 -> 1 head: per-tap dot products of the bf16-rounded activations
-                        const size_t plane = (size_t)P.H * P.W, o = (size_t)(y0 + j) * P.W + x;
+                        const size_t plane = (size_t)ui.H * ui.W, o = (size_t)(y0 + j) * ui.W + x;
+                        float *partials = (float *)ui.out;
                         float acc[9];
 #pragma unroll
                         for (int t = 0; t < 9; ++t) acc[t] = 0.f;
@@ -528,9 +579,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                             for (int t = 0; t < 9; ++t) acc[t] = fmaf(a, P.head_w[t * 64 + n], acc[t]);   // nine chains
                         }
 #pragma unroll
-                        for (int t = 0; t < 9; ++t) P.partials[t * plane + o] = acc[t];
+                        for (int t = 0; t < 9; ++t) partials[t * plane + o] = acc[t];
                     } else {
-                        store_pixel(v, P.out, P.out_fp8, P.out_inv_scale, P.H, P.W, y0 + j, x);
+                        store_pixel(v, ui.out, P.out_fp8, P.out_inv_scale, ui.H, ui.W, y0 + j, x);
                     }
                 }
             }
@@ -593,11 +644,17 @@ __device__ __forceinline__ void build_first_a(uint8_t *s_a, const float (*s_c)[T
     }
 }
 
-__global__ void __launch_bounds__(256) k_first_mma(const float *__restrict__ contone, int cpitch, int H, int W,
-                                                   uint64_t seed, uint32_t image, const uint8_t *__restrict__ w1pack,
-                                                   const float *__restrict__ b1, void *out, int out_fp8,
-                                                   float out_inv_scale, int *err)
+__global__ void __launch_bounds__(256) k_first_mma(const ImgDesc *__restrict__ imgs, int n_imgs, uint64_t seed,
+                                                   const uint8_t *__restrict__ w1pack, const float *__restrict__ b1,
+                                                   int out_fp8, float out_inv_scale, int *err)
 {
+    const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].f1_begin); });
+    const ImgDesc *D = imgs + im;
+    const int lt = (int)blockIdx.x - D->f1_begin;
+    const float *__restrict__ contone = D->contone;
+    const int cpitch = D->cpitch, H = D->H, W = D->W;
+    const uint32_t image = D->image;
+    void *out = D->act[0];
     extern __shared__ uint8_t f1_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)f1_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *s_a = base;                                        // 2 x [8 chunks][128 px][16 B]
@@ -609,7 +666,7 @@ __global__ void __launch_bounds__(256) k_first_mma(const float *__restrict__ con
     uint32_t *s_tmem = (uint32_t *)(s_bar + 2);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * TILE_M, y0 = blockIdx.y * F1_ROWS;
+    const int x0 = (lt % D->xtiles) * TILE_M, y0 = (lt / D->xtiles) * F1_ROWS;
     const int nrows = min(F1_ROWS, H - y0);
 
     for (int i = tid; i < (F1_ROWS + 2) * (TILE_M + 2); i += 256) {
@@ -727,15 +784,23 @@ __global__ void __launch_bounds__(256) k_first_mma(const float *__restrict__ con
 constexpr int HT_X = 32, HT_Y = 8;
 
 template <int K>
-__global__ void __launch_bounds__(HT_X *HT_Y) k_head_tc(const uint8_t *__restrict__ act, int H, int W,
+__global__ void __launch_bounds__(HT_X *HT_Y) k_head_tc(const ImgDesc *__restrict__ imgs, int n_imgs, int buf,
                                                         const float *__restrict__ wl, const float *__restrict__ bl,
-                                                        int head, int mode, uint64_t seed, uint32_t image,
-                                                        uint32_t *bits, int words, float *prob)
+                                                        int head, int mode, uint64_t seed)
 {
     extern __shared__ uint4 s_dyn[];
     uint4 *s_a = s_dyn;                                               // [8][HT_Y+2][HT_X+2]
     float *s_w = (float *)(s_a + 8 * (HT_Y + 2) * (HT_X + 2));       // [9][64][K]
-    const int x0 = blockIdx.x * HT_X, y0 = blockIdx.y * HT_Y;
+    const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].hd_begin); });
+    const ImgDesc *D = imgs + im;
+    const int lt = (int)blockIdx.x - D->hd_begin;
+    const int H = D->H, W = D->W, words = D->words;
+    const uint8_t *__restrict__ act = D->act[buf];
+    uint32_t *bits = D->bits;
+    float *prob = D->prob;
+    const uint32_t image = D->image;
+    const int hx = (W + HT_X - 1) / HT_X;
+    const int x0 = (lt % hx) * HT_X, y0 = (lt / hx) * HT_Y;
     const int tid = threadIdx.y * HT_X + threadIdx.x;
     for (int i = tid; i < 8 * (HT_Y + 2) * (HT_X + 2); i += HT_X * HT_Y) {
         const int c = i / ((HT_Y + 2) * (HT_X + 2)), rem = i % ((HT_Y + 2) * (HT_X + 2));
@@ -777,11 +842,16 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_tc(const uint8_t *__restric
 // 1-logit head from the per-tap partials written by the last conv layer:
 // z(y,x) = b + sum_{dy,dx} d_{dy,dx}(y+dy-1, x+dx-1) (zero outside the image).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const float *__restrict__ part, int H, int W, float bias,
-                                                              int mode, uint64_t seed, uint32_t image, uint32_t *bits,
-                                                              int words, float *prob)
+__global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__restrict__ imgs, int n_imgs, int buf,
+                                                              float bias, int mode, uint64_t seed)
 {
-    const int x0 = blockIdx.x * HT_X, y = blockIdx.y * HT_Y + threadIdx.y, x = x0 + threadIdx.x;
+    const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].hd_begin); });
+    const ImgDesc *D = imgs + im;
+    const int lt = (int)blockIdx.x - D->hd_begin;
+    const int H = D->H, W = D->W, words = D->words;
+    const float *__restrict__ part = (const float *)D->act[buf];
+    const int hx = (W + HT_X - 1) / HT_X;
+    const int x0 = (lt % hx) * HT_X, y = (lt / hx) * HT_Y + threadIdx.y, x = x0 + threadIdx.x;
     const size_t plane = (size_t)H * W;
     float z = bias;
     if (y < H && x < W) {
@@ -791,7 +861,7 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const float *__res
             if (yy >= 0 && yy < H && xx >= 0 && xx < W) z += __ldg(part + t * plane + (size_t)yy * W + xx);
         }
     }
-    ht_head_emit(&z, 1, HT_HEAD_SIGMOID, mode, seed, image, x0, y, H, W, bits, words, prob);
+    ht_head_emit(&z, 1, HT_HEAD_SIGMOID, mode, seed, D->image, x0, y, H, W, D->bits, words, D->prob);
 }
 
 // ---------------------------------------------------------------------------
@@ -978,89 +1048,150 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
 
 size_t ht_tc_ws_bytes(const ht_policy *p, int h, int w)
 {
-    const size_t eb = p->prec == HT_FP8_E4M3 ? 1 : 2;
-    // two ping-pong buffers; the bf16 one feeding the head is always 2 B/channel
-    return 2 * (size_t)h * w * 64 * 2 + 0 * eb + 256;
+    (void)p;
+    // two ping-pong buffers of 64 bf16 channels (the FP8 form stores e4m3 in the same space)
+    return 2 * (size_t)h * w * 64 * 2;
 }
 
-ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int mode, uint64_t seed,
-                    uint32_t *bits, float *prob, cudaStream_t s)
+namespace {
+size_t ws_budget()
 {
-    const int H = img.h, W = img.w;
+    static size_t b = 0;
+    if (!b) {
+        const char *e = getenv("HT_WS_BUDGET_GB");
+        const double gb = e ? atof(e) : 16.0;
+        b = (size_t)((gb > 0.5 ? gb : 0.5) * 1073741824.0);
+    }
+    return b;
+}
+}  // namespace
+
+size_t img_ws_slot(const ht_policy *p, const ht_image &img)
+{
+    return (ht_tc_ws_bytes(p, img.h, img.w) + 255) / 256 * 256;
+}
+
+size_t ht_tc_batch_ws_bytes(const ht_policy *p, const ht_image *imgs, int n)
+{
+    size_t maxg = 0, cur = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t b = img_ws_slot(p, imgs[i]);
+        if (cur > 0 && cur + b > ws_budget()) {      // same grouping rule as ht_run_tc_batch
+            maxg = cur > maxg ? cur : maxg;
+            cur = 0;
+        }
+        cur += b;
+    }
+    maxg = cur > maxg ? cur : maxg;
+    return maxg + (size_t)n * sizeof(ImgDesc) + 1024;
+}
+
+// All images of a call: grouped so that a group's activation buffers fit the
+// workspace budget; per group one launch of layer 1, one per 64 -> 64 layer and
+// one of the head, each over the whole group (persistent tile index space).
+ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
+                          uint32_t *const *bits, float *const *prob, cudaStream_t s)
+{
     const bool fp8 = (p->prec == HT_FP8_E4M3);
-    uint8_t *buf[2];
-    buf[0] = (uint8_t *)p->d_ws;
-    buf[1] = buf[0] + (size_t)H * W * 64 * 2;
     const int n_inner = p->L - 2;
     int *err = ht_device_error_flag();
     if (!err) return HT_ERR_CUDA;
-
-    // layer 1: output feeds inner layer 1 (e4m3 in the FP8 form)
-    {
-        const dim3 grid((W + TILE_M - 1) / TILE_M, (H + F1_ROWS - 1) / F1_ROWS);
-        const bool o8 = fp8 && n_inner > 0;
-        static bool attr1 = false;
-        if (!attr1) {
-            HT_CUDA_TRY(cudaFuncSetAttribute(k_first_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, F1_SMEM));
-            HT_CUDA_TRY(cudaFuncSetAttribute(k_first_mma, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-            attr1 = true;
-        }
-        ht_prof_start(HTK_FIRST_TC, s);
-        k_first_mma<<<grid, 256, F1_SMEM, s>>>(img.contone, img.pitch, H, W, seed, image_index,
-                                         (const uint8_t *)p->d_w1pack, p->d_b + p->b_off[0], buf[0], o8 ? 1 : 0,
-                                         o8 ? 1.f / p->act_scale[1] : 1.f, err);
-        ht_prof_stop(s);
-        HT_LAUNCH_CHECK();
+    // table slots after the activation region (one slot per image, never reused within a call)
+    const size_t need = ht_tc_batch_ws_bytes(p, imgs, n);
+    if (need > p->ws_bytes) {
+        ht_set_error("workspace too small");
+        return HT_ERR_INVALID_ARG;
     }
-    const int n_xtiles = (W + TILE_M - 1) / TILE_M;
-    const int rpu = RU;
-    int cur = 0;
-    for (int l = 1; l <= n_inner; ++l) {
-        const bool out8 = fp8 && (l < n_inner);
-        ConvParams P;
-        P.in = buf[cur];
-        P.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (l - 1);
-        for (int n = 0; n < 64; ++n) {
-            P.bias[n] = p->h_b[p->b_off[l] + n];
-            P.scale[n] = fp8 ? p->act_scale[l] * p->h_wscale[64 * (l - 1) + n] : 1.f;
-        }
-        P.out_inv_scale = out8 ? 1.f / p->act_scale[l + 1] : 1.f;
-        P.out_fp8 = out8 ? 1 : 0;
-        P.out = buf[cur ^ 1];
-        const bool fuse_head = (l == n_inner) && p->K == 1;
-        if (fuse_head) memcpy(P.head_w, p->h_headw, sizeof(P.head_w));
-        P.partials = fuse_head ? (float *)buf[cur ^ 1] : nullptr;
-        P.H = H;
-        P.W = W;
-        P.n_xtiles = n_xtiles;
-        P.rows_per_unit = rpu;
-        P.n_units = n_xtiles * ((H + rpu - 1) / rpu);
-        P.err = err;
-        const ht_status st = fp8 ? (fuse_head ? launch_conv<true, true>(P, s) : launch_conv<true, false>(P, s))
-                                 : (fuse_head ? launch_conv<false, true>(P, s) : launch_conv<false, false>(P, s));
-        if (st != HT_OK) return st;
-        cur ^= 1;
+    ImgDesc *d_table = (ImgDesc *)((uint8_t *)p->d_ws + (need - (size_t)n * sizeof(ImgDesc) - 512) / 256 * 256);
+    static bool attr_done = false;
+    if (!attr_done) {
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_first_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, F1_SMEM));
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_first_mma, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        const int hsmem = (int)(sizeof(uint4) * 8 * (HT_Y + 2) * (HT_X + 2) + sizeof(float) * 9 * 64 * 4);
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_head_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, hsmem));
+        attr_done = true;
     }
-    // head
-    {
-        static bool attr = false;
-        const size_t smem = sizeof(uint4) * 8 * (HT_Y + 2) * (HT_X + 2) + sizeof(float) * 9 * 64 * 4;
-        if (!attr) {
-            HT_CUDA_TRY(cudaFuncSetAttribute(k_head_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
+    int g0 = 0;
+    while (g0 < n) {
+        // group [g0, g1)
+        int g1 = g0;
+        size_t off = 0;
+        std::vector<ImgDesc> tab;
+        int units = 0, f1 = 0, hd = 0;
+        while (g1 < n) {
+            const size_t b = ht_tc_ws_bytes(p, imgs[g1].h, imgs[g1].w);
+            if (g1 > g0 && off + img_ws_slot(p, imgs[g1]) > ws_budget()) break;
+            ImgDesc D;
+            D.contone = imgs[g1].contone;
+            D.cpitch = imgs[g1].pitch;
+            D.H = imgs[g1].h;
+            D.W = imgs[g1].w;
+            D.act[0] = (uint8_t *)p->d_ws + off;
+            D.act[1] = D.act[0] + b / 2;
+            off += img_ws_slot(p, imgs[g1]);
+            D.bits = bits[g1];
+            D.prob = prob ? prob[g1] : nullptr;
+            D.words = ht_bits_row_words(D.W, p->head);
+            D.image = (uint32_t)g1;
+            D.xtiles = (D.W + TILE_M - 1) / TILE_M;
+            D.unit_begin = units;
+            D.f1_begin = f1;
+            D.hd_begin = hd;
+            units += D.xtiles * ((D.H + RU - 1) / RU);
+            f1 += D.xtiles * ((D.H + F1_ROWS - 1) / F1_ROWS);
+            hd += ((D.W + HT_X - 1) / HT_X) * ((D.H + HT_Y - 1) / HT_Y);
+            tab.push_back(D);
+            ++g1;
         }
-        const dim3 grid((W + HT_X - 1) / HT_X, (H + HT_Y - 1) / HT_Y);
-        const int words = ht_bits_row_words(W, p->head);
-        const float *wl = p->d_w + p->w_off[p->L - 1], *bl = p->d_b + p->b_off[p->L - 1];
-        ht_prof_start(HTK_HEAD_TC, s);
-        if (p->K == 1)
-            k_head_partials<<<grid, dim3(HT_X, HT_Y), 0, s>>>((const float *)buf[cur], H, W, p->head_bias, mode,
-                                                               seed, image_index, bits, words, prob);
-        else
-            k_head_tc<4><<<grid, dim3(HT_X, HT_Y), smem, s>>>(buf[cur], H, W, wl, bl, p->head, mode, seed,
-                                                              image_index, bits, words, prob);
-        ht_prof_stop(s);
-        HT_LAUNCH_CHECK();
+        const int ng = g1 - g0;
+        ImgDesc *dt = d_table + g0;
+        HT_CUDA_TRY(cudaMemcpyAsync(dt, tab.data(), sizeof(ImgDesc) * ng, cudaMemcpyHostToDevice, s));
+        // layer 1 -> act[0]
+        {
+            const bool o8 = fp8 && n_inner > 0;
+            ht_prof_start(HTK_FIRST_TC, s);
+            k_first_mma<<<f1, 256, F1_SMEM, s>>>(dt, ng, seed, (const uint8_t *)p->d_w1pack, p->d_b + p->b_off[0],
+                                                  o8 ? 1 : 0, o8 ? 1.f / p->act_scale[1] : 1.f, err);
+            ht_prof_stop(s);
+            HT_LAUNCH_CHECK();
+        }
+        int cur = 0;
+        for (int l = 1; l <= n_inner; ++l) {
+            const bool out8 = fp8 && (l < n_inner);
+            const bool fuse_head = (l == n_inner) && p->K == 1;
+            ConvParams P;
+            P.imgs = dt;
+            P.n_imgs = ng;
+            P.n_units = units;
+            P.in_buf = cur;
+            P.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (l - 1);
+            for (int c = 0; c < 64; ++c) {
+                P.bias[c] = p->h_b[p->b_off[l] + c];
+                P.scale[c] = fp8 ? p->act_scale[l] * p->h_wscale[64 * (l - 1) + c] : 1.f;
+            }
+            if (fuse_head) memcpy(P.head_w, p->h_headw, sizeof(P.head_w));
+            P.out_inv_scale = out8 ? 1.f / p->act_scale[l + 1] : 1.f;
+            P.out_fp8 = out8 ? 1 : 0;
+            P.err = err;
+            const ht_status st = fp8 ? (fuse_head ? launch_conv<true, true>(P, s) : launch_conv<true, false>(P, s))
+                                     : (fuse_head ? launch_conv<false, true>(P, s) : launch_conv<false, false>(P, s));
+            if (st != HT_OK) return st;
+            cur ^= 1;
+        }
+        // head
+        {
+            ht_prof_start(HTK_HEAD_TC, s);
+            if (p->K == 1) {
+                k_head_partials<<<hd, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, cur, p->head_bias, mode, seed);
+            } else {
+                const size_t hsmem = sizeof(uint4) * 8 * (HT_Y + 2) * (HT_X + 2) + sizeof(float) * 9 * 64 * 4;
+                k_head_tc<4><<<hd, dim3(HT_X, HT_Y), hsmem, s>>>(dt, ng, cur, p->d_w + p->w_off[p->L - 1],
+                                                                 p->d_b + p->b_off[p->L - 1], p->head, mode, seed);
+            }
+            ht_prof_stop(s);
+            HT_LAUNCH_CHECK();
+        }
+        g0 = g1;
     }
     return HT_OK;
 }

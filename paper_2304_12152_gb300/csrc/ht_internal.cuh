@@ -122,10 +122,11 @@ ht_status ht_fwd_fp32_save(ht_policy *p, const ht_image &img, uint32_t image_ind
 ht_status ht_dgrad_fp32(const float *g_out, const float *wt, int Cout, int Cin, int H, int W, const float *act_in,
                         float *g_in, cudaStream_t s);
 
-// tensor-core form, one image
-ht_status ht_run_tc(ht_policy *p, const ht_image &img, uint32_t image_index, int mode, uint64_t seed,
-                    uint32_t *bits, float *prob, cudaStream_t s);
+// tensor-core form, all images of a call (grouped under a workspace budget)
+ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
+                          uint32_t *const *bits, float *const *prob, cudaStream_t s);
 size_t ht_tc_ws_bytes(const ht_policy *p, int h, int w);
+size_t ht_tc_batch_ws_bytes(const ht_policy *p, const ht_image *imgs, int n);
 
 // reward / toggle deltas
 ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,

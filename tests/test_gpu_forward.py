@@ -157,3 +157,37 @@ def test_bf16_full_size_sampled():
             tot_bad += bad
     assert worst < BF16_Q_MAX and _p999(np.concatenate(diffs)) < BF16_Q_P999
     assert tot_bad <= max(1, 1e-3 * tot_n), (tot_bad, tot_n)
+
+
+GROUP_SCRIPT = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2304_12152_gb300 import _native as N, api, synth
+chs = synth.NET_WIDE
+ws, bs = synth.he_normal_policy(chs, 1)
+pol = api.Policy(chs, ws, bs, precision=N.HT_BF16)
+shapes = [(1500, 1200), (300, 200), (1024, 2000)]
+cs = [torch.from_numpy(synth.contone_image(h, w, seed=7, index=i)).cuda() for i, (h, w) in enumerate(shapes)]
+bits, _ = pol.halftone(cs, mode=1, seed=5)
+torch.cuda.synchronize()
+np.savez(sys.argv[2], *[b.cpu().numpy() for b in bits])
+'''
+
+
+def test_batch_grouping_is_invisible(tmp_path):
+    """Images split over several workspace groups (tiny budget: one image per group) give
+    the same bits as one group holding the whole call."""
+    import os
+    import subprocess
+    import sys
+    script = tmp_path / "g.py"
+    script.write_text(GROUP_SCRIPT)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for budget in ("64", "0.5"):
+        out = tmp_path / f"b{budget}.npz"
+        env = dict(os.environ, HT_WS_BUDGET_GB=budget)
+        subprocess.run([sys.executable, str(script), root, str(out)], check=True, env=env, timeout=600)
+        outs.append(np.load(out))
+    for k in outs[0].files:
+        np.testing.assert_array_equal(outs[0][k], outs[1][k])
