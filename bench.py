@@ -167,6 +167,10 @@ WORKLOADS = {
 
 def build_inputs(args, rank):
     from paper_2304_12152_gb300 import synth
+    if args.images and args.side:      # small case of any workload (profiling)
+        seed = WORKLOADS[args.workload][5]
+        shapes = [(args.side, args.side)] * args.images
+        return [synth.contone_image(h, w, seed=seed, index=rank * 1000 + i) for i, (h, w) in enumerate(shapes)], shapes
     if args.workload == "printer":
         shapes = [(args.size, args.size)] * args.batch
         seed = 1
@@ -191,6 +195,8 @@ def main():
     ap.add_argument("--workload", default="printer", choices=sorted(list(WORKLOADS) + ["train"]))
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--images", type=int, default=0, help="override: number of images (with --side)")
+    ap.add_argument("--side", type=int, default=0, help="override: square image side (with --images)")
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--ref-side", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -231,6 +231,7 @@ ht_status ht_destroy_policy(ht_policy *p)
     cudaFree(p->d_wpack);
     cudaFree(p->d_wscale);
     cudaFree(p->d_w1pack);
+    cudaFree(p->d_wpack4);
     cudaFree(p->d_ws);
     delete p;
     return HT_OK;

@@ -51,15 +51,30 @@ constexpr int TMEM_COLS = 512;
 constexpr int NTHREADS = 320;                // producer, MMA issuer, 8 epilogue warps
 constexpr unsigned long long kTimeoutNs = 2000000000ull;   // 2 s per wait
 
-template <bool FP8>
+// Kernel kinds built from one pipeline: a hidden 64 -> 64 layer, the last
+// hidden layer with the 1-logit head's per-tap partials fused into its
+// epilogue, and layer 1 (2 -> 64), whose input is the 16-byte-per-pixel bf16
+// hi/lo split of c and z written by k_first_input (one staged chunk; the second
+// K chunk of its MMAs is zero and stays resident in shared memory), and the
+// 64 -> 4 softmax head, whose three dy blocks are 16 columns wide (4 logits + 12
+// zero columns) and whose weights are kept exact as bf16 hi + lo (two MMAs per
+// K step); its epilogue applies softmax, draws the level and packs 2 bits/px.
+enum : int { KIND_HIDDEN = 0, KIND_HEADPART = 1, KIND_FIRST = 2, KIND_HEAD4 = 3 };
+
+template <bool FP8, int KIND>
 struct Cfg {
-    static constexpr int EB = FP8 ? 1 : 2;                    // bytes per element
-    static constexpr int CPC = 16 / EB;                        // channels per 16-byte chunk
-    static constexpr int NCHUNK = 64 / CPC;                    // chunks per pixel (8 / 4)
-    static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;    // 16640 / 8320
-    static constexpr int W_BYTES = 9 * NCHUNK * 64 * 16;       // 73728 / 36864 ([dx][chunk][3 dy][64 n][16 B])
-    static constexpr int KSTEPS = NCHUNK / 2;                  // MMAs per tap (K = 16 / 32)
-    static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 4096 /*barriers, bias, scales, head*/;
+    static constexpr bool FIRST = KIND == KIND_FIRST;
+    static constexpr bool HEAD4 = KIND == KIND_HEAD4;
+    static constexpr bool MMA8 = FP8 && !FIRST && !HEAD4;      // e4m3 operands (kind::f8f6f4)
+    static constexpr int NCHUNK = FIRST ? 2 : (MMA8 ? 4 : 8);  // 16-byte chunks per staged pixel
+    static constexpr int NCOPY = FIRST ? 1 : NCHUNK;           // chunks staged from HBM (layer 1: chunk 1 is zero)
+    static constexpr int NOUT = HEAD4 ? 16 : 64;               // output columns per dy block (= TMEM block stride)
+    static constexpr int NHL = HEAD4 ? 2 : 1;                  // weight parts (bf16 hi, lo)
+    static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;
+    static constexpr int W_PART = 3 * NCHUNK * 3 * NOUT * 16;  // [dx][chunk][3 dy][NOUT n][16 B]
+    static constexpr int W_BYTES = NHL * W_PART;
+    static constexpr int KSTEPS = NCHUNK / 2;                  // MMAs per dx (K = 16 / 32 per MMA)
+    static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 4096 /*barriers*/;
 };
 
 // ---------------------------------------------------------------------------
@@ -216,6 +231,11 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
     return (lo & 0xFFFFu) | (hi << 16);
 }
 __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo)
+{
+    hi = bf16_round(v);
+    lo = bf16_round(v - hi);
+}
 
 // Stores 64 channel values of one pixel into the chunk-planar layout.
 // out_fp8: e4m3(bf16(v) * inv_scale) (16 channels per chunk), else bf16 (8 per chunk).
@@ -251,31 +271,6 @@ __device__ __forceinline__ void store_pixel(const float *v, void *out, int out_f
     }
 }
 
-// Stores channels 32*half .. 32*half+31 of one pixel (chunk-planar layout).
-__device__ __forceinline__ void store_channels32(const float *v, int half, void *out, int out_fp8, float inv_scale,
-                                                 int H, int W, int y, int x)
-{
-    uint8_t *o = (uint8_t *)out;
-    if (out_fp8) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            float q[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) q[i] = bf16_round(v[16 * c + i]) * inv_scale;
-            const uint4 u = make_uint4(pack_e4m3x4(q[0], q[1], q[2], q[3]), pack_e4m3x4(q[4], q[5], q[6], q[7]),
-                                       pack_e4m3x4(q[8], q[9], q[10], q[11]), pack_e4m3x4(q[12], q[13], q[14], q[15]));
-            *reinterpret_cast<uint4 *>(o + (((size_t)(2 * half + c) * H + y) * W + x) * 16) = u;
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const uint4 u = make_uint4(pack_bf16x2(v[8 * c + 0], v[8 * c + 1]), pack_bf16x2(v[8 * c + 2], v[8 * c + 3]),
-                                       pack_bf16x2(v[8 * c + 4], v[8 * c + 5]), pack_bf16x2(v[8 * c + 6], v[8 * c + 7]));
-            *reinterpret_cast<uint4 *>(o + (((size_t)(4 * half + c) * H + y) * W + x) * 16) = u;
-        }
-    }
-}
-
 // One image of a batched call.  Every kernel of the tensor-core form walks a
 // flattened index space (conv units, layer-1 tiles, head tiles) over all images
 // of the call and finds its image through the *_begin prefix sums.
@@ -288,8 +283,8 @@ struct ImgDesc {
     uint32_t image;           // Philox image index (position in the call)
     int xtiles;               // ceil(W / 128)
     int unit_begin;           // first conv unit (xtiles * ceil(H / RU) units per image)
-    int f1_begin;             // first layer-1 tile (xtiles * ceil(H / F1_ROWS))
     int hd_begin;             // first head tile (ceil(W / 32) * ceil(H / 8))
+    int pre_begin;            // first layer-1 input group of 4 pixels (ceil(H * W / 4))
 };
 
 // largest i with begin(i) <= u (images sorted by their begin offsets)
@@ -306,6 +301,7 @@ __device__ __forceinline__ int find_image(int n, int u, F begin)
 }
 
 struct UnitInfo {
+    const ImgDesc *D;
     const uint8_t *in;
     uint8_t *out;
     int H, W, x0, y0, nrows;
@@ -324,6 +320,8 @@ struct ConvParams {
     float head_w[9 * 64];    // fused 1-logit head: last-layer weights [tap][channel]
     float out_inv_scale;     // FP8 output: 1 / scale of the next layer's input
     int out_fp8;
+    uint64_t seed;           // Philox seed (layer 1: noise channel; 4-logit head: level draw)
+    int mode;                // 4-logit head: HT_MODE_*
     int *err;
 };
 
@@ -335,6 +333,7 @@ __device__ __forceinline__ UnitInfo unit_info(const ConvParams &P, int u)
     const int lu = u - __ldg(&D->unit_begin);
     const int xt = __ldg(&D->xtiles);
     UnitInfo ui;
+    ui.D = D;
     ui.H = __ldg(&D->H);
     ui.W = __ldg(&D->W);
     ui.x0 = (lu % xt) * TILE_M;
@@ -361,10 +360,10 @@ __device__ __forceinline__ UnitInfo unit_info(const ConvParams &P, int u)
 // accumulator block is zeroed by the epilogue after it is drained, so all MMAs
 // accumulate.  Per output row: 12-15 MMAs of N = 192 instead of 36 of N = 64.
 // ---------------------------------------------------------------------------
-template <bool FP8, bool HEAD>
+template <bool FP8, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 {
-    using C = Cfg<FP8>;
+    using C = Cfg<FP8, KIND>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *s_w = smem;
@@ -406,6 +405,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         // tensor core's async proxy by a proxy fence before the barrier arrive.
         int last_issued[NSLOT];
         for (int i = 0; i < NSLOT; ++i) last_issued[i] = -1;
+        if constexpr (C::FIRST) {
+            for (int k = lane; k < NSLOT * ROW_PX; k += 32)
+                *reinterpret_cast<uint4 *>(s_rows + (k / ROW_PX) * C::SLOT_BYTES + (ROW_PX + k % ROW_PX) * 16) =
+                    make_uint4(0, 0, 0, 0);
+        }
         if (lane == 0) {
             mbar_arrive_expect_tx(smem_u32(wbar), C::W_BYTES);
             bulk_g2s(smem_u32(s_w), P.wpack, C::W_BYTES, smem_u32(wbar));
@@ -430,12 +434,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 const bool row_in = (yy >= 0 && yy < ui.H);
                 bool zeroed = false;
                 if (!row_in) {
-                    for (int k = lane; k < C::NCHUNK * ROW_PX; k += 32)
+                    for (int k = lane; k < C::NCOPY * ROW_PX; k += 32)
                         *reinterpret_cast<uint4 *>(dst + (size_t)k * 16) = make_uint4(0, 0, 0, 0);
                     zeroed = true;
                 } else if (lo > x0 - 1 || hi < x0 - 1 + ROW_PX) {
                     const int nl = lo - (x0 - 1), nr = (x0 - 1 + ROW_PX) - hi;
-                    for (int k = lane; k < C::NCHUNK * (nl + nr); k += 32) {
+                    for (int k = lane; k < C::NCOPY * (nl + nr); k += 32) {
                         const int c = k / (nl + nr), j = k % (nl + nr);
                         const int px = j < nl ? j : (hi - (x0 - 1)) + (j - nl);
                         *reinterpret_cast<uint4 *>(dst + ((size_t)c * ROW_PX + px) * 16) = make_uint4(0, 0, 0, 0);
@@ -447,8 +451,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 if (lane == 0) {
                     const uint32_t run = (uint32_t)(hi - lo) * 16u;
                     if (row_in && hi > lo) {
-                        mbar_arrive_expect_tx(smem_u32(&full[slot]), run * C::NCHUNK);
-                        for (int c = 0; c < C::NCHUNK; ++c)
+                        mbar_arrive_expect_tx(smem_u32(&full[slot]), run * C::NCOPY);
+                        for (int c = 0; c < C::NCOPY; ++c)
                             bulk_g2s(smem_u32(dst + ((size_t)c * ROW_PX + (lo - (x0 - 1))) * 16),
                                      ui.in + (((size_t)c * ui.H + yy) * ui.W + lo) * 16, run, smem_u32(&full[slot]));
                     } else {
@@ -472,7 +476,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         // Descriptors = base descriptor + compile-time / small offsets added to
         // the 14-bit start-address field (addresses stay below 256 KB).
         const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
-        const uint64_t b_base = sdesc(smem_u32(s_w), 3 * 1024, 128);
+        const uint64_t b_base = sdesc(smem_u32(s_w), 3 * C::NOUT * 16, 128);
         auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
             int got = 0;
             if (lane == 0) got = mbar_wait(bar, par, s_abort, P.err) ? 1 : 0;
@@ -489,18 +493,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 tc_fence_after();
                 if (lane == 0) {
                     const int jlo = max(0, k - 2), jhi = min(nrows - 1, k);
-                    const uint32_t n = (uint32_t)(jhi - jlo + 1) * 64u;
-                    const uint32_t idesc = idesc_m128<FP8>(n);
+                    const uint32_t n = (uint32_t)(jhi - jlo + 1) * C::NOUT;
+                    const uint32_t idesc = idesc_m128<C::MMA8>(n);
                     const uint32_t sb = (uint32_t)(2 - k + jlo);                       // first stacked dy block
-                    const uint32_t d = tmem_base + (uint32_t)jlo * 64u;
+                    const uint32_t d = tmem_base + (uint32_t)jlo * C::NOUT;
                     const uint64_t a_q = a_base + (uint64_t)(((q % NSLOT) * (uint32_t)C::SLOT_BYTES) >> 4);
-                    const uint64_t b_q = b_base + (uint64_t)((sb * 1024u) >> 4);
+                    const uint64_t b_q = b_base + (uint64_t)((sb * C::NOUT * 16u) >> 4);
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                         for (int ks = 0; ks < C::KSTEPS; ++ks)
-                            mma_ss<FP8>(d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
-                                        b_q + (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * 1024) >> 4), idesc, 1u);
+#pragma unroll
+                            for (int hl = 0; hl < C::NHL; ++hl)
+                                mma_ss<C::MMA8>(
+                                    d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
+                                    b_q + (uint64_t)((hl * C::W_PART + ((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4),
+                                    idesc, 1u);
                     mma_commit(smem_u32(&empty[q % NSLOT]));
                     if (k >= 2) mma_commit(smem_u32(&bfull[k - 2]));     // output row k-2 complete
                 }
@@ -527,7 +535,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         // accumulators start at zero (TMEM is undefined after allocation)
         for (int j = grp; j < RU; j += 2)
-            for (int c = 0; c < 64; c += 16) tmem_zero16(lane_base + j * 64 + c);
+            for (int c = 0; c < C::NOUT; c += 16) tmem_zero16(lane_base + j * C::NOUT + c);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
@@ -548,6 +556,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     break;
                 }
                 tc_fence_after();
+                if constexpr (C::HEAD4) {
+                    // 4-logit head: softmax, level draw, 2-bit packing (whole warp, 32 pixels)
+                    float v[16];
+                    if (j < nrows) {
+                        const uint32_t taddr = lane_base + j * C::NOUT;
+                        tmem_ld16(taddr, v);
+                        tmem_wait_ld();
+                        tmem_zero16(taddr);
+                        tmem_wait_st();
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&bfree[j]));
+                    if (j < nrows) {
+                        float z[4];
+#pragma unroll
+                        for (int k2 = 0; k2 < 4; ++k2) z[k2] = v[k2] + P.bias[k2];
+                        const ImgDesc *D = ui.D;
+                        ht_head_emit(z, 4, HT_HEAD_SOFTMAX, P.mode, P.seed, D->image, ui.x0 + quarter * 32, y0 + j,
+                                     ui.H, ui.W, D->bits, D->words, D->prob);
+                    }
+                    continue;
+                }
                 float v[64];
                 if (j < nrows) {
                     const uint32_t taddr = lane_base + j * 64u;
@@ -565,7 +596,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 if (j < nrows && x < ui.W) {
 #pragma unroll
                     for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], P.scale[n], P.bias[n]), 0.f);
-                    if constexpr (HEAD) {
+                    if constexpr (KIND == KIND_HEADPART) {
                         // fused 64 -> 1 head: per-tap dot products of the bf16-rounded activations
                         const size_t plane = (size_t)ui.H * ui.W, o = (size_t)(y0 + j) * ui.W + x;
                         float *partials = (float *)ui.out;
@@ -597,246 +628,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 }
 
 // ---------------------------------------------------------------------------
-// Layer 1 (2 -> 64) on tcgen05.  K would be 9 taps x 2 channels = 18, too thin
-// and too precise for one bf16 product, so every input v and weight w is split
-// into bf16 hi + lo parts and each product is taken as v_hi w_hi + v_hi w_lo +
-// v_lo w_hi (the dropped v_lo w_lo term is ~2^-16 relative): K = 9 x 6 = 54,
-// padded to 64.  One CTA = 128 pixels x F1_ROWS rows; per row the threads build
-// the A tile (im2col of c and z in the canonical no-swizzle layout), one thread
-// issues 4 MMAs (M = 128, N = 64, K = 16) into TMEM, and the epilogue applies
-// bias and ReLU and stores the chunk-planar activations.  Several CTAs share
-// an SM, so one CTA's MMA overlaps another's A build and stores.
+// Layer-1 input: per pixel (c_hi, c_hi, c_lo, z_hi, z_hi, z_lo, 0, 0) as bf16,
+// 16 bytes, pixel-major (one chunk of the chunk-planar layout) into act[1].
+// z comes from Philox4x32-10 with one call per aligned group of 4 indices g.
+// The (hi, hi, lo) pattern pairs with the weights' (w_hi, w_lo, w_hi), so one
+// bf16 MMA forms v_hi w_hi + v_hi w_lo + v_lo w_hi (~2^-16 relative error).
 // ---------------------------------------------------------------------------
-constexpr int F1_ROWS = 16;
-constexpr int F1_SMEM = 1024 + 2 * 8 * 128 * 16 + 8 * 64 * 16 + 2 * (F1_ROWS + 2) * (TILE_M + 2) * 4 + 64 * 4 + 64;
-
-__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo)
+__global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__ imgs, int n_imgs, uint64_t seed)
 {
-    hi = bf16_round(v);
-    lo = bf16_round(v - hi);
-}
-
-// A row of one pixel: per tap (c_hi, c_hi, c_lo, z_hi, z_hi, z_lo), then zeros,
-// stored as 8 chunks of 8 bf16 in the canonical no-swizzle layout.  Two threads
-// per pixel: half 0 writes chunks 0-3 (taps 0-4 and the first word of tap 5),
-// half 1 chunks 4-7.
-__device__ __forceinline__ void build_first_a(uint8_t *s_a, const float (*s_c)[TILE_M + 2],
-                                              const float (*s_z)[TILE_M + 2], int r, int px, int half)
-{
-    uint32_t w[32];
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;      // global 4-group index
+    const int im = find_image(n_imgs, gi, [&](int i) { return __ldg(&imgs[i].pre_begin); });
+    const ImgDesc *D = imgs + im;
+    const int H = D->H, W = D->W;
+    const uint64_t npx = (uint64_t)H * W;
+    const uint64_t g0 = (uint64_t)(gi - D->pre_begin) * 4;
+    if (g0 >= npx) return;
+    const uint4 r = ht_philox4x32_10(make_uint4((uint32_t)(g0 >> 2), D->image, 0u, 0u),
+                                     make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const uint32_t lanes[4] = {r.x, r.y, r.z, r.w};
+    float cv[4];
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        if (half == 0 ? tap > 5 : tap < 5) continue;
+    for (int l = 0; l < 4; ++l) {
+        const uint64_t g = g0 + l;
+        cv[l] = g < npx ? __ldg(D->contone + (size_t)(g / W) * D->cpitch + (g % W)) : 0.f;
+    }
+    uint4 *out = reinterpret_cast<uint4 *>(D->act[1]);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const uint64_t g = g0 + l;
+        if (g >= npx) break;
+        const float z = (float)(lanes[l] >> 8) * (1.0f / 16777216.0f);
         float ch, cl, zh, zl;
-        split_bf16(s_c[r + tap / 3][px + tap % 3], ch, cl);
-        split_bf16(s_z[r + tap / 3][px + tap % 3], zh, zl);
-        w[3 * tap + 0] = pack_bf16x2(ch, ch);
-        w[3 * tap + 1] = pack_bf16x2(cl, zh);
-        w[3 * tap + 2] = pack_bf16x2(zh, zl);
-    }
-#pragma unroll
-    for (int k = 27; k < 32; ++k) w[k] = 0u;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        if ((c >> 2) != half) continue;
-        *reinterpret_cast<uint4 *>(s_a + ((size_t)c * 128 + px) * 16) =
-            make_uint4(w[4 * c + 0], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+        split_bf16(cv[l], ch, cl);
+        split_bf16(z, zh, zl);
+        out[g] = make_uint4(pack_bf16x2(ch, ch), pack_bf16x2(cl, zh), pack_bf16x2(zh, zl), 0u);
     }
 }
 
-__global__ void __launch_bounds__(256) k_first_mma(const ImgDesc *__restrict__ imgs, int n_imgs, uint64_t seed,
-                                                   const uint8_t *__restrict__ w1pack, const float *__restrict__ b1,
-                                                   int out_fp8, float out_inv_scale, int *err)
-{
-    const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].f1_begin); });
-    const ImgDesc *D = imgs + im;
-    const int lt = (int)blockIdx.x - D->f1_begin;
-    const float *__restrict__ contone = D->contone;
-    const int cpitch = D->cpitch, H = D->H, W = D->W;
-    const uint32_t image = D->image;
-    void *out = D->act[0];
-    extern __shared__ uint8_t f1_raw[];
-    uint8_t *base = (uint8_t *)(((uintptr_t)f1_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *s_a = base;                                        // 2 x [8 chunks][128 px][16 B]
-    uint8_t *s_b = s_a + 2 * 8 * 128 * 16;                      // [8 chunks][64 n][16 B]
-    float (*s_c)[TILE_M + 2] = (float (*)[TILE_M + 2])(s_b + 8 * 64 * 16);
-    float (*s_z)[TILE_M + 2] = s_c + (F1_ROWS + 2);
-    float *s_bias = (float *)(s_z + (F1_ROWS + 2));
-    uint64_t *s_bar = (uint64_t *)(s_bias + 64);                // 2
-    uint32_t *s_tmem = (uint32_t *)(s_bar + 2);
-    volatile int *s_abort = (volatile int *)(s_tmem + 1);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = (lt % D->xtiles) * TILE_M, y0 = (lt / D->xtiles) * F1_ROWS;
-    const int nrows = min(F1_ROWS, H - y0);
-
-    for (int i = tid; i < (F1_ROWS + 2) * (TILE_M + 2); i += 256) {
-        const int yy = i / (TILE_M + 2), xx = i % (TILE_M + 2);
-        const int gy = y0 + yy - 1, gx = x0 + xx - 1;
-        float c = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) c = contone[(size_t)gy * cpitch + gx];
-        s_c[yy][xx] = c;
-        s_z[yy][xx] = 0.f;
-    }
-    __syncthreads();
-    // noise channel: one Philox4x32-10 call per aligned group of 4 pixel indices g
-    {
-        constexpr int GPR = (TILE_M + 2 + 3) / 4 + 1;          // groups touching one staged row
-        const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-        for (int i = tid; i < (F1_ROWS + 2) * GPR; i += 256) {
-            const int yy = i / GPR, k = i % GPR;
-            const int gy = y0 + yy - 1;
-            if (gy < 0 || gy >= H) continue;
-            const int gxa = max(x0 - 1, 0), gxb = min(x0 - 1 + TILE_M + 2, W);   // in-image staged columns
-            const uint64_t g0 = (uint64_t)gy * W + gxa, g1 = (uint64_t)gy * W + gxb;
-            const uint64_t gq = (g0 >> 2) + (uint64_t)k;                         // counter of this group
-            if ((gq << 2) >= g1) continue;
-            const uint4 r = ht_philox4x32_10(make_uint4((uint32_t)gq, image, 0u, 0u), key);
-            const uint32_t lanes[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const uint64_t g = (gq << 2) + l;
-                if (g < g0 || g >= g1) continue;
-                const int gx = (int)(g - (uint64_t)gy * W);
-                s_z[yy][gx - (x0 - 1)] = (float)(lanes[l] >> 8) * (1.0f / 16777216.0f);
-            }
-        }
-    }
-    for (int i = tid; i < 8 * 64; i += 256)
-        reinterpret_cast<uint4 *>(s_b)[i] = reinterpret_cast<const uint4 *>(w1pack)[i];
-    if (tid < 64) s_bias[tid] = b1[tid];
-    if (tid == 0) {
-        mbar_init(smem_u32(&s_bar[0]), 1);
-        mbar_init(smem_u32(&s_bar[1]), 1);
-        *s_abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) tmem_alloc(smem_u32(s_tmem), 128);
-    __syncthreads();
-    build_first_a(s_a, s_c, s_z, 0, tid & 127, tid >> 7);       // row 0 into buffer 0
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *s_tmem;
-    const uint64_t a_desc = sdesc(smem_u32(s_a), 128 * 16, 128);
-    const uint64_t b_desc = sdesc(smem_u32(s_b), 64 * 16, 128);
-    constexpr uint32_t idesc = idesc_m128<false>(64);
-    auto issue = [&](int r) {      // 4 MMAs of row r (A buffer r&1) into accumulator r&1
-        const uint32_t buf = (uint32_t)r & 1u;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks)
-            mma_ss<false>(tmem + buf * 64u,
-                          a_desc + (uint64_t)(((buf * 8 * 128 * 16) + 2 * ks * 128 * 16) >> 4),
-                          b_desc + (uint64_t)((2 * ks * 64 * 16) >> 4), idesc, ks > 0);
-        mma_commit(smem_u32(&s_bar[buf]));
-    };
-    if (tid == 0) issue(0);
-
-    bool ok = true;
-    int issued = 1;
-    for (int r = 0; r < nrows && ok; ++r) {
-        if (r + 1 < nrows) {
-            // row r+1 into the other buffer; its previous reader (row r-1) completed
-            build_first_a(s_a + ((r + 1) & 1) * (8 * 128 * 16), s_c, s_z, r + 1, tid & 127, tid >> 7);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
-            if (tid == 0) issue(r + 1);
-            ++issued;
-        }
-        ok = mbar_wait(smem_u32(&s_bar[r & 1]), ((uint32_t)r >> 1) & 1u, s_abort, err);
-        ok = __syncthreads_and(ok) != 0;
-        if (!ok) break;
-        tc_fence_after();
-        // warps q and q+4 share TMEM lane quarter q; each takes 32 of the 64 channels
-        const int quarter = warp & 3, chalf = warp >> 2;
-        float v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r & 1) * 64u + chalf * 32u;
-        tmem_ld16(taddr + 0, v + 0);
-        tmem_ld16(taddr + 16, v + 16);
-        tmem_wait_ld();
-        tc_fence_before();
-        const int x = x0 + quarter * 32 + lane;
-        if (x < W) {
-#pragma unroll
-            for (int n = 0; n < 32; ++n) v[n] = fmaxf(v[n] + s_bias[chalf * 32 + n], 0.f);
-            store_channels32(v, chalf, out, out_fp8, out_inv_scale, H, W, y0 + r, x);
-        }
-        __syncthreads();       // accumulator r&1 drained before row r+2 reuses it
-    }
-    if (!ok && tid == 0) {
-        // drain the commits still in flight before TMEM is released
-        for (int k = 0; k < issued; ++k) mbar_wait(smem_u32(&s_bar[k & 1]), ((uint32_t)k >> 1) & 1u, s_abort, err, true);
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        tmem_dealloc(tmem, 128);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Last layer (64 -> K) + head on CUDA cores, reading bf16 chunk-planar input.
-// Tile 32 x 8 pixels; one warp per tile row (the bit-packing granule).
-// ---------------------------------------------------------------------------
-constexpr int HT_X = 32, HT_Y = 8;
-
-template <int K>
-__global__ void __launch_bounds__(HT_X *HT_Y) k_head_tc(const ImgDesc *__restrict__ imgs, int n_imgs, int buf,
-                                                        const float *__restrict__ wl, const float *__restrict__ bl,
-                                                        int head, int mode, uint64_t seed)
-{
-    extern __shared__ uint4 s_dyn[];
-    uint4 *s_a = s_dyn;                                               // [8][HT_Y+2][HT_X+2]
-    float *s_w = (float *)(s_a + 8 * (HT_Y + 2) * (HT_X + 2));       // [9][64][K]
-    const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].hd_begin); });
-    const ImgDesc *D = imgs + im;
-    const int lt = (int)blockIdx.x - D->hd_begin;
-    const int H = D->H, W = D->W, words = D->words;
-    const uint8_t *__restrict__ act = D->act[buf];
-    uint32_t *bits = D->bits;
-    float *prob = D->prob;
-    const uint32_t image = D->image;
-    const int hx = (W + HT_X - 1) / HT_X;
-    const int x0 = (lt % hx) * HT_X, y0 = (lt / hx) * HT_Y;
-    const int tid = threadIdx.y * HT_X + threadIdx.x;
-    for (int i = tid; i < 8 * (HT_Y + 2) * (HT_X + 2); i += HT_X * HT_Y) {
-        const int c = i / ((HT_Y + 2) * (HT_X + 2)), rem = i % ((HT_Y + 2) * (HT_X + 2));
-        const int yy = rem / (HT_X + 2), xx = rem % (HT_X + 2);
-        const int gy = y0 + yy - 1, gx = x0 + xx - 1;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-            v = *reinterpret_cast<const uint4 *>(act + (((size_t)c * H + gy) * W + gx) * 16);
-        s_a[i] = v;
-    }
-    for (int i = tid; i < 9 * 64 * K; i += HT_X * HT_Y) {
-        const int tap = i / (64 * K), rem = i % (64 * K), c = rem / K, k = rem % K;
-        s_w[i] = wl[((size_t)k * 64 + c) * 9 + tap];
-    }
-    __syncthreads();
-    float z[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < K; ++k) z[k] = bl[k];
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-        const int yy = threadIdx.y + tap / 3, xx = threadIdx.x + tap % 3;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const uint4 q = s_a[(c * (HT_Y + 2) + yy) * (HT_X + 2) + xx];
-            const uint32_t wds[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float lo = __uint_as_float(wds[j] << 16), hi = __uint_as_float(wds[j] & 0xFFFF0000u);
-                const float *wp = s_w + (tap * 64 + c * 8 + 2 * j) * K;
-#pragma unroll
-                for (int k = 0; k < K; ++k) z[k] = fmaf(lo, wp[k], fmaf(hi, wp[K + k], z[k]));
-            }
-        }
-    }
-    ht_head_emit(z, K, head, mode, seed, image, x0, y0 + threadIdx.y, H, W, bits, words, prob);
-}
+constexpr int HT_X = 32, HT_Y = 8;   // head tile: one warp per tile row (the bit-packing granule)
 
 // ---------------------------------------------------------------------------
 // 1-logit head from the per-tap partials written by the last conv layer:
@@ -879,18 +708,19 @@ int num_sms()
     return n;
 }
 
-template <bool FP8, bool HEAD>
+template <bool FP8, int KIND>
 ht_status launch_conv(const ConvParams &P, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        HT_CUDA_TRY(
-            cudaFuncSetAttribute(k_conv_tc<FP8, HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FP8>::SMEM));
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<FP8, KIND>::SMEM));
         attr_set = true;
     }
     const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
-    ht_prof_start(FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
-    k_conv_tc<FP8, HEAD><<<grid, NTHREADS, Cfg<FP8>::SMEM, s>>>(P);
+    ht_prof_start(KIND == KIND_FIRST ? HTK_FIRST_TC : KIND == KIND_HEAD4 ? HTK_HEAD_TC
+                                                  : FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
+    k_conv_tc<FP8, KIND><<<grid, NTHREADS, Cfg<FP8, KIND>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -987,15 +817,17 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
         }
     }
     {
-        // layer 1: [kchunk 8][n 64][8 bf16], k = 6 tap + j with (w_hi(c), w_lo(c), w_hi(c), w_hi(z), w_lo(z), w_hi(z))
+        // layer 1: B = [dx][chunk 2][3 dy][64 n][8 bf16]; per tap k = 0..5 holds
+        // (w_hi(c), w_lo(c), w_hi(c), w_hi(z), w_lo(z), w_hi(z)), k = 6..15 zero
         float w0[64 * 2 * 9];
         e = cudaMemcpyAsync(w0, p->d_w + p->w_off[0], sizeof(w0), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        uint16_t pk[8 * 64 * 8];
+        uint16_t pk[3 * 2 * 3 * 64 * 8];
         memset(pk, 0, sizeof(pk));
         for (int n = 0; n < 64; ++n)
             for (int tap = 0; tap < 9; ++tap)
                 for (int ci = 0; ci < 2; ++ci) {
+                    const int dy = tap / 3, dx = tap % 3;
                     const float w = w0[(n * 2 + ci) * 9 + tap];
                     const uint16_t hi = f32_to_bf16_rne(w);
                     uint32_t hb32 = (uint32_t)hi << 16;
@@ -1004,8 +836,8 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
                     const uint16_t lo = f32_to_bf16_rne(w - hf);
                     const uint16_t trip[3] = {hi, lo, hi};
                     for (int j = 0; j < 3; ++j) {
-                        const int k = 6 * tap + 3 * ci + j;
-                        pk[((k / 8) * 64 + n) * 8 + (k % 8)] = trip[j];
+                        const int k = 3 * ci + j;            // chunk 0 only
+                        pk[(((dx * 2 + 0) * 3 + (2 - dy)) * 64 + n) * 8 + k] = trip[j];
                     }
                 }
         if (e == cudaSuccess && !p->d_w1pack) e = cudaMalloc(&p->d_w1pack, sizeof(pk));
@@ -1036,6 +868,35 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
         p->head_bias = p->h_b[p->b_off[p->L - 1]];
     }
     if (fp8) memcpy(p->h_wscale, hs, sizeof(float) * 64 * n_inner);
+    if (p->K == 4) {
+        float wl[4 * 64 * 9];
+        e = cudaMemcpyAsync(wl, p->d_w + p->w_off[p->L - 1], sizeof(wl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        const size_t part = (size_t)3 * 8 * 3 * 16 * 8;          // bf16 elements per weight part
+        std::vector<uint16_t> pk(2 * part, 0);
+        for (int n = 0; n < 4; ++n)
+            for (int c = 0; c < 64; ++c)
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+                    const float w = wl[(n * 64 + c) * 9 + tap];
+                    const uint16_t hi = f32_to_bf16_rne(w);
+                    uint32_t hb32 = (uint32_t)hi << 16;
+                    float hf;
+                    memcpy(&hf, &hb32, 4);
+                    const uint16_t lo = f32_to_bf16_rne(w - hf);
+                    const size_t off = ((((size_t)dx * 8 + c / 8) * 3 + (2 - dy)) * 16 + n) * 8 + (c % 8);
+                    pk[off] = hi;
+                    pk[part + off] = lo;
+                }
+        if (e == cudaSuccess && !p->d_wpack4) e = cudaMalloc(&p->d_wpack4, pk.size() * 2);
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_wpack4, pk.data(), pk.size() * 2, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free(hw);
+            free(hp);
+            free(hs);
+            HT_CUDA_TRY(e);
+        }
+    }
     e = cudaMemcpyAsync(p->d_wpack, hp, layer_bytes * n_inner, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && fp8) e = cudaMemcpyAsync(p->d_wscale, hs, sizeof(float) * 64 * n_inner, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1105,10 +966,6 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
     ImgDesc *d_table = (ImgDesc *)((uint8_t *)p->d_ws + (need - (size_t)n * sizeof(ImgDesc) - 512) / 256 * 256);
     static bool attr_done = false;
     if (!attr_done) {
-        HT_CUDA_TRY(cudaFuncSetAttribute(k_first_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, F1_SMEM));
-        HT_CUDA_TRY(cudaFuncSetAttribute(k_first_mma, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        const int hsmem = (int)(sizeof(uint4) * 8 * (HT_Y + 2) * (HT_X + 2) + sizeof(float) * 9 * 64 * 4);
-        HT_CUDA_TRY(cudaFuncSetAttribute(k_head_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, hsmem));
         attr_done = true;
     }
     int g0 = 0;
@@ -1117,7 +974,7 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
         int g1 = g0;
         size_t off = 0;
         std::vector<ImgDesc> tab;
-        int units = 0, f1 = 0, hd = 0;
+        int units = 0, hd = 0, pre = 0;
         while (g1 < n) {
             const size_t b = ht_tc_ws_bytes(p, imgs[g1].h, imgs[g1].w);
             if (g1 > g0 && off + img_ws_slot(p, imgs[g1]) > ws_budget()) break;
@@ -1135,25 +992,42 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
             D.image = (uint32_t)g1;
             D.xtiles = (D.W + TILE_M - 1) / TILE_M;
             D.unit_begin = units;
-            D.f1_begin = f1;
             D.hd_begin = hd;
+            D.pre_begin = pre;
             units += D.xtiles * ((D.H + RU - 1) / RU);
-            f1 += D.xtiles * ((D.H + F1_ROWS - 1) / F1_ROWS);
             hd += ((D.W + HT_X - 1) / HT_X) * ((D.H + HT_Y - 1) / HT_Y);
+            pre += (int)(((size_t)D.H * D.W + 3) / 4);
             tab.push_back(D);
             ++g1;
         }
         const int ng = g1 - g0;
         ImgDesc *dt = d_table + g0;
         HT_CUDA_TRY(cudaMemcpyAsync(dt, tab.data(), sizeof(ImgDesc) * ng, cudaMemcpyHostToDevice, s));
-        // layer 1 -> act[0]
+        // layer 1: input split into act[1], then the conv pipeline -> act[0]
         {
-            const bool o8 = fp8 && n_inner > 0;
             ht_prof_start(HTK_FIRST_TC, s);
-            k_first_mma<<<f1, 256, F1_SMEM, s>>>(dt, ng, seed, (const uint8_t *)p->d_w1pack, p->d_b + p->b_off[0],
-                                                  o8 ? 1 : 0, o8 ? 1.f / p->act_scale[1] : 1.f, err);
+            k_first_input<<<(pre + 255) / 256, 256, 0, s>>>(dt, ng, seed);
             ht_prof_stop(s);
             HT_LAUNCH_CHECK();
+        }
+        {
+            const bool o8 = fp8 && n_inner > 0;
+            ConvParams P;
+            P.imgs = dt;
+            P.n_imgs = ng;
+            P.n_units = units;
+            P.in_buf = 1;                          // reads the split input in act[1], writes act[0]
+            P.wpack = p->d_w1pack;
+            for (int c = 0; c < 64; ++c) {
+                P.bias[c] = p->h_b[p->b_off[0] + c];
+                P.scale[c] = 1.f;
+            }
+            P.out_inv_scale = o8 ? 1.f / p->act_scale[1] : 1.f;
+            P.out_fp8 = o8 ? 1 : 0;
+            P.seed = seed;
+            P.err = err;
+            const ht_status st = fp8 ? launch_conv<true, KIND_FIRST>(P, s) : launch_conv<false, KIND_FIRST>(P, s);
+            if (st != HT_OK) return st;
         }
         int cur = 0;
         for (int l = 1; l <= n_inner; ++l) {
@@ -1173,8 +1047,10 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
             P.out_inv_scale = out8 ? 1.f / p->act_scale[l + 1] : 1.f;
             P.out_fp8 = out8 ? 1 : 0;
             P.err = err;
-            const ht_status st = fp8 ? (fuse_head ? launch_conv<true, true>(P, s) : launch_conv<true, false>(P, s))
-                                     : (fuse_head ? launch_conv<false, true>(P, s) : launch_conv<false, false>(P, s));
+            P.seed = seed;
+            const ht_status st =
+                fp8 ? (fuse_head ? launch_conv<true, KIND_HEADPART>(P, s) : launch_conv<true, KIND_HIDDEN>(P, s))
+                    : (fuse_head ? launch_conv<false, KIND_HEADPART>(P, s) : launch_conv<false, KIND_HIDDEN>(P, s));
             if (st != HT_OK) return st;
             cur ^= 1;
         }
@@ -1183,13 +1059,28 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
             ht_prof_start(HTK_HEAD_TC, s);
             if (p->K == 1) {
                 k_head_partials<<<hd, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, cur, p->head_bias, mode, seed);
+                ht_prof_stop(s);
+                HT_LAUNCH_CHECK();
             } else {
-                const size_t hsmem = sizeof(uint4) * 8 * (HT_Y + 2) * (HT_X + 2) + sizeof(float) * 9 * 64 * 4;
-                k_head_tc<4><<<hd, dim3(HT_X, HT_Y), hsmem, s>>>(dt, ng, cur, p->d_w + p->w_off[p->L - 1],
-                                                                 p->d_b + p->b_off[p->L - 1], p->head, mode, seed);
+                ht_prof_stop(s);
+                ConvParams P;
+                P.imgs = dt;
+                P.n_imgs = ng;
+                P.n_units = units;
+                P.in_buf = cur;
+                P.wpack = p->d_wpack4;
+                for (int c = 0; c < 64; ++c) {
+                    P.bias[c] = c < 4 ? p->h_b[p->b_off[p->L - 1] + c] : 0.f;
+                    P.scale[c] = 1.f;
+                }
+                P.out_inv_scale = 1.f;
+                P.out_fp8 = 0;
+                P.seed = seed;
+                P.mode = mode;
+                P.err = err;
+                const ht_status st = launch_conv<false, KIND_HEAD4>(P, s);
+                if (st != HT_OK) return st;
             }
-            ht_prof_stop(s);
-            HT_LAUNCH_CHECK();
         }
         g0 = g1;
     }

@@ -60,16 +60,27 @@ __device__ void tile_moments(const float *__restrict__ c, int cpitch, const uint
     const int r = wn.r, span = RT + 2 * r;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const float cref = c[(size_t)min(vy0 + r, H - 1) * cpitch + min(vx0 + r, W - 1)];
-    for (int i = tid; i < span * span; i += 256) {
+    constexpr int MAXSPAN = RT + 2 * MAXR, NPER = (MAXSPAN * MAXSPAN + 255) / 256;
+    float hvs[NPER], cvs[NPER];
+#pragma unroll
+    for (int k = 0; k < NPER; ++k) {          // loads first (one memory latency), then the shared stores
+        const int i = tid + 256 * k;
         const int yy = i / span, xx = i % span;
         const int gy = vy0 + yy, gx = vx0 + xx;       // image coords of tile input
-        float hv = 0.f, cv = 0.f;
-        if (gy < H && gx < W) {
-            hv = hbit(bits, words, gy, gx);
-            cv = c[(size_t)gy * cpitch + gx] - cref;
+        hvs[k] = 0.f;
+        cvs[k] = 0.f;
+        if (i < span * span && gy < H && gx < W) {
+            hvs[k] = hbit(bits, words, gy, gx);
+            cvs[k] = __ldg(c + (size_t)gy * cpitch + gx) - cref;
         }
-        s_h[yy][xx] = hv;
-        s_c[yy][xx] = cv;
+    }
+#pragma unroll
+    for (int k = 0; k < NPER; ++k) {
+        const int i = tid + 256 * k;
+        if (i < span * span) {
+            s_h[i / span][i % span] = hvs[k];
+            s_c[i / span][i % span] = cvs[k];
+        }
     }
     __syncthreads();
     // row pass: s_row[q][yy][x] for yy in [0, span), x in [0, 32)
@@ -222,13 +233,22 @@ k_toggle_delta(const float *__restrict__ c, int cpitch, const uint32_t *__restri
     const int ay0 = blockIdx.y * DTY, ax0 = blockIdx.x * DTX;
     const int tid = threadIdx.y * DTX + threadIdx.x;
     // stage maps for output positions j in [a0 - r, a0 + tile + r) (image coords)
-    for (int i = tid; i < NMAP * SH * SW; i += DTX * DTY) {
+    constexpr int NT = NMAP * SH * SW, NPER = (NT + DTX * DTY - 1) / (DTX * DTY);
+    float vals[NPER];
+#pragma unroll
+    for (int k = 0; k < NPER; ++k) {          // loads first, then the shared stores
+        const int i = tid + k * DTX * DTY;
         const int q = i / (SH * SW), rem = i % (SH * SW);
         const int yy = rem / SW, xx = rem % SW;
         const int jy = ay0 - r + yy, jx = ax0 - r + xx;       // image coords of output j
-        float v = 0.f;
-        if (jy >= r && jy < H - r && jx >= r && jx < W - r) v = maps[q * plane + (size_t)(jy - r) * VW + (jx - r)];
-        s_m[q][yy][xx] = v;
+        vals[k] = 0.f;
+        if (i < NT && jy >= r && jy < H - r && jx >= r && jx < W - r)
+            vals[k] = __ldg(maps + q * plane + (size_t)(jy - r) * VW + (jx - r));
+    }
+#pragma unroll
+    for (int k = 0; k < NPER; ++k) {
+        const int i = tid + k * DTX * DTY;
+        if (i < NT) s_m[i / (SH * SW)][(i % (SH * SW)) / SW][i % SW] = vals[k];
     }
     __syncthreads();
     const int ay = ay0 + threadIdx.y, ax = ax0 + threadIdx.x;
