@@ -404,19 +404,29 @@ def fp32_alu_peak(clocks):
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def code_hash(path):
+    """sha256 of a C/CUDA source with comments and blank lines removed, so that a change of
+    comments alone keeps a committed counter capture valid."""
+    import hashlib
+    import re
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in txt.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()
+
+
 def conv_traffic(args, kname, px_per_step, launches_per_step):
     """DRAM bytes per launch of the conv kernel, from the committed ncu summary when its
     recorded source hash matches the current kernel source (else null)."""
-    import hashlib
+    import re
     src = os.path.join(ROOT, "paper_2304_12152_gb300", "csrc", "conv_tc.cu")
     summ = os.path.join(ROOT, "profiles", "k_conv_tc_bf16_2048.md")
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        h = code_hash(src)
         txt = open(summ).read()
     except OSError:
         return None
-    import re
-    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m = re.search(r"code_sha256:\s*([0-9a-f]{64})", txt)
     b = re.search(r"dram_bytes_per_px_per_layer:\s*([0-9.]+)", txt)
     if not m or not b or m.group(1) != h or kname != "k_conv_tc_bf16":
         return None

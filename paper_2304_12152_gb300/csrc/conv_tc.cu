@@ -1,37 +1,38 @@
 // conv_tc.cu -- tensor-core form of the policy forward on sm_103a.
 //
 // Policy (Sec. III "State"/"Agents", Sec. VI-A): 3x3 convolutions, zero
-// padding 1, ReLU between layers, sigmoid / softmax head.  Three kernels:
+// padding 1, ReLU between layers, sigmoid / softmax head.
 //
-//  k_first_tc  layer 1 (2 -> 64): too thin for the tensor pipe (K = 18); FP32
-//              CUDA-core FMAs, the noise channel z drawn in-kernel from Philox
-//              stream 0, ReLU, stored in the chunk-planar layout below.
-//  k_conv_tc   every 64 -> 64 layer: implicit GEMM on tcgen05.  One MMA tile is
-//              128 consecutive output pixels of one row (M = 128) x 64 output
-//              channels (N = 64); K runs over the 9 taps x 64 input channels.
-//              Input rows are staged by TMA into a ring of shared-memory slots
-//              (one image row of 130 pixels incl. the halo per slot); every tap
-//              is a *shifted descriptor* into the staged rows, so no im2col
-//              copy exists.  Weights stay resident in shared memory; the FP32
-//              accumulator lives in TMEM (two 64-column buffers so the
-//              epilogue of row i overlaps the MMAs of row i+1).  Epilogue:
-//              tcgen05.ld -> (dequant) + bias -> ReLU -> bf16 / e4m3 -> global.
-//  k_head_tc   last layer (64 -> K) + sigmoid/softmax + Philox sampling +
-//              bit packing (shared head epilogue).
+//  k_first_input  per pixel, c and the noise channel z (Philox stream 0) as a
+//                 bf16 hi/lo split, one 16-byte chunk.
+//  k_conv_tc      one pipeline, four kinds: layer 1 (2 -> 64, on the split
+//                 input), a hidden 64 -> 64 layer, the last hidden layer with
+//                 the 1-logit head's per-tap partials fused into its epilogue,
+//                 and the 64 -> 4 softmax head.  Implicit GEMM on tcgen05: an
+//                 MMA tile is 128 consecutive pixels of one input row (M = 128)
+//                 against the three kernel rows stacked along N; K runs over the
+//                 input channels, one shifted descriptor per dx.  Input rows are
+//                 staged by bulk async copies into a ring of shared-memory
+//                 slots; weights stay resident in shared memory; FP32
+//                 accumulators live in TMEM (one block per output row of a unit).
+//                 Epilogue: tcgen05.ld -> (dequant) + bias -> ReLU -> bf16 / e4m3
+//                 -> global (or head partials, or softmax + level draw + packing).
+//  k_head_partials  1-logit head: sum of the 9 partials + bias, sigmoid, Philox
+//                 stream 1 draw, bit packing.
 //
 // Activation layout in HBM ("chunk-planar"): [chunk][H][W][16 bytes], a chunk
-// being 8 bf16 channels (8 chunks) or 16 e4m3 channels (4 chunks).  A TMA box
-// {16 B, 130 px, 1 row, all chunks} lands in shared memory exactly in the
-// canonical no-swizzle K-major core-matrix layout that tcgen05 descriptors
-// read: pixels at a 16-byte stride (SBO = 128 B per 8-pixel core matrix),
-// chunks 130 * 16 B apart (LBO).  A one-pixel shift of the A operand is a
-// 16-byte shift of the descriptor start address.
+// being 8 bf16 channels (8 chunks) or 16 e4m3 channels (4 chunks).  One image
+// row of one chunk is contiguous, so a staged row is one bulk copy per chunk,
+// and it lands in shared memory in the canonical no-swizzle K-major layout
+// that tcgen05 descriptors read: pixels at a 16-byte stride (SBO = 128 B per
+// 8-pixel core matrix), chunks ROW_PX * 16 B apart (LBO).  A one-pixel shift of
+// the A operand is a 16-byte shift of the descriptor start address.
 //
-// Warp roles (192 threads, one persistent CTA per SM): warp 0 = TMA producer
-// (and TMEM owner), warp 1 = MMA issuer, warps 2-5 = epilogue (TMEM lane
-// quarters 2, 3, 0, 1).  Every mbarrier wait is bounded (globaltimer); on
-// expiry the kernel records HT_ERR_TIMEOUT, drains its own copies and MMAs,
-// frees TMEM and returns.
+// Warp roles (320 threads, one persistent CTA per SM): warp 0 = copy producer
+// (and TMEM owner), warp 1 = MMA issuer, warps 2-9 = epilogue (two per TMEM
+// lane quarter).  Every mbarrier wait is bounded (globaltimer); on expiry the
+// kernel records HT_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM
+// and returns.
 #include <stdlib.h>
 
 #include <vector>
