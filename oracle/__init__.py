@@ -82,8 +82,9 @@ def lib():
                                              C.c_void_p, C.c_void_p]
             L.or_backward.restype = C.c_int
             L.or_backward.argtypes = [fp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
-                                      C.POINTER(C.c_void_p), C.c_uint64, C.c_uint32, C.POINTER(C.c_void_p),
-                                      dp, dp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]
+                                      C.POINTER(C.c_void_p), C.c_uint64, C.c_uint32, C.c_int,
+                                      C.POINTER(C.c_void_p), dp, dp, C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p)]
             L.or_num_threads.restype = C.c_int
             L.or_set_num_threads.argtypes = [C.c_int]
             _lib = L
@@ -236,8 +237,10 @@ def anisotropy_loss(q: np.ndarray, mode: int = 0, n_rad: int = 32, n_ang: int = 
 
 
 def backward(contone: np.ndarray, weights, biases, noise_seed: int, image: int, acts, logits: np.ndarray,
-             dprob: np.ndarray):
-    """dL/dW, dL/db (double) for a sigmoid-head policy on a whole image."""
+             dprob: np.ndarray, quant: int = 0):
+    """dL/dW, dL/db (double) for a sigmoid-head policy on a whole image.  quant 1: the BF16
+    form's rounding points (inner layers' data gradients with bf16 weights, hidden-layer
+    pre-activation gradients rounded to bf16); pass acts and logits of the quant-1 forward."""
     c = np.ascontiguousarray(contone, dtype=np.float32)
     h, w = c.shape
     ws, bs, ch, wp, bp, chp = _layers(weights, biases)
@@ -249,7 +252,7 @@ def backward(contone: np.ndarray, weights, biases, noise_seed: int, image: int, 
     accp = (C.c_void_p * max(1, L - 1))(*[a.ctypes.data for a in acts]) if acts else None
     lg = np.ascontiguousarray(logits.reshape(h, w), dtype=np.float64)
     dp = np.ascontiguousarray(dprob.reshape(h, w), dtype=np.float64)
-    rc = lib().or_backward(c, h, w, w, L, chp, wp, noise_seed, image, accp, lg, dp, gwp, gbp)
+    rc = lib().or_backward(c, h, w, w, L, chp, wp, noise_seed, image, quant, accp, lg, dp, gwp, gbp)
     if rc != 0:
         raise ValueError("or_backward failed")
     return gw, gb

@@ -714,10 +714,15 @@ int or_anisotropy_loss(const double *q, int n, int mode, int n_rad, int n_ang,
 /* activations of or_forward(save_acts) and the exact logits, accumulate      */
 /* dL/dW (OIHW) and dL/db into gw/gb (double, caller zeroes them).            */
 /* ReLU derivative: 1 where the activation is > 0, else 0.                    */
+/* quant 1 (BF16 form, with acts from the quant-1 forward): the data          */
+/* gradient of an inner (64 -> 64) layer uses that layer's bf16-rounded        */
+/* weights, as its forward does, and every hidden layer's pre-activation       */
+/* gradient (after the ReLU mask) is rounded to bf16, the precision it is      */
+/* stored in between layers.  The head's and layer 1's weights stay exact.     */
 /* ------------------------------------------------------------------------- */
 int or_backward(const float *contone, int h, int w, int pitch,
                 int n_layers, const int *ch, const float *const *weights,
-                uint64_t noise_seed, uint32_t image,
+                uint64_t noise_seed, uint32_t image, int quant,
                 const double *const *acts, const double *logits, const double *dprob,
                 double **gw, double **gb)
 {
@@ -772,6 +777,7 @@ int or_backward(const float *contone, int h, int w, int pitch,
                 for (int ky = 0; ky < 3; ++ky)
                     for (int kx = 0; kx < 3; ++kx) {
                         double wv = (double)weights[l][(((size_t)o * ci + i) * 3 + ky) * 3 + kx];
+                        if (quant == 1 && l < L - 1) wv = or_round_bf16(wv);
                         for (int y = 0; y < h; ++y) {
                             int yy = y + ky - 1;
                             if (yy < 0 || yy >= h) continue;
@@ -782,8 +788,10 @@ int or_backward(const float *contone, int h, int w, int pitch,
                             }
                         }
                     }
-        for (size_t k = 0; k < (size_t)ci * npx; ++k)
+        for (size_t k = 0; k < (size_t)ci * npx; ++k) {
             if (!(acts[l - 1][k] > 0.0)) gin[k] = 0.0;
+            if (quant == 1) gin[k] = or_round_bf16(gin[k]);
+        }
         free(gout);
         gout = gin;
     }
