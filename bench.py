@@ -435,7 +435,8 @@ def conv_traffic(args, kname, px_per_step, launches_per_step):
 
 
 def run_train(args):
-    """Training step (Algorithm 1 TRAIN) timing: 16 crops 256x256 + 4 gray patches, S = 4."""
+    """Training step (Algorithm 1 TRAIN) timing: 16 crops 256x256 + 4 gray patches, S = 4,
+    BF16 tensor-core form (FP32 master weights), with the FP32 CUDA-core form beside it."""
     import torch
     from paper_2304_12152_gb300 import _native as N
     from paper_2304_12152_gb300 import api, synth
@@ -443,38 +444,48 @@ def run_train(args):
     torch.cuda.set_device(local)
     chs = synth.NET_WIDE
     ws, bs = synth.he_normal_policy(chs, 3)
-    pol = api.Policy(chs, ws, bs, precision=N.HT_FP32)
-    tr = api.Trainer(pol, (256, 256), max_crops=16, n_samples=4, n_gray=4, gray_n=256, las_mode=1, n_rad=32,
-                     n_ang=16, w_a=0.002)
     crops = [torch.from_numpy(synth.contone_image(256, 256, seed=3, index=i)).cuda() for i in range(16)]
     levels = [0.1, 0.25, 0.5, 0.75]
-    gw = torch.empty(pol.num_params() - sum(chs[1:]), device="cuda")
+    gw = torch.empty(sum(chs[i] * chs[i + 1] * 9 for i in range(len(chs) - 1)), device="cuda")
     gb = torch.empty(sum(chs[1:]), device="cuda")
-    for _ in range(args.warmup):
-        tr.forward(crops, levels, 1)
-        tr.backward(gw, gb)
-    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    api.profile_begin()
-    with Clocks(local) as clk:
-        e0.record(stream)
-        for k in range(args.steps):
-            losses = tr.forward(crops, levels, 1 + k)
+
+    def timed(prec, steps, warmup, profile):
+        pol = api.Policy(chs, ws, bs, precision=prec)
+        tr = api.Trainer(pol, (256, 256), max_crops=16, n_samples=4, n_gray=4, gray_n=256, las_mode=1, n_rad=32,
+                         n_ang=16, w_a=0.002)
+        for _ in range(warmup):
+            tr.forward(crops, levels, 1)
             tr.backward(gw, gb)
-        e1.record(stream)
         torch.cuda.synchronize()
-    prof = api.profile_end()
-    ms = e0.elapsed_time(e1) / args.steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if profile:
+            api.profile_begin()
+        with Clocks(local) as clk:
+            e0.record(stream)
+            for k in range(steps):
+                losses = tr.forward(crops, levels, 1 + k)
+                tr.backward(gw, gb)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        prof = api.profile_end() if profile else {}
+        return e0.elapsed_time(e1) / steps, losses, prof, clk.summary()
+
+    ms, losses, prof, clocks = timed(N.HT_BF16, args.steps, args.warmup, True)
+    fp32 = None
+    if args.fp32_steps > 0:
+        ms32, _, _, _ = timed(N.HT_FP32, args.fp32_steps, 1, False)
+        fp32 = {"value": ms32, "unit": "ms", "steps": args.fp32_steps}
     print(json.dumps({
         "metric": "training step time", "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "train: 16 crops 256x256 + 4 gray 256x256 {0.1,0.25,0.5,0.75}, S=4, "
-                               "2->64x7->1, w_s 0.06, w_a 0.002, 32x16-bin anisotropy loss"},
+                               "2->64x7->1, w_s 0.06, w_a 0.002, 32x16-bin anisotropy loss, FP32 master weights"},
         "losses": {"total": losses[0], "marl": losses[1], "las": losses[2], "mean_R": losses[3]},
+        "fp32_plain": fp32,
         "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
-        "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk.summary()}), flush=True)
+        "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clocks}), flush=True)
 
 
 if __name__ == "__main__":

@@ -208,6 +208,11 @@ typedef struct {
 
 typedef struct ht_train ht_train;
 
+/* Training workspace for policy p.  An FP32 policy trains in FP32 on CUDA cores;
+ * a BF16 policy (2 -> 64 x (L-1) -> 1, sigmoid head) trains on the tensor cores:
+ * bf16 weights, activations and hidden gradients, FP32 accumulation, FP32
+ * gradients of the FP32 master weights.  FP8 and softmax-head policies return
+ * HT_ERR_UNSUPPORTED. */
 ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out);
 ht_status ht_train_destroy(ht_train *t);
 
@@ -216,7 +221,8 @@ ht_status ht_train_destroy(ht_train *t);
  * toggle deltas per sample, L_MARL (Eq. marl, averaged over crops and samples)
  * and w_a * L_AS (averaged over patches).  Keeps what the backward needs.
  * losses_host (host, 4 doubles, written after the call synchronises `stream`):
- * L_total, L_MARL, L_AS, mean reward R. */
+ * L_total, L_MARL, L_AS, mean reward R.  n may be 0 when the trainer has gray
+ * patches: the step then optimises w_a * L_AS alone (L_MARL and R read 0). */
 ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const float *gray_levels,
                             uint64_t seed, double *losses_host, void *stream);
 

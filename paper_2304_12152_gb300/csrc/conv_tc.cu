@@ -37,20 +37,15 @@
 
 #include <vector>
 
-#include "head.cuh"
+#include "tc_common.cuh"
 
 namespace {
 
 #ifndef HT_CONV_NSLOT
 #define HT_CONV_NSLOT 6
 #endif
-constexpr int TILE_M = 128;                // output pixels per MMA tile (one row segment)
-constexpr int ROW_PX = TILE_M + 2;         // staged pixels per input row (halo of 1 each side)
-constexpr int RU = 8;                      // output rows per work unit = TMEM accumulator blocks (8 x 64 cols)
 constexpr int NSLOT = HT_CONV_NSLOT;       // input-row ring depth (lookahead of the copy engine)
-constexpr int TMEM_COLS = 512;
-constexpr int NTHREADS = 320;                // producer, MMA issuer, 8 epilogue warps
-constexpr unsigned long long kTimeoutNs = 2000000000ull;   // 2 s per wait
+constexpr int NTHREADS = 320;              // producer, MMA issuer, 8 epilogue warps
 
 // Kernel kinds built from one pipeline: a hidden 64 -> 64 layer, the last
 // hidden layer with the 1-logit head's per-tap partials fused into its
@@ -78,236 +73,6 @@ struct Cfg {
     static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 4096 /*barriers*/;
 };
 
-// ---------------------------------------------------------------------------
-// PTX helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t globaltimer_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait.  Returns false on timeout (which it records) or when another
-// role has already aborted (unless ignore_abort).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, bool ignore_abort = false)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 31u) == 0) {
-            if (!ignore_abort && *abort_flag) return false;
-            if (globaltimer_ns() - t0 > kTimeoutNs || it > (1u << 28)) {
-                *abort_flag = 1;
-                atomicExch(err, (int)HT_ERR_TIMEOUT);
-                return false;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// Shared-memory matrix descriptor: canonical K-major layout without swizzle.
-// start >> 4 in [0,14), LBO >> 4 in [16,30), SBO >> 4 in [32,46), version 1 at
-// bit 46, base offset 0, swizzle 0.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor: D = F32 (bit 4), A/B format at bits 7/10 (BF16 = 1
-// for kind::f16, E4M3 = 0 for kind::f8f6f4), both K-major, N >> 3 at bit 17,
-// M >> 4 at bit 24.
-template <bool FP8>
-__host__ __device__ constexpr uint32_t idesc_m128(uint32_t n)
-{
-    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
-}
-
-template <bool FP8>
-__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
-{
-    if constexpr (FP8) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    }
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_zero16(uint32_t taddr)
-{
-    const uint32_t z = 0u;
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
-        "%1};" ::"r"(taddr),
-        "r"(z)
-        : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
-{
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&h);
-}
-__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d)
-{
-    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-    return (lo & 0xFFFFu) | (hi << 16);
-}
-__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo)
-{
-    hi = bf16_round(v);
-    lo = bf16_round(v - hi);
-}
-
-// Stores 64 channel values of one pixel into the chunk-planar layout.
-// out_fp8: e4m3(bf16(v) * inv_scale) (16 channels per chunk), else bf16 (8 per chunk).
-__device__ __forceinline__ void store_pixel(const float *v, void *out, int out_fp8, float inv_scale, int H, int W,
-                                            int y, int x)
-{
-    if (out_fp8) {
-        uint8_t *o = (uint8_t *)out;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            uint4 q;
-            q.x = pack_e4m3x4(bf16_round(v[16 * c + 0]) * inv_scale, bf16_round(v[16 * c + 1]) * inv_scale,
-                              bf16_round(v[16 * c + 2]) * inv_scale, bf16_round(v[16 * c + 3]) * inv_scale);
-            q.y = pack_e4m3x4(bf16_round(v[16 * c + 4]) * inv_scale, bf16_round(v[16 * c + 5]) * inv_scale,
-                              bf16_round(v[16 * c + 6]) * inv_scale, bf16_round(v[16 * c + 7]) * inv_scale);
-            q.z = pack_e4m3x4(bf16_round(v[16 * c + 8]) * inv_scale, bf16_round(v[16 * c + 9]) * inv_scale,
-                              bf16_round(v[16 * c + 10]) * inv_scale, bf16_round(v[16 * c + 11]) * inv_scale);
-            q.w = pack_e4m3x4(bf16_round(v[16 * c + 12]) * inv_scale, bf16_round(v[16 * c + 13]) * inv_scale,
-                              bf16_round(v[16 * c + 14]) * inv_scale, bf16_round(v[16 * c + 15]) * inv_scale);
-            *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = q;
-        }
-    } else {
-        uint8_t *o = (uint8_t *)out;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            uint4 q;
-            q.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
-            q.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
-            q.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
-            q.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
-            *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = q;
-        }
-    }
-}
-
-// One image of a batched call.  Every kernel of the tensor-core form walks a
-// flattened index space (conv units, layer-1 tiles, head tiles) over all images
-// of the call and finds its image through the *_begin prefix sums.
-struct ImgDesc {
-    const float *contone;
-    uint8_t *act[2];          // ping-pong chunk-planar activation buffers
-    uint32_t *bits;
-    float *prob;              // nullable
-    int cpitch, H, W, words;
-    uint32_t image;           // Philox image index (position in the call)
-    int xtiles;               // ceil(W / 128)
-    int unit_begin;           // first conv unit (xtiles * ceil(H / RU) units per image)
-    int hd_begin;             // first head tile (ceil(W / 32) * ceil(H / 8))
-    int pre_begin;            // first layer-1 input group of 4 pixels (ceil(H * W / 4))
-};
-
-// largest i with begin(i) <= u (images sorted by their begin offsets)
-template <typename F>
-__device__ __forceinline__ int find_image(int n, int u, F begin)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (begin(mid) <= u) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-struct UnitInfo {
-    const ImgDesc *D;
-    const uint8_t *in;
-    uint8_t *out;
-    int H, W, x0, y0, nrows;
-};
-
 struct ConvParams {
     const ImgDesc *imgs;     // device table of the call's images
     int n_imgs, n_units;
@@ -323,27 +88,10 @@ struct ConvParams {
     int out_fp8;
     uint64_t seed;           // Philox seed (layer 1: noise channel; 4-logit head: level draw)
     int mode;                // 4-logit head: HT_MODE_*
+    int dgrad;               // 1: data-gradient layer (no bias, no ReLU; mask from the table, bf16 out)
     int *err;
 };
 
-template <int RUx>
-__device__ __forceinline__ UnitInfo unit_info(const ConvParams &P, int u)
-{
-    const int im = find_image(P.n_imgs, u, [&](int i) { return __ldg(&P.imgs[i].unit_begin); });
-    const ImgDesc *D = P.imgs + im;
-    const int lu = u - __ldg(&D->unit_begin);
-    const int xt = __ldg(&D->xtiles);
-    UnitInfo ui;
-    ui.D = D;
-    ui.H = __ldg(&D->H);
-    ui.W = __ldg(&D->W);
-    ui.x0 = (lu % xt) * TILE_M;
-    ui.y0 = (lu / xt) * RUx;
-    ui.nrows = min(ui.H, ui.y0 + RUx) - ui.y0;
-    ui.in = (const uint8_t *)D->act[P.in_buf];
-    ui.out = D->act[P.in_buf ^ 1];
-    return ui;
-}
 
 // ---------------------------------------------------------------------------
 // 64 -> 64 layer on tcgen05
@@ -418,7 +166,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         uint32_t li = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
-            const UnitInfo ui = unit_info<RU>(P, u);
+            const UnitInfo ui = unit_info(P.imgs, P.n_imgs, P.in_buf, u);
             const int y0 = ui.y0, y1 = ui.y0 + ui.nrows, x0 = ui.x0;
             const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, ui.W);   // in-image pixel range
             for (int r = 0; r < (y1 - y0) + 2; ++r, ++li) {
@@ -486,7 +234,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         bool ok = wait1(smem_u32(wbar), 0);
         uint32_t q = 0, uit = 0;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
-            const int nrows = unit_info<RU>(P, u).nrows;
+            const int nrows = unit_info(P.imgs, P.n_imgs, P.in_buf, u).nrows;
             for (int k = 0; k < nrows + 2 && ok; ++k, ++q) {
                 ok = wait1(smem_u32(&full[q % NSLOT]), (q / NSLOT) & 1u);
                 if (ok && k < nrows) ok = wait1(smem_u32(&bfree[k]), uit & 1u);   // block k enters use
@@ -545,7 +293,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         uint32_t uit = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
-            const UnitInfo ui = unit_info<RU>(P, u);
+            const UnitInfo ui = unit_info(P.imgs, P.n_imgs, P.in_buf, u);
             const int y0 = ui.y0, nrows = ui.nrows;
             const int x = ui.x0 + px;
             for (int j = grp; j < RU; j += 2) {
@@ -595,11 +343,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&bfree[j]));
                 if (j < nrows && x < ui.W) {
+                    const size_t o = (size_t)(y0 + j) * ui.W + x;
+                    if (P.dgrad) {
+                        // data gradient: mask by the ReLU of the layer this gradient flows into
+                        const uint2 m = __ldg(ui.D->mask + o);
+#pragma unroll
+                        for (int n = 0; n < 64; ++n)
+                            if (!(((n < 32 ? m.x : m.y) >> (n & 31)) & 1u)) v[n] = 0.f;
+                        store_pixel(v, ui.out, 0, 1.f, ui.H, ui.W, y0 + j, x);
+                        continue;
+                    }
 #pragma unroll
                     for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], P.scale[n], P.bias[n]), 0.f);
+                    if (ui.D->mask) {
+                        // training forward: which stored (bf16) activations are positive
+                        uint2 m = make_uint2(0u, 0u);
+#pragma unroll
+                        for (int n = 0; n < 32; ++n) {
+                            m.x |= (bf16_round(v[n]) > 0.f ? 1u : 0u) << n;
+                            m.y |= (bf16_round(v[n + 32]) > 0.f ? 1u : 0u) << n;
+                        }
+                        ui.D->mask[o] = m;
+                    }
                     if constexpr (KIND == KIND_HEADPART) {
                         // fused 64 -> 1 head: per-tap dot products of the bf16-rounded activations
-                        const size_t plane = (size_t)ui.H * ui.W, o = (size_t)(y0 + j) * ui.W + x;
+                        const size_t plane = (size_t)ui.H * ui.W;
                         float *partials = (float *)ui.out;
                         float acc[9];
 #pragma unroll
@@ -612,6 +380,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         }
 #pragma unroll
                         for (int t = 0; t < 9; ++t) partials[t * plane + o] = acc[t];
+                        if (ui.D->save) store_pixel(v, ui.D->save, 0, 1.f, ui.H, ui.W, y0 + j, x);
                     } else {
                         store_pixel(v, ui.out, P.out_fp8, P.out_inv_scale, ui.H, ui.W, y0 + j, x);
                     }
@@ -666,7 +435,6 @@ __global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__
     }
 }
 
-constexpr int HT_X = 32, HT_Y = 8;   // head tile: one warp per tile row (the bit-packing granule)
 
 // ---------------------------------------------------------------------------
 // 1-logit head from the per-tap partials written by the last conv layer:
@@ -697,18 +465,6 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__r
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-int num_sms()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
 template <bool FP8, int KIND>
 ht_status launch_conv(const ConvParams &P, cudaStream_t s)
 {
@@ -948,6 +704,53 @@ size_t ht_tc_batch_ws_bytes(const ht_policy *p, const ht_image *imgs, int n)
     return maxg + (size_t)n * sizeof(ImgDesc) + 1024;
 }
 
+ht_status ht_tc_conv(const ht_tc_layer &a, cudaStream_t s)
+{
+    int *err = ht_device_error_flag();
+    if (!err) return HT_ERR_CUDA;
+    ConvParams P{};
+    P.imgs = (const ImgDesc *)a.table;
+    P.n_imgs = a.n_imgs;
+    P.n_units = a.n_units;
+    P.in_buf = a.in_buf;
+    P.wpack = a.wpack;
+    for (int c = 0; c < 64; ++c) {
+        P.scale[c] = a.scale ? a.scale[c] : 1.f;
+        P.bias[c] = a.bias ? a.bias[c] : 0.f;
+    }
+    if (a.head_w) memcpy(P.head_w, a.head_w, sizeof(P.head_w));
+    P.out_inv_scale = 1.f;
+    P.out_fp8 = 0;
+    P.seed = a.seed;
+    P.dgrad = a.dgrad;
+    P.err = err;
+    switch (a.kind) {
+    case KIND_HIDDEN: return launch_conv<false, KIND_HIDDEN>(P, s);
+    case KIND_HEADPART: return launch_conv<false, KIND_HEADPART>(P, s);
+    case KIND_FIRST: return launch_conv<false, KIND_FIRST>(P, s);
+    default: ht_set_error("ht_tc_conv: bad kind %d", a.kind); return HT_ERR_INVALID_ARG;
+    }
+}
+
+ht_status ht_tc_first_input(const void *table, int n_imgs, int n_groups, uint64_t seed, cudaStream_t s)
+{
+    ht_prof_start(HTK_FIRST_TC, s);
+    k_first_input<<<(n_groups + 255) / 256, 256, 0, s>>>((const ImgDesc *)table, n_imgs, seed);
+    ht_prof_stop(s);
+    HT_LAUNCH_CHECK();
+    return HT_OK;
+}
+
+ht_status ht_tc_head_partials(const void *table, int n_imgs, int n_tiles, int buf, float bias, int mode,
+                              uint64_t seed, cudaStream_t s)
+{
+    ht_prof_start(HTK_HEAD_TC, s);
+    k_head_partials<<<n_tiles, dim3(HT_X, HT_Y), 0, s>>>((const ImgDesc *)table, n_imgs, buf, bias, mode, seed);
+    ht_prof_stop(s);
+    HT_LAUNCH_CHECK();
+    return HT_OK;
+}
+
 // All images of a call: grouped so that a group's activation buffers fit the
 // workspace budget; per group one launch of layer 1, one per 64 -> 64 layer and
 // one of the head, each over the whole group (persistent tile index space).
@@ -979,7 +782,7 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
         while (g1 < n) {
             const size_t b = ht_tc_ws_bytes(p, imgs[g1].h, imgs[g1].w);
             if (g1 > g0 && off + img_ws_slot(p, imgs[g1]) > ws_budget()) break;
-            ImgDesc D;
+            ImgDesc D{};
             D.contone = imgs[g1].contone;
             D.cpitch = imgs[g1].pitch;
             D.H = imgs[g1].h;
@@ -991,13 +794,7 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
             D.prob = prob ? prob[g1] : nullptr;
             D.words = ht_bits_row_words(D.W, p->head);
             D.image = (uint32_t)g1;
-            D.xtiles = (D.W + TILE_M - 1) / TILE_M;
-            D.unit_begin = units;
-            D.hd_begin = hd;
-            D.pre_begin = pre;
-            units += D.xtiles * ((D.H + RU - 1) / RU);
-            hd += ((D.W + HT_X - 1) / HT_X) * ((D.H + HT_Y - 1) / HT_Y);
-            pre += (int)(((size_t)D.H * D.W + 3) / 4);
+            set_begins(D, units, hd, pre);
             tab.push_back(D);
             ++g1;
         }
@@ -1013,7 +810,7 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
         }
         {
             const bool o8 = fp8 && n_inner > 0;
-            ConvParams P;
+            ConvParams P{};
             P.imgs = dt;
             P.n_imgs = ng;
             P.n_units = units;
@@ -1034,7 +831,7 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
         for (int l = 1; l <= n_inner; ++l) {
             const bool out8 = fp8 && (l < n_inner);
             const bool fuse_head = (l == n_inner) && p->K == 1;
-            ConvParams P;
+            ConvParams P{};
             P.imgs = dt;
             P.n_imgs = ng;
             P.n_units = units;
@@ -1064,7 +861,7 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
                 HT_LAUNCH_CHECK();
             } else {
                 ht_prof_stop(s);
-                ConvParams P;
+                ConvParams P{};
                 P.imgs = dt;
                 P.n_imgs = ng;
                 P.n_units = units;

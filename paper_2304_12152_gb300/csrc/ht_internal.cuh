@@ -7,6 +7,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <vector>
+
 #include "ht.h"
 
 // ---------------------------------------------------------------------------
@@ -129,6 +131,22 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
 size_t ht_tc_ws_bytes(const ht_policy *p, int h, int w);
 size_t ht_tc_batch_ws_bytes(const ht_policy *p, const ht_image *imgs, int n);
 
+// single launches of the BF16 conv pipeline over a caller-built image table (training form)
+struct ht_tc_layer {
+    const void *table;        // device ImgDesc table (tc_common.cuh)
+    int n_imgs, n_units, in_buf;
+    int kind;                 // 0 hidden 64 -> 64, 1 last hidden + 1-logit head partials, 2 layer 1
+    const void *wpack;        // packed bf16 weights ([dx][chunk][3 dy][64][16 B])
+    const float *scale, *bias;   // host, 64 each (nullable: 1 / 0)
+    const float *head_w;      // host [9][64] (kind 1)
+    int dgrad;                // data-gradient layer: no bias / ReLU, mask from the table
+    uint64_t seed;
+};
+ht_status ht_tc_conv(const ht_tc_layer &a, cudaStream_t s);
+ht_status ht_tc_first_input(const void *table, int n_imgs, int n_groups, uint64_t seed, cudaStream_t s);
+ht_status ht_tc_head_partials(const void *table, int n_imgs, int n_tiles, int buf, float bias, int mode,
+                              uint64_t seed, cudaStream_t s);
+
 // reward / toggle deltas
 ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
                            double *out, cudaStream_t s);
@@ -140,3 +158,26 @@ size_t ht_toggle_scratch_floats(int h, int w, int r);
 ht_status ht_las_launch(const float *q, int n_patches, int n, int mode, int n_rad, int n_ang, double *out_loss,
                         float *grad, void *scratch, size_t scratch_bytes, cudaStream_t s);
 size_t ht_las_scratch_bytes(int n_patches, int n, int n_rad, int n_ang);
+
+// BF16 tensor-core training form (train_tc.cu): 2 -> 64 x (L-1) -> 1 sigmoid policies
+struct ht_train_tc_ws {
+    void *arena = nullptr;            // per-image activations, masks, split input, head partials, gradients
+    std::vector<size_t> slot_off;     // per image slot (crops, then gray patches): byte offset into the arena
+    std::vector<size_t> img_off;      // per image of the step: byte offset into the arena
+    std::vector<size_t> prob_off;     // per image: offset into prob / dz
+    std::vector<size_t> bits_off;     // per image: word offset into hbits
+    float *prob = nullptr, *dz = nullptr;
+    uint32_t *hbits = nullptr;        // thresholded head output (unused by training, written by the head)
+    void *tables = nullptr;           // device image tables of the step
+    void *scratch = nullptr;          // reduction partials + packed data-gradient weights
+    size_t scratch_bytes = 0, wt_off = 0;
+    int units = 0, hd = 0;
+};
+bool ht_train_tc_supported(const ht_policy *p);
+size_t ht_train_tc_image_bytes(const ht_policy *p, size_t px);
+size_t ht_train_tc_table_bytes(const ht_policy *p, int n_img);
+void ht_train_tc_scratch_layout(const ht_policy *p, int n_tiles, size_t *wt_off, size_t *total);
+ht_status ht_train_tc_forward(ht_policy *p, ht_train_tc_ws &w, const ht_image *imgs, int nimg, uint64_t seed,
+                              cudaStream_t s);
+ht_status ht_train_tc_backward(ht_policy *p, ht_train_tc_ws &w, int nimg, uint64_t seed, float *grad_w,
+                               float *grad_b, cudaStream_t s);

@@ -1,0 +1,296 @@
+// tc_common.cuh -- pieces shared by the tcgen05 kernels (forward conv
+// pipeline, weight-gradient pipeline): inline-PTX wrappers for mbarriers, bulk
+// async copies, TMEM and tcgen05.mma; bf16 / e4m3 packing; the chunk-planar
+// activation store; the per-call image-descriptor table.
+#pragma once
+
+#include "head.cuh"
+
+namespace {
+
+constexpr int TILE_M = 128;                // pixels per MMA tile (one row segment)
+constexpr int ROW_PX = TILE_M + 2;         // staged pixels per input row (halo of 1 each side)
+constexpr int RU = 8;                      // output rows per work unit
+constexpr int TMEM_COLS = 512;
+constexpr int HT_X = 32, HT_Y = 8;         // head tile: one warp per tile row (the bit-packing granule)
+constexpr unsigned long long kTimeoutNs = 2000000000ull;   // 2 s per wait
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait.  Returns false on timeout (which it records) or when another
+// role has already aborted (unless ignore_abort).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, bool ignore_abort = false)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31u) == 0) {
+            if (!ignore_abort && *abort_flag) return false;
+            if (globaltimer_ns() - t0 > kTimeoutNs || it > (1u << 28)) {
+                *abort_flag = 1;
+                atomicExch(err, (int)HT_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: canonical K-major layout without swizzle.
+// start >> 4 in [0,14), LBO >> 4 in [16,30), SBO >> 4 in [32,46), version 1 at
+// bit 46, base offset 0, swizzle 0.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: D = F32 (bit 4), A/B format at bits 7/10 (BF16 = 1
+// for kind::f16, E4M3 = 0 for kind::f8f6f4), both K-major, N >> 3 at bit 17,
+// M >> 4 at bit 24.
+template <bool FP8>
+__host__ __device__ constexpr uint32_t idesc_m128(uint32_t n)
+{
+    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr)
+{
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d)
+{
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return (lo & 0xFFFFu) | (hi << 16);
+}
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo)
+{
+    hi = bf16_round(v);
+    lo = bf16_round(v - hi);
+}
+
+// Stores 64 channel values of one pixel into the chunk-planar layout.
+// out_fp8: e4m3(bf16(v) * inv_scale) (16 channels per chunk), else bf16 (8 per chunk).
+__device__ __forceinline__ void store_pixel(const float *v, void *out, int out_fp8, float inv_scale, int H, int W,
+                                            int y, int x)
+{
+    if (out_fp8) {
+        uint8_t *o = (uint8_t *)out;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint4 q;
+            q.x = pack_e4m3x4(bf16_round(v[16 * c + 0]) * inv_scale, bf16_round(v[16 * c + 1]) * inv_scale,
+                              bf16_round(v[16 * c + 2]) * inv_scale, bf16_round(v[16 * c + 3]) * inv_scale);
+            q.y = pack_e4m3x4(bf16_round(v[16 * c + 4]) * inv_scale, bf16_round(v[16 * c + 5]) * inv_scale,
+                              bf16_round(v[16 * c + 6]) * inv_scale, bf16_round(v[16 * c + 7]) * inv_scale);
+            q.z = pack_e4m3x4(bf16_round(v[16 * c + 8]) * inv_scale, bf16_round(v[16 * c + 9]) * inv_scale,
+                              bf16_round(v[16 * c + 10]) * inv_scale, bf16_round(v[16 * c + 11]) * inv_scale);
+            q.w = pack_e4m3x4(bf16_round(v[16 * c + 12]) * inv_scale, bf16_round(v[16 * c + 13]) * inv_scale,
+                              bf16_round(v[16 * c + 14]) * inv_scale, bf16_round(v[16 * c + 15]) * inv_scale);
+            *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = q;
+        }
+    } else {
+        uint8_t *o = (uint8_t *)out;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uint4 q;
+            q.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+            q.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+            q.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+            q.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+            *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = q;
+        }
+    }
+}
+
+// One image of a batched call.  Every kernel of the tensor-core form walks a
+// flattened index space (conv units, layer-1 tiles, head tiles) over all images
+// of the call and finds its image through the *_begin prefix sums.
+struct ImgDesc {
+    const float *contone;
+    uint8_t *act[2];          // chunk-planar activation buffers (input / output by in_buf)
+    uint32_t *bits;
+    float *prob;              // nullable
+    uint2 *mask;              // nullable: 64-bit ReLU mask per pixel of the layer's output
+                              // (written by a forward layer, applied by a data-gradient layer)
+    uint8_t *save;            // nullable: last hidden layer with fused head partials also
+                              // stores its activations here (training forward)
+    int cpitch, H, W, words;
+    uint32_t image;           // Philox image index (position in the call)
+    int xtiles;               // ceil(W / 128)
+    int unit_begin;           // first conv unit (xtiles * ceil(H / RU) units per image)
+    int hd_begin;             // first head tile (ceil(W / 32) * ceil(H / 8))
+    int pre_begin;            // first layer-1 input group of 4 pixels (ceil(H * W / 4))
+};
+
+// largest i with begin(i) <= u (images sorted by their begin offsets)
+template <typename F>
+__device__ __forceinline__ int find_image(int n, int u, F begin)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin(mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct UnitInfo {
+    const ImgDesc *D;
+    const uint8_t *in;
+    uint8_t *out;
+    int H, W, x0, y0, nrows;
+};
+
+// Unit u of a call: RU rows x one 128-pixel column tile of one image.
+__device__ __forceinline__ UnitInfo unit_info(const ImgDesc *imgs, int n_imgs, int in_buf, int u)
+{
+    const int im = find_image(n_imgs, u, [&](int i) { return __ldg(&imgs[i].unit_begin); });
+    const ImgDesc *D = imgs + im;
+    const int lu = u - __ldg(&D->unit_begin);
+    const int xt = __ldg(&D->xtiles);
+    UnitInfo ui;
+    ui.D = D;
+    ui.H = __ldg(&D->H);
+    ui.W = __ldg(&D->W);
+    ui.x0 = (lu % xt) * TILE_M;
+    ui.y0 = (lu / xt) * RU;
+    ui.nrows = min(ui.H, ui.y0 + RU) - ui.y0;
+    ui.in = (const uint8_t *)D->act[in_buf];
+    ui.out = D->act[in_buf ^ 1];
+    return ui;
+}
+
+// Work-index layout of one image inside a call's table: conv units, head tiles,
+// layer-1 input groups (prefix sums over the images in table order).
+inline void set_begins(ImgDesc &D, int &units, int &hd, int &pre)
+{
+    D.xtiles = (D.W + TILE_M - 1) / TILE_M;
+    D.unit_begin = units;
+    D.hd_begin = hd;
+    D.pre_begin = pre;
+    units += D.xtiles * ((D.H + RU - 1) / RU);
+    hd += ((D.W + HT_X - 1) / HT_X) * ((D.H + HT_Y - 1) / HT_Y);
+    pre += (int)(((size_t)D.H * D.W + 3) / 4);
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace

@@ -1,8 +1,13 @@
 // train.cu -- one iteration of Algorithm 1 (TRAIN step): forward and backward.
 //
+// Two forms.  A BF16 policy of the 2 -> 64 x (L-1) -> 1 shape runs the
+// tensor-core form of train_tc.cu (forward on the conv pipeline with saved
+// bf16 activations, tcgen05 weight gradients, data gradients on the pipeline);
+// an FP32 policy runs the plain form below on CUDA cores.  Steps 2-6 are shared.
+//
 // Forward (ht_train_step_fwd):
-//   1. policy forward on every crop and every constant-gray patch in the FP32
-//      form, keeping each hidden activation for the backward pass;
+//   1. policy forward on every crop and every constant-gray patch, keeping each
+//      hidden activation for the backward pass;
 //   2. per crop, S Bernoulli samples h^s = [u^s < p] (Philox stream 1 + s)
 //      (Eq. independent: all agents act at once);
 //   3. per sample, reward R(h^s) and toggle deltas dR^s (Eq. final_reward,
@@ -43,8 +48,11 @@ struct ht_train {
     size_t las_scratch_bytes = 0;
     double *dacc = nullptr;        // [0] L_MARL, [1..G] L_AS per patch, rewards [B*S*4]
     int n_last = 0;                // crops in the last forward
+    bool fwd_done = false;         // a forward has run (its buffers hold what the backward needs)
     uint64_t seed_last = 0;
     std::vector<ht_image> crops_last;
+    bool tc = false;               // BF16 tensor-core form (train_tc.cu)
+    ht_train_tc_ws tcw;
 };
 
 namespace {
@@ -208,6 +216,10 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
     HT_CHECK_ARG(p && d && out, "null argument");
     *out = nullptr;
     HT_CHECK_ARG(p->head == HT_HEAD_SIGMOID, "training needs the sigmoid head");
+    if (p->prec == HT_FP8_E4M3 || (p->prec == HT_BF16 && !ht_train_tc_supported(p))) {
+        ht_set_error("training supports the FP32 form and the BF16 form of 2 -> 64 x (L-1) -> 1 policies");
+        return HT_ERR_UNSUPPORTED;
+    }
     HT_CHECK_ARG(d->max_crops >= 1 && d->crop_h >= 2 * d->reward.radius + 1 && d->crop_w >= 2 * d->reward.radius + 1,
                  "crops must be at least the reward window");
     HT_CHECK_ARG(d->n_samples >= 1 && d->n_samples <= 64, "n_samples must be in [1, 64]");
@@ -247,20 +259,42 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
     auto alloc = [&](void **ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes < 16 ? 16 : bytes);
     };
-    alloc((void **)&t->acts, sizeof(float) * image_act_floats(t, t->crop_px) * B +
-                                 sizeof(float) * image_act_floats(t, t->gray_px) * G);
+    const bool tc = ht_train_tc_supported(p);
+    if (!tc)
+        alloc((void **)&t->acts, sizeof(float) * image_act_floats(t, t->crop_px) * B +
+                                     sizeof(float) * image_act_floats(t, t->gray_px) * G);
     alloc((void **)&t->prob, sizeof(float) * all_px);
     alloc((void **)&t->dprob, sizeof(float) * all_px);
     alloc((void **)&t->tbits, sizeof(uint32_t) * (size_t)gmax * words_max);
     alloc((void **)&t->sbits, sizeof(uint32_t) * (size_t)B * S * d->crop_h * words);
     alloc((void **)&t->dR, sizeof(float) * (size_t)B * S * t->crop_px);
     alloc((void **)&t->gray_img, sizeof(float) * t->gray_px * (G > 0 ? G : 1));
-    alloc((void **)&t->gbuf[0], sizeof(float) * cmax * max_px);
-    alloc((void **)&t->gbuf[1], sizeof(float) * cmax * max_px);
-    alloc((void **)&t->wflip, sizeof(float) * wmax);
+    if (!tc) alloc((void **)&t->gbuf[0], sizeof(float) * cmax * max_px);
+    if (!tc) alloc((void **)&t->gbuf[1], sizeof(float) * cmax * max_px);
+    if (!tc) alloc((void **)&t->wflip, sizeof(float) * wmax);
     alloc((void **)&t->toggle_scratch, sizeof(float) * t->toggle_scratch_floats);
     if (G > 0) alloc(&t->las_scratch, t->las_scratch_bytes);
     alloc((void **)&t->dacc, sizeof(double) * (1 + G + (size_t)B * S * 4));
+    t->tc = tc;
+    if (t->tc) {
+        ht_train_tc_ws &w = t->tcw;
+        size_t arena = 0;
+        for (int k = 0; k < B + G; ++k) {
+            w.slot_off.push_back(arena);
+            arena += ht_train_tc_image_bytes(p, k < B ? t->crop_px : t->gray_px);
+        }
+        const int wg = ht_bits_row_words(d->gray_n, HT_HEAD_SIGMOID);
+        int tiles = B * ((d->crop_w + 31) / 32) * ((d->crop_h + 7) / 8) + G * ((d->gray_n + 31) / 32) * ((d->gray_n + 7) / 8);
+        size_t total = 0;
+        ht_train_tc_scratch_layout(p, tiles, &w.wt_off, &total);
+        w.scratch_bytes = total;
+        alloc(&w.arena, arena);
+        alloc((void **)&w.dz, sizeof(float) * all_px);
+        alloc((void **)&w.hbits, sizeof(uint32_t) * ((size_t)B * d->crop_h * words + (size_t)G * d->gray_n * wg));
+        alloc(&w.tables, ht_train_tc_table_bytes(p, B + G));
+        alloc(&w.scratch, w.scratch_bytes);
+        w.prob = t->prob;
+    }
     if (e != cudaSuccess) {
         ht_set_error("training workspace: %s", cudaGetErrorString(e));
         ht_train_destroy(t);
@@ -287,6 +321,11 @@ ht_status ht_train_destroy(ht_train *t)
     cudaFree(t->toggle_scratch);
     cudaFree(t->las_scratch);
     cudaFree(t->dacc);
+    cudaFree(t->tcw.arena);
+    cudaFree(t->tcw.dz);
+    cudaFree(t->tcw.hbits);
+    cudaFree(t->tcw.tables);
+    cudaFree(t->tcw.scratch);
     delete t;
     return HT_OK;
 }
@@ -294,9 +333,10 @@ ht_status ht_train_destroy(ht_train *t)
 ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const float *gray_levels, uint64_t seed,
                             double *losses_host, void *stream)
 {
-    HT_CHECK_ARG(t && crops && losses_host, "null argument");
-    HT_CHECK_ARG(n >= 1 && n <= t->d.max_crops, "n must be in [1, max_crops]");
+    HT_CHECK_ARG(t && (crops || n == 0) && losses_host, "null argument");
     const int G = t->d.n_gray, S = t->d.n_samples;
+    HT_CHECK_ARG(n >= 0 && n <= t->d.max_crops && n + G >= 1,
+                 "n must be in [0, max_crops] (0 only with gray patches)");
     HT_CHECK_ARG(G == 0 || gray_levels, "gray levels required");
     for (int i = 0; i < n; ++i) {
         HT_CHECK_ARG(crops[i].contone && crops[i].h == t->d.crop_h && crops[i].w == t->d.crop_w &&
@@ -309,7 +349,35 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
     const int B = t->d.max_crops;
     HT_CUDA_TRY(cudaMemsetAsync(t->dacc, 0, sizeof(double) * (1 + G), s));
     // 1. forward, keeping activations
-    for (int i = 0; i < n + G; ++i) {
+    if (t->tc) {
+        std::vector<ht_image> imgs(n + G);
+        ht_train_tc_ws &w = t->tcw;
+        w.img_off.assign(n + G, 0);
+        w.prob_off.assign(n + G, 0);
+        w.bits_off.assign(n + G, 0);
+        const int words_g = ht_bits_row_words(t->d.gray_n, HT_HEAD_SIGMOID);
+        for (int i = 0; i < n + G; ++i) {
+            const bool gray = i >= n;
+            const int slot = gray ? B + (i - n) : i;
+            if (!gray) {
+                imgs[i] = crops[i];
+            } else {
+                const int gidx = i - n;
+                float *gi = t->gray_img + t->gray_px * gidx;
+                k_fill<<<nblk(t->gray_px), 256, 0, s>>>(gi, t->gray_px, gray_levels[gidx]);
+                HT_LAUNCH_CHECK();
+                imgs[i].contone = gi;
+                imgs[i].h = imgs[i].w = imgs[i].pitch = t->d.gray_n;
+            }
+            w.img_off[i] = w.slot_off[slot];
+            w.prob_off[i] = img_px_offset(t, slot);
+            w.bits_off[i] = slot < B ? (size_t)slot * H * words
+                                     : (size_t)B * H * words + (size_t)(slot - B) * t->d.gray_n * words_g;
+        }
+        ht_status st = ht_train_tc_forward(p, w, imgs.data(), n + G, seed, s);
+        if (st != HT_OK) return st;
+    }
+    for (int i = 0; i < n + G && !t->tc; ++i) {
         const bool gray = i >= n;
         const int slot = gray ? B + (i - n) : i;
         ht_image img;
@@ -371,12 +439,13 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
     for (int g = 0; g < G; ++g) las += h[1 + g];
     if (G > 0) las /= G;
     for (int k = 0; k < n * S; ++k) rmean += h[1 + G + 4 * (size_t)k + 3];
-    rmean /= (double)n * S;
+    if (n > 0) rmean /= (double)n * S;
     losses_host[0] = h[0] + (double)t->d.w_a * las;
     losses_host[1] = h[0];
     losses_host[2] = las;
     losses_host[3] = rmean;
     t->n_last = n;
+    t->fwd_done = true;
     t->seed_last = seed;
     t->crops_last.assign(crops, crops + n);
     return HT_OK;
@@ -385,12 +454,18 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
 ht_status ht_train_step_bwd(ht_train *t, float *grad_w, float *grad_b, void *stream)
 {
     HT_CHECK_ARG(t && grad_w && grad_b, "null argument");
-    HT_CHECK_ARG(t->n_last > 0, "no forward to differentiate");
+    HT_CHECK_ARG(t->fwd_done, "no forward to differentiate");
     ht_policy *p = t->p;
     cudaStream_t s = (cudaStream_t)stream;
     HT_CUDA_TRY(cudaMemsetAsync(grad_w, 0, sizeof(float) * p->n_w, s));
     HT_CUDA_TRY(cudaMemsetAsync(grad_b, 0, sizeof(float) * p->n_b, s));
     const int n = t->n_last, G = t->d.n_gray, B = t->d.max_crops;
+    if (t->tc) {
+        const size_t all_px = t->crop_px * B + t->gray_px * G;
+        k_dlogit<<<nblk(all_px), 256, 0, s>>>(t->dprob, t->prob, all_px, t->tcw.dz);
+        HT_LAUNCH_CHECK();
+        return ht_train_tc_backward(p, t->tcw, n + G, t->seed_last, grad_w, grad_b, s);
+    }
     for (int i = 0; i < n + G; ++i) {
         const bool gray = i >= n;
         const int slot = gray ? B + (i - n) : i;

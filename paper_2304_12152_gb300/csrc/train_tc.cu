@@ -1,0 +1,772 @@
+// train_tc.cu -- BF16 tensor-core form of one training iteration (Algorithm 1,
+// TRAIN step) for the 2 -> 64 x (L-1) -> 1 policy.
+//
+// Forward: the inference pipeline of conv_tc.cu run layer by layer over all
+// crops and gray patches of the step, keeping every hidden activation (bf16,
+// chunk-planar) and its ReLU mask (64 bits per pixel), and the sigmoid
+// probabilities (FP32) of the head.
+//
+// Backward (chain rule through Eq. marl / Eq. as, ReLU and the convolutions):
+//   dz = dL/dp * p (1 - p)                                       (train.cu)
+//   head 64 -> 1 (CUDA cores, k_head_bwd): g_{L-2} = mask * sum_tap w dz(shifted),
+//        dW_head = sum_px dz * a_{L-2}(shifted), db_head = sum dz
+//   every 64 -> 64 layer l:
+//        dW_l = sum_px g_l (x) a_{l-1}(shifted)    tcgen05, k_wgrad_tc
+//        db_l = sum_px g_l                           (same kernel)
+//        g_{l-1} = mask_{l-1} * conv(g_l, W_l flipped and transposed)
+//                                                    conv_tc.cu pipeline, dgrad epilogue
+//   layer 1 (CUDA cores, k_first_wgrad): dW_1 = sum_px g_1 (x) (c, z)(shifted), db_1.
+// Rounding points (the oracle's quant-1 backward follows them): inner-layer
+// weights bf16 in both passes, activations and hidden gradients stored bf16,
+// FP32 accumulation, weight-gradient partial sums reduced in FP64 in a fixed
+// order (deterministic).
+#include <string.h>
+
+#include <vector>
+
+#include "tc_common.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Weight gradient of a 64 -> 64 layer on tcgen05.
+//
+// GEMM over pixels: D[m][n] += sum_k A[m][k] B[n][k], k = 16 pixels per MMA.
+//   B[n][k]  = g[n](y, x0 + k): one staged gradient row, chunk-planar, i.e. the
+//              MN-major canonical layout (8 channels contiguous, pixels at a
+//              16-byte stride).
+//   A[m][k]  = a[c](y + dy - 1, x0 + k + dx - 1), m = (row half, c): the two
+//              halves of M are two consecutive staged activation rows, so one
+//              MMA covers taps (dy, dx) and (dy + 1, dx).  Staged rows sit in a
+//              ring whose slot 0 is mirrored after the last slot, so two
+//              consecutive rows are always contiguous; the pixel shift dx is a
+//              16-byte shift of the descriptor start.
+// Six accumulator tiles of 128 lanes x 64 columns (dx x {dy 0|1, dy 2|unused})
+// stay in TMEM for the whole persistent CTA; the epilogue warps zero them at
+// the start, sum the staged gradient rows per channel while the MMAs run (bias
+// gradient), and write the CTA's partial sums at the end.
+// ---------------------------------------------------------------------------
+constexpr int WG_NSA = 6;                       // activation-row ring (+1 mirror slot)
+constexpr int WG_NSG = 3;                       // gradient-row ring
+constexpr int WG_ASLOT = 8 * ROW_PX * 16;       // [chunk][130 px][16 B]
+constexpr int WG_GSLOT = 8 * TILE_M * 16;       // [chunk][128 px][16 B]
+constexpr int WG_NTHREADS = 192;                // producer, MMA issuer, 4 epilogue warps
+constexpr int WG_TILES = 6;
+constexpr int WG_SMEM = (WG_NSA + 1) * WG_ASLOT + WG_NSG * WG_GSLOT + 1024 /*align*/ + 1024 /*barriers*/;
+
+struct WgParams {
+    const ImgDesc *imgs;      // act[0] = layer input a (chunk-planar bf16), act[1] = gradient g
+    int n_imgs, n_units;
+    float *partials;          // [grid][6 tiles][64 n][128 lanes]
+    float *colsum;            // [grid][64]
+    int *err;
+};
+
+// instruction descriptor: F32 accumulate, bf16 A/B, both MN-major, N = 64, M = 128
+constexpr uint32_t kWgIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((64u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+__global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *s_a = smem;
+    uint8_t *s_g = s_a + (WG_NSA + 1) * WG_ASLOT;
+    uint64_t *bars = (uint64_t *)(s_g + WG_NSG * WG_GSLOT);
+    uint64_t *a_full = bars, *a_empty = bars + WG_NSA, *g_full = bars + 2 * WG_NSA,
+             *g_empty = bars + 2 * WG_NSA + WG_NSG, *tzero = bars + 2 * WG_NSA + 2 * WG_NSG, *done = tzero + 1;
+    uint32_t *s_tmem = (uint32_t *)(done + 1);
+    volatile int *s_abort = (volatile int *)(s_tmem + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < WG_NSA; ++i) {
+            mbar_init(smem_u32(&a_full[i]), 1);
+            mbar_init(smem_u32(&a_empty[i]), 1);
+        }
+        for (int i = 0; i < WG_NSG; ++i) {
+            mbar_init(smem_u32(&g_full[i]), 1);
+            mbar_init(smem_u32(&g_empty[i]), 1 + 4);     // MMA commit + 4 epilogue warps (bias sums)
+        }
+        mbar_init(smem_u32(tzero), 4);
+        mbar_init(smem_u32(done), 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(s_tmem), TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *s_tmem;
+
+    if (warp == 0) {
+        // ------------------------- producer -------------------------
+        int a_last[WG_NSA], g_last[WG_NSG];
+        for (int i = 0; i < WG_NSA; ++i) a_last[i] = -1;
+        for (int i = 0; i < WG_NSG; ++i) g_last[i] = -1;
+        uint32_t la = 0, lg = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
+            const UnitInfo ui = unit_info(P.imgs, P.n_imgs, 0, u);
+            const int x0 = ui.x0;
+            const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, ui.W);
+            for (int r = 0; r < ui.nrows + 2 && ok; ++r) {
+                // activation row y0 - 1 + r into ring slot la % NSA (slot 0 also into the mirror)
+                {
+                    const int slot = (int)(la % WG_NSA);
+                    int got = 0;
+                    if (lane == 0)
+                        got = mbar_wait(smem_u32(&a_empty[slot]), ((la / WG_NSA) & 1u) ^ 1u, s_abort, P.err) ? 1 : 0;
+                    if (!__shfl_sync(0xffffffffu, got, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    const int ncopy = slot == 0 ? 2 : 1;
+                    const int yy = ui.y0 - 1 + r;
+                    const bool row_in = (yy >= 0 && yy < ui.H);
+                    bool zeroed = false;
+                    for (int cp = 0; cp < ncopy; ++cp) {
+                        uint8_t *dst = s_a + (cp ? WG_NSA : slot) * WG_ASLOT;
+                        if (!row_in) {
+                            for (int k = lane; k < 8 * ROW_PX; k += 32)
+                                *reinterpret_cast<uint4 *>(dst + (size_t)k * 16) = make_uint4(0, 0, 0, 0);
+                            zeroed = true;
+                        } else if (lo > x0 - 1 || hi < x0 - 1 + ROW_PX) {
+                            const int nl = lo - (x0 - 1), nr = (x0 - 1 + ROW_PX) - hi;
+                            for (int k = lane; k < 8 * (nl + nr); k += 32) {
+                                const int c = k / (nl + nr), j = k % (nl + nr);
+                                const int px = j < nl ? j : (hi - (x0 - 1)) + (j - nl);
+                                *reinterpret_cast<uint4 *>(dst + ((size_t)c * ROW_PX + px) * 16) = make_uint4(0, 0, 0, 0);
+                            }
+                            zeroed = true;
+                        }
+                    }
+                    if (zeroed) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        const uint32_t run = (uint32_t)(hi - lo) * 16u;
+                        if (row_in && hi > lo) {
+                            mbar_arrive_expect_tx(smem_u32(&a_full[slot]), run * 8u * (uint32_t)ncopy);
+                            for (int cp = 0; cp < ncopy; ++cp) {
+                                uint8_t *dst = s_a + (cp ? WG_NSA : slot) * WG_ASLOT;
+                                for (int c = 0; c < 8; ++c)
+                                    bulk_g2s(smem_u32(dst + ((size_t)c * ROW_PX + (lo - (x0 - 1))) * 16),
+                                             ui.in + (((size_t)c * ui.H + yy) * ui.W + lo) * 16, run,
+                                             smem_u32(&a_full[slot]));
+                            }
+                        } else {
+                            mbar_arrive(smem_u32(&a_full[slot]));
+                        }
+                    }
+                    a_last[slot] = (int)la;
+                    ++la;
+                }
+                if (r < 2) continue;
+                // gradient row y0 + r - 2 into ring slot lg % NSG
+                {
+                    const int slot = (int)(lg % WG_NSG);
+                    int got = 0;
+                    if (lane == 0)
+                        got = mbar_wait(smem_u32(&g_empty[slot]), ((lg / WG_NSG) & 1u) ^ 1u, s_abort, P.err) ? 1 : 0;
+                    if (!__shfl_sync(0xffffffffu, got, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *dst = s_g + slot * WG_GSLOT;
+                    const int yy = ui.y0 + r - 2;
+                    const int nin = min(TILE_M, ui.W - x0);
+                    if (nin < TILE_M) {
+                        for (int k = lane; k < 8 * (TILE_M - nin); k += 32) {
+                            const int c = k / (TILE_M - nin), px = nin + k % (TILE_M - nin);
+                            *reinterpret_cast<uint4 *>(dst + ((size_t)c * TILE_M + px) * 16) = make_uint4(0, 0, 0, 0);
+                        }
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        const uint32_t run = (uint32_t)nin * 16u;
+                        mbar_arrive_expect_tx(smem_u32(&g_full[slot]), run * 8u);
+                        const uint8_t *g = ui.out;
+                        for (int c = 0; c < 8; ++c)
+                            bulk_g2s(smem_u32(dst + (size_t)c * TILE_M * 16), g + (((size_t)c * ui.H + yy) * ui.W + x0) * 16,
+                                     run, smem_u32(&g_full[slot]));
+                    }
+                    g_last[slot] = (int)lg;
+                    ++lg;
+                }
+            }
+        }
+        if (lane == 0) {
+            for (int s2 = 0; s2 < WG_NSA; ++s2)
+                if (a_last[s2] >= 0)
+                    mbar_wait(smem_u32(&a_full[s2]), ((uint32_t)a_last[s2] / WG_NSA) & 1u, s_abort, P.err, true);
+            for (int s2 = 0; s2 < WG_NSG; ++s2)
+                if (g_last[s2] >= 0)
+                    mbar_wait(smem_u32(&g_full[s2]), ((uint32_t)g_last[s2] / WG_NSG) & 1u, s_abort, P.err, true);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------- MMA issuer -------------------------
+        auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
+            int got = 0;
+            if (lane == 0) got = mbar_wait(bar, par, s_abort, P.err) ? 1 : 0;
+            return __shfl_sync(0xffffffffu, got, 0) != 0;
+        };
+        // MN-major, no swizzle: LBO = stride between 8-pixel groups (K), SBO = stride
+        // between 8-channel groups (M or N)
+        const uint64_t a_base = sdesc(smem_u32(s_a), 128, ROW_PX * 16);
+        const uint64_t g_base = sdesc(smem_u32(s_g), 128, TILE_M * 16);
+        bool ok = wait1(smem_u32(tzero), 0);
+        if (ok) tc_fence_after();
+        uint32_t qa = 0, qg = 0;
+        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
+            const int nrows = unit_info(P.imgs, P.n_imgs, 0, u).nrows;
+            const uint32_t base = qa;
+            ok = wait1(smem_u32(&a_full[base % WG_NSA]), (base / WG_NSA) & 1u) &&
+                 wait1(smem_u32(&a_full[(base + 1) % WG_NSA]), ((base + 1) / WG_NSA) & 1u);
+            for (int j = 0; j < nrows && ok; ++j, ++qg) {
+                const uint32_t qn = base + (uint32_t)j + 2u;
+                ok = wait1(smem_u32(&a_full[qn % WG_NSA]), (qn / WG_NSA) & 1u) &&
+                     wait1(smem_u32(&g_full[qg % WG_NSG]), (qg / WG_NSG) & 1u);
+                if (!ok) break;
+                tc_fence_after();
+                if (lane == 0) {
+                    const uint64_t b_q = g_base + (uint64_t)(((qg % WG_NSG) * (uint32_t)WG_GSLOT) >> 4);
+#pragma unroll
+                    for (int pair = 0; pair < 2; ++pair) {
+                        const uint32_t s = (base + (uint32_t)j + 2u * pair) % WG_NSA;
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint64_t a_q = a_base + (uint64_t)((s * (uint32_t)WG_ASLOT + dx * 16u) >> 4);
+                            const uint32_t d = tmem_base + (uint32_t)(dx * 2 + pair) * 64u;
+#pragma unroll
+                            for (int ks = 0; ks < 8; ++ks)
+                                mma_ss<false>(d, a_q + (uint64_t)((ks * 256) >> 4), b_q + (uint64_t)((ks * 256) >> 4),
+                                              kWgIdesc, 1u);
+                        }
+                    }
+                    mma_commit(smem_u32(&g_empty[qg % WG_NSG]));
+                    mma_commit(smem_u32(&a_empty[(base + (uint32_t)j) % WG_NSA]));
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+            if (lane == 0) {
+                mma_commit(smem_u32(&a_empty[(base + (uint32_t)nrows) % WG_NSA]));
+                mma_commit(smem_u32(&a_empty[(base + (uint32_t)nrows + 1u) % WG_NSA]));
+            }
+            __syncwarp();
+            qa = base + (uint32_t)nrows + 2u;
+        }
+        if (lane == 0) mma_commit(smem_u32(done));     // all issued MMAs, aborted or not
+        __syncwarp();
+    } else {
+        // ------------------------- epilogue -------------------------
+        const int quarter = warp & 3;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        for (int t = 0; t < WG_TILES; ++t)
+            for (int c = 0; c < 64; c += 16) tmem_zero16(lane_base + t * 64 + c);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(tzero));
+        // bias gradient: per-channel sums of the staged gradient rows
+        const int e = (warp - 2) * 32 + lane;             // 0..127
+        const int chunk = e >> 4, pg = e & 15;            // 8 pixels pg*8 .. +7 of one chunk
+        float cs[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cs[i] = 0.f;
+        uint32_t qg = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
+            const int nrows = unit_info(P.imgs, P.n_imgs, 0, u).nrows;
+            for (int j = 0; j < nrows; ++j, ++qg) {
+                int got = 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&g_full[qg % WG_NSG]), (qg / WG_NSG) & 1u, s_abort, P.err) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, got, 0)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t *src = s_g + (qg % WG_NSG) * WG_GSLOT + ((size_t)chunk * TILE_M + pg * 8) * 16;
+#pragma unroll
+                for (int px = 0; px < 8; ++px) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(src + px * 16);
+                    const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        cs[2 * h] += __uint_as_float(w4[h] << 16);
+                        cs[2 * h + 1] += __uint_as_float(w4[h] & 0xFFFF0000u);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&g_empty[qg % WG_NSG]));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) cs[i] += __shfl_xor_sync(0xffffffffu, cs[i], o);
+        }
+        if (pg == 0)
+            for (int i = 0; i < 8; ++i) P.colsum[(size_t)blockIdx.x * 64 + chunk * 8 + i] = cs[i];
+        // weight-gradient partial sums of this CTA
+        int got = 0;
+        if (lane == 0) got = mbar_wait(smem_u32(done), 0, s_abort, P.err, true) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        tc_fence_after();
+        if (got) {
+            for (int t = 0; t < WG_TILES; ++t)
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(lane_base + t * 64 + c0, v);
+                    tmem_wait_ld();
+                    float *dst = P.partials + (((size_t)blockIdx.x * WG_TILES + t) * 64 + c0) * 128 + quarter * 32 + lane;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) dst[(size_t)i * 128] = v[i];
+                }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// dW[n][c][dy][dx] and db[n] of a 64 -> 64 layer from the CTAs' partial sums
+// (FP64, CTA order).  Thread = (tile, n, lane) so that the partial reads coalesce.
+__global__ void k_reduce_wgrad_tc(const float *__restrict__ partials, const float *__restrict__ colsum, int ncta,
+                                  float *__restrict__ gw, float *__restrict__ gb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < WG_TILES * 64 * 128) {
+        const int t = i / (64 * 128), n = (i / 128) % 64, lane = i % 128;
+        const int dx = t >> 1, pair = t & 1;
+        if (pair == 1 && lane >= 64) return;               // rows of no tap
+        const int dy = pair ? 2 : (lane >> 6), c = lane & 63;
+        double s = 0.0;
+        for (int k = 0; k < ncta; ++k) s += (double)partials[(size_t)k * WG_TILES * 64 * 128 + i];
+        gw[((n * 64 + c) * 3 + dy) * 3 + dx] = (float)s;
+    } else if (i < WG_TILES * 64 * 128 + 64) {
+        const int n = i - WG_TILES * 64 * 128;
+        double s = 0.0;
+        for (int k = 0; k < ncta; ++k) s += (double)colsum[(size_t)k * 64 + n];
+        gb[n] = (float)s;
+    }
+}
+
+// Data-gradient weights of a 64 -> 64 layer in the pipeline's B layout:
+// Wt[c][n][dy][dx] = W[n][c][2 - dy][2 - dx] packed as [dx][chunk of n][2 - dy][c][8 n].
+__global__ void k_pack_dgrad(const float *__restrict__ w, __nv_bfloat16 *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * 8 * 3 * 64 * 8) return;
+    const int e = i % 8, o = (i / 8) % 64, s = (i / 512) % 3, k = (i / 1536) % 8, dx = i / 12288;
+    const int n = k * 8 + e, c = o;                     // Wt input channel n, output channel c
+    // Wt[c][n][dy = 2 - s][dx] = W[n][c][s][2 - dx]
+    out[i] = __float2bfloat16_rn(w[((n * 64 + c) * 3 + s) * 3 + (2 - dx)]);
+}
+
+// ---------------------------------------------------------------------------
+// Head (64 -> 1) backward on CUDA cores, one 32 x 8 tile per block.
+// Table: act[0] = a_{L-2} (bf16), act[1] = g_{L-2} output (bf16), mask = ReLU mask
+// of a_{L-2}, prob = dz (FP32 [H][W]).
+//   g(y,x)[c] = mask * sum_{dy,dx} w[c][dy][dx] dz(y - dy + 1, x - dx + 1)
+//   dW[c][dy][dx] += sum dz(y,x) a[c](y + dy - 1, x + dx - 1);  db += sum dz
+// Per-block partial sums (576 weights + bias) go to partials[block][577].
+// ---------------------------------------------------------------------------
+struct HeadBwdParams {
+    const ImgDesc *imgs;
+    int n_imgs;
+    float w[9 * 64];          // [tap][c]
+    float *partials;
+};
+
+__global__ void __launch_bounds__(HT_X *HT_Y) k_head_bwd(const HeadBwdParams P)
+{
+    __shared__ float s_dz[HT_Y + 2][HT_X + 2];
+    __shared__ __align__(16) __nv_bfloat16 s_a[(HT_Y + 2) * (HT_X + 2) * 64];
+    const int im = find_image(P.n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&P.imgs[i].hd_begin); });
+    const ImgDesc *D = P.imgs + im;
+    const int lt = (int)blockIdx.x - D->hd_begin;
+    const int H = D->H, W = D->W;
+    const int hx = (W + HT_X - 1) / HT_X;
+    const int x0 = (lt % hx) * HT_X, y0 = (lt / hx) * HT_Y;
+    const int tid = threadIdx.y * HT_X + threadIdx.x;
+    const float *dz = D->prob;
+    const uint8_t *a = D->act[0];
+    for (int k = tid; k < (HT_Y + 2) * (HT_X + 2); k += HT_X * HT_Y) {
+        const int yy = y0 - 1 + k / (HT_X + 2), xx = x0 - 1 + k % (HT_X + 2);
+        s_dz[k / (HT_X + 2)][k % (HT_X + 2)] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? dz[(size_t)yy * W + xx] : 0.f;
+    }
+    for (int k = tid; k < (HT_Y + 2) * (HT_X + 2) * 8; k += HT_X * HT_Y) {
+        const int chunk = k % 8, p = k / 8;
+        const int yy = y0 - 1 + p / (HT_X + 2), xx = x0 - 1 + p % (HT_X + 2);
+        uint4 q = make_uint4(0, 0, 0, 0);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+            q = *reinterpret_cast<const uint4 *>(a + (((size_t)chunk * H + yy) * W + xx) * 16);
+        *reinterpret_cast<uint4 *>(&s_a[(size_t)p * 64 + chunk * 8]) = q;
+    }
+    __syncthreads();
+    // data gradient at this thread's pixel
+    const int y = y0 + threadIdx.y, x = x0 + threadIdx.x;
+    if (y < H && x < W) {
+        float d[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) d[t] = s_dz[threadIdx.y + 2 - t / 3][threadIdx.x + 2 - t % 3];
+        const uint2 m = D->mask[(size_t)y * W + x];
+        float g[64];
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc = fmaf(P.w[t * 64 + c], d[t], acc);
+            g[c] = (((c < 32 ? m.x : m.y) >> (c & 31)) & 1u) ? acc : 0.f;
+        }
+        store_pixel(g, D->act[1], 0, 1.f, H, W, y, x);
+    }
+    // weight and bias gradient partial sums of this tile
+    for (int idx = tid; idx < 577; idx += HT_X * HT_Y) {
+        float s = 0.f;
+        if (idx < 576) {
+            const int c = idx % 64, t = idx / 64, dy = t / 3, dx = t % 3;
+            for (int py = 0; py < HT_Y; ++py)
+                for (int px = 0; px < HT_X; ++px)
+                    s = fmaf(s_dz[py + 1][px + 1], __bfloat162float(s_a[((py + dy) * (HT_X + 2) + px + dx) * 64 + c]), s);
+        } else {
+            for (int py = 0; py < HT_Y; ++py)
+                for (int px = 0; px < HT_X; ++px) s += s_dz[py + 1][px + 1];
+        }
+        P.partials[(size_t)blockIdx.x * 577 + idx] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Layer-1 (2 -> 64) weight gradient on CUDA cores, one 32 x 8 tile per block.
+// Table: act[0] = g_1 (bf16), contone, image (Philox index).  Input channels
+// c and z (Philox stream 0, the forward's noise) exactly as FP32.
+//   dW[n][ci][dy][dx] += sum g[n](y,x) x_ci(y + dy - 1, x + dx - 1); db[n] += sum g[n]
+// partials[block][1152 + 64] with weight entry (ci*9 + tap)*64 + n.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(HT_X *HT_Y) k_first_wgrad(const ImgDesc *__restrict__ imgs, int n_imgs, uint64_t seed,
+                                                           float *__restrict__ partials)
+{
+    __shared__ float s_x[2][HT_Y + 2][HT_X + 2];
+    __shared__ __align__(16) __nv_bfloat16 s_g[HT_Y * HT_X * 64];
+    const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].hd_begin); });
+    const ImgDesc *D = imgs + im;
+    const int lt = (int)blockIdx.x - D->hd_begin;
+    const int H = D->H, W = D->W;
+    const int hx = (W + HT_X - 1) / HT_X;
+    const int x0 = (lt % hx) * HT_X, y0 = (lt / hx) * HT_Y;
+    const int tid = threadIdx.y * HT_X + threadIdx.x;
+    for (int k = tid; k < (HT_Y + 2) * (HT_X + 2); k += HT_X * HT_Y) {
+        const int r = k / (HT_X + 2), q = k % (HT_X + 2);
+        const int yy = y0 - 1 + r, xx = x0 - 1 + q;
+        const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        s_x[0][r][q] = in ? D->contone[(size_t)yy * D->cpitch + xx] : 0.f;
+        s_x[1][r][q] = in ? ht_uniform24(seed, D->image, 0u, (uint64_t)yy * W + xx) : 0.f;
+    }
+    for (int k = tid; k < HT_Y * HT_X * 8; k += HT_X * HT_Y) {
+        const int chunk = k % 8, p = k / 8;
+        const int yy = y0 + p / HT_X, xx = x0 + p % HT_X;
+        uint4 q = make_uint4(0, 0, 0, 0);
+        if (yy < H && xx < W) q = *reinterpret_cast<const uint4 *>(D->act[0] + (((size_t)chunk * H + yy) * W + xx) * 16);
+        *reinterpret_cast<uint4 *>(&s_g[(size_t)p * 64 + chunk * 8]) = q;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 1152 + 64; idx += HT_X * HT_Y) {
+        float s = 0.f;
+        if (idx < 1152) {
+            const int n = idx % 64, k = idx / 64, ci = k / 9, t = k % 9, dy = t / 3, dx = t % 3;
+            for (int py = 0; py < HT_Y; ++py)
+                for (int px = 0; px < HT_X; ++px)
+                    s = fmaf(__bfloat162float(s_g[(py * HT_X + px) * 64 + n]), s_x[ci][py + dy][px + dx], s);
+        } else {
+            const int n = idx - 1152;
+            for (int p = 0; p < HT_Y * HT_X; ++p) s += __bfloat162float(s_g[p * 64 + n]);
+        }
+        partials[(size_t)blockIdx.x * 1216 + idx] = s;
+    }
+}
+
+// Sum of per-block partials (FP64, block order).  mode 0: head, entries [tap][c]
+// + bias; mode 1: layer 1, entries [(ci*9 + tap)][n] + 64 biases.
+__global__ void k_reduce_blocks(const float *__restrict__ partials, int nblk, int nval, int mode, float *__restrict__ gw,
+                                float *__restrict__ gb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nval) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += (double)partials[(size_t)b * nval + i];
+    if (mode == 0) {
+        if (i < 576) gw[(i % 64) * 9 + i / 64] = (float)s;       // W_head[0][c][tap]
+        else gb[0] = (float)s;
+    } else {
+        if (i < 1152) {
+            const int n = i % 64, k = i / 64;                      // k = ci*9 + tap
+            gw[(n * 2 + k / 9) * 9 + k % 9] = (float)s;
+        } else {
+            gb[i - 1152] = (float)s;
+        }
+    }
+}
+
+unsigned nblk256(size_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+bool ht_train_tc_supported(const ht_policy *p)
+{
+    if (p->prec != HT_BF16 || p->head != HT_HEAD_SIGMOID || p->K != 1 || p->L < 3) return false;
+    if (p->ch[0] != 2) return false;
+    for (int l = 1; l < p->L; ++l)
+        if (p->ch[l] != 64) return false;
+    return true;
+}
+
+// Per image of a step, in the arena (px = h * w), each region 256-byte aligned:
+// hidden activations [L-1][px][128 B], ReLU masks [L-1][px] x 8 B, layer-1 split
+// input [px][16 B], head partials [9][px] x 4 B, gradient ping-pong 2 x [px][128 B].
+namespace {
+inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+struct ImgRegions {
+    size_t acts, masks, split, part9, g0, g1, total;
+};
+ImgRegions img_regions(int nh, size_t px)
+{
+    ImgRegions r;
+    r.acts = 0;
+    r.masks = r.acts + al256((size_t)nh * px * 128);
+    r.split = r.masks + al256((size_t)nh * px * 8);
+    r.part9 = r.split + al256(px * 16);
+    r.g0 = r.part9 + al256(px * 36);
+    r.g1 = r.g0 + al256(px * 128);
+    r.total = r.g1 + al256(px * 128);
+    return r;
+}
+}  // namespace
+
+size_t ht_train_tc_image_bytes(const ht_policy *p, size_t px) { return img_regions(p->L - 1, px).total; }
+
+size_t ht_train_tc_table_bytes(const ht_policy *p, int n_img)
+{
+    return (size_t)(3 * p->L - 2) * n_img * sizeof(ImgDesc);
+}
+
+// partial-sum region (CTA partials of the tcgen05 weight gradient, or per-tile
+// partials of the CUDA-core ones) followed by the packed data-gradient weights
+void ht_train_tc_scratch_layout(const ht_policy *p, int n_tiles, size_t *wt_off, size_t *total)
+{
+    const size_t wg = (size_t)num_sms() * (WG_TILES * 64 * 128 + 64) * sizeof(float);
+    const size_t blk = (size_t)n_tiles * 1216 * sizeof(float);
+    const size_t part = ((wg > blk ? wg : blk) + 255) / 256 * 256;
+    *wt_off = part;
+    *total = part + (size_t)(p->L > 2 ? p->L - 2 : 1) * 36864 * sizeof(__nv_bfloat16);
+}
+
+namespace {
+// Table indices of one step (each table = one ImgDesc per image of the step).
+constexpr int T_FIRST = 0;                               // layer 1
+inline int T_FWD(int l) { return l; }                    // inner layer l = 1 .. L-2
+inline int T_HEAD(int L) { return L - 1; }               // head forward
+inline int T_HB(int L) { return L; }                     // head backward
+inline int T_WG(int L, int l) { return L + l; }          // weight gradient of inner layer l
+inline int T_W1(int L) { return 2 * L - 1; }             // layer-1 weight gradient
+inline int T_DG(int L, int l) { return 2 * L - 1 + l; }  // data gradient through inner layer l
+inline int n_tables(int L) { return 3 * L - 2; }
+
+void build_tables(const ht_policy *p, const ht_train_tc_ws &w, const ht_image *imgs, int nimg,
+                  std::vector<ImgDesc> &all, int &units, int &hd, int &pre)
+{
+    const int L = p->L, nh = L - 1;
+    units = hd = pre = 0;
+    std::vector<ImgDesc> D0(nimg);
+    for (int i = 0; i < nimg; ++i) {
+        ImgDesc D{};
+        D.contone = imgs[i].contone;
+        D.cpitch = imgs[i].pitch;
+        D.H = imgs[i].h;
+        D.W = imgs[i].w;
+        D.image = (uint32_t)i;
+        D.words = ht_bits_row_words(D.W, HT_HEAD_SIGMOID);
+        set_begins(D, units, hd, pre);
+        D0[i] = D;
+    }
+    all.assign((size_t)n_tables(L) * nimg, ImgDesc{});
+    for (int i = 0; i < nimg; ++i) {
+        const size_t px = (size_t)imgs[i].h * imgs[i].w;
+        const ImgRegions R = img_regions(nh, px);
+        uint8_t *b = (uint8_t *)w.arena + w.img_off[i];
+        uint8_t *acts = b + R.acts;
+        uint2 *masks = (uint2 *)(b + R.masks);
+        uint8_t *split = b + R.split;
+        float *part9 = (float *)(b + R.part9);
+        uint8_t *g0 = b + R.g0;
+        uint8_t *g1 = b + R.g1;
+        auto act = [&](int l) { return acts + (size_t)l * px * 128; };
+        auto msk = [&](int l) { return masks + (size_t)l * px; };
+        auto gbuf = [&](int l) { return (l & 1) ? g1 : g0; };   // g_l: gradient at layer l's pre-activation
+        auto T = [&](int t) -> ImgDesc & { return all[(size_t)t * nimg + i]; };
+        // forward
+        T(T_FIRST) = D0[i];
+        T(T_FIRST).act[0] = act(0);
+        T(T_FIRST).act[1] = split;
+        T(T_FIRST).mask = msk(0);
+        for (int l = 1; l <= L - 2; ++l) {
+            ImgDesc &D = T(T_FWD(l));
+            D = D0[i];
+            D.act[0] = act(l - 1);
+            D.act[1] = l == L - 2 ? (uint8_t *)part9 : act(l);
+            D.mask = msk(l);
+            D.save = l == L - 2 ? act(l) : nullptr;
+        }
+        {
+            ImgDesc &D = T(T_HEAD(L));
+            D = D0[i];
+            D.act[0] = (uint8_t *)part9;
+            D.prob = w.prob + w.prob_off[i];
+            D.bits = w.hbits + w.bits_off[i];
+        }
+        // backward
+        {
+            ImgDesc &D = T(T_HB(L));
+            D = D0[i];
+            D.act[0] = act(L - 2);
+            D.act[1] = gbuf(L - 2);
+            D.mask = msk(L - 2);
+            D.prob = w.dz + w.prob_off[i];
+        }
+        for (int l = 1; l <= L - 2; ++l) {
+            ImgDesc &Wg = T(T_WG(L, l));
+            Wg = D0[i];
+            Wg.act[0] = act(l - 1);
+            Wg.act[1] = gbuf(l);
+            ImgDesc &Dg = T(T_DG(L, l));
+            Dg = D0[i];
+            Dg.act[0] = gbuf(l);
+            Dg.act[1] = gbuf(l - 1);
+            Dg.mask = msk(l - 1);
+        }
+        T(T_W1(L)) = D0[i];
+        T(T_W1(L)).act[0] = gbuf(0);
+    }
+}
+}  // namespace
+
+ht_status ht_train_tc_forward(ht_policy *p, ht_train_tc_ws &w, const ht_image *imgs, int nimg, uint64_t seed,
+                              cudaStream_t s)
+{
+    const int L = p->L;
+    std::vector<ImgDesc> all;
+    int units, hd, pre;
+    build_tables(p, w, imgs, nimg, all, units, hd, pre);
+    w.units = units;
+    w.hd = hd;
+    HT_CUDA_TRY(cudaMemcpyAsync(w.tables, all.data(), all.size() * sizeof(ImgDesc), cudaMemcpyHostToDevice, s));
+    auto tab = [&](int t) { return (const void *)((const ImgDesc *)w.tables + (size_t)t * nimg); };
+    ht_status st = ht_tc_first_input(tab(T_FIRST), nimg, pre, seed, s);
+    if (st != HT_OK) return st;
+    {
+        ht_tc_layer a{};
+        a.table = tab(T_FIRST);
+        a.n_imgs = nimg;
+        a.n_units = units;
+        a.in_buf = 1;
+        a.kind = 2;
+        a.wpack = p->d_w1pack;
+        a.bias = p->h_b + p->b_off[0];
+        a.seed = seed;
+        if ((st = ht_tc_conv(a, s)) != HT_OK) return st;
+    }
+    for (int l = 1; l <= L - 2; ++l) {
+        ht_tc_layer a{};
+        a.table = tab(T_FWD(l));
+        a.n_imgs = nimg;
+        a.n_units = units;
+        a.in_buf = 0;
+        a.kind = l == L - 2 ? 1 : 0;
+        a.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (l - 1);
+        a.bias = p->h_b + p->b_off[l];
+        a.head_w = l == L - 2 ? p->h_headw : nullptr;
+        a.seed = seed;
+        if ((st = ht_tc_conv(a, s)) != HT_OK) return st;
+    }
+    return ht_tc_head_partials(tab(T_HEAD(L)), nimg, hd, 0, p->head_bias, HT_MODE_THRESHOLD, seed, s);
+}
+
+ht_status ht_train_tc_backward(ht_policy *p, ht_train_tc_ws &w, int nimg, uint64_t seed, float *grad_w, float *grad_b,
+                               cudaStream_t s)
+{
+    const int L = p->L;
+    int *err = ht_device_error_flag();
+    if (!err) return HT_ERR_CUDA;
+    auto tab = [&](int t) { return (const ImgDesc *)w.tables + (size_t)t * nimg; };
+    float *wpart = (float *)w.scratch;
+    __nv_bfloat16 *wt = (__nv_bfloat16 *)((uint8_t *)w.scratch + w.wt_off);
+    // data-gradient weights of every inner layer
+    for (int l = 1; l <= L - 2; ++l) {
+        k_pack_dgrad<<<nblk256(36864), 256, 0, s>>>(p->d_w + p->w_off[l], wt + (size_t)(l - 1) * 36864);
+        HT_LAUNCH_CHECK();
+    }
+    // head backward: g_{L-2}, dW / db of the head
+    {
+        HeadBwdParams P;
+        P.imgs = tab(T_HB(L));
+        P.n_imgs = nimg;
+        memcpy(P.w, p->h_headw, sizeof(P.w));
+        P.partials = wpart;
+        ht_prof_start(HTK_TRAIN, s);
+        k_head_bwd<<<w.hd, dim3(HT_X, HT_Y), 0, s>>>(P);
+        ht_prof_stop(s);
+        HT_LAUNCH_CHECK();
+        k_reduce_blocks<<<nblk256(577), 256, 0, s>>>(wpart, w.hd, 577, 0, grad_w + p->w_off[L - 1],
+                                                     grad_b + p->b_off[L - 1]);
+        HT_LAUNCH_CHECK();
+    }
+    static bool attr = false;
+    if (!attr) {
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM));
+        attr = true;
+    }
+    const int grid = w.units < num_sms() ? w.units : num_sms();
+    for (int l = L - 2; l >= 1; --l) {
+        WgParams P;
+        P.imgs = tab(T_WG(L, l));
+        P.n_imgs = nimg;
+        P.n_units = w.units;
+        P.partials = wpart;
+        P.colsum = wpart + (size_t)grid * WG_TILES * 64 * 128;
+        P.err = err;
+        ht_prof_start(HTK_TRAIN, s);
+        k_wgrad_tc<<<grid, WG_NTHREADS, WG_SMEM, s>>>(P);
+        ht_prof_stop(s);
+        HT_LAUNCH_CHECK();
+        k_reduce_wgrad_tc<<<nblk256(WG_TILES * 64 * 128 + 64), 256, 0, s>>>(P.partials, P.colsum, grid,
+                                                                           grad_w + p->w_off[l], grad_b + p->b_off[l]);
+        HT_LAUNCH_CHECK();
+        ht_tc_layer a{};
+        a.table = tab(T_DG(L, l));
+        a.n_imgs = nimg;
+        a.n_units = w.units;
+        a.in_buf = 0;
+        a.kind = 0;
+        a.wpack = wt + (size_t)(l - 1) * 36864;
+        a.dgrad = 1;
+        a.seed = seed;
+        ht_status st = ht_tc_conv(a, s);
+        if (st != HT_OK) return st;
+    }
+    ht_prof_start(HTK_TRAIN, s);
+    k_first_wgrad<<<w.hd, dim3(HT_X, HT_Y), 0, s>>>(tab(T_W1(L)), nimg, seed, wpart);
+    ht_prof_stop(s);
+    HT_LAUNCH_CHECK();
+    k_reduce_blocks<<<nblk256(1216), 256, 0, s>>>(wpart, w.hd, 1216, 1, grad_w + p->w_off[0], grad_b + p->b_off[0]);
+    HT_LAUNCH_CHECK();
+    return HT_OK;
+}

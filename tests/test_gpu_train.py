@@ -18,14 +18,14 @@ from paper_2304_12152_gb300 import api, synth
 pytestmark = pytest.mark.gpu
 
 
-def oracle_step(crops, grays, ws, bs, seed, S, w_a, las_mode, n_rad, n_ang):
+def oracle_step(crops, grays, ws, bs, seed, S, w_a, las_mode, n_rad, n_ang, quant=0):
     n, G = len(crops), len(grays)
     gw = [np.zeros(w.shape) for w in ws]
     gb = [np.zeros(b.shape) for b in bs]
     l_marl, rs = 0.0, []
     for i, c in enumerate(crops):
         h, w = c.shape
-        lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=i, save_acts=True)
+        lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=i, quant=quant, save_acts=True)
         dp = np.zeros((h, w))
         for s in range(S):
             u = O.uniform_map(seed, i, 1 + s, h, w)
@@ -36,21 +36,21 @@ def oracle_step(crops, grays, ws, bs, seed, S, w_a, las_mode, n_rad, n_ang):
             l_marl += val / (n * S)
             dp += grad / (n * S)
             rs.append(r["R"])
-        a, b = O.backward(c, ws, bs, seed, i, acts, lg, dp)
+        a, b = O.backward(c, ws, bs, seed, i, acts, lg, dp, quant=quant)
         for l in range(len(ws)):
             gw[l] += a[l]
             gb[l] += b[l]
     l_as = 0.0
     for g, (lev, nn) in enumerate(grays):
         c = np.full((nn, nn), lev, np.float32)
-        lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=n + g, save_acts=True)
+        lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=n + g, quant=quant, save_acts=True)
         r = O.anisotropy_loss(p[0], mode=las_mode, n_rad=n_rad, n_ang=n_ang, grad=True)
         l_as += r["loss"] / G
-        a, b = O.backward(c, ws, bs, seed, n + g, acts, lg, w_a * r["grad"] / G)
+        a, b = O.backward(c, ws, bs, seed, n + g, acts, lg, w_a * r["grad"] / G, quant=quant)
         for l in range(len(ws)):
             gw[l] += a[l]
             gb[l] += b[l]
-    return l_marl + w_a * l_as, l_marl, l_as, float(np.mean(rs)), gw, gb
+    return l_marl + w_a * l_as, l_marl, l_as, float(np.mean(rs)) if rs else 0.0, gw, gb
 
 
 @pytest.mark.parametrize("las_mode,n_rad,n_ang", [(0, 1, 1), (1, 4, 4)])
@@ -99,3 +99,88 @@ def test_autograd_function_drives_adam():
     opt.step()
     loss2 = api.HalftonePolicyFn.apply(w, b, tr, crops, [0.5], 3)
     assert torch.isfinite(loss2) and float(loss2) != float(loss)
+
+
+def _grad_errors(gw, gb, ref_w, ref_b):
+    """Per layer: max |error| of the weight and of the bias gradient, each over the
+    layer's largest reference gradient entry."""
+    gw = gw.cpu().numpy().astype(np.float64)
+    gb = gb.cpu().numpy().astype(np.float64)
+    ow = ob = 0
+    errs = []
+    for rw, rb in zip(ref_w, ref_b):
+        rw, rb = rw.ravel(), rb.ravel()
+        scale = max(np.abs(rw).max(), np.abs(rb).max())
+        errs.append((np.abs(gw[ow:ow + rw.size] - rw).max() / scale, np.abs(gb[ob:ob + rb.size] - rb).max() / scale))
+        ow += rw.size
+        ob += rb.size
+    return errs
+
+
+WIDE4 = (2, 64, 64, 64, 1)      # layer 1, a 64 -> 64 layer, the 64 -> 64 layer with the head partials, head
+
+
+def test_bf16_backward_anisotropy_only_matches_bf16_oracle():
+    """BF16 tensor-core backward without sampling: a step on two 128 x 128 gray patches
+    only, so dL/dp is w_a dL_AS/dp of the probability maps and every pass (head
+    backward, tcgen05 weight gradients, data gradients on the conv pipeline, layer-1
+    weight gradient) is compared with the oracle's quant-1 backward.  The remaining
+    differences start in the forward: where an activation's FP32 sum (GPU) and FP64 sum
+    (oracle) straddle a bf16 rounding boundary the two sides store values one bf16 ulp
+    apart, and through the depth of the net p differs by ~5e-4 typically, 4e-3 at most
+    (the BF16 forward bounds).  dL_AS/dp and the gradients inherit a relative
+    difference of that size: tolerance 3e-4 on L_AS and 6e-3 of the layer's largest
+    gradient entry (measured 9e-5 and 0.04-0.34%)."""
+    ws, _ = synth.he_normal_policy(WIDE4, 61)
+    bs = synth.random_biases(WIDE4, 62, scale=0.1)
+    levels = [0.35, 0.8]
+    gn, seed, w_a = 128, 11, 1.0
+    pol = api.Policy(WIDE4, ws, bs, precision=N.HT_BF16)
+    tr = api.Trainer(pol, (16, 16), max_crops=1, n_samples=1, n_gray=2, gray_n=gn, las_mode=1, n_rad=8, n_ang=8,
+                     w_a=w_a)
+    losses = tr.forward([], levels, seed)
+    gw, gb = tr.backward()
+    torch.cuda.synchronize()
+    ref = oracle_step([], [(l, gn) for l in levels], ws, bs, seed, 1, w_a, 1, 8, 8, quant=1)
+    errs = _grad_errors(gw, gb, ref[4], ref[5])
+    print("L_AS", losses[2], ref[2], "relative gradient errors (weights, biases) per layer:", errs)
+    assert abs(losses[2] - ref[2]) <= 3e-4 * abs(ref[2]), (losses, ref[:4])
+    assert losses[1] == 0.0 and losses[3] == 0.0
+    for ew, eb in errs:
+        assert ew <= 6e-3 and eb <= 6e-3, errs
+
+
+def test_bf16_train_step_matches_bf16_oracle():
+    """Full BF16 step (crops and gray patches) against the quant-1 oracle.  Crops 40 x 150:
+    two 128-pixel column tiles, one ragged, five 8-row units per crop.  The samples
+    h = [u < p] of the two sides differ wherever |p - u| is below the forward's BF16
+    error (a few of the 24 000 pixel-samples here), and each flip changes the toggle
+    deltas in its 21 x 21 neighbourhood; the loss is held to 1e-3 relative and the
+    gradients to 2e-2 of the layer's largest entry, which still catches any wiring error
+    of the step (measured: 0.6-0.8%)."""
+    ws, _ = synth.he_normal_policy(WIDE4, 51)
+    bs = synth.random_biases(WIDE4, 52, scale=0.1)
+    crops = [synth.contone_image(40, 150, seed=53, index=i) for i in range(2)]
+    levels = [0.3, 0.7]
+    gn, S, seed, w_a = 32, 2, 9, 0.5
+    pol = api.Policy(WIDE4, ws, bs, precision=N.HT_BF16)
+    tr = api.Trainer(pol, (40, 150), max_crops=2, n_samples=S, n_gray=2, gray_n=gn, las_mode=1, n_rad=4, n_ang=4,
+                     w_a=w_a)
+    losses = tr.forward([torch.from_numpy(c).cuda() for c in crops], levels, seed)
+    gw, gb = tr.backward()
+    torch.cuda.synchronize()
+    ref = oracle_step(crops, [(l, gn) for l in levels], ws, bs, seed, S, w_a, 1, 4, 4, quant=1)
+    errs = _grad_errors(gw, gb, ref[4], ref[5])
+    print("losses", losses, ref[:4], "relative gradient errors (weights, biases) per layer:", errs)
+    for k in range(4):
+        assert abs(losses[k] - ref[k]) <= 1e-3 * abs(ref[k]) + 1e-7, (k, losses, ref[:4])
+    for ew, eb in errs:
+        assert ew <= 2e-2 and eb <= 2e-2, errs
+
+
+def test_training_rejects_fp8_policies():
+    """Training runs in the FP32 form or the BF16 tensor-core form; an FP8 policy is refused."""
+    ws, bs = synth.he_normal_policy(WIDE4, 1)
+    pol = api.Policy(WIDE4, ws, bs, precision=N.HT_FP8_E4M3)
+    with pytest.raises(N.HTError):
+        api.Trainer(pol, (24, 24), max_crops=1, n_samples=1)
