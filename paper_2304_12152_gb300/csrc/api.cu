@@ -428,12 +428,8 @@ ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, int n,
     st = validate_images(c, n, 2 * opts->radius + 1);
     if (st != HT_OK) return st;
     HT_CHECK_ARG(bits && dR, "null argument");
-    size_t need = 0;
-    for (int i = 0; i < n; ++i) {
-        HT_CHECK_ARG(bits[i] && dR[i], "image %d: null pointer", i);
-        const size_t f = ht_toggle_scratch_floats(c[i].h, c[i].w, opts->radius);
-        need = f > need ? f : need;
-    }
+    for (int i = 0; i < n; ++i) HT_CHECK_ARG(bits[i] && dR[i], "image %d: null pointer", i);
+    const size_t need = ht_toggle_scratch_floats_batch(c, n, opts->radius);
     cudaStream_t s = (cudaStream_t)stream;
     float *scratch = nullptr;
     HT_CUDA_TRY(cudaMallocAsync((void **)&scratch, need * sizeof(float), s));

@@ -153,6 +153,7 @@ ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n
 ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
                            float *const *dR, float *scratch, size_t scratch_floats, cudaStream_t s);
 size_t ht_toggle_scratch_floats(int h, int w, int r);
+size_t ht_toggle_scratch_floats_batch(const ht_image *c, int n, int r);   // what ht_toggle_launch needs for c[0..n)
 
 // spectrum
 ht_status ht_las_launch(const float *q, int n_patches, int n, int mode, int n_rad, int n_ang, double *out_loss,

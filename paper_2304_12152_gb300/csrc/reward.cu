@@ -40,6 +40,21 @@ struct Win {
     float c1, c2, k, ws;
 };
 
+// Up to RW_MAXB images per launch, passed in the kernel parameter (blockIdx.z =
+// image); grid x / y cover the largest image, blocks past an image's extent exit.
+constexpr int RW_MAXB = 32;
+struct RwImg {
+    const float *c;
+    const uint32_t *bits;
+    float *maps;              // toggle deltas: NMAP moment maps of this image
+    float *dR;                // toggle deltas: output
+    double *acc;              // reward: 3 FP64 accumulators
+    int cpitch, H, W, words;
+};
+struct RwBatch {
+    RwImg im[RW_MAXB];
+};
+
 __device__ __forceinline__ float hbit(const uint32_t *bits, int words, int y, int x)
 {
     return (float)((bits[(size_t)y * words + (x >> 5)] >> (x & 31)) & 1u);
@@ -136,17 +151,19 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-__global__ void __launch_bounds__(256)
-k_reward_tiles(const float *__restrict__ c, int cpitch, const uint32_t *__restrict__ bits, int words, int H, int W,
-               Win wn, double *__restrict__ acc /* 3 doubles */)
+__global__ void __launch_bounds__(256) k_reward_tiles(const __grid_constant__ RwBatch B, const Win wn)
 {
     __shared__ float s_h[RT + 2 * MAXR][RT + 2 * MAXR];
     __shared__ float s_c[RT + 2 * MAXR][RT + 2 * MAXR];
     __shared__ float s_row[NQ][RT + 2 * MAXR][RT];
     __shared__ double s_red[3][8];
+    const RwImg &I = B.im[blockIdx.z];
+    if ((int)blockIdx.y * RT >= I.H - 2 * wn.r || (int)blockIdx.x * RT >= I.W - 2 * wn.r) return;
+    double *acc = I.acc;
     Moments m[4];
     bool valid[4];
-    tile_moments(c, cpitch, bits, words, H, W, wn, blockIdx.y * RT, blockIdx.x * RT, s_h, s_c, s_row, m, valid);
+    tile_moments(I.c, I.cpitch, I.bits, I.words, I.H, I.W, wn, blockIdx.y * RT, blockIdx.x * RT, s_h, s_c, s_row, m,
+                 valid);
     double se = 0.0, ss = 0.0, sc = 0.0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -191,18 +208,19 @@ __global__ void k_reward_finalize(const double *__restrict__ acc, int n, const d
 // 0 e, 1 mu_h, 2 mu_c, 3 var_c + C2, 4 cov, 5 sigma, 6 SSIM.
 constexpr int NMAP = 7;
 
-__global__ void __launch_bounds__(256)
-k_moment_maps(const float *__restrict__ c, int cpitch, const uint32_t *__restrict__ bits, int words, int H, int W,
-              Win wn, float *__restrict__ maps)
+__global__ void __launch_bounds__(256) k_moment_maps(const __grid_constant__ RwBatch B, const Win wn)
 {
     __shared__ float s_h[RT + 2 * MAXR][RT + 2 * MAXR];
     __shared__ float s_c[RT + 2 * MAXR][RT + 2 * MAXR];
     __shared__ float s_row[NQ][RT + 2 * MAXR][RT];
+    const RwImg &I = B.im[blockIdx.z];
+    const int VH = I.H - 2 * wn.r, VW = I.W - 2 * wn.r;
+    const int vy0 = blockIdx.y * RT, vx0 = blockIdx.x * RT;
+    if (vy0 >= VH || vx0 >= VW) return;
+    float *maps = I.maps;
     Moments m[4];
     bool valid[4];
-    const int vy0 = blockIdx.y * RT, vx0 = blockIdx.x * RT;
-    tile_moments(c, cpitch, bits, words, H, W, wn, vy0, vx0, s_h, s_c, s_row, m, valid);
-    const int VH = H - 2 * wn.r, VW = W - 2 * wn.r;
+    tile_moments(I.c, I.cpitch, I.bits, I.words, I.H, I.W, wn, vy0, vx0, s_h, s_c, s_row, m, valid);
     const size_t plane = (size_t)VH * VW;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -221,16 +239,21 @@ k_moment_maps(const float *__restrict__ c, int cpitch, const uint32_t *__restric
 
 constexpr int DTX = 32, DTY = 8;
 
-__global__ void __launch_bounds__(DTX *DTY)
-k_toggle_delta(const float *__restrict__ c, int cpitch, const uint32_t *__restrict__ bits, int words, int H, int W,
-               Win wn, const float *__restrict__ maps, float *__restrict__ dR)
+__global__ void __launch_bounds__(DTX *DTY) k_toggle_delta(const __grid_constant__ RwBatch B, const Win wn)
 {
     constexpr int SH = DTY + 2 * MAXR, SW = DTX + 2 * MAXR;
     __shared__ float s_m[NMAP][SH][SW];
+    const RwImg &I = B.im[blockIdx.z];
+    const float *__restrict__ c = I.c;
+    const uint32_t *__restrict__ bits = I.bits;
+    const float *__restrict__ maps = I.maps;
+    float *__restrict__ dR = I.dR;
+    const int cpitch = I.cpitch, H = I.H, W = I.W, words = I.words;
     const int r = wn.r;
     const int VH = H - 2 * r, VW = W - 2 * r;
     const size_t plane = (size_t)VH * VW;
     const int ay0 = blockIdx.y * DTY, ax0 = blockIdx.x * DTX;
+    if (ay0 >= H || ax0 >= W) return;
     const int tid = threadIdx.y * DTX + threadIdx.x;
     // stage maps for output positions j in [a0 - r, a0 + tile + r) (image coords)
     constexpr int NT = NMAP * SH * SW, NPER = (NT + DTX * DTY - 1) / (DTX * DTY);
@@ -304,6 +327,38 @@ Win make_win(const ht_reward_opts &o)
 
 }  // namespace
 
+namespace {
+RwImg rw_img(const ht_image &c, const uint32_t *bits)
+{
+    RwImg I{};
+    I.c = c.contone;
+    I.bits = bits;
+    I.cpitch = c.pitch;
+    I.H = c.h;
+    I.W = c.w;
+    I.words = ht_bits_row_words(c.w, 0);
+    return I;
+}
+
+// reward window sums of images [base, base + cnt) into acc[3 i] (launch only)
+ht_status launch_reward_tiles(const ht_image *c, const uint32_t *const *bits, int base, int cnt, const Win &wn,
+                              double *acc, cudaStream_t s)
+{
+    RwBatch B{};
+    int gx = 1, gy = 1;
+    for (int k = 0; k < cnt; ++k) {
+        const int i = base + k;
+        B.im[k] = rw_img(c[i], bits[i]);
+        B.im[k].acc = acc + 3 * (size_t)k;
+        gx = max(gx, (c[i].w - 2 * wn.r + RT - 1) / RT);
+        gy = max(gy, (c[i].h - 2 * wn.r + RT - 1) / RT);
+    }
+    k_reward_tiles<<<dim3(gx, gy, cnt), dim3(32, 8), 0, s>>>(B, wn);
+    HT_LAUNCH_CHECK();
+    return HT_OK;
+}
+}  // namespace
+
 ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
                            double *out, cudaStream_t s)
 {
@@ -317,13 +372,12 @@ ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n
     cudaError_t ce = cudaMemcpyAsync(acc + 3 * n, inv_m_h, sizeof(double) * n, cudaMemcpyHostToDevice, s);
     free(inv_m_h);
     HT_CUDA_TRY(ce);
-    for (int i = 0; i < n; ++i) {
-        const int VH = c[i].h - 2 * o.radius, VW = c[i].w - 2 * o.radius;
-        const dim3 grid((VW + RT - 1) / RT, (VH + RT - 1) / RT);
-        k_reward_tiles<<<grid, dim3(32, 8), 0, s>>>(c[i].contone, c[i].pitch, bits[i], ht_bits_row_words(c[i].w, 0),
-                                                    c[i].h, c[i].w, wn, acc + 3 * i);
-        HT_LAUNCH_CHECK();
+    ht_prof_start(HTK_REWARD, s);
+    for (int base = 0; base < n; base += RW_MAXB) {
+        const ht_status st = launch_reward_tiles(c, bits, base, min(RW_MAXB, n - base), wn, acc + 3 * (size_t)base, s);
+        if (st != HT_OK) return st;
     }
+    ht_prof_stop(s);
     k_reward_finalize<<<(n + 127) / 128, 128, 0, s>>>(acc, n, acc + 3 * n, o.w_s, out);
     HT_LAUNCH_CHECK();
     HT_CUDA_TRY(cudaFreeAsync(acc, s));
@@ -334,24 +388,49 @@ ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, int n
                            float *const *dR, float *scratch, size_t scratch_floats, cudaStream_t s)
 {
     const Win wn = make_win(o);
-    for (int i = 0; i < n; ++i) {
-        const int H = c[i].h, W = c[i].w, VH = H - 2 * o.radius, VW = W - 2 * o.radius;
-        if ((size_t)NMAP * VH * VW > scratch_floats) {
+    for (int base = 0; base < n; base += RW_MAXB) {
+        const int cnt = min(RW_MAXB, n - base);
+        RwBatch B{};
+        size_t off = 0;
+        int gx = 1, gy = 1, tx = 1, ty = 1;
+        for (int k = 0; k < cnt; ++k) {
+            const int i = base + k;
+            const int VH = c[i].h - 2 * o.radius, VW = c[i].w - 2 * o.radius;
+            B.im[k] = rw_img(c[i], bits[i]);
+            B.im[k].maps = scratch + off;
+            B.im[k].dR = dR[i];
+            off += (size_t)NMAP * VH * VW;
+            gx = max(gx, (VW + RT - 1) / RT);
+            gy = max(gy, (VH + RT - 1) / RT);
+            tx = max(tx, (c[i].w + DTX - 1) / DTX);
+            ty = max(ty, (c[i].h + DTY - 1) / DTY);
+        }
+        if (off > scratch_floats) {
             ht_set_error("toggle-delta scratch too small");
             return HT_ERR_INVALID_ARG;
         }
-        const int words = ht_bits_row_words(W, 0);
-        k_moment_maps<<<dim3((VW + RT - 1) / RT, (VH + RT - 1) / RT), dim3(32, 8), 0, s>>>(
-            c[i].contone, c[i].pitch, bits[i], words, H, W, wn, scratch);
+        ht_prof_start(HTK_TOGGLE, s);
+        k_moment_maps<<<dim3(gx, gy, cnt), dim3(32, 8), 0, s>>>(B, wn);
         HT_LAUNCH_CHECK();
-        k_toggle_delta<<<dim3((W + DTX - 1) / DTX, (H + DTY - 1) / DTY), dim3(DTX, DTY), 0, s>>>(
-            c[i].contone, c[i].pitch, bits[i], words, H, W, wn, scratch, dR[i]);
+        k_toggle_delta<<<dim3(tx, ty, cnt), dim3(DTX, DTY), 0, s>>>(B, wn);
+        ht_prof_stop(s);
         HT_LAUNCH_CHECK();
     }
     return HT_OK;
 }
 
 size_t ht_toggle_scratch_floats(int h, int w, int r) { return (size_t)NMAP * (h - 2 * r) * (w - 2 * r); }
+
+size_t ht_toggle_scratch_floats_batch(const ht_image *c, int n, int r)
+{
+    size_t best = 0;
+    for (int base = 0; base < n; base += RW_MAXB) {
+        size_t sum = 0;
+        for (int i = base; i < n && i < base + RW_MAXB; ++i) sum += ht_toggle_scratch_floats(c[i].h, c[i].w, r);
+        best = sum > best ? sum : best;
+    }
+    return best;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free reward.
@@ -435,12 +514,9 @@ extern "C" ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const 
     cudaStream_t s = (cudaStream_t)stream;
     const Win wn = make_win(*opts);
     HT_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)n, s));
-    for (int i = 0; i < n; ++i) {
-        const int VH = c[i].h - 2 * r, VW = c[i].w - 2 * r;
-        const dim3 grid((VW + RT - 1) / RT, (VH + RT - 1) / RT);
-        k_reward_tiles<<<grid, dim3(32, 8), 0, s>>>(c[i].contone, c[i].pitch, bits[i], ht_bits_row_words(c[i].w, 0),
-                                                    c[i].h, c[i].w, wn, acc + 3 * i);
-        HT_LAUNCH_CHECK();
+    for (int base = 0; base < n; base += RW_MAXB) {
+        const ht_status st = launch_reward_tiles(c, bits, base, min(RW_MAXB, n - base), wn, acc + 3 * (size_t)base, s);
+        if (st != HT_OK) return st;
     }
     for (int base = 0; base < n; base += 64) {
         const int count = n - base < 64 ? n - base : 64;

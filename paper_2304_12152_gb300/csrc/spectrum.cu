@@ -134,9 +134,13 @@ __global__ void k_bin_accum(const float2 *__restrict__ C, int n, int mode, int n
 // one CTA per patch: per-bin coefficients for G(f) and (mode 1) the loss.
 // coef[patch][nb]: mode 0 -> ring mean (NaN when the ring is skipped);
 //                  mode 1 -> dL/da_k / n_k ; coefm[patch][n_rad] -> dL/dm / n_rho
-__global__ void k_bin_finalize(const double *__restrict__ sums, const int *__restrict__ cnt, int mode, int n_rad,
-                               int n_ang, int nb, double *__restrict__ coef, double *__restrict__ coefm,
-                               double *__restrict__ loss)
+// Mode 1: one warp per radial bin (lanes over angular bins), then the loss as an
+// ordered sum over radial bins by thread 0.
+constexpr int FIN_MAX_RAD = 256;                 // largest n_rad the entry points accept
+__global__ void __launch_bounds__(1024) k_bin_finalize(const double *__restrict__ sums, const int *__restrict__ cnt,
+                                                       int mode, int n_rad, int n_ang, int nb,
+                                                       double *__restrict__ coef, double *__restrict__ coefm,
+                                                       double *__restrict__ loss)
 {
     const size_t pb = (size_t)blockIdx.x * nb;
     if (mode == 0) {
@@ -144,40 +148,81 @@ __global__ void k_bin_finalize(const double *__restrict__ sums, const int *__res
             coef[pb + i] = cnt[pb + i] >= 2 ? sums[pb + i] / cnt[pb + i] : (double)NAN;
         return;
     }
-    // mode 1: serial over radial bins (n_rad small)
-    if (threadIdx.x != 0) return;
-    int n_used = 0;
-    for (int br = 0; br < n_rad; ++br) {
-        int K = 0;
-        for (int bt = 0; bt < n_ang; ++bt) K += cnt[pb + br * n_ang + bt] > 0;
-        if (K >= 2) n_used++;
-    }
-    double L = 0.0;
-    for (int br = 0; br < n_rad; ++br) {
+    __shared__ int s_used[FIN_MAX_RAD];
+    __shared__ double s_term[FIN_MAX_RAD];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // per radial bin: total, count, occupied angular bins
+    for (int br = warp; br < n_rad; br += nw) {
         double tot = 0.0;
         int c = 0, K = 0;
-        for (int bt = 0; bt < n_ang; ++bt) {
+        for (int bt = lane; bt < n_ang; bt += 32) {
             tot += sums[pb + br * n_ang + bt];
             c += cnt[pb + br * n_ang + bt];
             K += cnt[pb + br * n_ang + bt] > 0;
         }
-        coefm[(size_t)blockIdx.x * n_rad + br] = 0.0;
-        for (int bt = 0; bt < n_ang; ++bt) coef[pb + br * n_ang + bt] = 0.0;
-        if (K < 2) continue;
-        const double m = tot / c;
-        double A = 0.0, dm = 0.0;
-        for (int bt = 0; bt < n_ang; ++bt) {
-            const int j = br * n_ang + bt;
-            if (cnt[pb + j] == 0) continue;
-            const double ak = sums[pb + j] / cnt[pb + j];
-            A += (ak - m) * (ak - m);
-            coef[pb + j] = 2.0 * (ak - m) / (m * m) / (K - 1) / cnt[pb + j] / n_used;
-            dm += (-2.0 * (ak - m) / (m * m) - 2.0 * (ak - m) * (ak - m) / (m * m * m)) / (K - 1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            K += __shfl_xor_sync(0xffffffffu, K, o);
         }
-        L += A / ((double)(K - 1) * m * m);
-        coefm[(size_t)blockIdx.x * n_rad + br] = dm / c / n_used;
+        if (lane == 0) s_used[br] = K >= 2 ? 1 : 0;
     }
-    loss[blockIdx.x] = n_used > 0 ? L / n_used : 0.0;
+    __syncthreads();
+    int n_used = 0;
+    for (int br = 0; br < n_rad; ++br) n_used += s_used[br];
+    for (int br = warp; br < n_rad; br += nw) {
+        double tot = 0.0;
+        int c = 0, K = 0;
+        for (int bt = lane; bt < n_ang; bt += 32) {
+            tot += sums[pb + br * n_ang + bt];
+            c += cnt[pb + br * n_ang + bt];
+            K += cnt[pb + br * n_ang + bt] > 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            K += __shfl_xor_sync(0xffffffffu, K, o);
+        }
+        if (K < 2) {
+            for (int bt = lane; bt < n_ang; bt += 32) coef[pb + br * n_ang + bt] = 0.0;
+            if (lane == 0) {
+                coefm[(size_t)blockIdx.x * n_rad + br] = 0.0;
+                s_term[br] = 0.0;
+            }
+            continue;
+        }
+        const double m = tot / c, im = 1.0 / m, iK1 = 1.0 / (K - 1), iu = 1.0 / n_used;
+        double A = 0.0, dm = 0.0;
+        for (int bt = lane; bt < n_ang; bt += 32) {
+            const int j = br * n_ang + bt;
+            const int cj = cnt[pb + j];
+            double cf = 0.0;
+            if (cj > 0) {
+                const double ak = sums[pb + j] / cj, d = (ak - m) * im;   // (a_k - m) / m
+                A += d * d;
+                cf = 2.0 * d * im * iK1 / cj * iu;
+                dm += (-2.0 * d * im - 2.0 * d * d * im) * iK1;
+            }
+            coef[pb + j] = cf;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            A += __shfl_xor_sync(0xffffffffu, A, o);
+            dm += __shfl_xor_sync(0xffffffffu, dm, o);
+        }
+        if (lane == 0) {
+            coefm[(size_t)blockIdx.x * n_rad + br] = dm / c * iu;
+            s_term[br] = A * iK1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double L = 0.0;
+        for (int br = 0; br < n_rad; ++br) L += s_term[br];
+        loss[blockIdx.x] = n_used > 0 ? L / n_used : 0.0;
+    }
 }
 
 // G(f) F(f) into C (in place); mode 0 also accumulates the loss.
@@ -240,6 +285,10 @@ ht_status ht_las_launch(const float *q, int n_patches, int n, int mode, int n_ra
     const int logn = ilog2(n);
     const int n_rings = (int)lround(sqrt(2.0) * (n / 2)) + 2;
     const int nb = mode == 0 ? n_rings : n_rad * n_ang;
+    if (mode == 1 && (n_rad < 1 || n_rad > FIN_MAX_RAD)) {
+        ht_set_error("n_rad out of range");
+        return HT_ERR_INVALID_ARG;
+    }
     if (scratch_bytes < ht_las_scratch_bytes(n_patches, n, n_rad, n_ang)) {
         ht_set_error("spectrum scratch too small");
         return HT_ERR_INVALID_ARG;
@@ -268,7 +317,7 @@ ht_status ht_las_launch(const float *q, int n_patches, int n, int mode, int n_ra
     const size_t bin_smem = (size_t)nb * (sizeof(double) + sizeof(int));
     k_bin_accum<<<dim3(nblk, n_patches), 256, bin_smem, s>>>(C, n, mode, n_rad, n_ang, nb, sums, cnt);
     HT_LAUNCH_CHECK();
-    k_bin_finalize<<<n_patches, 128, 0, s>>>(sums, cnt, mode, n_rad, n_ang, nb, coef, coefm, out_loss);
+    k_bin_finalize<<<n_patches, 1024, 0, s>>>(sums, cnt, mode, n_rad, n_ang, nb, coef, coefm, out_loss);
     HT_LAUNCH_CHECK();
     k_apply_G<<<dim3(nblk, n_patches), 256, 0, s>>>(C, n, mode, n_rad, n_ang, nb, coef, coefm, out_loss,
                                                     grad != nullptr);

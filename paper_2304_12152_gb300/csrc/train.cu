@@ -64,13 +64,17 @@ __global__ void k_fill(float *p, size_t n, float v)
 }
 
 // h^s = [u^s < p], u^s from Philox stream 1 + s; packed LSB-first, 32 px per warp.
-__global__ void k_sample_bits(const float *__restrict__ prob, int H, int W, int words, uint64_t seed, uint32_t image,
-                              uint32_t stream, uint32_t *__restrict__ bits)
+// blockIdx.z = i S + s over all crops i (probability maps px apart) and samples s.
+__global__ void k_sample_bits(const float *__restrict__ prob0, size_t px, int H, int W, int words, uint64_t seed, int S,
+                              uint32_t *__restrict__ bits0)
 {
+    const int z = blockIdx.z, i = z / S, sm = z % S;
+    const float *prob = prob0 + (size_t)i * px;
+    uint32_t *bits = bits0 + (size_t)z * H * words;
     const int y = blockIdx.y, x0 = blockIdx.x * 32, x = x0 + threadIdx.x;
     bool h = false;
     if (x < W) {
-        const float u = ht_uniform24(seed, image, stream, (uint64_t)y * W + x);
+        const float u = ht_uniform24(seed, (uint32_t)i, 1u + (uint32_t)sm, (uint64_t)y * W + x);
         h = u < prob[(size_t)y * W + x];
     }
     const uint32_t word = __ballot_sync(0xffffffffu, h);
@@ -78,11 +82,18 @@ __global__ void k_sample_bits(const float *__restrict__ prob, int H, int W, int 
 }
 
 // dp_a = -inv * sum_s dR^s_a; L += -inv * sum_s sum_a (R_s + (p_a - h_a) dR_a)
-__global__ void k_marl(const float *__restrict__ prob, const float *__restrict__ dR, const uint32_t *__restrict__ bits,
-                       const double *__restrict__ rewards, int S, int H, int W, int words, double inv,
-                       float *__restrict__ dprob, double *__restrict__ loss)
+// blockIdx.y = crop i (maps npx apart; S samples per crop).
+__global__ void k_marl(const float *__restrict__ prob0, const float *__restrict__ dR0, const uint32_t *__restrict__ bits0,
+                       const double *__restrict__ rewards0, int S, int H, int W, int words, double inv,
+                       float *__restrict__ dprob0, double *__restrict__ loss)
 {
     const size_t npx = (size_t)H * W;
+    const int i = blockIdx.y;
+    const float *prob = prob0 + (size_t)i * npx;
+    const float *dR = dR0 + (size_t)i * S * npx;
+    const uint32_t *bits = bits0 + (size_t)i * S * H * words;
+    const double *rewards = rewards0 + (size_t)i * S * 4;
+    float *dprob = dprob0 + (size_t)i * npx;
     const size_t a = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
     if (a < npx) {
@@ -228,6 +239,8 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
         HT_CHECK_ARG(d->gray_n >= 8 && d->gray_n <= 1024 && (d->gray_n & (d->gray_n - 1)) == 0,
                      "gray_n must be a power of two in [8, 1024]");
     HT_CHECK_ARG(d->las_mode == 0 || d->las_mode == 1, "las_mode must be 0 or 1");
+    if (d->las_mode == 1)
+        HT_CHECK_ARG(d->n_rad >= 1 && d->n_rad <= 256 && d->n_ang >= 2 && d->n_ang <= 64, "bad bin counts");
     HT_CHECK_ARG(d->reward.radius >= 1 && d->reward.radius <= 7, "reward radius must be in [1, 7]");
     ht_train *t = new ht_train();
     t->p = p;
@@ -251,7 +264,10 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
         const size_t n = (size_t)p->ch[l] * p->ch[l + 1] * 9;
         wmax = n > wmax ? n : wmax;
     }
-    t->toggle_scratch_floats = ht_toggle_scratch_floats(d->crop_h, d->crop_w, d->reward.radius);
+    {
+        const int batch = B * S < 32 ? B * S : 32;       // ht_toggle_launch works in batches of up to 32 images
+        t->toggle_scratch_floats = (size_t)batch * ht_toggle_scratch_floats(d->crop_h, d->crop_w, d->reward.radius);
+    }
     t->las_scratch_bytes = G > 0 ? ht_las_scratch_bytes(G, d->gray_n, t->d.n_rad, t->d.n_ang) : 0;
     const int gmax = (int)(d->crop_h > d->gray_n ? d->crop_h : d->gray_n);
     const int words_max = ht_bits_row_words(d->crop_w > d->gray_n ? d->crop_w : d->gray_n, HT_HEAD_SIGMOID);
@@ -398,27 +414,27 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
     }
     // 2.-4. samples, rewards, toggle deltas, L_MARL and its gradient
     double *rewards = t->dacc + 1 + G;
-    for (int i = 0; i < n; ++i) {
-        const float *pr = t->prob + img_px_offset(t, i);
-        std::vector<ht_image> cimg(S, crops[i]);
-        std::vector<const uint32_t *> bp(S);
-        std::vector<float *> dp(S);
-        for (int sm = 0; sm < S; ++sm) {
-            uint32_t *b = t->sbits + ((size_t)i * S + sm) * H * words;
-            k_sample_bits<<<dim3(words, H), 32, 0, s>>>(pr, H, W, words, seed, (uint32_t)i, 1u + sm, b);
-            HT_LAUNCH_CHECK();
-            bp[sm] = b;
-            dp[sm] = t->dR + ((size_t)i * S + sm) * t->crop_px;
-        }
-        ht_status st = ht_reward_launch(cimg.data(), bp.data(), S, t->d.reward, rewards + (size_t)i * S * 4, s);
+    if (n > 0) {
+        // all crops x samples in one launch per kernel (reward / toggle deltas in batches)
+        k_sample_bits<<<dim3(words, H, n * S), 32, 0, s>>>(t->prob, t->crop_px, H, W, words, seed, S, t->sbits);
+        HT_LAUNCH_CHECK();
+        std::vector<ht_image> cimg((size_t)n * S);
+        std::vector<const uint32_t *> bp((size_t)n * S);
+        std::vector<float *> dp((size_t)n * S);
+        for (int i = 0; i < n; ++i)
+            for (int sm = 0; sm < S; ++sm) {
+                const size_t k = (size_t)i * S + sm;
+                cimg[k] = crops[i];
+                bp[k] = t->sbits + k * H * words;
+                dp[k] = t->dR + k * t->crop_px;
+            }
+        ht_status st = ht_reward_launch(cimg.data(), bp.data(), n * S, t->d.reward, rewards, s);
         if (st != HT_OK) return st;
-        st = ht_toggle_launch(cimg.data(), bp.data(), S, t->d.reward, dp.data(), t->toggle_scratch,
+        st = ht_toggle_launch(cimg.data(), bp.data(), n * S, t->d.reward, dp.data(), t->toggle_scratch,
                               t->toggle_scratch_floats, s);
         if (st != HT_OK) return st;
-        k_marl<<<nblk(t->crop_px), 256, 0, s>>>(pr, t->dR + (size_t)i * S * t->crop_px,
-                                                  t->sbits + (size_t)i * S * H * words, rewards + (size_t)i * S * 4, S,
-                                                  H, W, words, 1.0 / ((double)n * S), t->dprob + img_px_offset(t, i),
-                                                  t->dacc);
+        k_marl<<<dim3(nblk(t->crop_px), n), 256, 0, s>>>(t->prob, t->dR, t->sbits, rewards, S, H, W, words,
+                                                         1.0 / ((double)n * S), t->dprob, t->dacc);
         HT_LAUNCH_CHECK();
     }
     // 5. anisotropy loss on the gray patches' probability maps

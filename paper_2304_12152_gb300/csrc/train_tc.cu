@@ -346,9 +346,15 @@ __global__ void k_reduce_wgrad_tc(const float *__restrict__ partials, const floa
         const int dx = t >> 1, pair = t & 1;
         if (pair == 1 && lane >= 64) return;               // rows of no tap
         const int dy = pair ? 2 : (lane >> 6), c = lane & 63;
-        double s = 0.0;
-        for (int k = 0; k < ncta; ++k) s += (double)partials[(size_t)k * WG_TILES * 64 * 128 + i];
-        gw[((n * 64 + c) * 3 + dy) * 3 + dx] = (float)s;
+        double s[4] = {0.0, 0.0, 0.0, 0.0};              // CTA k goes to s[k % 4]; fixed order
+        const size_t st = (size_t)WG_TILES * 64 * 128;
+        int k = 0;
+        for (; k + 4 <= ncta; k += 4) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s[j] += (double)partials[(size_t)(k + j) * st + i];
+        }
+        for (; k < ncta; ++k) s[k & 3] += (double)partials[(size_t)k * st + i];
+        gw[((n * 64 + c) * 3 + dy) * 3 + dx] = (float)((s[0] + s[1]) + (s[2] + s[3]));
     } else if (i < WG_TILES * 64 * 128 + 64) {
         const int n = i - WG_TILES * 64 * 128;
         double s = 0.0;
@@ -379,67 +385,84 @@ __global__ void k_pack_dgrad(const float *__restrict__ w, __nv_bfloat16 *__restr
 // ---------------------------------------------------------------------------
 struct HeadBwdParams {
     const ImgDesc *imgs;
-    int n_imgs;
+    int n_imgs, n_tiles;
     float w[9 * 64];          // [tap][c]
-    float *partials;
+    float *partials;          // [gridDim.x][577]
 };
 
+// Persistent: block b handles tiles b, b + grid, ...; its weight-gradient sums stay
+// in registers across tiles and are written once.
 __global__ void __launch_bounds__(HT_X *HT_Y) k_head_bwd(const HeadBwdParams P)
 {
     __shared__ float s_dz[HT_Y + 2][HT_X + 2];
     __shared__ __align__(16) __nv_bfloat16 s_a[(HT_Y + 2) * (HT_X + 2) * 64];
-    const int im = find_image(P.n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&P.imgs[i].hd_begin); });
-    const ImgDesc *D = P.imgs + im;
-    const int lt = (int)blockIdx.x - D->hd_begin;
-    const int H = D->H, W = D->W;
-    const int hx = (W + HT_X - 1) / HT_X;
-    const int x0 = (lt % hx) * HT_X, y0 = (lt / hx) * HT_Y;
     const int tid = threadIdx.y * HT_X + threadIdx.x;
-    const float *dz = D->prob;
-    const uint8_t *a = D->act[0];
-    for (int k = tid; k < (HT_Y + 2) * (HT_X + 2); k += HT_X * HT_Y) {
-        const int yy = y0 - 1 + k / (HT_X + 2), xx = x0 - 1 + k % (HT_X + 2);
-        s_dz[k / (HT_X + 2)][k % (HT_X + 2)] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? dz[(size_t)yy * W + xx] : 0.f;
-    }
-    for (int k = tid; k < (HT_Y + 2) * (HT_X + 2) * 8; k += HT_X * HT_Y) {
-        const int chunk = k % 8, p = k / 8;
-        const int yy = y0 - 1 + p / (HT_X + 2), xx = x0 - 1 + p % (HT_X + 2);
-        uint4 q = make_uint4(0, 0, 0, 0);
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-            q = *reinterpret_cast<const uint4 *>(a + (((size_t)chunk * H + yy) * W + xx) * 16);
-        *reinterpret_cast<uint4 *>(&s_a[(size_t)p * 64 + chunk * 8]) = q;
-    }
-    __syncthreads();
-    // data gradient at this thread's pixel
-    const int y = y0 + threadIdx.y, x = x0 + threadIdx.x;
-    if (y < H && x < W) {
-        float d[9];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) d[t] = s_dz[threadIdx.y + 2 - t / 3][threadIdx.x + 2 - t % 3];
-        const uint2 m = D->mask[(size_t)y * W + x];
-        float g[64];
-#pragma unroll
-        for (int c = 0; c < 64; ++c) {
-            float acc = 0.f;
-#pragma unroll
-            for (int t = 0; t < 9; ++t) acc = fmaf(P.w[t * 64 + c], d[t], acc);
-            g[c] = (((c < 32 ? m.x : m.y) >> (c & 31)) & 1u) ? acc : 0.f;
+    float wacc[3] = {0.f, 0.f, 0.f};                    // entries tid, tid + 256, tid + 512 (< 577)
+    for (int tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x) {
+        const int im = find_image(P.n_imgs, tile, [&](int i) { return __ldg(&P.imgs[i].hd_begin); });
+        const ImgDesc *D = P.imgs + im;
+        const int lt = tile - D->hd_begin;
+        const int H = D->H, W = D->W;
+        const int hx = (W + HT_X - 1) / HT_X;
+        const int x0 = (lt % hx) * HT_X, y0 = (lt / hx) * HT_Y;
+        const float *dz = D->prob;
+        const uint8_t *a = D->act[0];
+        __syncthreads();                                 // previous tile's shared reads are done
+        for (int k = tid; k < (HT_Y + 2) * (HT_X + 2); k += HT_X * HT_Y) {
+            const int yy = y0 - 1 + k / (HT_X + 2), xx = x0 - 1 + k % (HT_X + 2);
+            s_dz[k / (HT_X + 2)][k % (HT_X + 2)] =
+                (yy >= 0 && yy < H && xx >= 0 && xx < W) ? dz[(size_t)yy * W + xx] : 0.f;
         }
-        store_pixel(g, D->act[1], 0, 1.f, H, W, y, x);
-    }
-    // weight and bias gradient partial sums of this tile
-    for (int idx = tid; idx < 577; idx += HT_X * HT_Y) {
-        float s = 0.f;
-        if (idx < 576) {
-            const int c = idx % 64, t = idx / 64, dy = t / 3, dx = t % 3;
-            for (int py = 0; py < HT_Y; ++py)
-                for (int px = 0; px < HT_X; ++px)
-                    s = fmaf(s_dz[py + 1][px + 1], __bfloat162float(s_a[((py + dy) * (HT_X + 2) + px + dx) * 64 + c]), s);
-        } else {
-            for (int py = 0; py < HT_Y; ++py)
-                for (int px = 0; px < HT_X; ++px) s += s_dz[py + 1][px + 1];
+        for (int k = tid; k < (HT_Y + 2) * (HT_X + 2) * 8; k += HT_X * HT_Y) {
+            const int chunk = k % 8, p = k / 8;
+            const int yy = y0 - 1 + p / (HT_X + 2), xx = x0 - 1 + p % (HT_X + 2);
+            uint4 q = make_uint4(0, 0, 0, 0);
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                q = *reinterpret_cast<const uint4 *>(a + (((size_t)chunk * H + yy) * W + xx) * 16);
+            *reinterpret_cast<uint4 *>(&s_a[(size_t)p * 64 + chunk * 8]) = q;
         }
-        P.partials[(size_t)blockIdx.x * 577 + idx] = s;
+        __syncthreads();
+        // data gradient at this thread's pixel
+        const int y = y0 + threadIdx.y, x = x0 + threadIdx.x;
+        if (y < H && x < W) {
+            float d[9];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) d[t] = s_dz[threadIdx.y + 2 - t / 3][threadIdx.x + 2 - t % 3];
+            const uint2 m = D->mask[(size_t)y * W + x];
+            float g[64];
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) acc = fmaf(P.w[t * 64 + c], d[t], acc);
+                g[c] = (((c < 32 ? m.x : m.y) >> (c & 31)) & 1u) ? acc : 0.f;
+            }
+            store_pixel(g, D->act[1], 0, 1.f, H, W, y, x);
+        }
+        // weight and bias gradient sums of this tile
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int idx = tid + r * HT_X * HT_Y;
+            if (idx < 576) {
+                const int c = idx % 64, t = idx / 64, dy = t / 3, dx = t % 3;
+                float s = 0.f;
+                for (int py = 0; py < HT_Y; ++py)
+#pragma unroll 8
+                    for (int px = 0; px < HT_X; ++px)
+                        s = fmaf(s_dz[py + 1][px + 1], __bfloat162float(s_a[((py + dy) * (HT_X + 2) + px + dx) * 64 + c]), s);
+                wacc[r] += s;
+            } else if (idx == 576) {
+                float s = 0.f;
+                for (int py = 0; py < HT_Y; ++py)
+                    for (int px = 0; px < HT_X; ++px) s += s_dz[py + 1][px + 1];
+                wacc[r] += s;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int idx = tid + r * HT_X * HT_Y;
+        if (idx < 577) P.partials[(size_t)blockIdx.x * 577 + idx] = wacc[r];
     }
 }
 
@@ -450,57 +473,76 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_bwd(const HeadBwdParams P)
 //   dW[n][ci][dy][dx] += sum g[n](y,x) x_ci(y + dy - 1, x + dx - 1); db[n] += sum g[n]
 // partials[block][1152 + 64] with weight entry (ci*9 + tap)*64 + n.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(HT_X *HT_Y) k_first_wgrad(const ImgDesc *__restrict__ imgs, int n_imgs, uint64_t seed,
-                                                           float *__restrict__ partials)
+__global__ void __launch_bounds__(HT_X *HT_Y) k_first_wgrad(const ImgDesc *__restrict__ imgs, int n_imgs, int n_tiles,
+                                                           uint64_t seed, float *__restrict__ partials)
 {
     __shared__ float s_x[2][HT_Y + 2][HT_X + 2];
     __shared__ __align__(16) __nv_bfloat16 s_g[HT_Y * HT_X * 64];
-    const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].hd_begin); });
-    const ImgDesc *D = imgs + im;
-    const int lt = (int)blockIdx.x - D->hd_begin;
-    const int H = D->H, W = D->W;
-    const int hx = (W + HT_X - 1) / HT_X;
-    const int x0 = (lt % hx) * HT_X, y0 = (lt / hx) * HT_Y;
     const int tid = threadIdx.y * HT_X + threadIdx.x;
-    for (int k = tid; k < (HT_Y + 2) * (HT_X + 2); k += HT_X * HT_Y) {
-        const int r = k / (HT_X + 2), q = k % (HT_X + 2);
-        const int yy = y0 - 1 + r, xx = x0 - 1 + q;
-        const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
-        s_x[0][r][q] = in ? D->contone[(size_t)yy * D->cpitch + xx] : 0.f;
-        s_x[1][r][q] = in ? ht_uniform24(seed, D->image, 0u, (uint64_t)yy * W + xx) : 0.f;
-    }
-    for (int k = tid; k < HT_Y * HT_X * 8; k += HT_X * HT_Y) {
-        const int chunk = k % 8, p = k / 8;
-        const int yy = y0 + p / HT_X, xx = x0 + p % HT_X;
-        uint4 q = make_uint4(0, 0, 0, 0);
-        if (yy < H && xx < W) q = *reinterpret_cast<const uint4 *>(D->act[0] + (((size_t)chunk * H + yy) * W + xx) * 16);
-        *reinterpret_cast<uint4 *>(&s_g[(size_t)p * 64 + chunk * 8]) = q;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < 1152 + 64; idx += HT_X * HT_Y) {
-        float s = 0.f;
-        if (idx < 1152) {
-            const int n = idx % 64, k = idx / 64, ci = k / 9, t = k % 9, dy = t / 3, dx = t % 3;
-            for (int py = 0; py < HT_Y; ++py)
-                for (int px = 0; px < HT_X; ++px)
-                    s = fmaf(__bfloat162float(s_g[(py * HT_X + px) * 64 + n]), s_x[ci][py + dy][px + dx], s);
-        } else {
-            const int n = idx - 1152;
-            for (int p = 0; p < HT_Y * HT_X; ++p) s += __bfloat162float(s_g[p * 64 + n]);
+    float wacc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};          // entries tid + 256 r (< 1216)
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int im = find_image(n_imgs, tile, [&](int i) { return __ldg(&imgs[i].hd_begin); });
+        const ImgDesc *D = imgs + im;
+        const int lt = tile - D->hd_begin;
+        const int H = D->H, W = D->W;
+        const int hx = (W + HT_X - 1) / HT_X;
+        const int x0 = (lt % hx) * HT_X, y0 = (lt / hx) * HT_Y;
+        __syncthreads();
+        for (int k = tid; k < (HT_Y + 2) * (HT_X + 2); k += HT_X * HT_Y) {
+            const int r = k / (HT_X + 2), q = k % (HT_X + 2);
+            const int yy = y0 - 1 + r, xx = x0 - 1 + q;
+            const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            s_x[0][r][q] = in ? D->contone[(size_t)yy * D->cpitch + xx] : 0.f;
+            s_x[1][r][q] = in ? ht_uniform24(seed, D->image, 0u, (uint64_t)yy * W + xx) : 0.f;
         }
-        partials[(size_t)blockIdx.x * 1216 + idx] = s;
+        for (int k = tid; k < HT_Y * HT_X * 8; k += HT_X * HT_Y) {
+            const int chunk = k % 8, p = k / 8;
+            const int yy = y0 + p / HT_X, xx = x0 + p % HT_X;
+            uint4 q = make_uint4(0, 0, 0, 0);
+            if (yy < H && xx < W) q = *reinterpret_cast<const uint4 *>(D->act[0] + (((size_t)chunk * H + yy) * W + xx) * 16);
+            *reinterpret_cast<uint4 *>(&s_g[(size_t)p * 64 + chunk * 8]) = q;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            const int idx = tid + r * HT_X * HT_Y;
+            float s = 0.f;
+            if (idx < 1152) {
+                const int n = idx % 64, k = idx / 64, ci = k / 9, t = k % 9, dy = t / 3, dx = t % 3;
+                for (int py = 0; py < HT_Y; ++py)
+#pragma unroll 8
+                    for (int px = 0; px < HT_X; ++px)
+                        s = fmaf(__bfloat162float(s_g[(py * HT_X + px) * 64 + n]), s_x[ci][py + dy][px + dx], s);
+            } else if (idx < 1216) {
+                const int n = idx - 1152;
+                for (int p = 0; p < HT_Y * HT_X; ++p) s += __bfloat162float(s_g[p * 64 + n]);
+            }
+            wacc[r] += s;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const int idx = tid + r * HT_X * HT_Y;
+        if (idx < 1216) partials[(size_t)blockIdx.x * 1216 + idx] = wacc[r];
     }
 }
 
-// Sum of per-block partials (FP64, block order).  mode 0: head, entries [tap][c]
-// + bias; mode 1: layer 1, entries [(ci*9 + tap)][n] + 64 biases.
-__global__ void k_reduce_blocks(const float *__restrict__ partials, int nblk, int nval, int mode, float *__restrict__ gw,
-                                float *__restrict__ gb)
+// Sum of per-block partials (FP64, fixed order: slice r sums blocks r, r + 8, ...,
+// then the 8 slices in order).  CTA = 32 values x 8 slices.  mode 0: head, entries
+// [tap][c] + bias; mode 1: layer 1, entries [(ci*9 + tap)][n] + 64 biases.
+__global__ void __launch_bounds__(256) k_reduce_blocks(const float *__restrict__ partials, int nblk, int nval, int mode,
+                                                       float *__restrict__ gw, float *__restrict__ gb)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nval) return;
+    __shared__ double s_part[8][32];
+    const int v = threadIdx.x & 31, r = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + v;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += (double)partials[(size_t)b * nval + i];
+    if (i < nval)
+        for (int b = r; b < nblk; b += 8) s += (double)partials[(size_t)b * nval + i];
+    s_part[r][v] = s;
+    __syncthreads();
+    if (r != 0 || i >= nval) return;
+    for (int k = 1; k < 8; ++k) s += s_part[k][v];
     if (mode == 0) {
         if (i < 576) gw[(i % 64) * 9 + i / 64] = (float)s;       // W_head[0][c][tap]
         else gb[0] = (float)s;
@@ -714,19 +756,21 @@ ht_status ht_train_tc_backward(ht_policy *p, ht_train_tc_ws &w, int nimg, uint64
         k_pack_dgrad<<<nblk256(36864), 256, 0, s>>>(p->d_w + p->w_off[l], wt + (size_t)(l - 1) * 36864);
         HT_LAUNCH_CHECK();
     }
-    // head backward: g_{L-2}, dW / db of the head
+    // head backward: g_{L-2}, dW / db of the head (persistent blocks over the head tiles)
+    const int nbg = w.hd < 4 * num_sms() ? w.hd : 4 * num_sms();
     {
         HeadBwdParams P;
         P.imgs = tab(T_HB(L));
         P.n_imgs = nimg;
+        P.n_tiles = w.hd;
         memcpy(P.w, p->h_headw, sizeof(P.w));
         P.partials = wpart;
         ht_prof_start(HTK_TRAIN, s);
-        k_head_bwd<<<w.hd, dim3(HT_X, HT_Y), 0, s>>>(P);
+        k_head_bwd<<<nbg, dim3(HT_X, HT_Y), 0, s>>>(P);
         ht_prof_stop(s);
         HT_LAUNCH_CHECK();
-        k_reduce_blocks<<<nblk256(577), 256, 0, s>>>(wpart, w.hd, 577, 0, grad_w + p->w_off[L - 1],
-                                                     grad_b + p->b_off[L - 1]);
+        k_reduce_blocks<<<(577 + 31) / 32, 256, 0, s>>>(wpart, nbg, 577, 0, grad_w + p->w_off[L - 1],
+                                                       grad_b + p->b_off[L - 1]);
         HT_LAUNCH_CHECK();
     }
     static bool attr = false;
@@ -763,10 +807,10 @@ ht_status ht_train_tc_backward(ht_policy *p, ht_train_tc_ws &w, int nimg, uint64
         if (st != HT_OK) return st;
     }
     ht_prof_start(HTK_TRAIN, s);
-    k_first_wgrad<<<w.hd, dim3(HT_X, HT_Y), 0, s>>>(tab(T_W1(L)), nimg, seed, wpart);
+    k_first_wgrad<<<nbg, dim3(HT_X, HT_Y), 0, s>>>(tab(T_W1(L)), nimg, w.hd, seed, wpart);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
-    k_reduce_blocks<<<nblk256(1216), 256, 0, s>>>(wpart, w.hd, 1216, 1, grad_w + p->w_off[0], grad_b + p->b_off[0]);
+    k_reduce_blocks<<<(1216 + 31) / 32, 256, 0, s>>>(wpart, nbg, 1216, 1, grad_w + p->w_off[0], grad_b + p->b_off[0]);
     HT_LAUNCH_CHECK();
     return HT_OK;
 }
