@@ -192,6 +192,47 @@ ht_status ht_anisotropy_loss(const float *q, int n_patches, int n, int mode, int
                              double *out_loss, float *grad, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Plans: one ht_halftone call (tensor-core forms) captured into a CUDA graph */
+/* and replayed.  The plan owns its workspace and the image table; images,   */
+/* output buffers, mode and seed are fixed at creation (the caller may write  */
+/* new pixel values into the same contone buffers between launches).  When  */
+/* the policy's weights or scales change, the next launch captures again.     */
+/* Returns HT_ERR_UNSUPPORTED for FP32 policies.  The policy must outlive the */
+/* plan.                                                                      */
+/* ------------------------------------------------------------------------ */
+typedef struct ht_plan ht_plan;
+
+ht_status ht_plan_create(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
+                         uint32_t *const *out_bits, float *const *out_prob, ht_plan **out);
+ht_status ht_plan_launch(ht_plan *plan, void *stream);
+ht_status ht_plan_destroy(ht_plan *plan);
+
+/* ------------------------------------------------------------------------ */
+/* Schedule autotuner (tensor-core forms).  Runs the caller's ht_halftone call */
+/* (outputs are written) under every candidate conv schedule -- rows per work */
+/* unit (TMEM accumulator blocks: 8, 6, 4) x unit order (row bands first,      */
+/* column tiles first) -- reps times each after a warm-up, timed with CUDA    */
+/* events on `stream`, and keeps the fastest in the policy (used by later     */
+/* ht_halftone calls and plans).  results: nullable host array of up to       */
+/* max_results entries, *n_results written.  Outputs are bit-identical under  */
+/* every schedule (same per-pixel accumulation order).                         */
+/* ------------------------------------------------------------------------ */
+#define HT_TUNE_CANDIDATES 6
+typedef struct {
+    int rows_per_unit;
+    int unit_order;
+    float ms;                 /* mean time of one call */
+} ht_tune_result;
+
+/* Sets the conv schedule directly (rows_per_unit in [3, 8], unit_order 0 or 1),
+ * e.g. one found by an earlier ht_policy_autotune run. */
+ht_status ht_policy_set_schedule(ht_policy *p, int rows_per_unit, int unit_order);
+
+ht_status ht_policy_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
+                             uint32_t *const *out_bits, float *const *out_prob, int reps, ht_tune_result *results,
+                             int max_results, int *n_results, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Training (Algorithm 1, TRAIN step).                                       */
 /* ------------------------------------------------------------------------ */
 typedef struct {

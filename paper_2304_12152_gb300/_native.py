@@ -23,6 +23,7 @@ EXPORTS = (
     "ht_policy_calibrate",
     "ht_policy_num_params", "ht_policy_flops_per_px", "ht_bits_row_words", "ht_halftone",
     "ht_reward_opts_default", "ht_reward", "ht_reward_noalloc", "ht_toggle_delta", "ht_anisotropy_loss",
+    "ht_plan_create", "ht_plan_launch", "ht_plan_destroy", "ht_policy_set_schedule", "ht_policy_autotune",
     "ht_train_create", "ht_train_destroy", "ht_train_step_fwd", "ht_train_step_bwd",
     "ht_profile_begin", "ht_profile_end", "ht_sync", "ht_last_error", "ht_version",
 )
@@ -44,6 +45,13 @@ class RewardOpts(C.Structure):
 
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("rows_per_unit", C.c_int), ("unit_order", C.c_int), ("ms", C.c_float)]
+
+
+HT_TUNE_CANDIDATES = 6
 
 
 class TrainDesc(C.Structure):
@@ -94,6 +102,11 @@ def load(build_if_missing: bool = True):
         L.ht_reward_noalloc.argtypes = [P(Image), vp, i, P(RewardOpts), vp, vp]
         L.ht_toggle_delta.argtypes = [P(Image), vp, i, P(RewardOpts), vp, vp]
         L.ht_anisotropy_loss.argtypes = [vp, i, i, i, i, i, vp, vp, vp]
+        L.ht_plan_create.argtypes = [vp, P(Image), i, i, u64, vp, vp, P(vp)]
+        L.ht_plan_launch.argtypes = [vp, vp]
+        L.ht_plan_destroy.argtypes = [vp]
+        L.ht_policy_set_schedule.argtypes = [vp, i, i]
+        L.ht_policy_autotune.argtypes = [vp, P(Image), i, i, u64, vp, vp, i, P(TuneResult), i, P(i), vp]
         L.ht_train_create.argtypes = [vp, P(TrainDesc), P(vp)]
         L.ht_train_destroy.argtypes = [vp]
         L.ht_train_step_fwd.argtypes = [vp, P(Image), i, vp, u64, vp, vp]

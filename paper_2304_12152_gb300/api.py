@@ -107,6 +107,20 @@ class Policy:
         check(N.load().ht_halftone(self._h, imgs, len(contones), mode, seed, _ptrs(bits),
                                    _ptrs(probs) if probs is not None else None, _stream(stream)))
 
+    def set_schedule(self, rows_per_unit: int, unit_order: int) -> None:
+        check(N.load().ht_policy_set_schedule(self._h, rows_per_unit, unit_order))
+
+    def autotune(self, contones: Sequence[torch.Tensor], bits: Sequence[torch.Tensor], mode: int, seed: int,
+                 probs: Optional[Sequence[Optional[torch.Tensor]]] = None, reps: int = 3, stream=None):
+        """ht_policy_autotune: times every conv schedule on this call, keeps the fastest.
+        Returns [(rows_per_unit, unit_order, ms)] in candidate order."""
+        res = (N.TuneResult * N.HT_TUNE_CANDIDATES)()
+        n = C.c_int(0)
+        check(N.load().ht_policy_autotune(self._h, _images(contones), len(contones), mode, seed, _ptrs(bits),
+                                          _ptrs(probs) if probs is not None else None, reps, res,
+                                          N.HT_TUNE_CANDIDATES, C.byref(n), _stream(stream)))
+        return [(res[k].rows_per_unit, res[k].unit_order, float(res[k].ms)) for k in range(n.value)]
+
     def halftone(self, contones: Sequence[torch.Tensor], mode: int = N.HT_MODE_THRESHOLD, seed: int = 0,
                  want_prob: bool = False, stream=None):
         bits = [self.alloc_bits(c.shape[0], c.shape[1], c.device) for c in contones]
@@ -116,6 +130,33 @@ class Policy:
                      for c in contones]
         self.halftone_into(contones, bits, mode, seed, probs, stream)
         return bits, probs
+
+
+class Plan:
+    """ht_plan: one halftone call (fixed images, outputs, mode, seed) captured into a
+    CUDA graph; launch() replays it.  Keeps references to the tensors it points at."""
+
+    def __init__(self, policy: Policy, contones: Sequence[torch.Tensor], bits: Sequence[torch.Tensor], mode: int,
+                 seed: int, probs: Optional[Sequence[Optional[torch.Tensor]]] = None):
+        h = C.c_void_p()
+        check(N.load().ht_plan_create(policy.handle, _images(contones), len(contones), mode, seed, _ptrs(bits),
+                                      _ptrs(probs) if probs is not None else None, C.byref(h)))
+        self._h, self.policy = h, policy
+        self._keep = (list(contones), list(bits), list(probs) if probs is not None else None)
+
+    def launch(self, stream=None) -> None:
+        check(N.load().ht_plan_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.load().ht_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def reward(contones: Sequence[torch.Tensor], bits: Sequence[torch.Tensor], opts: Optional[N.RewardOpts] = None,

@@ -30,8 +30,8 @@ int *ht_device_error_flag()
     std::lock_guard<std::mutex> g(g_flag_mu);
     if (!g_flags[dev]) {
         int *p = nullptr;
-        if (cudaMalloc((void **)&p, sizeof(int)) != cudaSuccess) return nullptr;
-        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMalloc((void **)&p, 8 * sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, 8 * sizeof(int)) != cudaSuccess) return nullptr;
         g_flags[dev] = p;
     }
     return g_flags[dev];
@@ -63,10 +63,16 @@ cudaEvent_t pool_event()
 }
 }  // namespace
 
+static bool capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 void ht_prof_start(int kid, cudaStream_t s)
 {
     std::lock_guard<std::mutex> g(g_prof_mu);
-    if (!g_prof_on) return;
+    if (!g_prof_on || capturing(s)) return;
     ProfRec r;
     r.kid = kid;
     r.a = pool_event();
@@ -78,7 +84,7 @@ void ht_prof_start(int kid, cudaStream_t s)
 void ht_prof_stop(cudaStream_t s)
 {
     std::lock_guard<std::mutex> g(g_prof_mu);
-    if (!g_prof_on || g_prof.empty()) return;
+    if (!g_prof_on || g_prof.empty() || capturing(s)) return;
     cudaEventRecord(g_prof.back().b, s);
 }
 
@@ -188,6 +194,7 @@ ht_status ht_create_policy(const ht_policy_desc *desc, const float *weights_host
     ht_status st = validate_desc(desc);
     if (st != HT_OK) return st;
     HT_CHECK_ARG(weights_host && biases_host, "weights and biases are required");
+    ht_preload_kernels();
     ht_policy *p = new ht_policy();
     p->L = desc->n_layers;
     memcpy(p->ch, desc->channels, sizeof(p->ch));
@@ -251,10 +258,10 @@ ht_status ht_policy_set_act_scales(ht_policy *p, const float *scales_host, int n
 {
     HT_CHECK_ARG(p && scales_host, "null argument");
     HT_CHECK_ARG(n == p->L, "expected %d scales", p->L);
-    for (int l = 0; l < n; ++l) {
+    for (int l = 0; l < n; ++l)
         HT_CHECK_ARG(scales_host[l] > 0.f && isfinite(scales_host[l]), "scale %d must be positive", l);
-        p->act_scale[l] = scales_host[l];
-    }
+    for (int l = 0; l < n; ++l) p->act_scale[l] = scales_host[l];
+    ++p->version;
     return HT_OK;
 }
 
@@ -400,6 +407,64 @@ ht_status ht_halftone(ht_policy *p, const ht_image *imgs, int n, int mode, uint6
     return HT_OK;
 }
 
+static ht_status validate_call(const ht_policy *p, const ht_image *imgs, int n, int mode, uint32_t *const *out_bits)
+{
+    HT_CHECK_ARG(p != nullptr, "null policy");
+    ht_status st = validate_images(imgs, n, 1);
+    if (st != HT_OK) return st;
+    HT_CHECK_ARG(mode == HT_MODE_THRESHOLD || mode == HT_MODE_BERNOULLI, "unknown mode %d", mode);
+    HT_CHECK_ARG(out_bits != nullptr, "null output array");
+    for (int i = 0; i < n; ++i) HT_CHECK_ARG(out_bits[i] != nullptr, "image %d: null bits pointer", i);
+    return HT_OK;
+}
+
+ht_status ht_plan_create(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed, uint32_t *const *out_bits,
+                         float *const *out_prob, ht_plan **out)
+{
+    HT_CHECK_ARG(out != nullptr, "null output pointer");
+    *out = nullptr;
+    const ht_status st = validate_call(p, imgs, n, mode, out_bits);
+    if (st != HT_OK) return st;
+    return ht_plan_create_impl(p, imgs, n, mode, seed, out_bits, out_prob, out);
+}
+
+ht_status ht_plan_launch(ht_plan *plan, void *stream)
+{
+    HT_CHECK_ARG(plan != nullptr, "null plan");
+    return ht_plan_launch_impl(plan, (cudaStream_t)stream);
+}
+
+ht_status ht_plan_destroy(ht_plan *plan) { return ht_plan_destroy_impl(plan); }
+
+ht_status ht_policy_set_schedule(ht_policy *p, int rows_per_unit, int unit_order)
+{
+    HT_CHECK_ARG(p != nullptr, "null policy");
+    HT_CHECK_ARG(rows_per_unit >= 3 && rows_per_unit <= 8, "rows_per_unit must be in [3, 8]");
+    HT_CHECK_ARG(unit_order == 0 || unit_order == 1, "unit_order must be 0 or 1");
+    p->tune_ru = rows_per_unit;
+    p->tune_order = unit_order;
+    return HT_OK;
+}
+
+ht_status ht_policy_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
+                             uint32_t *const *out_bits, float *const *out_prob, int reps, ht_tune_result *results,
+                             int max_results, int *n_results, void *stream)
+{
+    ht_status st = validate_call(p, imgs, n, mode, out_bits);
+    if (st != HT_OK) return st;
+    HT_CHECK_ARG(reps >= 1 && reps <= 1000, "reps must be in [1, 1000]");
+    HT_CHECK_ARG(max_results >= 0 && (results || max_results == 0), "bad results array");
+    if (n_results) *n_results = 0;
+    if (p->prec == HT_FP32) {
+        ht_set_error("the autotuner schedules the tensor-core forms (BF16, FP8)");
+        return HT_ERR_UNSUPPORTED;
+    }
+    st = ht_policy_ensure_ws(p, ht_tc_batch_ws_bytes(p, imgs, n));
+    if (st != HT_OK) return st;
+    return ht_tc_autotune(p, imgs, n, mode, seed, out_bits, out_prob, reps, results, max_results, n_results,
+                          (cudaStream_t)stream);
+}
+
 static ht_status validate_opts(const ht_reward_opts *o)
 {
     HT_CHECK_ARG(o != nullptr, "null reward options");
@@ -464,14 +529,34 @@ ht_status ht_sync(void *stream)
     HT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     int *flag = ht_device_error_flag();
     if (!flag) return HT_ERR_CUDA;
-    int v = 0;
-    HT_CUDA_TRY(cudaMemcpy(&v, flag, sizeof(int), cudaMemcpyDeviceToHost));
-    if (v != 0) {
-        cudaMemset(flag, 0, sizeof(int));
-        ht_set_error("device-side wait expired (error %d)", v);
-        return (ht_status)v;
+    int v[8];
+    HT_CUDA_TRY(cudaMemcpy(v, flag, sizeof(v), cudaMemcpyDeviceToHost));
+    if (v[0] != 0) {
+        cudaMemset(flag, 0, sizeof(v));
+        unsigned long long el;
+        memcpy(&el, v + 6, sizeof(el));
+        ht_set_error("device-side wait expired (error %d): barrier at shared 0x%x, block %d of %d threads, warp %d, "
+                     "%d polls, %.3f s",
+                     v[0], (unsigned)v[2], v[4], (unsigned)v[3] >> 16, v[3] & 0xFFFF, v[5], (double)el * 1e-9);
+        return (ht_status)v[0];
     }
     return HT_OK;
 }
 
 }  // extern "C"
+
+void ht_preload_kernels()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        ht_preload_conv_tc();
+        ht_preload_conv_fp32();
+        ht_preload_reward();
+        ht_preload_spectrum();
+        ht_preload_train();
+        ht_preload_train_tc();
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, k_absmax);
+        cudaGetLastError();
+    });
+}

@@ -205,3 +205,9 @@ ht_status ht_dgrad_fp32(const float *g_out, const float *wt, int Cout, int Cin, 
     HT_LAUNCH_CHECK();
     return HT_OK;
 }
+
+void ht_preload_conv_fp32()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_conv3x3_fp32);
+}

@@ -89,6 +89,7 @@ struct ConvParams {
     uint64_t seed;           // Philox seed (layer 1: noise channel; 4-logit head: level draw)
     int mode;                // 4-logit head: HT_MODE_*
     int dgrad;               // 1: data-gradient layer (no bias, no ReLU; mask from the table, bf16 out)
+    int ru, order;           // unit geometry: rows per unit (<= RU TMEM blocks) and unit order
     int *err;
 };
 
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         uint32_t li = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
-            const UnitInfo ui = unit_info(P.imgs, P.n_imgs, P.in_buf, u);
+            const UnitInfo ui = unit_info(P.imgs, P.n_imgs, P.in_buf, u, P.ru, P.order);
             const int y0 = ui.y0, y1 = ui.y0 + ui.nrows, x0 = ui.x0;
             const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, ui.W);   // in-image pixel range
             for (int r = 0; r < (y1 - y0) + 2; ++r, ++li) {
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         bool ok = wait1(smem_u32(wbar), 0);
         uint32_t q = 0, uit = 0;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
-            const int nrows = unit_info(P.imgs, P.n_imgs, P.in_buf, u).nrows;
+            const int nrows = unit_info(P.imgs, P.n_imgs, P.in_buf, u, P.ru, P.order).nrows;
             for (int k = 0; k < nrows + 2 && ok; ++k, ++q) {
                 ok = wait1(smem_u32(&full[q % NSLOT]), (q / NSLOT) & 1u);
                 if (ok && k < nrows) ok = wait1(smem_u32(&bfree[k]), uit & 1u);   // block k enters use
@@ -264,10 +265,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 __syncwarp();
             }
             if (!ok) break;
-            // keep every block's barrier phases in step for short units
-            if (lane == 0)
-                for (int j = nrows; j < RU; ++j) mma_commit(smem_u32(&bfull[j]));
-            __syncwarp();
+            // Blocks a short unit leaves unused still go through one full/free round per
+            // unit, so that every block's barriers stay in step.  Wait until the epilogue
+            // has released the block from the previous unit before signalling it: a parity
+            // wait cannot tell phase k from phase k + 2, so no barrier may run two phases
+            // ahead of its consumer (two short units in a row would otherwise do that).
+            for (int j = nrows; j < P.ru && ok; ++j) {
+                ok = wait1(smem_u32(&bfree[j]), uit & 1u);
+                if (ok && lane == 0) mma_commit(smem_u32(&bfull[j]));
+                __syncwarp();
+            }
+            if (!ok) break;
         }
         // drain: all issued MMAs complete before TMEM is released
         if (lane == 0) {
@@ -283,20 +291,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         const int px = quarter * 32 + lane;           // pixel within the tile
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         // accumulators start at zero (TMEM is undefined after allocation)
-        for (int j = grp; j < RU; j += 2)
+        for (int j = grp; j < P.ru; j += 2)
             for (int c = 0; c < C::NOUT; c += 16) tmem_zero16(lane_base + j * C::NOUT + c);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0)
-            for (int j = grp; j < RU; j += 2) mbar_arrive(smem_u32(&bfree[j]));
+            for (int j = grp; j < P.ru; j += 2) mbar_arrive(smem_u32(&bfree[j]));
         uint32_t uit = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
-            const UnitInfo ui = unit_info(P.imgs, P.n_imgs, P.in_buf, u);
+            const UnitInfo ui = unit_info(P.imgs, P.n_imgs, P.in_buf, u, P.ru, P.order);
             const int y0 = ui.y0, nrows = ui.nrows;
             const int x = ui.x0 + px;
-            for (int j = grp; j < RU; j += 2) {
+            for (int j = grp; j < P.ru; j += 2) {
                 int got = 0;
                 if (lane == 0) got = mbar_wait(smem_u32(&bfull[j]), uit & 1u, s_abort, P.err) ? 1 : 0;
                 got = __shfl_sync(0xffffffffu, got, 0);
@@ -466,7 +474,7 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__r
 // Host side
 // ---------------------------------------------------------------------------
 template <bool FP8, int KIND>
-ht_status launch_conv(const ConvParams &P, cudaStream_t s)
+ht_status ensure_attr()
 {
     static bool attr_set = false;
     if (!attr_set) {
@@ -474,6 +482,26 @@ ht_status launch_conv(const ConvParams &P, cudaStream_t s)
                                          Cfg<FP8, KIND>::SMEM));
         attr_set = true;
     }
+    return HT_OK;
+}
+
+// every kernel attribute set before a stream capture records the launches
+ht_status ensure_all_attrs()
+{
+    ht_status st;
+    if ((st = ensure_attr<false, KIND_HIDDEN>()) != HT_OK || (st = ensure_attr<false, KIND_HEADPART>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_FIRST>()) != HT_OK || (st = ensure_attr<false, KIND_HEAD4>()) != HT_OK ||
+        (st = ensure_attr<true, KIND_HIDDEN>()) != HT_OK || (st = ensure_attr<true, KIND_HEADPART>()) != HT_OK ||
+        (st = ensure_attr<true, KIND_FIRST>()) != HT_OK)
+        return st;
+    return HT_OK;
+}
+
+template <bool FP8, int KIND>
+ht_status launch_conv(const ConvParams &P, cudaStream_t s)
+{
+    const ht_status st = ensure_attr<FP8, KIND>();
+    if (st != HT_OK) return st;
     const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
     ht_prof_start(KIND == KIND_FIRST ? HTK_FIRST_TC : KIND == KIND_HEAD4 ? HTK_HEAD_TC
                                                   : FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
@@ -661,6 +689,7 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
     free(hp);
     free(hs);
     HT_CUDA_TRY(e);
+    ++p->version;
     return HT_OK;
 }
 
@@ -704,6 +733,22 @@ size_t ht_tc_batch_ws_bytes(const ht_policy *p, const ht_image *imgs, int n)
     return maxg + (size_t)n * sizeof(ImgDesc) + 1024;
 }
 
+// Loads every kernel of this file (see ht_preload_kernels).
+void ht_preload_conv_tc()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEADPART>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEAD4>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_HIDDEN>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_HEADPART>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_FIRST>);
+    cudaFuncGetAttributes(&fa, k_first_input);
+    cudaFuncGetAttributes(&fa, k_head_partials);
+    ensure_all_attrs();
+}
+
 ht_status ht_tc_conv(const ht_tc_layer &a, cudaStream_t s)
 {
     int *err = ht_device_error_flag();
@@ -723,6 +768,8 @@ ht_status ht_tc_conv(const ht_tc_layer &a, cudaStream_t s)
     P.out_fp8 = 0;
     P.seed = a.seed;
     P.dgrad = a.dgrad;
+    P.ru = RU;
+    P.order = 0;
     P.err = err;
     switch (a.kind) {
     case KIND_HIDDEN: return launch_conv<false, KIND_HIDDEN>(P, s);
@@ -751,14 +798,139 @@ ht_status ht_tc_head_partials(const void *table, int n_imgs, int n_tiles, int bu
     return HT_OK;
 }
 
+namespace {
+// One group of a call's images: their activation buffers fit the workspace
+// budget together; each group is one launch per layer over all its images.
+struct TcGroup {
+    int g0, ng, units, hd, pre;
+};
+
+// Host side of a call: the image tables (into `tab`, one entry per image, in call
+// order) and the groups.  Activations of every group start at `ws`.
+void tc_make_groups(const ht_policy *p, const ht_image *imgs, int n, uint8_t *ws, int ru, uint32_t *const *bits,
+                    float *const *prob, std::vector<ImgDesc> &tab, std::vector<TcGroup> &groups)
+{
+    tab.assign(n, ImgDesc{});
+    groups.clear();
+    int g0 = 0;
+    while (g0 < n) {
+        TcGroup G{};
+        G.g0 = g0;
+        int g1 = g0;
+        size_t off = 0;
+        while (g1 < n) {
+            const size_t b = ht_tc_ws_bytes(p, imgs[g1].h, imgs[g1].w);
+            if (g1 > g0 && off + img_ws_slot(p, imgs[g1]) > ws_budget()) break;
+            ImgDesc &D = tab[g1];
+            D.contone = imgs[g1].contone;
+            D.cpitch = imgs[g1].pitch;
+            D.H = imgs[g1].h;
+            D.W = imgs[g1].w;
+            D.act[0] = ws + off;
+            D.act[1] = D.act[0] + b / 2;
+            off += img_ws_slot(p, imgs[g1]);
+            D.bits = bits[g1];
+            D.prob = prob ? prob[g1] : nullptr;
+            D.words = ht_bits_row_words(D.W, p->head);
+            D.image = (uint32_t)g1;
+            set_begins(D, G.units, G.hd, G.pre, ru);
+            ++g1;
+        }
+        G.ng = g1 - g0;
+        groups.push_back(G);
+        g0 = g1;
+    }
+}
+
+// Device side of a call: per group, layer 1 (input pass + pipeline), the 64 -> 64
+// layers and the head.  Kernel launches only (no copies, no allocation), so the
+// sequence can be captured into a CUDA graph.
+ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vector<TcGroup> &groups, int mode,
+                           uint64_t seed, int ru, int order, int *err, cudaStream_t s)
+{
+    const bool fp8 = (p->prec == HT_FP8_E4M3);
+    const int n_inner = p->L - 2;
+    for (const TcGroup &G : groups) {
+        const ImgDesc *dt = d_table + G.g0;
+        const int ng = G.ng;
+        ht_prof_start(HTK_FIRST_TC, s);
+        k_first_input<<<(G.pre + 255) / 256, 256, 0, s>>>(dt, ng, seed);
+        ht_prof_stop(s);
+        HT_LAUNCH_CHECK();
+        auto base = [&](ConvParams &P, int in_buf) {
+            P.imgs = dt;
+            P.n_imgs = ng;
+            P.n_units = G.units;
+            P.in_buf = in_buf;
+            P.ru = ru;
+            P.order = order;
+            P.seed = seed;
+            P.mode = mode;
+            P.err = err;
+        };
+        {
+            const bool o8 = fp8 && n_inner > 0;
+            ConvParams P{};
+            base(P, 1);                            // reads the split input in act[1], writes act[0]
+            P.wpack = p->d_w1pack;
+            for (int c = 0; c < 64; ++c) {
+                P.bias[c] = p->h_b[p->b_off[0] + c];
+                P.scale[c] = 1.f;
+            }
+            P.out_inv_scale = o8 ? 1.f / p->act_scale[1] : 1.f;
+            P.out_fp8 = o8 ? 1 : 0;
+            const ht_status st = fp8 ? launch_conv<true, KIND_FIRST>(P, s) : launch_conv<false, KIND_FIRST>(P, s);
+            if (st != HT_OK) return st;
+        }
+        int cur = 0;
+        for (int l = 1; l <= n_inner; ++l) {
+            const bool out8 = fp8 && (l < n_inner);
+            const bool fuse_head = (l == n_inner) && p->K == 1;
+            ConvParams P{};
+            base(P, cur);
+            P.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (l - 1);
+            for (int c = 0; c < 64; ++c) {
+                P.bias[c] = p->h_b[p->b_off[l] + c];
+                P.scale[c] = fp8 ? p->act_scale[l] * p->h_wscale[64 * (l - 1) + c] : 1.f;
+            }
+            if (fuse_head) memcpy(P.head_w, p->h_headw, sizeof(P.head_w));
+            P.out_inv_scale = out8 ? 1.f / p->act_scale[l + 1] : 1.f;
+            P.out_fp8 = out8 ? 1 : 0;
+            const ht_status st =
+                fp8 ? (fuse_head ? launch_conv<true, KIND_HEADPART>(P, s) : launch_conv<true, KIND_HIDDEN>(P, s))
+                    : (fuse_head ? launch_conv<false, KIND_HEADPART>(P, s) : launch_conv<false, KIND_HIDDEN>(P, s));
+            if (st != HT_OK) return st;
+            cur ^= 1;
+        }
+        if (p->K == 1) {
+            ht_prof_start(HTK_HEAD_TC, s);
+            k_head_partials<<<G.hd, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, cur, p->head_bias, mode, seed);
+            ht_prof_stop(s);
+            HT_LAUNCH_CHECK();
+        } else {
+            ConvParams P{};
+            base(P, cur);
+            P.wpack = p->d_wpack4;
+            for (int c = 0; c < 64; ++c) {
+                P.bias[c] = c < 4 ? p->h_b[p->b_off[p->L - 1] + c] : 0.f;
+                P.scale[c] = 1.f;
+            }
+            P.out_inv_scale = 1.f;
+            P.out_fp8 = 0;
+            const ht_status st = launch_conv<false, KIND_HEAD4>(P, s);
+            if (st != HT_OK) return st;
+        }
+    }
+    return HT_OK;
+}
+}  // namespace
+
 // All images of a call: grouped so that a group's activation buffers fit the
 // workspace budget; per group one launch of layer 1, one per 64 -> 64 layer and
 // one of the head, each over the whole group (persistent tile index space).
 ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
                           uint32_t *const *bits, float *const *prob, cudaStream_t s)
 {
-    const bool fp8 = (p->prec == HT_FP8_E4M3);
-    const int n_inner = p->L - 2;
     int *err = ht_device_error_flag();
     if (!err) return HT_ERR_CUDA;
     // table slots after the activation region (one slot per image, never reused within a call)
@@ -768,119 +940,180 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
         return HT_ERR_INVALID_ARG;
     }
     ImgDesc *d_table = (ImgDesc *)((uint8_t *)p->d_ws + (need - (size_t)n * sizeof(ImgDesc) - 512) / 256 * 256);
-    static bool attr_done = false;
-    if (!attr_done) {
-        attr_done = true;
+    std::vector<ImgDesc> tab;
+    std::vector<TcGroup> groups;
+    tc_make_groups(p, imgs, n, (uint8_t *)p->d_ws, p->tune_ru, bits, prob, tab, groups);
+    HT_CUDA_TRY(cudaMemcpyAsync(d_table, tab.data(), sizeof(ImgDesc) * n, cudaMemcpyHostToDevice, s));
+    return tc_launch_groups(p, d_table, groups, mode, seed, p->tune_ru, p->tune_order, err, s);
+}
+
+// ---------------------------------------------------------------------------
+// Plans: one call's launch sequence captured once into a CUDA graph.
+// ---------------------------------------------------------------------------
+struct ht_plan {
+    ht_policy *p = nullptr;
+    int n = 0, mode = 0, ru = RU, order = 0;
+    uint64_t seed = 0;
+    uint64_t version = 0;                 // policy weight version the graph was captured with
+    std::vector<ht_image> imgs;
+    std::vector<uint32_t *> bits;
+    std::vector<float *> prob;
+    void *ws = nullptr;                   // plan-owned activations and image table
+    ImgDesc *d_table = nullptr;
+    std::vector<TcGroup> groups;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+void plan_release_graph(ht_plan *pl)
+{
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    pl->exec = nullptr;
+    pl->graph = nullptr;
+}
+
+ht_status plan_capture(ht_plan *pl)
+{
+    plan_release_graph(pl);
+    int *err = ht_device_error_flag();
+    if (!err) return HT_ERR_CUDA;
+    ht_status st = ensure_all_attrs();
+    if (st != HT_OK) return st;
+    cudaStream_t cs = nullptr;
+    HT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = tc_launch_groups(pl->p, pl->d_table, pl->groups, pl->mode, pl->seed, pl->ru, pl->order, err, cs);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &pl->graph);
+        if (st == HT_OK && e2 != cudaSuccess) e = e2;
     }
-    int g0 = 0;
-    while (g0 < n) {
-        // group [g0, g1)
-        int g1 = g0;
-        size_t off = 0;
-        std::vector<ImgDesc> tab;
-        int units = 0, hd = 0, pre = 0;
-        while (g1 < n) {
-            const size_t b = ht_tc_ws_bytes(p, imgs[g1].h, imgs[g1].w);
-            if (g1 > g0 && off + img_ws_slot(p, imgs[g1]) > ws_budget()) break;
-            ImgDesc D{};
-            D.contone = imgs[g1].contone;
-            D.cpitch = imgs[g1].pitch;
-            D.H = imgs[g1].h;
-            D.W = imgs[g1].w;
-            D.act[0] = (uint8_t *)p->d_ws + off;
-            D.act[1] = D.act[0] + b / 2;
-            off += img_ws_slot(p, imgs[g1]);
-            D.bits = bits[g1];
-            D.prob = prob ? prob[g1] : nullptr;
-            D.words = ht_bits_row_words(D.W, p->head);
-            D.image = (uint32_t)g1;
-            set_begins(D, units, hd, pre);
-            tab.push_back(D);
-            ++g1;
-        }
-        const int ng = g1 - g0;
-        ImgDesc *dt = d_table + g0;
-        HT_CUDA_TRY(cudaMemcpyAsync(dt, tab.data(), sizeof(ImgDesc) * ng, cudaMemcpyHostToDevice, s));
-        // layer 1: input split into act[1], then the conv pipeline -> act[0]
-        {
-            ht_prof_start(HTK_FIRST_TC, s);
-            k_first_input<<<(pre + 255) / 256, 256, 0, s>>>(dt, ng, seed);
-            ht_prof_stop(s);
-            HT_LAUNCH_CHECK();
-        }
-        {
-            const bool o8 = fp8 && n_inner > 0;
-            ConvParams P{};
-            P.imgs = dt;
-            P.n_imgs = ng;
-            P.n_units = units;
-            P.in_buf = 1;                          // reads the split input in act[1], writes act[0]
-            P.wpack = p->d_w1pack;
-            for (int c = 0; c < 64; ++c) {
-                P.bias[c] = p->h_b[p->b_off[0] + c];
-                P.scale[c] = 1.f;
-            }
-            P.out_inv_scale = o8 ? 1.f / p->act_scale[1] : 1.f;
-            P.out_fp8 = o8 ? 1 : 0;
-            P.seed = seed;
-            P.err = err;
-            const ht_status st = fp8 ? launch_conv<true, KIND_FIRST>(P, s) : launch_conv<false, KIND_FIRST>(P, s);
-            if (st != HT_OK) return st;
-        }
-        int cur = 0;
-        for (int l = 1; l <= n_inner; ++l) {
-            const bool out8 = fp8 && (l < n_inner);
-            const bool fuse_head = (l == n_inner) && p->K == 1;
-            ConvParams P{};
-            P.imgs = dt;
-            P.n_imgs = ng;
-            P.n_units = units;
-            P.in_buf = cur;
-            P.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (l - 1);
-            for (int c = 0; c < 64; ++c) {
-                P.bias[c] = p->h_b[p->b_off[l] + c];
-                P.scale[c] = fp8 ? p->act_scale[l] * p->h_wscale[64 * (l - 1) + c] : 1.f;
-            }
-            if (fuse_head) memcpy(P.head_w, p->h_headw, sizeof(P.head_w));
-            P.out_inv_scale = out8 ? 1.f / p->act_scale[l + 1] : 1.f;
-            P.out_fp8 = out8 ? 1 : 0;
-            P.err = err;
-            P.seed = seed;
-            const ht_status st =
-                fp8 ? (fuse_head ? launch_conv<true, KIND_HEADPART>(P, s) : launch_conv<true, KIND_HIDDEN>(P, s))
-                    : (fuse_head ? launch_conv<false, KIND_HEADPART>(P, s) : launch_conv<false, KIND_HIDDEN>(P, s));
-            if (st != HT_OK) return st;
-            cur ^= 1;
-        }
-        // head
-        {
-            ht_prof_start(HTK_HEAD_TC, s);
-            if (p->K == 1) {
-                k_head_partials<<<hd, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, cur, p->head_bias, mode, seed);
-                ht_prof_stop(s);
-                HT_LAUNCH_CHECK();
-            } else {
-                ht_prof_stop(s);
-                ConvParams P{};
-                P.imgs = dt;
-                P.n_imgs = ng;
-                P.n_units = units;
-                P.in_buf = cur;
-                P.wpack = p->d_wpack4;
-                for (int c = 0; c < 64; ++c) {
-                    P.bias[c] = c < 4 ? p->h_b[p->b_off[p->L - 1] + c] : 0.f;
-                    P.scale[c] = 1.f;
-                }
-                P.out_inv_scale = 1.f;
-                P.out_fp8 = 0;
-                P.seed = seed;
-                P.mode = mode;
-                P.err = err;
-                const ht_status st = launch_conv<false, KIND_HEAD4>(P, s);
-                if (st != HT_OK) return st;
-            }
-        }
-        g0 = g1;
+    if (e == cudaSuccess && st == HT_OK) e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+    cudaStreamDestroy(cs);
+    if (st != HT_OK) {
+        plan_release_graph(pl);
+        return st;
     }
+    if (e != cudaSuccess) {
+        plan_release_graph(pl);
+        HT_CUDA_TRY(e);
+    }
+    pl->version = pl->p->version;
+    return HT_OK;
+}
+}  // namespace
+
+ht_status ht_plan_create_impl(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
+                              uint32_t *const *bits, float *const *prob, ht_plan **out)
+{
+    if (p->prec == HT_FP32) {
+        ht_set_error("plans capture the tensor-core forms (BF16, FP8)");
+        return HT_ERR_UNSUPPORTED;
+    }
+    ht_plan *pl = new ht_plan();
+    pl->p = p;
+    pl->n = n;
+    pl->mode = mode;
+    pl->seed = seed;
+    pl->ru = p->tune_ru;
+    pl->order = p->tune_order;
+    pl->imgs.assign(imgs, imgs + n);
+    pl->bits.assign(bits, bits + n);
+    if (prob) pl->prob.assign(prob, prob + n);
+    const size_t need = ht_tc_batch_ws_bytes(p, imgs, n);
+    cudaError_t e = cudaMalloc(&pl->ws, need);
+    if (e != cudaSuccess) {
+        delete pl;
+        ht_set_error("plan workspace: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? HT_ERR_OOM : HT_ERR_CUDA;
+    }
+    pl->d_table = (ImgDesc *)((uint8_t *)pl->ws + (need - (size_t)n * sizeof(ImgDesc) - 512) / 256 * 256);
+    std::vector<ImgDesc> tab;
+    tc_make_groups(p, imgs, n, (uint8_t *)pl->ws, pl->ru, pl->bits.data(), prob ? pl->prob.data() : nullptr, tab,
+                   pl->groups);
+    e = cudaMemcpy(pl->d_table, tab.data(), sizeof(ImgDesc) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        ht_plan_destroy_impl(pl);
+        HT_CUDA_TRY(e);
+    }
+    const ht_status st = plan_capture(pl);
+    if (st != HT_OK) {
+        ht_plan_destroy_impl(pl);
+        return st;
+    }
+    *out = pl;
+    return HT_OK;
+}
+
+ht_status ht_plan_launch_impl(ht_plan *pl, cudaStream_t s)
+{
+    if (pl->version != pl->p->version) {            // weights, scales or biases changed: capture again
+        const ht_status st = plan_capture(pl);
+        if (st != HT_OK) return st;
+    }
+    HT_CUDA_TRY(cudaGraphLaunch(pl->exec, s));
+    return HT_OK;
+}
+
+ht_status ht_plan_destroy_impl(ht_plan *pl)
+{
+    if (!pl) return HT_OK;
+    plan_release_graph(pl);
+    cudaFree(pl->ws);
+    delete pl;
+    return HT_OK;
+}
+
+// Autotuner: times every unit geometry on the caller's own call and keeps the fastest.
+ht_status ht_tc_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed, uint32_t *const *bits,
+                         float *const *prob, int reps, ht_tune_result *out, int max_out, int *n_out, cudaStream_t s)
+{
+    static const int cand[][2] = {{8, 0}, {8, 1}, {6, 0}, {6, 1}, {4, 0}, {4, 1}};
+    const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+    cudaEvent_t e0, e1;
+    HT_CUDA_TRY(cudaEventCreate(&e0));
+    HT_CUDA_TRY(cudaEventCreate(&e1));
+    const int keep_ru = p->tune_ru, keep_order = p->tune_order;
+    float best = 1e30f;
+    int bi = 0, k_out = 0;
+    ht_status st = HT_OK;
+    for (int c = 0; c < nc && st == HT_OK; ++c) {
+        p->tune_ru = cand[c][0];
+        p->tune_order = cand[c][1];
+        st = ht_run_tc_batch(p, imgs, n, mode, seed, bits, prob, s);       // warm-up
+        if (st != HT_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == HT_OK; ++r) st = ht_run_tc_batch(p, imgs, n, mode, seed, bits, prob, s);
+        cudaEventRecord(e1, s);
+        if (st != HT_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = HT_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        if (out && k_out < max_out) {
+            out[k_out].rows_per_unit = cand[c][0];
+            out[k_out].unit_order = cand[c][1];
+            out[k_out].ms = ms;
+            ++k_out;
+        }
+        if (ms < best) {
+            best = ms;
+            bi = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HT_OK) {
+        p->tune_ru = keep_ru;
+        p->tune_order = keep_order;
+        return st;
+    }
+    p->tune_ru = cand[bi][0];
+    p->tune_order = cand[bi][1];
+    if (n_out) *n_out = k_out;
     return HT_OK;
 }

@@ -42,8 +42,10 @@ void ht_set_error(const char *fmt, ...);
         }                                                                              \
     } while (0)
 
-// Device-side error flag (one per device context): kernels whose bounded wait
-// expires store HT_ERR_TIMEOUT here; ht_sync() reads and clears it.
+// Device-side error record (8 ints, one per device context): [0] status
+// (HT_ERR_TIMEOUT when a bounded wait expires), [1] set once, [2..7] where the
+// first expiry happened (barrier address, threads and warp, block, polls,
+// elapsed ns as u64).  ht_sync() reads, reports and clears it.
 int *ht_device_error_flag();
 
 // Kernel timing hooks (no-ops unless ht_profile_begin was called).
@@ -105,6 +107,10 @@ struct ht_policy {
     void *d_w1pack = nullptr;       // layer 1 for the tensor cores: bf16 hi/lo split, [dx][chunk][3 dy][n][8]
     void *d_wpack4 = nullptr;       // 4-logit head: bf16 hi and lo parts, [part][dx][chunk][3 dy][16 n][8]
     float head_bias = 0.f;
+    // conv schedule of the tensor-core forms (set by ht_policy_autotune): rows per
+    // work unit (TMEM accumulator blocks) and unit order
+    int tune_ru = 8, tune_order = 0;
+    uint64_t version = 0;           // bumped by every change of weights or scales (plans re-capture)
     // per-call workspace (grown on demand; library owned)
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
@@ -130,6 +136,25 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
                           uint32_t *const *bits, float *const *prob, cudaStream_t s);
 size_t ht_tc_ws_bytes(const ht_policy *p, int h, int w);
 size_t ht_tc_batch_ws_bytes(const ht_policy *p, const ht_image *imgs, int n);
+
+// Kernel preloading: every kernel of the library is loaded when the first policy
+// is created (with lazy module loading a first launch can otherwise stall work
+// already running on the GPU while the loader runs).
+void ht_preload_conv_tc();
+void ht_preload_conv_fp32();
+void ht_preload_reward();
+void ht_preload_spectrum();
+void ht_preload_train();
+void ht_preload_train_tc();
+void ht_preload_kernels();
+
+// CUDA-graph plans and the schedule autotuner of the tensor-core forms (conv_tc.cu)
+ht_status ht_plan_create_impl(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
+                              uint32_t *const *bits, float *const *prob, ht_plan **out);
+ht_status ht_plan_launch_impl(ht_plan *pl, cudaStream_t s);
+ht_status ht_plan_destroy_impl(ht_plan *pl);
+ht_status ht_tc_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed, uint32_t *const *bits,
+                         float *const *prob, int reps, ht_tune_result *out, int max_out, int *n_out, cudaStream_t s);
 
 // single launches of the BF16 conv pipeline over a caller-built image table (training form)
 struct ht_tc_layer {

@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_moment_maps(const __grid_constant__ RwB
 
 constexpr int DTX = 32, DTY = 8;
 
-__global__ void __launch_bounds__(DTX *DTY) k_toggle_delta(const __grid_constant__ RwBatch B, const Win wn)
+__global__ void __launch_bounds__(DTX *DTY, 3) k_toggle_delta(const __grid_constant__ RwBatch B, const Win wn)
 {
     constexpr int SH = DTY + 2 * MAXR, SW = DTX + 2 * MAXR;
     __shared__ float s_m[NMAP][SH][SW];
@@ -256,22 +256,25 @@ __global__ void __launch_bounds__(DTX *DTY) k_toggle_delta(const __grid_constant
     if (ay0 >= H || ax0 >= W) return;
     const int tid = threadIdx.y * DTX + threadIdx.x;
     // stage maps for output positions j in [a0 - r, a0 + tile + r) (image coords)
-    constexpr int NT = NMAP * SH * SW, NPER = (NT + DTX * DTY - 1) / (DTX * DTY);
-    float vals[NPER];
+    constexpr int NT = NMAP * SH * SW, NPER = (NT + DTX * DTY - 1) / (DTX * DTY), NB = (NPER + 1) / 2;
 #pragma unroll
-    for (int k = 0; k < NPER; ++k) {          // loads first, then the shared stores
-        const int i = tid + k * DTX * DTY;
-        const int q = i / (SH * SW), rem = i % (SH * SW);
-        const int yy = rem / SW, xx = rem % SW;
-        const int jy = ay0 - r + yy, jx = ax0 - r + xx;       // image coords of output j
-        vals[k] = 0.f;
-        if (i < NT && jy >= r && jy < H - r && jx >= r && jx < W - r)
-            vals[k] = __ldg(maps + q * plane + (size_t)(jy - r) * VW + (jx - r));
-    }
+    for (int k0 = 0; k0 < NPER; k0 += NB) {   // two batches: loads first, then the shared stores
+        float vals[NB];
 #pragma unroll
-    for (int k = 0; k < NPER; ++k) {
-        const int i = tid + k * DTX * DTY;
-        if (i < NT) s_m[i / (SH * SW)][(i % (SH * SW)) / SW][i % SW] = vals[k];
+        for (int k = 0; k < NB; ++k) {
+            const int i = tid + (k0 + k) * DTX * DTY;
+            const int q = i / (SH * SW), rem = i % (SH * SW);
+            const int yy = rem / SW, xx = rem % SW;
+            const int jy = ay0 - r + yy, jx = ax0 - r + xx;   // image coords of output j
+            vals[k] = 0.f;
+            if (k0 + k < NPER && i < NT && jy >= r && jy < H - r && jx >= r && jx < W - r)
+                vals[k] = __ldg(maps + q * plane + (size_t)(jy - r) * VW + (jx - r));
+        }
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int i = tid + (k0 + k) * DTX * DTY;
+            if (k0 + k < NPER && i < NT) s_m[i / (SH * SW)][(i % (SH * SW)) / SW][i % SW] = vals[k];
+        }
     }
     __syncthreads();
     const int ay = ay0 + threadIdx.y, ax = ax0 + threadIdx.x;
@@ -295,8 +298,9 @@ __global__ void __launch_bounds__(DTX *DTY) k_toggle_delta(const __grid_constant
             const float muh2 = muh + delta * w;
             const float varh2 = muh2 - muh2 * muh2;
             const float cov2 = cov + delta * w * (ca - muc);
-            const float s2 = ((2.f * muh2 * muc + wn.c1) * (2.f * cov2 + wn.c2)) /
-                             ((muh2 * muh2 + muc * muc + wn.c1) * (varh2 + varc2));
+            // the denominator lies in [C1 C2, ~5]: the fast division (2 ulp) is exact enough
+            const float s2 = __fdividef((2.f * muh2 * muc + wn.c1) * (2.f * cov2 + wn.c2),
+                                        (muh2 * muh2 + muc * muc + wn.c1) * (varh2 + varc2));
             acc += -(2.f * g * e + delta * g * g) + delta * wn.ws * sig * (s2 - ss);
         }
     }
@@ -527,4 +531,14 @@ extern "C" ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const 
         HT_LAUNCH_CHECK();
     }
     return HT_OK;
+}
+
+void ht_preload_reward()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_reward_tiles);
+    cudaFuncGetAttributes(&fa, k_reward_finalize);
+    cudaFuncGetAttributes(&fa, k_moment_maps);
+    cudaFuncGetAttributes(&fa, k_toggle_delta);
+    cudaFuncGetAttributes(&fa, k_reward_finalize_noalloc);
 }

@@ -331,3 +331,13 @@ ht_status ht_las_launch(const float *q, int n_patches, int n, int mode, int n_ra
     }
     return HT_OK;
 }
+
+void ht_preload_spectrum()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_fft_rows);
+    cudaFuncGetAttributes(&fa, k_fft_cols);
+    cudaFuncGetAttributes(&fa, k_bin_accum);
+    cudaFuncGetAttributes(&fa, k_bin_finalize);
+    cudaFuncGetAttributes(&fa, k_apply_G);
+}

@@ -62,9 +62,17 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_fla
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 31u) == 0) {
             if (!ignore_abort && *abort_flag) return false;
-            if (globaltimer_ns() - t0 > kTimeoutNs || it > (1u << 28)) {
+            const uint64_t el = globaltimer_ns() - t0;
+            if (el > kTimeoutNs || it > (1u << 28)) {
                 *abort_flag = 1;
                 atomicExch(err, (int)HT_ERR_TIMEOUT);
+                if (atomicCAS(err + 1, 0, 1) == 0) {        // first expiry: where, and after how long
+                    err[2] = (int)bar;
+                    err[3] = (int)((blockDim.x << 16) | (threadIdx.x >> 5));
+                    err[4] = (int)blockIdx.x;
+                    err[5] = (int)it;
+                    *reinterpret_cast<unsigned long long *>(err + 6) = el;
+                }
                 return false;
             }
         }
@@ -249,8 +257,11 @@ struct UnitInfo {
     int H, W, x0, y0, nrows;
 };
 
-// Unit u of a call: RU rows x one 128-pixel column tile of one image.
-__device__ __forceinline__ UnitInfo unit_info(const ImgDesc *imgs, int n_imgs, int in_buf, int u)
+// Unit u of a call: ru (<= RU) rows x one 128-pixel column tile of one image.
+// order 0 walks an image's units row band by row band, order 1 column tile by
+// column tile.
+__device__ __forceinline__ UnitInfo unit_info(const ImgDesc *imgs, int n_imgs, int in_buf, int u, int ru = RU,
+                                              int order = 0)
 {
     const int im = find_image(n_imgs, u, [&](int i) { return __ldg(&imgs[i].unit_begin); });
     const ImgDesc *D = imgs + im;
@@ -260,9 +271,15 @@ __device__ __forceinline__ UnitInfo unit_info(const ImgDesc *imgs, int n_imgs, i
     ui.D = D;
     ui.H = __ldg(&D->H);
     ui.W = __ldg(&D->W);
-    ui.x0 = (lu % xt) * TILE_M;
-    ui.y0 = (lu / xt) * RU;
-    ui.nrows = min(ui.H, ui.y0 + RU) - ui.y0;
+    if (order == 0) {
+        ui.x0 = (lu % xt) * TILE_M;
+        ui.y0 = (lu / xt) * ru;
+    } else {
+        const int nb = (ui.H + ru - 1) / ru;
+        ui.x0 = (lu / nb) * TILE_M;
+        ui.y0 = (lu % nb) * ru;
+    }
+    ui.nrows = min(ui.H, ui.y0 + ru) - ui.y0;
     ui.in = (const uint8_t *)D->act[in_buf];
     ui.out = D->act[in_buf ^ 1];
     return ui;
@@ -270,13 +287,13 @@ __device__ __forceinline__ UnitInfo unit_info(const ImgDesc *imgs, int n_imgs, i
 
 // Work-index layout of one image inside a call's table: conv units, head tiles,
 // layer-1 input groups (prefix sums over the images in table order).
-inline void set_begins(ImgDesc &D, int &units, int &hd, int &pre)
+inline void set_begins(ImgDesc &D, int &units, int &hd, int &pre, int ru = RU)
 {
     D.xtiles = (D.W + TILE_M - 1) / TILE_M;
     D.unit_begin = units;
     D.hd_begin = hd;
     D.pre_begin = pre;
-    units += D.xtiles * ((D.H + RU - 1) / RU);
+    units += D.xtiles * ((D.H + ru - 1) / ru);
     hd += ((D.W + HT_X - 1) / HT_X) * ((D.H + HT_Y - 1) / HT_Y);
     pre += (int)(((size_t)D.H * D.W + 3) / 4);
 }

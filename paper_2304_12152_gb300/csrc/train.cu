@@ -521,3 +521,15 @@ ht_status ht_train_step_bwd(ht_train *t, float *grad_w, float *grad_b, void *str
 }
 
 }  // extern "C"
+
+void ht_preload_train()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_fill);
+    cudaFuncGetAttributes(&fa, k_sample_bits);
+    cudaFuncGetAttributes(&fa, k_marl);
+    cudaFuncGetAttributes(&fa, k_scale_into);
+    cudaFuncGetAttributes(&fa, k_dlogit);
+    cudaFuncGetAttributes(&fa, k_flip);
+    cudaFuncGetAttributes(&fa, k_wgrad);
+}

@@ -18,8 +18,8 @@
 //   layer 1 (CUDA cores, k_first_wgrad): dW_1 = sum_px g_1 (x) (c, z)(shifted), db_1.
 // Rounding points (the oracle's quant-1 backward follows them): inner-layer
 // weights bf16 in both passes, activations and hidden gradients stored bf16,
-// FP32 accumulation, weight-gradient partial sums reduced in FP64 in a fixed
-// order (deterministic).
+// FP32 accumulation, weight-gradient partial sums reduced with compensated FP32
+// sums in a fixed order (deterministic).
 #include <string.h>
 
 #include <vector>
@@ -46,6 +46,19 @@ namespace {
 // the start, sum the staged gradient rows per channel while the MMAs run (bias
 // gradient), and write the CTA's partial sums at the end.
 // ---------------------------------------------------------------------------
+// Compensated (Kahan) FP32 accumulation: error ~1 ulp of the sum whatever the
+// number of terms, in a fixed order (deterministic), without the GPU's slow FP64 pipe.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
 constexpr int WG_NSA = 6;                       // activation-row ring (+1 mirror slot)
 constexpr int WG_NSG = 3;                       // gradient-row ring
 constexpr int WG_ASLOT = 8 * ROW_PX * 16;       // [chunk][130 px][16 B]
@@ -336,30 +349,42 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
 }
 
 // dW[n][c][dy][dx] and db[n] of a 64 -> 64 layer from the CTAs' partial sums
-// (FP64, CTA order).  Thread = (tile, n, lane) so that the partial reads coalesce.
-__global__ void k_reduce_wgrad_tc(const float *__restrict__ partials, const float *__restrict__ colsum, int ncta,
-                                  float *__restrict__ gw, float *__restrict__ gb)
+// (compensated FP32, fixed order: slice r sums CTAs r, r + 4, ..., then the slices
+// in order).
+// Block = 64 values (tile, n, lane order, so the reads coalesce) x 4 CTA slices.
+constexpr int RWG_VALS = WG_TILES * 64 * 128 + 64;
+__global__ void __launch_bounds__(256) k_reduce_wgrad_tc(const float *__restrict__ partials,
+                                                         const float *__restrict__ colsum, int ncta,
+                                                         float *__restrict__ gw, float *__restrict__ gb)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float s_part[4][2][64];
+    const int v = threadIdx.x & 63, r = threadIdx.x >> 6;
+    const int i = blockIdx.x * 64 + v;
+    const size_t st = (size_t)WG_TILES * 64 * 128;
+    Kahan acc;
+    if (i < WG_TILES * 64 * 128) {
+#pragma unroll 4
+        for (int k = r; k < ncta; k += 4) acc.add(partials[(size_t)k * st + i]);
+    } else if (i < RWG_VALS) {
+        for (int k = r; k < ncta; k += 4) acc.add(colsum[(size_t)k * 64 + (i - WG_TILES * 64 * 128)]);
+    }
+    s_part[r][0][v] = acc.s;
+    s_part[r][1][v] = acc.c;
+    __syncthreads();
+    if (r != 0 || i >= RWG_VALS) return;
+    for (int k = 1; k < 4; ++k) {
+        acc.add(s_part[k][0][v]);
+        acc.add(-s_part[k][1][v]);
+    }
+    const float s = acc.s;
     if (i < WG_TILES * 64 * 128) {
         const int t = i / (64 * 128), n = (i / 128) % 64, lane = i % 128;
         const int dx = t >> 1, pair = t & 1;
         if (pair == 1 && lane >= 64) return;               // rows of no tap
         const int dy = pair ? 2 : (lane >> 6), c = lane & 63;
-        double s[4] = {0.0, 0.0, 0.0, 0.0};              // CTA k goes to s[k % 4]; fixed order
-        const size_t st = (size_t)WG_TILES * 64 * 128;
-        int k = 0;
-        for (; k + 4 <= ncta; k += 4) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) s[j] += (double)partials[(size_t)(k + j) * st + i];
-        }
-        for (; k < ncta; ++k) s[k & 3] += (double)partials[(size_t)k * st + i];
-        gw[((n * 64 + c) * 3 + dy) * 3 + dx] = (float)((s[0] + s[1]) + (s[2] + s[3]));
-    } else if (i < WG_TILES * 64 * 128 + 64) {
-        const int n = i - WG_TILES * 64 * 128;
-        double s = 0.0;
-        for (int k = 0; k < ncta; ++k) s += (double)colsum[(size_t)k * 64 + n];
-        gb[n] = (float)s;
+        gw[((n * 64 + c) * 3 + dy) * 3 + dx] = s;
+    } else {
+        gb[i - WG_TILES * 64 * 128] = s;
     }
 }
 
@@ -397,7 +422,7 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_bwd(const HeadBwdParams P)
     __shared__ float s_dz[HT_Y + 2][HT_X + 2];
     __shared__ __align__(16) __nv_bfloat16 s_a[(HT_Y + 2) * (HT_X + 2) * 64];
     const int tid = threadIdx.y * HT_X + threadIdx.x;
-    float wacc[3] = {0.f, 0.f, 0.f};                    // entries tid, tid + 256, tid + 512 (< 577)
+    float wacc[3] = {0.f, 0.f, 0.f};                    // (c, dy) threads: dx = 0, 1, 2; thread 192: bias
     for (int tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x) {
         const int im = find_image(P.n_imgs, tile, [&](int i) { return __ldg(&P.imgs[i].hd_begin); });
         const ImgDesc *D = P.imgs + im;
@@ -439,30 +464,34 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_bwd(const HeadBwdParams P)
             }
             store_pixel(g, D->act[1], 0, 1.f, H, W, y, x);
         }
-        // weight and bias gradient sums of this tile
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const int idx = tid + r * HT_X * HT_Y;
-            if (idx < 576) {
-                const int c = idx % 64, t = idx / 64, dy = t / 3, dx = t % 3;
-                float s = 0.f;
-                for (int py = 0; py < HT_Y; ++py)
+        // weight and bias gradient sums of this tile: thread (c, dy) keeps the three dx
+        // taps and slides along the row (one activation load per pixel); thread 192 sums dz
+        if (tid < 192) {
+            const int c = tid & 63, dy = tid >> 6;
+            for (int py = 0; py < HT_Y; ++py) {
+                const __nv_bfloat16 *arow = s_a + (size_t)(py + dy) * (HT_X + 2) * 64 + c;
+                float a0 = __bfloat162float(arow[0]), a1 = __bfloat162float(arow[64]);
 #pragma unroll 8
-                    for (int px = 0; px < HT_X; ++px)
-                        s = fmaf(s_dz[py + 1][px + 1], __bfloat162float(s_a[((py + dy) * (HT_X + 2) + px + dx) * 64 + c]), s);
-                wacc[r] += s;
-            } else if (idx == 576) {
-                float s = 0.f;
-                for (int py = 0; py < HT_Y; ++py)
-                    for (int px = 0; px < HT_X; ++px) s += s_dz[py + 1][px + 1];
-                wacc[r] += s;
+                for (int px = 0; px < HT_X; ++px) {
+                    const float a2 = __bfloat162float(arow[(px + 2) * 64]);
+                    const float d = s_dz[py + 1][px + 1];
+                    wacc[0] = fmaf(d, a0, wacc[0]);
+                    wacc[1] = fmaf(d, a1, wacc[1]);
+                    wacc[2] = fmaf(d, a2, wacc[2]);
+                    a0 = a1;
+                    a1 = a2;
+                }
             }
+        } else if (tid == 192) {
+            for (int py = 0; py < HT_Y; ++py)
+                for (int px = 0; px < HT_X; ++px) wacc[0] += s_dz[py + 1][px + 1];
         }
     }
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const int idx = tid + r * HT_X * HT_Y;
-        if (idx < 577) P.partials[(size_t)blockIdx.x * 577 + idx] = wacc[r];
+    if (tid < 192) {
+        const int c = tid & 63, dy = tid >> 6;
+        for (int dx = 0; dx < 3; ++dx) P.partials[(size_t)blockIdx.x * 577 + (dy * 3 + dx) * 64 + c] = wacc[dx];
+    } else if (tid == 192) {
+        P.partials[(size_t)blockIdx.x * 577 + 576] = wacc[0];
     }
 }
 
@@ -478,8 +507,14 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_first_wgrad(const ImgDesc *__res
 {
     __shared__ float s_x[2][HT_Y + 2][HT_X + 2];
     __shared__ __align__(16) __nv_bfloat16 s_g[HT_Y * HT_X * 64];
+    __shared__ float s_half[1216];
     const int tid = threadIdx.y * HT_X + threadIdx.x;
-    float wacc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};          // entries tid + 256 r (< 1216)
+    // thread (n, ci, half): the nine taps of weight (n, ci) over tile rows half*4 .. +3;
+    // ci = 0 threads also sum g[n] (bias)
+    const int n = tid & 63, ci = (tid >> 6) & 1, half = tid >> 7;
+    float wacc[9], bacc = 0.f;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) wacc[t] = 0.f;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int im = find_image(n_imgs, tile, [&](int i) { return __ldg(&imgs[i].hd_begin); });
         const ImgDesc *D = imgs + im;
@@ -503,55 +538,61 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_first_wgrad(const ImgDesc *__res
             *reinterpret_cast<uint4 *>(&s_g[(size_t)p * 64 + chunk * 8]) = q;
         }
         __syncthreads();
+        for (int py = half * (HT_Y / 2); py < (half + 1) * (HT_Y / 2); ++py)
+#pragma unroll 4
+            for (int px = 0; px < HT_X; ++px) {
+                const float g = __bfloat162float(s_g[(py * HT_X + px) * 64 + n]);
+                bacc += g;
 #pragma unroll
-        for (int r = 0; r < 5; ++r) {
-            const int idx = tid + r * HT_X * HT_Y;
-            float s = 0.f;
-            if (idx < 1152) {
-                const int n = idx % 64, k = idx / 64, ci = k / 9, t = k % 9, dy = t / 3, dx = t % 3;
-                for (int py = 0; py < HT_Y; ++py)
-#pragma unroll 8
-                    for (int px = 0; px < HT_X; ++px)
-                        s = fmaf(__bfloat162float(s_g[(py * HT_X + px) * 64 + n]), s_x[ci][py + dy][px + dx], s);
-            } else if (idx < 1216) {
-                const int n = idx - 1152;
-                for (int p = 0; p < HT_Y * HT_X; ++p) s += __bfloat162float(s_g[p * 64 + n]);
+                for (int t = 0; t < 9; ++t) wacc[t] = fmaf(g, s_x[ci][py + t / 3][px + t % 3], wacc[t]);
             }
-            wacc[r] += s;
-        }
     }
+    // combine the two row halves in a fixed order
+    __syncthreads();
+    if (half == 1) {
 #pragma unroll
-    for (int r = 0; r < 5; ++r) {
-        const int idx = tid + r * HT_X * HT_Y;
-        if (idx < 1216) partials[(size_t)blockIdx.x * 1216 + idx] = wacc[r];
+        for (int t = 0; t < 9; ++t) s_half[(ci * 9 + t) * 64 + n] = wacc[t];
+        if (ci == 0) s_half[1152 + n] = bacc;
+    }
+    __syncthreads();
+    if (half == 0) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+            partials[(size_t)blockIdx.x * 1216 + (ci * 9 + t) * 64 + n] = wacc[t] + s_half[(ci * 9 + t) * 64 + n];
+        if (ci == 0) partials[(size_t)blockIdx.x * 1216 + 1152 + n] = bacc + s_half[1152 + n];
     }
 }
 
-// Sum of per-block partials (FP64, fixed order: slice r sums blocks r, r + 8, ...,
-// then the 8 slices in order).  CTA = 32 values x 8 slices.  mode 0: head, entries
+// Sum of per-block partials (compensated FP32, fixed order: slice r sums blocks r,
+// r + 8, ..., then the 8 slices in order).  CTA = 32 values x 8 slices.  mode 0: head, entries
 // [tap][c] + bias; mode 1: layer 1, entries [(ci*9 + tap)][n] + 64 biases.
 __global__ void __launch_bounds__(256) k_reduce_blocks(const float *__restrict__ partials, int nblk, int nval, int mode,
                                                        float *__restrict__ gw, float *__restrict__ gb)
 {
-    __shared__ double s_part[8][32];
+    __shared__ float s_part[8][2][32];
     const int v = threadIdx.x & 31, r = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + v;
-    double s = 0.0;
+    Kahan acc;
     if (i < nval)
-        for (int b = r; b < nblk; b += 8) s += (double)partials[(size_t)b * nval + i];
-    s_part[r][v] = s;
+        for (int b = r; b < nblk; b += 8) acc.add(partials[(size_t)b * nval + i]);
+    s_part[r][0][v] = acc.s;
+    s_part[r][1][v] = acc.c;
     __syncthreads();
     if (r != 0 || i >= nval) return;
-    for (int k = 1; k < 8; ++k) s += s_part[k][v];
+    for (int k = 1; k < 8; ++k) {
+        acc.add(s_part[k][0][v]);
+        acc.add(-s_part[k][1][v]);
+    }
+    const float s = acc.s;
     if (mode == 0) {
-        if (i < 576) gw[(i % 64) * 9 + i / 64] = (float)s;       // W_head[0][c][tap]
-        else gb[0] = (float)s;
+        if (i < 576) gw[(i % 64) * 9 + i / 64] = s;              // W_head[0][c][tap]
+        else gb[0] = s;
     } else {
         if (i < 1152) {
             const int n = i % 64, k = i / 64;                      // k = ci*9 + tap
-            gw[(n * 2 + k / 9) * 9 + k % 9] = (float)s;
+            gw[(n * 2 + k / 9) * 9 + k % 9] = s;
         } else {
-            gb[i - 1152] = (float)s;
+            gb[i - 1152] = s;
         }
     }
 }
@@ -791,8 +832,8 @@ ht_status ht_train_tc_backward(ht_policy *p, ht_train_tc_ws &w, int nimg, uint64
         k_wgrad_tc<<<grid, WG_NTHREADS, WG_SMEM, s>>>(P);
         ht_prof_stop(s);
         HT_LAUNCH_CHECK();
-        k_reduce_wgrad_tc<<<nblk256(WG_TILES * 64 * 128 + 64), 256, 0, s>>>(P.partials, P.colsum, grid,
-                                                                           grad_w + p->w_off[l], grad_b + p->b_off[l]);
+        k_reduce_wgrad_tc<<<(RWG_VALS + 63) / 64, 256, 0, s>>>(P.partials, P.colsum, grid, grad_w + p->w_off[l],
+                                                               grad_b + p->b_off[l]);
         HT_LAUNCH_CHECK();
         ht_tc_layer a{};
         a.table = tab(T_DG(L, l));
@@ -813,4 +854,16 @@ ht_status ht_train_tc_backward(ht_policy *p, ht_train_tc_ws &w, int nimg, uint64
     k_reduce_blocks<<<(1216 + 31) / 32, 256, 0, s>>>(wpart, nbg, 1216, 1, grad_w + p->w_off[0], grad_b + p->b_off[0]);
     HT_LAUNCH_CHECK();
     return HT_OK;
+}
+
+void ht_preload_train_tc()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_wgrad_tc);
+    cudaFuncGetAttributes(&fa, k_reduce_wgrad_tc);
+    cudaFuncGetAttributes(&fa, k_pack_dgrad);
+    cudaFuncGetAttributes(&fa, k_head_bwd);
+    cudaFuncGetAttributes(&fa, k_first_wgrad);
+    cudaFuncGetAttributes(&fa, k_reduce_blocks);
+    cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM);
 }

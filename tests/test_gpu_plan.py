@@ -1,0 +1,114 @@
+"""CUDA-graph plans and the conv-schedule autotuner (tensor-core forms).
+
+A plan replays the exact launch sequence of ht_halftone, and every schedule the
+autotuner tries keeps each output pixel's accumulation order, so the outputs are
+compared bit for bit: plan vs direct call, every schedule vs the default one."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2304_12152_gb300 import _native as N
+from paper_2304_12152_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(300, 200), (37, 515), (129, 131), (8, 9)]     # ragged tiles, partial units, a tiny image
+
+
+def _batch(seed):
+    return [torch.from_numpy(synth.contone_image(h, w, seed=seed, index=i)).cuda() for i, (h, w) in enumerate(SHAPES)]
+
+
+def _policy(prec, chs=synth.NET_WIDE, seed=5):
+    ws, bs = synth.he_normal_policy(chs, seed)
+    return api.Policy(chs, ws, bs, precision=prec), ws, bs
+
+
+@pytest.mark.parametrize("prec", [N.HT_BF16, N.HT_FP8_E4M3])
+def test_plan_matches_direct_call(prec):
+    pol, _, _ = _policy(prec)
+    imgs = _batch(3)
+    if prec == N.HT_FP8_E4M3:
+        pol.calibrate(imgs[0], seed=9)
+    ref, pref = pol.halftone(imgs, mode=N.HT_MODE_BERNOULLI, seed=7, want_prob=True)
+    bits = [torch.zeros_like(b) for b in ref]
+    probs = [torch.zeros_like(p) for p in pref]
+    plan = api.Plan(pol, imgs, bits, N.HT_MODE_BERNOULLI, 7, probs)
+    for _ in range(2):
+        plan.launch()
+    torch.cuda.synchronize()
+    for a, b in zip(bits, ref):
+        assert torch.equal(a, b)
+    for a, b in zip(probs, pref):
+        assert torch.equal(a, b)
+
+
+def test_plan_recaptures_after_weight_change():
+    pol, ws, bs = _policy(N.HT_BF16)
+    imgs = _batch(4)
+    bits = [pol.alloc_bits(c.shape[0], c.shape[1]) for c in imgs]
+    plan = api.Plan(pol, imgs, bits, N.HT_MODE_THRESHOLD, 1)
+    plan.launch()
+    ws2, bs2 = synth.he_normal_policy(synth.NET_WIDE, 6)
+    w = torch.from_numpy(np.concatenate([x.ravel() for x in ws2])).cuda()
+    b = torch.from_numpy(np.concatenate([x.ravel() for x in bs2])).cuda()
+    pol.set_weights(w, b)
+    plan.launch()                                  # new weights -> captured again
+    ref, _ = pol.halftone(imgs, mode=N.HT_MODE_THRESHOLD, seed=1)
+    torch.cuda.synchronize()
+    for a, r in zip(bits, ref):
+        assert torch.equal(a, r)
+
+
+def test_plan_refuses_fp32():
+    pol, _, _ = _policy(N.HT_FP32, chs=synth.NET_SMALL)
+    imgs = _batch(5)[:1]
+    bits = [pol.alloc_bits(c.shape[0], c.shape[1]) for c in imgs]
+    with pytest.raises(N.HTError):
+        api.Plan(pol, imgs, bits, N.HT_MODE_THRESHOLD, 0)
+
+
+def test_autotune_schedules_are_bit_identical():
+    pol, _, _ = _policy(N.HT_BF16)
+    imgs = _batch(6)
+    ref, pref = pol.halftone(imgs, mode=N.HT_MODE_BERNOULLI, seed=2, want_prob=True)
+    bits = [torch.zeros_like(b) for b in ref]
+    probs = [torch.zeros_like(p) for p in pref]
+    res = pol.autotune(imgs, bits, N.HT_MODE_BERNOULLI, 2, probs, reps=2)
+    torch.cuda.synchronize()
+    assert len(res) == N.HT_TUNE_CANDIDATES
+    assert sorted((r, o) for r, o, _ in res) == sorted([(8, 0), (8, 1), (6, 0), (6, 1), (4, 0), (4, 1)])
+    assert all(ms > 0 for _, _, ms in res)
+    # the last candidate's outputs, and the chosen schedule's later calls, equal the default schedule's
+    for a, b in zip(bits, ref):
+        assert torch.equal(a, b)
+    for a, b in zip(probs, pref):
+        assert torch.equal(a, b)
+    again, pagain = pol.halftone(imgs, mode=N.HT_MODE_BERNOULLI, seed=2, want_prob=True)
+    torch.cuda.synchronize()
+    for a, b in zip(again, ref):
+        assert torch.equal(a, b)
+    for a, b in zip(pagain, pref):
+        assert torch.equal(a, b)
+
+
+def test_many_short_units_every_schedule():
+    """Stress of the conv pipeline's per-block barriers: 160 images of 13 x 300 give
+    CTAs long runs of units whose last row band is short (5 of 8 rows, and for rows per
+    unit 6 / 4 other remainders), i.e. TMEM blocks left unused unit after unit.  Every
+    schedule must finish without a wait expiring and give the same bits."""
+    pol, _, _ = _policy(N.HT_BF16)
+    imgs = [torch.from_numpy(synth.contone_image(13, 300, seed=8, index=i)).cuda() for i in range(160)]
+    bits = [pol.alloc_bits(13, 300) for _ in imgs]
+    ref = None
+    for ru, order in [(8, 0), (8, 1), (6, 0), (6, 1), (4, 0), (4, 1), (3, 0), (7, 1)]:
+        pol.set_schedule(ru, order)
+        for _ in range(3):
+            pol.halftone_into(imgs, bits, N.HT_MODE_BERNOULLI, 3)
+            api.sync()
+        if ref is None:
+            ref = [b.clone() for b in bits]
+        else:
+            for a, b in zip(bits, ref):
+                assert torch.equal(a, b), (ru, order)
+    pol.set_schedule(8, 0)
