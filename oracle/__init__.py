@@ -271,6 +271,20 @@ def set_num_threads(n: int) -> None:
 # above (Algorithm 1).
 # ---------------------------------------------------------------------------
 
+def coma_surrogate(prob: np.ndarray, h_bits: np.ndarray, dR: np.ndarray, R: float):
+    """Eq. (coma) with the counterfactual baseline Eq. (baseline), one sample:
+    b_a = sum_{h'} pi_a(h') R({h', h_-a}), so R(h) - b_a = (1 - p_a) dR_a if h_a = 1 and
+    -p_a dR_a if h_a = 0, with dR_a = R(h_a = 1) - R(h_a = 0).  Surrogate loss
+    L_COMA = -sum_a log pi_a(h_a) (R(h) - b_a) with R - b held constant.
+    Returns (value, dL/dp) where d log pi_a(h_a) / dp_a = h_a / p_a - (1 - h_a) / (1 - p_a)."""
+    p = prob.reshape(dR.shape).astype(np.float64)
+    hb = h_bits.reshape(dR.shape).astype(np.float64)
+    adv = np.where(hb > 0, (1.0 - p) * dR, -p * dR)
+    logpi = np.where(hb > 0, np.log(np.where(hb > 0, p, 1.0)), np.log(np.where(hb > 0, 1.0, 1.0 - p)))
+    dlogpi = np.where(hb > 0, 1.0 / np.where(hb > 0, p, 1.0), -1.0 / np.where(hb > 0, 1.0, 1.0 - p))
+    return float(-np.sum(logpi * adv)), -dlogpi * adv
+
+
 def le_surrogate(prob: np.ndarray, h_bits: np.ndarray, dR: np.ndarray, R: float):
     """Eq. (marl) / Algorithm 1: L_MARL = -sum_a sum_{h'} R({h'_a, h_-a}) pi_a(h'_a)
     for one sample, with R(h_a = h'_a) = R + (h'_a - h_a) dR_a.

@@ -110,7 +110,7 @@ struct ConvParams {
 // accumulator block is zeroed by the epilogue after it is drained, so all MMAs
 // accumulate.  Per output row: 12-15 MMAs of N = 192 instead of 36 of N = 64.
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND>
+template <bool FP8, int KIND, bool TR = false>
 __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 {
     using C = Cfg<FP8, KIND>;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 if (lane == 0) mbar_arrive(smem_u32(&bfree[j]));
                 if (j < nrows && x < ui.W) {
                     const size_t o = (size_t)(y0 + j) * ui.W + x;
-                    if (P.dgrad) {
+                    if (TR && P.dgrad) {
                         // data gradient: mask by the ReLU of the layer this gradient flows into
                         const uint2 m = __ldg(ui.D->mask + o);
 #pragma unroll
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     }
 #pragma unroll
                     for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], P.scale[n], P.bias[n]), 0.f);
-                    if (ui.D->mask) {
+                    if (TR && ui.D->mask) {
                         // training forward: which stored (bf16) activations are positive
                         uint2 m = make_uint2(0u, 0u);
 #pragma unroll
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         }
 #pragma unroll
                         for (int t = 0; t < 9; ++t) partials[t * plane + o] = acc[t];
-                        if (ui.D->save) store_pixel(v, ui.D->save, 0, 1.f, ui.H, ui.W, y0 + j, x);
+                        if (TR && ui.D->save) store_pixel(v, ui.D->save, 0, 1.f, ui.H, ui.W, y0 + j, x);
                     } else {
                         store_pixel(v, ui.out, P.out_fp8, P.out_inv_scale, ui.H, ui.W, y0 + j, x);
                     }
@@ -473,12 +473,12 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__r
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND>
+template <bool FP8, int KIND, bool TR = false>
 ht_status ensure_attr()
 {
     static bool attr_set = false;
     if (!attr_set) {
-        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg<FP8, KIND>::SMEM));
         attr_set = true;
     }
@@ -492,20 +492,21 @@ ht_status ensure_all_attrs()
     if ((st = ensure_attr<false, KIND_HIDDEN>()) != HT_OK || (st = ensure_attr<false, KIND_HEADPART>()) != HT_OK ||
         (st = ensure_attr<false, KIND_FIRST>()) != HT_OK || (st = ensure_attr<false, KIND_HEAD4>()) != HT_OK ||
         (st = ensure_attr<true, KIND_HIDDEN>()) != HT_OK || (st = ensure_attr<true, KIND_HEADPART>()) != HT_OK ||
-        (st = ensure_attr<true, KIND_FIRST>()) != HT_OK)
+        (st = ensure_attr<true, KIND_FIRST>()) != HT_OK || (st = ensure_attr<false, KIND_HIDDEN, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HEADPART, true>()) != HT_OK || (st = ensure_attr<false, KIND_FIRST, true>()) != HT_OK)
         return st;
     return HT_OK;
 }
 
-template <bool FP8, int KIND>
+template <bool FP8, int KIND, bool TR = false>
 ht_status launch_conv(const ConvParams &P, cudaStream_t s)
 {
-    const ht_status st = ensure_attr<FP8, KIND>();
+    const ht_status st = ensure_attr<FP8, KIND, TR>();
     if (st != HT_OK) return st;
     const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
     ht_prof_start(KIND == KIND_FIRST ? HTK_FIRST_TC : KIND == KIND_HEAD4 ? HTK_HEAD_TC
                                                   : FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
-    k_conv_tc<FP8, KIND><<<grid, NTHREADS, Cfg<FP8, KIND>::SMEM, s>>>(P);
+    k_conv_tc<FP8, KIND, TR><<<grid, NTHREADS, Cfg<FP8, KIND>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -744,6 +745,9 @@ void ht_preload_conv_tc()
     cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_HIDDEN>);
     cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_HEADPART>);
     cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_FIRST>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEADPART, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, true>);
     cudaFuncGetAttributes(&fa, k_first_input);
     cudaFuncGetAttributes(&fa, k_head_partials);
     ensure_all_attrs();
@@ -772,9 +776,9 @@ ht_status ht_tc_conv(const ht_tc_layer &a, cudaStream_t s)
     P.order = 0;
     P.err = err;
     switch (a.kind) {
-    case KIND_HIDDEN: return launch_conv<false, KIND_HIDDEN>(P, s);
-    case KIND_HEADPART: return launch_conv<false, KIND_HEADPART>(P, s);
-    case KIND_FIRST: return launch_conv<false, KIND_FIRST>(P, s);
+    case KIND_HIDDEN: return launch_conv<false, KIND_HIDDEN, true>(P, s);
+    case KIND_HEADPART: return launch_conv<false, KIND_HEADPART, true>(P, s);
+    case KIND_FIRST: return launch_conv<false, KIND_FIRST, true>(P, s);
     default: ht_set_error("ht_tc_conv: bad kind %d", a.kind); return HT_ERR_INVALID_ARG;
     }
 }
