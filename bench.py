@@ -200,6 +200,7 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--ref-side", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default="", help="ROWS,ORDER: set the conv schedule instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -244,10 +245,15 @@ def main():
     tune = None
     plan = None
     if prec != N.HT_FP32:
-        res = pol.autotune(cs, bits, mode, seed, reps=2)
-        best = min(res, key=lambda r: r[2])
-        tune = {"choice": {"rows_per_unit": best[0], "unit_order": best[1]},
-                "candidates": [{"rows_per_unit": r, "unit_order": o, "ms": ms} for r, o, ms in res]}
+        if args.schedule:
+            ru, order = (int(x) for x in args.schedule.split(","))
+            pol.set_schedule(ru, order)
+            tune = {"choice": {"rows_per_unit": ru, "unit_order": order}, "candidates": None}
+        else:
+            res = pol.autotune(cs, bits, mode, seed, reps=2)
+            best = min(res, key=lambda r: r[2])
+            tune = {"choice": {"rows_per_unit": best[0], "unit_order": best[1]},
+                    "candidates": [{"rows_per_unit": r, "unit_order": o, "ms": ms} for r, o, ms in res]}
         plan = api.Plan(pol, cs, bits, mode, seed)
 
     def step():

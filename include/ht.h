@@ -245,7 +245,11 @@ typedef struct {
     int n_rad, n_ang;     /* binned form */
     float w_a;            /* anisotropy weight (paper: 0.002) */
     ht_reward_opts reward;
+    int estimator;        /* HT_EST_LE: local expectation (Eq. le, the paper's choice);
+                             HT_EST_COMA: counterfactual baseline (Eq. coma) */
 } ht_train_desc;
+
+enum { HT_EST_LE = 0, HT_EST_COMA = 1 };
 
 typedef struct ht_train ht_train;
 

@@ -16,6 +16,7 @@ HT_OK, HT_ERR_INVALID_ARG, HT_ERR_UNSUPPORTED, HT_ERR_OOM, HT_ERR_CUDA, HT_ERR_T
 HT_FP32, HT_BF16, HT_FP8_E4M3 = 0, 1, 2
 HT_HEAD_SIGMOID, HT_HEAD_SOFTMAX = 0, 1
 HT_MODE_THRESHOLD, HT_MODE_BERNOULLI = 0, 1
+HT_EST_LE, HT_EST_COMA = 0, 1
 
 # Every entry point declared in include/ht.h.
 EXPORTS = (
@@ -57,7 +58,7 @@ HT_TUNE_CANDIDATES = 6
 class TrainDesc(C.Structure):
     _fields_ = [("max_crops", C.c_int), ("crop_h", C.c_int), ("crop_w", C.c_int), ("n_gray", C.c_int),
                 ("gray_n", C.c_int), ("n_samples", C.c_int), ("las_mode", C.c_int), ("n_rad", C.c_int),
-                ("n_ang", C.c_int), ("w_a", C.c_float), ("reward", RewardOpts)]
+                ("n_ang", C.c_int), ("w_a", C.c_float), ("reward", RewardOpts), ("estimator", C.c_int)]
 
 
 _lock = threading.Lock()

@@ -14,7 +14,7 @@
 //      Eq. le, Sec. III-C);
 //   4. L_MARL = -(1/(B S)) sum_{i,s} sum_a sum_{h'} R({h'_a, h_-a}) pi_a(h')
 //      (Algorithm 1, Eq. marl) with R({h'_a, h_-a}) = R + (h'_a - h_a) dR_a, so
-//      dL_MARL/dp_a = -(1/(B S)) sum_s dR^s_a;
+//      dL_MARL/dp_a = -(1/(B S)) sum_s dR^s_a  (or the COMA estimator, k_marl);
 //   5. L_AS on the gray patches' probability maps (Sec. IV, Eq. as, proxy
 //      p(h = 1 | c_g, z_g)), averaged over patches, with its gradient;
 //   6. L_total = L_MARL + w_a L_AS.
@@ -81,10 +81,16 @@ __global__ void k_sample_bits(const float *__restrict__ prob0, size_t px, int H,
     if (threadIdx.x == 0) bits[(size_t)y * words + (x0 >> 5)] = word;
 }
 
-// dp_a = -inv * sum_s dR^s_a; L += -inv * sum_s sum_a (R_s + (p_a - h_a) dR_a)
+// Local expectation (Eq. le, Eq. marl):
+//   dp_a = -inv * sum_s dR^s_a; L += -inv * sum_s sum_a (R_s + (p_a - h_a) dR_a)
+// COMA (Eq. coma, baseline Eq. baseline), R - b_a = (1 - p) dR if h_a = 1, -p dR if 0:
+//   dp_a = -inv * sum_s (d log pi_a(h_a) / dp_a) (R - b_a)
+//        = -inv * sum_s dR^s_a * ((1 - p) / p if h_a = 1, p / (1 - p) if 0)
+//   L += -inv * sum_s sum_a log pi_a(h_a) (R - b_a)
+// (h_a = 1 needs u < p, so p > 0; h_a = 0 needs p <= u < 1: no division by zero.)
 // blockIdx.y = crop i (maps npx apart; S samples per crop).
 __global__ void k_marl(const float *__restrict__ prob0, const float *__restrict__ dR0, const uint32_t *__restrict__ bits0,
-                       const double *__restrict__ rewards0, int S, int H, int W, int words, double inv,
+                       const double *__restrict__ rewards0, int S, int H, int W, int words, double inv, int coma,
                        float *__restrict__ dprob0, double *__restrict__ loss)
 {
     const size_t npx = (size_t)H * W;
@@ -102,9 +108,15 @@ __global__ void k_marl(const float *__restrict__ prob0, const float *__restrict_
         double g = 0.0;
         for (int s = 0; s < S; ++s) {
             const float d = dR[(size_t)s * npx + a];
-            const float h = (float)((bits[(size_t)s * H * words + (size_t)y * words + (x >> 5)] >> (x & 31)) & 1u);
-            g += d;
-            l += -(rewards[4 * s + 3] + ((double)p - h) * (double)d);
+            const bool hb = (bits[(size_t)s * H * words + (size_t)y * words + (x >> 5)] >> (x & 31)) & 1u;
+            if (coma) {
+                g += hb ? d * ((1.f - p) / p) : d * (p / (1.f - p));
+                const float adv = hb ? (1.f - p) * d : -p * d;
+                l += -(double)(hb ? logf(p) : log1pf(-p)) * (double)adv;
+            } else {
+                g += d;
+                l += -(rewards[4 * s + 3] + ((double)p - (hb ? 1.0 : 0.0)) * (double)d);
+            }
         }
         dprob[a] = (float)(-inv * g);
         l *= inv;
@@ -239,6 +251,7 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
         HT_CHECK_ARG(d->gray_n >= 8 && d->gray_n <= 1024 && (d->gray_n & (d->gray_n - 1)) == 0,
                      "gray_n must be a power of two in [8, 1024]");
     HT_CHECK_ARG(d->las_mode == 0 || d->las_mode == 1, "las_mode must be 0 or 1");
+    HT_CHECK_ARG(d->estimator == HT_EST_LE || d->estimator == HT_EST_COMA, "unknown estimator %d", d->estimator);
     if (d->las_mode == 1)
         HT_CHECK_ARG(d->n_rad >= 1 && d->n_rad <= 256 && d->n_ang >= 2 && d->n_ang <= 64, "bad bin counts");
     HT_CHECK_ARG(d->reward.radius >= 1 && d->reward.radius <= 7, "reward radius must be in [1, 7]");
@@ -434,7 +447,7 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
                               t->toggle_scratch_floats, s);
         if (st != HT_OK) return st;
         k_marl<<<dim3(nblk(t->crop_px), n), 256, 0, s>>>(t->prob, t->dR, t->sbits, rewards, S, H, W, words,
-                                                         1.0 / ((double)n * S), t->dprob, t->dacc);
+                                                         1.0 / ((double)n * S), t->d.estimator, t->dprob, t->dacc);
         HT_LAUNCH_CHECK();
     }
     // 5. anisotropy loss on the gray patches' probability maps

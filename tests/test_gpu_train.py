@@ -18,7 +18,7 @@ from paper_2304_12152_gb300 import api, synth
 pytestmark = pytest.mark.gpu
 
 
-def oracle_step(crops, grays, ws, bs, seed, S, w_a, las_mode, n_rad, n_ang, quant=0):
+def oracle_step(crops, grays, ws, bs, seed, S, w_a, las_mode, n_rad, n_ang, quant=0, coma=False):
     n, G = len(crops), len(grays)
     gw = [np.zeros(w.shape) for w in ws]
     gb = [np.zeros(b.shape) for b in bs]
@@ -32,7 +32,7 @@ def oracle_step(crops, grays, ws, bs, seed, S, w_a, las_mode, n_rad, n_ang, quan
             hb = (u < p[0]).astype(np.uint8)
             r = O.reward(c, hb)
             dR = O.toggle_delta(c, hb).reshape(h, w)
-            val, grad = O.le_surrogate(p[0], hb, dR, r["R"])
+            val, grad = (O.coma_surrogate if coma else O.le_surrogate)(p[0], hb, dR, r["R"])
             l_marl += val / (n * S)
             dp += grad / (n * S)
             rs.append(r["R"])
@@ -80,6 +80,27 @@ def test_train_step_matches_oracle(las_mode, n_rad, n_ang):
         assert np.abs(gb[ob:ob + rb.size] - rb).max() <= 2e-3 * scale, l
         ow += rw.size
         ob += rb.size
+
+
+def test_coma_train_step_matches_oracle():
+    """FP32 step with the COMA estimator (Eq. coma) against the oracle's COMA surrogate:
+    same tolerances as the local-expectation step."""
+    chs = (2, 8, 8, 1)
+    ws, _ = synth.he_normal_policy(chs, 71)
+    bs = synth.random_biases(chs, 72, scale=0.1)
+    crops = [synth.contone_image(32, 40, seed=73, index=i) for i in range(2)]
+    S, seed = 3, 13
+    pol = api.Policy(chs, ws, bs, precision=N.HT_FP32)
+    tr = api.Trainer(pol, (32, 40), max_crops=2, n_samples=S, n_gray=0, las_mode=1, n_rad=4, n_ang=4, w_a=0.0,
+                     estimator=N.HT_EST_COMA)
+    losses = tr.forward([torch.from_numpy(c).cuda() for c in crops], [], seed)
+    gw, gb = tr.backward()
+    torch.cuda.synchronize()
+    ref = oracle_step(crops, [], ws, bs, seed, S, 0.0, 1, 4, 4, coma=True)
+    assert abs(losses[1] - ref[1]) <= 1e-4 * abs(ref[1]) + 1e-9, (losses, ref[:4])
+    errs = _grad_errors(gw, gb, ref[4], ref[5])
+    for ew, eb in errs:
+        assert ew <= 2e-3 and eb <= 2e-3, errs
 
 
 def test_autograd_function_drives_adam():
