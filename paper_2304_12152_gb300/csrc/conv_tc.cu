@@ -52,9 +52,10 @@ constexpr int NTHREADS = 320;              // producer, MMA issuer, 8 epilogue w
 // epilogue, and layer 1 (2 -> 64), whose input is the 16-byte-per-pixel bf16
 // hi/lo split of c and z written by k_first_input (one staged chunk; the second
 // K chunk of its MMAs is zero and stays resident in shared memory), and the
-// 64 -> 4 softmax head, whose three dy blocks are 16 columns wide (4 logits + 12
-// zero columns) and whose weights are kept exact as bf16 hi + lo (two MMAs per
-// K step); its epilogue applies softmax, draws the level and packs 2 bits/px.
+// 64 -> 4 softmax head, whose three dy blocks are 16 columns wide (4 logits with
+// bf16 hi weights, the same 4 with the lo parts, 8 zero columns: the weights stay
+// exact as hi + lo in one MMA per K step); its epilogue adds the two parts,
+// applies softmax, draws the level and packs 2 bits/px.
 enum : int { KIND_HIDDEN = 0, KIND_HEADPART = 1, KIND_FIRST = 2, KIND_HEAD4 = 3 };
 
 template <bool FP8, int KIND>
@@ -65,10 +66,8 @@ struct Cfg {
     static constexpr int NCHUNK = FIRST ? 2 : (MMA8 ? 4 : 8);  // 16-byte chunks per staged pixel
     static constexpr int NCOPY = FIRST ? 1 : NCHUNK;           // chunks staged from HBM (layer 1: chunk 1 is zero)
     static constexpr int NOUT = HEAD4 ? 16 : 64;               // output columns per dy block (= TMEM block stride)
-    static constexpr int NHL = HEAD4 ? 2 : 1;                  // weight parts (bf16 hi, lo)
     static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;
-    static constexpr int W_PART = 3 * NCHUNK * 3 * NOUT * 16;  // [dx][chunk][3 dy][NOUT n][16 B]
-    static constexpr int W_BYTES = NHL * W_PART;
+    static constexpr int W_BYTES = 3 * NCHUNK * 3 * NOUT * 16; // [dx][chunk][3 dy][NOUT n][16 B]
     static constexpr int KSTEPS = NCHUNK / 2;                  // MMAs per dx (K = 16 / 32 per MMA)
     static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 4096 /*barriers*/;
 };
@@ -253,12 +252,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                         for (int ks = 0; ks < C::KSTEPS; ++ks)
-#pragma unroll
-                            for (int hl = 0; hl < C::NHL; ++hl)
-                                mma_ss<C::MMA8>(
-                                    d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
-                                    b_q + (uint64_t)((hl * C::W_PART + ((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4),
-                                    idesc, 1u);
+                            mma_ss<C::MMA8>(d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
+                                            b_q + (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4),
+                                            idesc, 1u);
                     mma_commit(smem_u32(&empty[q % NSLOT]));
                     if (k >= 2) mma_commit(smem_u32(&bfull[k - 2]));     // output row k-2 complete
                 }
@@ -329,7 +325,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     if (j < nrows) {
                         float z[4];
 #pragma unroll
-                        for (int k2 = 0; k2 < 4; ++k2) z[k2] = v[k2] + P.bias[k2];
+                        for (int k2 = 0; k2 < 4; ++k2) z[k2] = (v[k2] + v[k2 + 4]) + P.bias[k2];   // hi + lo parts
                         const ImgDesc *D = ui.D;
                         ht_head_emit(z, 4, HT_HEAD_SOFTMAX, P.mode, P.seed, D->image, ui.x0 + quarter * 32, y0 + j,
                                      ui.H, ui.W, D->bits, D->words, D->prob);
@@ -658,8 +654,8 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
         float wl[4 * 64 * 9];
         e = cudaMemcpyAsync(wl, p->d_w + p->w_off[p->L - 1], sizeof(wl), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        const size_t part = (size_t)3 * 8 * 3 * 16 * 8;          // bf16 elements per weight part
-        std::vector<uint16_t> pk(2 * part, 0);
+        const size_t part = (size_t)3 * 8 * 3 * 16 * 8;          // bf16 elements
+        std::vector<uint16_t> pk(part, 0);
         for (int n = 0; n < 4; ++n)
             for (int c = 0; c < 64; ++c)
                 for (int tap = 0; tap < 9; ++tap) {
@@ -670,9 +666,10 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
                     float hf;
                     memcpy(&hf, &hb32, 4);
                     const uint16_t lo = f32_to_bf16_rne(w - hf);
+                    // columns n (hi part) and 4 + n (lo part) of the 16-column dy block
                     const size_t off = ((((size_t)dx * 8 + c / 8) * 3 + (2 - dy)) * 16 + n) * 8 + (c % 8);
                     pk[off] = hi;
-                    pk[part + off] = lo;
+                    pk[off + 4 * 8] = lo;
                 }
         if (e == cudaSuccess && !p->d_wpack4) e = cudaMalloc(&p->d_wpack4, pk.size() * 2);
         if (e == cudaSuccess) e = cudaMemcpy(p->d_wpack4, pk.data(), pk.size() * 2, cudaMemcpyHostToDevice);

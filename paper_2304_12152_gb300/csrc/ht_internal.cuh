@@ -105,7 +105,7 @@ struct ht_policy {
     float h_wscale[HT_MAX_LAYERS * 64];
     float h_headw[9 * 64];          // 1-logit head: last-layer weights as [9 taps][64]
     void *d_w1pack = nullptr;       // layer 1 for the tensor cores: bf16 hi/lo split, [dx][chunk][3 dy][n][8]
-    void *d_wpack4 = nullptr;       // 4-logit head: bf16 hi and lo parts, [part][dx][chunk][3 dy][16 n][8]
+    void *d_wpack4 = nullptr;       // 4-logit head: [dx][chunk][3 dy][16 n][8] bf16, n = hi 0..3, lo 4..7
     float head_bias = 0.f;
     // conv schedule of the tensor-core forms (set by ht_policy_autotune): rows per
     // work unit (TMEM accumulator blocks) and unit order
