@@ -71,11 +71,11 @@ def lib():
                                     C.c_int, C.c_uint64, C.c_uint32, u8p, C.c_void_p]
             L.or_gauss2d.argtypes = [C.c_double, C.c_int, dp]
             L.or_reward.restype = C.c_int
-            L.or_reward.argtypes = [fp, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.POINTER(RewardOpts), dp,
-                                    C.c_void_p, C.c_void_p, C.c_void_p]
+            L.or_reward.argtypes = [fp, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(RewardOpts),
+                                    dp, C.c_void_p, C.c_void_p, C.c_void_p]
             L.or_toggle_delta.restype = C.c_int
-            L.or_toggle_delta.argtypes = [fp, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.POINTER(RewardOpts),
-                                          i64p, C.c_int64, dp]
+            L.or_toggle_delta.argtypes = [fp, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
+                                          C.POINTER(RewardOpts), i64p, C.c_int64, dp]
             L.or_dft2.argtypes = [dp, C.c_void_p, C.c_int, C.c_int, dp, dp]
             L.or_anisotropy_loss.restype = C.c_int
             L.or_anisotropy_loss.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_int, dp, C.c_void_p, C.c_int,
@@ -174,8 +174,10 @@ def gauss2d(sigma: float, radius: int = 5) -> np.ndarray:
     return g
 
 
-def reward(contone: np.ndarray, h_bits: np.ndarray, opts: Optional[RewardOpts] = None, maps: bool = False):
-    """Returns dict(mse, ssim, cssim, R[, e, ssim_map, sigma])."""
+def reward(contone: np.ndarray, h_bits: np.ndarray, opts: Optional[RewardOpts] = None, maps: bool = False,
+           levels: int = 2):
+    """Returns dict(mse, ssim, cssim, R[, e, ssim_map, sigma]).  h_bits: level indices
+    0 .. levels-1 (halftone value index / (levels - 1); binary for levels = 2)."""
     o = opts or reward_opts()
     c = np.ascontiguousarray(contone, dtype=np.float32)
     hb = np.ascontiguousarray(h_bits, dtype=np.uint8)
@@ -185,7 +187,7 @@ def reward(contone: np.ndarray, h_bits: np.ndarray, opts: Optional[RewardOpts] =
     e = s = sg = None
     if maps:
         e = np.zeros((H - 2 * r, W - 2 * r)); s = np.zeros_like(e); sg = np.zeros_like(e)
-    rc = lib().or_reward(c, W, hb, W, H, W, C.byref(o), out, _ptr(e), _ptr(s), _ptr(sg))
+    rc = lib().or_reward(c, W, hb, W, H, W, 1.0 / (levels - 1), C.byref(o), out, _ptr(e), _ptr(s), _ptr(sg))
     if rc != 0:
         raise ValueError("or_reward: image smaller than the window")
     d = dict(mse=out[0], ssim=out[1], cssim=out[2], R=out[3])
@@ -195,7 +197,10 @@ def reward(contone: np.ndarray, h_bits: np.ndarray, opts: Optional[RewardOpts] =
 
 
 def toggle_delta(contone: np.ndarray, h_bits: np.ndarray, idx: Optional[np.ndarray] = None,
-                 opts: Optional[RewardOpts] = None) -> np.ndarray:
+                 opts: Optional[RewardOpts] = None, levels: int = 2, lo: Optional[np.ndarray] = None) -> np.ndarray:
+    """dR_a = R(h_a = hi) - R(h_a = lo) per requested pixel.  Binary: lo 0, hi 1.  Multitone
+    prototype (levels > 2): lo = the lower level index of the pair around the output
+    (multitone_pair), hi = lo + 1; h_bits holds level indices."""
     o = opts or reward_opts()
     c = np.ascontiguousarray(contone, dtype=np.float32)
     hb = np.ascontiguousarray(h_bits, dtype=np.uint8)
@@ -204,7 +209,9 @@ def toggle_delta(contone: np.ndarray, h_bits: np.ndarray, idx: Optional[np.ndarr
         idx = np.arange(H * W, dtype=np.int64)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     out = np.zeros(idx.shape[0], dtype=np.float64)
-    rc = lib().or_toggle_delta(c, W, hb, W, H, W, C.byref(o), idx, idx.shape[0], out)
+    lo_a = None if lo is None else np.ascontiguousarray(lo, dtype=np.uint8).reshape(H, W)
+    rc = lib().or_toggle_delta(c, W, hb, W, H, W, 1.0 / (levels - 1), _ptr(lo_a), C.byref(o), idx, idx.shape[0],
+                               out)
     if rc != 0:
         raise ValueError("or_toggle_delta: image smaller than the window")
     return out
@@ -270,6 +277,38 @@ def set_num_threads(n: int) -> None:
 # Composite helpers written from the paper's formulas on top of the routines
 # above (Algorithm 1).
 # ---------------------------------------------------------------------------
+
+def multitone_pair(v: np.ndarray, levels: int):
+    """Sec. VI-E: the two levels around the output v in [0, 1] with L = levels ink levels,
+    Delta = 1 / (L - 1): lower index k = floor(v (L - 1)) (at most L - 2) and the
+    probability (v - k Delta) / Delta of the upper one.  Returns (k, frac)."""
+    t = np.asarray(v, np.float64) * (levels - 1)
+    k = np.minimum(np.floor(t), levels - 2).astype(np.int64)
+    return k, t - k
+
+
+def sample_multitone(v: np.ndarray, levels: int, u: Optional[np.ndarray] = None):
+    """Action of the multitone prototype: level k + 1 with probability frac, else k
+    (u given: Bernoulli with u < frac; u None: threshold, frac > 0.5)."""
+    k, frac = multitone_pair(v, levels)
+    up = (frac > 0.5) if u is None else (np.asarray(u) < frac)
+    return (k + up).astype(np.uint8)
+
+
+def le_surrogate_multitone(v: np.ndarray, h_levels: np.ndarray, dR: np.ndarray, R: float, levels: int):
+    """L_MARL of the multitone prototype for one sample (Sec. VI-E: the same target with
+    the binary action between the two levels around v):
+      L = -sum_a [pi_a(hi) R(h_a = hi) + pi_a(lo) R(h_a = lo)],
+      pi_a(hi) = (v_a - lo Delta) / Delta, dR_a = R(hi) - R(lo), so dL/dv_a = -dR_a / Delta.
+    Returns (value, dL/dv)."""
+    k, frac = multitone_pair(v.reshape(dR.shape), levels)
+    hl = h_levels.reshape(dR.shape).astype(np.int64)
+    at_hi = (hl == k + 1).astype(np.float64)
+    r_hi = R + (1.0 - at_hi) * dR
+    r_lo = R - at_hi * dR
+    val = -np.sum(frac * r_hi + (1.0 - frac) * r_lo)
+    return float(val), -dR * (levels - 1)
+
 
 def coma_surrogate(prob: np.ndarray, h_bits: np.ndarray, dR: np.ndarray, R: float):
     """Eq. (coma) with the counterfactual baseline Eq. (baseline), one sample:

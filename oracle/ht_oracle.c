@@ -368,16 +368,19 @@ static void gauss2d(double sigma, int r, double *g)
 void or_gauss2d(double sigma, int r, double *g) { gauss2d(sigma, r, g); }
 
 /* Per-output-position terms; hval(y,x) returns the halftone value.  */
+/* h holds level indices; the halftone value is index * hscale (hscale = 1 for a
+ * binary halftone, 1/(L-1) for L ink levels, Sec. VI-E). */
 typedef struct {
     const float *c; int cpitch;
     const uint8_t *hb; int hpitch;
-    int fy, fx; double fval;   /* optional override of one pixel (toggle) */
+    int fy, fx; double fval;   /* optional override of one pixel (toggle), as a value */
+    double hscale;
 } or_img;
 
 static inline double img_h(const or_img *im, int y, int x)
 {
     if (y == im->fy && x == im->fx) return im->fval;
-    return (double)im->hb[(size_t)y * im->hpitch + x];
+    return (double)im->hb[(size_t)y * im->hpitch + x] * im->hscale;
 }
 static inline double img_c(const or_img *im, int y, int x)
 {
@@ -416,7 +419,7 @@ static void term_at(const or_img *im, int y, int x, const or_reward_opts *o,
 
 /* out[0..3] = MSE, SSIM (mean map), CSSIM, R; maps (optional, each M values,
  * row-major over the valid region): e (HVS(h)-HVS(c)), SSIM_j, sigma_j. */
-int or_reward(const float *c, int cpitch, const uint8_t *hb, int hpitch, int h, int w,
+int or_reward(const float *c, int cpitch, const uint8_t *hb, int hpitch, int h, int w, double hscale,
               const or_reward_opts *o, double out[4], double *e_map, double *ssim_map, double *sig_map)
 {
     int r = o->radius;
@@ -426,7 +429,7 @@ int or_reward(const float *c, int cpitch, const uint8_t *hb, int hpitch, int h, 
     double *gw = (double *)malloc((size_t)n * n * sizeof(double));
     gauss2d(o->sigma_hvs, r, ghvs);
     gauss2d(o->sigma_ssim, r, gw);
-    or_img im = {c, cpitch, hb, hpitch, -1, -1, 0.0};
+    or_img im = {c, cpitch, hb, hpitch, -1, -1, 0.0, hscale};
     int vh = h - 2 * r, vw = w - 2 * r;
     double mse = 0, ssim = 0, cssim = 0;
 #pragma omp parallel for reduction(+:mse,ssim,cssim) schedule(static)
@@ -467,9 +470,13 @@ int or_reward(const float *c, int cpitch, const uint8_t *hb, int hpitch, int h, 
 /* Toggle deltas (Eq. le / Eq. marl, Sec. III-C): for each requested pixel a,
  * dR_a = R(h with h_a = 1) - R(h with h_a = 0).  Only the reward terms whose
  * window contains a change; they are recomputed from scratch for both values
- * of h_a (direct windows, no moment updates).  idx: pixel indices y*w+x. */
-int or_toggle_delta(const float *c, int cpitch, const uint8_t *hb, int hpitch, int h, int w,
-                    const or_reward_opts *o, const int64_t *idx, int64_t n_idx, double *out)
+ * of h_a (direct windows, no moment updates).  idx: pixel indices y*w+x.
+ * Multitone prototype (Sec. VI-E): h holds level indices scaled by hscale, and
+ * the two actions of pixel a are the levels lo[a] and lo[a] + 1 around its
+ * output: dR_a = R(h_a = (lo_a + 1) hscale) - R(h_a = lo_a hscale) (lo NULL:
+ * the binary pair 0, 1). */
+int or_toggle_delta(const float *c, int cpitch, const uint8_t *hb, int hpitch, int h, int w, double hscale,
+                    const uint8_t *lo, const or_reward_opts *o, const int64_t *idx, int64_t n_idx, double *out)
 {
     int r = o->radius;
     if (h < 2 * r + 1 || w < 2 * r + 1) return OR_EINVAL;
@@ -488,7 +495,8 @@ int or_toggle_delta(const float *c, int cpitch, const uint8_t *hb, int hpitch, i
             for (int x = ax - r; x <= ax + r; ++x) {
                 if (x < r || x >= w - r) continue;
                 for (int b = 0; b < 2; ++b) {
-                    or_img im = {c, cpitch, hb, hpitch, ay, ax, (double)b};
+                    const double lev = (lo ? (double)lo[(size_t)ay * w + ax] : 0.0) + (double)b;
+                    or_img im = {c, cpitch, hb, hpitch, ay, ax, lev * hscale, hscale};
                     double e2, s, cs;
                     term_at(&im, y, x, o, ghvs, gw, &e2, &s, &cs);
                     double term = -e2 + o->w_s * cs;
