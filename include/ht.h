@@ -68,13 +68,19 @@ typedef enum {
 } ht_status;
 
 typedef enum { HT_FP32 = 0, HT_BF16 = 1, HT_FP8_E4M3 = 2 } ht_precision;
-typedef enum { HT_HEAD_SIGMOID = 0, HT_HEAD_SOFTMAX = 1 } ht_head;
+typedef enum { HT_HEAD_SIGMOID = 0, HT_HEAD_SOFTMAX = 1, HT_HEAD_MULTITONE = 2 } ht_head;
 typedef enum { HT_MODE_THRESHOLD = 0, HT_MODE_BERNOULLI = 1 } ht_mode;
 
 /* Policy network (Sec. III "Agents"; Sec. VI-A): n_layers 3x3 convolutions,
  * stride 1, zero padding 1, ReLU between layers, channels[0] == 2 (c and z),
- * channels[n_layers] == 1 with head SIGMOID or == 4 with head SOFTMAX
- * (4 output levels {0, 1/3, 2/3, 1}, Sec. VI-E).  Hidden widths <= 64.
+ * channels[n_layers] == 1 with head SIGMOID or MULTITONE, == 4 with head SOFTMAX
+ * (4 output levels {0, 1/3, 2/3, 1}).  Hidden widths <= 64.
+ * Heads: SIGMOID = binary halftone, 1 bit/px (Sec. III); SOFTMAX = 4 levels,
+ * softmax over 4 logits, 2 bits/px; MULTITONE = the multitoning prototype of
+ * Sec. VI-E: sigmoid output v, action between the two levels around v among
+ * `levels` (2..4) ink levels k / (levels - 1), the upper one with probability
+ * equal to v's distance from the lower one over the level spacing (threshold
+ * mode: the nearest level), level index packed in 2 bits/px.
  * precision: FP32 = plain CUDA-core form; BF16 / FP8_E4M3 = tensor-core form
  * (hidden widths must then all be 64; FP32 accumulation). */
 typedef struct {
@@ -82,6 +88,7 @@ typedef struct {
     int channels[HT_MAX_LAYERS + 1];
     int head;
     int precision;
+    int levels;           /* MULTITONE head: ink levels, 2..4 (ignored otherwise) */
 } ht_policy_desc;
 
 typedef struct {
@@ -144,12 +151,15 @@ ht_status ht_halftone(ht_policy *p, const ht_image *imgs, int n, int mode, uint6
 typedef struct {
     float sigma_hvs, sigma_ssim, k_contrast, w_s, c1, c2;
     int radius;
+    int levels;           /* 2: binary halftones (1 bit/px); 3 or 4: multi-level halftones of the
+                             multitoning prototype (Sec. VI-E), 2-bit level index per px, value
+                             index / (levels - 1) */
 } ht_reward_opts;
 
-/* Fill opts with the paper's defaults: 2.0, 1.5, 2, 0.06, 1e-4, 9e-4, 5. */
+/* Fill opts with the paper's defaults: 2.0, 1.5, 2, 0.06, 1e-4, 9e-4, 5, levels 2. */
 void ht_reward_opts_default(ht_reward_opts *opts);
 
-/* Reward of n (contone, halftone) pairs (binary halftones only).
+/* Reward of n (contone, halftone) pairs (binary, or multi-level with opts->levels > 2).
  * out: device array of 4*n doubles: MSE, SSIM (mean map), CSSIM, R per image.
  * Requires h, w >= 2r + 1. */
 ht_status ht_reward(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts *opts,
@@ -176,8 +186,12 @@ ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const *bits, int 
 
 /* Toggle deltas of the local-expectation gradient (Eq. le, Sec. III-C):
  * dR[a] = R(h with h_a = 1) - R(h with h_a = 0) for every pixel a.
+ * Multi-level halftones (opts->levels > 2, Sec. VI-E): the two actions of pixel a
+ * are the levels lo = floor(v_a (L - 1)) (at most L - 2) and lo + 1 around the
+ * policy output v_a, and dR[a] = R(h_a = lo + 1) - R(h_a = lo).
+ * v: NULL for binary halftones, else host array of n device pointers to float [h][w].
  * dR: host array of n device pointers, each float [h][w]. */
-ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, int n,
+ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, const float *const *v, int n,
                           const ht_reward_opts *opts, float *const *dR, void *stream);
 
 /* Anisotropy-suppressing loss of n_patches probability maps q (device float

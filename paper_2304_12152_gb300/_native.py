@@ -14,7 +14,7 @@ from . import build as _build
 HT_MAX_LAYERS = 16
 HT_OK, HT_ERR_INVALID_ARG, HT_ERR_UNSUPPORTED, HT_ERR_OOM, HT_ERR_CUDA, HT_ERR_TIMEOUT = range(6)
 HT_FP32, HT_BF16, HT_FP8_E4M3 = 0, 1, 2
-HT_HEAD_SIGMOID, HT_HEAD_SOFTMAX = 0, 1
+HT_HEAD_SIGMOID, HT_HEAD_SOFTMAX, HT_HEAD_MULTITONE = 0, 1, 2
 HT_MODE_THRESHOLD, HT_MODE_BERNOULLI = 0, 1
 HT_EST_LE, HT_EST_COMA = 0, 1
 
@@ -32,7 +32,7 @@ EXPORTS = (
 
 class PolicyDesc(C.Structure):
     _fields_ = [("n_layers", C.c_int), ("channels", C.c_int * (HT_MAX_LAYERS + 1)), ("head", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("levels", C.c_int)]
 
 
 class Image(C.Structure):
@@ -41,7 +41,7 @@ class Image(C.Structure):
 
 class RewardOpts(C.Structure):
     _fields_ = [("sigma_hvs", C.c_float), ("sigma_ssim", C.c_float), ("k_contrast", C.c_float), ("w_s", C.c_float),
-                ("c1", C.c_float), ("c2", C.c_float), ("radius", C.c_int)]
+                ("c1", C.c_float), ("c2", C.c_float), ("radius", C.c_int), ("levels", C.c_int)]
 
 
 class KernelStat(C.Structure):
@@ -101,7 +101,7 @@ def load(build_if_missing: bool = True):
         L.ht_reward_opts_default.restype = None
         L.ht_reward.argtypes = [P(Image), vp, i, P(RewardOpts), vp, vp]
         L.ht_reward_noalloc.argtypes = [P(Image), vp, i, P(RewardOpts), vp, vp]
-        L.ht_toggle_delta.argtypes = [P(Image), vp, i, P(RewardOpts), vp, vp]
+        L.ht_toggle_delta.argtypes = [P(Image), vp, vp, i, P(RewardOpts), vp, vp]
         L.ht_anisotropy_loss.argtypes = [vp, i, i, i, i, i, vp, vp, vp]
         L.ht_plan_create.argtypes = [vp, P(Image), i, i, u64, vp, vp, P(vp)]
         L.ht_plan_launch.argtypes = [vp, vp]

@@ -49,13 +49,14 @@ class Policy:
     """ht_policy: owns packed weights and the forward workspace."""
 
     def __init__(self, channels: Sequence[int], weights: Sequence[np.ndarray], biases: Sequence[np.ndarray],
-                 head: int = N.HT_HEAD_SIGMOID, precision: int = N.HT_FP32):
+                 head: int = N.HT_HEAD_SIGMOID, precision: int = N.HT_FP32, levels: int = 4):
         L = N.load()
         d = N.PolicyDesc()
         d.n_layers = len(channels) - 1
         for i, c in enumerate(channels):
             d.channels[i] = int(c)
         d.head, d.precision = head, precision
+        d.levels = levels if head == N.HT_HEAD_MULTITONE else 0
         w = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).ravel() for x in weights]))
         b = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).ravel() for x in biases]))
         h = C.c_void_p()
@@ -63,6 +64,7 @@ class Policy:
         self._h = h
         self.channels = tuple(int(c) for c in channels)
         self.head, self.precision = head, precision
+        self.levels = levels if head == N.HT_HEAD_MULTITONE else (4 if head == N.HT_HEAD_SOFTMAX else 2)
         self.K = self.channels[-1]
 
     def close(self):
@@ -170,11 +172,13 @@ def reward(contones: Sequence[torch.Tensor], bits: Sequence[torch.Tensor], opts:
 
 
 def toggle_delta(contones: Sequence[torch.Tensor], bits: Sequence[torch.Tensor],
-                 opts: Optional[N.RewardOpts] = None, stream=None) -> List[torch.Tensor]:
+                 opts: Optional[N.RewardOpts] = None, stream=None,
+                 v: Optional[Sequence[torch.Tensor]] = None) -> List[torch.Tensor]:
+    """dR per pixel; multi-level halftones (opts.levels > 2) need the policy outputs v."""
     o = opts or reward_opts()
     dR = [torch.empty_like(c) for c in contones]
-    check(N.load().ht_toggle_delta(_images(contones), _ptrs(bits), len(contones), C.byref(o), _ptrs(dR),
-                                   _stream(stream)))
+    check(N.load().ht_toggle_delta(_images(contones), _ptrs(bits), _ptrs(v) if v is not None else None,
+                                   len(contones), C.byref(o), _ptrs(dR), _stream(stream)))
     return dR
 
 

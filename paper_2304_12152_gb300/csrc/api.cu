@@ -140,7 +140,7 @@ const char *ht_version(void) { return "ht 0.1 (sm_103a)"; }
 int ht_bits_row_words(int w, int head)
 {
     if (w <= 0) return 0;
-    return head == HT_HEAD_SOFTMAX ? (w + 15) / 16 : (w + 31) / 32;
+    return head == HT_HEAD_SIGMOID ? (w + 31) / 32 : (w + 15) / 16;
 }
 
 void ht_reward_opts_default(ht_reward_opts *o)
@@ -153,6 +153,7 @@ void ht_reward_opts_default(ht_reward_opts *o)
     o->c1 = 0.01f * 0.01f;
     o->c2 = 0.03f * 0.03f;
     o->radius = 5;
+    o->levels = 2;
 }
 
 static ht_status validate_desc(const ht_policy_desc *d)
@@ -165,6 +166,9 @@ static ht_status validate_desc(const ht_policy_desc *d)
                      d->channels[l]);
     if (d->head == HT_HEAD_SIGMOID) {
         HT_CHECK_ARG(d->channels[d->n_layers] == 1, "sigmoid head needs 1 output channel");
+    } else if (d->head == HT_HEAD_MULTITONE) {
+        HT_CHECK_ARG(d->channels[d->n_layers] == 1, "multitone head needs 1 output channel");
+        HT_CHECK_ARG(d->levels >= 2 && d->levels <= 4, "multitone levels must be in [2, 4]");
     } else if (d->head == HT_HEAD_SOFTMAX) {
         HT_CHECK_ARG(d->channels[d->n_layers] == 4, "softmax head needs 4 output channels");
     } else {
@@ -199,6 +203,7 @@ ht_status ht_create_policy(const ht_policy_desc *desc, const float *weights_host
     p->L = desc->n_layers;
     memcpy(p->ch, desc->channels, sizeof(p->ch));
     p->head = desc->head;
+    p->levels = desc->head == HT_HEAD_MULTITONE ? desc->levels : desc->head == HT_HEAD_SOFTMAX ? 4 : 2;
     p->K = desc->channels[desc->n_layers];
     p->prec = desc->precision;
     cudaGetDevice(&p->device);
@@ -469,6 +474,7 @@ static ht_status validate_opts(const ht_reward_opts *o)
 {
     HT_CHECK_ARG(o != nullptr, "null reward options");
     HT_CHECK_ARG(o->radius >= 1 && o->radius <= 7, "radius must be in [1, 7]");
+    HT_CHECK_ARG(o->levels >= 2 && o->levels <= 4, "levels must be in [2, 4]");
     HT_CHECK_ARG(o->sigma_hvs > 0 && o->sigma_ssim > 0, "window sigmas must be positive");
     return HT_OK;
 }
@@ -485,20 +491,22 @@ ht_status ht_reward(const ht_image *c, const uint32_t *const *bits, int n, const
     return ht_reward_launch(c, bits, n, *opts, out, (cudaStream_t)stream);
 }
 
-ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts *opts,
-                          float *const *dR, void *stream)
+ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, const float *const *v, int n,
+                          const ht_reward_opts *opts, float *const *dR, void *stream)
 {
     ht_status st = validate_opts(opts);
     if (st != HT_OK) return st;
     st = validate_images(c, n, 2 * opts->radius + 1);
     if (st != HT_OK) return st;
     HT_CHECK_ARG(bits && dR, "null argument");
-    for (int i = 0; i < n; ++i) HT_CHECK_ARG(bits[i] && dR[i], "image %d: null pointer", i);
+    HT_CHECK_ARG(opts->levels == 2 || v, "multi-level toggle deltas need the policy outputs v");
+    for (int i = 0; i < n; ++i)
+        HT_CHECK_ARG(bits[i] && dR[i] && (opts->levels == 2 || v[i]), "image %d: null pointer", i);
     const size_t need = ht_toggle_scratch_floats_batch(c, n, opts->radius);
     cudaStream_t s = (cudaStream_t)stream;
     float *scratch = nullptr;
     HT_CUDA_TRY(cudaMallocAsync((void **)&scratch, need * sizeof(float), s));
-    st = ht_toggle_launch(c, bits, n, *opts, dR, scratch, need, s);
+    st = ht_toggle_launch(c, bits, v, n, *opts, dR, scratch, need, s);
     cudaFreeAsync(scratch, s);
     return st;
 }

@@ -23,6 +23,7 @@ constexpr int CO_T = 32;            // output channels per block
 struct HeadArgs {
     int head;          // -1: hidden layer (ReLU, store), else HT_HEAD_*
     int K;
+    int levels;        // multitone head: ink levels
     int mode;
     uint64_t seed;
     uint32_t image;
@@ -112,7 +113,7 @@ k_conv3x3_fp32(const float *__restrict__ in, const float *__restrict__ contone, 
     float z[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) z[k] = (k < ha.K) ? acc[k] + b[k] : 0.f;
-    ht_head_emit(z, ha.K, ha.head, ha.mode, ha.seed, ha.image, x0, y, H, W, ha.bits, ha.words, ha.prob);
+    ht_head_emit(z, ha.K, ha.head, ha.mode, ha.seed, ha.image, x0, y, H, W, ha.bits, ha.words, ha.prob, ha.levels);
 }
 
 }  // namespace
@@ -137,6 +138,7 @@ ht_status ht_run_fp32(ht_policy *p, const ht_image &img, uint32_t image_index, i
         HeadArgs ha;
         ha.head = last ? p->head : -1;
         ha.K = p->K;
+        ha.levels = p->levels;
         ha.mode = mode;
         ha.seed = seed;
         ha.image = image_index;
@@ -171,6 +173,7 @@ ht_status ht_fwd_fp32_save(ht_policy *p, const ht_image &img, uint32_t image_ind
         HeadArgs ha;
         ha.head = last ? p->head : -1;
         ha.K = p->K;
+        ha.levels = p->levels;
         ha.mode = HT_MODE_THRESHOLD;
         ha.seed = seed;
         ha.image = image_index;
@@ -198,6 +201,7 @@ ht_status ht_dgrad_fp32(const float *g_out, const float *wt, int Cout, int Cin, 
     HeadArgs ha;
     memset(&ha, 0, sizeof(ha));
     ha.head = -1;
+    ha.levels = 2;
     const dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, (Cin + CO_T - 1) / CO_T);
     ht_prof_start(HTK_TRAIN, s);
     k_conv3x3_fp32<<<grid, dim3(TX, TY), 0, s>>>(g_out, nullptr, 0, wt, nullptr, Cout, Cin, H, W, g_in, ha, act_in);

@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__
 // z(y,x) = b + sum_{dy,dx} d_{dy,dx}(y+dy-1, x+dx-1) (zero outside the image).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__restrict__ imgs, int n_imgs, int buf,
-                                                              float bias, int mode, uint64_t seed)
+                                                              float bias, int mode, uint64_t seed, int head, int levels)
 {
     const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].hd_begin); });
     const ImgDesc *D = imgs + im;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__r
             if (yy >= 0 && yy < H && xx >= 0 && xx < W) z += __ldg(part + t * plane + (size_t)yy * W + xx);
         }
     }
-    ht_head_emit(&z, 1, HT_HEAD_SIGMOID, mode, seed, D->image, x0, y, H, W, D->bits, words, D->prob);
+    ht_head_emit(&z, 1, head, mode, seed, D->image, x0, y, H, W, D->bits, words, D->prob, levels);
 }
 
 // ---------------------------------------------------------------------------
@@ -793,7 +793,8 @@ ht_status ht_tc_head_partials(const void *table, int n_imgs, int n_tiles, int bu
                               uint64_t seed, cudaStream_t s)
 {
     ht_prof_start(HTK_HEAD_TC, s);
-    k_head_partials<<<n_tiles, dim3(HT_X, HT_Y), 0, s>>>((const ImgDesc *)table, n_imgs, buf, bias, mode, seed);
+    k_head_partials<<<n_tiles, dim3(HT_X, HT_Y), 0, s>>>((const ImgDesc *)table, n_imgs, buf, bias, mode, seed,
+                                                         HT_HEAD_SIGMOID, 2);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -905,7 +906,8 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
         }
         if (p->K == 1) {
             ht_prof_start(HTK_HEAD_TC, s);
-            k_head_partials<<<G.hd, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, cur, p->head_bias, mode, seed);
+            k_head_partials<<<G.hd, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, cur, p->head_bias, mode, seed, p->head,
+                                                              p->levels);
             ht_prof_stop(s);
             HT_LAUNCH_CHECK();
         } else {

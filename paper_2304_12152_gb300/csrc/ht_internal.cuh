@@ -89,6 +89,7 @@ struct ht_policy {
     int L;                          // conv layers
     int ch[HT_MAX_LAYERS + 1];
     int head, K, prec;
+    int levels;                     // output levels (2 binary, 4 softmax head, 2..4 multitone head)
     int device;
     int64_t n_w, n_b;
     int64_t w_off[HT_MAX_LAYERS + 1], b_off[HT_MAX_LAYERS + 1];
@@ -175,8 +176,9 @@ ht_status ht_tc_head_partials(const void *table, int n_imgs, int n_tiles, int bu
 // reward / toggle deltas
 ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
                            double *out, cudaStream_t s);
-ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
-                           float *const *dR, float *scratch, size_t scratch_floats, cudaStream_t s);
+ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, const float *const *v, int n,
+                           const ht_reward_opts &o, float *const *dR, float *scratch, size_t scratch_floats,
+                           cudaStream_t s);
 size_t ht_toggle_scratch_floats(int h, int w, int r);
 size_t ht_toggle_scratch_floats_batch(const ht_image *c, int n, int r);   // what ht_toggle_launch needs for c[0..n)
 

@@ -45,11 +45,13 @@ struct Win {
 constexpr int RW_MAXB = 32;
 struct RwImg {
     const float *c;
-    const uint32_t *bits;
-    float *maps;              // toggle deltas: NMAP moment maps of this image
+    const uint32_t *bits;     // 1 bit/px (binary) or a 2-bit level index/px (multitone)
+    float *maps;              // toggle deltas: NMAP(_LV) moment maps of this image
     float *dR;                // toggle deltas: output
     double *acc;              // reward: 3 FP64 accumulators
+    const float *v;           // multitone toggle deltas: the policy output v, [H][W]
     int cpitch, H, W, words;
+    int levels;               // 2 binary, else ink levels of the multitone prototype
 };
 struct RwBatch {
     RwImg im[RW_MAXB];
@@ -59,19 +61,34 @@ __device__ __forceinline__ float hbit(const uint32_t *bits, int words, int y, in
 {
     return (float)((bits[(size_t)y * words + (x >> 5)] >> (x & 31)) & 1u);
 }
+__device__ __forceinline__ int hlevel(const uint32_t *bits, int words, int y, int x)
+{
+    return (int)((bits[(size_t)y * words + (x >> 4)] >> (2 * (x & 15))) & 3u);
+}
+// halftone value of pixel (y, x): the bit (binary) or level index / (L - 1) (multitone)
+template <bool LV>
+__device__ __forceinline__ float hval(const RwImg &I, int y, int x)
+{
+    if constexpr (LV) return (float)hlevel(I.bits, I.words, y, x) / (float)(I.levels - 1);
+    else return hbit(I.bits, I.words, y, x);
+}
 
-// Computes the five window sums for a 32x32 tile of valid outputs.  Returns,
-// for the calling thread's outputs (rows ty, ty+8, ty+16, ty+24; column tx),
-// the per-output quantities through the callback-free arrays.
+// Computes the window sums for a 32x32 tile of valid outputs.  Returns, for the
+// calling thread's outputs (rows ty, ty+8, ty+16, ty+24; column tx), the
+// per-output quantities through the callback-free arrays.  Multi-level
+// halftones (LV) add the sixth sum W(h^2) (h^2 != h); its row pass runs after
+// the first five, into the contone tile's space (dead by then).
 struct Moments {
-    float e, muh, muc, varc, cov;
+    float e, muh, muc, varc, cov, eh2;
 };
 
-__device__ void tile_moments(const float *__restrict__ c, int cpitch, const uint32_t *__restrict__ bits, int words,
-                             int H, int W, const Win &wn, int vy0, int vx0, float (*s_h)[RT + 2 * MAXR],
+template <bool LV>
+__device__ void tile_moments(const RwImg &I, const Win &wn, int vy0, int vx0, float (*s_h)[RT + 2 * MAXR],
                              float (*s_c)[RT + 2 * MAXR], float (*s_row)[RT + 2 * MAXR][RT], Moments out[4],
                              bool valid[4])
 {
+    const float *__restrict__ c = I.c;
+    const int cpitch = I.cpitch, H = I.H, W = I.W;
     const int r = wn.r, span = RT + 2 * r;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const float cref = c[(size_t)min(vy0 + r, H - 1) * cpitch + min(vx0 + r, W - 1)];
@@ -85,7 +102,7 @@ __device__ void tile_moments(const float *__restrict__ c, int cpitch, const uint
         hvs[k] = 0.f;
         cvs[k] = 0.f;
         if (i < span * span && gy < H && gx < W) {
-            hvs[k] = hbit(bits, words, gy, gx);
+            hvs[k] = hval<LV>(I, gy, gx);
             cvs[k] = __ldg(c + (size_t)gy * cpitch + gx) - cref;
         }
     }
@@ -116,6 +133,18 @@ __device__ void tile_moments(const float *__restrict__ c, int cpitch, const uint
         s_row[4][yy][tx] = a4;
     }
     __syncthreads();
+    float(*s_h2)[RT] = reinterpret_cast<float(*)[RT]>(&s_c[0][0]);
+    if constexpr (LV) {
+        for (int yy = ty; yy < span; yy += 8) {
+            float a5 = 0.f;
+            for (int k = 0; k <= 2 * r; ++k) {
+                const float hv = s_h[yy][tx + k];
+                a5 = fmaf(wn.w[k], hv * hv, a5);
+            }
+            s_h2[yy][tx] = a5;
+        }
+        __syncthreads();
+    }
     const int VH = H - 2 * r, VW = W - 2 * r;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -134,6 +163,12 @@ __device__ void tile_moments(const float *__restrict__ c, int cpitch, const uint
         m.muc = a2 + cref;
         m.varc = fmaxf(a3 - a2 * a2, 0.f);
         m.cov = a4 - a1 * a2;
+        m.eh2 = a1;                                      // binary: h^2 = h
+        if constexpr (LV) {
+            float a5 = 0.f;
+            for (int k = 0; k <= 2 * r; ++k) a5 = fmaf(wn.w[k], s_h2[oy + k][tx], a5);
+            m.eh2 = a5;
+        }
         out[t] = m;
         valid[t] = (vy0 + oy < VH) && (vx0 + tx < VW);
     }
@@ -151,6 +186,7 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+template <bool LV>
 __global__ void __launch_bounds__(256) k_reward_tiles(const __grid_constant__ RwBatch B, const Win wn)
 {
     __shared__ float s_h[RT + 2 * MAXR][RT + 2 * MAXR];
@@ -162,13 +198,12 @@ __global__ void __launch_bounds__(256) k_reward_tiles(const __grid_constant__ Rw
     double *acc = I.acc;
     Moments m[4];
     bool valid[4];
-    tile_moments(I.c, I.cpitch, I.bits, I.words, I.H, I.W, wn, blockIdx.y * RT, blockIdx.x * RT, s_h, s_c, s_row, m,
-                 valid);
+    tile_moments<LV>(I, wn, blockIdx.y * RT, blockIdx.x * RT, s_h, s_c, s_row, m, valid);
     double se = 0.0, ss = 0.0, sc = 0.0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         if (!valid[t]) continue;
-        const float varh = m[t].muh - m[t].muh * m[t].muh;
+        const float varh = fmaxf(m[t].eh2 - m[t].muh * m[t].muh, 0.f);
         const float s = ssim_of(m[t].muh, m[t].muc, varh, m[t].varc, m[t].cov, wn.c1, wn.c2);
         const float sig = wn.k * sqrtf(m[t].varc);
         se += (double)m[t].e * (double)m[t].e;
@@ -205,9 +240,11 @@ __global__ void k_reward_finalize(const double *__restrict__ acc, int n, const d
 }
 
 // Per-output maps for the toggle deltas, valid coords [VH][VW]:
-// 0 e, 1 mu_h, 2 mu_c, 3 var_c + C2, 4 cov, 5 sigma, 6 SSIM.
-constexpr int NMAP = 7;
+// 0 e, 1 mu_h, 2 mu_c, 3 var_c + C2, 4 cov, 5 sigma, 6 SSIM (+ 7 E[h^2] for
+// multi-level halftones).
+constexpr int NMAP = 7, NMAP_LV = 8;
 
+template <bool LV>
 __global__ void __launch_bounds__(256) k_moment_maps(const __grid_constant__ RwBatch B, const Win wn)
 {
     __shared__ float s_h[RT + 2 * MAXR][RT + 2 * MAXR];
@@ -220,13 +257,14 @@ __global__ void __launch_bounds__(256) k_moment_maps(const __grid_constant__ RwB
     float *maps = I.maps;
     Moments m[4];
     bool valid[4];
-    tile_moments(I.c, I.cpitch, I.bits, I.words, I.H, I.W, wn, vy0, vx0, s_h, s_c, s_row, m, valid);
+    tile_moments<LV>(I, wn, vy0, vx0, s_h, s_c, s_row, m, valid);
     const size_t plane = (size_t)VH * VW;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         if (!valid[t]) continue;
         const size_t k = (size_t)(vy0 + threadIdx.y + 8 * t) * VW + vx0 + threadIdx.x;
-        const float varh = m[t].muh - m[t].muh * m[t].muh;
+        const float varh = fmaxf(m[t].eh2 - m[t].muh * m[t].muh, 0.f);
+        if constexpr (LV) maps[7 * plane + k] = m[t].eh2;
         maps[0 * plane + k] = m[t].e;
         maps[1 * plane + k] = m[t].muh;
         maps[2 * plane + k] = m[t].muc;
@@ -239,10 +277,18 @@ __global__ void __launch_bounds__(256) k_moment_maps(const __grid_constant__ RwB
 
 constexpr int DTX = 32, DTY = 8;
 
+// Multi-level halftones (LV, the multitoning prototype of Sec. VI-E): the two
+// actions of pixel a are the levels lo = floor(v_a (L - 1)) (at most L - 2) and
+// lo + 1 around the policy output v_a; dR_a = R(h_a = hi) - R(h_a = lo), as the
+// difference of the moment-shift updates for t = (hi - cur) / (L - 1) and
+// t = (lo - cur) / (L - 1) (one of them is 0 when the current level is one of
+// the pair):  e' = e + t g, mu_h' = mu_h + t w, E[h^2]' = E[h^2] + ((h_a + t)^2 -
+// h_a^2) w, cov' = cov + t w (c_a - mu_c).
+template <bool LV>
 __global__ void __launch_bounds__(DTX *DTY, 3) k_toggle_delta(const __grid_constant__ RwBatch B, const Win wn)
 {
-    constexpr int SH = DTY + 2 * MAXR, SW = DTX + 2 * MAXR;
-    __shared__ float s_m[NMAP][SH][SW];
+    constexpr int SH = DTY + 2 * MAXR, SW = DTX + 2 * MAXR, NM = LV ? NMAP_LV : NMAP;
+    __shared__ float s_m[NM][SH][SW];
     const RwImg &I = B.im[blockIdx.z];
     const float *__restrict__ c = I.c;
     const uint32_t *__restrict__ bits = I.bits;
@@ -256,7 +302,7 @@ __global__ void __launch_bounds__(DTX *DTY, 3) k_toggle_delta(const __grid_const
     if (ay0 >= H || ax0 >= W) return;
     const int tid = threadIdx.y * DTX + threadIdx.x;
     // stage maps for output positions j in [a0 - r, a0 + tile + r) (image coords)
-    constexpr int NT = NMAP * SH * SW, NPER = (NT + DTX * DTY - 1) / (DTX * DTY), NB = (NPER + 1) / 2;
+    constexpr int NT = NM * SH * SW, NPER = (NT + DTX * DTY - 1) / (DTX * DTY), NB = (NPER + 1) / 2;
 #pragma unroll
     for (int k0 = 0; k0 < NPER; k0 += NB) {   // two batches: loads first, then the shared stores
         float vals[NB];
@@ -279,8 +325,45 @@ __global__ void __launch_bounds__(DTX *DTY, 3) k_toggle_delta(const __grid_const
     __syncthreads();
     const int ay = ay0 + threadIdx.y, ax = ax0 + threadIdx.x;
     if (ay >= H || ax >= W) return;
-    const float ha = hbit(bits, words, ay, ax);
     const float ca = c[(size_t)ay * cpitch + ax];
+    if constexpr (LV) {
+        const float inv = 1.f / (float)(I.levels - 1);
+        const int cur = hlevel(bits, words, ay, ax);
+        const int lo = min((int)floorf(I.v[(size_t)ay * W + ax] * (float)(I.levels - 1)), I.levels - 2);
+        const float hv = (float)cur * inv;
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {                      // q = 0: hi (+), q = 1: lo (-)
+            const int lev = lo + (q == 0 ? 1 : 0);
+            if (lev == cur) continue;
+            const float t = (float)(lev - cur) * inv, sgn = q == 0 ? 1.f : -1.f;
+            const float dh2 = (hv + t) * (hv + t) - hv * hv;
+            for (int dy = -r; dy <= r; ++dy) {
+                const int jy = ay + dy;
+                if (jy < r || jy >= H - r) continue;
+                const float gy = wn.g[dy + r], wy = wn.w[dy + r];
+                for (int dx = -r; dx <= r; ++dx) {
+                    const int jx = ax + dx;
+                    if (jx < r || jx >= W - r) continue;
+                    const int sy = threadIdx.y + r + dy, sx = threadIdx.x + r + dx;
+                    const float g = gy * wn.g[dx + r];
+                    const float w = wy * wn.w[dx + r];
+                    const float e = s_m[0][sy][sx], muh = s_m[1][sy][sx], muc = s_m[2][sy][sx];
+                    const float varc2 = s_m[3][sy][sx], cov = s_m[4][sy][sx], sig = s_m[5][sy][sx];
+                    const float ss = s_m[6][sy][sx], eh2 = s_m[7][sy][sx];
+                    const float muh2 = muh + t * w;
+                    const float varh2 = fmaxf(eh2 + dh2 * w - muh2 * muh2, 0.f);
+                    const float cov2 = cov + t * w * (ca - muc);
+                    const float s2 = __fdividef((2.f * muh2 * muc + wn.c1) * (2.f * cov2 + wn.c2),
+                                                (muh2 * muh2 + muc * muc + wn.c1) * (varh2 + varc2));
+                    acc += sgn * (-(2.f * t * g * e + t * t * g * g) + wn.ws * sig * (s2 - ss));
+                }
+            }
+        }
+        dR[(size_t)ay * W + ax] = acc / ((float)VH * (float)VW);
+        return;
+    }
+    const float ha = hbit(bits, words, ay, ax);
     const float delta = 1.f - 2.f * ha;
     float acc = 0.f;
     for (int dy = -r; dy <= r; ++dy) {
@@ -332,7 +415,7 @@ Win make_win(const ht_reward_opts &o)
 }  // namespace
 
 namespace {
-RwImg rw_img(const ht_image &c, const uint32_t *bits)
+RwImg rw_img(const ht_image &c, const uint32_t *bits, int levels)
 {
     RwImg I{};
     I.c = c.contone;
@@ -340,24 +423,26 @@ RwImg rw_img(const ht_image &c, const uint32_t *bits)
     I.cpitch = c.pitch;
     I.H = c.h;
     I.W = c.w;
-    I.words = ht_bits_row_words(c.w, 0);
+    I.levels = levels;
+    I.words = ht_bits_row_words(c.w, levels > 2 ? HT_HEAD_MULTITONE : HT_HEAD_SIGMOID);
     return I;
 }
 
 // reward window sums of images [base, base + cnt) into acc[3 i] (launch only)
 ht_status launch_reward_tiles(const ht_image *c, const uint32_t *const *bits, int base, int cnt, const Win &wn,
-                              double *acc, cudaStream_t s)
+                              int levels, double *acc, cudaStream_t s)
 {
     RwBatch B{};
     int gx = 1, gy = 1;
     for (int k = 0; k < cnt; ++k) {
         const int i = base + k;
-        B.im[k] = rw_img(c[i], bits[i]);
+        B.im[k] = rw_img(c[i], bits[i], levels);
         B.im[k].acc = acc + 3 * (size_t)k;
         gx = max(gx, (c[i].w - 2 * wn.r + RT - 1) / RT);
         gy = max(gy, (c[i].h - 2 * wn.r + RT - 1) / RT);
     }
-    k_reward_tiles<<<dim3(gx, gy, cnt), dim3(32, 8), 0, s>>>(B, wn);
+    if (levels > 2) k_reward_tiles<true><<<dim3(gx, gy, cnt), dim3(32, 8), 0, s>>>(B, wn);
+    else k_reward_tiles<false><<<dim3(gx, gy, cnt), dim3(32, 8), 0, s>>>(B, wn);
     HT_LAUNCH_CHECK();
     return HT_OK;
 }
@@ -378,7 +463,8 @@ ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n
     HT_CUDA_TRY(ce);
     ht_prof_start(HTK_REWARD, s);
     for (int base = 0; base < n; base += RW_MAXB) {
-        const ht_status st = launch_reward_tiles(c, bits, base, min(RW_MAXB, n - base), wn, acc + 3 * (size_t)base, s);
+        const ht_status st =
+            launch_reward_tiles(c, bits, base, min(RW_MAXB, n - base), wn, o.levels, acc + 3 * (size_t)base, s);
         if (st != HT_OK) return st;
     }
     ht_prof_stop(s);
@@ -388,10 +474,13 @@ ht_status ht_reward_launch(const ht_image *c, const uint32_t *const *bits, int n
     return HT_OK;
 }
 
-ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts &o,
-                           float *const *dR, float *scratch, size_t scratch_floats, cudaStream_t s)
+ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, const float *const *v, int n,
+                           const ht_reward_opts &o, float *const *dR, float *scratch, size_t scratch_floats,
+                           cudaStream_t s)
 {
     const Win wn = make_win(o);
+    const bool lv = o.levels > 2;
+    const int nmap = lv ? NMAP_LV : NMAP;
     for (int base = 0; base < n; base += RW_MAXB) {
         const int cnt = min(RW_MAXB, n - base);
         RwBatch B{};
@@ -400,10 +489,11 @@ ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, int n
         for (int k = 0; k < cnt; ++k) {
             const int i = base + k;
             const int VH = c[i].h - 2 * o.radius, VW = c[i].w - 2 * o.radius;
-            B.im[k] = rw_img(c[i], bits[i]);
+            B.im[k] = rw_img(c[i], bits[i], o.levels);
             B.im[k].maps = scratch + off;
             B.im[k].dR = dR[i];
-            off += (size_t)NMAP * VH * VW;
+            B.im[k].v = lv ? v[i] : nullptr;
+            off += (size_t)nmap * VH * VW;
             gx = max(gx, (VW + RT - 1) / RT);
             gy = max(gy, (VH + RT - 1) / RT);
             tx = max(tx, (c[i].w + DTX - 1) / DTX);
@@ -414,16 +504,22 @@ ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, int n
             return HT_ERR_INVALID_ARG;
         }
         ht_prof_start(HTK_TOGGLE, s);
-        k_moment_maps<<<dim3(gx, gy, cnt), dim3(32, 8), 0, s>>>(B, wn);
-        HT_LAUNCH_CHECK();
-        k_toggle_delta<<<dim3(tx, ty, cnt), dim3(DTX, DTY), 0, s>>>(B, wn);
+        if (lv) {
+            k_moment_maps<true><<<dim3(gx, gy, cnt), dim3(32, 8), 0, s>>>(B, wn);
+            HT_LAUNCH_CHECK();
+            k_toggle_delta<true><<<dim3(tx, ty, cnt), dim3(DTX, DTY), 0, s>>>(B, wn);
+        } else {
+            k_moment_maps<false><<<dim3(gx, gy, cnt), dim3(32, 8), 0, s>>>(B, wn);
+            HT_LAUNCH_CHECK();
+            k_toggle_delta<false><<<dim3(tx, ty, cnt), dim3(DTX, DTY), 0, s>>>(B, wn);
+        }
         ht_prof_stop(s);
         HT_LAUNCH_CHECK();
     }
     return HT_OK;
 }
 
-size_t ht_toggle_scratch_floats(int h, int w, int r) { return (size_t)NMAP * (h - 2 * r) * (w - 2 * r); }
+size_t ht_toggle_scratch_floats(int h, int w, int r) { return (size_t)NMAP_LV * (h - 2 * r) * (w - 2 * r); }
 
 size_t ht_toggle_scratch_floats_batch(const ht_image *c, int n, int r)
 {
@@ -519,7 +615,8 @@ extern "C" ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const 
     const Win wn = make_win(*opts);
     HT_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)n, s));
     for (int base = 0; base < n; base += RW_MAXB) {
-        const ht_status st = launch_reward_tiles(c, bits, base, min(RW_MAXB, n - base), wn, acc + 3 * (size_t)base, s);
+        const ht_status st = launch_reward_tiles(c, bits, base, min(RW_MAXB, n - base), wn, opts->levels,
+                                                 acc + 3 * (size_t)base, s);
         if (st != HT_OK) return st;
     }
     for (int base = 0; base < n; base += 64) {
@@ -536,9 +633,12 @@ extern "C" ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const 
 void ht_preload_reward()
 {
     cudaFuncAttributes fa;
-    cudaFuncGetAttributes(&fa, k_reward_tiles);
+    cudaFuncGetAttributes(&fa, k_reward_tiles<false>);
+    cudaFuncGetAttributes(&fa, k_reward_tiles<true>);
     cudaFuncGetAttributes(&fa, k_reward_finalize);
-    cudaFuncGetAttributes(&fa, k_moment_maps);
-    cudaFuncGetAttributes(&fa, k_toggle_delta);
+    cudaFuncGetAttributes(&fa, k_moment_maps<false>);
+    cudaFuncGetAttributes(&fa, k_moment_maps<true>);
+    cudaFuncGetAttributes(&fa, k_toggle_delta<false>);
+    cudaFuncGetAttributes(&fa, k_toggle_delta<true>);
     cudaFuncGetAttributes(&fa, k_reward_finalize_noalloc);
 }

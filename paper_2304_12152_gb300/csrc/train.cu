@@ -26,7 +26,7 @@
 
 #include <vector>
 
-#include "ht_internal.cuh"
+#include "head.cuh"
 
 struct ht_train {
     ht_policy *p;
@@ -64,20 +64,26 @@ __global__ void k_fill(float *p, size_t n, float v)
 }
 
 // h^s = [u^s < p], u^s from Philox stream 1 + s; packed LSB-first, 32 px per warp.
+// Multitone prototype (levels > 2, Sec. VI-E): level k + [u^s < frac] with k, frac
+// from v (L - 1), 2 bits per pixel.
 // blockIdx.z = i S + s over all crops i (probability maps px apart) and samples s.
 __global__ void k_sample_bits(const float *__restrict__ prob0, size_t px, int H, int W, int words, uint64_t seed, int S,
-                              uint32_t *__restrict__ bits0)
+                              int levels, uint32_t *__restrict__ bits0)
 {
     const int z = blockIdx.z, i = z / S, sm = z % S;
     const float *prob = prob0 + (size_t)i * px;
     uint32_t *bits = bits0 + (size_t)z * H * words;
     const int y = blockIdx.y, x0 = blockIdx.x * 32, x = x0 + threadIdx.x;
-    bool h = false;
-    if (x < W) {
-        const float u = ht_uniform24(seed, (uint32_t)i, 1u + (uint32_t)sm, (uint64_t)y * W + x);
-        h = u < prob[(size_t)y * W + x];
+    const bool inside = x < W;
+    const float u = inside ? ht_uniform24(seed, (uint32_t)i, 1u + (uint32_t)sm, (uint64_t)y * W + x) : 0.f;
+    const float v = inside ? prob[(size_t)y * W + x] : 0.f;
+    if (levels > 2) {
+        const float t = v * (float)(levels - 1);
+        const int k = min((int)floorf(t), levels - 2);
+        ht_pack2(k + (u < t - (float)k ? 1 : 0), inside, (int)threadIdx.x, x0, y, H, bits, words);
+        return;
     }
-    const uint32_t word = __ballot_sync(0xffffffffu, h);
+    const uint32_t word = __ballot_sync(0xffffffffu, inside && u < v);
     if (threadIdx.x == 0) bits[(size_t)y * words + (x0 >> 5)] = word;
 }
 
@@ -88,10 +94,13 @@ __global__ void k_sample_bits(const float *__restrict__ prob0, size_t px, int H,
 //        = -inv * sum_s dR^s_a * ((1 - p) / p if h_a = 1, p / (1 - p) if 0)
 //   L += -inv * sum_s sum_a log pi_a(h_a) (R - b_a)
 // (h_a = 1 needs u < p, so p > 0; h_a = 0 needs p <= u < 1: no division by zero.)
+// Multitone prototype (levels L > 2, Sec. VI-E): actions lo = k, hi = k + 1 around v,
+// pi(hi) = frac, dR = R(hi) - R(lo), so dL/dv_a = -(L - 1) sum_s dR^s_a and
+//   L += -inv * sum_s sum_a (frac R(hi) + (1 - frac) R(lo)).
 // blockIdx.y = crop i (maps npx apart; S samples per crop).
 __global__ void k_marl(const float *__restrict__ prob0, const float *__restrict__ dR0, const uint32_t *__restrict__ bits0,
                        const double *__restrict__ rewards0, int S, int H, int W, int words, double inv, int coma,
-                       float *__restrict__ dprob0, double *__restrict__ loss)
+                       int levels, float *__restrict__ dprob0, double *__restrict__ loss)
 {
     const size_t npx = (size_t)H * W;
     const int i = blockIdx.y;
@@ -106,8 +115,20 @@ __global__ void k_marl(const float *__restrict__ prob0, const float *__restrict_
         const int y = (int)(a / W), x = (int)(a % W);
         const float p = prob[a];
         double g = 0.0;
+        const float t = p * (float)(levels - 1);
+        const int k = min((int)floorf(t), levels - 2);
+        const float frac = t - (float)k;
         for (int s = 0; s < S; ++s) {
             const float d = dR[(size_t)s * npx + a];
+            if (levels > 2) {
+                const uint32_t wd = bits[(size_t)s * H * words + (size_t)y * words + (x >> 4)];
+                const bool at_hi = (int)((wd >> (2 * (x & 15))) & 3u) == k + 1;
+                const double R = rewards[4 * s + 3];
+                const double r_hi = R + (at_hi ? 0.0 : (double)d), r_lo = R - (at_hi ? (double)d : 0.0);
+                g += d * (float)(levels - 1);
+                l += -((double)frac * r_hi + (1.0 - (double)frac) * r_lo);
+                continue;
+            }
             const bool hb = (bits[(size_t)s * H * words + (size_t)y * words + (x >> 5)] >> (x & 31)) & 1u;
             if (coma) {
                 g += hb ? d * ((1.f - p) / p) : d * (p / (1.f - p));
@@ -238,7 +259,10 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
 {
     HT_CHECK_ARG(p && d && out, "null argument");
     *out = nullptr;
-    HT_CHECK_ARG(p->head == HT_HEAD_SIGMOID, "training needs the sigmoid head");
+    HT_CHECK_ARG(p->head == HT_HEAD_SIGMOID || p->head == HT_HEAD_MULTITONE,
+                 "training needs a sigmoid-output head (binary or the multitoning prototype)");
+    HT_CHECK_ARG(p->head == HT_HEAD_SIGMOID || d->estimator == HT_EST_LE,
+                 "the multitoning prototype trains with the local-expectation estimator");
     if (p->prec == HT_FP8_E4M3 || (p->prec == HT_BF16 && !ht_train_tc_supported(p))) {
         ht_set_error("training supports the FP32 form and the BF16 form of 2 -> 64 x (L-1) -> 1 policies");
         return HT_ERR_UNSUPPORTED;
@@ -258,6 +282,7 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
     ht_train *t = new ht_train();
     t->p = p;
     t->d = *d;
+    t->d.reward.levels = p->levels;            // rewards and toggles of the policy's own halftones
     if (d->las_mode == 0) {
         t->d.n_rad = 1;
         t->d.n_ang = 1;
@@ -267,7 +292,7 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
     t->crop_px = (size_t)d->crop_h * d->crop_w;
     t->gray_px = (size_t)d->gray_n * d->gray_n;
     const int B = d->max_crops, G = d->n_gray, S = d->n_samples;
-    const int words = ht_bits_row_words(d->crop_w, HT_HEAD_SIGMOID);
+    const int words = ht_bits_row_words(d->crop_w, p->head);
     const size_t all_px = t->crop_px * B + t->gray_px * G;
     int cmax = 1;
     for (int l = 1; l < p->L; ++l) cmax = p->ch[l] > cmax ? p->ch[l] : cmax;
@@ -283,7 +308,7 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
     }
     t->las_scratch_bytes = G > 0 ? ht_las_scratch_bytes(G, d->gray_n, t->d.n_rad, t->d.n_ang) : 0;
     const int gmax = (int)(d->crop_h > d->gray_n ? d->crop_h : d->gray_n);
-    const int words_max = ht_bits_row_words(d->crop_w > d->gray_n ? d->crop_w : d->gray_n, HT_HEAD_SIGMOID);
+    const int words_max = ht_bits_row_words(d->crop_w > d->gray_n ? d->crop_w : d->gray_n, p->head);
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes < 16 ? 16 : bytes);
@@ -312,7 +337,7 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
             w.slot_off.push_back(arena);
             arena += ht_train_tc_image_bytes(p, k < B ? t->crop_px : t->gray_px);
         }
-        const int wg = ht_bits_row_words(d->gray_n, HT_HEAD_SIGMOID);
+        const int wg = ht_bits_row_words(d->gray_n, p->head);
         int tiles = B * ((d->crop_w + 31) / 32) * ((d->crop_h + 7) / 8) + G * ((d->gray_n + 31) / 32) * ((d->gray_n + 7) / 8);
         size_t total = 0;
         ht_train_tc_scratch_layout(p, tiles, &w.wt_off, &total);
@@ -374,7 +399,7 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
     }
     ht_policy *p = t->p;
     cudaStream_t s = (cudaStream_t)stream;
-    const int H = t->d.crop_h, W = t->d.crop_w, words = ht_bits_row_words(W, HT_HEAD_SIGMOID);
+    const int H = t->d.crop_h, W = t->d.crop_w, words = ht_bits_row_words(W, p->head);
     const int B = t->d.max_crops;
     HT_CUDA_TRY(cudaMemsetAsync(t->dacc, 0, sizeof(double) * (1 + G), s));
     // 1. forward, keeping activations
@@ -384,7 +409,7 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
         w.img_off.assign(n + G, 0);
         w.prob_off.assign(n + G, 0);
         w.bits_off.assign(n + G, 0);
-        const int words_g = ht_bits_row_words(t->d.gray_n, HT_HEAD_SIGMOID);
+        const int words_g = ht_bits_row_words(t->d.gray_n, p->head);
         for (int i = 0; i < n + G; ++i) {
             const bool gray = i >= n;
             const int slot = gray ? B + (i - n) : i;
@@ -429,25 +454,29 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
     double *rewards = t->dacc + 1 + G;
     if (n > 0) {
         // all crops x samples in one launch per kernel (reward / toggle deltas in batches)
-        k_sample_bits<<<dim3(words, H, n * S), 32, 0, s>>>(t->prob, t->crop_px, H, W, words, seed, S, t->sbits);
+        k_sample_bits<<<dim3((W + 31) / 32, H, n * S), 32, 0, s>>>(t->prob, t->crop_px, H, W, words, seed, S,
+                                                                   p->levels, t->sbits);
         HT_LAUNCH_CHECK();
         std::vector<ht_image> cimg((size_t)n * S);
         std::vector<const uint32_t *> bp((size_t)n * S);
         std::vector<float *> dp((size_t)n * S);
+        std::vector<const float *> vp((size_t)n * S);
         for (int i = 0; i < n; ++i)
             for (int sm = 0; sm < S; ++sm) {
                 const size_t k = (size_t)i * S + sm;
                 cimg[k] = crops[i];
                 bp[k] = t->sbits + k * H * words;
                 dp[k] = t->dR + k * t->crop_px;
+                vp[k] = t->prob + img_px_offset(t, i);
             }
         ht_status st = ht_reward_launch(cimg.data(), bp.data(), n * S, t->d.reward, rewards, s);
         if (st != HT_OK) return st;
-        st = ht_toggle_launch(cimg.data(), bp.data(), n * S, t->d.reward, dp.data(), t->toggle_scratch,
+        st = ht_toggle_launch(cimg.data(), bp.data(), vp.data(), n * S, t->d.reward, dp.data(), t->toggle_scratch,
                               t->toggle_scratch_floats, s);
         if (st != HT_OK) return st;
         k_marl<<<dim3(nblk(t->crop_px), n), 256, 0, s>>>(t->prob, t->dR, t->sbits, rewards, S, H, W, words,
-                                                         1.0 / ((double)n * S), t->d.estimator, t->dprob, t->dacc);
+                                                         1.0 / ((double)n * S), t->d.estimator, p->levels, t->dprob,
+                                                         t->dacc);
         HT_LAUNCH_CHECK();
     }
     // 5. anisotropy loss on the gray patches' probability maps

@@ -606,7 +606,8 @@ unsigned nblk256(size_t n) { return (unsigned)((n + 255) / 256); }
 // ---------------------------------------------------------------------------
 bool ht_train_tc_supported(const ht_policy *p)
 {
-    if (p->prec != HT_BF16 || p->head != HT_HEAD_SIGMOID || p->K != 1 || p->L < 3) return false;
+    if (p->prec != HT_BF16 || (p->head != HT_HEAD_SIGMOID && p->head != HT_HEAD_MULTITONE) || p->K != 1 || p->L < 3)
+        return false;
     if (p->ch[0] != 2) return false;
     for (int l = 1; l < p->L; ++l)
         if (p->ch[l] != 64) return false;

@@ -4,6 +4,7 @@ import pytest
 import torch
 
 import oracle as O
+from paper_2304_12152_gb300 import _native as N
 from paper_2304_12152_gb300 import api, synth
 
 pytestmark = pytest.mark.gpu
@@ -56,6 +57,51 @@ def test_toggle_delta_matches_oracle(shape):
         border = np.concatenate([np.arange(w), (h - 1) * w + np.arange(w), np.arange(h) * w, np.arange(h) * w + w - 1])
         idx = np.unique(np.concatenate([border, rng.integers(0, h * w, 1500)]))
     ref = O.toggle_delta(c, hb, idx)
+    scale = np.abs(ref).max()
+    err = np.abs(g.ravel()[idx] - ref)
+    assert err.max() < 2e-4 * scale, (err.max(), scale)
+
+
+@pytest.mark.parametrize("L", [3, 4])
+def test_multilevel_reward_matches_oracle(L):
+    """Reward of multi-level halftones (multitoning prototype, Sec. VI-E): SSIM needs
+    E[h^2] != E[h]."""
+    imgs = [synth.contone_image(h, w, seed=13, index=i) for i, (h, w) in enumerate(SHAPES)]
+    rng = np.random.default_rng(L)
+    levs = [O.sample_multitone(c.astype(np.float64), L, rng.random(c.shape)) for c in imgs]
+    cs = [torch.from_numpy(c).cuda() for c in imgs]
+    bits = [torch.from_numpy(api.pack_bits(h, N.HT_HEAD_MULTITONE)).cuda() for h in levs]
+    out = api.reward(cs, bits, api.reward_opts(levels=L)).cpu().numpy()
+    for i in range(len(imgs)):
+        r = O.reward(imgs[i], levs[i], levels=L)
+        assert abs(out[i, 0] - r["mse"]) <= 1e-5 * r["mse"] + 1e-9, (SHAPES[i], out[i, 0], r["mse"])
+        assert abs(out[i, 1] - r["ssim"]) < 2e-5
+        assert abs(out[i, 2] - r["cssim"]) < 2e-5
+        assert abs(out[i, 3] - r["R"]) < 2e-6
+
+
+@pytest.mark.parametrize("L,shape", [(3, (24, 24)), (4, (64, 96)), (4, (256, 256))])
+def test_multilevel_toggle_delta_matches_oracle(L, shape):
+    """dR_a = R(lo + 1) - R(lo) for the level pair around v_a, against the oracle."""
+    h, w = shape
+    c = synth.contone_image(h, w, seed=19)
+    rng = np.random.default_rng(7)
+    v = np.clip(c + 0.1 * rng.normal(size=c.shape), 0, 1).astype(np.float32)
+    k, _ = O.multitone_pair(v.astype(np.float64), L)
+    lev = O.sample_multitone(v.astype(np.float64), L, rng.random(c.shape))
+    vt = torch.from_numpy(v).cuda()
+    dR = api.toggle_delta([torch.from_numpy(c).cuda()],
+                          [torch.from_numpy(api.pack_bits(lev, N.HT_HEAD_MULTITONE)).cuda()],
+                          api.reward_opts(levels=L), v=[vt])[0]
+    g = dR.cpu().numpy().astype(np.float64)
+    # the kernel takes the level pair from v in FP32: compare where both sides agree on it
+    k32 = np.minimum(np.floor(v * np.float32(L - 1)), L - 2).astype(np.int64)
+    if h * w <= 4096:
+        idx = np.arange(h * w)
+    else:
+        idx = np.unique(rng.integers(0, h * w, 1500))
+    idx = idx[k32.ravel()[idx] == k.ravel()[idx]]
+    ref = O.toggle_delta(c, lev, idx, levels=L, lo=k.astype(np.uint8))
     scale = np.abs(ref).max()
     err = np.abs(g.ravel()[idx] - ref)
     assert err.max() < 2e-4 * scale, (err.max(), scale)

@@ -103,6 +103,57 @@ def test_coma_train_step_matches_oracle():
         assert ew <= 2e-3 and eb <= 2e-3, errs
 
 
+def oracle_step_multitone(crops, ws, bs, seed, S, L):
+    """Training step of the multitoning prototype (Sec. VI-E) from oracle routines:
+    levels h^s sampled from v with u^s (stream 1 + s), reward and toggle deltas of the
+    multi-level halftones, the LE surrogate with dL/dv = -(L - 1) dR, the backward."""
+    n = len(crops)
+    gw = [np.zeros(w.shape) for w in ws]
+    gb = [np.zeros(b.shape) for b in bs]
+    l_marl, rs = 0.0, []
+    for i, c in enumerate(crops):
+        h, w = c.shape
+        lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=i, save_acts=True)
+        v = p[0]
+        k, _ = O.multitone_pair(v, L)
+        dp = np.zeros((h, w))
+        for s in range(S):
+            u = O.uniform_map(seed, i, 1 + s, h, w)
+            lev = O.sample_multitone(v, L, u)
+            r = O.reward(c, lev, levels=L)
+            dR = O.toggle_delta(c, lev, levels=L, lo=k.astype(np.uint8)).reshape(h, w)
+            val, grad = O.le_surrogate_multitone(v, lev, dR, r["R"], L)
+            l_marl += val / (n * S)
+            dp += grad / (n * S)
+            rs.append(r["R"])
+        a, b = O.backward(c, ws, bs, seed, i, acts, lg, dp)
+        for l in range(len(ws)):
+            gw[l] += a[l]
+            gb[l] += b[l]
+    return l_marl, float(np.mean(rs)), gw, gb
+
+
+def test_multitone_train_step_matches_oracle():
+    """FP32 training step of the multitoning prototype (4 levels) against the oracle:
+    losses 1e-4 relative, gradients 2e-3 of the layer's largest entry."""
+    chs, L = (2, 8, 8, 1), 4
+    ws, _ = synth.he_normal_policy(chs, 81)
+    bs = synth.random_biases(chs, 82, scale=0.1)
+    crops = [synth.contone_image(28, 44, seed=83, index=i) for i in range(2)]
+    S, seed = 2, 17
+    pol = api.Policy(chs, ws, bs, head=N.HT_HEAD_MULTITONE, precision=N.HT_FP32, levels=L)
+    tr = api.Trainer(pol, (28, 44), max_crops=2, n_samples=S, n_gray=0, las_mode=1, n_rad=4, n_ang=4, w_a=0.0)
+    losses = tr.forward([torch.from_numpy(c).cuda() for c in crops], [], seed)
+    gw, gb = tr.backward()
+    torch.cuda.synchronize()
+    l_marl, r_mean, ref_w, ref_b = oracle_step_multitone(crops, ws, bs, seed, S, L)
+    assert abs(losses[1] - l_marl) <= 1e-4 * abs(l_marl), (losses, l_marl)
+    assert abs(losses[3] - r_mean) <= 1e-4 * abs(r_mean), (losses, r_mean)
+    errs = _grad_errors(gw, gb, ref_w, ref_b)
+    for ew, eb in errs:
+        assert ew <= 2e-3 and eb <= 2e-3, errs
+
+
 def test_autograd_function_drives_adam():
     """torch.autograd.Function wrapper: gradients reach torch parameters and an Adam
     step changes the loss deterministically."""
