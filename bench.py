@@ -108,9 +108,9 @@ def dist_info():
     return rank, world, local
 
 
-def cpu_oracle_sample(img, ws, bs, side, seed, image_id=0, quant=1, mode=1, scales=None):
+def cpu_oracle_sample(img, ws, bs, side, seed, image_id=0, quant=1, mode=1, scales=None, levels=0):
     """FP64 oracle (optionally emulating the reduced-precision rounding) forward and
-    actions on a side x side centre crop."""
+    actions on a side x side centre crop (levels > 0: the multitoning prototype's rule)."""
     import oracle as O
     h, w = img.shape
     side = min(side, h, w)
@@ -119,6 +119,8 @@ def cpu_oracle_sample(img, ws, bs, side, seed, image_id=0, quant=1, mode=1, scal
     t0 = time.perf_counter()
     _, p, _ = O.forward(img, ws, bs, noise_seed=seed, image=image_id, quant=quant, act_scale=scales, region=reg)
     lev, u = O.sample(p, h, w, reg, mode, seed, image_id)
+    if levels:
+        lev = O.sample_multitone(p[0], levels, u if mode == 1 else None)
     dt = time.perf_counter() - t0
     return dt, reg, p, lev, u
 
@@ -162,6 +164,8 @@ WORKLOADS = {
     "uneven": ("uneven batch of 64 images, sizes log-uniform 200x300..4096x3072 (seed 4), BF16, Bernoulli seed 4",
                "bf16", 0, "wide", 1, 4),
     "small": ("one 256x256 image (seed 0), 2->32x5->1 policy, plain FP32, threshold 0.5", "fp32", 0, "small", 0, 0),
+    "proto": ("multitoning prototype 4x4096x4096, 2->64x7->1 sigmoid output, action between the 2 of 4 levels "
+              "around it, BF16, Philox seed 2", "bf16", 2, "wide", 1, 2),
 }
 
 
@@ -174,7 +178,7 @@ def build_inputs(args, rank):
     if args.workload == "printer":
         shapes = [(args.size, args.size)] * args.batch
         seed = 1
-    elif args.workload == "multitone":
+    elif args.workload in ("multitone", "proto"):
         shapes = [(4096, 4096)] * 4
         seed = 2
     elif args.workload == "uneven":
@@ -226,7 +230,7 @@ def main():
     chs = {"wide": synth.NET_WIDE, "wide4": synth.NET_WIDE_K4, "small": synth.NET_SMALL}[netname]
     ws, bs = synth.he_normal_policy(chs, 1)
     prec = {"bf16": N.HT_BF16, "fp8": N.HT_FP8_E4M3, "fp32": N.HT_FP32}[precision]
-    pol = api.Policy(chs, ws, bs, head=head, precision=prec)
+    pol = api.Policy(chs, ws, bs, head=head, precision=prec, levels=4)
     dev = torch.device("cuda", local)
     if prec == N.HT_FP8_E4M3:
         calib = torch.from_numpy(synth.contone_image(256, 256, seed=99)).to(dev)
@@ -331,7 +335,7 @@ def main():
     # ---------------- plain FP32 form of the same net ----------------
     fp32 = None
     if prec != N.HT_FP32 and args.fp32_steps > 0:
-        pol32 = api.Policy(chs, ws, bs, head=head, precision=N.HT_FP32)
+        pol32 = api.Policy(chs, ws, bs, head=head, precision=N.HT_FP32, levels=4)
         pol32.halftone_into(cs, bits, mode, seed)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -386,10 +390,12 @@ def main():
         O.build()
         quant = {N.HT_BF16: 1, N.HT_FP8_E4M3: 2, N.HT_FP32: 0}[prec]
         side = 32
-        dt, *_ = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None)
+        lv = 4 if head == N.HT_HEAD_MULTITONE else 0
+        dt, *_ = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None, levels=lv)
         side = int(min(min(imgs_np[0].shape), 1024, max(32, side * math.sqrt(15.0 / max(dt, 1e-3)))))
         side -= side % 8
-        dt, reg, p, lev_or, u = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None)
+        dt, reg, p, lev_or, u = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None,
+                                                  levels=lv)
         cpu = {"value": side * side / dt / 1e6, "unit": "Mpx/s", "cores": O.num_threads(), "kind": "oracle",
                "sample": f"{side}x{side} centre crop of image 0 (+halo), FP64 forward"
                          f"{' emulating the ' + precision.upper() + ' rounding' if quant else ''} + actions",
@@ -397,7 +403,11 @@ def main():
         if quant != 2:   # FP8 scales come from the library's calibration: no bit comparison
             y0, x0, rh, rw = reg
             lev_gpu = api.unpack_bits(bits[0], imgs_np[0].shape[0], imgs_np[0].shape[1], head)[y0:y0 + rh, x0:x0 + rw]
-            if p.shape[0] == 1:
+            if lv:
+                t = p[0] * (lv - 1)
+                _, frac = O.multitone_pair(p[0], lv)
+                decided = (np.abs(frac - (u if mode == 1 else 0.5)) > 1e-4) & (np.abs(t - np.rint(t)) > 1e-4)
+            elif p.shape[0] == 1:
                 decided = np.abs(p[0] - u) > 1e-4
             else:
                 cdf = np.cumsum(p, 0)

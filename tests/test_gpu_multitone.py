@@ -63,7 +63,9 @@ def test_bf16_multitone_head_matches_bf16_oracle():
     dec = _decided(v, L, u)
     mism = int((lev[dec] != ref[dec]).sum())
     assert mism <= max(2, int((L - 1) * 1e-3 * dec.sum())), (mism, int(dec.sum()))
-    assert np.abs(probs[0][0].cpu().numpy() - v).max() < 4e-3
+    dv = np.abs(probs[0][0].cpu().numpy() - v)
+    # the BF16 forward bounds of the binary head (p99.9 2e-3; max as against pure FP64, 6e-3)
+    assert np.quantile(dv, 0.999) < 2e-3 and dv.max() < 6e-3, (np.quantile(dv, 0.999), dv.max())
     # levels are the two around v
     v32 = probs[0][0].cpu().numpy()
     k = np.minimum(np.floor(v32 * np.float32(L - 1)), L - 2).astype(np.int64)   # the kernel's FP32 rule

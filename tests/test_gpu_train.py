@@ -103,7 +103,7 @@ def test_coma_train_step_matches_oracle():
         assert ew <= 2e-3 and eb <= 2e-3, errs
 
 
-def oracle_step_multitone(crops, ws, bs, seed, S, L):
+def oracle_step_multitone(crops, ws, bs, seed, S, L, quant=0):
     """Training step of the multitoning prototype (Sec. VI-E) from oracle routines:
     levels h^s sampled from v with u^s (stream 1 + s), reward and toggle deltas of the
     multi-level halftones, the LE surrogate with dL/dv = -(L - 1) dR, the backward."""
@@ -113,7 +113,7 @@ def oracle_step_multitone(crops, ws, bs, seed, S, L):
     l_marl, rs = 0.0, []
     for i, c in enumerate(crops):
         h, w = c.shape
-        lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=i, save_acts=True)
+        lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=i, quant=quant, save_acts=True)
         v = p[0]
         k, _ = O.multitone_pair(v, L)
         dp = np.zeros((h, w))
@@ -126,7 +126,7 @@ def oracle_step_multitone(crops, ws, bs, seed, S, L):
             l_marl += val / (n * S)
             dp += grad / (n * S)
             rs.append(r["R"])
-        a, b = O.backward(c, ws, bs, seed, i, acts, lg, dp)
+        a, b = O.backward(c, ws, bs, seed, i, acts, lg, dp, quant=quant)
         for l in range(len(ws)):
             gw[l] += a[l]
             gb[l] += b[l]
@@ -152,6 +152,30 @@ def test_multitone_train_step_matches_oracle():
     errs = _grad_errors(gw, gb, ref_w, ref_b)
     for ew, eb in errs:
         assert ew <= 2e-3 and eb <= 2e-3, errs
+
+
+def test_bf16_multitone_train_step_matches_bf16_oracle():
+    """BF16 tensor-core training of the multitoning prototype (4 levels) against the
+    quant-1 oracle.  As in the binary BF16 step, samples flip where the level rule's
+    margin is below the forward error (L - 1 times more often than for the binary rule):
+    losses 3e-3 relative, gradients 4e-2 of the layer's largest entry."""
+    L = 4
+    ws, _ = synth.he_normal_policy(WIDE4, 91)
+    bs = synth.random_biases(WIDE4, 92, scale=0.1)
+    crops = [synth.contone_image(40, 150, seed=93, index=i) for i in range(2)]
+    S, seed = 2, 19
+    pol = api.Policy(WIDE4, ws, bs, head=N.HT_HEAD_MULTITONE, precision=N.HT_BF16, levels=L)
+    tr = api.Trainer(pol, (40, 150), max_crops=2, n_samples=S, n_gray=0, las_mode=1, n_rad=4, n_ang=4, w_a=0.0)
+    losses = tr.forward([torch.from_numpy(c).cuda() for c in crops], [], seed)
+    gw, gb = tr.backward()
+    torch.cuda.synchronize()
+    l_marl, r_mean, ref_w, ref_b = oracle_step_multitone(crops, ws, bs, seed, S, L, quant=1)
+    errs = _grad_errors(gw, gb, ref_w, ref_b)
+    print("multitone bf16: losses", losses, l_marl, r_mean, "errors", errs)
+    assert abs(losses[1] - l_marl) <= 3e-3 * abs(l_marl), (losses, l_marl)
+    assert abs(losses[3] - r_mean) <= 3e-3 * abs(r_mean), (losses, r_mean)
+    for ew, eb in errs:
+        assert ew <= 4e-2 and eb <= 4e-2, errs
 
 
 def test_autograd_function_drives_adam():
