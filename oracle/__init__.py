@@ -85,6 +85,10 @@ def lib():
                                       C.POINTER(C.c_void_p), C.c_uint64, C.c_uint32, C.c_int,
                                       C.POINTER(C.c_void_p), dp, dp, C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_void_p)]
+            L.or_forward_resnet.restype = C.c_int
+            L.or_forward_resnet.argtypes = [fp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                            C.POINTER(C.c_void_p), C.c_uint64, C.c_uint32, C.c_int, C.c_void_p,
+                                            C.c_void_p]
             L.or_num_threads.restype = C.c_int
             L.or_set_num_threads.argtypes = [C.c_int]
             _lib = L
@@ -241,6 +245,27 @@ def anisotropy_loss(q: np.ndarray, mode: int = 0, n_rad: int = 32, n_ang: int = 
     if rings < 0:
         raise ValueError("anisotropy loss needs an even n >= 4")
     return dict(loss=out[0], aniso=an, psd=psd, grad=g)
+
+
+def forward_resnet(contone: np.ndarray, weights, biases, noise_seed: int, image: int = 0, quant: int = 0):
+    """Residual policy (Sec. VI-A): stem 2 -> C, len(weights) // 2 - 1 residual blocks
+    y = ReLU(x + conv2(ReLU(conv1(x)))), output C -> 1, sigmoid.  Returns (logits, probs)
+    as [h][w] arrays."""
+    c = np.ascontiguousarray(contone, dtype=np.float32)
+    h, w = c.shape
+    ws = [np.ascontiguousarray(x, dtype=np.float32) for x in weights]
+    bs = [np.ascontiguousarray(x, dtype=np.float32) for x in biases]
+    L = len(ws)
+    nb = (L - 2) // 2
+    C_ = ws[0].shape[0]
+    wp = (C.c_void_p * L)(*[x.ctypes.data for x in ws])
+    bp = (C.c_void_p * L)(*[x.ctypes.data for x in bs])
+    lg = np.zeros((h, w))
+    pr = np.zeros((h, w))
+    rc = lib().or_forward_resnet(c, h, w, w, nb, C_, wp, bp, noise_seed, image, quant, _ptr(lg), _ptr(pr))
+    if rc != 0:
+        raise ValueError("or_forward_resnet failed")
+    return lg, pr
 
 
 def backward(contone: np.ndarray, weights, biases, noise_seed: int, image: int, acts, logits: np.ndarray,

@@ -807,6 +807,94 @@ int or_backward(const float *contone, int h, int w, int pitch,
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Residual policy of Sec. VI-A (He et al. 2016 blocks): a stem convolution   */
+/* 2 -> C with ReLU, n_blocks residual blocks                                 */
+/*   y = ReLU(x + conv2(ReLU(conv1(x))))   (identity shortcut, C -> C)         */
+/* and an output convolution C -> 1 followed by the sigmoid.  All 3x3, stride  */
+/* 1, zero padding 1.  Layers in order: stem, (conv1, conv2) per block, out;   */
+/* weights OIHW.  Whole image only.  quant 1 (BF16 form): block weights and   */
+/* every stored activation (stem output, conv1 output, block output) rounded  */
+/* to bf16; the stem and output weights stay exact.                            */
+/* ------------------------------------------------------------------------- */
+static void conv3x3_full(const double *in, int ci, int co, int h, int w, const double *wt, const float *b,
+                         double *out)
+{
+    size_t np = (size_t)h * w;
+#pragma omp parallel for schedule(static)
+    for (int o = 0; o < co; ++o) {
+        double *op = out + (size_t)o * np;
+        for (size_t k = 0; k < np; ++k) op[k] = (double)b[o];
+        for (int i = 0; i < ci; ++i)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx) {
+                    double wv = wt[(((size_t)o * ci + i) * 3 + ky) * 3 + kx];
+                    for (int y = 0; y < h; ++y) {
+                        int yy = y + ky - 1;
+                        if (yy < 0 || yy >= h) continue;
+                        for (int x = 0; x < w; ++x) {
+                            int xx = x + kx - 1;
+                            if (xx < 0 || xx >= w) continue;
+                            op[(size_t)y * w + x] += wv * in[(size_t)i * np + (size_t)yy * w + xx];
+                        }
+                    }
+                }
+    }
+}
+
+int or_forward_resnet(const float *contone, int h, int w, int pitch, int n_blocks, int C,
+                      const float *const *weights, const float *const *biases, uint64_t noise_seed, uint32_t image,
+                      int quant, double *logits_out, double *prob_out)
+{
+    if (h < 1 || w < 1 || n_blocks < 0 || C < 1) return OR_EINVAL;
+    const int L = 2 + 2 * n_blocks;
+    size_t np = (size_t)h * w;
+    double *x = (double *)malloc((size_t)C * np * sizeof(double));
+    double *t = (double *)malloc((size_t)C * np * sizeof(double));
+    double *u = (double *)malloc((size_t)C * np * sizeof(double));
+    double *in0 = (double *)malloc(2 * np * sizeof(double));
+    double *wq = (double *)malloc((size_t)C * C * 9 * sizeof(double));
+    if (!x || !t || !u || !in0 || !wq) return OR_ENOMEM;
+    for (int y = 0; y < h; ++y)
+        for (int xx = 0; xx < w; ++xx) {
+            in0[(size_t)y * w + xx] = (double)contone[(size_t)y * pitch + xx];
+            in0[np + (size_t)y * w + xx] = or_uniform(noise_seed, image, 0u, (uint64_t)y * w + xx);
+        }
+    /* stem */
+    for (size_t k = 0; k < (size_t)C * 2 * 9; ++k) wq[k] = (double)weights[0][k];
+    conv3x3_full(in0, 2, C, h, w, wq, biases[0], x);
+    for (size_t k = 0; k < (size_t)C * np; ++k) {
+        double v = x[k] > 0.0 ? x[k] : 0.0;
+        x[k] = quant == 1 ? or_round_bf16(v) : v;
+    }
+    for (int b = 0; b < n_blocks; ++b) {
+        const int l1 = 1 + 2 * b, l2 = l1 + 1;
+        for (size_t k = 0; k < (size_t)C * C * 9; ++k)
+            wq[k] = quant == 1 ? or_round_bf16((double)weights[l1][k]) : (double)weights[l1][k];
+        conv3x3_full(x, C, C, h, w, wq, biases[l1], t);
+        for (size_t k = 0; k < (size_t)C * np; ++k) {
+            double v = t[k] > 0.0 ? t[k] : 0.0;
+            t[k] = quant == 1 ? or_round_bf16(v) : v;
+        }
+        for (size_t k = 0; k < (size_t)C * C * 9; ++k)
+            wq[k] = quant == 1 ? or_round_bf16((double)weights[l2][k]) : (double)weights[l2][k];
+        conv3x3_full(t, C, C, h, w, wq, biases[l2], u);
+        for (size_t k = 0; k < (size_t)C * np; ++k) {
+            double v = u[k] + x[k];
+            v = v > 0.0 ? v : 0.0;
+            x[k] = quant == 1 ? or_round_bf16(v) : v;
+        }
+    }
+    for (size_t k = 0; k < (size_t)C * 9; ++k) wq[k] = (double)weights[L - 1][k];
+    conv3x3_full(x, C, 1, h, w, wq, biases[L - 1], t);
+    for (size_t k = 0; k < np; ++k) {
+        if (logits_out) logits_out[k] = t[k];
+        if (prob_out) prob_out[k] = 1.0 / (1.0 + exp(-t[k]));
+    }
+    free(x); free(t); free(u); free(in0); free(wq);
+    return OR_OK;
+}
+
 int or_num_threads(void)
 {
 #ifdef _OPENMP

@@ -91,6 +91,23 @@ def he_normal_policy(channels: Sequence[int], seed: int) -> Tuple[List[np.ndarra
     return ws, bs
 
 
+def resnet_policy(n_blocks: int, width: int, seed: int, branch_scale: float = 0.0) -> Tuple[List[np.ndarray], List[np.ndarray]]:
+    """Residual policy weights (layers: stem, (conv1, conv2) per block, out), He-normal
+    with each block's second convolution scaled by branch_scale (default 1 / sqrt(n_blocks),
+    so that the residual stream does not grow with depth); zero biases."""
+    ch = resnet_channels(n_blocks, width)
+    ws, bs = he_normal_policy(ch, seed)
+    k = branch_scale or 1.0 / math.sqrt(max(1, n_blocks))
+    for b in range(n_blocks):
+        ws[2 + 2 * b] = (ws[2 + 2 * b] * k).astype(np.float32)
+    return ws, bs
+
+
+def resnet_channels(n_blocks: int, width: int) -> Tuple[int, ...]:
+    """Channels per layer boundary of the residual policy (stem, 2 per block, out)."""
+    return (2,) + (width,) * (1 + 2 * n_blocks) + (1,)
+
+
 def random_biases(channels: Sequence[int], seed: int, scale: float = 0.05) -> List[np.ndarray]:
     """Small non-zero biases (tests use them so that the bias path is exercised)."""
     out = []
@@ -124,6 +141,7 @@ def uneven_shapes(n: int, seed: int, min_hw=(200, 300), max_hw=(4096, 3072),
 NET_SMALL = (2, 32, 32, 32, 32, 32, 1)            # 6 conv layers, 32 wide
 NET_WIDE = (2, 64, 64, 64, 64, 64, 64, 64, 1)     # 8 conv layers, 64 wide
 NET_WIDE_K4 = (2, 64, 64, 64, 64, 64, 64, 64, 4)  # 4-logit softmax head
+RESNET_BLOCKS, RESNET_WIDTH = 16, 32              # residual policy of Sec. VI-A
 
 
 def net_flops_per_px(channels: Sequence[int]) -> int:
