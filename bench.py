@@ -108,16 +108,21 @@ def dist_info():
     return rank, world, local
 
 
-def cpu_oracle_sample(img, ws, bs, side, seed, image_id=0, quant=1, mode=1, scales=None, levels=0):
+def cpu_oracle_sample(img, ws, bs, side, seed, image_id=0, quant=1, mode=1, scales=None, levels=0, resnet=False):
     """FP64 oracle (optionally emulating the reduced-precision rounding) forward and
-    actions on a side x side centre crop (levels > 0: the multitoning prototype's rule)."""
+    actions on a side x side centre crop (levels > 0: the multitoning prototype's rule;
+    resnet: the residual policy)."""
     import oracle as O
     h, w = img.shape
     side = min(side, h, w)
     y0, x0 = (h - side) // 2, (w - side) // 2
     reg = (y0, x0, side, side)
     t0 = time.perf_counter()
-    _, p, _ = O.forward(img, ws, bs, noise_seed=seed, image=image_id, quant=quant, act_scale=scales, region=reg)
+    if resnet:
+        _, p1 = O.forward_resnet(img, ws, bs, seed, image_id, quant=quant, region=reg)
+        p = p1[None]
+    else:
+        _, p, _ = O.forward(img, ws, bs, noise_seed=seed, image=image_id, quant=quant, act_scale=scales, region=reg)
     lev, u = O.sample(p, h, w, reg, mode, seed, image_id)
     if levels:
         lev = O.sample_multitone(p[0], levels, u if mode == 1 else None)
@@ -166,6 +171,10 @@ WORKLOADS = {
     "small": ("one 256x256 image (seed 0), 2->32x5->1 policy, plain FP32, threshold 0.5", "fp32", 0, "small", 0, 0),
     "proto": ("multitoning prototype 4x4096x4096, 2->64x7->1 sigmoid output, action between the 2 of 4 levels "
               "around it, BF16, Philox seed 2", "bf16", 2, "wide", 1, 2),
+    "resnet512": ("residual policy (16 blocks x 32 ch, 34 conv layers) on one 512x512 image (the paper's "
+                  "runtime setting), BF16, threshold", "bf16", 0, "resnet", 0, 5),
+    "resnet": ("residual policy (16 blocks x 32 ch, 34 conv layers) on 8x2048x2048, BF16, Bernoulli seed 1",
+               "bf16", 0, "resnet", 1, 1),
 }
 
 
@@ -181,6 +190,9 @@ def build_inputs(args, rank):
     elif args.workload in ("multitone", "proto"):
         shapes = [(4096, 4096)] * 4
         seed = 2
+    elif args.workload == "resnet512":
+        shapes = [(512, 512)]
+        seed = 5
     elif args.workload == "uneven":
         shapes = synth.uneven_shapes(64, seed=4)
         seed = 4
@@ -227,10 +239,16 @@ def main():
     from paper_2304_12152_gb300 import api, synth
 
     desc, precision, head, netname, mode, seed = WORKLOADS[args.workload]
-    chs = {"wide": synth.NET_WIDE, "wide4": synth.NET_WIDE_K4, "small": synth.NET_SMALL}[netname]
-    ws, bs = synth.he_normal_policy(chs, 1)
+    resnet = netname == "resnet"
+    if resnet:
+        chs = synth.resnet_channels(synth.RESNET_BLOCKS, synth.RESNET_WIDTH)
+        ws, bs = synth.resnet_policy(synth.RESNET_BLOCKS, synth.RESNET_WIDTH, 1)
+    else:
+        chs = {"wide": synth.NET_WIDE, "wide4": synth.NET_WIDE_K4, "small": synth.NET_SMALL}[netname]
+        ws, bs = synth.he_normal_policy(chs, 1)
     prec = {"bf16": N.HT_BF16, "fp8": N.HT_FP8_E4M3, "fp32": N.HT_FP32}[precision]
-    pol = api.Policy(chs, ws, bs, head=head, precision=prec, levels=4)
+    pol = api.Policy(chs, ws, bs, head=head, precision=prec, levels=4,
+                     arch=N.HT_ARCH_RESNET if resnet else N.HT_ARCH_PLAIN)
     dev = torch.device("cuda", local)
     if prec == N.HT_FP8_E4M3:
         calib = torch.from_numpy(synth.contone_image(256, 256, seed=99)).to(dev)
@@ -334,7 +352,7 @@ def main():
 
     # ---------------- plain FP32 form of the same net ----------------
     fp32 = None
-    if prec != N.HT_FP32 and args.fp32_steps > 0:
+    if prec != N.HT_FP32 and args.fp32_steps > 0 and not resnet:
         pol32 = api.Policy(chs, ws, bs, head=head, precision=N.HT_FP32, levels=4)
         pol32.halftone_into(cs, bits, mode, seed)
         torch.cuda.synchronize()
@@ -391,11 +409,12 @@ def main():
         quant = {N.HT_BF16: 1, N.HT_FP8_E4M3: 2, N.HT_FP32: 0}[prec]
         side = 32
         lv = 4 if head == N.HT_HEAD_MULTITONE else 0
-        dt, *_ = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None, levels=lv)
+        dt, *_ = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None, levels=lv,
+                                   resnet=resnet)
         side = int(min(min(imgs_np[0].shape), 1024, max(32, side * math.sqrt(15.0 / max(dt, 1e-3)))))
         side -= side % 8
         dt, reg, p, lev_or, u = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None,
-                                                  levels=lv)
+                                                  levels=lv, resnet=resnet)
         cpu = {"value": side * side / dt / 1e6, "unit": "Mpx/s", "cores": O.num_threads(), "kind": "oracle",
                "sample": f"{side}x{side} centre crop of image 0 (+halo), FP64 forward"
                          f"{' emulating the ' + precision.upper() + ' rounding' if quant else ''} + actions",

@@ -55,7 +55,7 @@
 extern "C" {
 #endif
 
-#define HT_MAX_LAYERS 16
+#define HT_MAX_LAYERS 40
 #define HT_MAX_CHANNELS 64
 
 typedef enum {
@@ -83,12 +83,22 @@ typedef enum { HT_MODE_THRESHOLD = 0, HT_MODE_BERNOULLI = 1 } ht_mode;
  * mode: the nearest level), level index packed in 2 bits/px.
  * precision: FP32 = plain CUDA-core form; BF16 / FP8_E4M3 = tensor-core form
  * (hidden widths must then all be 64; FP32 accumulation). */
+typedef enum { HT_ARCH_PLAIN = 0, HT_ARCH_RESNET = 1 } ht_arch;
+
+/* arch RESNET: the residual policy of Sec. VI-A.  Layers: a stem convolution
+ * 2 -> C with ReLU, then per residual block conv1 (C -> C, ReLU) and conv2
+ * (C -> C) with the identity shortcut y = ReLU(x + conv2(ReLU(conv1(x)))), then
+ * the output convolution C -> 1 (sigmoid or multitone head).  n_layers = 2 + 2 x
+ * blocks; every hidden width C = 32; BF16 tensor-core form only (other
+ * precisions return HT_ERR_UNSUPPORTED).  Weights in the same layer order,
+ * canonical OIHW. */
 typedef struct {
     int n_layers;
     int channels[HT_MAX_LAYERS + 1];
     int head;
     int precision;
     int levels;           /* MULTITONE head: ink levels, 2..4 (ignored otherwise) */
+    int arch;             /* HT_ARCH_PLAIN (the 3x3 conv stack above) or HT_ARCH_RESNET */
 } ht_policy_desc;
 
 typedef struct {

@@ -87,8 +87,8 @@ def lib():
                                       C.POINTER(C.c_void_p)]
             L.or_forward_resnet.restype = C.c_int
             L.or_forward_resnet.argtypes = [fp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p),
-                                            C.POINTER(C.c_void_p), C.c_uint64, C.c_uint32, C.c_int, C.c_void_p,
-                                            C.c_void_p]
+                                            C.POINTER(C.c_void_p), C.c_uint64, C.c_uint32, C.c_int, C.c_int,
+                                            C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
             L.or_num_threads.restype = C.c_int
             L.or_set_num_threads.argtypes = [C.c_int]
             _lib = L
@@ -247,12 +247,14 @@ def anisotropy_loss(q: np.ndarray, mode: int = 0, n_rad: int = 32, n_ang: int = 
     return dict(loss=out[0], aniso=an, psd=psd, grad=g)
 
 
-def forward_resnet(contone: np.ndarray, weights, biases, noise_seed: int, image: int = 0, quant: int = 0):
+def forward_resnet(contone: np.ndarray, weights, biases, noise_seed: int, image: int = 0, quant: int = 0,
+                   region: Optional[Tuple[int, int, int, int]] = None):
     """Residual policy (Sec. VI-A): stem 2 -> C, len(weights) // 2 - 1 residual blocks
     y = ReLU(x + conv2(ReLU(conv1(x)))), output C -> 1, sigmoid.  Returns (logits, probs)
-    as [h][w] arrays."""
+    as [rh][rw] arrays over region (y0, x0, rh, rw) (default: the whole image)."""
     c = np.ascontiguousarray(contone, dtype=np.float32)
-    h, w = c.shape
+    H, W = c.shape
+    y0, x0, h, w = region if region is not None else (0, 0, H, W)
     ws = [np.ascontiguousarray(x, dtype=np.float32) for x in weights]
     bs = [np.ascontiguousarray(x, dtype=np.float32) for x in biases]
     L = len(ws)
@@ -262,7 +264,8 @@ def forward_resnet(contone: np.ndarray, weights, biases, noise_seed: int, image:
     bp = (C.c_void_p * L)(*[x.ctypes.data for x in bs])
     lg = np.zeros((h, w))
     pr = np.zeros((h, w))
-    rc = lib().or_forward_resnet(c, h, w, w, nb, C_, wp, bp, noise_seed, image, quant, _ptr(lg), _ptr(pr))
+    rc = lib().or_forward_resnet(c, H, W, W, nb, C_, wp, bp, noise_seed, image, quant, y0, x0, h, w, _ptr(lg),
+                                 _ptr(pr))
     if rc != 0:
         raise ValueError("or_forward_resnet failed")
     return lg, pr

@@ -842,12 +842,19 @@ static void conv3x3_full(const double *in, int ci, int co, int h, int w, const d
     }
 }
 
-int or_forward_resnet(const float *contone, int h, int w, int pitch, int n_blocks, int C,
+int or_forward_resnet(const float *contone, int H, int W, int pitch, int n_blocks, int C,
                       const float *const *weights, const float *const *biases, uint64_t noise_seed, uint32_t image,
-                      int quant, double *logits_out, double *prob_out)
+                      int quant, int y0, int x0, int rh, int rw, double *logits_out, double *prob_out)
 {
-    if (h < 1 || w < 1 || n_blocks < 0 || C < 1) return OR_EINVAL;
+    /* outputs over the rectangle (y0, x0, rh, rw): the net runs on the rectangle grown
+     * by L pixels (clamped to the image; its cut edges are zero-padded, which only
+     * reaches L pixels in) with the noise channel at image coordinates */
+    if (H < 1 || W < 1 || n_blocks < 0 || C < 1 || rh < 1 || rw < 1 || y0 < 0 || x0 < 0 || y0 + rh > H ||
+        x0 + rw > W)
+        return OR_EINVAL;
     const int L = 2 + 2 * n_blocks;
+    or_rect R = rect_grow(y0, x0, rh, rw, L, H, W);
+    const int h = R.yhi - R.ylo, w = R.xhi - R.xlo;
     size_t np = (size_t)h * w;
     double *x = (double *)malloc((size_t)C * np * sizeof(double));
     double *t = (double *)malloc((size_t)C * np * sizeof(double));
@@ -857,8 +864,9 @@ int or_forward_resnet(const float *contone, int h, int w, int pitch, int n_block
     if (!x || !t || !u || !in0 || !wq) return OR_ENOMEM;
     for (int y = 0; y < h; ++y)
         for (int xx = 0; xx < w; ++xx) {
-            in0[(size_t)y * w + xx] = (double)contone[(size_t)y * pitch + xx];
-            in0[np + (size_t)y * w + xx] = or_uniform(noise_seed, image, 0u, (uint64_t)y * w + xx);
+            const int gy = R.ylo + y, gx = R.xlo + xx;
+            in0[(size_t)y * w + xx] = (double)contone[(size_t)gy * pitch + gx];
+            in0[np + (size_t)y * w + xx] = or_uniform(noise_seed, image, 0u, (uint64_t)gy * W + gx);
         }
     /* stem */
     for (size_t k = 0; k < (size_t)C * 2 * 9; ++k) wq[k] = (double)weights[0][k];
@@ -887,10 +895,12 @@ int or_forward_resnet(const float *contone, int h, int w, int pitch, int n_block
     }
     for (size_t k = 0; k < (size_t)C * 9; ++k) wq[k] = (double)weights[L - 1][k];
     conv3x3_full(x, C, 1, h, w, wq, biases[L - 1], t);
-    for (size_t k = 0; k < np; ++k) {
-        if (logits_out) logits_out[k] = t[k];
-        if (prob_out) prob_out[k] = 1.0 / (1.0 + exp(-t[k]));
-    }
+    for (int y = 0; y < rh; ++y)
+        for (int xx = 0; xx < rw; ++xx) {
+            const double v = t[(size_t)(y0 - R.ylo + y) * w + (x0 - R.xlo + xx)];
+            if (logits_out) logits_out[(size_t)y * rw + xx] = v;
+            if (prob_out) prob_out[(size_t)y * rw + xx] = 1.0 / (1.0 + exp(-v));
+        }
     free(x); free(t); free(u); free(in0); free(wq);
     return OR_OK;
 }

@@ -11,12 +11,13 @@ import threading
 
 from . import build as _build
 
-HT_MAX_LAYERS = 16
+HT_MAX_LAYERS = 40
 HT_OK, HT_ERR_INVALID_ARG, HT_ERR_UNSUPPORTED, HT_ERR_OOM, HT_ERR_CUDA, HT_ERR_TIMEOUT = range(6)
 HT_FP32, HT_BF16, HT_FP8_E4M3 = 0, 1, 2
 HT_HEAD_SIGMOID, HT_HEAD_SOFTMAX, HT_HEAD_MULTITONE = 0, 1, 2
 HT_MODE_THRESHOLD, HT_MODE_BERNOULLI = 0, 1
 HT_EST_LE, HT_EST_COMA = 0, 1
+HT_ARCH_PLAIN, HT_ARCH_RESNET = 0, 1
 
 # Every entry point declared in include/ht.h.
 EXPORTS = (
@@ -32,7 +33,7 @@ EXPORTS = (
 
 class PolicyDesc(C.Structure):
     _fields_ = [("n_layers", C.c_int), ("channels", C.c_int * (HT_MAX_LAYERS + 1)), ("head", C.c_int),
-                ("precision", C.c_int), ("levels", C.c_int)]
+                ("precision", C.c_int), ("levels", C.c_int), ("arch", C.c_int)]
 
 
 class Image(C.Structure):

@@ -49,9 +49,11 @@ class Policy:
     """ht_policy: owns packed weights and the forward workspace."""
 
     def __init__(self, channels: Sequence[int], weights: Sequence[np.ndarray], biases: Sequence[np.ndarray],
-                 head: int = N.HT_HEAD_SIGMOID, precision: int = N.HT_FP32, levels: int = 4):
+                 head: int = N.HT_HEAD_SIGMOID, precision: int = N.HT_FP32, levels: int = 4,
+                 arch: int = N.HT_ARCH_PLAIN):
         L = N.load()
         d = N.PolicyDesc()
+        d.arch = arch
         d.n_layers = len(channels) - 1
         for i, c in enumerate(channels):
             d.channels[i] = int(c)

@@ -176,6 +176,21 @@ static ht_status validate_desc(const ht_policy_desc *d)
     }
     HT_CHECK_ARG(d->precision == HT_FP32 || d->precision == HT_BF16 || d->precision == HT_FP8_E4M3,
                  "unknown precision %d", d->precision);
+    HT_CHECK_ARG(d->arch == HT_ARCH_PLAIN || d->arch == HT_ARCH_RESNET, "unknown arch %d", d->arch);
+    if (d->arch == HT_ARCH_RESNET) {
+        HT_CHECK_ARG(d->n_layers >= 4 && d->n_layers % 2 == 0, "residual policy: n_layers = 2 + 2 x blocks");
+        HT_CHECK_ARG(d->head != HT_HEAD_SOFTMAX, "residual policy: sigmoid-output heads only");
+        for (int l = 1; l < d->n_layers; ++l)
+            if (d->channels[l] != 32) {
+                ht_set_error("residual policy: every hidden width must be 32");
+                return HT_ERR_UNSUPPORTED;
+            }
+        if (d->precision != HT_BF16) {
+            ht_set_error("residual policy: BF16 tensor-core form only");
+            return HT_ERR_UNSUPPORTED;
+        }
+        return HT_OK;
+    }
     if (d->precision != HT_FP32) {
         if (d->n_layers < 3) {
             ht_set_error("tensor-core forms need at least one 64 -> 64 layer");
@@ -204,6 +219,8 @@ ht_status ht_create_policy(const ht_policy_desc *desc, const float *weights_host
     memcpy(p->ch, desc->channels, sizeof(p->ch));
     p->head = desc->head;
     p->levels = desc->head == HT_HEAD_MULTITONE ? desc->levels : desc->head == HT_HEAD_SOFTMAX ? 4 : 2;
+    p->arch = desc->arch;
+    p->width = desc->arch == HT_ARCH_RESNET ? 32 : 64;
     p->K = desc->channels[desc->n_layers];
     p->prec = desc->precision;
     cudaGetDevice(&p->device);

@@ -56,16 +56,23 @@ constexpr int NTHREADS = 320;              // producer, MMA issuer, 8 epilogue w
 // bf16 hi weights, the same 4 with the lo parts, 8 zero columns: the weights stay
 // exact as hi + lo in one MMA per K step); its epilogue adds the two parts,
 // applies softmax, draws the level and packs 2 bits/px.
-enum : int { KIND_HIDDEN = 0, KIND_HEADPART = 1, KIND_FIRST = 2, KIND_HEAD4 = 3 };
+// Residual policy (Sec. VI-A, CH = 32): KIND_RES is a block's second convolution,
+// whose epilogue adds the block input -- read in place from the output buffer
+// before it is overwritten -- ahead of the ReLU; KIND_RESHEAD is the last block's,
+// which turns its output into the head partials instead of storing it.
+enum : int { KIND_HIDDEN = 0, KIND_HEADPART = 1, KIND_FIRST = 2, KIND_HEAD4 = 3, KIND_RES = 4, KIND_RESHEAD = 5 };
 
-template <bool FP8, int KIND>
+template <bool FP8, int KIND, int CH = 64>
 struct Cfg {
     static constexpr bool FIRST = KIND == KIND_FIRST;
     static constexpr bool HEAD4 = KIND == KIND_HEAD4;
+    static constexpr bool RES = KIND == KIND_RES || KIND == KIND_RESHEAD;
+    static constexpr bool HEADP = KIND == KIND_HEADPART || KIND == KIND_RESHEAD;   // fused head partials
     static constexpr bool MMA8 = FP8 && !FIRST && !HEAD4;      // e4m3 operands (kind::f8f6f4)
-    static constexpr int NCHUNK = FIRST ? 2 : (MMA8 ? 4 : 8);  // 16-byte chunks per staged pixel
+    static constexpr int CO = CH;                              // output channels (all but the 4-logit head)
+    static constexpr int NCHUNK = FIRST ? 2 : (MMA8 ? CH / 16 : CH / 8);   // 16-byte chunks per staged pixel
     static constexpr int NCOPY = FIRST ? 1 : NCHUNK;           // chunks staged from HBM (layer 1: chunk 1 is zero)
-    static constexpr int NOUT = HEAD4 ? 16 : 64;               // output columns per dy block (= TMEM block stride)
+    static constexpr int NOUT = HEAD4 ? 16 : CH;               // output columns per dy block (= TMEM block stride)
     static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;
     static constexpr int W_BYTES = 3 * NCHUNK * 3 * NOUT * 16; // [dx][chunk][3 dy][NOUT n][16 B]
     static constexpr int KSTEPS = NCHUNK / 2;                  // MMAs per dx (K = 16 / 32 per MMA)
@@ -109,10 +116,10 @@ struct ConvParams {
 // accumulator block is zeroed by the epilogue after it is drained, so all MMAs
 // accumulate.  Per output row: 12-15 MMAs of N = 192 instead of 36 of N = 64.
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND, bool TR = false>
+template <bool FP8, int KIND, bool TR = false, int CH = 64>
 __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 {
-    using C = Cfg<FP8, KIND>;
+    using C = Cfg<FP8, KIND, CH>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *s_w = smem;
@@ -332,15 +339,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     }
                     continue;
                 }
-                float v[64];
+                float v[C::CO];
                 if (j < nrows) {
-                    const uint32_t taddr = lane_base + j * 64u;
-                    tmem_ld16(taddr + 0, v + 0);
-                    tmem_ld16(taddr + 16, v + 16);
-                    tmem_ld16(taddr + 32, v + 32);
-                    tmem_ld16(taddr + 48, v + 48);
+                    const uint32_t taddr = lane_base + j * (uint32_t)C::NOUT;
+#pragma unroll
+                    for (int c = 0; c < C::CO; c += 16) tmem_ld16(taddr + c, v + c);
                     tmem_wait_ld();
-                    for (int c = 0; c < 64; c += 16) tmem_zero16(taddr + c);
+                    for (int c = 0; c < C::CO; c += 16) tmem_zero16(taddr + c);
                     tmem_wait_st();
                 }
                 tc_fence_before();
@@ -352,41 +357,57 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         // data gradient: mask by the ReLU of the layer this gradient flows into
                         const uint2 m = __ldg(ui.D->mask + o);
 #pragma unroll
-                        for (int n = 0; n < 64; ++n)
+                        for (int n = 0; n < C::CO; ++n)
                             if (!(((n < 32 ? m.x : m.y) >> (n & 31)) & 1u)) v[n] = 0.f;
-                        store_pixel(v, ui.out, 0, 1.f, ui.H, ui.W, y0 + j, x);
+                        store_pixel<C::CO>(v, ui.out, 0, 1.f, ui.H, ui.W, y0 + j, x);
                         continue;
                     }
 #pragma unroll
-                    for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], P.scale[n], P.bias[n]), 0.f);
+                    for (int n = 0; n < C::CO; ++n) v[n] = fmaf(v[n], P.scale[n], P.bias[n]);
+                    if constexpr (C::RES) {
+                        // identity shortcut: the block input, stored (bf16) where this output goes
+#pragma unroll
+                        for (int c = 0; c < C::CO / 8; ++c) {
+                            const uint4 q = *reinterpret_cast<const uint4 *>(
+                                ui.out + (((size_t)c * ui.H + y0 + j) * ui.W + x) * 16);
+                            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                v[8 * c + 2 * h] += __uint_as_float(w4[h] << 16);
+                                v[8 * c + 2 * h + 1] += __uint_as_float(w4[h] & 0xFFFF0000u);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int n = 0; n < C::CO; ++n) v[n] = fmaxf(v[n], 0.f);
                     if (TR && ui.D->mask) {
                         // training forward: which stored (bf16) activations are positive
                         uint2 m = make_uint2(0u, 0u);
 #pragma unroll
                         for (int n = 0; n < 32; ++n) {
                             m.x |= (bf16_round(v[n]) > 0.f ? 1u : 0u) << n;
-                            m.y |= (bf16_round(v[n + 32]) > 0.f ? 1u : 0u) << n;
+                            if (C::CO > 32) m.y |= (bf16_round(v[(n + 32) % C::CO]) > 0.f ? 1u : 0u) << n;
                         }
                         ui.D->mask[o] = m;
                     }
-                    if constexpr (KIND == KIND_HEADPART) {
-                        // fused 64 -> 1 head: per-tap dot products of the bf16-rounded activations
+                    if constexpr (C::HEADP) {
+                        // fused C -> 1 head: per-tap dot products of the bf16-rounded activations
                         const size_t plane = (size_t)ui.H * ui.W;
-                        float *partials = (float *)ui.out;
+                        float *partials = ui.D->part ? ui.D->part : (float *)ui.out;
                         float acc[9];
 #pragma unroll
                         for (int t = 0; t < 9; ++t) acc[t] = 0.f;
 #pragma unroll
-                        for (int n = 0; n < 64; ++n) {
+                        for (int n = 0; n < C::CO; ++n) {
                             const float a = bf16_round(v[n]);
 #pragma unroll
-                            for (int t = 0; t < 9; ++t) acc[t] = fmaf(a, P.head_w[t * 64 + n], acc[t]);   // nine chains
+                            for (int t = 0; t < 9; ++t) acc[t] = fmaf(a, P.head_w[t * C::CO + n], acc[t]);   // nine chains
                         }
 #pragma unroll
                         for (int t = 0; t < 9; ++t) partials[t * plane + o] = acc[t];
-                        if (TR && ui.D->save) store_pixel(v, ui.D->save, 0, 1.f, ui.H, ui.W, y0 + j, x);
+                        if (TR && ui.D->save) store_pixel<C::CO>(v, ui.D->save, 0, 1.f, ui.H, ui.W, y0 + j, x);
                     } else {
-                        store_pixel(v, ui.out, P.out_fp8, P.out_inv_scale, ui.H, ui.W, y0 + j, x);
+                        store_pixel<C::CO>(v, ui.out, P.out_fp8, P.out_inv_scale, ui.H, ui.W, y0 + j, x);
                     }
                 }
             }
@@ -451,7 +472,7 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__r
     const ImgDesc *D = imgs + im;
     const int lt = (int)blockIdx.x - D->hd_begin;
     const int H = D->H, W = D->W, words = D->words;
-    const float *__restrict__ part = (const float *)D->act[buf];
+    const float *__restrict__ part = D->part ? D->part : (const float *)D->act[buf];
     const int hx = (W + HT_X - 1) / HT_X;
     const int x0 = (lt % hx) * HT_X, y = (lt / hx) * HT_Y + threadIdx.y, x = x0 + threadIdx.x;
     const size_t plane = (size_t)H * W;
@@ -469,13 +490,13 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__r
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND, bool TR = false>
+template <bool FP8, int KIND, bool TR = false, int CH = 64>
 ht_status ensure_attr()
 {
     static bool attr_set = false;
     if (!attr_set) {
-        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg<FP8, KIND>::SMEM));
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND, TR, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<FP8, KIND, CH>::SMEM));
         attr_set = true;
     }
     return HT_OK;
@@ -489,20 +510,24 @@ ht_status ensure_all_attrs()
         (st = ensure_attr<false, KIND_FIRST>()) != HT_OK || (st = ensure_attr<false, KIND_HEAD4>()) != HT_OK ||
         (st = ensure_attr<true, KIND_HIDDEN>()) != HT_OK || (st = ensure_attr<true, KIND_HEADPART>()) != HT_OK ||
         (st = ensure_attr<true, KIND_FIRST>()) != HT_OK || (st = ensure_attr<false, KIND_HIDDEN, true>()) != HT_OK ||
-        (st = ensure_attr<false, KIND_HEADPART, true>()) != HT_OK || (st = ensure_attr<false, KIND_FIRST, true>()) != HT_OK)
+        (st = ensure_attr<false, KIND_HEADPART, true>()) != HT_OK || (st = ensure_attr<false, KIND_FIRST, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_FIRST, false, 32>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HIDDEN, false, 32>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_RES, false, 32>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_RESHEAD, false, 32>()) != HT_OK)
         return st;
     return HT_OK;
 }
 
-template <bool FP8, int KIND, bool TR = false>
+template <bool FP8, int KIND, bool TR = false, int CH = 64>
 ht_status launch_conv(const ConvParams &P, cudaStream_t s)
 {
-    const ht_status st = ensure_attr<FP8, KIND, TR>();
+    const ht_status st = ensure_attr<FP8, KIND, TR, CH>();
     if (st != HT_OK) return st;
     const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
     ht_prof_start(KIND == KIND_FIRST ? HTK_FIRST_TC : KIND == KIND_HEAD4 ? HTK_HEAD_TC
                                                   : FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
-    k_conv_tc<FP8, KIND, TR><<<grid, NTHREADS, Cfg<FP8, KIND>::SMEM, s>>>(P);
+    k_conv_tc<FP8, KIND, TR, CH><<<grid, NTHREADS, Cfg<FP8, KIND, CH>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -548,14 +573,15 @@ uint8_t f64_to_e4m3_rne(double x)
 ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
 {
     const bool fp8 = (p->prec == HT_FP8_E4M3);
-    const int cpc = fp8 ? 16 : 8, nchunk = fp8 ? 4 : 8;
-    const size_t layer_bytes = (size_t)9 * nchunk * 64 * 16;
+    const int CH = p->width;                                   // hidden width (64, or 32 for the residual policy)
+    const int cpc = fp8 ? 16 : 8, nchunk = CH / cpc;
+    const size_t layer_bytes = (size_t)9 * nchunk * CH * 16;
     const int n_inner = p->L - 2;
     p->wpack_layer_bytes = layer_bytes;
     if (!p->d_wpack) HT_CUDA_TRY(cudaMalloc(&p->d_wpack, layer_bytes * n_inner));
     if (fp8 && !p->d_wscale) HT_CUDA_TRY(cudaMalloc((void **)&p->d_wscale, sizeof(float) * 64 * n_inner));
     // pull the current fp32 weights of the inner layers to the host
-    const size_t nw = (size_t)64 * 64 * 9;
+    const size_t nw = (size_t)CH * CH * 9;
     float *hw = (float *)malloc(sizeof(float) * nw * n_inner);
     uint8_t *hp = (uint8_t *)malloc(layer_bytes * n_inner);
     float *hs = (float *)malloc(sizeof(float) * 64 * n_inner);
@@ -576,19 +602,19 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
     for (int l = 0; l < n_inner; ++l) {
         const float *W = hw + nw * l;     // [n][c][3][3]
         uint8_t *dst = hp + layer_bytes * l;
-        for (int n = 0; n < 64; ++n) {
+        for (int n = 0; n < CH; ++n) {
             double sc = 1.0;
             if (fp8) {
                 double amax = 0.0;
-                for (int k = 0; k < 64 * 9; ++k) amax = fmax(amax, fabs((double)W[(size_t)n * 576 + k]));
+                for (int k = 0; k < CH * 9; ++k) amax = fmax(amax, fabs((double)W[(size_t)n * CH * 9 + k]));
                 sc = amax > 0.0 ? amax / 448.0 : 1.0;
                 hs[64 * l + n] = (float)sc;
             }
             for (int tap = 0; tap < 9; ++tap)
-                for (int c = 0; c < 64; ++c) {
-                    const float wv = W[((size_t)n * 64 + c) * 9 + tap];
+                for (int c = 0; c < CH; ++c) {
+                    const float wv = W[((size_t)n * CH + c) * 9 + tap];
                     const int dy = tap / 3, dx = tap % 3;
-                    const size_t off = ((((size_t)dx * nchunk + c / cpc) * 3 + (2 - dy)) * 64 + n) * 16;
+                    const size_t off = ((((size_t)dx * nchunk + c / cpc) * 3 + (2 - dy)) * CH + n) * 16;
                     if (fp8) {
                         dst[off + (c % cpc)] = f64_to_e4m3_rne((double)wv / sc);
                     } else {
@@ -599,14 +625,14 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
         }
     }
     {
-        // layer 1: B = [dx][chunk 2][3 dy][64 n][8 bf16]; per tap k = 0..5 holds
+        // layer 1: B = [dx][chunk 2][3 dy][CH n][8 bf16]; per tap k = 0..5 holds
         // (w_hi(c), w_lo(c), w_hi(c), w_hi(z), w_lo(z), w_hi(z)), k = 6..15 zero
         float w0[64 * 2 * 9];
-        e = cudaMemcpyAsync(w0, p->d_w + p->w_off[0], sizeof(w0), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(w0, p->d_w + p->w_off[0], sizeof(float) * CH * 2 * 9, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         uint16_t pk[3 * 2 * 3 * 64 * 8];
         memset(pk, 0, sizeof(pk));
-        for (int n = 0; n < 64; ++n)
+        for (int n = 0; n < CH; ++n)
             for (int tap = 0; tap < 9; ++tap)
                 for (int ci = 0; ci < 2; ++ci) {
                     const int dy = tap / 3, dx = tap % 3;
@@ -619,7 +645,7 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
                     const uint16_t trip[3] = {hi, lo, hi};
                     for (int j = 0; j < 3; ++j) {
                         const int k = 3 * ci + j;            // chunk 0 only
-                        pk[(((dx * 2 + 0) * 3 + (2 - dy)) * 64 + n) * 8 + k] = trip[j];
+                        pk[(((dx * 2 + 0) * 3 + (2 - dy)) * CH + n) * 8 + k] = trip[j];
                     }
                 }
         if (e == cudaSuccess && !p->d_w1pack) e = cudaMalloc(&p->d_w1pack, sizeof(pk));
@@ -634,7 +660,7 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
     // biases and (1-logit head) last-layer weights, host side, for the kernel parameters
     e = cudaMemcpyAsync(p->h_b, p->d_b, sizeof(float) * p->n_b, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && p->K == 1)
-        e = cudaMemcpyAsync(p->h_headw, p->d_w + p->w_off[p->L - 1], sizeof(float) * 64 * 9, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(p->h_headw, p->d_w + p->w_off[p->L - 1], sizeof(float) * CH * 9, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         free(hw);
@@ -644,9 +670,9 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
     }
     if (p->K == 1) {
         float tmp[9 * 64];
-        memcpy(tmp, p->h_headw, sizeof(tmp));                 // [c][tap] -> [tap][c]
-        for (int c = 0; c < 64; ++c)
-            for (int t = 0; t < 9; ++t) p->h_headw[t * 64 + c] = tmp[c * 9 + t];
+        memcpy(tmp, p->h_headw, sizeof(float) * 9 * CH);      // [c][tap] -> [tap][c]
+        for (int c = 0; c < CH; ++c)
+            for (int t = 0; t < 9; ++t) p->h_headw[t * CH + c] = tmp[c * 9 + t];
         p->head_bias = p->h_b[p->b_off[p->L - 1]];
     }
     if (fp8) memcpy(p->h_wscale, hs, sizeof(float) * 64 * n_inner);
@@ -745,6 +771,10 @@ void ht_preload_conv_tc()
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, true>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEADPART, true>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, false, 32>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, false, 32>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_RES, false, 32>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_RESHEAD, false, 32>);
     cudaFuncGetAttributes(&fa, k_first_input);
     cudaFuncGetAttributes(&fa, k_head_partials);
     ensure_all_attrs();
@@ -835,6 +865,8 @@ void tc_make_groups(const ht_policy *p, const ht_image *imgs, int n, uint8_t *ws
             D.prob = prob ? prob[g1] : nullptr;
             D.words = ht_bits_row_words(D.W, p->head);
             D.image = (uint32_t)g1;
+            if (p->arch == HT_ARCH_RESNET)   // 32-wide buffers use half of each 128 B/px slot
+                D.part = (float *)(D.act[1] + (size_t)D.H * D.W * 64);
             set_begins(D, G.units, G.hd, G.pre, ru);
             ++g1;
         }
@@ -881,8 +913,42 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
             }
             P.out_inv_scale = o8 ? 1.f / p->act_scale[1] : 1.f;
             P.out_fp8 = o8 ? 1 : 0;
-            const ht_status st = fp8 ? launch_conv<true, KIND_FIRST>(P, s) : launch_conv<false, KIND_FIRST>(P, s);
+            const ht_status st = p->arch == HT_ARCH_RESNET ? launch_conv<false, KIND_FIRST, false, 32>(P, s)
+                                 : fp8                      ? launch_conv<true, KIND_FIRST>(P, s)
+                                                            : launch_conv<false, KIND_FIRST>(P, s);
             if (st != HT_OK) return st;
+        }
+        if (p->arch == HT_ARCH_RESNET) {
+            // residual blocks: conv1 x (act[0]) -> t (act[1]); conv2 t -> y, shortcut x, in place in act[0]
+            const int nb = n_inner / 2;
+            for (int b = 0; b < nb; ++b) {
+                for (int half = 0; half < 2; ++half) {
+                    const int l = 1 + 2 * b + half;
+                    ConvParams P{};
+                    base(P, half);
+                    P.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (l - 1);
+                    for (int c = 0; c < 32; ++c) {
+                        P.bias[c] = p->h_b[p->b_off[l] + c];
+                        P.scale[c] = 1.f;
+                    }
+                    P.out_inv_scale = 1.f;
+                    ht_status st;
+                    if (half == 0) {
+                        st = launch_conv<false, KIND_HIDDEN, false, 32>(P, s);
+                    } else if (b + 1 < nb) {
+                        st = launch_conv<false, KIND_RES, false, 32>(P, s);
+                    } else {
+                        memcpy(P.head_w, p->h_headw, sizeof(float) * 9 * 32);
+                        st = launch_conv<false, KIND_RESHEAD, false, 32>(P, s);
+                    }
+                    if (st != HT_OK) return st;
+                }
+            }
+            ht_prof_start(HTK_HEAD_TC, s);
+            k_head_partials<<<G.hd, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, 0, p->head_bias, mode, seed, p->head, p->levels);
+            ht_prof_stop(s);
+            HT_LAUNCH_CHECK();
+            continue;
         }
         int cur = 0;
         for (int l = 1; l <= n_inner; ++l) {

@@ -90,6 +90,8 @@ struct ht_policy {
     int ch[HT_MAX_LAYERS + 1];
     int head, K, prec;
     int levels;                     // output levels (2 binary, 4 softmax head, 2..4 multitone head)
+    int arch;                       // HT_ARCH_PLAIN or HT_ARCH_RESNET
+    int width;                      // hidden width of the tensor-core forms (64; 32 for the residual policy)
     int device;
     int64_t n_w, n_b;
     int64_t w_off[HT_MAX_LAYERS + 1], b_off[HT_MAX_LAYERS + 1];

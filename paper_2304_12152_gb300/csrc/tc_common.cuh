@@ -183,15 +183,16 @@ __device__ __forceinline__ void split_bf16(float v, float &hi, float &lo)
     lo = bf16_round(v - hi);
 }
 
-// Stores 64 channel values of one pixel into the chunk-planar layout.
+// Stores CO channel values of one pixel into the chunk-planar layout.
 // out_fp8: e4m3(bf16(v) * inv_scale) (16 channels per chunk), else bf16 (8 per chunk).
+template <int CO = 64>
 __device__ __forceinline__ void store_pixel(const float *v, void *out, int out_fp8, float inv_scale, int H, int W,
                                             int y, int x)
 {
     if (out_fp8) {
         uint8_t *o = (uint8_t *)out;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < CO / 16; ++c) {
             uint4 q;
             q.x = pack_e4m3x4(bf16_round(v[16 * c + 0]) * inv_scale, bf16_round(v[16 * c + 1]) * inv_scale,
                               bf16_round(v[16 * c + 2]) * inv_scale, bf16_round(v[16 * c + 3]) * inv_scale);
@@ -206,7 +207,7 @@ __device__ __forceinline__ void store_pixel(const float *v, void *out, int out_f
     } else {
         uint8_t *o = (uint8_t *)out;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < CO / 8; ++c) {
             uint4 q;
             q.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
             q.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
@@ -229,6 +230,7 @@ struct ImgDesc {
                               // (written by a forward layer, applied by a data-gradient layer)
     uint8_t *save;            // nullable: last hidden layer with fused head partials also
                               // stores its activations here (training forward)
+    float *part;              // nullable: where the fused head partials go (else act[out])
     int cpitch, H, W, words;
     uint32_t image;           // Philox image index (position in the call)
     int xtiles;               // ceil(W / 128)

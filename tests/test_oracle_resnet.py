@@ -64,3 +64,16 @@ def test_resnet_parameter_count_near_the_paper():
     ws, bs = synth.resnet_policy(16, 32, seed=0)
     n = sum(w.size for w in ws) + sum(b.size for b in bs)
     assert n == 296833 and abs(n - 299e3) / 299e3 < 0.01
+
+
+def test_resnet_region_equals_the_whole_image_slice():
+    """A region is computed on the rectangle grown by the receptive field, with the noise
+    at image coordinates: it equals the slice of the whole-image result."""
+    ws, _ = synth.resnet_policy(2, 8, seed=13)
+    bs = synth.random_biases(synth.resnet_channels(2, 8), seed=14, scale=0.1)
+    c = synth.contone_image(40, 37, seed=15)
+    lg, _ = O.forward_resnet(c, ws, bs, 16, 2)
+    for reg in [(10, 9, 12, 15), (0, 0, 5, 37), (30, 20, 10, 17)]:
+        y0, x0, rh, rw = reg
+        lr, _ = O.forward_resnet(c, ws, bs, 16, 2, region=reg)
+        np.testing.assert_allclose(lr, lg[y0:y0 + rh, x0:x0 + rw], rtol=1e-12, atol=1e-14)
