@@ -101,6 +101,17 @@ class Clocks:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time (all ranks take part): max all-reduce of one float."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -288,12 +299,6 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     for _ in range(args.warmup):
         step()
@@ -311,7 +316,7 @@ def main():
         torch.cuda.synchronize()
     barrier()
     api.sync()
-    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_step = ms / args.steps
     value = world * px_per_step / (ms_step * 1e-3) / 1e6
 
@@ -347,7 +352,7 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
     e2e_val = world * px_per_step / (e2e_ms * 1e-3) / 1e6
 
     # ---------------- plain FP32 form of the same net ----------------
@@ -362,7 +367,7 @@ def main():
             pol32.halftone_into(cs, bits, mode, seed)
         f1.record(stream)
         torch.cuda.synchronize()
-        fms = max_over_ranks(f0.elapsed_time(f1)) / args.fp32_steps
+        fms = max_over_ranks(f0.elapsed_time(f1), world, dev) / args.fp32_steps
         fp32 = {"value": world * px_per_step / (fms * 1e-3) / 1e6, "unit": "Mpx/s", "ms_per_step": fms,
                 "steps": args.fp32_steps}
         del pol32
@@ -381,7 +386,17 @@ def main():
         # one launch = one C -> C layer over one image group: layers x pixels / launches
         flops_launch = 2 * 9 * cmid * cmid * px_per_step * prof_steps * n_mid / launches
         achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
-        if prec == N.HT_FP32:
+        if resnet:
+            # 32-wide layers: 18 432 flop/px against 128 B/px (conv1: read + write bf16) or
+            # 192 B/px (conv2: + the shortcut read), mean 160 B/px -> 115 flop/B, below the
+            # bf16 ridge (~250 flop/B): HBM-bound
+            bytes_launch = 160.0 * px_per_step * prof_steps * n_mid / launches
+            gbs = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+            hbm = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+            roof = {"bound": "hbm", "kernel": kname, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                    "traffic": None, "per_launch_ms": per_launch_ms, "tensor_tflops": achieved,
+                    "peak_source": f"{src} HBM copy bandwidth"}
+        elif prec == N.HT_FP32:
             roof = {"bound": "alu", "kernel": kname, "achieved": achieved,
                     "peak": fp32_alu_peak(clk.summary()), "unit": "TFLOP/s", "traffic": None,
                     "per_launch_ms": per_launch_ms,
@@ -504,11 +519,16 @@ def run_train(args):
     import torch
     from paper_2304_12152_gb300 import _native as N
     from paper_2304_12152_gb300 import api, synth
+    import torch.distributed as dist
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl")
     chs = synth.NET_WIDE
     ws, bs = synth.he_normal_policy(chs, 3)
-    crops = [torch.from_numpy(synth.contone_image(256, 256, seed=3, index=i)).cuda() for i in range(16)]
+    # data parallel: each rank its own 16 crops; gradients averaged with one all-reduce per step
+    crops = [torch.from_numpy(synth.contone_image(256, 256, seed=3, index=rank * 1000 + i)).cuda() for i in range(16)]
     levels = [0.1, 0.25, 0.5, 0.75]
     gw = torch.empty(sum(chs[i] * chs[i + 1] * 9 for i in range(len(chs) - 1)), device="cuda")
     gb = torch.empty(sum(chs[1:]), device="cuda")
@@ -521,7 +541,10 @@ def run_train(args):
         for _ in range(warmup):
             tr.forward(crops, levels, 1)
             tr.backward(gw, gb)
+            api.allreduce_grads([gw, gb])
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if profile:
             api.profile_begin()
@@ -530,18 +553,23 @@ def run_train(args):
             for k in range(steps):
                 losses = tr.forward(crops, levels, 1 + k)
                 tr.backward(gw, gb)
+                api.allreduce_grads([gw, gb])
             e1.record(stream)
             torch.cuda.synchronize()
         prof = api.profile_end() if profile else {}
-        return e0.elapsed_time(e1) / steps, losses, prof, clk.summary()
+        return max_over_ranks(e0.elapsed_time(e1), world, dev) / steps, losses, prof, clk.summary()
 
     ms, losses, prof, clocks = timed(N.HT_BF16, args.steps, args.warmup, True)
     fp32 = None
-    if args.fp32_steps > 0:
+    if args.fp32_steps > 0 and world == 1:
         ms32, _, _, _ = timed(N.HT_FP32, args.fp32_steps, 1, False)
         fp32 = {"value": ms32, "unit": "ms", "steps": args.fp32_steps}
+    if rank != 0:
+        dist.barrier()
+        dist.destroy_process_group()
+        return
     print(json.dumps({
-        "metric": "training step time", "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "metric": "training step time", "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "train: 16 crops 256x256 + 4 gray 256x256 {0.1,0.25,0.5,0.75}, S=4, "
@@ -549,7 +577,11 @@ def run_train(args):
         "losses": {"total": losses[0], "marl": losses[1], "las": losses[2], "mean_R": losses[3]},
         "fp32_plain": fp32,
         "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
-        "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clocks}), flush=True)
+        "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clocks,
+        "parallelism": f"data parallel x{world}, one gradient all-reduce per step"}), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

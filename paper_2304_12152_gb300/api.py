@@ -244,6 +244,27 @@ class Trainer:
         return grad_w, grad_b
 
 
+def allreduce_grads(grads: Sequence[torch.Tensor], group=None) -> Sequence[torch.Tensor]:
+    """Data-parallel training over the ranks of a process group (each rank steps on its own
+    crops): averages the gradient tensors in place with one all-reduce of their
+    concatenation -- the training path's only exchange (0.9 MB of FP32 for the 8-layer
+    64-wide policy).  No-op without an initialised process group of size > 1."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return grads
+    world = dist.get_world_size(group)
+    if world == 1:
+        return grads
+    flat = torch.cat([g.reshape(-1) for g in grads])
+    dist.all_reduce(flat, group=group)
+    flat.div_(world)
+    off = 0
+    for g in grads:
+        g.copy_(flat[off:off + g.numel()].view_as(g))
+        off += g.numel()
+    return grads
+
+
 class HalftonePolicyFn(torch.autograd.Function):
     """torch.autograd.Function driving one training iteration of the library.
 

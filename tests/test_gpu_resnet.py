@@ -25,8 +25,9 @@ def test_resnet_bf16_matches_bf16_oracle(shape, mode):
     differs by about as much as BF16 rounding moves p at all: FP32-vs-FP64 accumulation
     flips early bf16 roundings, and through the undamped residual stream the two sides
     become independent BF16 realisations.  Bound, from the oracle alone: the p99.9 and max
-    of |p_gpu - p_q1| within 1.5x those of |p_q1 - p_fp64|.  Actions equal on all but
-    <= 2e-3 of the decided pixels."""
+    of |p_gpu - p_q1| within 1.5x those of |p_q1 - p_fp64|.  Actions: a decided pixel can
+    only flip if the GPU's p moves across u, so the mismatches are bounded by the decided
+    pixels whose margin |p - u| lies inside that band (1.5x the p99.9 BF16 effect)."""
     H, W = shape
     pol, ws, bs = _policy(41)
     img = synth.contone_image(H, W, seed=42)
@@ -44,7 +45,9 @@ def test_resnet_bf16_matches_bf16_oracle(shape, mode):
     ref = (u < p) if mode == N.HT_MODE_BERNOULLI else (p > 0.5)
     dec = np.abs(p - u) > 1e-4
     mism = int(((lev == 1) != ref)[dec].sum())
-    assert mism <= max(2, int(2e-3 * dec.sum())), (mism, int(dec.sum()))
+    band = int((dec & (np.abs(p - u) < 1.5 * np.quantile(eff, 0.999))).sum())
+    print("resnet mismatches %d of %d decided, %d inside the BF16 band" % (mism, int(dec.sum()), band))
+    assert mism <= max(2, band), (mism, band)
 
 
 def test_resnet_batch_and_plan_match_single_calls():
