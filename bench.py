@@ -413,6 +413,16 @@ def main():
                     "per_launch_ms": per_launch_ms, "peak_source": psrc}
     tot_ms = max(1e-9, sum(x[1] for x in prof.values()))
     kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / tot_ms} for k, v in prof.items()}
+    # HBM-bound passes around the conv stack: algorithmic bytes per pixel, achieved GB/s
+    hbm_bytes = {"k_first_input": 4.0 + 16.0}            # contone read, split c / z write
+    if head != N.HT_HEAD_SOFTMAX:
+        hbm_bytes["k_head_tc"] = 36.0 + 0.25             # 9 partials read, packed levels written
+    hbm_peak = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    hbm = {}
+    for k, bpp in hbm_bytes.items():
+        if k in prof and prof[k][1] > 0:
+            gbs = bpp * px_per_step * prof_steps / (prof[k][1] * 1e-3) / 1e9
+            hbm[k] = {"bytes_per_px": bpp, "achieved_gbs": gbs, "frac": gbs / hbm_peak}
     # launches inside the timed region: the replayed graph holds the same launches as one direct call
     gpu_launches = sum(v[0] for v in prof.values()) * args.steps // prof_steps
 
@@ -466,7 +476,7 @@ def main():
             "timing": ("value and e2e: CUDA-graph replay of the call (ht_plan); kernels and roofline: "
                        f"{prof_steps} direct calls, each launch bracketed by CUDA events") if plan is not None
                       else "direct calls",
-            "autotune": tune,
+            "autotune": tune, "hbm_kernels": hbm,
         }
         if args.workload == "uneven":
             line["config"]["shapes"] = shapes
@@ -568,6 +578,16 @@ def run_train(args):
         dist.barrier()
         dist.destroy_process_group()
         return
+    # reward window sums and toggle deltas: algorithmic bytes per crop-sample pixel
+    # (contone 4 B + 1/8 B bits; toggles: + 7 moment maps written and read, dR written)
+    px_samples = 16 * 4 * 256 * 256 * args.steps
+    hbm_peak = peaks()[0].get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    filt = {}
+    for k, bpp in (("k_reward", 4.125), ("k_toggle_delta", 4.125 + 28.0 + 28.0 + 4.125 + 4.0)):
+        if k in prof and prof[k][1] > 0:
+            gbs = bpp * px_samples / (prof[k][1] * 1e-3) / 1e9
+            filt[k] = {"bytes_per_px": bpp, "achieved_gbs": gbs, "frac": gbs / hbm_peak,
+                       "note": "ALU-bound stencils (5-6 window sums; toggles ~3.6 kflop/px)"}
     print(json.dumps({
         "metric": "training step time", "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -578,7 +598,7 @@ def run_train(args):
         "fp32_plain": fp32,
         "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
         "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clocks,
-        "parallelism": f"data parallel x{world}, one gradient all-reduce per step"}), flush=True)
+        "parallelism": f"data parallel x{world}, one gradient all-reduce per step", "hbm_kernels": filt}), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

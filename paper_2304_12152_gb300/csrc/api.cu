@@ -48,7 +48,7 @@ std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_ev_pool;
 const char *const g_kernel_names[HTK_COUNT] = {"k_first_tc",   "k_conv_tc_bf16", "k_conv_tc_fp8", "k_head_tc",
                                                "k_conv3x3_fp32", "k_head_fp32",  "k_reward",      "k_toggle_delta",
-                                               "k_spectrum",   "k_train"};
+                                               "k_spectrum",   "k_train", "k_first_input"};
 
 cudaEvent_t pool_event()
 {

@@ -812,7 +812,7 @@ ht_status ht_tc_conv(const ht_tc_layer &a, cudaStream_t s)
 
 ht_status ht_tc_first_input(const void *table, int n_imgs, int n_groups, uint64_t seed, cudaStream_t s)
 {
-    ht_prof_start(HTK_FIRST_TC, s);
+    ht_prof_start(HTK_FIRST_INPUT, s);
     k_first_input<<<(n_groups + 255) / 256, 256, 0, s>>>((const ImgDesc *)table, n_imgs, seed);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
@@ -887,7 +887,7 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
     for (const TcGroup &G : groups) {
         const ImgDesc *dt = d_table + G.g0;
         const int ng = G.ng;
-        ht_prof_start(HTK_FIRST_TC, s);
+        ht_prof_start(HTK_FIRST_INPUT, s);
         k_first_input<<<(G.pre + 255) / 256, 256, 0, s>>>(dt, ng, seed);
         ht_prof_stop(s);
         HT_LAUNCH_CHECK();

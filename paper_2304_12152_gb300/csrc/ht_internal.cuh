@@ -50,7 +50,7 @@ int *ht_device_error_flag();
 
 // Kernel timing hooks (no-ops unless ht_profile_begin was called).
 enum ht_kernel_id { HTK_FIRST_TC = 0, HTK_CONV_TC_BF16, HTK_CONV_TC_FP8, HTK_HEAD_TC, HTK_CONV_FP32, HTK_HEAD_FP32,
-                    HTK_REWARD, HTK_TOGGLE, HTK_SPECTRUM, HTK_TRAIN, HTK_COUNT };
+                    HTK_REWARD, HTK_TOGGLE, HTK_SPECTRUM, HTK_TRAIN, HTK_FIRST_INPUT, HTK_COUNT };
 void ht_prof_start(int kid, cudaStream_t s);
 void ht_prof_stop(cudaStream_t s);
 
