@@ -271,6 +271,10 @@ typedef struct {
     ht_reward_opts reward;
     int estimator;        /* HT_EST_LE: local expectation (Eq. le, the paper's choice);
                              HT_EST_COMA: counterfactual baseline (Eq. coma) */
+    int ckpt_stride;      /* BF16 form, activation recomputation for large crops: 0 or 1 keeps
+                             every hidden activation for the backward; k >= 2 keeps every k-th
+                             (and the head's input) and recomputes the others, segment by
+                             segment, during the backward (results unchanged) */
 } ht_train_desc;
 
 enum { HT_EST_LE = 0, HT_EST_COMA = 1 };

@@ -59,7 +59,8 @@ HT_TUNE_CANDIDATES = 6
 class TrainDesc(C.Structure):
     _fields_ = [("max_crops", C.c_int), ("crop_h", C.c_int), ("crop_w", C.c_int), ("n_gray", C.c_int),
                 ("gray_n", C.c_int), ("n_samples", C.c_int), ("las_mode", C.c_int), ("n_rad", C.c_int),
-                ("n_ang", C.c_int), ("w_a", C.c_float), ("reward", RewardOpts), ("estimator", C.c_int)]
+                ("n_ang", C.c_int), ("w_a", C.c_float), ("reward", RewardOpts), ("estimator", C.c_int),
+                ("ckpt_stride", C.c_int)]
 
 
 _lock = threading.Lock()

@@ -202,9 +202,11 @@ class Trainer:
 
     def __init__(self, policy: Policy, crop_hw: Tuple[int, int], max_crops: int, n_samples: int = 4,
                  n_gray: int = 0, gray_n: int = 256, las_mode: int = 1, n_rad: int = 32, n_ang: int = 16,
-                 w_a: float = 0.002, reward: Optional[N.RewardOpts] = None, estimator: int = N.HT_EST_LE):
+                 w_a: float = 0.002, reward: Optional[N.RewardOpts] = None, estimator: int = N.HT_EST_LE,
+                 ckpt_stride: int = 0):
         d = N.TrainDesc()
         d.estimator = estimator
+        d.ckpt_stride = ckpt_stride
         d.max_crops, (d.crop_h, d.crop_w) = max_crops, crop_hw
         d.n_gray, d.gray_n, d.n_samples = n_gray, gray_n, n_samples
         d.las_mode, d.n_rad, d.n_ang, d.w_a = las_mode, n_rad, n_ang, w_a

@@ -202,9 +202,10 @@ struct ht_train_tc_ws {
     void *scratch = nullptr;          // reduction partials + packed data-gradient weights
     size_t scratch_bytes = 0, wt_off = 0;
     int units = 0, hd = 0;
+    int ckpt = 1;                     // activation checkpoint stride (1: keep every hidden activation)
 };
 bool ht_train_tc_supported(const ht_policy *p);
-size_t ht_train_tc_image_bytes(const ht_policy *p, size_t px);
+size_t ht_train_tc_image_bytes(const ht_policy *p, int ckpt, size_t px);
 size_t ht_train_tc_table_bytes(const ht_policy *p, int n_img);
 void ht_train_tc_scratch_layout(const ht_policy *p, int n_tiles, size_t *wt_off, size_t *total);
 ht_status ht_train_tc_forward(ht_policy *p, ht_train_tc_ws &w, const ht_image *imgs, int nimg, uint64_t seed,

@@ -276,6 +276,7 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
                      "gray_n must be a power of two in [8, 1024]");
     HT_CHECK_ARG(d->las_mode == 0 || d->las_mode == 1, "las_mode must be 0 or 1");
     HT_CHECK_ARG(d->estimator == HT_EST_LE || d->estimator == HT_EST_COMA, "unknown estimator %d", d->estimator);
+    HT_CHECK_ARG(d->ckpt_stride >= 0 && d->ckpt_stride <= 16, "ckpt_stride must be in [0, 16]");
     if (d->las_mode == 1)
         HT_CHECK_ARG(d->n_rad >= 1 && d->n_rad <= 256 && d->n_ang >= 2 && d->n_ang <= 64, "bad bin counts");
     HT_CHECK_ARG(d->reward.radius >= 1 && d->reward.radius <= 7, "reward radius must be in [1, 7]");
@@ -332,10 +333,11 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
     t->tc = tc;
     if (t->tc) {
         ht_train_tc_ws &w = t->tcw;
+        w.ckpt = d->ckpt_stride > 1 ? d->ckpt_stride : 1;
         size_t arena = 0;
         for (int k = 0; k < B + G; ++k) {
             w.slot_off.push_back(arena);
-            arena += ht_train_tc_image_bytes(p, k < B ? t->crop_px : t->gray_px);
+            arena += ht_train_tc_image_bytes(p, w.ckpt, k < B ? t->crop_px : t->gray_px);
         }
         const int wg = ht_bits_row_words(d->gray_n, p->head);
         int tiles = B * ((d->crop_w + 31) / 32) * ((d->crop_h + 7) / 8) + G * ((d->gray_n + 31) / 32) * ((d->gray_n + 7) / 8);

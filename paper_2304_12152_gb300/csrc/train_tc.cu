@@ -615,18 +615,41 @@ bool ht_train_tc_supported(const ht_policy *p)
 }
 
 // Per image of a step, in the arena (px = h * w), each region 256-byte aligned:
-// hidden activations [L-1][px][128 B], ReLU masks [L-1][px] x 8 B, layer-1 split
+// activation buffers [nbuf][px][128 B], ReLU masks [L-1][px] x 8 B, layer-1 split
 // input [px][16 B], head partials [9][px] x 4 B, gradient ping-pong 2 x [px][128 B].
+//
+// Activation recomputation (checkpoint stride k > 1): only the hidden activations
+// a_l with l % k == 0, and a_{L-2} (the head's input), keep a buffer for the
+// backward; the others use k - 1 scratch buffers (a_l in scratch l % k - 1), which
+// the forward overwrites segment by segment and the backward refills by running the
+// segment's forward layers again from its checkpoint (the kernels are
+// deterministic, so the refilled activations and masks are the forward's).
 namespace {
 inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 struct ImgRegions {
     size_t acts, masks, split, part9, g0, g1, total;
 };
-ImgRegions img_regions(int nh, size_t px)
+inline bool is_ckpt(int l, int k, int L) { return k <= 1 || l % k == 0 || l == L - 2; }
+inline int n_ckpt(int k, int L)
+{
+    int n = 0;
+    for (int l = 0; l <= L - 2; ++l) n += is_ckpt(l, k, L) ? 1 : 0;
+    return n;
+}
+inline int n_act_bufs(int k, int L) { return n_ckpt(k, L) + (k > 1 ? k - 1 : 0); }
+// buffer of hidden activation a_l
+inline int act_buf(int l, int k, int L)
+{
+    if (!is_ckpt(l, k, L)) return n_ckpt(k, L) + (l % k) - 1;
+    int i = 0;
+    for (int j = 0; j < l; ++j) i += is_ckpt(j, k, L) ? 1 : 0;
+    return i;
+}
+ImgRegions img_regions(int nh, int nbuf, size_t px)
 {
     ImgRegions r;
     r.acts = 0;
-    r.masks = r.acts + al256((size_t)nh * px * 128);
+    r.masks = r.acts + al256((size_t)nbuf * px * 128);
     r.split = r.masks + al256((size_t)nh * px * 8);
     r.part9 = r.split + al256(px * 16);
     r.g0 = r.part9 + al256(px * 36);
@@ -636,7 +659,10 @@ ImgRegions img_regions(int nh, size_t px)
 }
 }  // namespace
 
-size_t ht_train_tc_image_bytes(const ht_policy *p, size_t px) { return img_regions(p->L - 1, px).total; }
+size_t ht_train_tc_image_bytes(const ht_policy *p, int ckpt, size_t px)
+{
+    return img_regions(p->L - 1, n_act_bufs(ckpt, p->L), px).total;
+}
 
 size_t ht_train_tc_table_bytes(const ht_policy *p, int n_img)
 {
@@ -685,7 +711,7 @@ void build_tables(const ht_policy *p, const ht_train_tc_ws &w, const ht_image *i
     all.assign((size_t)n_tables(L) * nimg, ImgDesc{});
     for (int i = 0; i < nimg; ++i) {
         const size_t px = (size_t)imgs[i].h * imgs[i].w;
-        const ImgRegions R = img_regions(nh, px);
+        const ImgRegions R = img_regions(nh, n_act_bufs(w.ckpt, L), px);
         uint8_t *b = (uint8_t *)w.arena + w.img_off[i];
         uint8_t *acts = b + R.acts;
         uint2 *masks = (uint2 *)(b + R.masks);
@@ -693,7 +719,7 @@ void build_tables(const ht_policy *p, const ht_train_tc_ws &w, const ht_image *i
         float *part9 = (float *)(b + R.part9);
         uint8_t *g0 = b + R.g0;
         uint8_t *g1 = b + R.g1;
-        auto act = [&](int l) { return acts + (size_t)l * px * 128; };
+        auto act = [&](int l) { return acts + (size_t)act_buf(l, w.ckpt, L) * px * 128; };
         auto msk = [&](int l) { return masks + (size_t)l * px; };
         auto gbuf = [&](int l) { return (l & 1) ? g1 : g0; };   // g_l: gradient at layer l's pre-activation
         auto T = [&](int t) -> ImgDesc & { return all[(size_t)t * nimg + i]; };
@@ -821,7 +847,27 @@ ht_status ht_train_tc_backward(ht_policy *p, ht_train_tc_ws &w, int nimg, uint64
         attr = true;
     }
     const int grid = w.units < num_sms() ? w.units : num_sms();
+    int seg_ready = -1;                                     // checkpoint below the segment held in scratch
     for (int l = L - 2; l >= 1; --l) {
+        if (!is_ckpt(l - 1, w.ckpt, L)) {
+            const int c = (l - 1) - (l - 1) % w.ckpt;
+            if (seg_ready != c) {                           // refill a_{c+1} .. a_{l-1} from checkpoint a_c
+                for (int j = c + 1; j <= l - 1; ++j) {
+                    ht_tc_layer a{};
+                    a.table = tab(T_FWD(j));
+                    a.n_imgs = nimg;
+                    a.n_units = w.units;
+                    a.in_buf = 0;
+                    a.kind = 0;
+                    a.wpack = (const uint8_t *)p->d_wpack + p->wpack_layer_bytes * (j - 1);
+                    a.bias = p->h_b + p->b_off[j];
+                    a.seed = seed;
+                    const ht_status st = ht_tc_conv(a, s);
+                    if (st != HT_OK) return st;
+                }
+                seg_ready = c;
+            }
+        }
         WgParams P;
         P.imgs = tab(T_WG(L, l));
         P.n_imgs = nimg;

@@ -274,6 +274,28 @@ def test_bf16_train_step_matches_bf16_oracle():
         assert ew <= 2e-2 and eb <= 2e-2, errs
 
 
+@pytest.mark.parametrize("stride", [2, 3])
+def test_bf16_activation_recomputation_is_exact(stride):
+    """Checkpointed training (every stride-th hidden activation kept, the rest recomputed
+    in the backward) gives bit-identical losses and gradients."""
+    chs = (2, 64, 64, 64, 64, 64, 1)
+    ws, _ = synth.he_normal_policy(chs, 61)
+    bs = synth.random_biases(chs, 62, scale=0.1)
+    crops = [torch.from_numpy(synth.contone_image(40, 150, seed=63, index=i)).cuda() for i in range(2)]
+    pol = api.Policy(chs, ws, bs, precision=N.HT_BF16)
+    out = []
+    for k in (1, stride):
+        tr = api.Trainer(pol, (40, 150), max_crops=2, n_samples=2, n_gray=1, gray_n=32, las_mode=1, n_rad=4, n_ang=4,
+                         ckpt_stride=k)
+        losses = tr.forward(crops, [0.4], 5)
+        gw, gb = tr.backward()
+        torch.cuda.synchronize()
+        out.append((losses, gw.clone(), gb.clone()))
+        tr.close()
+    assert out[0][0] == out[1][0]
+    assert torch.equal(out[0][1], out[1][1]) and torch.equal(out[0][2], out[1][2])
+
+
 def test_training_rejects_fp8_policies():
     """Training runs in the FP32 form or the BF16 tensor-core form; an FP8 policy is refused."""
     ws, bs = synth.he_normal_policy(WIDE4, 1)
