@@ -431,13 +431,15 @@ int or_reward(const float *c, int cpitch, const uint8_t *hb, int hpitch, int h, 
     gauss2d(o->sigma_ssim, r, gw);
     or_img im = {c, cpitch, hb, hpitch, -1, -1, 0.0, hscale};
     int vh = h - 2 * r, vw = w - 2 * r;
-    double mse = 0, ssim = 0, cssim = 0;
-#pragma omp parallel for reduction(+:mse,ssim,cssim) schedule(static)
+    /* per-row sums, then a serial sum over rows: the result does not depend on the
+     * number of threads or on how OpenMP combines partial sums */
+    double *rows = (double *)calloc((size_t)3 * (vh > 0 ? vh : 1), sizeof(double));
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < vh; ++y)
         for (int x = 0; x < vw; ++x) {
             double e2, s, cs;
             term_at(&im, y + r, x + r, o, ghvs, gw, &e2, &s, &cs);
-            mse += e2; ssim += s; cssim += cs;
+            rows[3 * y] += e2; rows[3 * y + 1] += s; rows[3 * y + 2] += cs;
             size_t k = (size_t)y * vw + x;
             if (ssim_map) ssim_map[k] = s;
             if (e_map || sig_map) {
@@ -458,6 +460,11 @@ int or_reward(const float *c, int cpitch, const uint8_t *hb, int hpitch, int h, 
                 if (sig_map) sig_map[k] = o->k_contrast * sqrt(vc);
             }
         }
+    double mse = 0, ssim = 0, cssim = 0;
+    for (int y = 0; y < vh; ++y) {
+        mse += rows[3 * y]; ssim += rows[3 * y + 1]; cssim += rows[3 * y + 2];
+    }
+    free(rows);
     double M = (double)vh * vw;
     out[0] = mse / M;
     out[1] = ssim / M;
