@@ -227,7 +227,8 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--ref-side", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--schedule", default="", help="ROWS,ORDER: set the conv schedule instead of autotuning")
+    ap.add_argument("--schedule", default="",
+                    help="ROWS,ORDER[,PAIR]: set the conv schedule instead of autotuning (PAIR 1 = CTA-pair 64->64 layers)")
     ap.add_argument("--ckpt", type=int, default=0, help="train: activation checkpoint stride (recomputation)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -280,14 +281,16 @@ def main():
     plan = None
     if prec != N.HT_FP32:
         if args.schedule:
-            ru, order = (int(x) for x in args.schedule.split(","))
-            pol.set_schedule(ru, order)
-            tune = {"choice": {"rows_per_unit": ru, "unit_order": order}, "candidates": None}
+            sched = [int(x) for x in args.schedule.split(",")]
+            ru, order, pair = sched[0], sched[1], (sched[2] if len(sched) > 2 else 0)
+            pol.set_schedule(ru, order, pair)
+            tune = {"choice": {"rows_per_unit": ru, "unit_order": order, "cta_pair": pair}, "candidates": None}
         else:
             res = pol.autotune(cs, bits, mode, seed, reps=2)
-            best = min(res, key=lambda r: r[2])
-            tune = {"choice": {"rows_per_unit": best[0], "unit_order": best[1]},
-                    "candidates": [{"rows_per_unit": r, "unit_order": o, "ms": ms} for r, o, ms in res]}
+            best = min(res, key=lambda r: r[3])
+            tune = {"choice": {"rows_per_unit": best[0], "unit_order": best[1], "cta_pair": best[2]},
+                    "candidates": [{"rows_per_unit": r, "unit_order": o, "cta_pair": pr, "ms": ms}
+                                   for r, o, pr, ms in res]}
         plan = api.Plan(pol, cs, bits, mode, seed)
 
     def step():

@@ -235,22 +235,28 @@ ht_status ht_plan_destroy(ht_plan *plan);
 /* Schedule autotuner (tensor-core forms).  Runs the caller's ht_halftone call */
 /* (outputs are written) under every candidate conv schedule -- rows per work */
 /* unit (TMEM accumulator blocks: 8, 6, 4) x unit order (row bands first,      */
-/* column tiles first) -- reps times each after a warm-up, timed with CUDA    */
-/* events on `stream`, and keeps the fastest in the policy (used by later     */
-/* ht_halftone calls and plans).  results: nullable host array of up to       */
-/* max_results entries, *n_results written.  Outputs are bit-identical under  */
-/* every schedule (same per-pixel accumulation order).                         */
+/* column tiles first) x CTA form of the 64 -> 64 layers (one CTA per 128-    */
+/* pixel tile, M = 128 MMAs; or a CTA pair per 256-pixel tile, M = 256 MMAs   */
+/* of tcgen05 cta_group::2, policies of the 64-wide plain architecture only)  */
+/* -- reps times each after a warm-up, timed with CUDA events on `stream`,    */
+/* and keeps the fastest in the policy (used by later ht_halftone calls and   */
+/* plans).  results: nullable host array of up to max_results entries,        */
+/* *n_results written (12 candidates, or 6 where the pair form does not       */
+/* apply).  Outputs are bit-identical under every schedule (same per-pixel     */
+/* accumulation order).                                                        */
 /* ------------------------------------------------------------------------ */
-#define HT_TUNE_CANDIDATES 6
+#define HT_TUNE_CANDIDATES 12
 typedef struct {
     int rows_per_unit;
     int unit_order;
+    int cta_pair;             /* 1: 64 -> 64 layers as CTA pairs */
     float ms;                 /* mean time of one call */
 } ht_tune_result;
 
-/* Sets the conv schedule directly (rows_per_unit in [3, 8], unit_order 0 or 1),
- * e.g. one found by an earlier ht_policy_autotune run. */
-ht_status ht_policy_set_schedule(ht_policy *p, int rows_per_unit, int unit_order);
+/* Sets the conv schedule directly (rows_per_unit in [3, 8], unit_order 0 or 1,
+ * cta_pair 0 or 1; the pair form is used only where it applies), e.g. one found
+ * by an earlier ht_policy_autotune run. */
+ht_status ht_policy_set_schedule(ht_policy *p, int rows_per_unit, int unit_order, int cta_pair);
 
 ht_status ht_policy_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,
                              uint32_t *const *out_bits, float *const *out_prob, int reps, ht_tune_result *results,

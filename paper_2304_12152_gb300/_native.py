@@ -50,10 +50,10 @@ class KernelStat(C.Structure):
 
 
 class TuneResult(C.Structure):
-    _fields_ = [("rows_per_unit", C.c_int), ("unit_order", C.c_int), ("ms", C.c_float)]
+    _fields_ = [("rows_per_unit", C.c_int), ("unit_order", C.c_int), ("cta_pair", C.c_int), ("ms", C.c_float)]
 
 
-HT_TUNE_CANDIDATES = 6
+HT_TUNE_CANDIDATES = 12
 
 
 class TrainDesc(C.Structure):
@@ -108,7 +108,7 @@ def load(build_if_missing: bool = True):
         L.ht_plan_create.argtypes = [vp, P(Image), i, i, u64, vp, vp, P(vp)]
         L.ht_plan_launch.argtypes = [vp, vp]
         L.ht_plan_destroy.argtypes = [vp]
-        L.ht_policy_set_schedule.argtypes = [vp, i, i]
+        L.ht_policy_set_schedule.argtypes = [vp, i, i, i]
         L.ht_policy_autotune.argtypes = [vp, P(Image), i, i, u64, vp, vp, i, P(TuneResult), i, P(i), vp]
         L.ht_train_create.argtypes = [vp, P(TrainDesc), P(vp)]
         L.ht_train_destroy.argtypes = [vp]

@@ -111,19 +111,19 @@ class Policy:
         check(N.load().ht_halftone(self._h, imgs, len(contones), mode, seed, _ptrs(bits),
                                    _ptrs(probs) if probs is not None else None, _stream(stream)))
 
-    def set_schedule(self, rows_per_unit: int, unit_order: int) -> None:
-        check(N.load().ht_policy_set_schedule(self._h, rows_per_unit, unit_order))
+    def set_schedule(self, rows_per_unit: int, unit_order: int, cta_pair: int = 0) -> None:
+        check(N.load().ht_policy_set_schedule(self._h, rows_per_unit, unit_order, cta_pair))
 
     def autotune(self, contones: Sequence[torch.Tensor], bits: Sequence[torch.Tensor], mode: int, seed: int,
                  probs: Optional[Sequence[Optional[torch.Tensor]]] = None, reps: int = 3, stream=None):
         """ht_policy_autotune: times every conv schedule on this call, keeps the fastest.
-        Returns [(rows_per_unit, unit_order, ms)] in candidate order."""
+        Returns [(rows_per_unit, unit_order, cta_pair, ms)] in candidate order."""
         res = (N.TuneResult * N.HT_TUNE_CANDIDATES)()
         n = C.c_int(0)
         check(N.load().ht_policy_autotune(self._h, _images(contones), len(contones), mode, seed, _ptrs(bits),
                                           _ptrs(probs) if probs is not None else None, reps, res,
                                           N.HT_TUNE_CANDIDATES, C.byref(n), _stream(stream)))
-        return [(res[k].rows_per_unit, res[k].unit_order, float(res[k].ms)) for k in range(n.value)]
+        return [(res[k].rows_per_unit, res[k].unit_order, res[k].cta_pair, float(res[k].ms)) for k in range(n.value)]
 
     def halftone(self, contones: Sequence[torch.Tensor], mode: int = N.HT_MODE_THRESHOLD, seed: int = 0,
                  want_prob: bool = False, stream=None):

@@ -258,6 +258,7 @@ ht_status ht_destroy_policy(ht_policy *p)
     cudaFree(p->d_w);
     cudaFree(p->d_b);
     cudaFree(p->d_wpack);
+    cudaFree(p->d_wpack2);
     cudaFree(p->d_wscale);
     cudaFree(p->d_w1pack);
     cudaFree(p->d_wpack4);
@@ -458,13 +459,15 @@ ht_status ht_plan_launch(ht_plan *plan, void *stream)
 
 ht_status ht_plan_destroy(ht_plan *plan) { return ht_plan_destroy_impl(plan); }
 
-ht_status ht_policy_set_schedule(ht_policy *p, int rows_per_unit, int unit_order)
+ht_status ht_policy_set_schedule(ht_policy *p, int rows_per_unit, int unit_order, int cta_pair)
 {
     HT_CHECK_ARG(p != nullptr, "null policy");
     HT_CHECK_ARG(rows_per_unit >= 3 && rows_per_unit <= 8, "rows_per_unit must be in [3, 8]");
     HT_CHECK_ARG(unit_order == 0 || unit_order == 1, "unit_order must be 0 or 1");
+    HT_CHECK_ARG(cta_pair == 0 || cta_pair == 1, "cta_pair must be 0 or 1");
     p->tune_ru = rows_per_unit;
     p->tune_order = unit_order;
+    p->tune_pair = cta_pair;
     return HT_OK;
 }
 

@@ -423,6 +423,348 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 }
 
 // ---------------------------------------------------------------------------
+// CTA-pair form of the 64 -> 64 layer (hidden, and the last hidden layer with
+// the fused head partials): tcgen05 cta_group::2, M = 256.
+//
+// A cluster of two CTAs works on one unit = RU output rows x one 256-pixel
+// column tile; CTA r stages and stores pixels [x0 + 128 r, x0 + 128 r + 128).
+// The first CTA's MMA warp issues every MMA of the unit: A = both CTAs' staged
+// rows (each 128 x K at the same shared offset), B = the dy-stacked weights
+// split by N between the CTAs, D = each CTA's own TMEM blocks.  A single-CTA
+// MMA (M = 128) re-fetches its 128-row A tile from shared memory for every
+// instruction; with a pair each SM still supplies 128 rows of A but only half
+// of B, and the instruction stream runs at the tensor pipe's own rate.
+//
+// Weights (this CTA's half): per (dx, K step) one group of PV_ROWS rows x 32 B
+// holding, for each N range an MMA of a unit can cover, the CTA's n/2 rows
+// (variant v: stacked columns [start, start + n) of [dy=2 | dy=1 | dy=0]).
+//
+// Hand-offs between the CTAs: the second CTA's warp 1 relays "my row landed"
+// and "my weights landed" to the first CTA (remote mbarrier arrive on pfull /
+// pwbar); the second CTA's epilogue warps release accumulator blocks on the
+// first CTA's bfree; the MMA warp's commits arrive on both CTAs' barriers
+// (multicast).  The producer passes (k, nrows) of every staged row, and an end
+// marker, through s_meta, so the MMA warp needs no image-table lookups.
+// ---------------------------------------------------------------------------
+constexpr int PV_ROWS = 320;                    // 96 + 32 + 64 + 64 + 32 + 32
+constexpr int PV_GROUP_BYTES = PV_ROWS * 32;    // two 16-byte K chunks per row
+__host__ __device__ constexpr int pv_start(int v) { return v == 1 ? 128 : (v == 2 || v == 5) ? 64 : 0; }
+__host__ __device__ constexpr int pv_n(int v) { return v == 0 ? 192 : (v == 2 || v == 3) ? 128 : 64; }
+__host__ __device__ constexpr int pv_row(int v)
+{
+    return v == 0 ? 0 : v == 1 ? 96 : v == 2 ? 128 : v == 3 ? 192 : v == 4 ? 256 : 288;
+}
+// variant of an MMA that starts at dy block sb (0 = dy 2) and covers n columns
+__device__ __forceinline__ int pv_of(int sb, int n)
+{
+    return n == 192 ? 0 : n == 128 ? (sb == 1 ? 2 : 3) : (sb == 2 ? 1 : sb == 0 ? 4 : 5);
+}
+
+template <bool FP8>
+struct Cfg2 {
+    static constexpr int NCHUNK = FP8 ? 4 : 8;                  // 16-byte chunks per staged pixel
+    static constexpr int KSTEPS = NCHUNK / 2;                   // MMAs per dx (K = 16 bf16 / 32 e4m3)
+    static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;
+    static constexpr int W_BYTES = 3 * KSTEPS * PV_GROUP_BYTES; // this CTA's weight image
+    static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 4096 /*barriers, meta*/;
+};
+
+template <bool FP8, int KIND>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_tc2(const ConvParams P)
+{
+    using C = Cfg2<FP8>;
+    constexpr bool HEADP = KIND == KIND_HEADPART;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *s_w = smem;
+    uint8_t *s_rows = smem + C::W_BYTES;
+    uint64_t *bars = (uint64_t *)(s_rows + NSLOT * C::SLOT_BYTES);
+    uint64_t *full = bars, *pfull = bars + NSLOT, *empty = bars + 2 * NSLOT, *wbar = bars + 3 * NSLOT,
+             *pwbar = wbar + 1, *bfull = wbar + 2, *bfree = bfull + RU, *drain = bfree + RU;
+    int2 *s_meta = (int2 *)(drain + 1);                         // (k, nrows) of the row in each slot
+    uint32_t *s_tmem = (uint32_t *)(s_meta + NSLOT);
+    volatile int *s_abort = (volatile int *)(s_tmem + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int pair_id = (int)blockIdx.x >> 1, n_pairs = (int)gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSLOT; ++i) {
+            mbar_init(smem_u32(&full[i]), 1);
+            mbar_init(smem_u32(&pfull[i]), 1);
+            mbar_init(smem_u32(&empty[i]), 1);
+        }
+        mbar_init(smem_u32(wbar), 1);
+        mbar_init(smem_u32(pwbar), 1);
+        for (int i = 0; i < RU; ++i) {
+            mbar_init(smem_u32(&bfull[i]), 1);
+            mbar_init(smem_u32(&bfree[i]), 8);                 // 4 epilogue warps in each CTA
+        }
+        mbar_init(smem_u32(drain), 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    cluster_sync_all();          // both CTAs' barriers exist before any remote arrive or multicast commit
+    if (warp == 0) tmem_alloc_pair(smem_u32(s_tmem), TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem_base = *s_tmem;
+    const uint32_t peer_abort = mapa_rank(smem_u32((const void *)s_abort), rank ^ 1u);
+
+    if (warp == 0) {
+        // ------------------------- producer (both CTAs) -------------------------
+        int last_issued[NSLOT];
+        for (int i = 0; i < NSLOT; ++i) last_issued[i] = -1;
+        if (lane == 0) {
+            mbar_arrive_expect_tx(smem_u32(wbar), C::W_BYTES);
+            bulk_g2s(smem_u32(s_w), (const uint8_t *)P.wpack + (size_t)rank * C::W_BYTES, C::W_BYTES, smem_u32(wbar));
+        }
+        uint32_t li = 0;
+        bool ok = true;
+        for (int u = pair_id; u < P.n_units && ok; u += n_pairs) {
+            const UnitInfo ui = unit_info<true>(P.imgs, P.n_imgs, P.in_buf, u, P.ru, P.order);
+            const int y0 = ui.y0, nrows = ui.nrows, x0 = ui.x0 + TILE_M * (int)rank;
+            const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, ui.W);   // in-image pixel range
+            for (int r = 0; r < nrows + 2; ++r, ++li) {
+                const int slot = (int)(li % NSLOT);
+                const uint32_t ph = (li / NSLOT) & 1u;
+                int got = 0;
+                if (lane == 0) got = mbar_wait_cl(smem_u32(&empty[slot]), ph ^ 1u, s_abort, peer_abort, P.err) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, got, 0)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *dst = s_rows + slot * C::SLOT_BYTES;
+                const int yy = y0 - 1 + r;
+                const bool any = (yy >= 0 && yy < ui.H && hi > lo);
+                bool zeroed = false;
+                if (!any) {
+                    for (int k = lane; k < C::NCHUNK * ROW_PX; k += 32)
+                        *reinterpret_cast<uint4 *>(dst + (size_t)k * 16) = make_uint4(0, 0, 0, 0);
+                    zeroed = true;
+                } else if (lo > x0 - 1 || hi < x0 - 1 + ROW_PX) {
+                    const int nl = lo - (x0 - 1), nr = (x0 - 1 + ROW_PX) - hi;   // both in [0, ROW_PX)
+                    for (int k = lane; k < C::NCHUNK * (nl + nr); k += 32) {
+                        const int c = k / (nl + nr), j = k % (nl + nr);
+                        const int px = j < nl ? j : (hi - (x0 - 1)) + (j - nl);
+                        *reinterpret_cast<uint4 *>(dst + ((size_t)c * ROW_PX + px) * 16) = make_uint4(0, 0, 0, 0);
+                    }
+                    zeroed = true;
+                }
+                if (zeroed) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    s_meta[slot] = make_int2(r, nrows);
+                    if (any) {
+                        const uint32_t run = (uint32_t)(hi - lo) * 16u;
+                        mbar_arrive_expect_tx(smem_u32(&full[slot]), run * C::NCHUNK);
+                        for (int c = 0; c < C::NCHUNK; ++c)
+                            bulk_g2s(smem_u32(dst + ((size_t)c * ROW_PX + (lo - (x0 - 1))) * 16),
+                                     ui.in + (((size_t)c * ui.H + yy) * ui.W + lo) * 16, run, smem_u32(&full[slot]));
+                    } else {
+                        mbar_arrive(smem_u32(&full[slot]));
+                    }
+                }
+                last_issued[slot] = (int)li;
+            }
+        }
+        if (ok) {
+            // end marker: the consumers stop at a row with k = -1
+            const int slot = (int)(li % NSLOT);
+            int got = 0;
+            if (lane == 0)
+                got = mbar_wait_cl(smem_u32(&empty[slot]), ((li / NSLOT) & 1u) ^ 1u, s_abort, peer_abort, P.err) ? 1 : 0;
+            if (__shfl_sync(0xffffffffu, got, 0)) {
+                if (lane == 0) {
+                    s_meta[slot] = make_int2(-1, 0);
+                    mbar_arrive(smem_u32(&full[slot]));
+                }
+                // the marker is this slot's newest phase: the drain below waits for it
+                // (its parity), which implies the slot's earlier copies have landed
+                last_issued[slot] = (int)li;
+            }
+        }
+        // drain: every issued copy must have landed before the CTA exits
+        if (lane == 0) {
+            for (int s2 = 0; s2 < NSLOT; ++s2)
+                if (last_issued[s2] >= 0)
+                    mbar_wait(smem_u32(&full[s2]), ((uint32_t)last_issued[s2] / NSLOT) & 1u, s_abort, P.err, true);
+            mbar_wait(smem_u32(wbar), 0, s_abort, P.err, true);
+        }
+        __syncwarp();
+    } else if (warp == 1 && leader) {
+        // ------------------------- MMA issuer (first CTA) -------------------------
+        const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
+        const uint32_t w_addr = smem_u32(s_w);
+        auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
+            int got = 0;
+            if (lane == 0) got = mbar_wait_cl(bar, par, s_abort, peer_abort, P.err) ? 1 : 0;
+            return __shfl_sync(0xffffffffu, got, 0) != 0;
+        };
+        bool ok = wait1(smem_u32(wbar), 0) && wait1(smem_u32(pwbar), 0);
+        uint32_t q = 0, uit = 0;
+        while (ok) {
+            const int slot = (int)(q % NSLOT);
+            const uint32_t ph = (q / NSLOT) & 1u;
+            ok = wait1(smem_u32(&full[slot]), ph) && wait1(smem_u32(&pfull[slot]), ph);
+            if (!ok) break;
+            int mk = 0, mn = 0;
+            if (lane == 0) {
+                const volatile int *mv = (const volatile int *)&s_meta[slot];
+                mk = mv[0];
+                mn = mv[1];
+            }
+            const int k = __shfl_sync(0xffffffffu, mk, 0), nrows = __shfl_sync(0xffffffffu, mn, 0);
+            if (k < 0) break;
+            if (k < nrows) {
+                ok = wait1(smem_u32(&bfree[k]), uit & 1u);     // block k enters use
+                if (!ok) break;
+            }
+            tc_fence_after();
+            if (lane == 0) {
+                const int jlo = max(0, k - 2), jhi = min(nrows - 1, k);
+                const uint32_t n = (uint32_t)(jhi - jlo + 1) * 64u;
+                const int sb = 2 - k + jlo;                                  // first stacked dy block
+                const int v = pv_of(sb, (int)n);
+                const uint64_t b_q = sdesc(w_addr + (uint32_t)pv_row(v) * 32u, (uint32_t)(pv_n(v) / 2) * 16u, 128u);
+                const uint32_t idesc = idesc_m256<FP8>(n);
+                const uint32_t d = tmem_base + (uint32_t)jlo * 64u;
+                const uint64_t a_q = a_base + (uint64_t)(((uint32_t)slot * (uint32_t)C::SLOT_BYTES) >> 4);
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                    for (int ks = 0; ks < C::KSTEPS; ++ks)
+                        mma_ss_pair<FP8>(d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
+                                         b_q + (uint64_t)(((dx * C::KSTEPS + ks) * PV_GROUP_BYTES) >> 4), idesc, 1u);
+                mma_commit_pair(smem_u32(&empty[slot]));
+                if (k >= 2) mma_commit_pair(smem_u32(&bfull[k - 2]));       // output row k-2 complete
+            }
+            __syncwarp();
+            ++q;
+            if (k == nrows + 1) {
+                // blocks this unit leaves unused still go through one full/free round
+                for (int j = nrows; j < P.ru && ok; ++j) {
+                    ok = wait1(smem_u32(&bfree[j]), uit & 1u);
+                    if (ok && lane == 0) mma_commit_pair(smem_u32(&bfull[j]));
+                    __syncwarp();
+                }
+                ++uit;
+            }
+        }
+        // drain: every issued MMA completes before TMEM is released
+        if (lane == 0) {
+            mma_commit_pair(smem_u32(drain));
+            mbar_wait_cl(smem_u32(drain), 0, s_abort, 0u, P.err, true);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------- relay (second CTA) -------------------------
+        auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
+            int got = 0;
+            if (lane == 0) got = mbar_wait_cl(bar, par, s_abort, peer_abort, P.err) ? 1 : 0;
+            return __shfl_sync(0xffffffffu, got, 0) != 0;
+        };
+        bool ok = wait1(smem_u32(wbar), 0);
+        if (ok && lane == 0) mbar_arrive_cluster(mapa_rank(smem_u32(pwbar), 0u));
+        for (uint32_t q = 0; ok; ++q) {
+            const int slot = (int)(q % NSLOT);
+            ok = wait1(smem_u32(&full[slot]), (q / NSLOT) & 1u);
+            if (!ok) break;
+            int k = 0;
+            if (lane == 0) {
+                k = ((const volatile int *)&s_meta[slot])[0];
+                mbar_arrive_cluster(mapa_rank(smem_u32(&pfull[slot]), 0u));
+            }
+            if (__shfl_sync(0xffffffffu, k, 0) < 0) break;
+        }
+        // the first CTA's last MMAs read this CTA's shared memory and write its TMEM
+        if (lane == 0) mbar_wait_cl(smem_u32(drain), 0, s_abort, 0u, P.err, true);
+        __syncwarp();
+    } else {
+        // ------------------------- epilogue (both CTAs) -------------------------
+        const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
+        const int grp = (warp - 2) >> 2;              // 0 or 1
+        const int px = quarter * 32 + lane;           // pixel within this CTA's 128-pixel half
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        auto release = [&](int j) {
+            if (leader) mbar_arrive(smem_u32(&bfree[j]));
+            else mbar_arrive_cluster(mapa_rank(smem_u32(&bfree[j]), 0u));
+        };
+        for (int j = grp; j < P.ru; j += 2)
+            for (int c = 0; c < 64; c += 16) tmem_zero16(lane_base + j * 64 + c);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+            for (int j = grp; j < P.ru; j += 2) release(j);
+        uint32_t uit = 0;
+        bool ok = true;
+        for (int u = pair_id; u < P.n_units && ok; u += n_pairs, ++uit) {
+            const UnitInfo ui = unit_info<true>(P.imgs, P.n_imgs, P.in_buf, u, P.ru, P.order);
+            const int y0 = ui.y0, nrows = ui.nrows;
+            const int x = ui.x0 + TILE_M * (int)rank + px;
+            for (int j = grp; j < P.ru; j += 2) {
+                int got = 0;
+                if (lane == 0) got = mbar_wait_cl(smem_u32(&bfull[j]), uit & 1u, s_abort, peer_abort, P.err) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                float v[64];
+                if (j < nrows) {
+                    const uint32_t taddr = lane_base + j * 64u;
+#pragma unroll
+                    for (int c = 0; c < 64; c += 16) tmem_ld16(taddr + c, v + c);
+                    tmem_wait_ld();
+                    for (int c = 0; c < 64; c += 16) tmem_zero16(taddr + c);
+                    tmem_wait_st();
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) release(j);
+                if (j < nrows && x < ui.W) {
+                    const size_t o = (size_t)(y0 + j) * ui.W + x;
+#pragma unroll
+                    for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], P.scale[n], P.bias[n]), 0.f);
+                    if constexpr (HEADP) {
+                        const size_t plane = (size_t)ui.H * ui.W;
+                        float *partials = ui.D->part ? ui.D->part : (float *)ui.out;
+                        float acc[9];
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+#pragma unroll
+                        for (int n = 0; n < 64; ++n) {
+                            const float a = bf16_round(v[n]);
+#pragma unroll
+                            for (int t = 0; t < 9; ++t) acc[t] = fmaf(a, P.head_w[t * 64 + n], acc[t]);
+                        }
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) partials[t * plane + o] = acc[t];
+                    } else {
+                        store_pixel<64>(v, ui.out, P.out_fp8, P.out_inv_scale, ui.H, ui.W, y0 + j, x);
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();          // neither CTA frees TMEM or exits while the pair's MMAs may touch it
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Layer-1 input: per pixel (c_hi, c_hi, c_lo, z_hi, z_hi, z_lo, 0, 0) as bf16,
 // 16 bytes, pixel-major (one chunk of the chunk-planar layout) into act[1].
 // z comes from Philox4x32-10 with one call per aligned group of 4 indices g.
@@ -502,10 +844,46 @@ ht_status ensure_attr()
     return HT_OK;
 }
 
+template <bool FP8, int KIND>
+ht_status ensure_attr2()
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc2<FP8, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg2<FP8>::SMEM));
+        attr_set = true;
+    }
+    return HT_OK;
+}
+
+// CTA pairs that can be resident at once (1 CTA per SM; a pair needs two SMs of one GPC)
+int max_pairs()
+{
+    static int n = 0;
+    if (!n) {
+        int clusters = 0;
+        if (ensure_attr2<false, KIND_HIDDEN>() == HT_OK) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(2 * (num_sms() / 2), 1, 1);
+            cfg.blockDim = dim3(NTHREADS, 1, 1);
+            cfg.dynamicSmemBytes = Cfg2<false>::SMEM;
+            if (cudaOccupancyMaxActiveClusters(&clusters, k_conv_tc2<false, KIND_HIDDEN>, &cfg) != cudaSuccess)
+                clusters = 0;
+        }
+        cudaGetLastError();
+        n = clusters > 0 ? clusters : (num_sms() / 2 > 0 ? num_sms() / 2 : 1);
+    }
+    return n;
+}
+
 // every kernel attribute set before a stream capture records the launches
 ht_status ensure_all_attrs()
 {
     ht_status st;
+    if ((st = ensure_attr2<false, KIND_HIDDEN>()) != HT_OK || (st = ensure_attr2<false, KIND_HEADPART>()) != HT_OK ||
+        (st = ensure_attr2<true, KIND_HIDDEN>()) != HT_OK || (st = ensure_attr2<true, KIND_HEADPART>()) != HT_OK)
+        return st;
+    max_pairs();
     if ((st = ensure_attr<false, KIND_HIDDEN>()) != HT_OK || (st = ensure_attr<false, KIND_HEADPART>()) != HT_OK ||
         (st = ensure_attr<false, KIND_FIRST>()) != HT_OK || (st = ensure_attr<false, KIND_HEAD4>()) != HT_OK ||
         (st = ensure_attr<true, KIND_HIDDEN>()) != HT_OK || (st = ensure_attr<true, KIND_HEADPART>()) != HT_OK ||
@@ -528,6 +906,22 @@ ht_status launch_conv(const ConvParams &P, cudaStream_t s)
     ht_prof_start(KIND == KIND_FIRST ? HTK_FIRST_TC : KIND == KIND_HEAD4 ? HTK_HEAD_TC
                                                   : FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
     k_conv_tc<FP8, KIND, TR, CH><<<grid, NTHREADS, Cfg<FP8, KIND, CH>::SMEM, s>>>(P);
+    ht_prof_stop(s);
+    HT_LAUNCH_CHECK();
+    return HT_OK;
+}
+
+// CTA-pair form: P.n_units counts 256-pixel units (ImgDesc::unit2_begin), P.wpack
+// holds both CTAs' weight images (CTA r at r * Cfg2::W_BYTES).
+template <bool FP8, int KIND>
+ht_status launch_conv2(const ConvParams &P, cudaStream_t s)
+{
+    const ht_status st = ensure_attr2<FP8, KIND>();
+    if (st != HT_OK) return st;
+    if (P.n_units <= 0) return HT_OK;
+    const int pairs = P.n_units < max_pairs() ? P.n_units : max_pairs();
+    ht_prof_start(FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
+    k_conv_tc2<FP8, KIND><<<2 * pairs, NTHREADS, Cfg2<FP8>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -708,6 +1102,34 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
     }
     e = cudaMemcpyAsync(p->d_wpack, hp, layer_bytes * n_inner, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && fp8) e = cudaMemcpyAsync(p->d_wscale, hs, sizeof(float) * 64 * n_inner, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && CH == 64 && n_inner > 0) {
+        // CTA-pair images: for CTA r, per (dx, K step) group, variant v's rows
+        // [r n/2, (r+1) n/2) of its stacked column range, both 16-byte K chunks
+        const int ksteps = nchunk / 2;
+        const size_t wb = (size_t)3 * ksteps * PV_GROUP_BYTES;     // one CTA's image of one layer
+        p->wpack2_layer_bytes = 2 * wb;
+        std::vector<uint8_t> h2(p->wpack2_layer_bytes * n_inner);
+        for (int l = 0; l < n_inner; ++l)
+            for (int r = 0; r < 2; ++r)
+                for (int dx = 0; dx < 3; ++dx)
+                    for (int ks = 0; ks < ksteps; ++ks)
+                        for (int v = 0; v < 6; ++v) {
+                            const int half = pv_n(v) / 2;
+                            for (int c = 0; c < 2; ++c)
+                                for (int row = 0; row < half; ++row) {
+                                    const int col = pv_start(v) + r * half + row;    // in [dy=2 | dy=1 | dy=0]
+                                    const size_t src = layer_bytes * l +
+                                        ((((size_t)dx * nchunk + 2 * ks + c) * 3 + col / 64) * CH + col % 64) * 16;
+                                    const size_t dst = p->wpack2_layer_bytes * l + wb * r +
+                                        (size_t)(dx * ksteps + ks) * PV_GROUP_BYTES + (size_t)pv_row(v) * 32 +
+                                        (size_t)c * half * 16 + (size_t)row * 16;
+                                    memcpy(&h2[dst], hp + src, 16);
+                                }
+                        }
+        if (!p->d_wpack2) e = cudaMalloc(&p->d_wpack2, h2.size());
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_wpack2, h2.data(), h2.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     free(hw);
     free(hp);
@@ -775,6 +1197,10 @@ void ht_preload_conv_tc()
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, false, 32>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_RES, false, 32>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_RESHEAD, false, 32>);
+    cudaFuncGetAttributes(&fa, k_conv_tc2<false, KIND_HIDDEN>);
+    cudaFuncGetAttributes(&fa, k_conv_tc2<false, KIND_HEADPART>);
+    cudaFuncGetAttributes(&fa, k_conv_tc2<true, KIND_HIDDEN>);
+    cudaFuncGetAttributes(&fa, k_conv_tc2<true, KIND_HEADPART>);
     cudaFuncGetAttributes(&fa, k_first_input);
     cudaFuncGetAttributes(&fa, k_head_partials);
     ensure_all_attrs();
@@ -835,6 +1261,7 @@ namespace {
 // budget together; each group is one launch per layer over all its images.
 struct TcGroup {
     int g0, ng, units, hd, pre;
+    int units2;                 // conv units of the CTA-pair form (256-pixel tiles)
 };
 
 // Host side of a call: the image tables (into `tab`, one entry per image, in call
@@ -867,7 +1294,7 @@ void tc_make_groups(const ht_policy *p, const ht_image *imgs, int n, uint8_t *ws
             D.image = (uint32_t)g1;
             if (p->arch == HT_ARCH_RESNET)   // 32-wide buffers use half of each 128 B/px slot
                 D.part = (float *)(D.act[1] + (size_t)D.H * D.W * 64);
-            set_begins(D, G.units, G.hd, G.pre, ru);
+            set_begins(D, G.units, G.hd, G.pre, ru, &G.units2);
             ++g1;
         }
         G.ng = g1 - g0;
@@ -880,9 +1307,10 @@ void tc_make_groups(const ht_policy *p, const ht_image *imgs, int n, uint8_t *ws
 // layers and the head.  Kernel launches only (no copies, no allocation), so the
 // sequence can be captured into a CUDA graph.
 ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vector<TcGroup> &groups, int mode,
-                           uint64_t seed, int ru, int order, int *err, cudaStream_t s)
+                           uint64_t seed, int ru, int order, int pair, int *err, cudaStream_t s)
 {
     const bool fp8 = (p->prec == HT_FP8_E4M3);
+    pair = pair && p->d_wpack2 && p->arch != HT_ARCH_RESNET;
     const int n_inner = p->L - 2;
     for (const TcGroup &G : groups) {
         const ImgDesc *dt = d_table + G.g0;
@@ -964,6 +1392,16 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
             if (fuse_head) memcpy(P.head_w, p->h_headw, sizeof(P.head_w));
             P.out_inv_scale = out8 ? 1.f / p->act_scale[l + 1] : 1.f;
             P.out_fp8 = out8 ? 1 : 0;
+            if (pair) {
+                P.n_units = G.units2;
+                P.wpack = (const uint8_t *)p->d_wpack2 + p->wpack2_layer_bytes * (l - 1);
+                const ht_status st =
+                    fp8 ? (fuse_head ? launch_conv2<true, KIND_HEADPART>(P, s) : launch_conv2<true, KIND_HIDDEN>(P, s))
+                        : (fuse_head ? launch_conv2<false, KIND_HEADPART>(P, s) : launch_conv2<false, KIND_HIDDEN>(P, s));
+                if (st != HT_OK) return st;
+                cur ^= 1;
+                continue;
+            }
             const ht_status st =
                 fp8 ? (fuse_head ? launch_conv<true, KIND_HEADPART>(P, s) : launch_conv<true, KIND_HIDDEN>(P, s))
                     : (fuse_head ? launch_conv<false, KIND_HEADPART>(P, s) : launch_conv<false, KIND_HIDDEN>(P, s));
@@ -1013,7 +1451,7 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
     std::vector<TcGroup> groups;
     tc_make_groups(p, imgs, n, (uint8_t *)p->d_ws, p->tune_ru, bits, prob, tab, groups);
     HT_CUDA_TRY(cudaMemcpyAsync(d_table, tab.data(), sizeof(ImgDesc) * n, cudaMemcpyHostToDevice, s));
-    return tc_launch_groups(p, d_table, groups, mode, seed, p->tune_ru, p->tune_order, err, s);
+    return tc_launch_groups(p, d_table, groups, mode, seed, p->tune_ru, p->tune_order, p->tune_pair, err, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1021,7 +1459,7 @@ ht_status ht_run_tc_batch(ht_policy *p, const ht_image *imgs, int n, int mode, u
 // ---------------------------------------------------------------------------
 struct ht_plan {
     ht_policy *p = nullptr;
-    int n = 0, mode = 0, ru = RU, order = 0;
+    int n = 0, mode = 0, ru = RU, order = 0, pair = 0;
     uint64_t seed = 0;
     uint64_t version = 0;                 // policy weight version the graph was captured with
     std::vector<ht_image> imgs;
@@ -1054,7 +1492,7 @@ ht_status plan_capture(ht_plan *pl)
     HT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        st = tc_launch_groups(pl->p, pl->d_table, pl->groups, pl->mode, pl->seed, pl->ru, pl->order, err, cs);
+        st = tc_launch_groups(pl->p, pl->d_table, pl->groups, pl->mode, pl->seed, pl->ru, pl->order, pl->pair, err, cs);
         const cudaError_t e2 = cudaStreamEndCapture(cs, &pl->graph);
         if (st == HT_OK && e2 != cudaSuccess) e = e2;
     }
@@ -1087,6 +1525,7 @@ ht_status ht_plan_create_impl(ht_policy *p, const ht_image *imgs, int n, int mod
     pl->seed = seed;
     pl->ru = p->tune_ru;
     pl->order = p->tune_order;
+    pl->pair = p->tune_pair;
     pl->imgs.assign(imgs, imgs + n);
     pl->bits.assign(bits, bits + n);
     if (prob) pl->prob.assign(prob, prob + n);
@@ -1138,18 +1577,20 @@ ht_status ht_plan_destroy_impl(ht_plan *pl)
 ht_status ht_tc_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed, uint32_t *const *bits,
                          float *const *prob, int reps, ht_tune_result *out, int max_out, int *n_out, cudaStream_t s)
 {
-    static const int cand[][2] = {{8, 0}, {8, 1}, {6, 0}, {6, 1}, {4, 0}, {4, 1}};
-    const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+    static const int cand[][3] = {{8, 0, 0}, {8, 1, 0}, {6, 0, 0}, {6, 1, 0}, {4, 0, 0}, {4, 1, 0},
+                                  {8, 0, 1}, {8, 1, 1}, {6, 0, 1}, {6, 1, 1}, {4, 0, 1}, {4, 1, 1}};
+    const int nc = p->d_wpack2 && p->arch != HT_ARCH_RESNET ? 12 : 6;
     cudaEvent_t e0, e1;
     HT_CUDA_TRY(cudaEventCreate(&e0));
     HT_CUDA_TRY(cudaEventCreate(&e1));
-    const int keep_ru = p->tune_ru, keep_order = p->tune_order;
+    const int keep_ru = p->tune_ru, keep_order = p->tune_order, keep_pair = p->tune_pair;
     float best = 1e30f;
     int bi = 0, k_out = 0;
     ht_status st = HT_OK;
     for (int c = 0; c < nc && st == HT_OK; ++c) {
         p->tune_ru = cand[c][0];
         p->tune_order = cand[c][1];
+        p->tune_pair = cand[c][2];
         st = ht_run_tc_batch(p, imgs, n, mode, seed, bits, prob, s);       // warm-up
         if (st != HT_OK) break;
         cudaEventRecord(e0, s);
@@ -1166,6 +1607,7 @@ ht_status ht_tc_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, ui
         if (out && k_out < max_out) {
             out[k_out].rows_per_unit = cand[c][0];
             out[k_out].unit_order = cand[c][1];
+            out[k_out].cta_pair = cand[c][2];
             out[k_out].ms = ms;
             ++k_out;
         }
@@ -1179,10 +1621,12 @@ ht_status ht_tc_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, ui
     if (st != HT_OK) {
         p->tune_ru = keep_ru;
         p->tune_order = keep_order;
+        p->tune_pair = keep_pair;
         return st;
     }
     p->tune_ru = cand[bi][0];
     p->tune_order = cand[bi][1];
+    p->tune_pair = cand[bi][2];
     if (n_out) *n_out = k_out;
     return HT_OK;
 }

@@ -113,6 +113,10 @@ struct ht_policy {
     // conv schedule of the tensor-core forms (set by ht_policy_autotune): rows per
     // work unit (TMEM accumulator blocks) and unit order
     int tune_ru = 8, tune_order = 0;
+    int tune_pair = 0;              // 1: 64 -> 64 layers of the inference forms run as CTA pairs (M = 256)
+    // CTA-pair weight images of the inner 64 -> 64 layers (two per layer, one per CTA of a pair)
+    void *d_wpack2 = nullptr;
+    size_t wpack2_layer_bytes = 0;
     uint64_t version = 0;           // bumped by every change of weights or scales (plans re-capture)
     // per-call workspace (grown on demand; library owned)
     void *d_ws = nullptr;

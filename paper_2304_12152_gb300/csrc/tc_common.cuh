@@ -141,6 +141,120 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// CTA pairs (cluster of 2, tcgen05 cta_group::2).  Both CTAs allocate and free
+// TMEM together (one warp in each); only the pair's first CTA issues MMAs,
+// whose M = 256 rows are the two CTAs' 128-row A tiles and whose B operand is
+// split by N: the first CTA holds rows [0, N/2), the second [N/2, N), at the
+// same shared-memory offset.  Each CTA's TMEM receives its own 128 rows.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v)
+{
+    asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cl(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait with cluster-scope acquire (barriers that the peer CTA arrives on).
+// On expiry it records the timeout like mbar_wait and also raises the peer's
+// abort flag (peer_abort: shared::cluster address, 0 = none).
+__device__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t peer_abort, int *err,
+                             bool ignore_abort = false)
+{
+    if (mbar_try_wait_cl(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait_cl(bar, parity)) return true;
+        if ((it & 31u) == 0) {
+            if (!ignore_abort && *abort_flag) return false;
+            const uint64_t el = globaltimer_ns() - t0;
+            if (el > kTimeoutNs || it > (1u << 28)) {
+                *abort_flag = 1;
+                if (peer_abort) st_cluster_u32(peer_abort, 1u);
+                atomicExch(err, (int)HT_ERR_TIMEOUT);
+                if (atomicCAS(err + 1, 0, 1) == 0) {
+                    err[2] = (int)bar;
+                    err[3] = (int)((blockDim.x << 16) | (threadIdx.x >> 5));
+                    err[4] = (int)blockIdx.x;
+                    err[5] = (int)it;
+                    *reinterpret_cast<unsigned long long *>(err + 6) = el;
+                }
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+template <bool FP8>
+__host__ __device__ constexpr uint32_t idesc_m256(uint32_t n)
+{
+    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((n >> 3) << 17) | ((256u >> 4) << 24);
+}
+template <bool FP8>
+__device__ __forceinline__ void mma_ss_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    }
+}
+// arrives on the barrier at this shared offset in both CTAs of the pair once
+// every MMA issued so far has completed
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 {
     uint32_t r[16];
@@ -237,6 +351,8 @@ struct ImgDesc {
     int unit_begin;           // first conv unit (xtiles * ceil(H / RU) units per image)
     int hd_begin;             // first head tile (ceil(W / 32) * ceil(H / 8))
     int pre_begin;            // first layer-1 input group of 4 pixels (ceil(H * W / 4))
+    int xtiles2;              // ceil(W / 256): column tiles of a CTA pair
+    int unit2_begin;          // first conv unit of the CTA-pair form (xtiles2 * ceil(H / RU) units per image)
 };
 
 // largest i with begin(i) <= u (images sorted by their begin offsets)
@@ -259,26 +375,28 @@ struct UnitInfo {
     int H, W, x0, y0, nrows;
 };
 
-// Unit u of a call: ru (<= RU) rows x one 128-pixel column tile of one image.
-// order 0 walks an image's units row band by row band, order 1 column tile by
-// column tile.
+// Unit u of a call: ru (<= RU) rows x one 128-pixel column tile of one image
+// (PAIR: one 256-pixel tile, the two 128-pixel halves of a CTA pair).  order 0
+// walks an image's units row band by row band, order 1 column tile by column tile.
+template <bool PAIR = false>
 __device__ __forceinline__ UnitInfo unit_info(const ImgDesc *imgs, int n_imgs, int in_buf, int u, int ru = RU,
                                               int order = 0)
 {
-    const int im = find_image(n_imgs, u, [&](int i) { return __ldg(&imgs[i].unit_begin); });
+    const int im = find_image(n_imgs, u, [&](int i) { return PAIR ? __ldg(&imgs[i].unit2_begin) : __ldg(&imgs[i].unit_begin); });
     const ImgDesc *D = imgs + im;
-    const int lu = u - __ldg(&D->unit_begin);
-    const int xt = __ldg(&D->xtiles);
+    const int lu = u - (PAIR ? __ldg(&D->unit2_begin) : __ldg(&D->unit_begin));
+    const int xt = PAIR ? __ldg(&D->xtiles2) : __ldg(&D->xtiles);
+    constexpr int TW = PAIR ? 2 * TILE_M : TILE_M;
     UnitInfo ui;
     ui.D = D;
     ui.H = __ldg(&D->H);
     ui.W = __ldg(&D->W);
     if (order == 0) {
-        ui.x0 = (lu % xt) * TILE_M;
+        ui.x0 = (lu % xt) * TW;
         ui.y0 = (lu / xt) * ru;
     } else {
         const int nb = (ui.H + ru - 1) / ru;
-        ui.x0 = (lu / nb) * TILE_M;
+        ui.x0 = (lu / nb) * TW;
         ui.y0 = (lu % nb) * ru;
     }
     ui.nrows = min(ui.H, ui.y0 + ru) - ui.y0;
@@ -289,12 +407,15 @@ __device__ __forceinline__ UnitInfo unit_info(const ImgDesc *imgs, int n_imgs, i
 
 // Work-index layout of one image inside a call's table: conv units, head tiles,
 // layer-1 input groups (prefix sums over the images in table order).
-inline void set_begins(ImgDesc &D, int &units, int &hd, int &pre, int ru = RU)
+inline void set_begins(ImgDesc &D, int &units, int &hd, int &pre, int ru = RU, int *units2 = nullptr)
 {
     D.xtiles = (D.W + TILE_M - 1) / TILE_M;
     D.unit_begin = units;
     D.hd_begin = hd;
     D.pre_begin = pre;
+    D.xtiles2 = (D.W + 2 * TILE_M - 1) / (2 * TILE_M);
+    D.unit2_begin = units2 ? *units2 : 0;
+    if (units2) *units2 += D.xtiles2 * ((D.H + ru - 1) / ru);
     units += D.xtiles * ((D.H + ru - 1) / ru);
     hd += ((D.W + HT_X - 1) / HT_X) * ((D.H + HT_Y - 1) / HT_Y);
     pre += (int)(((size_t)D.H * D.W + 3) / 4);

@@ -36,7 +36,7 @@ def test_plan_matches_direct_call(prec):
     plan = api.Plan(pol, imgs, bits, N.HT_MODE_BERNOULLI, 7, probs)
     for _ in range(2):
         plan.launch()
-    torch.cuda.synchronize()
+    api.sync()
     for a, b in zip(bits, ref):
         assert torch.equal(a, b)
     for a, b in zip(probs, pref):
@@ -55,7 +55,7 @@ def test_plan_recaptures_after_weight_change():
     pol.set_weights(w, b)
     plan.launch()                                  # new weights -> captured again
     ref, _ = pol.halftone(imgs, mode=N.HT_MODE_THRESHOLD, seed=1)
-    torch.cuda.synchronize()
+    api.sync()
     for a, r in zip(bits, ref):
         assert torch.equal(a, r)
 
@@ -75,17 +75,18 @@ def test_autotune_schedules_are_bit_identical():
     bits = [torch.zeros_like(b) for b in ref]
     probs = [torch.zeros_like(p) for p in pref]
     res = pol.autotune(imgs, bits, N.HT_MODE_BERNOULLI, 2, probs, reps=2)
-    torch.cuda.synchronize()
+    api.sync()
     assert len(res) == N.HT_TUNE_CANDIDATES
-    assert sorted((r, o) for r, o, _ in res) == sorted([(8, 0), (8, 1), (6, 0), (6, 1), (4, 0), (4, 1)])
-    assert all(ms > 0 for _, _, ms in res)
+    assert sorted((r, o, pr) for r, o, pr, _ in res) == sorted(
+        [(r, o, pr) for pr in (0, 1) for r in (8, 6, 4) for o in (0, 1)])
+    assert all(ms > 0 for *_, ms in res)
     # the last candidate's outputs, and the chosen schedule's later calls, equal the default schedule's
     for a, b in zip(bits, ref):
         assert torch.equal(a, b)
     for a, b in zip(probs, pref):
         assert torch.equal(a, b)
     again, pagain = pol.halftone(imgs, mode=N.HT_MODE_BERNOULLI, seed=2, want_prob=True)
-    torch.cuda.synchronize()
+    api.sync()
     for a, b in zip(again, ref):
         assert torch.equal(a, b)
     for a, b in zip(pagain, pref):
@@ -101,8 +102,9 @@ def test_many_short_units_every_schedule():
     imgs = [torch.from_numpy(synth.contone_image(13, 300, seed=8, index=i)).cuda() for i in range(160)]
     bits = [pol.alloc_bits(13, 300) for _ in imgs]
     ref = None
-    for ru, order in [(8, 0), (8, 1), (6, 0), (6, 1), (4, 0), (4, 1), (3, 0), (7, 1)]:
-        pol.set_schedule(ru, order)
+    for ru, order, pair in [(8, 0, 0), (8, 1, 0), (6, 0, 0), (6, 1, 0), (4, 0, 0), (4, 1, 0), (3, 0, 0), (7, 1, 0),
+                            (8, 0, 1), (8, 1, 1), (6, 0, 1), (4, 1, 1), (3, 0, 1), (7, 1, 1)]:
+        pol.set_schedule(ru, order, pair)
         for _ in range(3):
             pol.halftone_into(imgs, bits, N.HT_MODE_BERNOULLI, 3)
             api.sync()
@@ -110,5 +112,43 @@ def test_many_short_units_every_schedule():
             ref = [b.clone() for b in bits]
         else:
             for a, b in zip(bits, ref):
-                assert torch.equal(a, b), (ru, order)
+                assert torch.equal(a, b), (ru, order, pair)
     pol.set_schedule(8, 0)
+
+
+PAIR_SHAPES = [(300, 200), (37, 515), (129, 131), (8, 9), (1, 1), (5, 700), (70, 256), (17, 257)]
+
+
+@pytest.mark.parametrize("prec", [N.HT_BF16, N.HT_FP8_E4M3])
+def test_cta_pair_form_matches_single_cta_form(prec):
+    """The CTA-pair form of the 64 -> 64 layers (M = 256 MMAs over a 256-pixel tile,
+    weights split by N between the two CTAs) accumulates every output pixel in the same
+    order as the single-CTA form, so bits and probabilities are equal bit for bit.
+    Widths leave the second CTA of a pair partly or wholly outside the image; heights
+    leave short row bands."""
+    ws, bs = synth.he_normal_policy(synth.NET_WIDE, 11)
+    bs = synth.random_biases(synth.NET_WIDE, 3)
+    pol = api.Policy(synth.NET_WIDE, ws, bs, precision=prec)
+    imgs = [torch.from_numpy(synth.contone_image(h, w, seed=12, index=i)).cuda() for i, (h, w) in enumerate(PAIR_SHAPES)]
+    if prec == N.HT_FP8_E4M3:
+        pol.calibrate(imgs[0], seed=9)
+    for mode in (N.HT_MODE_THRESHOLD, N.HT_MODE_BERNOULLI):
+        pol.set_schedule(8, 0, 0)
+        ref, pref = pol.halftone(imgs, mode=mode, seed=4, want_prob=True)
+        for ru, order in [(8, 0), (8, 1), (6, 1), (3, 0)]:
+            pol.set_schedule(ru, order, 1)
+            got, pgot = pol.halftone(imgs, mode=mode, seed=4, want_prob=True)
+            api.sync()                     # also raises a device-side wait expiry
+            for i, (a, b) in enumerate(zip(got, ref)):
+                assert torch.equal(a, b), (mode, ru, order, PAIR_SHAPES[i])
+            for i, (a, b) in enumerate(zip(pgot, pref)):
+                assert torch.equal(a, b), (mode, ru, order, PAIR_SHAPES[i])
+    # a plan captured with the pair form replays it
+    pol.set_schedule(8, 0, 1)
+    bits = [torch.zeros_like(b) for b in ref]
+    plan = api.Plan(pol, imgs, bits, N.HT_MODE_BERNOULLI, 4)
+    plan.launch()
+    api.sync()
+    for a, b in zip(bits, ref):
+        assert torch.equal(a, b)
+    pol.set_schedule(8, 0, 0)
