@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
     uint64_t *bars = (uint64_t *)(s_rows + NSLOT * C::SLOT_BYTES);
     uint64_t *full = bars, *empty = bars + NSLOT, *wbar = bars + 2 * NSLOT, *bfull = wbar + 1, *bfree = bfull + RU,
              *drain = bfree + RU;
-    uint32_t *s_tmem = (uint32_t *)(drain + 1);
+    int2 *s_meta = (int2 *)(drain + 1);                         // (k, nrows) of the row in each slot
+    uint32_t *s_tmem = (uint32_t *)(s_meta + NSLOT);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 if (zeroed) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) {
+                    s_meta[slot] = make_int2(r, y1 - y0);
                     const uint32_t run = (uint32_t)(hi - lo) * 16u;
                     if (row_in && hi > lo) {
                         mbar_arrive_expect_tx(smem_u32(&full[slot]), run * C::NCOPY);
@@ -218,6 +220,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 last_issued[slot] = (int)li;
             }
         }
+        if (ok) {
+            // end marker: the MMA warp stops at a row with k = -1
+            const int slot = (int)(li % NSLOT);
+            int got = 0;
+            if (lane == 0) got = mbar_wait(smem_u32(&empty[slot]), ((li / NSLOT) & 1u) ^ 1u, s_abort, P.err) ? 1 : 0;
+            if (__shfl_sync(0xffffffffu, got, 0)) {
+                if (lane == 0) {
+                    s_meta[slot] = make_int2(-1, 0);
+                    mbar_arrive(smem_u32(&full[slot]));
+                }
+                last_issued[slot] = (int)li;       // the marker is this slot's newest phase
+            }
+        }
         // drain: every issued copy must have landed before the CTA exits
         if (lane == 0) {
             for (int s2 = 0; s2 < NSLOT; ++s2)
@@ -228,64 +243,62 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------- MMA issuer -------------------------
-        // Warp-uniform schedule; lane 0 waits (result broadcast) and issues.
-        // Descriptors = base descriptor + compile-time / small offsets added to
-        // the 14-bit start-address field (addresses stay below 256 KB).
-        const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
-        const uint64_t b_base = sdesc(smem_u32(s_w), 3 * C::NOUT * 16, 128);
-        auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
-            int got = 0;
-            if (lane == 0) got = mbar_wait(bar, par, s_abort, P.err) ? 1 : 0;
-            return __shfl_sync(0xffffffffu, got, 0) != 0;
-        };
-        bool ok = wait1(smem_u32(wbar), 0);
-        uint32_t q = 0, uit = 0;
-        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
-            const int nrows = unit_info(P.imgs, P.n_imgs, P.in_buf, u, P.ru, P.order).nrows;
-            for (int k = 0; k < nrows + 2 && ok; ++k, ++q) {
-                ok = wait1(smem_u32(&full[q % NSLOT]), (q / NSLOT) & 1u);
-                if (ok && k < nrows) ok = wait1(smem_u32(&bfree[k]), uit & 1u);   // block k enters use
-                if (!ok) break;
-                tc_fence_after();
-                if (lane == 0) {
-                    const int jlo = max(0, k - 2), jhi = min(nrows - 1, k);
-                    const uint32_t n = (uint32_t)(jhi - jlo + 1) * C::NOUT;
-                    const uint32_t idesc = idesc_m128<C::MMA8>(n);
-                    const uint32_t sb = (uint32_t)(2 - k + jlo);                       // first stacked dy block
-                    const uint32_t d = tmem_base + (uint32_t)jlo * C::NOUT;
-                    const uint64_t a_q = a_base + (uint64_t)(((q % NSLOT) * (uint32_t)C::SLOT_BYTES) >> 4);
-                    const uint64_t b_q = b_base + (uint64_t)((sb * C::NOUT * 16u) >> 4);
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                        for (int ks = 0; ks < C::KSTEPS; ++ks)
-                            mma_ss<C::MMA8>(d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
-                                            b_q + (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4),
-                                            idesc, 1u);
-                    mma_commit(smem_u32(&empty[q % NSLOT]));
-                    if (k >= 2) mma_commit(smem_u32(&bfull[k - 2]));     // output row k-2 complete
-                }
-                __syncwarp();
-            }
-            if (!ok) break;
-            // Blocks a short unit leaves unused still go through one full/free round per
-            // unit, so that every block's barriers stay in step.  Wait until the epilogue
-            // has released the block from the previous unit before signalling it: a parity
-            // wait cannot tell phase k from phase k + 2, so no barrier may run two phases
-            // ahead of its consumer (two short units in a row would otherwise do that).
-            for (int j = nrows; j < P.ru && ok; ++j) {
-                ok = wait1(smem_u32(&bfree[j]), uit & 1u);
-                if (ok && lane == 0) mma_commit(smem_u32(&bfull[j]));
-                __syncwarp();
-            }
-            if (!ok) break;
-        }
-        // drain: all issued MMAs complete before TMEM is released
+        // Lane 0 alone runs the schedule: it takes each staged row's (k, nrows)
+        // from the producer's per-slot record, so no image-table lookups or warp
+        // collectives sit between one row's MMAs and the next.  Descriptors = base
+        // descriptor + compile-time / small offsets added to the 14-bit
+        // start-address field (addresses stay below 256 KB).
         if (lane == 0) {
+            const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
+            const uint64_t b_base = sdesc(smem_u32(s_w), 3 * C::NOUT * 16, 128);
+            bool ok = mbar_wait(smem_u32(wbar), 0, s_abort, P.err);
+            uint32_t q = 0, uit = 0;
+            while (ok) {
+                const uint32_t slot = q % NSLOT;
+                ok = mbar_wait(smem_u32(&full[slot]), (q / NSLOT) & 1u, s_abort, P.err);
+                if (!ok) break;
+                const volatile int *mv = (const volatile int *)&s_meta[slot];
+                const int k = mv[0], nrows = mv[1];
+                if (k < 0) break;
+                if (k < nrows) {
+                    ok = mbar_wait(smem_u32(&bfree[k]), uit & 1u, s_abort, P.err);   // block k enters use
+                    if (!ok) break;
+                }
+                tc_fence_after();
+                const int jlo = max(0, k - 2), jhi = min(nrows - 1, k);
+                const uint32_t n = (uint32_t)(jhi - jlo + 1) * C::NOUT;
+                const uint32_t idesc = idesc_m128<C::MMA8>(n);
+                const uint32_t sb = (uint32_t)(2 - k + jlo);                       // first stacked dy block
+                const uint32_t d = tmem_base + (uint32_t)jlo * C::NOUT;
+                const uint64_t a_q = a_base + (uint64_t)((slot * (uint32_t)C::SLOT_BYTES) >> 4);
+                const uint64_t b_q = b_base + (uint64_t)((sb * C::NOUT * 16u) >> 4);
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                    for (int ks = 0; ks < C::KSTEPS; ++ks)
+                        mma_ss<C::MMA8>(d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
+                                        b_q + (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4),
+                                        idesc, 1u);
+                mma_commit(smem_u32(&empty[slot]));
+                if (k >= 2) mma_commit(smem_u32(&bfull[k - 2]));     // output row k-2 complete
+                ++q;
+                if (k == nrows + 1) {
+                    // Blocks a short unit leaves unused still go through one full/free round per
+                    // unit, so that every block's barriers stay in step.  Wait until the epilogue
+                    // has released the block from the previous unit before signalling it: a parity
+                    // wait cannot tell phase k from phase k + 2, so no barrier may run two phases
+                    // ahead of its consumer (two short units in a row would otherwise do that).
+                    for (int j = nrows; j < P.ru && ok; ++j) {
+                        ok = mbar_wait(smem_u32(&bfree[j]), uit & 1u, s_abort, P.err);
+                        if (ok) mma_commit(smem_u32(&bfull[j]));
+                    }
+                    ++uit;
+                }
+            }
+            // drain: all issued MMAs complete before TMEM is released
             mma_commit(smem_u32(drain));
             mbar_wait(smem_u32(drain), 0, s_abort, P.err, true);
         }
-        __syncwarp();
     } else {
         // ------------------------- epilogue -------------------------
         // Eight warps: two per TMEM lane quarter; group g drains blocks j = g, g+2, ...
@@ -598,35 +611,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
         }
         __syncwarp();
     } else if (warp == 1 && leader) {
-        // ------------------------- MMA issuer (first CTA) -------------------------
-        const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
-        const uint32_t w_addr = smem_u32(s_w);
-        auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
-            int got = 0;
-            if (lane == 0) got = mbar_wait_cl(bar, par, s_abort, peer_abort, P.err) ? 1 : 0;
-            return __shfl_sync(0xffffffffu, got, 0) != 0;
-        };
-        bool ok = wait1(smem_u32(wbar), 0) && wait1(smem_u32(pwbar), 0);
-        uint32_t q = 0, uit = 0;
-        while (ok) {
-            const int slot = (int)(q % NSLOT);
-            const uint32_t ph = (q / NSLOT) & 1u;
-            ok = wait1(smem_u32(&full[slot]), ph) && wait1(smem_u32(&pfull[slot]), ph);
-            if (!ok) break;
-            int mk = 0, mn = 0;
-            if (lane == 0) {
-                const volatile int *mv = (const volatile int *)&s_meta[slot];
-                mk = mv[0];
-                mn = mv[1];
-            }
-            const int k = __shfl_sync(0xffffffffu, mk, 0), nrows = __shfl_sync(0xffffffffu, mn, 0);
-            if (k < 0) break;
-            if (k < nrows) {
-                ok = wait1(smem_u32(&bfree[k]), uit & 1u);     // block k enters use
+        // ------------------------- MMA issuer (first CTA, lane 0) -------------------------
+        if (lane == 0) {
+            const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
+            const uint32_t w_addr = smem_u32(s_w);
+            auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
+                return mbar_wait_cl(bar, par, s_abort, peer_abort, P.err);
+            };
+            bool ok = wait1(smem_u32(wbar), 0) && wait1(smem_u32(pwbar), 0);
+            uint32_t q = 0, uit = 0;
+            while (ok) {
+                const int slot = (int)(q % NSLOT);
+                const uint32_t ph = (q / NSLOT) & 1u;
+                ok = wait1(smem_u32(&full[slot]), ph) && wait1(smem_u32(&pfull[slot]), ph);
                 if (!ok) break;
-            }
-            tc_fence_after();
-            if (lane == 0) {
+                const volatile int *mv = (const volatile int *)&s_meta[slot];
+                const int k = mv[0], nrows = mv[1];
+                if (k < 0) break;
+                if (k < nrows) {
+                    ok = wait1(smem_u32(&bfree[k]), uit & 1u);     // block k enters use
+                    if (!ok) break;
+                }
+                tc_fence_after();
                 const int jlo = max(0, k - 2), jhi = min(nrows - 1, k);
                 const uint32_t n = (uint32_t)(jhi - jlo + 1) * 64u;
                 const int sb = 2 - k + jlo;                                  // first stacked dy block
@@ -643,48 +649,36 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                                          b_q + (uint64_t)(((dx * C::KSTEPS + ks) * PV_GROUP_BYTES) >> 4), idesc, 1u);
                 mma_commit_pair(smem_u32(&empty[slot]));
                 if (k >= 2) mma_commit_pair(smem_u32(&bfull[k - 2]));       // output row k-2 complete
-            }
-            __syncwarp();
-            ++q;
-            if (k == nrows + 1) {
-                // blocks this unit leaves unused still go through one full/free round
-                for (int j = nrows; j < P.ru && ok; ++j) {
-                    ok = wait1(smem_u32(&bfree[j]), uit & 1u);
-                    if (ok && lane == 0) mma_commit_pair(smem_u32(&bfull[j]));
-                    __syncwarp();
+                ++q;
+                if (k == nrows + 1) {
+                    // blocks this unit leaves unused still go through one full/free round
+                    for (int j = nrows; j < P.ru && ok; ++j) {
+                        ok = wait1(smem_u32(&bfree[j]), uit & 1u);
+                        if (ok) mma_commit_pair(smem_u32(&bfull[j]));
+                    }
+                    ++uit;
                 }
-                ++uit;
             }
-        }
-        // drain: every issued MMA completes before TMEM is released
-        if (lane == 0) {
+            // drain: every issued MMA completes before TMEM is released
             mma_commit_pair(smem_u32(drain));
             mbar_wait_cl(smem_u32(drain), 0, s_abort, 0u, P.err, true);
         }
-        __syncwarp();
     } else if (warp == 1) {
-        // ------------------------- relay (second CTA) -------------------------
-        auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
-            int got = 0;
-            if (lane == 0) got = mbar_wait_cl(bar, par, s_abort, peer_abort, P.err) ? 1 : 0;
-            return __shfl_sync(0xffffffffu, got, 0) != 0;
-        };
-        bool ok = wait1(smem_u32(wbar), 0);
-        if (ok && lane == 0) mbar_arrive_cluster(mapa_rank(smem_u32(pwbar), 0u));
-        for (uint32_t q = 0; ok; ++q) {
-            const int slot = (int)(q % NSLOT);
-            ok = wait1(smem_u32(&full[slot]), (q / NSLOT) & 1u);
-            if (!ok) break;
-            int k = 0;
-            if (lane == 0) {
-                k = ((const volatile int *)&s_meta[slot])[0];
+        // ------------------------- relay (second CTA, lane 0) -------------------------
+        if (lane == 0) {
+            bool ok = mbar_wait_cl(smem_u32(wbar), 0, s_abort, peer_abort, P.err);
+            if (ok) mbar_arrive_cluster(mapa_rank(smem_u32(pwbar), 0u));
+            for (uint32_t q = 0; ok; ++q) {
+                const int slot = (int)(q % NSLOT);
+                ok = mbar_wait_cl(smem_u32(&full[slot]), (q / NSLOT) & 1u, s_abort, peer_abort, P.err);
+                if (!ok) break;
+                const int k = ((const volatile int *)&s_meta[slot])[0];
                 mbar_arrive_cluster(mapa_rank(smem_u32(&pfull[slot]), 0u));
+                if (k < 0) break;
             }
-            if (__shfl_sync(0xffffffffu, k, 0) < 0) break;
+            // the first CTA's last MMAs read this CTA's shared memory and write its TMEM
+            mbar_wait_cl(smem_u32(drain), 0, s_abort, 0u, P.err, true);
         }
-        // the first CTA's last MMAs read this CTA's shared memory and write its TMEM
-        if (lane == 0) mbar_wait_cl(smem_u32(drain), 0, s_abort, 0u, P.err, true);
-        __syncwarp();
     } else {
         // ------------------------- epilogue (both CTAs) -------------------------
         const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31

@@ -165,36 +165,31 @@ __device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank)
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
     return r;
 }
+// Arrive on a barrier of another CTA of the cluster.  Default semantics
+// (release at CTA scope): the data the arrival publishes is either this CTA's
+// shared memory filled by the async proxy (bulk copies, observed complete on
+// this CTA's own barrier first) or TMEM reads already waited for, so no
+// cluster-scope fence is needed; a cluster-scope release here costs a full
+// memory barrier per arrival.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr)
 {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 __device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v)
 {
     asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait_cl(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait with cluster-scope acquire (barriers that the peer CTA arrives on).
-// On expiry it records the timeout like mbar_wait and also raises the peer's
-// abort flag (peer_abort: shared::cluster address, 0 = none).
+// Bounded wait on a barrier that the peer CTA may arrive on (default acquire
+// semantics, as for mbar_wait).  On expiry it records the timeout like mbar_wait
+// and also raises the peer's abort flag (peer_abort: shared::cluster address,
+// 0 = none).
 __device__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t peer_abort, int *err,
                              bool ignore_abort = false)
 {
-    if (mbar_try_wait_cl(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait_cl(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity)) return true;
         if ((it & 31u) == 0) {
             if (!ignore_abort && *abort_flag) return false;
             const uint64_t el = globaltimer_ns() - t0;
