@@ -249,17 +249,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         // descriptor + compile-time / small offsets added to the 14-bit
         // start-address field (addresses stay below 256 KB).
         if (lane == 0) {
+            // (k, nrows) is read from the producer's record only where a unit starts;
+            // within a unit k steps by one, so nothing but the barrier checks sits
+            // between one row's MMAs and the next.
             const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
             const uint64_t b_base = sdesc(smem_u32(s_w), 3 * C::NOUT * 16, 128);
             bool ok = mbar_wait(smem_u32(wbar), 0, s_abort, P.err);
-            uint32_t q = 0, uit = 0;
+            uint32_t slot = 0, ph = 0, uit = 0;
+            int k = 0, nrows = 0;
+            bool unit_start = true;
             while (ok) {
-                const uint32_t slot = q % NSLOT;
-                ok = mbar_wait(smem_u32(&full[slot]), (q / NSLOT) & 1u, s_abort, P.err);
+                ok = mbar_wait(smem_u32(&full[slot]), ph, s_abort, P.err);
                 if (!ok) break;
-                const volatile int *mv = (const volatile int *)&s_meta[slot];
-                const int k = mv[0], nrows = mv[1];
-                if (k < 0) break;
+                if (unit_start) {
+                    const volatile int *mv = (const volatile int *)&s_meta[slot];
+                    k = mv[0];
+                    nrows = mv[1];
+                    if (k < 0) break;
+                    unit_start = false;
+                }
                 if (k < nrows) {
                     ok = mbar_wait(smem_u32(&bfree[k]), uit & 1u, s_abort, P.err);   // block k enters use
                     if (!ok) break;
@@ -281,7 +289,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                                         idesc, 1u);
                 mma_commit(smem_u32(&empty[slot]));
                 if (k >= 2) mma_commit(smem_u32(&bfull[k - 2]));     // output row k-2 complete
-                ++q;
+                if (++slot == (uint32_t)NSLOT) {
+                    slot = 0;
+                    ph ^= 1u;
+                }
                 if (k == nrows + 1) {
                     // Blocks a short unit leaves unused still go through one full/free round per
                     // unit, so that every block's barriers stay in step.  Wait until the epilogue
@@ -293,6 +304,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         if (ok) mma_commit(smem_u32(&bfull[j]));
                     }
                     ++uit;
+                    unit_start = true;
+                } else {
+                    ++k;
                 }
             }
             // drain: all issued MMAs complete before TMEM is released
@@ -374,6 +388,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                             if (!(((n < 32 ? m.x : m.y) >> (n & 31)) & 1u)) v[n] = 0.f;
                         store_pixel<C::CO>(v, ui.out, 0, 1.f, ui.H, ui.W, y0 + j, x);
                         continue;
+                    }
+                    if constexpr (KIND == KIND_HIDDEN && !TR && CH == 64) {
+                        if (!P.out_fp8) {
+                            store_pixel_bias_relu_bf16(v, P.scale, P.bias, ui.out, ui.H, ui.W, y0 + j, x);
+                            continue;
+                        }
                     }
 #pragma unroll
                     for (int n = 0; n < C::CO; ++n) v[n] = fmaf(v[n], P.scale[n], P.bias[n]);
@@ -619,15 +639,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                 return mbar_wait_cl(bar, par, s_abort, peer_abort, P.err);
             };
             bool ok = wait1(smem_u32(wbar), 0) && wait1(smem_u32(pwbar), 0);
-            uint32_t q = 0, uit = 0;
+            uint32_t slot = 0, ph = 0, uit = 0;
+            int k = 0, nrows = 0;
+            bool unit_start = true;
             while (ok) {
-                const int slot = (int)(q % NSLOT);
-                const uint32_t ph = (q / NSLOT) & 1u;
                 ok = wait1(smem_u32(&full[slot]), ph) && wait1(smem_u32(&pfull[slot]), ph);
                 if (!ok) break;
-                const volatile int *mv = (const volatile int *)&s_meta[slot];
-                const int k = mv[0], nrows = mv[1];
-                if (k < 0) break;
+                if (unit_start) {
+                    const volatile int *mv = (const volatile int *)&s_meta[slot];
+                    k = mv[0];
+                    nrows = mv[1];
+                    if (k < 0) break;
+                    unit_start = false;
+                }
                 if (k < nrows) {
                     ok = wait1(smem_u32(&bfree[k]), uit & 1u);     // block k enters use
                     if (!ok) break;
@@ -640,7 +664,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                 const uint64_t b_q = sdesc(w_addr + (uint32_t)pv_row(v) * 32u, (uint32_t)(pv_n(v) / 2) * 16u, 128u);
                 const uint32_t idesc = idesc_m256<FP8>(n);
                 const uint32_t d = tmem_base + (uint32_t)jlo * 64u;
-                const uint64_t a_q = a_base + (uint64_t)(((uint32_t)slot * (uint32_t)C::SLOT_BYTES) >> 4);
+                const uint64_t a_q = a_base + (uint64_t)((slot * (uint32_t)C::SLOT_BYTES) >> 4);
 #pragma unroll
                 for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
@@ -649,7 +673,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                                          b_q + (uint64_t)(((dx * C::KSTEPS + ks) * PV_GROUP_BYTES) >> 4), idesc, 1u);
                 mma_commit_pair(smem_u32(&empty[slot]));
                 if (k >= 2) mma_commit_pair(smem_u32(&bfull[k - 2]));       // output row k-2 complete
-                ++q;
+                if (++slot == (uint32_t)NSLOT) {
+                    slot = 0;
+                    ph ^= 1u;
+                }
                 if (k == nrows + 1) {
                     // blocks this unit leaves unused still go through one full/free round
                     for (int j = nrows; j < P.ru && ok; ++j) {
@@ -657,6 +684,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                         if (ok) mma_commit_pair(smem_u32(&bfull[j]));
                     }
                     ++uit;
+                    unit_start = true;
+                } else {
+                    ++k;
                 }
             }
             // drain: every issued MMA completes before TMEM is released
@@ -725,6 +755,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                 if (lane == 0) release(j);
                 if (j < nrows && x < ui.W) {
                     const size_t o = (size_t)(y0 + j) * ui.W + x;
+                    if (!HEADP && !P.out_fp8) {
+                        store_pixel_bias_relu_bf16(v, P.scale, P.bias, ui.out, ui.H, ui.W, y0 + j, x);
+                        continue;
+                    }
 #pragma unroll
                     for (int n = 0; n < 64; ++n) v[n] = fmaxf(fmaf(v[n], P.scale[n], P.bias[n]), 0.f);
                     if constexpr (HEADP) {

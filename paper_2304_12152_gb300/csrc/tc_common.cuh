@@ -45,6 +45,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
+// As mbar_try_wait, but a thread whose phase is not complete is suspended (for
+// up to suspend_ns) until it completes, instead of returning at once: a waiting
+// warp then takes no issue slots from the warps it shares a sub-partition with.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t suspend_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(suspend_ns)
+        : "memory");
+    return ok != 0;
+}
+constexpr uint32_t kSuspendNs = 1000;      // per suspended try: the abort flag and the deadline are checked in between
+
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {
     uint64_t t;
@@ -53,14 +70,16 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 }
 
 // Bounded wait.  Returns false on timeout (which it records) or when another
-// role has already aborted (unless ignore_abort).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, bool ignore_abort = false)
+// role has already aborted (unless ignore_abort).  Inlined: a call in an MMA
+// issue loop (even one not taken) forces register traffic that starves the
+// tensor pipe between rows.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, bool ignore_abort = false)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 31u) == 0) {
+        if (mbar_try_wait_sleep(bar, parity, kSuspendNs)) return true;
+        if ((it & 3u) == 0) {
             if (!ignore_abort && *abort_flag) return false;
             const uint64_t el = globaltimer_ns() - t0;
             if (el > kTimeoutNs || it > (1u << 28)) {
@@ -183,14 +202,14 @@ __device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v
 // semantics, as for mbar_wait).  On expiry it records the timeout like mbar_wait
 // and also raises the peer's abort flag (peer_abort: shared::cluster address,
 // 0 = none).
-__device__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t peer_abort, int *err,
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t peer_abort, int *err,
                              bool ignore_abort = false)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 31u) == 0) {
+        if (mbar_try_wait_sleep(bar, parity, kSuspendNs)) return true;
+        if ((it & 3u) == 0) {
             if (!ignore_abort && *abort_flag) return false;
             const uint64_t el = globaltimer_ns() - t0;
             if (el > kTimeoutNs || it > (1u << 28)) {
@@ -324,6 +343,33 @@ __device__ __forceinline__ void store_pixel(const float *v, void *out, int out_f
             q.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
             *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = q;
         }
+    }
+}
+
+// Epilogue of a bf16-output layer: v * scale + bias (per channel), ReLU, bf16,
+// into the chunk-planar layout.  Two channels per instruction: a packed FP32
+// FMA (each lane an ordinary fmaf) and one convert that rounds to nearest even
+// and clamps negatives to zero (the same value as rounding max(x, 0)).
+__device__ __forceinline__ void store_pixel_bias_relu_bf16(const float *v, const float *scale, const float *bias,
+                                                          void *out, int H, int W, int y, int x)
+{
+    uint8_t *o = (uint8_t *)out;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int n = 8 * c + 2 * h;
+            unsigned long long vv, ss, bb, rr;
+            asm("mov.b64 %0, {%1, %2};" : "=l"(vv) : "f"(v[n]), "f"(v[n + 1]));
+            asm("mov.b64 %0, {%1, %2};" : "=l"(ss) : "f"(scale[n]), "f"(scale[n + 1]));
+            asm("mov.b64 %0, {%1, %2};" : "=l"(bb) : "f"(bias[n]), "f"(bias[n + 1]));
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rr) : "l"(vv), "l"(ss), "l"(bb));
+            float lo, hi;
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(rr));
+            asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w4[h]) : "f"(hi), "f"(lo));
+        }
+        *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
     }
 }
 
