@@ -90,6 +90,7 @@ struct ConvParams {
     float scale[64];
     float bias[64];
     float head_w[9 * 64];    // fused 1-logit head: last-layer weights [tap][channel]
+    unsigned long long head_w2[64][4];   // the same, taps (0,1) (2,3) (4,5) (6,7) packed per channel
     float out_inv_scale;     // FP8 output: 1 / scale of the next layer's input
     int out_fp8;
     uint64_t seed;           // Philox seed (layer 1: noise channel; 4-logit head: level draw)
@@ -98,6 +99,29 @@ struct ConvParams {
     int ru, order;           // unit geometry: rows per unit (<= RU TMEM blocks) and unit order
     int *err;
 };
+
+// Fused 1-logit head (Sec. VI-A output layer): the nine per-tap dot products of the
+// bf16-rounded activations, acc[t] = sum_n bf16(v[n]) * w[t][n] in channel order.
+// Taps 0-7 run as packed pairs (each lane an ordinary fmaf, so the per-tap sums are
+// bit-identical to nine scalar chains), tap 8 alone.
+template <int CO>
+__device__ __forceinline__ void head_partials9(const float *v, const ConvParams &P, float *acc)
+{
+    unsigned long long pr[4] = {0ull, 0ull, 0ull, 0ull};
+    float a8 = 0.f;
+#pragma unroll
+    for (int n = 0; n < CO; ++n) {
+        const float a = bf16_round(v[n]);
+        unsigned long long aa;
+        asm("mov.b64 %0, {%1, %1};" : "=l"(aa) : "f"(a));
+#pragma unroll
+        for (int t = 0; t < 4; ++t) asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(pr[t]) : "l"(aa), "l"(P.head_w2[n][t]));
+        a8 = fmaf(a, P.head_w[8 * CO + n], a8);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[2 * t]), "=f"(acc[2 * t + 1]) : "l"(pr[t]));
+    acc[8] = a8;
+}
 
 
 // ---------------------------------------------------------------------------
@@ -389,7 +413,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         store_pixel<C::CO>(v, ui.out, 0, 1.f, ui.H, ui.W, y0 + j, x);
                         continue;
                     }
-                    if constexpr (KIND == KIND_HIDDEN && !TR && CH == 64) {
+                    if constexpr ((KIND == KIND_HIDDEN || KIND == KIND_FIRST) && !TR && CH == 64) {
                         if (!P.out_fp8) {
                             store_pixel_bias_relu_bf16(v, P.scale, P.bias, ui.out, ui.H, ui.W, y0 + j, x);
                             continue;
@@ -428,14 +452,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         const size_t plane = (size_t)ui.H * ui.W;
                         float *partials = ui.D->part ? ui.D->part : (float *)ui.out;
                         float acc[9];
-#pragma unroll
-                        for (int t = 0; t < 9; ++t) acc[t] = 0.f;
-#pragma unroll
-                        for (int n = 0; n < C::CO; ++n) {
-                            const float a = bf16_round(v[n]);
-#pragma unroll
-                            for (int t = 0; t < 9; ++t) acc[t] = fmaf(a, P.head_w[t * C::CO + n], acc[t]);   // nine chains
-                        }
+                        head_partials9<C::CO>(v, P, acc);
 #pragma unroll
                         for (int t = 0; t < 9; ++t) partials[t * plane + o] = acc[t];
                         if (TR && ui.D->save) store_pixel<C::CO>(v, ui.D->save, 0, 1.f, ui.H, ui.W, y0 + j, x);
@@ -765,14 +782,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                         const size_t plane = (size_t)ui.H * ui.W;
                         float *partials = ui.D->part ? ui.D->part : (float *)ui.out;
                         float acc[9];
-#pragma unroll
-                        for (int t = 0; t < 9; ++t) acc[t] = 0.f;
-#pragma unroll
-                        for (int n = 0; n < 64; ++n) {
-                            const float a = bf16_round(v[n]);
-#pragma unroll
-                            for (int t = 0; t < 9; ++t) acc[t] = fmaf(a, P.head_w[t * 64 + n], acc[t]);
-                        }
+                        head_partials9<64>(v, P, acc);
 #pragma unroll
                         for (int t = 0; t < 9; ++t) partials[t * plane + o] = acc[t];
                     } else {
@@ -953,6 +963,18 @@ ht_status launch_conv2(const ConvParams &P, cudaStream_t s)
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
+}
+
+// Packs P.head_w ([9 taps][co]) into the tap-pair layout the fused head reads.
+void fill_head_w2(ConvParams &P, int co)
+{
+    for (int n = 0; n < co; ++n)
+        for (int t = 0; t < 4; ++t) {
+            uint32_t lo, hi;
+            memcpy(&lo, &P.head_w[(2 * t) * co + n], 4);
+            memcpy(&hi, &P.head_w[(2 * t + 1) * co + n], 4);
+            P.head_w2[n][t] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+        }
 }
 
 uint16_t f32_to_bf16_rne(float f)
@@ -1248,7 +1270,10 @@ ht_status ht_tc_conv(const ht_tc_layer &a, cudaStream_t s)
         P.scale[c] = a.scale ? a.scale[c] : 1.f;
         P.bias[c] = a.bias ? a.bias[c] : 0.f;
     }
-    if (a.head_w) memcpy(P.head_w, a.head_w, sizeof(P.head_w));
+    if (a.head_w) {
+        memcpy(P.head_w, a.head_w, sizeof(P.head_w));
+        fill_head_w2(P, 64);
+    }
     P.out_inv_scale = 1.f;
     P.out_fp8 = 0;
     P.seed = a.seed;
@@ -1395,6 +1420,7 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
                         st = launch_conv<false, KIND_RES, false, 32>(P, s);
                     } else {
                         memcpy(P.head_w, p->h_headw, sizeof(float) * 9 * 32);
+                        fill_head_w2(P, 32);
                         st = launch_conv<false, KIND_RESHEAD, false, 32>(P, s);
                     }
                     if (st != HT_OK) return st;
@@ -1417,7 +1443,10 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
                 P.bias[c] = p->h_b[p->b_off[l] + c];
                 P.scale[c] = fp8 ? p->act_scale[l] * p->h_wscale[64 * (l - 1) + c] : 1.f;
             }
-            if (fuse_head) memcpy(P.head_w, p->h_headw, sizeof(P.head_w));
+            if (fuse_head) {
+                memcpy(P.head_w, p->h_headw, sizeof(P.head_w));
+                fill_head_w2(P, 64);
+            }
             P.out_inv_scale = out8 ? 1.f / p->act_scale[l + 1] : 1.f;
             P.out_fp8 = out8 ? 1 : 0;
             if (pair) {
