@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
             int k = 0, nrows = 0;
             bool unit_start = true;
             while (ok) {
-                ok = mbar_wait(smem_u32(&full[slot]), ph, s_abort, P.err);
+                ok = mbar_wait_poll(smem_u32(&full[slot]), ph, s_abort, P.err);
                 if (!ok) break;
                 if (unit_start) {
                     const volatile int *mv = (const volatile int *)&s_meta[slot];
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     unit_start = false;
                 }
                 if (k < nrows) {
-                    ok = mbar_wait(smem_u32(&bfree[k]), uit & 1u, s_abort, P.err);   // block k enters use
+                    ok = mbar_wait_poll(smem_u32(&bfree[k]), uit & 1u, s_abort, P.err);   // block k enters use
                     if (!ok) break;
                 }
                 tc_fence_after();

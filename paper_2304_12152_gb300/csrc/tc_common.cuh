@@ -98,6 +98,46 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Non-blocking test of a phase (never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the MMA-issuing thread: polls without suspending, so the thread
+// resumes issuing as soon as the phase completes; the same expiry record as mbar_wait.
+__device__ __forceinline__ bool mbar_wait_poll(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
+{
+    if (mbar_test_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_test_wait(bar, parity)) return true;
+        if ((it & 63u) == 0) {
+            if (*abort_flag) return false;
+            const uint64_t el = globaltimer_ns() - t0;
+            if (el > kTimeoutNs || it > (1u << 30)) {
+                *abort_flag = 1;
+                atomicExch(err, (int)HT_ERR_TIMEOUT);
+                if (atomicCAS(err + 1, 0, 1) == 0) {
+                    err[2] = (int)bar;
+                    err[3] = (int)((blockDim.x << 16) | (threadIdx.x >> 5));
+                    err[4] = (int)blockIdx.x;
+                    err[5] = (int)it;
+                    *reinterpret_cast<unsigned long long *>(err + 6) = el;
+                }
+                return false;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
