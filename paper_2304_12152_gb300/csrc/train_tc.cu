@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
     uint64_t *bars = (uint64_t *)(s_g + WG_NSG * WG_GSLOT);
     uint64_t *a_full = bars, *a_empty = bars + WG_NSA, *g_full = bars + 2 * WG_NSA,
              *g_empty = bars + 2 * WG_NSA + WG_NSG, *tzero = bars + 2 * WG_NSA + 2 * WG_NSG, *done = tzero + 1;
-    uint32_t *s_tmem = (uint32_t *)(done + 1);
+    int2 *a_meta = (int2 *)(done + 1);                          // (r, nrows) of the activation row in each slot
+    int2 *g_meta = a_meta + WG_NSA;                             // (j, nrows) of the gradient row in each slot
+    uint32_t *s_tmem = (uint32_t *)(g_meta + WG_NSG);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -157,6 +159,7 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
                     if (zeroed) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) {
+                        a_meta[slot] = make_int2(r, ui.nrows);
                         const uint32_t run = (uint32_t)(hi - lo) * 16u;
                         if (row_in && hi > lo) {
                             mbar_arrive_expect_tx(smem_u32(&a_full[slot]), run * 8u * (uint32_t)ncopy);
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
                     }
                     __syncwarp();
                     if (lane == 0) {
+                        g_meta[slot] = make_int2(r - 2, ui.nrows);
                         const uint32_t run = (uint32_t)nin * 16u;
                         mbar_arrive_expect_tx(smem_u32(&g_full[slot]), run * 8u);
                         const uint8_t *g = ui.out;
@@ -209,6 +213,25 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
                 }
             }
         }
+        if (ok) {
+            // end markers (k = -1) for the MMA warp (activation ring) and the bias-sum warps
+            // (gradient ring); each is its slot's newest phase, which the drain below waits for
+            const int sa = (int)(la % WG_NSA), sg = (int)(lg % WG_NSG);
+            int got = 0;
+            if (lane == 0)
+                got = (mbar_wait(smem_u32(&a_empty[sa]), ((la / WG_NSA) & 1u) ^ 1u, s_abort, P.err) &&
+                       mbar_wait(smem_u32(&g_empty[sg]), ((lg / WG_NSG) & 1u) ^ 1u, s_abort, P.err)) ? 1 : 0;
+            if (__shfl_sync(0xffffffffu, got, 0)) {
+                if (lane == 0) {
+                    a_meta[sa] = make_int2(-1, 0);
+                    mbar_arrive(smem_u32(&a_full[sa]));
+                    g_meta[sg] = make_int2(-1, 0);
+                    mbar_arrive(smem_u32(&g_full[sg]));
+                }
+                a_last[sa] = (int)la;
+                g_last[sg] = (int)lg;
+            }
+        }
         if (lane == 0) {
             for (int s2 = 0; s2 < WG_NSA; ++s2)
                 if (a_last[s2] >= 0)
@@ -219,31 +242,32 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ------------------------- MMA issuer -------------------------
-        auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
-            int got = 0;
-            if (lane == 0) got = mbar_wait(bar, par, s_abort, P.err) ? 1 : 0;
-            return __shfl_sync(0xffffffffu, got, 0) != 0;
-        };
-        // MN-major, no swizzle: LBO = stride between 8-pixel groups (K), SBO = stride
-        // between 8-channel groups (M or N)
-        const uint64_t a_base = sdesc(smem_u32(s_a), 128, ROW_PX * 16);
-        const uint64_t g_base = sdesc(smem_u32(s_g), 128, TILE_M * 16);
-        bool ok = wait1(smem_u32(tzero), 0);
-        if (ok) tc_fence_after();
-        uint32_t qa = 0, qg = 0;
-        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
-            const int nrows = unit_info(P.imgs, P.n_imgs, 0, u).nrows;
-            const uint32_t base = qa;
-            ok = wait1(smem_u32(&a_full[base % WG_NSA]), (base / WG_NSA) & 1u) &&
-                 wait1(smem_u32(&a_full[(base + 1) % WG_NSA]), ((base + 1) / WG_NSA) & 1u);
-            for (int j = 0; j < nrows && ok; ++j, ++qg) {
-                const uint32_t qn = base + (uint32_t)j + 2u;
-                ok = wait1(smem_u32(&a_full[qn % WG_NSA]), (qn / WG_NSA) & 1u) &&
-                     wait1(smem_u32(&g_full[qg % WG_NSG]), (qg / WG_NSG) & 1u);
+        // ------------------------- MMA issuer (lane 0) -------------------------
+        // Each unit's row count comes from the producer's record in the activation
+        // ring (an end marker closes the sequence), so no image-table lookups sit in
+        // the issuing thread.
+        if (lane == 0) {
+            // MN-major, no swizzle: LBO = stride between 8-pixel groups (K), SBO = stride
+            // between 8-channel groups (M or N)
+            const uint64_t a_base = sdesc(smem_u32(s_a), 128, ROW_PX * 16);
+            const uint64_t g_base = sdesc(smem_u32(s_g), 128, TILE_M * 16);
+            bool ok = mbar_wait(smem_u32(tzero), 0, s_abort, P.err);
+            if (ok) tc_fence_after();
+            uint32_t qa = 0, qg = 0;
+            while (ok) {
+                const uint32_t base = qa;
+                ok = mbar_wait_poll(smem_u32(&a_full[base % WG_NSA]), (base / WG_NSA) & 1u, s_abort, P.err);
                 if (!ok) break;
-                tc_fence_after();
-                if (lane == 0) {
+                const volatile int *mv = (const volatile int *)&a_meta[base % WG_NSA];
+                const int k0 = mv[0], nrows = mv[1];
+                if (k0 < 0) break;
+                ok = mbar_wait_poll(smem_u32(&a_full[(base + 1) % WG_NSA]), ((base + 1) / WG_NSA) & 1u, s_abort, P.err);
+                for (int j = 0; j < nrows && ok; ++j, ++qg) {
+                    const uint32_t qn = base + (uint32_t)j + 2u;
+                    ok = mbar_wait_poll(smem_u32(&a_full[qn % WG_NSA]), (qn / WG_NSA) & 1u, s_abort, P.err) &&
+                         mbar_wait_poll(smem_u32(&g_full[qg % WG_NSG]), (qg / WG_NSG) & 1u, s_abort, P.err);
+                    if (!ok) break;
+                    tc_fence_after();
                     const uint64_t b_q = g_base + (uint64_t)(((qg % WG_NSG) * (uint32_t)WG_GSLOT) >> 4);
 #pragma unroll
                     for (int pair = 0; pair < 2; ++pair) {
@@ -261,18 +285,13 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
                     mma_commit(smem_u32(&g_empty[qg % WG_NSG]));
                     mma_commit(smem_u32(&a_empty[(base + (uint32_t)j) % WG_NSA]));
                 }
-                __syncwarp();
-            }
-            if (!ok) break;
-            if (lane == 0) {
+                if (!ok) break;
                 mma_commit(smem_u32(&a_empty[(base + (uint32_t)nrows) % WG_NSA]));
                 mma_commit(smem_u32(&a_empty[(base + (uint32_t)nrows + 1u) % WG_NSA]));
+                qa = base + (uint32_t)nrows + 2u;
             }
-            __syncwarp();
-            qa = base + (uint32_t)nrows + 2u;
+            mma_commit(smem_u32(done));     // all issued MMAs, aborted or not
         }
-        if (lane == 0) mma_commit(smem_u32(done));     // all issued MMAs, aborted or not
-        __syncwarp();
     } else {
         // ------------------------- epilogue -------------------------
         const int quarter = warp & 3;
@@ -289,17 +308,14 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
         float cs[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) cs[i] = 0.f;
-        uint32_t qg = 0;
-        bool ok = true;
-        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
-            const int nrows = unit_info(P.imgs, P.n_imgs, 0, u).nrows;
-            for (int j = 0; j < nrows; ++j, ++qg) {
-                int got = 0;
-                if (lane == 0) got = mbar_wait(smem_u32(&g_full[qg % WG_NSG]), (qg / WG_NSG) & 1u, s_abort, P.err) ? 1 : 0;
-                if (!__shfl_sync(0xffffffffu, got, 0)) {
-                    ok = false;
-                    break;
+        for (uint32_t qg = 0;; ++qg) {
+            {
+                int got = 0, k = 0;
+                if (lane == 0) {
+                    got = mbar_wait(smem_u32(&g_full[qg % WG_NSG]), (qg / WG_NSG) & 1u, s_abort, P.err) ? 1 : 0;
+                    if (got) k = ((const volatile int *)&g_meta[qg % WG_NSG])[0];
                 }
+                if (!__shfl_sync(0xffffffffu, got, 0) || __shfl_sync(0xffffffffu, k, 0) < 0) break;
                 const uint8_t *src = s_g + (qg % WG_NSG) * WG_GSLOT + ((size_t)chunk * TILE_M + pg * 8) * 16;
 #pragma unroll
                 for (int px = 0; px < 8; ++px) {
