@@ -119,16 +119,19 @@ def test_many_short_units_every_schedule():
 PAIR_SHAPES = [(300, 200), (37, 515), (129, 131), (8, 9), (1, 1), (5, 700), (70, 256), (17, 257)]
 
 
-@pytest.mark.parametrize("prec", [N.HT_BF16, N.HT_FP8_E4M3])
-def test_cta_pair_form_matches_single_cta_form(prec):
+@pytest.mark.parametrize("prec,head", [(N.HT_BF16, N.HT_HEAD_SIGMOID), (N.HT_FP8_E4M3, N.HT_HEAD_SIGMOID),
+                                       (N.HT_FP8_E4M3, N.HT_HEAD_SOFTMAX), (N.HT_BF16, N.HT_HEAD_MULTITONE)])
+def test_cta_pair_form_matches_single_cta_form(prec, head):
     """The CTA-pair form of the 64 -> 64 layers (M = 256 MMAs over a 256-pixel tile,
     weights split by N between the two CTAs) accumulates every output pixel in the same
-    order as the single-CTA form, so bits and probabilities are equal bit for bit.
-    Widths leave the second CTA of a pair partly or wholly outside the image; heights
-    leave short row bands."""
-    ws, bs = synth.he_normal_policy(synth.NET_WIDE, 11)
-    bs = synth.random_biases(synth.NET_WIDE, 3)
-    pol = api.Policy(synth.NET_WIDE, ws, bs, precision=prec)
+    order as the single-CTA form, so bits and probabilities are equal bit for bit, under
+    every head that follows those layers (1-logit sigmoid, 4-logit softmax, multitoning
+    prototype).  Widths leave the second CTA of a pair partly or wholly outside the
+    image; heights leave short row bands."""
+    chs = synth.NET_WIDE_K4 if head == N.HT_HEAD_SOFTMAX else synth.NET_WIDE
+    ws, bs = synth.he_normal_policy(chs, 11)
+    bs = synth.random_biases(chs, 3)
+    pol = api.Policy(chs, ws, bs, head=head, precision=prec, levels=4)
     imgs = [torch.from_numpy(synth.contone_image(h, w, seed=12, index=i)).cuda() for i, (h, w) in enumerate(PAIR_SHAPES)]
     if prec == N.HT_FP8_E4M3:
         pol.calibrate(imgs[0], seed=9)
