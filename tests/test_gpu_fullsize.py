@@ -9,7 +9,8 @@ policy is fully convolutional and the noise is keyed by the global pixel index, 
 crop's outputs are exact functions of the crop plus an L-pixel halo).  Rules as in the
 small-size tests: e4m3 form against the e4m3-emulating oracle, mismatched actions at most
 1% of the decided pixels; BF16 form against the BF16-emulating oracle, |dp| max 4e-3 and
-99.9th percentile 2e-3, mismatches at most 1e-3 of the decided pixels."""
+99.9th percentile 2e-3, mismatches at most 1e-3 of the decided pixels.  The training
+step's losses, which the oracle computes whole, are checked at the benchmark's size too."""
 import math
 
 import numpy as np
@@ -112,3 +113,44 @@ def test_uneven_batch_full_size_sampled():
     d = np.abs(np.concatenate(diffs))
     assert d.max() < 4e-3 and np.quantile(d, 0.999) < 2e-3, (d.max(), np.quantile(d, 0.999))
     assert tot_bad <= max(1, 1e-3 * tot_n), (tot_bad, tot_n)
+
+
+def test_training_step_full_size_losses():
+    """The benchmark's training step (16 generator crops of 256^2, 4 constant-gray patches
+    {0.1, 0.25, 0.5, 0.75} of 256^2, S = 4 Bernoulli samples, LE estimator, 32 x 16-bin
+    anisotropy loss, w_a = 0.002, BF16 form): its losses against the BF16-emulating oracle
+    computed whole (forward, samples, rewards and toggle deltas of all 64 crop-samples,
+    anisotropy loss of the gray patches).  As in the small BF16 step test the two sides'
+    samples differ wherever |p - u| is below the forward's BF16 error, so the losses are held
+    to 1e-3 relative."""
+    chs = synth.NET_WIDE
+    ws, bs = synth.he_normal_policy(chs, 3)
+    crops = [synth.contone_image(256, 256, seed=3, index=i) for i in range(16)]
+    levels = [0.1, 0.25, 0.5, 0.75]
+    S, seed, w_a = 4, 1, 0.002
+    pol = api.Policy(chs, ws, bs, precision=N.HT_BF16)
+    tr = api.Trainer(pol, (256, 256), max_crops=16, n_samples=S, n_gray=4, gray_n=256, las_mode=1, n_rad=32,
+                     n_ang=16, w_a=w_a)
+    losses = tr.forward([torch.from_numpy(c).cuda() for c in crops], levels, seed)
+    api.sync()
+    n = len(crops)
+    l_marl, rs = 0.0, []
+    for i, c in enumerate(crops):
+        _, p, _ = O.forward(c, ws, bs, noise_seed=seed, image=i, quant=1)
+        for s in range(S):
+            u = O.uniform_map(seed, i, 1 + s, 256, 256)
+            hb = (u < p[0]).astype(np.uint8)
+            r = O.reward(c, hb)
+            dR = O.toggle_delta(c, hb).reshape(256, 256)
+            val, _ = O.le_surrogate(p[0], hb, dR, r["R"])
+            l_marl += val / (n * S)
+            rs.append(r["R"])
+    l_as = 0.0
+    for g, lev in enumerate(levels):
+        c = np.full((256, 256), lev, np.float32)
+        _, p, _ = O.forward(c, ws, bs, noise_seed=seed, image=n + g, quant=1)
+        l_as += O.anisotropy_loss(p[0], mode=1, n_rad=32, n_ang=16)["loss"] / len(levels)
+    ref = (l_marl + w_a * l_as, l_marl, l_as, float(np.mean(rs)))
+    print("losses", losses, "oracle", ref)
+    for k in range(4):
+        assert abs(losses[k] - ref[k]) <= 1e-3 * abs(ref[k]) + 1e-7, (k, losses, ref)
