@@ -267,28 +267,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------- MMA issuer -------------------------
-        // Lane 0 alone runs the schedule: it takes each staged row's (k, nrows)
-        // from the producer's per-slot record, so no image-table lookups or warp
-        // collectives sit between one row's MMAs and the next.  Descriptors = base
-        // descriptor + compile-time / small offsets added to the 14-bit
-        // start-address field (addresses stay below 256 KB).
-        if (lane == 0) {
-            // (k, nrows) is read from the producer's record only where a unit starts;
-            // within a unit k steps by one, so nothing but the barrier checks sits
-            // between one row's MMAs and the next.
+        // The whole warp runs the schedule (its state stays warp-uniform) and one
+        // elected lane issues the MMAs and commits.  Each staged row's (k, nrows)
+        // comes from the producer's per-slot record, read only where a unit starts;
+        // within a unit k steps by one, so nothing but the barrier checks sits between
+        // one row's MMAs and the next.  Descriptors = base descriptor + compile-time /
+        // small offsets added to the 14-bit start-address field (addresses stay below
+        // 256 KB).
+        {
+            const uint32_t el = elect_one();
             const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
             const uint64_t b_base = sdesc(smem_u32(s_w), 3 * C::NOUT * 16, 128);
-            bool ok = mbar_wait(smem_u32(wbar), 0, s_abort, P.err);
+            bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(wbar), 0, s_abort, P.err));
             uint32_t slot = 0, ph = 0, uit = 0;
             int k = 0, nrows = 0;
             bool unit_start = true;
             while (ok) {
-                ok = mbar_wait_poll(smem_u32(&full[slot]), ph, s_abort, P.err);
+                ok = mbar_wait_poll_warp(smem_u32(&full[slot]), ph, s_abort, P.err);
                 if (!ok) break;
                 if (unit_start) {
                     const volatile int *mv = (const volatile int *)&s_meta[slot];
-                    k = mv[0];
-                    nrows = mv[1];
+                    k = __shfl_sync(0xffffffffu, mv[0], 0);
+                    nrows = __shfl_sync(0xffffffffu, mv[1], 0);
                     if (k < 0) break;
                     unit_start = false;
                     if (C::MMA8 && nrows == RU && P.ru == RU) {
@@ -300,11 +300,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 #pragma unroll
                         for (int kk = 0; kk < RU + 2; ++kk) {
                             if (kk > 0) {
-                                ok = mbar_wait_poll(smem_u32(&full[slot]), ph, s_abort, P.err);
+                                ok = mbar_wait_poll_warp(smem_u32(&full[slot]), ph, s_abort, P.err);
                                 if (!ok) break;
                             }
                             if (kk < RU) {
-                                ok = mbar_wait_poll(smem_u32(&bfree[kk]), uit & 1u, s_abort, P.err);
+                                ok = mbar_wait_poll_warp(smem_u32(&bfree[kk]), uit & 1u, s_abort, P.err);
                                 if (!ok) break;
                             }
                             tc_fence_after();
@@ -320,11 +320,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                             for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                                 for (int ks = 0; ks < C::KSTEPS; ++ks)
-                                    mma_ss<C::MMA8>(d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
+                                    mma_ss_el<C::MMA8>(el, d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
                                                     b_q + (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4),
-                                                    idesc, 1u);
-                            mma_commit(smem_u32(&empty[slot]));
-                            if (kk >= 2) mma_commit(smem_u32(&bfull[kk - 2]));
+                                                    idesc);
+                            mma_commit_el(el, smem_u32(&empty[slot]));
+                            if (kk >= 2) mma_commit_el(el, smem_u32(&bfull[kk - 2]));
                             if (++slot == (uint32_t)NSLOT) {
                                 slot = 0;
                                 ph ^= 1u;
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     }
                 }
                 if (k < nrows) {
-                    ok = mbar_wait_poll(smem_u32(&bfree[k]), uit & 1u, s_abort, P.err);   // block k enters use
+                    ok = mbar_wait_poll_warp(smem_u32(&bfree[k]), uit & 1u, s_abort, P.err);   // block k enters use
                     if (!ok) break;
                 }
                 tc_fence_after();
@@ -352,11 +352,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                     for (int ks = 0; ks < C::KSTEPS; ++ks)
-                        mma_ss<C::MMA8>(d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
+                        mma_ss_el<C::MMA8>(el, d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
                                         b_q + (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4),
-                                        idesc, 1u);
-                mma_commit(smem_u32(&empty[slot]));
-                if (k >= 2) mma_commit(smem_u32(&bfull[k - 2]));     // output row k-2 complete
+                                        idesc);
+                mma_commit_el(el, smem_u32(&empty[slot]));
+                if (k >= 2) mma_commit_el(el, smem_u32(&bfull[k - 2]));     // output row k-2 complete
                 if (++slot == (uint32_t)NSLOT) {
                     slot = 0;
                     ph ^= 1u;
@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     // wait cannot tell phase k from phase k + 2, so no barrier may run two phases
                     // ahead of its consumer (two short units in a row would otherwise do that).
                     for (int j = nrows; j < P.ru && ok; ++j) {
-                        ok = mbar_wait(smem_u32(&bfree[j]), uit & 1u, s_abort, P.err);
-                        if (ok) mma_commit(smem_u32(&bfull[j]));
+                        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bfree[j]), uit & 1u, s_abort, P.err));
+                        if (ok) mma_commit_el(el, smem_u32(&bfull[j]));
                     }
                     ++uit;
                     unit_start = true;
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 }
             }
             // drain: all issued MMAs complete before TMEM is released
-            mma_commit(smem_u32(drain));
+            mma_commit_el(el, smem_u32(drain));
             mbar_wait(smem_u32(drain), 0, s_abort, P.err, true);
         }
     } else {
@@ -692,12 +692,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
         }
         __syncwarp();
     } else if (warp == 1 && leader) {
-        // ------------------------- MMA issuer (first CTA, lane 0) -------------------------
-        if (lane == 0) {
+        // ------------------------- MMA issuer (first CTA, whole warp, elected lane issues) ----------
+        {
+            const uint32_t el = elect_one();
             const uint64_t a_base = sdesc(smem_u32(s_rows), ROW_PX * 16, 128);
             const uint32_t w_addr = smem_u32(s_w);
             auto wait1 = [&](uint32_t bar, uint32_t par) -> bool {
-                return mbar_wait_cl(bar, par, s_abort, peer_abort, P.err);
+                return __all_sync(0xffffffffu, mbar_wait_cl(bar, par, s_abort, peer_abort, P.err));
             };
             bool ok = wait1(smem_u32(wbar), 0) && wait1(smem_u32(pwbar), 0);
             uint32_t slot = 0, ph = 0, uit = 0;
@@ -708,8 +709,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                 if (!ok) break;
                 if (unit_start) {
                     const volatile int *mv = (const volatile int *)&s_meta[slot];
-                    k = mv[0];
-                    nrows = mv[1];
+                    k = __shfl_sync(0xffffffffu, mv[0], 0);
+                    nrows = __shfl_sync(0xffffffffu, mv[1], 0);
                     if (k < 0) break;
                     unit_start = false;
                 }
@@ -730,10 +731,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                 for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                     for (int ks = 0; ks < C::KSTEPS; ++ks)
-                        mma_ss_pair<FP8>(d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
-                                         b_q + (uint64_t)(((dx * C::KSTEPS + ks) * PV_GROUP_BYTES) >> 4), idesc, 1u);
-                mma_commit_pair(smem_u32(&empty[slot]));
-                if (k >= 2) mma_commit_pair(smem_u32(&bfull[k - 2]));       // output row k-2 complete
+                        mma_ss_pair_el<FP8>(el, d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
+                                         b_q + (uint64_t)(((dx * C::KSTEPS + ks) * PV_GROUP_BYTES) >> 4), idesc);
+                mma_commit_pair_el(el, smem_u32(&empty[slot]));
+                if (k >= 2) mma_commit_pair_el(el, smem_u32(&bfull[k - 2]));       // output row k-2 complete
                 if (++slot == (uint32_t)NSLOT) {
                     slot = 0;
                     ph ^= 1u;
@@ -742,7 +743,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                     // blocks this unit leaves unused still go through one full/free round
                     for (int j = nrows; j < P.ru && ok; ++j) {
                         ok = wait1(smem_u32(&bfree[j]), uit & 1u);
-                        if (ok) mma_commit_pair(smem_u32(&bfull[j]));
+                        if (ok) mma_commit_pair_el(el, smem_u32(&bfull[j]));
                     }
                     ++uit;
                     unit_start = true;
@@ -751,7 +752,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
                 }
             }
             // drain: every issued MMA completes before TMEM is released
-            mma_commit_pair(smem_u32(drain));
+            mma_commit_pair_el(el, smem_u32(drain));
             mbar_wait_cl(smem_u32(drain), 0, s_abort, 0u, P.err, true);
         }
     } else if (warp == 1) {

@@ -138,6 +138,12 @@ __device__ __forceinline__ bool mbar_wait_poll(uint32_t bar, uint32_t parity, vo
     }
 }
 
+// mbar_wait_poll by every lane of a warp, with a warp-uniform result.
+__device__ __forceinline__ bool mbar_wait_poll_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
+{
+    return __all_sync(0xffffffffu, mbar_wait_poll(bar, parity, abort_flag, err));
+}
+
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -198,6 +204,40 @@ __device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a, uint64_t b, 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Warp-wide issuing: the whole warp runs the MMA schedule, so its state (slot, row,
+// descriptors) is warp-uniform, and the one lane chosen by elect_one() issues each MMA
+// and commit under a predicate, with no divergent branch around them.
+__device__ __forceinline__ uint32_t elect_one()
+{
+    uint32_t e;
+    asm volatile("{\n\t.reg .pred p;\n\telect.sync _|p, 0xffffffff;\n\tselp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(e));
+    return e;
+}
+template <bool FP8>
+__device__ __forceinline__ void mma_ss_el(uint32_t el, uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc)
+{
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred e;\n\tsetp.ne.b32 e, %4, 0;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, 1;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(el)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred e;\n\tsetp.ne.b32 e, %4, 0;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(el)
+            : "memory");
+    }
+}
+__device__ __forceinline__ void mma_commit_el(uint32_t el, uint32_t bar)
+{
+    asm volatile("{\n\t.reg .pred e;\n\tsetp.ne.b32 e, %1, 0;\n\t"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(bar),
+                 "r"(el)
+                 : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -306,6 +346,32 @@ __device__ __forceinline__ void mma_commit_pair(uint32_t bar)
     asm volatile(
         "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
         "h"((uint16_t)3)
+        : "memory");
+}
+// elected-lane forms of the two above (see elect_one)
+template <bool FP8>
+__device__ __forceinline__ void mma_ss_pair_el(uint32_t el, uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc)
+{
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred e;\n\tsetp.ne.b32 e, %4, 0;\n\t"
+            "@e tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, 1;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(el)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred e;\n\tsetp.ne.b32 e, %4, 0;\n\t"
+            "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, 1;\n\t}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(el)
+            : "memory");
+    }
+}
+__device__ __forceinline__ void mma_commit_pair_el(uint32_t el, uint32_t bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\tsetp.ne.b32 e, %2, 0;\n\t"
+        "@e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n\t}\n" ::"r"(bar),
+        "h"((uint16_t)3), "r"(el)
         : "memory");
 }
 

@@ -242,30 +242,32 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ------------------------- MMA issuer (lane 0) -------------------------
-        // Each unit's row count comes from the producer's record in the activation
-        // ring (an end marker closes the sequence), so no image-table lookups sit in
-        // the issuing thread.
-        if (lane == 0) {
+        // ------------------------- MMA issuer -------------------------
+        // The whole warp runs the schedule (warp-uniform state) and one elected lane
+        // issues the MMAs and commits.  Each unit's row count comes from the producer's
+        // record in the activation ring (an end marker closes the sequence), so no
+        // image-table lookups sit in the issuing loop.
+        {
+            const uint32_t el = elect_one();
             // MN-major, no swizzle: LBO = stride between 8-pixel groups (K), SBO = stride
             // between 8-channel groups (M or N)
             const uint64_t a_base = sdesc(smem_u32(s_a), 128, ROW_PX * 16);
             const uint64_t g_base = sdesc(smem_u32(s_g), 128, TILE_M * 16);
-            bool ok = mbar_wait(smem_u32(tzero), 0, s_abort, P.err);
+            bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(tzero), 0, s_abort, P.err));
             if (ok) tc_fence_after();
             uint32_t qa = 0, qg = 0;
             while (ok) {
                 const uint32_t base = qa;
-                ok = mbar_wait_poll(smem_u32(&a_full[base % WG_NSA]), (base / WG_NSA) & 1u, s_abort, P.err);
+                ok = mbar_wait_poll_warp(smem_u32(&a_full[base % WG_NSA]), (base / WG_NSA) & 1u, s_abort, P.err);
                 if (!ok) break;
                 const volatile int *mv = (const volatile int *)&a_meta[base % WG_NSA];
-                const int k0 = mv[0], nrows = mv[1];
+                const int k0 = __shfl_sync(0xffffffffu, mv[0], 0), nrows = __shfl_sync(0xffffffffu, mv[1], 0);
                 if (k0 < 0) break;
-                ok = mbar_wait_poll(smem_u32(&a_full[(base + 1) % WG_NSA]), ((base + 1) / WG_NSA) & 1u, s_abort, P.err);
+                ok = mbar_wait_poll_warp(smem_u32(&a_full[(base + 1) % WG_NSA]), ((base + 1) / WG_NSA) & 1u, s_abort, P.err);
                 for (int j = 0; j < nrows && ok; ++j, ++qg) {
                     const uint32_t qn = base + (uint32_t)j + 2u;
-                    ok = mbar_wait_poll(smem_u32(&a_full[qn % WG_NSA]), (qn / WG_NSA) & 1u, s_abort, P.err) &&
-                         mbar_wait_poll(smem_u32(&g_full[qg % WG_NSG]), (qg / WG_NSG) & 1u, s_abort, P.err);
+                    ok = mbar_wait_poll_warp(smem_u32(&a_full[qn % WG_NSA]), (qn / WG_NSA) & 1u, s_abort, P.err) &&
+                         mbar_wait_poll_warp(smem_u32(&g_full[qg % WG_NSG]), (qg / WG_NSG) & 1u, s_abort, P.err);
                     if (!ok) break;
                     tc_fence_after();
                     const uint64_t b_q = g_base + (uint64_t)(((qg % WG_NSG) * (uint32_t)WG_GSLOT) >> 4);
@@ -278,19 +280,19 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
                             const uint32_t d = tmem_base + (uint32_t)(dx * 2 + pair) * 64u;
 #pragma unroll
                             for (int ks = 0; ks < 8; ++ks)
-                                mma_ss<false>(d, a_q + (uint64_t)((ks * 256) >> 4), b_q + (uint64_t)((ks * 256) >> 4),
-                                              kWgIdesc, 1u);
+                                mma_ss_el<false>(el, d, a_q + (uint64_t)((ks * 256) >> 4), b_q + (uint64_t)((ks * 256) >> 4),
+                                                 kWgIdesc);
                         }
                     }
-                    mma_commit(smem_u32(&g_empty[qg % WG_NSG]));
-                    mma_commit(smem_u32(&a_empty[(base + (uint32_t)j) % WG_NSA]));
+                    mma_commit_el(el, smem_u32(&g_empty[qg % WG_NSG]));
+                    mma_commit_el(el, smem_u32(&a_empty[(base + (uint32_t)j) % WG_NSA]));
                 }
                 if (!ok) break;
-                mma_commit(smem_u32(&a_empty[(base + (uint32_t)nrows) % WG_NSA]));
-                mma_commit(smem_u32(&a_empty[(base + (uint32_t)nrows + 1u) % WG_NSA]));
+                mma_commit_el(el, smem_u32(&a_empty[(base + (uint32_t)nrows) % WG_NSA]));
+                mma_commit_el(el, smem_u32(&a_empty[(base + (uint32_t)nrows + 1u) % WG_NSA]));
                 qa = base + (uint32_t)nrows + 2u;
             }
-            mma_commit(smem_u32(done));     // all issued MMAs, aborted or not
+            mma_commit_el(el, smem_u32(done));     // all issued MMAs, aborted or not
         }
     } else {
         // ------------------------- epilogue -------------------------
