@@ -17,7 +17,7 @@ A step = one ht_halftone call over the whole batch.
   fp32_plain : the plain FP32 CUDA-core form of the same net on the same batch
   cpu_baseline: the FP64 C oracle on a bounded crop of the same workload (host cores)
 
---impl reference times the oracle (the reference arm of this build) on bounded crops.
+--impl reference times the oracle (the benchmark's reference arm) on bounded crops.
 Multi-GPU (torchrun): independent replicas, weak scaling, max time over ranks.
 """
 from __future__ import annotations

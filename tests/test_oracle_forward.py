@@ -115,6 +115,28 @@ def test_sampling_rules():
     assert abs(b.mean() - 0.3) < 5 * np.sqrt(0.21 / b.size)
 
 
+def test_sampled_level_frequencies_follow_the_probabilities():
+    """Sampling (Algorithm 1, TEST with stochastic actions; the K-level head of Sec. VI-E):
+    over a 512 x 512 map with the same per-pixel distribution, the drawn level counts match
+    the probabilities by a chi-square test (3 degrees of freedom, 99.99% quantile 21.1), and a
+    binary map's fraction of ones matches p within 4.5 standard errors.  Independent of the
+    inverse-CDF rule as written: a level-index shift or a reversed comparison fails it."""
+    h = w = 512
+    n = h * w
+    q4 = np.array([0.1, 0.2, 0.3, 0.4])
+    probs = np.broadcast_to(q4[:, None, None], (4, h, w)).copy()
+    lev, _ = O.sample(probs, h, w, (0, 0, h, w), 1, 7)
+    cnt = np.bincount(lev.ravel(), minlength=4)
+    assert cnt.sum() == n
+    chi2 = float((((cnt - n * q4) ** 2) / (n * q4)).sum())
+    assert chi2 < 21.1, (cnt, chi2)
+    for p in (0.05, 0.5, 0.8):
+        pm = np.full((1, h, w), p)
+        hb, _ = O.sample(pm, h, w, (0, 0, h, w), 1, 11)
+        frac = hb.mean()
+        assert abs(frac - p) < 4.5 * np.sqrt(p * (1 - p) / n), (p, frac)
+
+
 def test_softmax_levels_sampling():
     K, h, w = 4, 64, 64
     rng = np.random.default_rng(3)
