@@ -1,0 +1,144 @@
+"""Mutation check of the oracle's pins (test infrastructure, run by hand; not collected by
+pytest).
+
+Plants one plausible mistake at a time in a scratch copy of the repository -- a wrong
+constant, a dropped term, a flipped sign or index, a transposed operand, a misplaced ring
+or bin edge -- in the C oracle or its Python helpers, rebuilds the oracle there, and runs the
+CPU suite (`-m "not gpu"`).  Every mutation must make some test fail ("killed"); one that
+passes ("SURVIVED") marks a part of the oracle its pins do not fix, unless the mutation
+cannot change any result (an equivalent mutation; the two known ones are listed below).
+
+    python tests/mutation_check.py --scratch /path/to/empty/dir [name-filter ...]
+
+Known equivalent mutations: including the DC ring (it holds one sample, and rings with fewer
+than two samples are skipped) and mapping frequency index n/2 to +n/2 instead of -n/2 (the
+radius is unchanged, and the binned form excludes radii >= n/2).
+"""
+import argparse
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+C = "oracle/ht_oracle.c"
+P = "oracle/__init__.py"
+M = [
+    ("philox multiplier", C, "0xD2511F53u * (uint64_t)c0", "0xD2511F55u * (uint64_t)c0"),
+    ("philox 9 rounds", C, "for (int r = 0; r < 10; ++r) {", "for (int r = 0; r < 9; ++r) {"),
+    ("philox key bump", C, "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;"),
+    ("philox lo swap", C, "uint32_t n1 = lo1;", "uint32_t n1 = lo0;"),
+    ("uniform bits", C, "(double)(x >> 8) * (1.0 / 16777216.0)", "(double)(x >> 9) * (1.0 / 8388608.0)"),
+    ("uniform lane", C, "uint32_t x = out[g & 3u];", "uint32_t x = out[(g + 1) & 3u];"),
+    ("counter image/stream", C, "{(uint32_t)(g >> 2), image, stream, 0u}", "{(uint32_t)(g >> 2), stream, image, 0u}"),
+    ("bf16 spacing", C, "double q = ldexp(1.0, e - 8);", "double q = ldexp(1.0, e - 9);"),
+    ("bf16 truncation", C, "return nearbyint(x / q) * q;        /* default", "return trunc(x / q) * q;        /* default"),
+    ("e4m3 saturation", C, "if (r > 448.0) r = 448.0;", "if (r > 480.0) r = 480.0;"),
+    ("e4m3 subnormal spacing", C, "q = ldexp(1.0, -9);", "q = ldexp(1.0, -10);"),
+    ("e4m3 mantissa bits", C, "q = ldexp(1.0, e - 1 - 3);", "q = ldexp(1.0, e - 1 - 2);"),
+    ("e4m3 weight scale", C, "s = amax > 0.0 ? amax / 448.0 : 1.0;", "s = amax > 0.0 ? amax / 240.0 : 1.0;"),
+    ("forward no bias", C, "for (int k = 0; k < oh * ow; ++k) op[k] = (double)biases[l][o];", "for (int k = 0; k < oh * ow; ++k) op[k] = 0.0;"),
+    ("forward kernel flip", C, "double wv = wq[l][(((size_t)o * ci + i) * 3 + ky) * 3 + kx];", "double wv = wq[l][(((size_t)o * ci + i) * 3 + (2 - ky)) * 3 + kx];"),
+    ("forward no relu", C, "double v = op[k] > 0.0 ? op[k] : 0.0;", "double v = op[k];"),
+    ("forward noise stream", C, "or_uniform(noise_seed, image, 0u, (uint64_t)gy * (uint64_t)w + (uint64_t)gx);", "or_uniform(noise_seed, image, 1u, (uint64_t)gy * (uint64_t)w + (uint64_t)gx);"),
+    ("forward noise index transposed", C, "or_uniform(noise_seed, image, 0u, (uint64_t)gy * (uint64_t)w + (uint64_t)gx);", "or_uniform(noise_seed, image, 0u, (uint64_t)gx * (uint64_t)h + (uint64_t)gy);"),
+    ("fp8 act quant on last layer", C, "if (quant == 2 && l > 0 && l < L - 1) {", "if (quant == 2 && l > 0) {"),
+    ("fp8 act quant skips scale", C, "in[k] = or_round_e4m3(in[k] / s) * s;", "in[k] = or_round_e4m3(in[k]);"),
+    ("bf16 act rounding off", C, "if (quant == 1 || quant == 2) v = or_round_bf16(v);", "if (quant == 2) v = or_round_bf16(v);"),
+    ("sigmoid sign", C, "prob_out[k] = 1.0 / (1.0 + exp(-in[k]));", "prob_out[k] = 1.0 / (1.0 + exp(in[k]));"),
+    ("softmax no max shift denominator", C, "for (int j = 0; j < K; ++j) s += exp(in[(size_t)j * npx + k] - m);", "for (int j = 1; j < K; ++j) s += exp(in[(size_t)j * npx + k] - m);"),
+    ("threshold tie", C, "(u < prob[k]) : (prob[k] > 0.5)", "(u < prob[k]) : (prob[k] >= 0.5)"),
+    ("bernoulli reversed", C, "(u < prob[k]) : (prob[k] > 0.5)", "(u > prob[k]) : (prob[k] > 0.5)"),
+    ("sample stream", C, "double u = mode == 1 ? or_uniform(seed, image, 1u, g) : 0.5;", "double u = mode == 1 ? or_uniform(seed, image, 2u, g) : 0.5;"),
+    ("argmax ties", C, "if (prob[(size_t)j * npx + k] > prob[(size_t)lev * npx + k]) lev = j;", "if (prob[(size_t)j * npx + k] >= prob[(size_t)lev * npx + k]) lev = j;"),
+    ("gauss sigma^2", C, "/ (2.0 * sigma * sigma));", "/ (sigma * sigma));"),
+    ("gauss unnormalised", C, "for (int k = 0; k < n * n; ++k) g[k] /= s;", "for (int k = 0; k < n * n; ++k) g[k] /= 1.0;"),
+    ("ssim cov factor", C, "(2.0 * cv2 + o->c2)", "(cv2 + o->c2)"),
+    ("ssim var", C, "vh += ww * hv * hv;", "vh += ww * hv;"),
+    ("contrast no sqrt", C, "double sig = o->k_contrast * sqrt(vc);", "double sig = o->k_contrast * vc;"),
+    ("cssim term", C, "*cssim = sig * s + (1.0 - sig);", "*cssim = sig * s + 1.0;"),
+    ("reward sign", C, "out[3] = -out[0] + o->w_s * out[2];", "out[3] = out[0] + o->w_s * out[2];"),
+    ("valid width", C, "int vh = h - 2 * r, vw = w - 2 * r;", "int vh = h - 2 * r, vw = w - 2 * r - 1;"),
+    ("hvs uses ssim window", C, "double gh = ghvs[(i + r) * n + (j + r)], ww = gw[(i + r) * n + (j + r)];", "double gh = gw[(i + r) * n + (j + r)], ww = gw[(i + r) * n + (j + r)];"),
+    ("toggle sign", C, "out[t] = (sum1 - sum0) / M;", "out[t] = (sum0 - sum1) / M;"),
+    ("toggle drops first valid row", C, "if (y < r || y >= h - r) continue;\n            for (int x = ax - r;", "if (y <= r || y >= h - r) continue;\n            for (int x = ax - r;"),
+    ("toggle multitone unscaled", C, "or_img im = {c, cpitch, hb, hpitch, ay, ax, lev * hscale, hscale};", "or_img im = {c, cpitch, hb, hpitch, ay, ax, lev, hscale};"),
+    ("psd normalisation", C, "P[k] = (Fr[k] * Fr[k] + Fi[k] * Fi[k]) / (double)N;", "P[k] = (Fr[k] * Fr[k] + Fi[k] * Fi[k]) / (double)n;"),
+    ("dc ring included", C, "if (rr == 0 || cnt[rr] < 2) continue;\n            double mean", "if (cnt[rr] < 2) continue;\n            double mean"),
+    ("ring floor", C, "int rr = (int)lround(sqrt((double)(u * u + v * v)));", "int rr = (int)floor(sqrt((double)(u * u + v * v)));"),
+    ("centred boundary", C, "static inline int centred(int k, int n) { return k < n / 2 ? k : k - n; }", "static inline int centred(int k, int n) { return k <= n / 2 ? k : k - n; }"),
+    ("ring grad factor", C, "G[k] = 2.0 * d;", "G[k] = d;"),
+    ("grad scale", C, "grad[k] = 2.0 / (double)N * Yr[k];", "grad[k] = 1.0 / (double)N * Yr[k];"),
+    ("bin radial scale", C, "int br = (int)floor(r / half * n_rad);", "int br = (int)floor(r / half * (n_rad - 1));"),
+    ("bin A normaliser", C, "A /= (double)(K - 1) * m * m;", "A /= (double)K * m * m;"),
+    ("bin dm second term", C, " - 2.0 * (ak - m) * (ak - m) / (m * m * m)) / (K - 1);", ") / (K - 1);"),
+    ("bin angle axes", C, "double th = atan2((double)u, (double)v);", "double th = atan2((double)v, (double)u);"),
+    ("backward sigmoid'", C, "gout[k] = dprob[k] * p * (1.0 - p);", "gout[k] = dprob[k] * p;"),
+    ("backward no relu mask", C, "if (!(acts[l - 1][k] > 0.0)) gin[k] = 0.0;", "if (!(acts[l - 1][k] >= 0.0)) gin[k] = 0.0;"),
+    ("backward wgrad flip", C, "gw[l][(((size_t)o * ci + i) * 3 + ky) * 3 + kx] += s;", "gw[l][(((size_t)o * ci + i) * 3 + (2 - ky)) * 3 + kx] += s;"),
+    ("backward bias", C, "gb[l][o] += s;", "gb[l][o] += 0.5 * s;"),
+    ("backward bf16 weights off", C, "if (quant == 1 && l < L - 1) wv = or_round_bf16(wv);", "if (quant == 3) wv = or_round_bf16(wv);"),
+    ("resnet no shortcut", C, "double v = u[k] + x[k];", "double v = u[k];"),
+    ("resnet no relu after add", C, "            v = v > 0.0 ? v : 0.0;\n            x[k] = quant", "            x[k] = quant"),
+    ("ssim c1", P, "c1=0.01 ** 2", "c1=0.01"),
+    ("ssim c2", P, "c2=0.03 ** 2", "c2=0.01 ** 2"),
+    ("w_s", P, "w_s=0.06", "w_s=0.6"),
+    ("contrast k", P, "k_contrast=2.0", "k_contrast=1.0"),
+    ("sigma hvs", P, "sigma_hvs=2.0", "sigma_hvs=1.5"),
+    ("le r1/r0", P, "r0 = R - hb * dR", "r0 = R - (1.0 - hb) * dR"),
+    ("coma advantage sign", P, "adv = np.where(hb > 0, (1.0 - p) * dR, -p * dR)", "adv = np.where(hb > 0, (1.0 - p) * dR, p * dR)"),
+    ("multitone pair clamp", P, "k = np.minimum(np.floor(t), levels - 2).astype(np.int64)", "k = np.minimum(np.floor(t), levels - 1).astype(np.int64)"),
+    ("multitone grad scale", P, "return float(val), -dR * (levels - 1)", "return float(val), -dR / (levels - 1)"),
+]
+
+
+
+def _copy(dst):
+    if os.path.exists(dst):
+        shutil.rmtree(dst)
+    ign = shutil.ignore_patterns(".git", "_work", "gpurun_out", "__pycache__", ".pytest_cache")
+    shutil.copytree(ROOT, dst, ignore=ign, symlinks=True)
+
+
+def _run_suite(cwd):
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests", "-m", "not gpu", "-x", "-q", "-p", "no:cacheprovider",
+                        "--ignore=tests/test_dist_cpu.py"], cwd=cwd, capture_output=True, text=True, timeout=1800)
+    first = next((ln[:150] for ln in r.stdout.splitlines() if ln.startswith(("FAILED", "ERROR"))), "")
+    return r.returncode, first
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scratch", default=None, help="directory for the scratch copy (default: a temporary one)")
+    ap.add_argument("only", nargs="*", help="run only mutations whose name contains one of these")
+    args = ap.parse_args()
+    scratch = args.scratch or tempfile.mkdtemp(prefix="ht_mutation_")
+    mut = os.path.join(scratch, "repo")
+    _copy(mut)
+    survived = []
+    for name, f, old, new in M:
+        if args.only and not any(o in name for o in args.only):
+            continue
+        path = os.path.join(mut, f)
+        src = open(path).read()
+        if src.count(old) != 1:
+            print(f"SKIP      {name}: pattern found {src.count(old)} times", flush=True)
+            continue
+        open(path, "w").write(src.replace(old, new))
+        shutil.rmtree(os.path.join(mut, "oracle", "_build"), ignore_errors=True)
+        t = time.time()
+        rc, first = _run_suite(mut)
+        open(path, "w").write(src)
+        shutil.rmtree(os.path.join(mut, "oracle", "_build"), ignore_errors=True)
+        status = "killed" if rc != 0 else "SURVIVED"
+        if rc == 0:
+            survived.append(name)
+        print(f"{status:9s} {name:34s} {time.time() - t:5.1f}s  {first}", flush=True)
+    print("survived:", survived)
+    shutil.rmtree(mut, ignore_errors=True)
+
+
+if __name__ == "__main__":
+    main()

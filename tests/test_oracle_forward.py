@@ -87,6 +87,42 @@ def test_e4m3_rounding_matches_torch():
     np.testing.assert_array_equal(got, ref)
 
 
+def test_fp8_form_forward_matches_torch_rounding_model():
+    """The E4M3 form's rounding points, rebuilt from torch's float8_e4m3fn cast and an FP64
+    conv2d chain: inner-layer weights per output channel scaled by amax / 448 and rounded;
+    each inner layer's input activations divided by that layer's scale, rounded (saturating
+    at +-448) and scaled back; every hidden ReLU output rounded to bf16; layer 1 and the head
+    exact.  Nonzero biases, and scales small enough that some activations saturate."""
+    chs = (2, 16, 16, 16, 1)
+    c = synth.contone_image(18, 21, seed=4)
+    ws, bs = synth.he_normal_policy(chs, seed=5)
+    rng = np.random.default_rng(6)
+    bs = [rng.normal(0, 0.1, b.shape).astype(np.float32) for b in bs]
+    sc = [1.0, 1.0 / 448, 2.0 / 448, 1.0]
+    lg8, _, _ = O.forward(c, ws, bs, noise_seed=3, quant=2, act_scale=sc)
+
+    def e4m3(t):
+        return t.clamp(-448, 448).to(torch.float8_e4m3fn).to(torch.float64)
+
+    z = torch.from_numpy(O.uniform_map(3, 0, 0, *c.shape))
+    x = torch.stack([torch.from_numpy(c.astype(np.float64)), z])[None]
+    L = len(ws)
+    saturated = 0
+    for l in range(L):
+        w = torch.from_numpy(ws[l].astype(np.float64))
+        inner = 0 < l < L - 1
+        if inner:
+            s_o = w.abs().amax(dim=(1, 2, 3), keepdim=True) / 448.0
+            w = e4m3((w / s_o).float()) * s_o
+            saturated += int((x.abs() > 448 * sc[l]).sum())
+            x = e4m3((x / sc[l]).float()) * sc[l]
+        x = F.conv2d(x, w, torch.from_numpy(bs[l].astype(np.float64)), padding=1)
+        if l < L - 1:
+            x = x.clamp_min(0).float().to(torch.bfloat16).to(torch.float64)
+    assert saturated > 0
+    np.testing.assert_allclose(lg8[0], x[0, 0].numpy(), rtol=0, atol=1e-11)
+
+
 def test_quantised_forms_stay_close():
     chs = (2, 16, 16, 16, 1)
     c = synth.contone_image(20, 20, seed=6)
@@ -148,3 +184,7 @@ def test_softmax_levels_sampling():
     np.testing.assert_array_equal(lev, ref)
     lev0, _ = O.sample(q, h, w, (0, 0, h, w), 0, 2)
     np.testing.assert_array_equal(lev0, np.argmax(q, 0))
+    # threshold mode on exact ties takes the lowest level index
+    qt = np.array([[0.3, 0.3, 0.2, 0.2], [0.1, 0.4, 0.4, 0.1], [0.25, 0.25, 0.25, 0.25]]).T.reshape(4, 1, 3)
+    lt, _ = O.sample(np.ascontiguousarray(qt), 1, 3, (0, 0, 1, 3), 0, 2)
+    np.testing.assert_array_equal(lt[0], [0, 1, 0])
