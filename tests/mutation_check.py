@@ -91,6 +91,23 @@ M = [
     ("coma advantage sign", P, "adv = np.where(hb > 0, (1.0 - p) * dR, -p * dR)", "adv = np.where(hb > 0, (1.0 - p) * dR, p * dR)"),
     ("multitone pair clamp", P, "k = np.minimum(np.floor(t), levels - 2).astype(np.int64)", "k = np.minimum(np.floor(t), levels - 1).astype(np.int64)"),
     ("multitone grad scale", P, "return float(val), -dR * (levels - 1)", "return float(val), -dR / (levels - 1)"),
+    ("region halo short", C, "or_rect rin = rect_grow(y0, x0, rh, rw, L, h, w);", "or_rect rin = rect_grow(y0, x0, rh, rw, L - 1, h, w);"),
+    ("bf16 weights of the head", C, "int inner = (l > 0 && l < L - 1);", "int inner = (l > 0);"),
+    ("bf16 weights off", C, "if (quant == 1 && inner) v = or_round_bf16(v);", "if (quant == 3 && inner) v = or_round_bf16(v);"),
+    ("toggle M over the whole image", C, "double M = (double)(h - 2 * r) * (w - 2 * r);", "double M = (double)h * w;"),
+    ("ring anisotropy normaliser", C, "aniso[rr] = dev2[rr] / (cnt[rr] - 1) / (mean * mean);", "aniso[rr] = dev2[rr] / cnt[rr] / (mean * mean);"),
+    ("bin diagonal edge", C, "else if (u == v) bt = n_ang / 4;", "else if (u == v) bt = n_ang / 4 - 1;"),
+    ("bin keeps r = n/2", C, "if (r <= 0.0 || r >= half) continue;", "if (r <= 0.0 || r > half) continue;"),
+    ("gradient transform sign", C, "dft2(Gr, Gi, n, +1, Yr, Yi);", "dft2(Gr, Gi, n, -1, Yr, Yi);"),
+    ("backward noise stream", C, "x0[npx + (size_t)y * w + x] = or_uniform(noise_seed, image, 0u, (uint64_t)y * w + x);", "x0[npx + (size_t)y * w + x] = or_uniform(noise_seed, image, 1u, (uint64_t)y * w + x);"),
+    ("resnet stem no relu", C, "double v = x[k] > 0.0 ? x[k] : 0.0;", "double v = x[k];"),
+    ("resnet inner act not rounded", C, "t[k] = quant == 1 ? or_round_bf16(v) : v;", "t[k] = v;"),
+    ("resnet head on block input", C, "conv3x3_full(x, C, 1, h, w, wq, biases[L - 1], t);", "conv3x3_full(x, C, 1, h, w, wq, biases[0], t);"),
+    ("reward level scale", P, "rc = lib().or_reward(c, W, hb, W, H, W, 1.0 / (levels - 1),", "rc = lib().or_reward(c, W, hb, W, H, W, 1.0 / levels,"),
+    ("toggle level scale", P, "rc = lib().or_toggle_delta(c, W, hb, W, H, W, 1.0 / (levels - 1),", "rc = lib().or_toggle_delta(c, W, hb, W, H, W, 1.0 / levels,"),
+    ("multitone threshold tie", P, "up = (frac > 0.5) if u is None", "up = (frac >= 0.5) if u is None"),
+    ("multitone le r_lo", P, "r_lo = R - at_hi * dR", "r_lo = R + at_hi * dR"),
+    ("coma log-policy gradient", P, "dlogpi = np.where(hb > 0, 1.0 / np.where(hb > 0, p, 1.0), -1.0 / np.where(hb > 0, 1.0, 1.0 - p))", "dlogpi = np.where(hb > 0, 1.0 / np.where(hb > 0, p, 1.0), 1.0 / np.where(hb > 0, 1.0, 1.0 - p))"),
 ]
 
 

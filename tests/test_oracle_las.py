@@ -156,7 +156,7 @@ def _angular_bin(u, v, n_ang):
     return bt
 
 
-F0S = [(3, 5), (0, 7), (4, 4), (5, -5), (-6, 2), (9, 11), (1, 7), (7, 1), (2, -13), (12, 3)]
+F0S = [(3, 5), (0, 7), (4, 4), (5, -5), (-6, 2), (9, 11), (1, 7), (7, 1), (2, -13), (12, 3), (15, 5), (-11, 11)]
 
 
 @pytest.mark.parametrize("f0", F0S)

@@ -25,6 +25,11 @@ def test_action_pair_and_rule(L):
     near = np.rint(v * (L - 1)).astype(np.int64)
     off = np.abs(frac - 0.5) > 1e-9
     assert np.array_equal(O.sample_multitone(v, L)[off], near[off])
+    # a tie (frac exactly 1/2: v (L - 1) = 0.5 or 1.5, exact in binary) goes to the lower
+    # level, as p = 1/2 does in the binary threshold rule
+    vt = np.array([{2: 0.5, 3: 0.25, 4: 0.5}[L]])
+    kt, ft = O.multitone_pair(vt, L)
+    assert ft[0] == 0.5 and O.sample_multitone(vt, L)[0] == kt[0]
     # Bernoulli: only the two levels around v, upper one with probability frac
     u = rng.random(v.shape)
     h = O.sample_multitone(v, L, u).astype(np.int64)
