@@ -111,7 +111,7 @@ __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the MMA-issuing thread: polls without suspending, so the thread
+// Bounded wait for the MMA-issuing warp: polls without suspending, so the warp
 // resumes issuing as soon as the phase completes; the same expiry record as mbar_wait.
 __device__ __forceinline__ bool mbar_wait_poll(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
 {
@@ -183,32 +183,12 @@ __host__ __device__ constexpr uint32_t idesc_m128(uint32_t n)
     return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-template <bool FP8>
-__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
-{
-    if constexpr (FP8) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    }
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
 // Warp-wide issuing: the whole warp runs the MMA schedule, so its state (slot, row,
 // descriptors) is warp-uniform, and the one lane chosen by elect_one() issues each MMA
-// and commit under a predicate, with no divergent branch around them.
+// and commit under a predicate, with no divergent branch around them.  Every MMA here
+// accumulates (D += A B; the enable-input-d operand is the constant 1): accumulators
+// are zeroed by the epilogue after it drains them, never by the MMA.  A commit arrives
+// on the barrier once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ uint32_t elect_one()
 {
     uint32_t e;
@@ -322,33 +302,8 @@ __host__ __device__ constexpr uint32_t idesc_m256(uint32_t n)
 {
     return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((n >> 3) << 17) | ((256u >> 4) << 24);
 }
-template <bool FP8>
-__device__ __forceinline__ void mma_ss_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
-{
-    if constexpr (FP8) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    }
-}
-// arrives on the barrier at this shared offset in both CTAs of the pair once
-// every MMA issued so far has completed
-__device__ __forceinline__ void mma_commit_pair(uint32_t bar)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-        "h"((uint16_t)3)
-        : "memory");
-}
-// elected-lane forms of the two above (see elect_one)
+// CTA-pair forms (cta_group::2, issued by the pair's first CTA): M = 256, A rows from
+// both CTAs, the commit arriving on the barrier at this shared offset in both CTAs.
 template <bool FP8>
 __device__ __forceinline__ void mma_ss_pair_el(uint32_t el, uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc)
 {
