@@ -64,7 +64,8 @@ typedef enum {
     HT_ERR_UNSUPPORTED = 2,
     HT_ERR_OOM = 3,
     HT_ERR_CUDA = 4,
-    HT_ERR_TIMEOUT = 5
+    HT_ERR_TIMEOUT = 5,
+    HT_ERR_IO = 6         /* checkpoint files: open / read / write failure, corrupt file */
 } ht_status;
 
 typedef enum { HT_FP32 = 0, HT_BF16 = 1, HT_FP8_E4M3 = 2 } ht_precision;
@@ -325,6 +326,37 @@ typedef struct {
 
 ht_status ht_profile_begin(void);
 ht_status ht_profile_end(ht_kernel_stat *out, int max, int *n_out);
+
+/* Policy checkpoints, for stopping and resuming a training run (Algorithm 1, TRAIN
+ * step, iterated).  Host only: no device memory, stream or CUDA call.  A checkpoint
+ * holds the policy descriptor, the canonical float32 weights and biases (the layout
+ * above: OIHW per layer, layers concatenated), the FP8 activation scales and the
+ * training iteration `step`; the optimiser's state is the caller's.  File format
+ * (little-endian): the tag "HTCKPT01", a u32 header length, the header (i32 n_layers,
+ * i32 channels[n_layers + 1], i32 head, precision, levels, arch, i64 step,
+ * f32 act_scale[n_layers], i64 n_weights, i64 n_biases), f32 weights, f32 biases and a
+ * 64-bit FNV-1a checksum of every preceding byte. */
+typedef struct {
+    ht_policy_desc desc;
+    int64_t step;
+    int64_t n_weights, n_biases;      /* parameter counts the descriptor implies */
+    float act_scale[HT_MAX_LAYERS];
+} ht_checkpoint_info;
+
+/* Write a checkpoint.  desc must be one ht_create_policy accepts; weights_host /
+ * biases_host hold the counts it implies; act_scales_host (n_layers values) may be
+ * NULL (all 1).  The file is written to "<path>.tmp" and renamed over `path`, so an
+ * interrupted save leaves the previous file intact.  Errors: INVALID_ARG /
+ * UNSUPPORTED (descriptor, null arrays, negative step), IO. */
+ht_status ht_checkpoint_save(const char *path, const ht_policy_desc *desc, const float *weights_host,
+                             const float *biases_host, const float *act_scales_host, int64_t step);
+
+/* Read a checkpoint into `info`; with weights_host and biases_host both non-NULL also
+ * the parameters (capacities in elements: at least info->n_weights / n_biases, else
+ * INVALID_ARG).  Both NULL: header only, to size the arrays.  A wrong tag, checksum,
+ * descriptor or length returns IO and leaves `info` untouched. */
+ht_status ht_checkpoint_load(const char *path, ht_checkpoint_info *info, float *weights_host, int64_t weights_cap,
+                             float *biases_host, int64_t biases_cap);
 
 /* Synchronise `stream` and report device-side errors (timeouts, faults). */
 ht_status ht_sync(void *stream);

@@ -12,7 +12,7 @@ import threading
 from . import build as _build
 
 HT_MAX_LAYERS = 40
-HT_OK, HT_ERR_INVALID_ARG, HT_ERR_UNSUPPORTED, HT_ERR_OOM, HT_ERR_CUDA, HT_ERR_TIMEOUT = range(6)
+HT_OK, HT_ERR_INVALID_ARG, HT_ERR_UNSUPPORTED, HT_ERR_OOM, HT_ERR_CUDA, HT_ERR_TIMEOUT, HT_ERR_IO = range(7)
 HT_FP32, HT_BF16, HT_FP8_E4M3 = 0, 1, 2
 HT_HEAD_SIGMOID, HT_HEAD_SOFTMAX, HT_HEAD_MULTITONE = 0, 1, 2
 HT_MODE_THRESHOLD, HT_MODE_BERNOULLI = 0, 1
@@ -27,6 +27,7 @@ EXPORTS = (
     "ht_reward_opts_default", "ht_reward", "ht_reward_noalloc", "ht_toggle_delta", "ht_anisotropy_loss",
     "ht_plan_create", "ht_plan_launch", "ht_plan_destroy", "ht_policy_set_schedule", "ht_policy_autotune",
     "ht_train_create", "ht_train_destroy", "ht_train_step_fwd", "ht_train_step_bwd",
+    "ht_checkpoint_save", "ht_checkpoint_load",
     "ht_profile_begin", "ht_profile_end", "ht_sync", "ht_last_error", "ht_version",
 )
 
@@ -47,6 +48,11 @@ class RewardOpts(C.Structure):
 
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+class CheckpointInfo(C.Structure):
+    _fields_ = [("desc", PolicyDesc), ("step", C.c_int64), ("n_weights", C.c_int64), ("n_biases", C.c_int64),
+                ("act_scale", C.c_float * HT_MAX_LAYERS)]
 
 
 class TuneResult(C.Structure):
@@ -117,6 +123,8 @@ def load(build_if_missing: bool = True):
         L.ht_profile_begin.argtypes = []
         L.ht_profile_end.argtypes = [P(KernelStat), i, P(i)]
         L.ht_sync.argtypes = [vp]
+        L.ht_checkpoint_save.argtypes = [C.c_char_p, P(PolicyDesc), vp, vp, vp, i64]
+        L.ht_checkpoint_load.argtypes = [C.c_char_p, P(CheckpointInfo), vp, i64, vp, i64]
         L.ht_last_error.restype = C.c_char_p
         L.ht_version.restype = C.c_char_p
         _lib = L

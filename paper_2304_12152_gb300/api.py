@@ -6,6 +6,7 @@ memory and the current stream.  Function names follow include/ht.h.
 from __future__ import annotations
 
 import ctypes as C
+import os
 from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
@@ -301,6 +302,65 @@ def profile_end() -> dict:
     n = C.c_int(0)
     check(N.load().ht_profile_end(arr, 32, C.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def _flat_f32(x) -> np.ndarray:
+    """A flat float32 host array from a torch tensor (any device), an array or a
+    sequence of per-layer arrays."""
+    if isinstance(x, torch.Tensor):
+        return np.ascontiguousarray(x.detach().to("cpu", torch.float32).reshape(-1).numpy())
+    if isinstance(x, np.ndarray):
+        return np.ascontiguousarray(x.astype(np.float32, copy=False).reshape(-1))
+    return np.ascontiguousarray(np.concatenate([np.asarray(
+        t.detach().cpu() if isinstance(t, torch.Tensor) else t, np.float32).ravel() for t in x]))
+
+
+def save_checkpoint(path: str, channels: Sequence[int], weights, biases, head: int = N.HT_HEAD_SIGMOID,
+                    precision: int = N.HT_FP32, levels: int = 4, arch: int = N.HT_ARCH_PLAIN,
+                    act_scales: Optional[Sequence[float]] = None, step: int = 0) -> None:
+    """ht_checkpoint_save: the policy's descriptor and canonical float32 parameters (flat
+    tensors such as a training run's master weights, or per-layer OIHW arrays), the FP8
+    activation scales and the training iteration.  The optimiser's state is saved by torch."""
+    d = N.PolicyDesc()
+    d.arch = arch
+    d.n_layers = len(channels) - 1
+    for k, c in enumerate(channels):
+        d.channels[k] = int(c)
+    d.head, d.precision = head, precision
+    d.levels = levels if head == N.HT_HEAD_MULTITONE else 0
+    w, b = _flat_f32(weights), _flat_f32(biases)
+    sc = None if act_scales is None else np.ascontiguousarray(act_scales, np.float32)
+    if sc is not None and sc.size != d.n_layers:
+        raise ValueError(f"act_scales needs {d.n_layers} values")
+    check(N.load().ht_checkpoint_save(os.fsencode(path), C.byref(d), w.ctypes.data, b.ctypes.data,
+                                      None if sc is None else sc.ctypes.data, int(step)))
+
+
+def load_checkpoint(path: str) -> dict:
+    """ht_checkpoint_load.  Returns channels, head, precision, levels, arch, step,
+    act_scales, the flat parameters (w_flat, b_flat), the per-layer weights (OIHW) and
+    biases, and policy_kwargs such that Policy(**policy_kwargs) rebuilds the policy."""
+    L = N.load()
+    info = N.CheckpointInfo()
+    check(L.ht_checkpoint_load(os.fsencode(path), C.byref(info), None, 0, None, 0))
+    w = np.empty(info.n_weights, np.float32)
+    b = np.empty(info.n_biases, np.float32)
+    check(L.ht_checkpoint_load(os.fsencode(path), C.byref(info), w.ctypes.data, w.size, b.ctypes.data, b.size))
+    d = info.desc
+    chs = tuple(int(d.channels[k]) for k in range(d.n_layers + 1))
+    ws, bs, ow, ob = [], [], 0, 0
+    for l in range(d.n_layers):
+        nw = chs[l + 1] * chs[l] * 9
+        ws.append(w[ow:ow + nw].reshape(chs[l + 1], chs[l], 3, 3))
+        bs.append(b[ob:ob + chs[l + 1]])
+        ow, ob = ow + nw, ob + chs[l + 1]
+    levels = d.levels if d.head == N.HT_HEAD_MULTITONE else 4
+    out = dict(channels=chs, head=d.head, precision=d.precision, levels=levels, arch=d.arch, step=int(info.step),
+               act_scales=[float(info.act_scale[l]) for l in range(d.n_layers)], w_flat=w, b_flat=b,
+               weights=ws, biases=bs)
+    out["policy_kwargs"] = dict(channels=chs, weights=ws, biases=bs, head=d.head, precision=d.precision,
+                                levels=levels, arch=d.arch)
+    return out
 
 
 def sync(stream=None) -> None:

@@ -290,6 +290,8 @@ ht_status ht_policy_set_act_scales(ht_policy *p, const float *scales_host, int n
 
 }  // extern "C"
 
+ht_status ht_validate_desc(const ht_policy_desc *d) { return validate_desc(d); }
+
 namespace {
 __global__ void k_absmax(const float *__restrict__ a, size_t n, unsigned int *__restrict__ out)
 {

@@ -124,6 +124,8 @@ struct ht_policy {
 };
 
 ht_status ht_policy_ensure_ws(ht_policy *p, size_t bytes);
+// The descriptor checks of ht_create_policy (shape, head, precision, architecture).
+ht_status ht_validate_desc(const ht_policy_desc *d);
 ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
