@@ -10,8 +10,9 @@ cannot change any result (an equivalent mutation; the two known ones are listed 
 
     python tests/mutation_check.py --scratch /path/to/empty/dir [name-filter ...]
 
-Each mutation reruns the CPU suite (about 5-10 s); the whole check takes 10-15 minutes and
-is best run with nothing else busy on the cores.
+Each mutation reruns the CPU suite (about 5-10 s); the whole check takes 10-15 minutes.  Run
+it with nothing else busy on the cores: the oracle's OpenMP thread pools spin while they wait,
+and two suites sharing the cores slow each other down many times over.
 
 Known equivalent mutations: including the DC ring (it holds one sample, and rings with fewer
 than two samples are skipped) and mapping frequency index n/2 to +n/2 instead of -n/2 (the
@@ -123,12 +124,8 @@ def _copy(dst):
 
 
 def _run_suite(cwd):
-    # passive OpenMP waits: spinning thread pools of two processes on the same cores slow
-    # each other down by orders of magnitude
-    env = dict(os.environ, OMP_WAIT_POLICY="PASSIVE")
     r = subprocess.run([sys.executable, "-m", "pytest", "tests", "-m", "not gpu", "-x", "-q", "-p", "no:cacheprovider",
-                        "--ignore=tests/test_dist_cpu.py"], cwd=cwd, capture_output=True, text=True, timeout=1800,
-                       env=env)
+                        "--ignore=tests/test_dist_cpu.py"], cwd=cwd, capture_output=True, text=True, timeout=1800)
     first = next((ln[:150] for ln in r.stdout.splitlines() if ln.startswith(("FAILED", "ERROR"))), "")
     return r.returncode, first
 
