@@ -208,6 +208,7 @@ static ht_status validate_desc(const ht_policy_desc *d)
 ht_status ht_create_policy(const ht_policy_desc *desc, const float *weights_host, const float *biases_host,
                            ht_policy **out)
 {
+    HT_RANGE("ht_create_policy");
     HT_CHECK_ARG(out != nullptr, "null output pointer");
     *out = nullptr;
     ht_status st = validate_desc(desc);
@@ -269,6 +270,7 @@ ht_status ht_destroy_policy(ht_policy *p)
 
 ht_status ht_policy_set_weights(ht_policy *p, const float *weights_dev, const float *biases_dev, void *stream)
 {
+    HT_RANGE("ht_policy_set_weights");
     HT_CHECK_ARG(p && weights_dev && biases_dev, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     HT_CUDA_TRY(cudaMemcpyAsync(p->d_w, weights_dev, sizeof(float) * p->n_w, cudaMemcpyDeviceToDevice, s));
@@ -308,6 +310,7 @@ extern "C" {
 
 ht_status ht_policy_calibrate(ht_policy *p, const ht_image *img, uint64_t seed, void *stream)
 {
+    HT_RANGE("ht_policy_calibrate");
     HT_CHECK_ARG(p && img && img->contone, "null argument");
     HT_CHECK_ARG(img->h >= 1 && img->w >= 1 && img->pitch >= img->w, "bad calibration image");
     cudaStream_t s = (cudaStream_t)stream;
@@ -403,6 +406,7 @@ static ht_status validate_images(const ht_image *imgs, int n, int min_side)
 ht_status ht_halftone(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed, uint32_t *const *out_bits,
                       float *const *out_prob, void *stream)
 {
+    HT_RANGE("ht_halftone");
     HT_CHECK_ARG(p != nullptr, "null policy");
     ht_status st = validate_images(imgs, n, 1);
     if (st != HT_OK) return st;
@@ -446,6 +450,7 @@ static ht_status validate_call(const ht_policy *p, const ht_image *imgs, int n, 
 ht_status ht_plan_create(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed, uint32_t *const *out_bits,
                          float *const *out_prob, ht_plan **out)
 {
+    HT_RANGE("ht_plan_create");
     HT_CHECK_ARG(out != nullptr, "null output pointer");
     *out = nullptr;
     const ht_status st = validate_call(p, imgs, n, mode, out_bits);
@@ -455,6 +460,7 @@ ht_status ht_plan_create(ht_policy *p, const ht_image *imgs, int n, int mode, ui
 
 ht_status ht_plan_launch(ht_plan *plan, void *stream)
 {
+    HT_RANGE("ht_plan_launch");
     HT_CHECK_ARG(plan != nullptr, "null plan");
     return ht_plan_launch_impl(plan, (cudaStream_t)stream);
 }
@@ -477,6 +483,7 @@ ht_status ht_policy_autotune(ht_policy *p, const ht_image *imgs, int n, int mode
                              uint32_t *const *out_bits, float *const *out_prob, int reps, ht_tune_result *results,
                              int max_results, int *n_results, void *stream)
 {
+    HT_RANGE("ht_policy_autotune");
     ht_status st = validate_call(p, imgs, n, mode, out_bits);
     if (st != HT_OK) return st;
     HT_CHECK_ARG(reps >= 1 && reps <= 1000, "reps must be in [1, 1000]");
@@ -504,6 +511,7 @@ static ht_status validate_opts(const ht_reward_opts *o)
 ht_status ht_reward(const ht_image *c, const uint32_t *const *bits, int n, const ht_reward_opts *opts, double *out,
                     void *stream)
 {
+    HT_RANGE("ht_reward");
     ht_status st = validate_opts(opts);
     if (st != HT_OK) return st;
     st = validate_images(c, n, 2 * opts->radius + 1);
@@ -516,6 +524,7 @@ ht_status ht_reward(const ht_image *c, const uint32_t *const *bits, int n, const
 ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, const float *const *v, int n,
                           const ht_reward_opts *opts, float *const *dR, void *stream)
 {
+    HT_RANGE("ht_toggle_delta");
     ht_status st = validate_opts(opts);
     if (st != HT_OK) return st;
     st = validate_images(c, n, 2 * opts->radius + 1);
@@ -536,6 +545,7 @@ ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, const 
 ht_status ht_anisotropy_loss(const float *q, int n_patches, int n, int mode, int n_rad, int n_ang, double *out_loss,
                              float *grad, void *stream)
 {
+    HT_RANGE("ht_anisotropy_loss");
     HT_CHECK_ARG(q && out_loss, "null argument");
     HT_CHECK_ARG(n_patches >= 1, "need at least one patch");
     HT_CHECK_ARG(n >= 8 && n <= 1024 && (n & (n - 1)) == 0, "n must be a power of two in [8, 1024]");
@@ -556,6 +566,7 @@ ht_status ht_anisotropy_loss(const float *q, int n_patches, int n, int mode, int
 
 ht_status ht_sync(void *stream)
 {
+    HT_RANGE("ht_sync");
     HT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     int *flag = ht_device_error_flag();
     if (!flag) return HT_ERR_CUDA;

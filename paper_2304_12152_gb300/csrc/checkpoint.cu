@@ -146,6 +146,7 @@ ht_status parse(const std::vector<unsigned char> &img, const char *path, ht_chec
 extern "C" ht_status ht_checkpoint_save(const char *path, const ht_policy_desc *desc, const float *weights_host,
                                         const float *biases_host, const float *act_scales_host, int64_t step)
 {
+    HT_RANGE("ht_checkpoint_save");
     HT_CHECK_ARG(path && path[0], "empty checkpoint path");
     HT_CHECK_ARG(weights_host && biases_host, "weights and biases are required");
     HT_CHECK_ARG(step >= 0, "negative step");
@@ -195,6 +196,7 @@ extern "C" ht_status ht_checkpoint_save(const char *path, const ht_policy_desc *
 extern "C" ht_status ht_checkpoint_load(const char *path, ht_checkpoint_info *info, float *weights_host,
                                         int64_t weights_cap, float *biases_host, int64_t biases_cap)
 {
+    HT_RANGE("ht_checkpoint_load");
     HT_CHECK_ARG(path && path[0], "empty checkpoint path");
     HT_CHECK_ARG(info != nullptr, "null info pointer");
     FILE *fp = fopen(path, "rb");

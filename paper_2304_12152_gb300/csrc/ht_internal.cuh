@@ -9,7 +9,20 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ht.h"
+
+// NVTX range over one public entry point, named after it, for timelines and for
+// ncu --nvtx filtering.  Header-only NVTX 3: without an attached tool each push / pop
+// is a call through a no-op stub.
+struct HtRange {
+    explicit HtRange(const char *name) { nvtxRangePushA(name); }
+    ~HtRange() { nvtxRangePop(); }
+    HtRange(const HtRange &) = delete;
+    HtRange &operator=(const HtRange &) = delete;
+};
+#define HT_RANGE(name) HtRange ht_range_(name)
 
 // ---------------------------------------------------------------------------
 // Error plumbing

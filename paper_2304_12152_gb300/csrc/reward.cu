@@ -580,6 +580,7 @@ __global__ void k_reward_finalize_noalloc(const double *__restrict__ acc, int co
 extern "C" ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const *bits, int n,
                                        const ht_reward_opts *opts, double *out, void *stream)
 {
+    HT_RANGE("ht_reward_noalloc");
     HT_CHECK_ARG(opts != nullptr, "null reward options");
     HT_CHECK_ARG(opts->radius >= 1 && opts->radius <= 7, "radius must be in [1, 7]");
     HT_CHECK_ARG(opts->sigma_hvs > 0 && opts->sigma_ssim > 0, "window sigmas must be positive");

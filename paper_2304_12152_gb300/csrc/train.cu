@@ -257,6 +257,7 @@ extern "C" {
 
 ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
 {
+    HT_RANGE("ht_train_create");
     HT_CHECK_ARG(p && d && out, "null argument");
     *out = nullptr;
     HT_CHECK_ARG(p->head == HT_HEAD_SIGMOID || p->head == HT_HEAD_MULTITONE,
@@ -389,6 +390,7 @@ ht_status ht_train_destroy(ht_train *t)
 ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const float *gray_levels, uint64_t seed,
                             double *losses_host, void *stream)
 {
+    HT_RANGE("ht_train_step_fwd");
     HT_CHECK_ARG(t && (crops || n == 0) && losses_host, "null argument");
     const int G = t->d.n_gray, S = t->d.n_samples;
     HT_CHECK_ARG(n >= 0 && n <= t->d.max_crops && n + G >= 1,
@@ -513,6 +515,7 @@ ht_status ht_train_step_fwd(ht_train *t, const ht_image *crops, int n, const flo
 
 ht_status ht_train_step_bwd(ht_train *t, float *grad_w, float *grad_b, void *stream)
 {
+    HT_RANGE("ht_train_step_bwd");
     HT_CHECK_ARG(t && grad_w && grad_b, "null argument");
     HT_CHECK_ARG(t->fwd_done, "no forward to differentiate");
     ht_policy *p = t->p;
