@@ -17,6 +17,10 @@ def test_action_pair_and_rule(L):
     d = 1.0 / (L - 1)
     assert np.all((k >= 0) & (k <= L - 2)) and np.all((frac >= 0) & (frac < 1))
     np.testing.assert_allclose(k * d + frac * d, v, atol=1e-15)          # v = floor + frac * Delta
+    # v = 1 belongs to the top pair (L - 2, L - 1) with the upper level certain, so its toggle
+    # is between two valid levels
+    k1, f1 = O.multitone_pair(np.array([1.0, 0.0]), L)
+    assert (k1[0], f1[0]) == (L - 2, 1.0) and (k1[1], f1[1]) == (0, 0.0)
     # exact levels map to themselves (threshold and any u); 0 and 1 included
     lv = np.arange(L) / (L - 1)
     assert np.array_equal(O.sample_multitone(lv, L), np.arange(L))
