@@ -112,6 +112,21 @@ M = [
     ("multitone threshold tie", P, "up = (frac > 0.5) if u is None", "up = (frac >= 0.5) if u is None"),
     ("multitone le r_lo", P, "r_lo = R - at_hi * dR", "r_lo = R + at_hi * dR"),
     ("coma log-policy gradient", P, "dlogpi = np.where(hb > 0, 1.0 / np.where(hb > 0, p, 1.0), -1.0 / np.where(hb > 0, 1.0, 1.0 - p))", "dlogpi = np.where(hb > 0, 1.0 / np.where(hb > 0, p, 1.0), 1.0 / np.where(hb > 0, 1.0, 1.0 - p))"),
+    ("rect grow clamp", C, "r.yhi = y0 + rh + g > h ? h : y0 + rh + g;", "r.yhi = y0 + rh + g > h ? h - 1 : y0 + rh + g;"),
+    ("bf16 subnormal exponent", C, "if (e < -125) e = -125;", "if (e < -126) e = -126;"),
+    ("e4m3 negative saturation", C, "if (r < -448.0) r = -448.0;", "if (r < -480.0) r = -480.0;"),
+    ("backward gradient rounding off", C, "if (quant == 1) gin[k] = or_round_bf16(gin[k]);", "if (quant == 3) gin[k] = or_round_bf16(gin[k]);"),
+    ("bin loss over all radial bins", C, "loss /= n_used;", "loss /= n_rad;"),
+    ("sample ignores region offset", C, "uint64_t g = (uint64_t)(y0 + y) * (uint64_t)w + (uint64_t)(x0 + x);", "uint64_t g = (uint64_t)y * (uint64_t)w + (uint64_t)x;"),
+    ("resnet halo short", C, "or_rect R = rect_grow(y0, x0, rh, rw, L, H, W);", "or_rect R = rect_grow(y0, x0, rh, rw, L - 1, H, W);"),
+    ("resnet noise row pitch", C, "in0[np + (size_t)y * w + xx] = or_uniform(noise_seed, image, 0u, (uint64_t)gy * W + gx);", "in0[np + (size_t)y * w + xx] = or_uniform(noise_seed, image, 0u, (uint64_t)gy * w + gx);"),
+    ("resnet output column offset", C, "const double v = t[(size_t)(y0 - R.ylo + y) * w + (x0 - R.xlo + xx)];", "const double v = t[(size_t)(y0 - R.ylo + y) * w + (x0 + xx)];"),
+    ("ssim cross term", C, "cv2 += ww * hv * cv;", "cv2 += ww * hv * hv;"),
+    ("toggle drops first valid column", C, "if (x < r || x >= w - r) continue;", "if (x <= r || x >= w - r) continue;"),
+    ("error map sign", C, "if (e_map) e_map[k] = Hh - Hc;", "if (e_map) e_map[k] = Hc - Hh;"),
+    ("forward wrapper drops act scales", P, "noise_seed, image, quant, _ptr(sc),", "noise_seed, image, quant, _ptr(None),"),
+    ("sample wrapper drops image index", P, "lib().or_sample(np.ascontiguousarray(probs), K, h, w, y0, x0, rh, rw, mode, seed, image, out, _ptr(u))", "lib().or_sample(np.ascontiguousarray(probs), K, h, w, y0, x0, rh, rw, mode, seed, 0, out, _ptr(u))"),
+    ("uniform map image/stream swap", P, "lib().or_uniform_map(seed, image, stream, h, w, out)", "lib().or_uniform_map(seed, stream, image, h, w, out)"),
 ]
 
 

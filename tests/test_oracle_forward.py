@@ -71,7 +71,9 @@ def test_crop_equals_full_image():
 
 def test_bf16_rounding_matches_torch():
     rng = np.random.default_rng(0)
-    xs = np.concatenate([rng.normal(0, 1, 2000), rng.normal(0, 1e-3, 500), [1.00390625, 1.01171875, -3.0, 0.0]])
+    # float32 subnormals too (bf16 keeps fp32's exponent range: subnormal spacing 2^-133)
+    sub = np.array([3e-39, 1.1e-39, -7e-40, 2.0 ** -130, 1.5 * 2.0 ** -133, 2.5 * 2.0 ** -133, -5.5 * 2.0 ** -133])
+    xs = np.concatenate([rng.normal(0, 1, 2000), rng.normal(0, 1e-3, 500), [1.00390625, 1.01171875, -3.0, 0.0], sub])
     ref = torch.from_numpy(xs.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
     got = np.array([O.round_bf16(float(np.float32(x))) for x in xs])
     np.testing.assert_array_equal(got, ref)
@@ -149,6 +151,23 @@ def test_sampling_rules():
     pp = np.full((1, 128, 128), 0.3)
     b, _ = O.sample(pp, 128, 128, (0, 0, 128, 128), 1, 9)
     assert abs(b.mean() - 0.3) < 5 * np.sqrt(0.21 / b.size)
+
+
+def test_sampling_over_a_region_and_image_index():
+    """A region's actions are the matching slice of the whole image's (the uniforms are
+    keyed by the global pixel index), and the image index selects the Philox counter."""
+    h, w = 23, 37
+    rng = np.random.default_rng(8)
+    p = rng.random((1, h, w))
+    q4 = rng.dirichlet(np.ones(4), size=(h, w)).transpose(2, 0, 1).copy()
+    for probs in (p, q4):
+        full, uf = O.sample(probs, h, w, (0, 0, h, w), 1, 9, image=3)
+        y0, x0, rh, rw = 5, 11, 9, 17
+        part, up = O.sample(np.ascontiguousarray(probs[:, y0:y0 + rh, x0:x0 + rw]), h, w, (y0, x0, rh, rw), 1, 9, image=3)
+        np.testing.assert_array_equal(part, full[y0:y0 + rh, x0:x0 + rw])
+        np.testing.assert_array_equal(up, uf[y0:y0 + rh, x0:x0 + rw])
+    np.testing.assert_array_equal(uf, O.uniform_map(9, 3, 1, h, w))
+    assert not np.array_equal(uf, O.uniform_map(9, 0, 1, h, w))
 
 
 def test_sampled_level_frequencies_follow_the_probabilities():
