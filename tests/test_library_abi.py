@@ -72,3 +72,38 @@ def test_argument_errors_before_launch():
     o.radius = 9
     img2 = (N.Image * 1)(N.Image(16, 20, 20, 20))
     assert L.ht_reward(img2, q, 1, C.byref(o), q, None) == N.HT_ERR_INVALID_ARG
+
+
+def test_null_handles_and_out_of_range_arguments():
+    """Every entry point that takes a handle refuses a null one before touching the device,
+    with a message; destroying a null handle is a no-op."""
+    L = N.load()
+    vp = C.c_void_p
+    img = (N.Image * 1)(N.Image(16, 8, 8, 8))
+    bits = (vp * 1)(16)
+    out = vp()
+    res = (N.TuneResult * N.HT_TUNE_CANDIDATES)()
+    nres = C.c_int()
+    losses = (C.c_double * 4)()
+    sc = (C.c_float * 8)(*([1.0] * 8))
+    calls = [
+        lambda: L.ht_halftone(None, img, 1, 0, 0, bits, None, None),
+        lambda: L.ht_plan_create(None, img, 1, 0, 0, bits, None, C.byref(out)),
+        lambda: L.ht_plan_create(vp(16), img, 1, 0, 0, bits, None, None),
+        lambda: L.ht_plan_launch(None, None),
+        lambda: L.ht_policy_set_weights(None, vp(16), vp(16), None),
+        lambda: L.ht_policy_set_act_scales(None, sc, 8),
+        lambda: L.ht_policy_calibrate(None, img, 0, None),
+        lambda: L.ht_policy_set_schedule(None, 8, 0, 0),
+        lambda: L.ht_policy_autotune(None, img, 1, 0, 0, bits, None, 1, res, N.HT_TUNE_CANDIDATES, C.byref(nres), None),
+        lambda: L.ht_train_create(None, None, C.byref(out)),
+        lambda: L.ht_train_step_fwd(None, img, 1, None, 0, losses, None),
+        lambda: L.ht_train_step_bwd(None, vp(16), vp(16), None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == N.HT_ERR_INVALID_ARG, k
+        assert len(L.ht_last_error()) > 0, k
+    assert not out.value
+    assert L.ht_destroy_policy(None) == N.HT_OK
+    assert L.ht_plan_destroy(None) == N.HT_OK
+    assert L.ht_train_destroy(None) == N.HT_OK
