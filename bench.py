@@ -227,6 +227,8 @@ def main():
     ap.add_argument("--images", type=int, default=0, help="override: number of images (with --side)")
     ap.add_argument("--side", type=int, default=0, help="override: square image side (with --images)")
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--torch-fp32-steps", type=int, default=1,
+                    help="timed passes of the plain PyTorch FP32 form (cuDNN, TF32 off); 0 skips it")
     ap.add_argument("--ref-side", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="",
@@ -501,6 +503,11 @@ def main():
             cpu["bit_match"] = {"decided": int(decided.sum()), "mismatch": mism,
                                 "rate": 1.0 - mism / max(1, int(decided.sum())), "margin": 1e-4}
 
+    # ---------------- the plain PyTorch FP32 form (context; after every other measurement) ----------------
+    torch32 = None
+    if rank == 0 and world == 1 and args.torch_fp32_steps > 0 and not resnet:
+        torch32 = torch_fp32_form(args.torch_fp32_steps, cs, ws, bs, head == N.HT_HEAD_SOFTMAX, px_per_step)
+
     if rank == 0:
         wdesc = desc.format(b=args.batch, h=args.size, w=args.size)
         line = {
@@ -515,7 +522,7 @@ def main():
                     "method": "pinned host buffers; per step all inputs H2D and all halftones D2H inside the "
                               "timed region, on two copy streams overlapping the neighbouring steps' compute "
                               "(two buffer sets, one CUDA-graph plan each)"},
-            "roofline": roof, "fp32_plain": fp32, "cpu_baseline": cpu, "kernels": kernels,
+            "roofline": roof, "fp32_plain": fp32, "torch_fp32": torch32, "cpu_baseline": cpu, "kernels": kernels,
             "gpu_launches": gpu_launches, "clocks": clk.summary(),
             "timing": ("value and e2e: CUDA-graph replay of the call (ht_plan); kernels and roofline: "
                        f"{prof_steps} direct calls, each launch bracketed by CUDA events") if plan is not None
@@ -546,6 +553,70 @@ def code_hash(path):
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in txt.splitlines()]
     return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()
+
+
+def torch_fp32_form(steps, cs, ws, bs, softmax_head, px_per_step):
+    """The same policy as plain PyTorch FP32 operators, for context beside the library's
+    forms: cuDNN convolutions with TF32 off (3x3, zero padding 1) and ReLU, then the sigmoid
+    (softmax over 4 logits) and a Bernoulli comparison against torch uniforms, one image at
+    a time, into an unpacked per-pixel map.  One untimed pass, then `steps` timed ones
+    (CUDA events on a GPU, wall clock on the CPU).  Any failure, out-of-memory included, is
+    returned as an error string rather than raised."""
+    import time
+
+    import torch
+    import torch.nn.functional as F
+    prev = (torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32)
+    try:
+        torch.backends.cudnn.allow_tf32 = False
+        torch.backends.cuda.matmul.allow_tf32 = False
+        dev = cs[0].device
+        wt = [torch.from_numpy(w).to(dev) for w in ws]
+        bt = [torch.from_numpy(b).to(dev) for b in bs]
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1)
+        zs = [torch.rand(tuple(c.shape), device=dev, generator=gen) for c in cs]
+
+        def one_pass():
+            out = []
+            for c, z in zip(cs, zs):
+                x = torch.stack([c, z])[None]
+                for l in range(len(wt)):
+                    x = F.conv2d(x, wt[l], bt[l], padding=1)
+                    if l < len(wt) - 1:
+                        x = torch.relu_(x)
+                u = torch.rand(tuple(c.shape), device=dev, generator=gen)
+                if softmax_head:
+                    h = (torch.cumsum(torch.softmax(x[0], 0), 0) <= u[None]).sum(0)
+                else:
+                    h = u < torch.sigmoid(x[0, 0])
+                out.append(h)
+            return out
+
+        cuda = dev.type == "cuda"
+        one_pass()
+        if cuda:
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one_pass()
+        if cuda:
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+        else:
+            ms = (time.perf_counter() - t0) * 1e3 / steps
+        return {"value": px_per_step / (ms * 1e-3) / 1e6, "unit": "Mpx/s", "ms_per_step": ms, "steps": steps,
+                "form": "torch F.conv2d FP32 (cuDNN, TF32 off) + ReLU, sigmoid / softmax, Bernoulli comparison; "
+                        "one image at a time, unpacked output"}
+    except Exception as e:          # context only: report, never abort the bench line
+        return {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+    finally:
+        torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32 = prev
+        if torch.cuda.is_available():
+            torch.cuda.empty_cache()
 
 
 def conv_traffic(args, kname, px_per_step, launches_per_step):

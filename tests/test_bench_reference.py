@@ -26,3 +26,26 @@ def test_reference_arm_json_line():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_torch_fp32_form_runs_and_reports_errors_on_cpu():
+    """The bench's plain PyTorch FP32 form (context beside the library's forms) on small CPU
+    tensors: both heads give a throughput line; a failure comes back as an error string."""
+    import numpy as np
+    import torch
+
+    import bench
+    from paper_2304_12152_gb300 import synth
+    prev = (torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32)
+    cs = [torch.from_numpy(synth.contone_image(24, 31, seed=1, index=i)) for i in range(2)]
+    px = sum(c.numel() for c in cs)
+    for chs, softmax in ((synth.NET_SMALL, False), ((2, 8, 8, 4), True)):
+        ws, bs = synth.he_normal_policy(chs, 1)
+        r = bench.torch_fp32_form(1, cs, ws, bs, softmax, px)
+        assert "error" not in r, r
+        assert r["value"] > 0 and r["unit"] == "Mpx/s" and r["steps"] == 1
+    ws, bs = synth.he_normal_policy(synth.NET_SMALL, 1)
+    bad = bench.torch_fp32_form(1, cs, ws[1:], bs[1:], False, px)      # first layer missing
+    assert set(bad) == {"error"} and "RuntimeError" in bad["error"]
+    assert (torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32) == prev   # restored
+    assert np.isfinite(r["ms_per_step"])
