@@ -1,0 +1,246 @@
+"""CPU model of the conv kernel's barrier protocol (k_conv_tc), run under random
+interleavings.  compute-sanitizer is closed on the GPU pool, so the pipeline's ordering
+argument is checked here instead, on a faithful model of its synchronisation:
+
+* a producer that stages each unit's nrows + 2 input rows in a ring of NSLOT slots
+  (wait `empty`, write the row record, copies landing asynchronously on `full`), then an
+  end-of-work marker, then a drain that waits for its own newest copy in every slot;
+* the MMA issuer: waits `full` for each row, reads the record at a unit's start, waits the
+  accumulator-release barrier `bfree[k]` before block k's first MMA, queues the row's MMAs
+  and commits (`empty` for the slot, `bfull[k - 2]` for the completed block), and gives the
+  blocks a short unit leaves unused one release-wait + commit round;
+* the tensor pipe, completing MMAs and commits in issue order after random delays;
+* eight epilogue warps in two groups (blocks g, g + 2, ...), each waiting `bfull`, reading
+  and zeroing its TMEM lane quarter, and arriving on `bfree` (four arrivals per block).
+
+Barriers follow mbarrier parity semantics: a wait on parity q returns once the barrier's
+current phase has parity != q, so a waiter that falls two phases behind stalls.  Checked:
+no deadlock; every wait returns on exactly the phase it means; a slot is overwritten only
+after the MMAs that read it completed and read only after its copy landed; a TMEM block is
+accumulated into only after all four of its epilogue warps drained and zeroed it; a block
+is drained only after its three contributing rows' MMAs completed.  Two earlier protocol
+bugs are kept as variants that the model must catch."""
+import random
+
+import pytest
+
+NSLOT = 6
+
+
+class Bar:
+    def __init__(self, name, count):
+        self.name, self.count, self.pending, self.phases = name, count, count, 0
+
+    def arrive(self):
+        self.pending -= 1
+        assert self.pending >= 0, f"{self.name}: too many arrivals"
+        if self.pending == 0:
+            self.phases += 1
+            self.pending = self.count
+
+    def done(self, parity):
+        return parity != (self.phases & 1)
+
+
+class Violation(AssertionError):
+    pass
+
+
+def wait(bar, phase):
+    """Generator: wait for completion of phase `phase` (0-based; -1 = the phase before the
+    first, complete from the start) by its parity, then check it was exactly that phase."""
+    parity = phase & 1
+    while not bar.done(parity):
+        yield lambda: bar.done(parity)              # blocked until this holds
+    if bar.phases != phase + 1:
+        raise Violation(f"{bar.name}: waited for phase {phase}, barrier at {bar.phases} completed phases")
+
+
+class Sim:
+    """One CTA's conv pipeline over a list of units (output rows per unit), scheduled at random."""
+
+    def __init__(self, units, ru, rng, variant=None):
+        self.units, self.ru, self.rng, self.variant = units, ru, rng, variant
+        self.full = [Bar(f"full[{s}]", 1) for s in range(NSLOT)]
+        self.empty = [Bar(f"empty[{s}]", 1) for s in range(NSLOT)]
+        self.wbar, self.drain = Bar("wbar", 1), Bar("drain", 1)
+        self.bfull = [Bar(f"bfull[{j}]", 1) for j in range(ru)]
+        self.bfree = [Bar(f"bfree[{j}]", 4) for j in range(ru)]
+        self.meta = [None] * NSLOT
+        self.slot_row = [None] * NSLOT          # ring index of the row staged in the slot
+        self.slot_landed = [False] * NSLOT
+        self.slot_readers = [0] * NSLOT         # queued MMAs reading the slot, not yet completed
+        self.pipe = []                          # tensor pipe, in issue order
+        self.copies = [("w",)]                  # copies in flight (they land in any order)
+        self.blk_unit = [-1] * ru               # unit whose sums the block holds
+        self.blk_rows = [0] * ru                # its contributing rows completed so far
+        self.blk_zeroed = [4] * ru              # epilogue warps that drained + zeroed it (4 = free)
+        # relative speeds of this run: a slow epilogue, tensor pipe or copy engine lets the
+        # other roles run as far ahead as the barriers allow
+        self.speed = {k: rng.choice([1.0, 0.2, 0.03]) for k in ("epilogue", "#pipe", "#copy")}
+
+    def producer(self):
+        li = 0
+        last = [-1] * NSLOT
+        for nrows in self.units:
+            for r in range(nrows + 2):
+                slot, rnd = li % NSLOT, li // NSLOT
+                yield from wait(self.empty[slot], rnd - 1)
+                if self.slot_readers[slot]:
+                    raise Violation(f"slot {slot} overwritten while MMAs still read it")
+                self.meta[slot] = (r, nrows)
+                self.slot_row[slot], self.slot_landed[slot] = li, False
+                if self.rng.random() < 0.25:            # a halo row: zero-filled, arrive at once
+                    self.slot_landed[slot] = True
+                    self.full[slot].arrive()
+                else:
+                    self.copies.append((slot, li))
+                last[slot] = li
+                li += 1
+                yield None
+        slot, rnd = li % NSLOT, li // NSLOT              # end-of-work marker
+        yield from wait(self.empty[slot], rnd - 1)
+        self.meta[slot] = (-1, 0)
+        self.slot_row[slot], self.slot_landed[slot] = li, True
+        self.full[slot].arrive()
+        if self.variant != "marker_not_recorded":
+            last[slot] = li
+        for s in range(NSLOT):                            # drain: own newest phase of every slot
+            if last[s] >= 0:
+                yield from wait(self.full[s], last[s] // NSLOT)
+
+    def mma(self):
+        yield from wait(self.wbar, 0)
+        li, uit, start, k, nrows = 0, 0, True, 0, 0
+        while True:
+            slot, rnd = li % NSLOT, li // NSLOT
+            yield from wait(self.full[slot], rnd)
+            if start:
+                k, nrows = self.meta[slot]
+                if k < 0:
+                    break
+                start = False
+            if not self.slot_landed[slot] or self.slot_row[slot] != li:
+                raise Violation(f"row {li} read before it landed")
+            if k < nrows:
+                yield from wait(self.bfree[k], uit)
+                if self.blk_zeroed[k] != 4:
+                    raise Violation(f"block {k} accumulated before all its epilogue warps drained it")
+                self.blk_zeroed[k], self.blk_unit[k], self.blk_rows[k] = 0, uit, 0
+            blocks = list(range(max(0, k - 2), min(nrows - 1, k) + 1))
+            self.slot_readers[slot] += 1
+            self.pipe.append(("mma", slot, uit, blocks))
+            self.pipe.append(("commit", self.empty[slot]))
+            if k >= 2:
+                self.pipe.append(("commit", self.bfull[k - 2]))
+            li += 1
+            yield None
+            if k == nrows + 1:
+                for j in range(nrows, self.ru):           # unused blocks: one release / commit round
+                    if self.variant != "skip_unused_wait":
+                        yield from wait(self.bfree[j], uit)
+                    self.pipe.append(("commit", self.bfull[j]))
+                uit, start = uit + 1, True
+            else:
+                k += 1
+        self.pipe.append(("commit", self.drain))
+        yield from wait(self.drain, 0)
+
+    def epilogue(self, g):
+        for j in range(g, self.ru, 2):                   # blocks start zeroed and free
+            self.bfree[j].arrive()
+            yield None
+        for uit, nrows in enumerate(self.units):
+            for j in range(g, self.ru, 2):
+                yield from wait(self.bfull[j], uit)
+                if j < nrows:
+                    if self.blk_unit[j] != uit or self.blk_rows[j] != 3:
+                        raise Violation(f"block {j} of unit {uit} drained before its three rows completed")
+                    yield None                             # TMEM read and zeroing of this warp's quarter
+                    self.blk_zeroed[j] += 1
+                self.bfree[j].arrive()
+                yield None
+
+    def step_pipe(self):
+        op = self.pipe.pop(0)
+        if op[0] == "commit":
+            op[1].arrive()
+            return
+        _, slot, uit, blocks = op
+        for j in blocks:
+            if self.blk_unit[j] != uit:
+                raise Violation(f"MMA of unit {uit} landed in block {j} held by unit {self.blk_unit[j]}")
+            self.blk_rows[j] += 1
+        self.slot_readers[slot] -= 1
+
+    def step_copy(self):
+        c = self.copies.pop(self.rng.randrange(len(self.copies)))
+        if c[0] == "w":
+            self.wbar.arrive()
+            return
+        slot, li = c
+        assert self.slot_row[slot] == li
+        self.slot_landed[slot] = True
+        self.full[slot].arrive()
+
+    def run(self):
+        procs = {"producer": self.producer(), "mma": self.mma()}
+        for g in range(2):
+            for q in range(4):
+                procs[f"epilogue{g}.{q}"] = self.epilogue(g)
+        blocked = dict.fromkeys(procs)
+        for _ in range(10 ** 6):
+            if not procs and not self.pipe and not self.copies:
+                return
+            cands = [n for n in procs if blocked[n] is None or blocked[n]()]
+            if self.pipe:
+                cands.append("#pipe")
+            if self.copies:
+                cands.append("#copy")
+            if not cands:
+                raise Violation(f"deadlock: {sorted(procs)} wait forever")
+            weights = [self.speed.get("epilogue" if n.startswith("epilogue") else n, 1.0) for n in cands]
+            c = self.rng.choices(cands, weights)[0]
+            if c == "#pipe":
+                self.step_pipe()
+            elif c == "#copy":
+                self.step_copy()
+            else:
+                try:
+                    blocked[c] = next(procs[c])
+                except StopIteration:
+                    del procs[c], blocked[c]
+        raise AssertionError("simulation did not finish")
+
+
+def _units(rng, ru):
+    """A CTA's units: mostly full, with short ones (image bottoms, small images) and runs of
+    consecutive short units."""
+    n = rng.randint(1, 9)
+    return [ru if rng.random() < 0.4 else rng.randint(1, ru) for _ in range(n)]
+
+
+@pytest.mark.parametrize("ru", [3, 4, 5, 6, 7, 8])
+def test_conv_pipeline_protocol_holds(ru):
+    rng = random.Random(1000 + ru)
+    for trial in range(60):
+        units = _units(rng, ru)
+        Sim(units, ru, random.Random(rng.random())).run()
+
+
+@pytest.mark.parametrize("variant", ["skip_unused_wait", "marker_not_recorded"])
+def test_model_catches_the_earlier_protocol_bugs(variant):
+    """The two faults found on the GPU (both reported by the bounded waits' timeout record):
+    committing a short unit's unused blocks without waiting for their release (two short
+    units in a row run a block two phases ahead), and a drain that did not count the end
+    marker as its slot's newest phase."""
+    rng = random.Random(7)
+    caught = 0
+    for trial in range(60):
+        units = [rng.randint(1, 2) for _ in range(rng.randint(3, 8))] if variant == "skip_unused_wait" \
+            else _units(rng, 8)
+        try:
+            Sim(units, 8, random.Random(rng.random()), variant).run()
+        except Violation:
+            caught += 1
+    assert caught >= 5, caught
