@@ -183,11 +183,15 @@ class Sim:
         self.slot_landed[slot] = True
         self.full[slot].arrive()
 
-    def run(self):
+    def _procs(self):
         procs = {"producer": self.producer(), "mma": self.mma()}
         for g in range(2):
             for q in range(4):
                 procs[f"epilogue{g}.{q}"] = self.epilogue(g)
+        return procs
+
+    def run(self):
+        procs = self._procs()
         blocked = dict.fromkeys(procs)
         for _ in range(10 ** 6):
             if not procs and not self.pipe and not self.copies:
@@ -241,6 +245,184 @@ def test_model_catches_the_earlier_protocol_bugs(variant):
             else _units(rng, 8)
         try:
             Sim(units, 8, random.Random(rng.random()), variant).run()
+        except Violation:
+            caught += 1
+    assert caught >= 5, caught
+
+
+# ---------------------------------------------------------------------------
+# Weight-gradient kernel (k_wgrad_tc): an activation-row ring (NSA slots) and a
+# gradient-row ring (NSG slots).  Per unit of nrows gradient rows the MMA warp needs
+# activation rows base .. base + nrows + 1; gradient row j pairs with activation rows
+# base + j .. base + j + 2 (the second half of the dy-2 tile also reads base + j + 3 into
+# TMEM lanes that are never read back, so that read is not a dependence).  A gradient
+# slot is released by the MMA commit and by the four bias-sum warps (count 5).
+# ---------------------------------------------------------------------------
+WG_NSA, WG_NSG = 6, 3
+
+
+class WgSim:
+    def __init__(self, units, rng, variant=None):
+        self.units, self.rng, self.variant = units, rng, variant
+        g_count = 1 if variant == "g_release_mma_only" else 5
+        self.a_full = [Bar(f"a_full[{s}]", 1) for s in range(WG_NSA)]
+        self.a_empty = [Bar(f"a_empty[{s}]", 1) for s in range(WG_NSA)]
+        self.g_full = [Bar(f"g_full[{s}]", 1) for s in range(WG_NSG)]
+        self.g_empty = [Bar(f"g_empty[{s}]", g_count) for s in range(WG_NSG)]
+        self.tzero, self.done = Bar("tzero", 4), Bar("done", 1)
+        self.a_meta, self.g_meta = [None] * WG_NSA, [None] * WG_NSG
+        self.a_row, self.g_row = [None] * WG_NSA, [None] * WG_NSG
+        self.a_landed, self.g_landed = [False] * WG_NSA, [False] * WG_NSG
+        self.a_readers, self.g_readers = [0] * WG_NSA, [0] * WG_NSG
+        self.g_epi_reads = [0] * WG_NSG          # bias-sum warps still to read the slot's row
+        self.pipe, self.copies = [], []
+        self.speed = {k: rng.choice([1.0, 0.2, 0.03]) for k in ("epilogue", "#pipe", "#copy")}
+
+    def _stage(self, full, row, landed, meta, slot, li, rec, async_ok=True):
+        meta[slot] = rec
+        row[slot], landed[slot] = li, False
+        if async_ok and self.rng.random() < 0.75:
+            self.copies.append((full, row, landed, slot, li))
+        else:
+            landed[slot] = True
+            full[slot].arrive()
+
+    def producer(self):
+        la = lg = 0
+        a_last, g_last = [-1] * WG_NSA, [-1] * WG_NSG
+        for nrows in self.units:
+            for r in range(nrows + 2):
+                sa = la % WG_NSA
+                yield from wait(self.a_empty[sa], la // WG_NSA - 1)
+                if self.a_readers[sa]:
+                    raise Violation(f"activation slot {sa} overwritten while MMAs read it")
+                self._stage(self.a_full, self.a_row, self.a_landed, self.a_meta, sa, la, (r, nrows))
+                a_last[sa] = la
+                la += 1
+                yield None
+                if r < 2:
+                    continue
+                sg = lg % WG_NSG
+                yield from wait(self.g_empty[sg], lg // WG_NSG - 1)
+                if self.g_readers[sg] or self.g_epi_reads[sg]:
+                    raise Violation(f"gradient slot {sg} overwritten while it is still read")
+                self._stage(self.g_full, self.g_row, self.g_landed, self.g_meta, sg, lg, (r - 2, nrows))
+                self.g_epi_reads[sg] = 4
+                g_last[sg] = lg
+                lg += 1
+                yield None
+        sa, sg = la % WG_NSA, lg % WG_NSG                  # end markers on both rings
+        yield from wait(self.a_empty[sa], la // WG_NSA - 1)
+        yield from wait(self.g_empty[sg], lg // WG_NSG - 1)
+        self._stage(self.a_full, self.a_row, self.a_landed, self.a_meta, sa, la, (-1, 0), async_ok=False)
+        self._stage(self.g_full, self.g_row, self.g_landed, self.g_meta, sg, lg, (-1, 0), async_ok=False)
+        a_last[sa], g_last[sg] = la, lg
+        for s in range(WG_NSA):
+            if a_last[s] >= 0:
+                yield from wait(self.a_full[s], a_last[s] // WG_NSA)
+        for s in range(WG_NSG):
+            if g_last[s] >= 0:
+                yield from wait(self.g_full[s], g_last[s] // WG_NSG)
+
+    def _need_a(self, q):
+        s = q % WG_NSA
+        if not self.a_landed[s] or self.a_row[s] != q:
+            raise Violation(f"activation row {q} read before it landed")
+        return s
+
+    def mma(self):
+        yield from wait(self.tzero, 0)
+        qa = qg = 0
+        while True:
+            base = qa
+            yield from wait(self.a_full[base % WG_NSA], base // WG_NSA)
+            k0, nrows = self.a_meta[base % WG_NSA]
+            if k0 < 0:
+                break
+            yield from wait(self.a_full[(base + 1) % WG_NSA], (base + 1) // WG_NSA)
+            for j in range(nrows):
+                qn = base + j + 2
+                yield from wait(self.a_full[qn % WG_NSA], qn // WG_NSA)
+                yield from wait(self.g_full[qg % WG_NSG], qg // WG_NSG)
+                sg = qg % WG_NSG
+                if not self.g_landed[sg] or self.g_row[sg] != qg:
+                    raise Violation(f"gradient row {qg} read before it landed")
+                slots = [self._need_a(base + j + d) for d in range(3)]
+                for s in slots:
+                    self.a_readers[s] += 1
+                self.g_readers[sg] += 1
+                self.pipe.append(("mma", slots, sg))
+                self.pipe.append(("commit", self.g_empty[sg]))
+                self.pipe.append(("commit", self.a_empty[(base + j) % WG_NSA]))
+                qg += 1
+                yield None
+            self.pipe.append(("commit", self.a_empty[(base + nrows) % WG_NSA]))
+            self.pipe.append(("commit", self.a_empty[(base + nrows + 1) % WG_NSA]))
+            qa = base + nrows + 2
+        self.pipe.append(("commit", self.done))
+
+    def epilogue(self):
+        self.tzero.arrive()
+        yield None
+        qg = 0
+        while True:
+            sg = qg % WG_NSG
+            yield from wait(self.g_full[sg], qg // WG_NSG)
+            if self.g_meta[sg][0] < 0:
+                break
+            if not self.g_landed[sg] or self.g_row[sg] != qg:
+                raise Violation(f"bias sums read gradient row {qg} before it landed")
+            yield None                                     # the bias sums read the row
+            if self.g_row[sg] != qg:
+                raise Violation(f"gradient row {qg} overwritten while the bias sums read it")
+            self.g_epi_reads[sg] -= 1
+            if self.variant != "g_release_mma_only":
+                self.g_empty[sg].arrive()
+            qg += 1
+            yield None
+        yield from wait(self.done, 0)
+
+    def step_pipe(self):
+        op = self.pipe.pop(0)
+        if op[0] == "commit":
+            op[1].arrive()
+            return
+        _, slots, sg = op
+        for s in slots:
+            self.a_readers[s] -= 1
+        self.g_readers[sg] -= 1
+
+    def step_copy(self):
+        full, row, landed, slot, li = self.copies.pop(self.rng.randrange(len(self.copies)))
+        assert row[slot] == li
+        landed[slot] = True
+        full[slot].arrive()
+
+    run = Sim.run
+
+    def _procs(self):
+        procs = {"producer": self.producer(), "mma": self.mma()}
+        for q in range(4):
+            procs[f"epilogue.{q}"] = self.epilogue()
+        return procs
+
+
+def test_wgrad_pipeline_protocol_holds():
+    rng = random.Random(2024)
+    for trial in range(150):
+        units = [rng.choice([8, 8, rng.randint(1, 8)]) for _ in range(rng.randint(1, 7))]
+        WgSim(units, random.Random(rng.random())).run()
+
+
+def test_wgrad_model_catches_a_gradient_slot_released_by_the_mma_alone():
+    """If the gradient ring's slots were released by the MMA commit alone, the producer
+    could refill a slot the bias-sum warps are still reading."""
+    rng = random.Random(5)
+    caught = 0
+    for trial in range(60):
+        units = [rng.randint(1, 8) for _ in range(rng.randint(2, 7))]
+        try:
+            WgSim(units, random.Random(rng.random()), "g_release_mma_only").run()
         except Violation:
             caught += 1
     assert caught >= 5, caught
