@@ -426,3 +426,202 @@ def test_wgrad_model_catches_a_gradient_slot_released_by_the_mma_alone():
         except Violation:
             caught += 1
     assert caught >= 5, caught
+
+
+# ---------------------------------------------------------------------------
+# CTA-pair form (k_conv_tc2, cluster of two CTAs, M = 256).  Each CTA stages its own
+# 128-pixel half of every row in its own ring; the second CTA's relay warp forwards "my
+# weights / my row landed" (and the end marker) to the first CTA's pwbar / pfull by
+# remote arrives; the first CTA's MMA warp waits on both, reads both CTAs' slots and
+# accumulates into both CTAs' TMEM blocks; its commits arrive on the barrier of both
+# CTAs (multicast); the epilogue warps of both CTAs release blocks on the first CTA's
+# bfree (8 arrivals).
+# ---------------------------------------------------------------------------
+class Ring:
+    def __init__(self, cta):
+        self.full = [Bar(f"cta{cta}.full[{s}]", 1) for s in range(NSLOT)]
+        self.empty = [Bar(f"cta{cta}.empty[{s}]", 1) for s in range(NSLOT)]
+        self.meta = [None] * NSLOT
+        self.row = [None] * NSLOT
+        self.landed = [False] * NSLOT
+        self.readers = [0] * NSLOT
+
+
+class PairSim:
+    def __init__(self, units, ru, rng, variant=None):
+        self.units, self.ru, self.rng, self.variant = units, ru, rng, variant
+        self.ring = [Ring(0), Ring(1)]
+        self.wbar = [Bar("cta0.wbar", 1), Bar("cta1.wbar", 1)]
+        self.pwbar = Bar("cta0.pwbar", 1)
+        self.pfull = [Bar(f"cta0.pfull[{s}]", 1) for s in range(NSLOT)]
+        self.drain = [Bar("cta0.drain", 1), Bar("cta1.drain", 1)]
+        self.bfull = [[Bar(f"cta{c}.bfull[{j}]", 1) for j in range(ru)] for c in range(2)]
+        self.bfree = [Bar(f"cta0.bfree[{j}]", 8) for j in range(ru)]
+        self.blk_unit = [[-1] * ru for _ in range(2)]
+        self.blk_rows = [[0] * ru for _ in range(2)]
+        self.blk_zeroed = [[4] * ru for _ in range(2)]
+        self.pipe, self.copies = [], [("w", 0), ("w", 1)]
+        self.speed = {k: rng.choice([1.0, 0.2, 0.03]) for k in ("epilogue", "#pipe", "#copy", "relay")}
+
+    def producer(self, c):
+        R = self.ring[c]
+        li = 0
+        last = [-1] * NSLOT
+        for nrows in self.units:
+            for r in range(nrows + 2):
+                slot, rnd = li % NSLOT, li // NSLOT
+                yield from wait(R.empty[slot], rnd - 1)
+                if R.readers[slot]:
+                    raise Violation(f"cta{c} slot {slot} overwritten while MMAs still read it")
+                R.meta[slot] = (r, nrows)
+                R.row[slot], R.landed[slot] = li, False
+                if self.rng.random() < 0.25:
+                    R.landed[slot] = True
+                    R.full[slot].arrive()
+                else:
+                    self.copies.append(("row", c, slot, li))
+                last[slot] = li
+                li += 1
+                yield None
+        slot, rnd = li % NSLOT, li // NSLOT
+        yield from wait(R.empty[slot], rnd - 1)
+        R.meta[slot] = (-1, 0)
+        R.row[slot], R.landed[slot] = li, True
+        R.full[slot].arrive()
+        if self.variant != "marker_not_recorded":
+            last[slot] = li
+        for s in range(NSLOT):
+            if last[s] >= 0:
+                yield from wait(R.full[s], last[s] // NSLOT)
+        yield from wait(self.wbar[c], 0)
+
+    def relay(self):
+        R = self.ring[1]
+        yield from wait(self.wbar[1], 0)
+        self.pwbar.arrive()
+        q = 0
+        while True:
+            slot = q % NSLOT
+            yield from wait(R.full[slot], q // NSLOT)
+            k = R.meta[slot][0]
+            if k < 0 and self.variant == "relay_drops_marker":
+                break
+            self.pfull[slot].arrive()
+            yield None
+            if k < 0:
+                break
+            q += 1
+        yield from wait(self.drain[1], 0)
+
+    def mma(self):
+        yield from wait(self.wbar[0], 0)
+        yield from wait(self.pwbar, 0)
+        li, uit, start, k, nrows = 0, 0, True, 0, 0
+        both = lambda bars: [bars[0], bars[1]]             # noqa: E731  multicast commit targets
+        while True:
+            slot, rnd = li % NSLOT, li // NSLOT
+            yield from wait(self.ring[0].full[slot], rnd)
+            yield from wait(self.pfull[slot], rnd)
+            if start:
+                k, nrows = self.ring[0].meta[slot]
+                if k < 0:
+                    break
+                start = False
+            for c in range(2):
+                R = self.ring[c]
+                if not R.landed[slot] or R.row[slot] != li:
+                    raise Violation(f"cta{c} row {li} read before it landed")
+            if k < nrows:
+                yield from wait(self.bfree[k], uit)
+                for c in range(2):
+                    if self.blk_zeroed[c][k] != 4:
+                        raise Violation(f"cta{c} block {k} accumulated before its epilogue warps drained it")
+                    self.blk_zeroed[c][k], self.blk_unit[c][k], self.blk_rows[c][k] = 0, uit, 0
+            blocks = list(range(max(0, k - 2), min(nrows - 1, k) + 1))
+            for c in range(2):
+                self.ring[c].readers[slot] += 1
+            self.pipe.append(("mma", slot, uit, blocks))
+            self.pipe.append(("commit", both([self.ring[0].empty[slot], self.ring[1].empty[slot]])))
+            if k >= 2:
+                self.pipe.append(("commit", both([self.bfull[0][k - 2], self.bfull[1][k - 2]])))
+            li += 1
+            yield None
+            if k == nrows + 1:
+                for j in range(nrows, self.ru):
+                    yield from wait(self.bfree[j], uit)
+                    self.pipe.append(("commit", both([self.bfull[0][j], self.bfull[1][j]])))
+                uit, start = uit + 1, True
+            else:
+                k += 1
+        self.pipe.append(("commit", both(self.drain)))
+        yield from wait(self.drain[0], 0)
+
+    def epilogue(self, c, g):
+        for j in range(g, self.ru, 2):
+            self.bfree[j].arrive()                         # the second CTA's arrive is remote
+            yield None
+        for uit, nrows in enumerate(self.units):
+            for j in range(g, self.ru, 2):
+                yield from wait(self.bfull[c][j], uit)
+                if j < nrows:
+                    if self.blk_unit[c][j] != uit or self.blk_rows[c][j] != 3:
+                        raise Violation(f"cta{c} block {j} of unit {uit} drained before its rows completed")
+                    yield None
+                    self.blk_zeroed[c][j] += 1
+                self.bfree[j].arrive()
+                yield None
+
+    def step_pipe(self):
+        op = self.pipe.pop(0)
+        if op[0] == "commit":
+            for b in op[1]:
+                b.arrive()
+            return
+        _, slot, uit, blocks = op
+        for c in range(2):
+            for j in blocks:
+                if self.blk_unit[c][j] != uit:
+                    raise Violation(f"MMA of unit {uit} landed in cta{c} block {j} held by unit {self.blk_unit[c][j]}")
+                self.blk_rows[c][j] += 1
+            self.ring[c].readers[slot] -= 1
+
+    def step_copy(self):
+        cp = self.copies.pop(self.rng.randrange(len(self.copies)))
+        if cp[0] == "w":
+            self.wbar[cp[1]].arrive()
+            return
+        _, c, slot, li = cp
+        R = self.ring[c]
+        assert R.row[slot] == li
+        R.landed[slot] = True
+        R.full[slot].arrive()
+
+    def _procs(self):
+        procs = {"producer0": self.producer(0), "producer1": self.producer(1), "mma": self.mma(),
+                 "relay": self.relay()}
+        for c in range(2):
+            for g in range(2):
+                for q in range(4):
+                    procs[f"epilogue{c}{g}.{q}"] = self.epilogue(c, g)
+        return procs
+
+    run = Sim.run
+
+
+@pytest.mark.parametrize("ru", [3, 5, 8])
+def test_cta_pair_protocol_holds(ru):
+    rng = random.Random(3000 + ru)
+    for trial in range(40):
+        PairSim(_units(rng, ru), ru, random.Random(rng.random())).run()
+
+
+@pytest.mark.parametrize("variant", ["marker_not_recorded", "relay_drops_marker"])
+def test_pair_model_catches_marker_faults(variant):
+    rng = random.Random(9)
+    caught = 0
+    for trial in range(30):
+        try:
+            PairSim(_units(rng, 8), 8, random.Random(rng.random()), variant).run()
+        except Violation:
+            caught += 1
+    assert caught >= 5, caught
