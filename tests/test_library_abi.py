@@ -107,3 +107,22 @@ def test_null_handles_and_out_of_range_arguments():
     assert L.ht_destroy_policy(None) == N.HT_OK
     assert L.ht_plan_destroy(None) == N.HT_OK
     assert L.ht_train_destroy(None) == N.HT_OK
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without the CUDA library the binding and the public API raise, naming
+    the missing file (checked in a fresh interpreter with HT_LIB_PATH at a missing path)."""
+    import subprocess
+    import sys
+    code = (
+        "from paper_2304_12152_gb300 import _native as N, api, synth\n"
+        "for f in (N.load, lambda: api.Policy(synth.NET_SMALL, *synth.he_normal_policy(synth.NET_SMALL, 0))):\n"
+        "    try:\n"
+        "        f()\n"
+        "        print('NO ERROR')\n"
+        "    except RuntimeError as e:\n"
+        "        print('RAISED', e)\n")
+    env = dict(os.environ, HT_LIB_PATH=str(tmp_path / "missing_libht.so"))
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    lines = r.stdout.strip().splitlines()
+    assert len(lines) == 2 and all(ln.startswith("RAISED") and "missing_libht.so" in ln for ln in lines), r.stdout + r.stderr
