@@ -127,6 +127,11 @@ M = [
     ("forward wrapper drops act scales", P, "noise_seed, image, quant, _ptr(sc),", "noise_seed, image, quant, _ptr(None),"),
     ("sample wrapper drops image index", P, "lib().or_sample(np.ascontiguousarray(probs), K, h, w, y0, x0, rh, rw, mode, seed, image, out, _ptr(u))", "lib().or_sample(np.ascontiguousarray(probs), K, h, w, y0, x0, rh, rw, mode, seed, 0, out, _ptr(u))"),
     ("uniform map image/stream swap", P, "lib().or_uniform_map(seed, image, stream, h, w, out)", "lib().or_uniform_map(seed, stream, image, h, w, out)"),
+    ("philox key words swapped", C, "uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};", "uint32_t key[2] = {(uint32_t)(seed >> 32), (uint32_t)seed};"),
+    ("spectrum with the inverse transform", C, "dft2(q, NULL, n, -1, Fr, Fi);", "dft2(q, NULL, n, +1, Fr, Fi);"),
+    ("ssim mean normaliser", C, "out[1] = ssim / M;", "out[1] = ssim / (M + 1.0);"),
+    ("threshold uniform", C, "double u = mode == 1 ? or_uniform(seed, image, 1u, g) : 0.5;", "double u = mode == 1 ? or_uniform(seed, image, 1u, g) : 0.5 + 1e-9;"),
+    ("resnet conv1 weights exact", C, "wq[k] = quant == 1 ? or_round_bf16((double)weights[l1][k]) : (double)weights[l1][k];", "wq[k] = (double)weights[l1][k];"),
 ]
 
 

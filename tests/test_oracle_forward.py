@@ -141,6 +141,7 @@ def test_sampling_rules():
     p = np.linspace(0, 1, h * w).reshape(1, h, w)
     p[0, 3, 3] = 0.5
     bits, u = O.sample(p, h, w, (0, 0, h, w), mode=0, seed=0)
+    assert np.all(u == 0.5)                                  # threshold = the Bernoulli rule at u = 1/2
     assert set(np.unique(bits)) <= {0, 1}
     np.testing.assert_array_equal(bits, (p[0] > 0.5).astype(np.uint8))
     assert bits[3, 3] == 0                                   # tie p = 0.5 -> 0
