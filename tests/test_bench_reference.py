@@ -49,3 +49,34 @@ def test_torch_fp32_form_runs_and_reports_errors_on_cpu():
     assert set(bad) == {"error"} and "RuntimeError" in bad["error"]
     assert (torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32) == prev   # restored
     assert np.isfinite(r["ms_per_step"])
+
+
+def test_clock_summary_rules():
+    """The bench's clocks record: median SM clock, the highest maximum seen, and every
+    throttle reason reported active (a run with a hardware or thermal slowdown is the
+    one to reject); unparsable samples are skipped, no samples reads as unsampled."""
+    import bench
+    c = bench.Clocks(0)
+    c.lines = ["2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "1980, 2070, 1390.2, 0x4, Not Active, Not Active, Not Active, Active",
+               "2010, 2070, 1200.0, 0x8, Active, Not Active, Not Active, Not Active",
+               "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+               "garbage"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2010 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    c.lines = []
+    assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_code_hash_ignores_comments_only(tmp_path):
+    """The committed counter capture stays attached to the kernel source: comment and blank
+    line edits keep the hash, a code edit changes it."""
+    import bench
+    a = tmp_path / "a.cu"
+    a.write_text("int f(int x) {\n    return x + 1;   // add one\n}\n")
+    h0 = bench.code_hash(str(a))
+    a.write_text("/* doc\n   block */\nint f(int x) {\n\n    return x + 1;   // add 1\n}\n")
+    assert bench.code_hash(str(a)) == h0
+    a.write_text("int f(int x) {\n    return x + 2;\n}\n")
+    assert bench.code_hash(str(a)) != h0
