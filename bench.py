@@ -143,6 +143,27 @@ def cpu_oracle_sample(img, ws, bs, side, seed, image_id=0, quant=1, mode=1, scal
     return dt, reg, p, lev, u
 
 
+def cpu_oracle_one_thread(img, ws, bs, seed, quant=1, mode=1, levels=0, resnet=False, seconds=5.0):
+    """The oracle's rate on one host thread, beside its all-threads rate: a centre crop
+    sized (by area, from a small first pass) for about `seconds` of work.  The oracle's
+    thread count is restored afterwards; a failure is reported, not raised."""
+    import oracle as O
+    n0 = O.num_threads()
+    try:
+        O.set_num_threads(1)
+        side = 16
+        dt, *_ = cpu_oracle_sample(img, ws, bs, side, seed, quant=quant, mode=mode, levels=levels, resnet=resnet)
+        side = int(min(min(img.shape), 512, max(16, side * math.sqrt(seconds / max(dt, 1e-3)))))
+        side -= side % 8
+        dt, *_ = cpu_oracle_sample(img, ws, bs, side, seed, quant=quant, mode=mode, levels=levels, resnet=resnet)
+        return {"value": side * side / dt / 1e6, "unit": "Mpx/s", "cores": 1,
+                "sample": f"{side}x{side} centre crop of image 0 (+halo)", "seconds": dt}
+    except Exception as e:          # context only: report, never abort the bench line
+        return {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+    finally:
+        O.set_num_threads(n0)
+
+
 def run_reference(args):
     rank, world, local = dist_info()
     if rank != 0:
@@ -487,6 +508,8 @@ def main():
                "sample": f"{side}x{side} centre crop of image 0 (+halo), FP64 forward"
                          f"{' emulating the ' + precision.upper() + ' rounding' if quant else ''} + actions",
                "seconds": dt}
+        cpu["one_thread"] = cpu_oracle_one_thread(imgs_np[0], ws, bs, seed, quant=quant, mode=mode, levels=lv,
+                                                  resnet=resnet)
         if quant != 2:   # FP8 scales come from the library's calibration: no bit comparison
             y0, x0, rh, rw = reg
             lev_gpu = api.unpack_bits(bits[0], imgs_np[0].shape[0], imgs_np[0].shape[1], head)[y0:y0 + rh, x0:x0 + rw]

@@ -80,3 +80,18 @@ def test_code_hash_ignores_comments_only(tmp_path):
     assert bench.code_hash(str(a)) == h0
     a.write_text("int f(int x) {\n    return x + 2;\n}\n")
     assert bench.code_hash(str(a)) != h0
+
+
+def test_cpu_oracle_one_thread_rate():
+    import oracle as O
+
+    import bench
+    from paper_2304_12152_gb300 import synth
+    O.build()
+    n0 = O.num_threads()
+    img = synth.contone_image(96, 96, seed=1)
+    ws, bs = synth.he_normal_policy(synth.NET_SMALL, 1)
+    r = bench.cpu_oracle_one_thread(img, ws, bs, 1, quant=0, mode=1, seconds=0.3)
+    assert "error" not in r, r
+    assert r["cores"] == 1 and r["value"] > 0 and r["seconds"] > 0
+    assert O.num_threads() == n0
