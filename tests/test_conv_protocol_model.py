@@ -517,7 +517,6 @@ class PairSim:
         yield from wait(self.wbar[0], 0)
         yield from wait(self.pwbar, 0)
         li, uit, start, k, nrows = 0, 0, True, 0, 0
-        both = lambda bars: [bars[0], bars[1]]             # noqa: E731  multicast commit targets
         while True:
             slot, rnd = li % NSLOT, li // NSLOT
             yield from wait(self.ring[0].full[slot], rnd)
@@ -541,19 +540,20 @@ class PairSim:
             for c in range(2):
                 self.ring[c].readers[slot] += 1
             self.pipe.append(("mma", slot, uit, blocks))
-            self.pipe.append(("commit", both([self.ring[0].empty[slot], self.ring[1].empty[slot]])))
+            # commits are multicast: they arrive on the barrier of both CTAs
+            self.pipe.append(("commit", [self.ring[0].empty[slot], self.ring[1].empty[slot]]))
             if k >= 2:
-                self.pipe.append(("commit", both([self.bfull[0][k - 2], self.bfull[1][k - 2]])))
+                self.pipe.append(("commit", [self.bfull[0][k - 2], self.bfull[1][k - 2]]))
             li += 1
             yield None
             if k == nrows + 1:
                 for j in range(nrows, self.ru):
                     yield from wait(self.bfree[j], uit)
-                    self.pipe.append(("commit", both([self.bfull[0][j], self.bfull[1][j]])))
+                    self.pipe.append(("commit", [self.bfull[0][j], self.bfull[1][j]]))
                 uit, start = uit + 1, True
             else:
                 k += 1
-        self.pipe.append(("commit", both(self.drain)))
+        self.pipe.append(("commit", list(self.drain)))
         yield from wait(self.drain[0], 0)
 
     def epilogue(self, c, g):
