@@ -62,6 +62,8 @@ def lib():
             L.or_round_bf16.argtypes = [C.c_double]
             L.or_round_e4m3.restype = C.c_double
             L.or_round_e4m3.argtypes = [C.c_double]
+            L.or_round_fp16.restype = C.c_double
+            L.or_round_fp16.argtypes = [C.c_double]
             L.or_forward.restype = C.c_int
             L.or_forward.argtypes = [fp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_uint64, C.c_uint32,
@@ -123,6 +125,10 @@ def round_bf16(x: float) -> float:
 
 def round_e4m3(x: float) -> float:
     return lib().or_round_e4m3(float(x))
+
+
+def round_fp16(x: float) -> float:
+    return lib().or_round_fp16(float(x))
 
 
 def _layers(weights: Sequence[np.ndarray], biases: Sequence[np.ndarray]):

@@ -104,6 +104,21 @@ double or_round_bf16(double x)
     return nearbyint(x / q) * q;        /* default rounding mode: to nearest, ties to even */
 }
 
+double or_round_fp16(double x)
+{
+    /* IEEE binary16: 11 significant bits, normal range from 2^-14, subnormal spacing 2^-24,
+     * largest finite 65504; a value that rounds past it becomes an infinity, as an IEEE
+     * round-to-nearest conversion does. */
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    frexp(x, &e);                       /* |x| = m * 2^e, m in [0.5, 1) */
+    if (e < -13) e = -13;               /* subnormal range: spacing stays 2^-24 */
+    double q = ldexp(1.0, e - 11);
+    double r = nearbyint(x / q) * q;
+    if (fabs(r) > 65504.0) r = r > 0 ? INFINITY : -INFINITY;
+    return r;
+}
+
 double or_round_e4m3(double x)
 {
     /* OCP FP8 E4M3 (fn): bias 7, 3 mantissa bits, max normal 448, min normal 2^-6,
@@ -145,7 +160,8 @@ double or_round_e4m3(double x)
 /*            channel with scale amax_o/448, each inner layer's input         */
 /*            activations quantised with the static scale act_scale[l]        */
 /*            (l = index of the layer that consumes them); the output of every */
-/*            hidden layer is first rounded to bf16 (the storage format).     */
+/*            hidden layer is first rounded to bf16 (the storage format);     */
+/*        3 = FP16 form: as 1 with IEEE binary16 in place of bf16.            */
 /* The quantised forms only decide where rounding happens; accumulation is    */
 /* exact (double).                                                            */
 /* ------------------------------------------------------------------------- */
@@ -201,6 +217,7 @@ int or_forward(const float *contone, int h, int w, int pitch,
                 double v = (double)weights[l][(size_t)o * ci * 9 + k];
                 if (quant == 1 && inner) v = or_round_bf16(v);
                 if (quant == 2 && inner) v = or_round_e4m3(v / s) * s;
+                if (quant == 3 && inner) v = or_round_fp16(v);
                 wq[l][(size_t)o * ci * 9 + k] = v;
             }
         }
@@ -260,6 +277,7 @@ int or_forward(const float *contone, int h, int w, int pitch,
                 for (int k = 0; k < oh * ow; ++k) {
                     double v = op[k] > 0.0 ? op[k] : 0.0;
                     if (quant == 1 || quant == 2) v = or_round_bf16(v);
+                    if (quant == 3) v = or_round_fp16(v);
                     op[k] = v;
                 }
             }

@@ -132,6 +132,11 @@ M = [
     ("ssim mean normaliser", C, "out[1] = ssim / M;", "out[1] = ssim / (M + 1.0);"),
     ("threshold uniform", C, "double u = mode == 1 ? or_uniform(seed, image, 1u, g) : 0.5;", "double u = mode == 1 ? or_uniform(seed, image, 1u, g) : 0.5 + 1e-9;"),
     ("resnet conv1 weights exact", C, "wq[k] = quant == 1 ? or_round_bf16((double)weights[l1][k]) : (double)weights[l1][k];", "wq[k] = (double)weights[l1][k];"),
+    ("fp16 spacing", C, "double q = ldexp(1.0, e - 11);", "double q = ldexp(1.0, e - 10);"),
+    ("fp16 subnormal exponent", C, "if (e < -13) e = -13;", "if (e < -14) e = -14;"),
+    ("fp16 overflow saturates", C, "if (fabs(r) > 65504.0) r = r > 0 ? INFINITY : -INFINITY;", "if (fabs(r) > 65504.0) r = r > 0 ? 65504.0 : -65504.0;"),
+    ("fp16 weights not rounded", C, "if (quant == 3 && inner) v = or_round_fp16(v);", ""),
+    ("fp16 activations not rounded", C, "                    if (quant == 3) v = or_round_fp16(v);\n", ""),
 ]
 
 

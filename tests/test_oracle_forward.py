@@ -125,6 +125,49 @@ def test_fp8_form_forward_matches_torch_rounding_model():
     np.testing.assert_allclose(lg8[0], x[0, 0].numpy(), rtol=0, atol=1e-11)
 
 
+def test_fp16_rounding_matches_torch():
+    rng = np.random.default_rng(2)
+    edge = [65504.0, 65519.0, 65520.0, 1e5, -7e4, 2.0 ** -14, 2.0 ** -24, 3 * 2.0 ** -25, 2.0 ** -26,
+            1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, -2049.0, 0.0]
+    xs = np.concatenate([rng.normal(0, 1, 2000), rng.normal(0, 1e-5, 500), rng.normal(0, 3e4, 200), edge])
+    xs32 = xs.astype(np.float32)
+    ref = torch.from_numpy(xs32).to(torch.float16).to(torch.float64).numpy()
+    got = np.array([O.round_fp16(float(x)) for x in xs32])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_fp16_form_forward_matches_torch_rounding_model():
+    """quant 3 (FP16 form): inner-layer weights rounded to IEEE binary16, every hidden ReLU
+    output rounded to binary16, layer 1 and the head weights exact -- rebuilt from torch's
+    float16 cast and an FP64 conv2d chain."""
+    chs = (2, 16, 16, 16, 1)
+    c = synth.contone_image(17, 22, seed=8)
+    ws, bs = synth.he_normal_policy(chs, seed=9)
+    rng = np.random.default_rng(10)
+    bs = [rng.normal(0, 0.1, b.shape).astype(np.float32) for b in bs]
+    lg16, _, _ = O.forward(c, ws, bs, noise_seed=4, quant=3)
+
+    def f16(t):
+        # one rounding from float64 (numpy converts double to half directly); going through
+        # float32 first would round twice and can land on a binary16 tie
+        return torch.from_numpy(t.numpy().astype(np.float16).astype(np.float64))
+
+    z = torch.from_numpy(O.uniform_map(4, 0, 0, *c.shape))
+    x = torch.stack([torch.from_numpy(c.astype(np.float64)), z])[None]
+    L = len(ws)
+    for l in range(L):
+        w = torch.from_numpy(ws[l].astype(np.float64))
+        if 0 < l < L - 1:
+            w = f16(w)
+        x = F.conv2d(x, w, torch.from_numpy(bs[l].astype(np.float64)), padding=1)
+        if l < L - 1:
+            x = f16(x.clamp_min(0))
+    np.testing.assert_allclose(lg16[0], x[0, 0].numpy(), rtol=0, atol=1e-11)
+    lg1, _, _ = O.forward(c, ws, bs, noise_seed=4, quant=1)
+    lg0, _, _ = O.forward(c, ws, bs, noise_seed=4)
+    assert np.abs(lg16 - lg0).max() < np.abs(lg1 - lg0).max()        # fp16 is the finer format
+
+
 def test_quantised_forms_stay_close():
     chs = (2, 16, 16, 16, 1)
     c = synth.contone_image(20, 20, seed=6)
