@@ -1,6 +1,6 @@
 """Policy checkpoints (host only, no GPU): round trips through the C ABI, the documented
-file layout read back independently, and the error paths (corrupt, truncated, forged or
-foreign files, bad descriptors, short output arrays)."""
+file layout read back independently, the error paths (corrupt, truncated, forged or
+foreign files, bad descriptors, short output arrays) and a stopped-and-resumed run."""
 import os
 import struct
 
@@ -170,3 +170,47 @@ def test_load_capacity_and_header_only_query(tmp_path):
     assert L.ht_checkpoint_load(os.fsencode(path), C.byref(info), w.ctypes.data, nw, None, 0) == N.HT_ERR_INVALID_ARG
     assert L.ht_checkpoint_load(None, C.byref(info), None, 0, None, 0) == N.HT_ERR_INVALID_ARG
     assert L.ht_checkpoint_load(os.fsencode(path), None, None, 0, None, 0) == N.HT_ERR_INVALID_ARG
+
+
+def test_resume_continues_a_run_bit_for_bit(tmp_path):
+    """The resume workflow: master weights, FP8 scales and the step go through the library's
+    checkpoint, the optimiser's state through torch.save; a run stopped after 3 steps and
+    resumed reaches the same weights, bit for bit, as one run of 6 steps (a deterministic
+    stand-in gradient replaces the training step, which needs the GPU)."""
+    import torch
+    chs = synth.NET_SMALL
+    ws, bs = synth.he_normal_policy(chs, 2)
+    w0 = torch.from_numpy(np.concatenate([w.ravel() for w in ws]))
+    b0 = torch.from_numpy(np.concatenate(bs))
+
+    def grads(w, b, step):
+        g = torch.Generator().manual_seed(1000 + step)
+        return (torch.sin(w * 3.0) + 0.01 * torch.randn(w.shape, generator=g),
+                torch.cos(b) + 0.01 * torch.randn(b.shape, generator=g))
+
+    def run(w, b, opt, steps, first):
+        for step in range(first, first + steps):
+            gw, gb = grads(w.detach(), b.detach(), step)
+            w.grad, b.grad = gw, gb
+            opt.step()
+
+    w, b = w0.clone().requires_grad_(True), b0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([w, b], lr=1e-3)
+    run(w, b, opt, 6, 0)
+    w_ref, b_ref = w.detach().clone(), b.detach().clone()
+
+    w, b = w0.clone().requires_grad_(True), b0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([w, b], lr=1e-3)
+    run(w, b, opt, 3, 0)
+    path = str(tmp_path / "run.htck")
+    api.save_checkpoint(path, chs, w, b, precision=N.HT_FP32, step=3)
+    torch.save(opt.state_dict(), str(tmp_path / "opt.pt"))
+    del w, b, opt
+
+    ck = api.load_checkpoint(path)
+    w = torch.from_numpy(ck["w_flat"].copy()).requires_grad_(True)
+    b = torch.from_numpy(ck["b_flat"].copy()).requires_grad_(True)
+    opt = torch.optim.Adam([w, b], lr=1e-3)
+    opt.load_state_dict(torch.load(str(tmp_path / "opt.pt")))
+    run(w, b, opt, 6 - ck["step"], ck["step"])
+    assert torch.equal(w.detach(), w_ref) and torch.equal(b.detach(), b_ref)
