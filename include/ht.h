@@ -68,7 +68,7 @@ typedef enum {
     HT_ERR_IO = 6         /* checkpoint files: open / read / write failure, corrupt file */
 } ht_status;
 
-typedef enum { HT_FP32 = 0, HT_BF16 = 1, HT_FP8_E4M3 = 2 } ht_precision;
+typedef enum { HT_FP32 = 0, HT_BF16 = 1, HT_FP8_E4M3 = 2, HT_FP16 = 3 } ht_precision;
 typedef enum { HT_HEAD_SIGMOID = 0, HT_HEAD_SOFTMAX = 1, HT_HEAD_MULTITONE = 2 } ht_head;
 typedef enum { HT_MODE_THRESHOLD = 0, HT_MODE_BERNOULLI = 1 } ht_mode;
 
@@ -82,8 +82,16 @@ typedef enum { HT_MODE_THRESHOLD = 0, HT_MODE_BERNOULLI = 1 } ht_mode;
  * `levels` (2..4) ink levels k / (levels - 1), the upper one with probability
  * equal to v's distance from the lower one over the level spacing (threshold
  * mode: the nearest level), level index packed in 2 bits/px.
- * precision: FP32 = plain CUDA-core form; BF16 / FP8_E4M3 = tensor-core form
- * (hidden widths must then all be 64; FP32 accumulation). */
+ * precision: FP32 = plain CUDA-core form; BF16 / FP8_E4M3 / FP16 = tensor-core form
+ * (hidden widths must then all be 64; FP32 accumulation).  Rounding points of the
+ * tensor-core forms: layer 1 is evaluated to float32 accuracy (inputs and weights as
+ * exact three-part bf16 splits); the inner layers' weights and every hidden
+ * activation are stored in the form's format (BF16: bfloat16; FP16: IEEE binary16, the
+ * same bytes and tensor rate as BF16 with three more significand bits; FP8_E4M3: e4m3
+ * with per-output-channel weight scales and per-layer activation scales, activations
+ * rounded to bfloat16 first); the last layer's weights stay float32 (4-logit head:
+ * exact as two 16-bit parts).  FP16 is an inference form: training it returns
+ * HT_ERR_UNSUPPORTED. */
 typedef enum { HT_ARCH_PLAIN = 0, HT_ARCH_RESNET = 1 } ht_arch;
 
 /* arch RESNET: the residual policy of Sec. VI-A.  Layers: a stem convolution

@@ -13,7 +13,7 @@ from . import build as _build
 
 HT_MAX_LAYERS = 40
 HT_OK, HT_ERR_INVALID_ARG, HT_ERR_UNSUPPORTED, HT_ERR_OOM, HT_ERR_CUDA, HT_ERR_TIMEOUT, HT_ERR_IO = range(7)
-HT_FP32, HT_BF16, HT_FP8_E4M3 = 0, 1, 2
+HT_FP32, HT_BF16, HT_FP8_E4M3, HT_FP16 = 0, 1, 2, 3
 HT_HEAD_SIGMOID, HT_HEAD_SOFTMAX, HT_HEAD_MULTITONE = 0, 1, 2
 HT_MODE_THRESHOLD, HT_MODE_BERNOULLI = 0, 1
 HT_EST_LE, HT_EST_COMA = 0, 1

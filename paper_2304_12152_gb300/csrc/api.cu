@@ -48,7 +48,7 @@ std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_ev_pool;
 const char *const g_kernel_names[HTK_COUNT] = {"k_first_tc",   "k_conv_tc_bf16", "k_conv_tc_fp8", "k_head_tc",
                                                "k_conv3x3_fp32", "k_head_fp32",  "k_reward",      "k_toggle_delta",
-                                               "k_spectrum",   "k_train", "k_first_input"};
+                                               "k_spectrum",   "k_train", "k_first_input", "k_conv_tc_fp16"};
 
 cudaEvent_t pool_event()
 {
@@ -174,7 +174,8 @@ static ht_status validate_desc(const ht_policy_desc *d)
     } else {
         HT_CHECK_ARG(false, "unknown head %d", d->head);
     }
-    HT_CHECK_ARG(d->precision == HT_FP32 || d->precision == HT_BF16 || d->precision == HT_FP8_E4M3,
+    HT_CHECK_ARG(d->precision == HT_FP32 || d->precision == HT_BF16 || d->precision == HT_FP8_E4M3 ||
+                     d->precision == HT_FP16,
                  "unknown precision %d", d->precision);
     HT_CHECK_ARG(d->arch == HT_ARCH_PLAIN || d->arch == HT_ARCH_RESNET, "unknown arch %d", d->arch);
     if (d->arch == HT_ARCH_RESNET) {
@@ -391,7 +392,7 @@ ht_status ht_policy_ensure_ws(ht_policy *p, size_t bytes)
 
 extern "C" {
 
-static ht_status validate_images(const ht_image *imgs, int n, int min_side)
+ht_status ht_validate_images(const ht_image *imgs, int n, int min_side)
 {
     HT_CHECK_ARG(imgs != nullptr && n >= 1, "need at least one image");
     for (int i = 0; i < n; ++i) {
@@ -408,7 +409,7 @@ ht_status ht_halftone(ht_policy *p, const ht_image *imgs, int n, int mode, uint6
 {
     HT_RANGE("ht_halftone");
     HT_CHECK_ARG(p != nullptr, "null policy");
-    ht_status st = validate_images(imgs, n, 1);
+    ht_status st = ht_validate_images(imgs, n, 1);
     if (st != HT_OK) return st;
     HT_CHECK_ARG(mode == HT_MODE_THRESHOLD || mode == HT_MODE_BERNOULLI, "unknown mode %d", mode);
     HT_CHECK_ARG(out_bits != nullptr, "null output array");
@@ -439,7 +440,7 @@ ht_status ht_halftone(ht_policy *p, const ht_image *imgs, int n, int mode, uint6
 static ht_status validate_call(const ht_policy *p, const ht_image *imgs, int n, int mode, uint32_t *const *out_bits)
 {
     HT_CHECK_ARG(p != nullptr, "null policy");
-    ht_status st = validate_images(imgs, n, 1);
+    ht_status st = ht_validate_images(imgs, n, 1);
     if (st != HT_OK) return st;
     HT_CHECK_ARG(mode == HT_MODE_THRESHOLD || mode == HT_MODE_BERNOULLI, "unknown mode %d", mode);
     HT_CHECK_ARG(out_bits != nullptr, "null output array");
@@ -499,7 +500,7 @@ ht_status ht_policy_autotune(ht_policy *p, const ht_image *imgs, int n, int mode
                           (cudaStream_t)stream);
 }
 
-static ht_status validate_opts(const ht_reward_opts *o)
+ht_status ht_validate_reward_opts(const ht_reward_opts *o)
 {
     HT_CHECK_ARG(o != nullptr, "null reward options");
     HT_CHECK_ARG(o->radius >= 1 && o->radius <= 7, "radius must be in [1, 7]");
@@ -512,9 +513,9 @@ ht_status ht_reward(const ht_image *c, const uint32_t *const *bits, int n, const
                     void *stream)
 {
     HT_RANGE("ht_reward");
-    ht_status st = validate_opts(opts);
+    ht_status st = ht_validate_reward_opts(opts);
     if (st != HT_OK) return st;
-    st = validate_images(c, n, 2 * opts->radius + 1);
+    st = ht_validate_images(c, n, 2 * opts->radius + 1);
     if (st != HT_OK) return st;
     HT_CHECK_ARG(bits && out, "null argument");
     for (int i = 0; i < n; ++i) HT_CHECK_ARG(bits[i] != nullptr, "image %d: null bits", i);
@@ -525,9 +526,9 @@ ht_status ht_toggle_delta(const ht_image *c, const uint32_t *const *bits, const 
                           const ht_reward_opts *opts, float *const *dR, void *stream)
 {
     HT_RANGE("ht_toggle_delta");
-    ht_status st = validate_opts(opts);
+    ht_status st = ht_validate_reward_opts(opts);
     if (st != HT_OK) return st;
-    st = validate_images(c, n, 2 * opts->radius + 1);
+    st = ht_validate_images(c, n, 2 * opts->radius + 1);
     if (st != HT_OK) return st;
     HT_CHECK_ARG(bits && dR, "null argument");
     HT_CHECK_ARG(opts->levels == 2 || v, "multi-level toggle deltas need the policy outputs v");

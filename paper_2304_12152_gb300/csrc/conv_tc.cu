@@ -3,8 +3,8 @@
 // Policy (Sec. III "State"/"Agents", Sec. VI-A): 3x3 convolutions, zero
 // padding 1, ReLU between layers, sigmoid / softmax head.
 //
-//  k_first_input  per pixel, c and the noise channel z (Philox stream 0) as a
-//                 bf16 hi/lo split, one 16-byte chunk.
+//  k_first_input  per pixel, c and the noise channel z (Philox stream 0), each
+//                 as an exact sum of three bf16 parts, two 16-byte chunks.
 //  k_conv_tc      one pipeline, four kinds: layer 1 (2 -> 64, on the split
 //                 input), a hidden 64 -> 64 layer, the last hidden layer with
 //                 the 1-logit head's per-tap partials fused into its epilogue,
@@ -49,9 +49,9 @@ constexpr int NTHREADS = 320;              // producer, MMA issuer, 8 epilogue w
 
 // Kernel kinds built from one pipeline: a hidden 64 -> 64 layer, the last
 // hidden layer with the 1-logit head's per-tap partials fused into its
-// epilogue, and layer 1 (2 -> 64), whose input is the 16-byte-per-pixel bf16
-// hi/lo split of c and z written by k_first_input (one staged chunk; the second
-// K chunk of its MMAs is zero and stays resident in shared memory), and the
+// epilogue, and layer 1 (2 -> 64), whose input is the 32-byte-per-pixel
+// three-part bf16 split of c and z written by k_first_input (two staged chunks,
+// K = 16 per MMA of which 12 carry products), and the
 // 64 -> 4 softmax head, whose three dy blocks are 16 columns wide (4 logits with
 // bf16 hi weights, the same 4 with the lo parts, 8 zero columns: the weights stay
 // exact as hi + lo in one MMA per K step); its epilogue adds the two parts,
@@ -62,16 +62,20 @@ constexpr int NTHREADS = 320;              // producer, MMA issuer, 8 epilogue w
 // which turns its output into the head partials instead of storing it.
 enum : int { KIND_HIDDEN = 0, KIND_HEADPART = 1, KIND_FIRST = 2, KIND_HEAD4 = 3, KIND_RES = 4, KIND_RESHEAD = 5 };
 
-template <bool FP8, int KIND, int CH = 64>
+template <bool FP8, int KIND, int CH = 64, bool F16 = false>
 struct Cfg {
     static constexpr bool FIRST = KIND == KIND_FIRST;
     static constexpr bool HEAD4 = KIND == KIND_HEAD4;
     static constexpr bool RES = KIND == KIND_RES || KIND == KIND_RESHEAD;
     static constexpr bool HEADP = KIND == KIND_HEADPART || KIND == KIND_RESHEAD;   // fused head partials
     static constexpr bool MMA8 = FP8 && !FIRST && !HEAD4;      // e4m3 operands (kind::f8f6f4)
+    // FP16 form: binary16 operands (kind::f16, format F16) in every layer but layer 1,
+    // whose split input and weights stay bf16 (its output is stored as binary16)
+    static constexpr bool F16OP = F16 && !FIRST;
+    static constexpr uint32_t AB = (MMA8 || F16OP) ? 0u : 1u;  // instruction-descriptor A/B format
     static constexpr int CO = CH;                              // output channels (all but the 4-logit head)
     static constexpr int NCHUNK = FIRST ? 2 : (MMA8 ? CH / 16 : CH / 8);   // 16-byte chunks per staged pixel
-    static constexpr int NCOPY = FIRST ? 1 : NCHUNK;           // chunks staged from HBM (layer 1: chunk 1 is zero)
+    static constexpr int NCOPY = NCHUNK;                       // chunks staged from HBM per pixel
     static constexpr int NOUT = HEAD4 ? 16 : CH;               // output columns per dy block (= TMEM block stride)
     static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;
     static constexpr int W_BYTES = 3 * NCHUNK * 3 * NOUT * 16; // [dx][chunk][3 dy][NOUT n][16 B]
@@ -101,17 +105,17 @@ struct ConvParams {
 };
 
 // Fused 1-logit head (Sec. VI-A output layer): the nine per-tap dot products of the
-// bf16-rounded activations, acc[t] = sum_n bf16(v[n]) * w[t][n] in channel order.
-// Taps 0-7 run as packed pairs (each lane an ordinary fmaf, so the per-tap sums are
-// bit-identical to nine scalar chains), tap 8 alone.
-template <int CO>
+// stored (bf16, or binary16 in the FP16 form) activations, acc[t] = sum_n r(v[n]) *
+// w[t][n] in channel order.  Taps 0-7 run as packed pairs (each lane an ordinary
+// fmaf, so the per-tap sums are bit-identical to nine scalar chains), tap 8 alone.
+template <int CO, bool F16 = false>
 __device__ __forceinline__ void head_partials9(const float *v, const ConvParams &P, float *acc)
 {
     unsigned long long pr[4] = {0ull, 0ull, 0ull, 0ull};
     float a8 = 0.f;
 #pragma unroll
     for (int n = 0; n < CO; ++n) {
-        const float a = bf16_round(v[n]);
+        const float a = act_round<F16>(v[n]);
         unsigned long long aa;
         asm("mov.b64 %0, {%1, %1};" : "=l"(aa) : "f"(a));
 #pragma unroll
@@ -140,10 +144,10 @@ __device__ __forceinline__ void head_partials9(const float *v, const ConvParams 
 // accumulator block is zeroed by the epilogue after it is drained, so all MMAs
 // accumulate.  Per output row: 12-15 MMAs of N = 192 instead of 36 of N = 64.
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND, bool TR = false, int CH = 64>
+template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false>
 __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 {
-    using C = Cfg<FP8, KIND, CH>;
+    using C = Cfg<FP8, KIND, CH, F16>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *s_w = smem;
@@ -186,11 +190,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         // tensor core's async proxy by a proxy fence before the barrier arrive.
         int last_issued[NSLOT];
         for (int i = 0; i < NSLOT; ++i) last_issued[i] = -1;
-        if constexpr (C::FIRST) {
-            for (int k = lane; k < NSLOT * ROW_PX; k += 32)
-                *reinterpret_cast<uint4 *>(s_rows + (k / ROW_PX) * C::SLOT_BYTES + (ROW_PX + k % ROW_PX) * 16) =
-                    make_uint4(0, 0, 0, 0);
-        }
         if (lane == 0) {
             mbar_arrive_expect_tx(smem_u32(wbar), C::W_BYTES);
             bulk_g2s(smem_u32(s_w), P.wpack, C::W_BYTES, smem_u32(wbar));
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                             constexpr int zero = 0;
                             const int jlo = kk - 2 > zero ? kk - 2 : zero, jhi = kk < RU - 1 ? kk : RU - 1;
                             const uint32_t n = (uint32_t)(jhi - jlo + 1) * C::NOUT;
-                            const uint32_t idesc = idesc_m128<C::MMA8>(n);
+                            const uint32_t idesc = idesc_m128_ab<C::AB>(n);
                             const uint32_t sb = (uint32_t)(2 - kk + jlo);
                             const uint32_t d = tmem_base + (uint32_t)jlo * C::NOUT;
                             const uint64_t a_q = a_base + (uint64_t)((slot * (uint32_t)C::SLOT_BYTES) >> 4);
@@ -343,7 +342,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 tc_fence_after();
                 const int jlo = max(0, k - 2), jhi = min(nrows - 1, k);
                 const uint32_t n = (uint32_t)(jhi - jlo + 1) * C::NOUT;
-                const uint32_t idesc = idesc_m128<C::MMA8>(n);
+                const uint32_t idesc = idesc_m128_ab<C::AB>(n);
                 const uint32_t sb = (uint32_t)(2 - k + jlo);                       // first stacked dy block
                 const uint32_t d = tmem_base + (uint32_t)jlo * C::NOUT;
                 const uint64_t a_q = a_base + (uint64_t)((slot * (uint32_t)C::SLOT_BYTES) >> 4);
@@ -427,7 +426,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     if (j < nrows) {
                         float z[4];
 #pragma unroll
-                        for (int k2 = 0; k2 < 4; ++k2) z[k2] = (v[k2] + v[k2 + 4]) + P.bias[k2];   // hi + lo parts
+                        for (int k2 = 0; k2 < 4; ++k2)                 // (hi + lo parts) x weight scale + bias
+                            z[k2] = fmaf(v[k2] + v[k2 + 4], P.scale[k2], P.bias[k2]);
                         const ImgDesc *D = ui.D;
                         ht_head_emit(z, 4, HT_HEAD_SOFTMAX, P.mode, P.seed, D->image, ui.x0 + quarter * 32, y0 + j,
                                      ui.H, ui.W, D->bits, D->words, D->prob);
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     }
                     if constexpr ((KIND == KIND_HIDDEN || KIND == KIND_FIRST) && !TR && CH == 64) {
                         if (!P.out_fp8) {
-                            store_pixel_bias_relu_bf16(v, P.scale, P.bias, ui.out, ui.H, ui.W, y0 + j, x);
+                            store_pixel_bias_relu_bf16<F16>(v, P.scale, P.bias, ui.out, ui.H, ui.W, y0 + j, x);
                             continue;
                         }
                     }
@@ -496,10 +496,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         const size_t plane = (size_t)ui.H * ui.W;
                         float *partials = ui.D->part ? ui.D->part : (float *)ui.out;
                         float acc[9];
-                        head_partials9<C::CO>(v, P, acc);
+                        head_partials9<C::CO, F16>(v, P, acc);
 #pragma unroll
                         for (int t = 0; t < 9; ++t) partials[t * plane + o] = acc[t];
                         if (TR && ui.D->save) store_pixel<C::CO>(v, ui.D->save, 0, 1.f, ui.H, ui.W, y0 + j, x);
+                    } else if constexpr (F16 && CH == 64) {
+                        store_pixel_f16(v, ui.out, ui.H, ui.W, y0 + j, x);
                     } else {
                         store_pixel<C::CO>(v, ui.out, P.out_fp8, P.out_inv_scale, ui.H, ui.W, y0 + j, x);
                     }
@@ -848,11 +850,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
 }
 
 // ---------------------------------------------------------------------------
-// Layer-1 input: per pixel (c_hi, c_hi, c_lo, z_hi, z_hi, z_lo, 0, 0) as bf16,
-// 16 bytes, pixel-major (one chunk of the chunk-planar layout) into act[1].
+// Layer-1 input: per pixel, c and z each split exactly into three bf16 parts
+// v = v0 + v1 + v2 (split3_bf16), laid out as the K elements
+//   (c0, c0, c1, c0, c1, c2, z0, z0 | z1, z0, z1, z2, 0, 0, 0, 0)
+// in two 16-byte chunks of the chunk-planar layout (chunk 0 in act[1], chunk 1
+// H*W*16 bytes after it).  The packed layer-1 weights hold the matching
+// (w0, w1, w0, w2, w1, w0) per input channel, so one bf16 MMA forms
+// v0 w0 + v0 w1 + v1 w0 + v0 w2 + v1 w1 + v2 w0: every product whose size is
+// above 2^-24 |v w| (the terms left out are below 2^-25 |v w|), i.e. the
+// layer-1 sums carry float32-level error, as a float32 convolution would.
 // z comes from Philox4x32-10 with one call per aligned group of 4 indices g.
-// The (hi, hi, lo) pattern pairs with the weights' (w_hi, w_lo, w_hi), so one
-// bf16 MMA forms v_hi w_hi + v_hi w_lo + v_lo w_hi (~2^-16 relative error).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__ imgs, int n_imgs, uint64_t seed)
 {
@@ -878,10 +885,11 @@ __global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__
         const uint64_t g = g0 + l;
         if (g >= npx) break;
         const float z = (float)(lanes[l] >> 8) * (1.0f / 16777216.0f);
-        float ch, cl, zh, zl;
-        split_bf16(cv[l], ch, cl);
-        split_bf16(z, zh, zl);
-        out[g] = make_uint4(pack_bf16x2(ch, ch), pack_bf16x2(cl, zh), pack_bf16x2(zh, zl), 0u);
+        float c0, c1, c2, z0, z1, z2;
+        split3_bf16(cv[l], c0, c1, c2);
+        split3_bf16(z, z0, z1, z2);
+        out[g] = make_uint4(pack_bf16x2(c0, c0), pack_bf16x2(c1, c0), pack_bf16x2(c1, c2), pack_bf16x2(z0, z0));
+        out[npx + g] = make_uint4(pack_bf16x2(z1, z0), pack_bf16x2(z1, z2), 0u, 0u);
     }
 }
 
@@ -915,13 +923,13 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__r
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND, bool TR = false, int CH = 64>
+template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false>
 ht_status ensure_attr()
 {
     static bool attr_set = false;
     if (!attr_set) {
-        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND, TR, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg<FP8, KIND, CH>::SMEM));
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND, TR, CH, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<FP8, KIND, CH, F16>::SMEM));
         attr_set = true;
     }
     return HT_OK;
@@ -975,20 +983,24 @@ ht_status ensure_all_attrs()
         (st = ensure_attr<false, KIND_FIRST, false, 32>()) != HT_OK ||
         (st = ensure_attr<false, KIND_HIDDEN, false, 32>()) != HT_OK ||
         (st = ensure_attr<false, KIND_RES, false, 32>()) != HT_OK ||
-        (st = ensure_attr<false, KIND_RESHEAD, false, 32>()) != HT_OK)
+        (st = ensure_attr<false, KIND_RESHEAD, false, 32>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_FIRST, false, 64, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HIDDEN, false, 64, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HEADPART, false, 64, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HEAD4, false, 64, true>()) != HT_OK)
         return st;
     return HT_OK;
 }
 
-template <bool FP8, int KIND, bool TR = false, int CH = 64>
+template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false>
 ht_status launch_conv(const ConvParams &P, cudaStream_t s)
 {
-    const ht_status st = ensure_attr<FP8, KIND, TR, CH>();
+    const ht_status st = ensure_attr<FP8, KIND, TR, CH, F16>();
     if (st != HT_OK) return st;
     const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
     ht_prof_start(KIND == KIND_FIRST ? HTK_FIRST_TC : KIND == KIND_HEAD4 ? HTK_HEAD_TC
-                                                  : FP8 ? HTK_CONV_TC_FP8 : HTK_CONV_TC_BF16, s);
-    k_conv_tc<FP8, KIND, TR, CH><<<grid, NTHREADS, Cfg<FP8, KIND, CH>::SMEM, s>>>(P);
+                  : FP8 ? HTK_CONV_TC_FP8 : F16 ? HTK_CONV_TC_FP16 : HTK_CONV_TC_BF16, s);
+    k_conv_tc<FP8, KIND, TR, CH, F16><<<grid, NTHREADS, Cfg<FP8, KIND, CH, F16>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -1059,9 +1071,24 @@ uint8_t f64_to_e4m3_rne(double x)
 
 }  // namespace
 
+uint16_t f32_to_f16_rne_host(float f)
+{
+    const __half h = __float2half_rn(f);
+    uint16_t b;
+    memcpy(&b, &h, 2);
+    return b;
+}
+float f16_to_f32_host(uint16_t b)
+{
+    __half h;
+    memcpy(&h, &b, 2);
+    return __half2float(h);
+}
+
 ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
 {
     const bool fp8 = (p->prec == HT_FP8_E4M3);
+    const bool f16 = (p->prec == HT_FP16);
     const int CH = p->width;                                   // hidden width (64, or 32 for the residual policy)
     const int cpc = fp8 ? 16 : 8, nchunk = CH / cpc;
     const size_t layer_bytes = (size_t)9 * nchunk * CH * 16;
@@ -1106,6 +1133,9 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
                     const size_t off = ((((size_t)dx * nchunk + c / cpc) * 3 + (2 - dy)) * CH + n) * 16;
                     if (fp8) {
                         dst[off + (c % cpc)] = f64_to_e4m3_rne((double)wv / sc);
+                    } else if (f16) {
+                        const uint16_t b = f32_to_f16_rne_host(wv);
+                        memcpy(dst + off + 2 * (c % cpc), &b, 2);
                     } else {
                         const uint16_t b = f32_to_bf16_rne(wv);
                         memcpy(dst + off + 2 * (c % cpc), &b, 2);
@@ -1114,8 +1144,10 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
         }
     }
     {
-        // layer 1: B = [dx][chunk 2][3 dy][CH n][8 bf16]; per tap k = 0..5 holds
-        // (w_hi(c), w_lo(c), w_hi(c), w_hi(z), w_lo(z), w_hi(z)), k = 6..15 zero
+        // layer 1: B = [dx][chunk 2][3 dy][CH n][8 bf16]; per tap, K elements
+        // k = 6 ci + j (ci = 0 for c, 1 for z) hold (w0, w1, w0, w2, w1, w0) of the exact
+        // three-part bf16 split w = w0 + w1 + w2, k = 12..15 zero (the pairing of
+        // k_first_input's (v0, v0, v1, v0, v1, v2))
         float w0[64 * 2 * 9];
         e = cudaMemcpyAsync(w0, p->d_w + p->w_off[0], sizeof(float) * CH * 2 * 9, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1126,15 +1158,19 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
                 for (int ci = 0; ci < 2; ++ci) {
                     const int dy = tap / 3, dx = tap % 3;
                     const float w = w0[(n * 2 + ci) * 9 + tap];
-                    const uint16_t hi = f32_to_bf16_rne(w);
-                    uint32_t hb32 = (uint32_t)hi << 16;
-                    float hf;
-                    memcpy(&hf, &hb32, 4);
-                    const uint16_t lo = f32_to_bf16_rne(w - hf);
-                    const uint16_t trip[3] = {hi, lo, hi};
-                    for (int j = 0; j < 3; ++j) {
-                        const int k = 3 * ci + j;            // chunk 0 only
-                        pk[(((dx * 2 + 0) * 3 + (2 - dy)) * CH + n) * 8 + k] = trip[j];
+                    uint16_t part[3];
+                    float rest = w;
+                    for (int q = 0; q < 3; ++q) {            // exact: each remainder fits float32
+                        part[q] = f32_to_bf16_rne(rest);
+                        const uint32_t b32 = (uint32_t)part[q] << 16;
+                        float pf;
+                        memcpy(&pf, &b32, 4);
+                        rest -= pf;
+                    }
+                    const uint16_t six[6] = {part[0], part[1], part[0], part[2], part[1], part[0]};
+                    for (int j = 0; j < 6; ++j) {
+                        const int k = 6 * ci + j;
+                        pk[(((dx * 2 + k / 8) * 3 + (2 - dy)) * CH + n) * 8 + k % 8] = six[j];
                     }
                 }
         if (e == cudaSuccess && !p->d_w1pack) e = cudaMalloc(&p->d_w1pack, sizeof(pk));
@@ -1169,18 +1205,36 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
         float wl[4 * 64 * 9];
         e = cudaMemcpyAsync(wl, p->d_w + p->w_off[p->L - 1], sizeof(wl), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        const size_t part = (size_t)3 * 8 * 3 * 16 * 8;          // bf16 elements
+        const size_t part = (size_t)3 * 8 * 3 * 16 * 8;          // 16-bit elements
         std::vector<uint16_t> pk(part, 0);
+        // FP16 form: binary16 hi / lo parts of w x 2^k, with 2^k putting the largest |w| near
+        // 2^14 (the parts stay normal binary16 numbers); the logits are multiplied by 2^-k
+        float wsc = 1.f;
+        p->head4_inv_scale = 1.f;
+        if (f16) {
+            float amax = 0.f;
+            for (int k = 0; k < 4 * 64 * 9; ++k) amax = fmaxf(amax, fabsf(wl[k]));
+            int k2 = amax > 0.f ? (int)floor(log2(16384.0 / amax)) : 0;
+            k2 = k2 < -14 ? -14 : k2 > 24 ? 24 : k2;
+            wsc = ldexpf(1.f, k2);
+            p->head4_inv_scale = ldexpf(1.f, -k2);
+        }
         for (int n = 0; n < 4; ++n)
             for (int c = 0; c < 64; ++c)
                 for (int tap = 0; tap < 9; ++tap) {
                     const int dy = tap / 3, dx = tap % 3;
-                    const float w = wl[(n * 64 + c) * 9 + tap];
-                    const uint16_t hi = f32_to_bf16_rne(w);
-                    uint32_t hb32 = (uint32_t)hi << 16;
-                    float hf;
-                    memcpy(&hf, &hb32, 4);
-                    const uint16_t lo = f32_to_bf16_rne(w - hf);
+                    const float w = wl[(n * 64 + c) * 9 + tap] * wsc;
+                    uint16_t hi, lo;
+                    if (f16) {
+                        hi = f32_to_f16_rne_host(w);
+                        lo = f32_to_f16_rne_host(w - f16_to_f32_host(hi));
+                    } else {
+                        hi = f32_to_bf16_rne(w);
+                        uint32_t hb32 = (uint32_t)hi << 16;
+                        float hf;
+                        memcpy(&hf, &hb32, 4);
+                        lo = f32_to_bf16_rne(w - hf);
+                    }
                     // columns n (hi part) and 4 + n (lo part) of the 16-column dy block
                     const size_t off = ((((size_t)dx * 8 + c / 8) * 3 + (2 - dy)) * 16 + n) * 8 + (c % 8);
                     pk[off] = hi;
@@ -1197,8 +1251,8 @@ ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s)
     }
     e = cudaMemcpyAsync(p->d_wpack, hp, layer_bytes * n_inner, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && fp8) e = cudaMemcpyAsync(p->d_wscale, hs, sizeof(float) * 64 * n_inner, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && CH == 64 && n_inner > 0) {
-        // CTA-pair images: for CTA r, per (dx, K step) group, variant v's rows
+    if (e == cudaSuccess && CH == 64 && n_inner > 0 && !f16) {
+        // CTA-pair images (BF16 and FP8 forms): for CTA r, per (dx, K step) group, variant v's rows
         // [r n/2, (r+1) n/2) of its stacked column range, both 16-byte K chunks
         const int ksteps = nchunk / 2;
         const size_t wb = (size_t)3 * ksteps * PV_GROUP_BYTES;     // one CTA's image of one layer
@@ -1292,6 +1346,10 @@ void ht_preload_conv_tc()
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, false, 32>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_RES, false, 32>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_RESHEAD, false, 32>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, false, 64, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, false, 64, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEADPART, false, 64, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEAD4, false, 64, true>);
     cudaFuncGetAttributes(&fa, k_conv_tc2<false, KIND_HIDDEN>);
     cudaFuncGetAttributes(&fa, k_conv_tc2<false, KIND_HEADPART>);
     cudaFuncGetAttributes(&fa, k_conv_tc2<true, KIND_HIDDEN>);
@@ -1408,7 +1466,8 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
                            uint64_t seed, int ru, int order, int pair, int *err, cudaStream_t s)
 {
     const bool fp8 = (p->prec == HT_FP8_E4M3);
-    pair = pair && p->d_wpack2 && p->arch != HT_ARCH_RESNET;
+    const bool f16 = (p->prec == HT_FP16);
+    pair = pair && p->d_wpack2 && p->arch != HT_ARCH_RESNET && !f16;
     const int n_inner = p->L - 2;
     for (const TcGroup &G : groups) {
         const ImgDesc *dt = d_table + G.g0;
@@ -1441,6 +1500,7 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
             P.out_fp8 = o8 ? 1 : 0;
             const ht_status st = p->arch == HT_ARCH_RESNET ? launch_conv<false, KIND_FIRST, false, 32>(P, s)
                                  : fp8                      ? launch_conv<true, KIND_FIRST>(P, s)
+                                 : f16                      ? launch_conv<false, KIND_FIRST, false, 64, true>(P, s)
                                                             : launch_conv<false, KIND_FIRST>(P, s);
             if (st != HT_OK) return st;
         }
@@ -1505,8 +1565,10 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
                 continue;
             }
             const ht_status st =
-                fp8 ? (fuse_head ? launch_conv<true, KIND_HEADPART>(P, s) : launch_conv<true, KIND_HIDDEN>(P, s))
-                    : (fuse_head ? launch_conv<false, KIND_HEADPART>(P, s) : launch_conv<false, KIND_HIDDEN>(P, s));
+                fp8   ? (fuse_head ? launch_conv<true, KIND_HEADPART>(P, s) : launch_conv<true, KIND_HIDDEN>(P, s))
+                : f16 ? (fuse_head ? launch_conv<false, KIND_HEADPART, false, 64, true>(P, s)
+                                   : launch_conv<false, KIND_HIDDEN, false, 64, true>(P, s))
+                      : (fuse_head ? launch_conv<false, KIND_HEADPART>(P, s) : launch_conv<false, KIND_HIDDEN>(P, s));
             if (st != HT_OK) return st;
             cur ^= 1;
         }
@@ -1522,11 +1584,12 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
             P.wpack = p->d_wpack4;
             for (int c = 0; c < 64; ++c) {
                 P.bias[c] = c < 4 ? p->h_b[p->b_off[p->L - 1] + c] : 0.f;
-                P.scale[c] = 1.f;
+                P.scale[c] = c < 4 ? p->head4_inv_scale : 1.f;
             }
             P.out_inv_scale = 1.f;
             P.out_fp8 = 0;
-            const ht_status st = launch_conv<false, KIND_HEAD4>(P, s);
+            const ht_status st = f16 ? launch_conv<false, KIND_HEAD4, false, 64, true>(P, s)
+                                     : launch_conv<false, KIND_HEAD4>(P, s);
             if (st != HT_OK) return st;
         }
     }

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -63,7 +64,7 @@ int *ht_device_error_flag();
 
 // Kernel timing hooks (no-ops unless ht_profile_begin was called).
 enum ht_kernel_id { HTK_FIRST_TC = 0, HTK_CONV_TC_BF16, HTK_CONV_TC_FP8, HTK_HEAD_TC, HTK_CONV_FP32, HTK_HEAD_FP32,
-                    HTK_REWARD, HTK_TOGGLE, HTK_SPECTRUM, HTK_TRAIN, HTK_FIRST_INPUT, HTK_COUNT };
+                    HTK_REWARD, HTK_TOGGLE, HTK_SPECTRUM, HTK_TRAIN, HTK_FIRST_INPUT, HTK_CONV_TC_FP16, HTK_COUNT };
 void ht_prof_start(int kid, cudaStream_t s);
 void ht_prof_stop(cudaStream_t s);
 
@@ -121,7 +122,10 @@ struct ht_policy {
     float h_wscale[HT_MAX_LAYERS * 64];
     float h_headw[9 * 64];          // 1-logit head: last-layer weights as [9 taps][64]
     void *d_w1pack = nullptr;       // layer 1 for the tensor cores: bf16 hi/lo split, [dx][chunk][3 dy][n][8]
-    void *d_wpack4 = nullptr;       // 4-logit head: [dx][chunk][3 dy][16 n][8] bf16, n = hi 0..3, lo 4..7
+    void *d_wpack4 = nullptr;       // 4-logit head: [dx][chunk][3 dy][16 n][8] bf16 (FP16 form: binary16),
+                                    // n = hi 0..3, lo 4..7
+    float head4_inv_scale = 1.f;    // FP16 form: the 4-logit head's weights are stored x 2^k (kept in the
+                                    // binary16 normal range), its logits multiplied back by 2^-k
     float head_bias = 0.f;
     // conv schedule of the tensor-core forms (set by ht_policy_autotune): rows per
     // work unit (TMEM accumulator blocks) and unit order
@@ -137,6 +141,11 @@ struct ht_policy {
 };
 
 ht_status ht_policy_ensure_ws(ht_policy *p, size_t bytes);
+// Argument checks shared by entry points (host only, no CUDA call): reward options
+// (radius, levels, window sigmas) and image descriptors (non-null, min_side <= h, w <= 16384,
+// pitch >= w).  Defined in api.cu inside its extern "C" block.
+extern "C" ht_status ht_validate_reward_opts(const ht_reward_opts *o);
+extern "C" ht_status ht_validate_images(const ht_image *imgs, int n, int min_side);
 // The descriptor checks of ht_create_policy (shape, head, precision, architecture).
 ht_status ht_validate_desc(const ht_policy_desc *d);
 ht_status ht_pack_tc_weights(ht_policy *p, cudaStream_t s);

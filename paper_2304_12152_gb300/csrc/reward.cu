@@ -544,11 +544,14 @@ size_t ht_toggle_scratch_floats_batch(const ht_image *c, int n, int r)
 // device array below instead, which every GPU that loads the library holds
 // until the process exits.
 //
-// Host code only sees the array's host-side stand-in; its device address is
-// looked up once per device with cudaGetSymbolAddress (with that device
-// current) on the first call, and cached.  All calls share the array: the
-// accumulators are cleared at the start of every call, and calls whose work
-// overlaps on the GPU (different streams, no ordering) race on it.
+// Host code only sees the array's host-side stand-in; its device address comes
+// from cudaGetSymbolAddress with the calling device current.  It is looked up on
+// every call made outside a stream capture (so a device reset, which reloads the
+// module at a new address, is followed), and the call caches it per device; a call
+// whose stream is capturing uses that cache, so the first call on a device must
+// come before any capture.  All calls share the array: the accumulators are
+// cleared at the start of every call, and calls whose work overlaps on the GPU
+// (different streams, no ordering) race on it.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) double g_reward_noalloc_acc[3 * HT_REWARD_NOALLOC_MAX_IMAGES];
 
@@ -581,27 +584,26 @@ extern "C" ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const 
                                        const ht_reward_opts *opts, double *out, void *stream)
 {
     HT_RANGE("ht_reward_noalloc");
-    HT_CHECK_ARG(opts != nullptr, "null reward options");
-    HT_CHECK_ARG(opts->radius >= 1 && opts->radius <= 7, "radius must be in [1, 7]");
-    HT_CHECK_ARG(opts->sigma_hvs > 0 && opts->sigma_ssim > 0, "window sigmas must be positive");
-    HT_CHECK_ARG(c != nullptr && n >= 1, "need at least one image");
+    // the same argument checks as ht_reward, plus the array's capacity
+    ht_status st = ht_validate_reward_opts(opts);
+    if (st != HT_OK) return st;
+    st = ht_validate_images(c, n, 2 * opts->radius + 1);
+    if (st != HT_OK) return st;
     HT_CHECK_ARG(n <= HT_REWARD_NOALLOC_MAX_IMAGES, "ht_reward_noalloc takes at most %d images per call (got %d)",
                  HT_REWARD_NOALLOC_MAX_IMAGES, n);
     HT_CHECK_ARG(bits && out, "null argument");
+    for (int i = 0; i < n; ++i) HT_CHECK_ARG(bits[i] != nullptr, "image %d: null bits", i);
     const int r = opts->radius;
-    for (int i = 0; i < n; ++i) {
-        HT_CHECK_ARG(c[i].contone && bits[i], "image %d: null pointer", i);
-        HT_CHECK_ARG(c[i].h >= 2 * r + 1 && c[i].w >= 2 * r + 1 && c[i].h <= 16384 && c[i].w <= 16384,
-                     "image %d: size %dx%d outside [%d, 16384]", i, c[i].h, c[i].w, 2 * r + 1);
-        HT_CHECK_ARG(c[i].pitch >= c[i].w, "image %d: pitch < width", i);
-    }
     int dev = 0;
     HT_CUDA_TRY(cudaGetDevice(&dev));
     HT_CHECK_ARG(dev >= 0 && dev < 64, "device index %d out of range", dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    HT_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
     double *acc = nullptr;
     {
         std::lock_guard<std::mutex> g(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void *addr = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&addr, g_reward_noalloc_acc);
             if (e != cudaSuccess || addr == nullptr) {
@@ -609,15 +611,16 @@ extern "C" ht_status ht_reward_noalloc(const ht_image *c, const uint32_t *const 
                 return HT_ERR_CUDA;
             }
             g_noalloc_addr[dev] = (double *)addr;
+        } else if (!g_noalloc_addr[dev]) {
+            ht_set_error("ht_reward_noalloc: the first call on a device must come before any stream capture");
+            return HT_ERR_INVALID_ARG;
         }
         acc = g_noalloc_addr[dev];
     }
-    cudaStream_t s = (cudaStream_t)stream;
     const Win wn = make_win(*opts);
     HT_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)n, s));
     for (int base = 0; base < n; base += RW_MAXB) {
-        const ht_status st = launch_reward_tiles(c, bits, base, min(RW_MAXB, n - base), wn, opts->levels,
-                                                 acc + 3 * (size_t)base, s);
+        st = launch_reward_tiles(c, bits, base, min(RW_MAXB, n - base), wn, opts->levels, acc + 3 * (size_t)base, s);
         if (st != HT_OK) return st;
     }
     for (int base = 0; base < n; base += 64) {

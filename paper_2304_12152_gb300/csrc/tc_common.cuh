@@ -174,13 +174,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor: D = F32 (bit 4), A/B format at bits 7/10 (BF16 = 1
-// for kind::f16, E4M3 = 0 for kind::f8f6f4), both K-major, N >> 3 at bit 17,
-// M >> 4 at bit 24.
+// Instruction descriptor: D = F32 (bit 4), A/B format at bits 7/10 (kind::f16:
+// F16 = 0, BF16 = 1; kind::f8f6f4: E4M3 = 0), both K-major, N >> 3 at bit 17,
+// M >> 4 at bit 24.  AB is the A/B format code (A and B always share it).
+template <uint32_t AB>
+__host__ __device__ constexpr uint32_t idesc_m128_ab(uint32_t n)
+{
+    return (1u << 4) | (AB << 7) | (AB << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
 template <bool FP8>
 __host__ __device__ constexpr uint32_t idesc_m128(uint32_t n)
 {
-    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+    return idesc_m128_ab<FP8 ? 0u : 1u>(n);
 }
 
 // Warp-wide issuing: the whole warp runs the MMA schedule, so its state (slot, row,
@@ -366,10 +371,28 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
     return (lo & 0xFFFFu) | (hi << 16);
 }
 __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo)
+__device__ __forceinline__ float f16_round(float v) { return __half2float(__float2half_rn(v)); }
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b)
 {
-    hi = bf16_round(v);
-    lo = bf16_round(v - hi);
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+// rounding of a stored activation: bf16, or IEEE binary16 in the FP16 form
+template <bool F16>
+__device__ __forceinline__ float act_round(float v)
+{
+    if constexpr (F16) return f16_round(v);
+    else return bf16_round(v);
+}
+// v = a + b + c exactly for a float32 v: a = bf16(v) holds its top 8 significant bits,
+// v - a (exact in float32) has at most 16 significant bits, b = bf16(v - a) the next 8,
+// and the remainder v - a - b has at most 8, so c = bf16(v - a - b) is exact.
+__device__ __forceinline__ void split3_bf16(float v, float &a, float &b, float &c)
+{
+    a = bf16_round(v);
+    const float r = v - a;
+    b = bf16_round(r);
+    c = bf16_round(r - b);
 }
 
 // Stores CO channel values of one pixel into the chunk-planar layout.
@@ -407,10 +430,27 @@ __device__ __forceinline__ void store_pixel(const float *v, void *out, int out_f
     }
 }
 
-// Epilogue of a bf16-output layer: v * scale + bias (per channel), ReLU, bf16,
-// into the chunk-planar layout.  Two channels per instruction: a packed FP32
-// FMA (each lane an ordinary fmaf) and one convert that rounds to nearest even
-// and clamps negatives to zero (the same value as rounding max(x, 0)).
+// Stores 64 channel values of one pixel as IEEE binary16 (8 per chunk).
+__device__ __forceinline__ void store_pixel_f16(const float *v, void *out, int H, int W, int y, int x)
+{
+    uint8_t *o = (uint8_t *)out;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint4 q;
+        q.x = pack_f16x2(v[8 * c + 0], v[8 * c + 1]);
+        q.y = pack_f16x2(v[8 * c + 2], v[8 * c + 3]);
+        q.z = pack_f16x2(v[8 * c + 4], v[8 * c + 5]);
+        q.w = pack_f16x2(v[8 * c + 6], v[8 * c + 7]);
+        *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = q;
+    }
+}
+
+// Epilogue of a bf16-output layer (F16: binary16 output): v * scale + bias (per
+// channel), ReLU, rounding, into the chunk-planar layout.  Two channels per
+// instruction: a packed FP32 FMA (each lane an ordinary fmaf) and one convert that
+// rounds to nearest even and clamps negatives to zero (the same value as rounding
+// max(x, 0)).
+template <bool F16 = false>
 __device__ __forceinline__ void store_pixel_bias_relu_bf16(const float *v, const float *scale, const float *bias,
                                                           void *out, int H, int W, int y, int x)
 {
@@ -428,7 +468,8 @@ __device__ __forceinline__ void store_pixel_bias_relu_bf16(const float *v, const
             asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rr) : "l"(vv), "l"(ss), "l"(bb));
             float lo, hi;
             asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(rr));
-            asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w4[h]) : "f"(hi), "f"(lo));
+            if constexpr (F16) asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(w4[h]) : "f"(hi), "f"(lo));
+            else asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w4[h]) : "f"(hi), "f"(lo));
         }
         *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
     }

@@ -264,7 +264,7 @@ ht_status ht_train_create(ht_policy *p, const ht_train_desc *d, ht_train **out)
                  "training needs a sigmoid-output head (binary or the multitoning prototype)");
     HT_CHECK_ARG(p->head == HT_HEAD_SIGMOID || d->estimator == HT_EST_LE,
                  "the multitoning prototype trains with the local-expectation estimator");
-    if (p->prec == HT_FP8_E4M3 || (p->prec == HT_BF16 && !ht_train_tc_supported(p))) {
+    if (p->prec == HT_FP8_E4M3 || p->prec == HT_FP16 || (p->prec == HT_BF16 && !ht_train_tc_supported(p))) {
         ht_set_error("training supports the FP32 form and the BF16 form of 2 -> 64 x (L-1) -> 1 policies");
         return HT_ERR_UNSUPPORTED;
     }

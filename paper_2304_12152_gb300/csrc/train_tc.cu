@@ -634,7 +634,7 @@ bool ht_train_tc_supported(const ht_policy *p)
 
 // Per image of a step, in the arena (px = h * w), each region 256-byte aligned:
 // activation buffers [nbuf][px][128 B], ReLU masks [L-1][px] x 8 B, layer-1 split
-// input [px][16 B], head partials [9][px] x 4 B, gradient ping-pong 2 x [px][128 B].
+// input [2 chunks][px][16 B], head partials [9][px] x 4 B, gradient ping-pong 2 x [px][128 B].
 //
 // Activation recomputation (checkpoint stride k > 1): only the hidden activations
 // a_l with l % k == 0, and a_{L-2} (the head's input), keep a buffer for the
@@ -669,7 +669,7 @@ ImgRegions img_regions(int nh, int nbuf, size_t px)
     r.acts = 0;
     r.masks = r.acts + al256((size_t)nbuf * px * 128);
     r.split = r.masks + al256((size_t)nh * px * 8);
-    r.part9 = r.split + al256(px * 16);
+    r.part9 = r.split + al256(px * 32);
     r.g0 = r.part9 + al256(px * 36);
     r.g1 = r.g0 + al256(px * 128);
     r.total = r.g1 + al256(px * 128);
