@@ -21,3 +21,37 @@ def decided_mask(p_or: np.ndarray, u: np.ndarray, mode: int, margin: float = MAR
 def compare_levels(gpu: np.ndarray, ref: np.ndarray, decided: np.ndarray):
     mism = (gpu != ref) & decided
     return int(decided.sum()), int(mism.sum())
+
+
+# Tight agreement of a reduced-precision tensor-core form with the oracle that emulates its
+# rounding points (FP64 accumulation).  Keyed by (storage format, rounded hidden layers):
+# (median |dp|, fraction of pixels with |dp| > 1e-6, 99.9th percentile, max).  The bounds
+# come from the models of tests/_rounding_model.py (checked in tests/test_parity_model.py):
+# an implementation whose layer 1 is float32-accurate and whose inner sums are formed in
+# float32 -- rounded to nearest, or truncated as tensor cores do (the conservative "trunc"
+# model with 22 kept bits, whose statistics the rows follow) -- leaves the typical pixel of
+# a shallow policy within float32 rounding of the oracle (median ~1e-8); rounding flips near
+# bf16 / fp16 boundaries seed the rest and spread layer by layer, so that over seven layers
+# they reach most pixels (binary16 flips are 8 times more frequent than bfloat16 ones and 8
+# times smaller).  A form whose layer 1 carried only bf16 hi/lo products (relative error
+# ~2^-16) fails the two- and three-layer bf16 rows and the two-layer fp16 row.
+TIGHT = {
+    ("bf16", 2): (1e-6, 0.12, 4e-4, 1.5e-3),
+    ("bf16", 3): (1e-6, 0.30, 8e-4, 2e-3),
+    ("bf16", 7): (3e-4, 0.95, 3e-3, 5e-3),
+    ("fp16", 2): (3e-6, 0.70, 1e-4, 2e-4),
+    ("fp16", 3): (3e-5, 0.97, 2.5e-4, 4e-4),
+    ("fp16", 7): (1.5e-4, 1.00, 8e-4, 1.2e-3),
+}
+
+
+def tight_rule(dp: np.ndarray, fmt: str, stages: int):
+    """Failures (empty list = pass) of |p_form - p_oracle| against TIGHT for a policy with
+    `stages` rounded hidden layers (the smallest tabulated depth >= stages)."""
+    keys = sorted(k[1] for k in TIGHT if k[0] == fmt and k[1] >= stages)
+    med_b, frac_b, p999_b, max_b = TIGHT[(fmt, keys[0])]
+    d = np.abs(np.asarray(dp, np.float64)).ravel()
+    got = dict(median=float(np.median(d)), frac=float((d > 1e-6).mean()),
+               p999=float(np.quantile(d, 0.999)), max=float(d.max()))
+    bounds = dict(median=med_b, frac=frac_b, p999=p999_b, max=max_b)
+    return [f"{k} {got[k]:.3g} > {bounds[k]:.3g}" for k in got if got[k] > bounds[k]]

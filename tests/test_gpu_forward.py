@@ -1,18 +1,16 @@
 """GPU parity of the policy forward + head (both forms) against the FP64 oracle.
 
 Rules: FP32 form -- actions equal the oracle's on every pixel the oracle decides by
-more than 1e-4 (|p - u| > 1e-4), probabilities within 2e-5.  BF16 form -- the same bit
-rule against the oracle emulating the BF16 rounding points (residual mismatches
-counted, at most 1e-3 of the decided pixels).  Probabilities: the BF16-emulating
-oracle rounds at the same points but accumulates in FP64, so any hidden activation whose
-FP32 accumulation lands within the accumulation error of a bf16 rounding boundary rounds
-the other way; with ~1e5 activations in a pixel's receptive field a few such one-ulp
-flips reach every pixel, which bounds the agreement at 99.9% within 2e-3 and all within
-4e-3.  Against the pure FP64 oracle: seven bf16 rounding stages (unit roundoff 2^-9) move
-a logit of magnitude ~2 by up to ~1e-2, i.e. p by up to ~3e-3: 99.9% within 3e-3, all
-within 6e-3."""
+more than 1e-4 (|p - u| > 1e-4), probabilities within 2e-5.  BF16 form -- against the
+oracle emulating the BF16 rounding points (quant 1), the tight rule of tests/_cases.TIGHT
+for seven rounded hidden layers: median |dp| <= 1e-6 (the typical pixel agrees to float32
+rounding), |dp| > 1e-6 on at most 55% of the pixels, 99.9% within 2e-3, all within 4e-3
+-- the spread that float32 accumulation itself produces on this policy (rounding flips
+near bf16 boundaries, tests/test_parity_model.py); the same bit rule, residual mismatches
+at most 2e-4 of the decided pixels.  Against the pure FP64 oracle: seven bf16 rounding
+stages (unit roundoff 2^-9) move a logit of magnitude ~2 by up to ~1e-2, i.e. p by up to
+~3e-3: 99.9% within 3e-3, all within 6e-3."""
 
-BF16_Q_P999, BF16_Q_MAX = 2e-3, 4e-3
 BF16_X_P999, BF16_X_MAX = 3e-3, 6e-3
 
 
@@ -26,7 +24,7 @@ import oracle as O
 from paper_2304_12152_gb300 import _native as N
 from paper_2304_12152_gb300 import api, synth
 
-from _cases import compare_levels, decided_mask
+from _cases import compare_levels, decided_mask, tight_rule
 
 pytestmark = pytest.mark.gpu
 
@@ -118,15 +116,18 @@ def test_bf16_wide_net_tiles_and_tails(mode):
     ref_q = _oracle(imgs, ws, bs, mode, 1, quant=1)
     ref_x = _oracle(imgs, ws, bs, mode, 1, quant=0)
     tot_n = tot_bad = 0
+    diffs = []
     for i in range(len(imgs)):
         p_q, lev_q, u = ref_q[i]
         p_x = ref_x[i][0]
-        assert np.abs(probs[i] - p_q).max() < BF16_Q_MAX and _p999(probs[i] - p_q) < BF16_Q_P999
+        diffs.append((probs[i] - p_q).ravel())
         assert np.abs(probs[i] - p_x).max() < BF16_X_MAX and _p999(probs[i] - p_x) < BF16_X_P999
         n, bad = compare_levels(lev[i], lev_q, decided_mask(p_q, u, mode))
         tot_n += n
         tot_bad += bad
-    assert tot_bad <= max(1, 1e-3 * tot_n), (tot_bad, tot_n)
+    fails = tight_rule(np.concatenate(diffs), "bf16", 7)
+    assert fails == [], fails
+    assert tot_bad <= max(2, 2e-4 * tot_n), (tot_bad, tot_n)
 
 
 def test_bf16_full_size_sampled():
@@ -139,7 +140,6 @@ def test_bf16_full_size_sampled():
     lev, probs, _ = _run(pol, imgs, 1, seed=1)
     rng = np.random.default_rng(0)
     tot_n = tot_bad = 0
-    worst = 0.0
     diffs = []
     for i in range(8):
         y, x = rng.integers(32, 2048 - 64, size=2)
@@ -150,13 +150,13 @@ def test_bf16_full_size_sampled():
             y0, x0, rh, rw = reg
             (p_q, lev_q, u), = _oracle([imgs[i]], ws, bs, 1, 1, quant=1, region=reg, image_ids=[i])
             pg = probs[i][:, y0:y0 + rh, x0:x0 + rw]
-            worst = max(worst, float(np.abs(pg - p_q).max()))
             diffs.append((pg - p_q).ravel())
             n, bad = compare_levels(lev[i][y0:y0 + rh, x0:x0 + rw], lev_q, decided_mask(p_q, u, 1))
             tot_n += n
             tot_bad += bad
-    assert worst < BF16_Q_MAX and _p999(np.concatenate(diffs)) < BF16_Q_P999
-    assert tot_bad <= max(1, 1e-3 * tot_n), (tot_bad, tot_n)
+    fails = tight_rule(np.concatenate(diffs), "bf16", 7)
+    assert fails == [], fails
+    assert tot_bad <= max(2, 2e-4 * tot_n), (tot_bad, tot_n)
     # the CTA-pair schedule (the benchmark's autotuned launch) gives the same outputs bit for bit
     pol.set_schedule(8, 0, 1)
     lev2, probs2, _ = _run(pol, imgs, 1, seed=1)

@@ -103,14 +103,17 @@ def test_coma_train_step_matches_oracle():
         assert ew <= 2e-3 and eb <= 2e-3, errs
 
 
-def oracle_step_multitone(crops, ws, bs, seed, S, L, quant=0):
+def oracle_step_multitone(crops, ws, bs, seed, S, L, quant=0, band=0.0):
     """Training step of the multitoning prototype (Sec. VI-E) from oracle routines:
     levels h^s sampled from v with u^s (stream 1 + s), reward and toggle deltas of the
-    multi-level halftones, the LE surrogate with dL/dv = -(L - 1) dR, the backward."""
+    multi-level halftones, the LE surrogate with dL/dv = -(L - 1) dR, the backward.
+    With band > 0 it also returns the flip bound: the mean over crops and samples of
+    sum |dR_a| over the pixels whose action a form with |dv| <= band may take the other
+    way (|frac - u| or the distance of v (L - 1) from a level within (L - 1) band)."""
     n = len(crops)
     gw = [np.zeros(w.shape) for w in ws]
     gb = [np.zeros(b.shape) for b in bs]
-    l_marl, rs = 0.0, []
+    l_marl, rs, flip = 0.0, [], 0.0
     for i, c in enumerate(crops):
         h, w = c.shape
         lg, p, acts = O.forward(c, ws, bs, noise_seed=seed, image=i, quant=quant, save_acts=True)
@@ -126,10 +129,17 @@ def oracle_step_multitone(crops, ws, bs, seed, S, L, quant=0):
             l_marl += val / (n * S)
             dp += grad / (n * S)
             rs.append(r["R"])
+            if band > 0:
+                t = v * (L - 1)
+                _, frac = O.multitone_pair(v, L)
+                near = (np.abs(frac - u) <= (L - 1) * band) | (np.abs(t - np.rint(t)) <= (L - 1) * band)
+                flip += float(np.abs(dR[near]).sum()) / (n * S)
         a, b = O.backward(c, ws, bs, seed, i, acts, lg, dp, quant=quant)
         for l in range(len(ws)):
             gw[l] += a[l]
             gb[l] += b[l]
+    if band > 0:
+        return l_marl, float(np.mean(rs)), gw, gb, flip
     return l_marl, float(np.mean(rs)), gw, gb
 
 
@@ -157,8 +167,13 @@ def test_multitone_train_step_matches_oracle():
 def test_bf16_multitone_train_step_matches_bf16_oracle():
     """BF16 tensor-core training of the multitoning prototype (4 levels) against the
     quant-1 oracle.  As in the binary BF16 step, samples flip where the level rule's
-    margin is below the forward error (L - 1 times more often than for the binary rule):
-    losses 3e-3 relative, gradients 4e-2 of the layer's largest entry."""
+    margin is below the forward error (L - 1 times more often than for the binary rule).
+    A flip of pixel a moves that sample's reward by its toggle delta dR_a and L_MARL by
+    about (h w) dR_a, so the mean reward is held to the oracle's flip bound (the sum of
+    |dR_a| over the pixels within (L - 1) x 2e-3 of a decision, 2e-3 being the 99.9th
+    percentile bound on |dv| of the 7-layer BF16 rule in tests/_cases.TIGHT), with 1.5x
+    for flips that share a window, and L_MARL to h w times that; gradients 4e-2 of the
+    layer's largest entry."""
     L = 4
     ws, _ = synth.he_normal_policy(WIDE4, 91)
     bs = synth.random_biases(WIDE4, 92, scale=0.1)
@@ -169,11 +184,12 @@ def test_bf16_multitone_train_step_matches_bf16_oracle():
     losses = tr.forward([torch.from_numpy(c).cuda() for c in crops], [], seed)
     gw, gb = tr.backward()
     torch.cuda.synchronize()
-    l_marl, r_mean, ref_w, ref_b = oracle_step_multitone(crops, ws, bs, seed, S, L, quant=1)
+    l_marl, r_mean, ref_w, ref_b, flip = oracle_step_multitone(crops, ws, bs, seed, S, L, quant=1, band=2e-3)
     errs = _grad_errors(gw, gb, ref_w, ref_b)
-    print("multitone bf16: losses", losses, l_marl, r_mean, "errors", errs)
-    assert abs(losses[1] - l_marl) <= 3e-3 * abs(l_marl), (losses, l_marl)
-    assert abs(losses[3] - r_mean) <= 3e-3 * abs(r_mean), (losses, r_mean)
+    print("multitone bf16: losses", losses, l_marl, r_mean, "flip bound", flip, "errors", errs)
+    npx = crops[0].size
+    assert abs(losses[3] - r_mean) <= 1.5 * flip + 1e-9, (losses, r_mean, flip)
+    assert abs(losses[1] - l_marl) <= 1.5 * npx * flip + 1e-6 * abs(l_marl), (losses, l_marl, flip)
     for ew, eb in errs:
         assert ew <= 4e-2 and eb <= 4e-2, errs
 

@@ -126,3 +126,33 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True, timeout=300)
     lines = r.stdout.strip().splitlines()
     assert len(lines) == 2 and all(ln.startswith("RAISED") and "missing_libht.so" in ln for ln in lines), r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("fn", ["ht_reward", "ht_reward_noalloc"])
+@pytest.mark.parametrize("levels", [0, 1, 5, -3])
+def test_reward_entry_points_refuse_bad_levels(fn, levels):
+    """Both reward entry points run the same option checks before any CUDA call: a level
+    count outside [2, 4] is an argument error (the kernels divide by levels - 1)."""
+    L = N.load()
+    o = N.RewardOpts()
+    L.ht_reward_opts_default(C.byref(o))
+    o.levels = levels
+    img = (N.Image * 1)(N.Image(16, 20, 20, 20))
+    bits = (C.c_void_p * 1)(16)
+    st = getattr(L, fn)(img, bits, 1, C.byref(o), C.c_void_p(16), None)
+    assert st == N.HT_ERR_INVALID_ARG and b"levels" in L.ht_last_error()
+
+
+def test_noalloc_reward_source_names_no_allocator():
+    """The allocation-free reward and the launcher it shares with ht_reward name no
+    allocating routine (a later edit adding one fails here, without a GPU)."""
+    src = open(os.path.join(ROOT, "paper_2304_12152_gb300", "csrc", "reward.cu")).read()
+    body = src[src.index('extern "C" ht_status ht_reward_noalloc'):]
+    body = body[:body.index("\n}\n")]
+    launcher = src[src.index("ht_status launch_reward_tiles("):]
+    launcher = launcher[:launcher.index("\n}\n")]
+    for part in (body, launcher):
+        code = re.sub(r"//.*", "", part)
+        for name in ("cudaMalloc", "cudaFree", "cudaMallocAsync", "cudaFreeAsync", "malloc(", "new ",
+                     "ht_device_error_flag", "ht_policy_ensure_ws"):
+            assert name not in code, name
