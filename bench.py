@@ -1,8 +1,8 @@
 #!/usr/bin/env python3
 """Throughput of one-shot halftoning on GB300 (one JSON line on rank 0).
 
-Workload (default): printer-scale inference -- 8 synthetic 2048x2048 contone images,
-8-layer 64-wide policy (2 -> 64 x 7 -> 1) in the BF16 tensor-core form with FP32
+Headline workload (default): printer-scale inference -- 8 synthetic 2048x2048 contone
+images, 8-layer 64-wide policy (2 -> 64 x 7 -> 1) in the BF16 tensor-core form with FP32
 accumulation, fused sigmoid + Philox Bernoulli sampling (seed 1) + 1-bit packing.
 A step = one ht_halftone call over the whole batch.
 
@@ -12,13 +12,19 @@ A step = one ht_halftone call over the whole batch.
                step; copies on their own streams, overlapping the neighbouring steps'
                compute through two buffer sets, as a streaming caller would run it)
   roofline   : dominant kernel (the 64 -> 64 tcgen05 conv) -- algorithmic FLOPs per
-               launch / its mean launch time, measured by the library's CUDA-event
-               instrumentation over the timed region
+               launch / its mean launch time (each launch timed alone by the library's
+               CUDA-event instrumentation, so against the burst peak), with its HBM
+               side (256 algorithmic bytes per pixel) beside it
   fp32_plain : the plain FP32 CUDA-core form of the same net on the same batch
   cpu_baseline: the FP64 C oracle on a bounded crop of the same workload (host cores)
+  configs    : the other workloads, each timed the same way with its own clocks and
+               roofline: the FP16 form of the printer workload, the FP8 multitone batch
+               (4 x 4096^2), the 64-image uneven batch, the plain FP32 256^2 case with its
+               HVS-MSE reward, and the training step (16 x 256^2 + 4 gray, S = 4)
 
 --impl reference times the oracle (the benchmark's reference arm) on bounded crops.
-Multi-GPU (torchrun): independent replicas, weak scaling, max time over ranks.
+Multi-GPU (torchrun): independent replicas, weak scaling, max time over ranks (the
+headline workload only).
 """
 from __future__ import annotations
 
@@ -198,11 +204,14 @@ def run_reference(args):
 WORKLOADS = {
     # name: (description, precision, head, net, mode, seed)
     "printer": ("printer {b}x{h}x{w}, 2->64x7->1 policy, BF16, Bernoulli seed 1, 1-bit packed", "bf16", 0, "wide", 1, 1),
+    "printer_fp16": ("printer {b}x{h}x{w}, 2->64x7->1 policy, FP16 (binary16 weights and activations), Bernoulli "
+                     "seed 1, 1-bit packed", "fp16", 0, "wide", 1, 1),
     "multitone": ("multitone 4x4096x4096, 2->64x7->4 softmax head (levels 0,1/3,2/3,1), FP8 E4M3, Philox seed 2",
                   "fp8", 1, "wide4", 1, 2),
     "uneven": ("uneven batch of 64 images, sizes log-uniform 200x300..4096x3072 (seed 4), BF16, Bernoulli seed 4",
                "bf16", 0, "wide", 1, 4),
-    "small": ("one 256x256 image (seed 0), 2->32x5->1 policy, plain FP32, threshold 0.5", "fp32", 0, "small", 0, 0),
+    "small": ("one 256x256 image (seed 0), 2->32x5->1 policy, plain FP32, threshold 0.5, + HVS-MSE reward",
+              "fp32", 0, "small", 0, 0),
     "proto": ("multitoning prototype 4x4096x4096, 2->64x7->1 sigmoid output, action between the 2 of 4 levels "
               "around it, BF16, Philox seed 2", "bf16", 2, "wide", 1, 2),
     "resnet512": ("residual policy (16 blocks x 32 ch, 34 conv layers) on one 512x512 image (the paper's "
@@ -211,23 +220,27 @@ WORKLOADS = {
                "bf16", 0, "resnet", 1, 1),
 }
 
+# sub-records of the default run (rank 0, one GPU): BASELINE configs 1, 3, 4, 5 and the FP16 form
+SUB_CONFIGS = ("printer_fp16", "multitone", "uneven", "small", "train")
 
-def build_inputs(args, rank):
+
+def build_inputs(args, rank, workload=None):
     from paper_2304_12152_gb300 import synth
+    workload = workload or args.workload
     if args.images and args.side:      # small case of any workload (profiling)
-        seed = WORKLOADS[args.workload][5]
+        seed = WORKLOADS[workload][5]
         shapes = [(args.side, args.side)] * args.images
         return [synth.contone_image(h, w, seed=seed, index=rank * 1000 + i) for i, (h, w) in enumerate(shapes)], shapes
-    if args.workload in ("printer", "resnet"):
+    if workload in ("printer", "printer_fp16", "resnet"):
         shapes = [(args.size, args.size)] * args.batch
         seed = 1
-    elif args.workload in ("multitone", "proto"):
+    elif workload in ("multitone", "proto"):
         shapes = [(4096, 4096)] * 4
         seed = 2
-    elif args.workload == "resnet512":
+    elif workload == "resnet512":
         shapes = [(512, 512)]
         seed = 5
-    elif args.workload == "uneven":
+    elif workload == "uneven":
         shapes = synth.uneven_shapes(64, seed=4)
         seed = 4
     else:
@@ -236,47 +249,90 @@ def build_inputs(args, rank):
     return [synth.contone_image(h, w, seed=seed, index=rank * 1000 + i) for i, (h, w) in enumerate(shapes)], shapes
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="printer", choices=sorted(list(WORKLOADS) + ["train"]))
-    ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--size", type=int, default=2048)
-    ap.add_argument("--images", type=int, default=0, help="override: number of images (with --side)")
-    ap.add_argument("--side", type=int, default=0, help="override: square image side (with --images)")
-    ap.add_argument("--fp32-steps", type=int, default=2)
-    ap.add_argument("--torch-fp32-steps", type=int, default=1,
-                    help="timed passes of the plain PyTorch FP32 form (cuDNN, TF32 off); 0 skips it")
-    ap.add_argument("--ref-side", type=int, default=64)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--schedule", default="",
-                    help="ROWS,ORDER[,PAIR]: set the conv schedule instead of autotuning (PAIR 1 = CTA-pair 64->64 layers)")
-    ap.add_argument("--ckpt", type=int, default=0, help="train: activation checkpoint stride (recomputation)")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+def conv_roofline(prof, prec_name, chs, px_per_step, prof_steps, clocks, resnet, args):
+    """Roofline record of the dominant kernel: the C -> C conv layers.  Every launch is
+    timed alone (CUDA events around it), so a tensor-bound kernel is compared with the
+    burst peak; the sustained figure is given beside it for context."""
+    pk, src = peaks()
+    kname = {"bf16": "k_conv_tc_bf16", "fp8": "k_conv_tc_fp8", "fp16": "k_conv_tc_fp16",
+             "fp32": "k_conv3x3_fp32"}[prec_name]
+    if kname not in prof:
+        return None
+    launches, tot = prof[kname]
+    per_launch_ms = tot / launches
+    cmid = chs[1]
+    n_mid = len(chs) - 3 if prec_name != "fp32" else len(chs) - 2
+    layer_px = px_per_step * prof_steps * n_mid / launches          # pixels one launch processes
+    flops_launch = 2 * 9 * cmid * cmid * layer_px
+    achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
+    sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    hbm_peak = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    base = {"kernel": kname, "per_launch_ms": per_launch_ms, "px_per_launch": layer_px,
+            "sm_mhz": sm_mhz, "cycles_per_launch": per_launch_ms * 1e-3 * sm_mhz * 1e6}
+    if resnet:
+        # 32-wide layers: 18 432 flop/px against 128 B/px (conv1: read + write bf16) or
+        # 192 B/px (conv2: + the shortcut read), mean 160 B/px -> 115 flop/B, below the
+        # bf16 ridge (~250 flop/B): HBM-bound
+        gbs = 160.0 * layer_px / (per_launch_ms * 1e-3) / 1e9
+        return dict(base, bound="hbm", achieved=gbs, peak=hbm_peak, unit="GB/s", frac=gbs / hbm_peak, traffic=None,
+                    tensor_tflops=achieved, peak_source=f"{src} HBM copy bandwidth")
+    if prec_name == "fp32":
+        peak = fp32_alu_peak(clocks)
+        return dict(base, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                    traffic=None, peak_source="SM count x 128 FP32 FMA/clk x 2 x median SM clock under load")
+    burst = pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+    sust = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+    ratio, dt = (2.0, "e4m3") if prec_name == "fp8" else (1.0, prec_name)
+    peak = burst * ratio
+    psrc = (f"{src} bf16 dense, burst (each launch timed alone)"
+            + (" x 2 (nominal e4m3/bf16 ratio 4.5/2.25)" if ratio != 1.0 else "")
+            + (" = the fp16 dense rate (nominal 2.25 PF for both)" if prec_name == "fp16" else ""))
+    act_bytes = 128.0 if prec_name == "fp8" else 256.0              # read + write 64 channels per pixel
+    gbs = act_bytes * layer_px / (per_launch_ms * 1e-3) / 1e9
+    return dict(base, bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                frac_sustained=achieved / (sust * ratio), dtype=dt,
+                traffic=conv_traffic(kname, layer_px), peak_source=psrc,
+                peak_sm_mhz=(pk.get("clocks_under_load") or {}).get("sm_mhz_median"),
+                hbm={"bytes_per_px": act_bytes, "achieved_gbs": gbs, "peak": hbm_peak, "frac": gbs / hbm_peak,
+                     "note": "the same launches on the HBM side: one activation read and one write per pixel"})
 
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "train":
-        return run_train(args)
 
+def crop_parity(img, ws, bs, seed, prec_name, mode, probs_gpu, bits_gpu, head, side=48):
+    """Probability error against the pure FP64 oracle, and the bit-match rate against it at
+    margin 1e-4, on a side x side centre crop of image 0 (the stated bit-match rate)."""
+    import numpy as np
+    import oracle as O
+    from paper_2304_12152_gb300 import api
+    h, w = img.shape
+    y0, x0 = (h - side) // 2, (w - side) // 2
+    reg = (y0, x0, side, side)
+    _, p, _ = O.forward(img, ws, bs, noise_seed=seed, image=0, region=reg)
+    lev_or, u = O.sample(p, h, w, reg, mode, seed, 0)
+    pg = probs_gpu[:, y0:y0 + side, x0:x0 + side].astype(np.float64)
+    lev = api.unpack_bits(bits_gpu, h, w, head)[y0:y0 + side, x0:x0 + side]
+    if p.shape[0] == 1:
+        decided = np.abs(p[0] - u) > 1e-4
+    else:
+        cdf = np.cumsum(p, 0)
+        decided = np.all(np.abs(cdf - u[None]) > 1e-4, 0) if mode == 1 else np.ones(u.shape, bool)
+    mism = int(((lev != lev_or) & decided).sum())
+    d = np.abs(pg - p)
+    return {"vs": "pure FP64 oracle", "crop": f"{side}x{side} centre of image 0", "max_abs_dp": float(d.max()),
+            "p999_abs_dp": float(np.quantile(d, 0.999)), "bit_match": {"decided": int(decided.sum()),
+            "mismatch": mism, "rate": 1.0 - mism / max(1, int(decided.sum())), "margin": 1e-4}}
+
+
+def forward_record(workload, args, rank, world, local, full):
+    """Times one forward workload.  full: the headline line (e2e through host buffers, the
+    plain FP32 forms, the CPU oracle); else a sub-record (device-resident value, kernels,
+    roofline, clocks, error against the FP64 oracle on a crop)."""
     import numpy as np
     import torch
     import torch.distributed as dist
-
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-
     from paper_2304_12152_gb300 import _native as N
     from paper_2304_12152_gb300 import api, synth
 
-    desc, precision, head, netname, mode, seed = WORKLOADS[args.workload]
+    desc, precision, head, netname, mode, seed = WORKLOADS[workload]
     resnet = netname == "resnet"
     if resnet:
         chs = synth.resnet_channels(synth.RESNET_BLOCKS, synth.RESNET_WIDTH)
@@ -284,21 +340,25 @@ def main():
     else:
         chs = {"wide": synth.NET_WIDE, "wide4": synth.NET_WIDE_K4, "small": synth.NET_SMALL}[netname]
         ws, bs = synth.he_normal_policy(chs, 1)
-    prec = {"bf16": N.HT_BF16, "fp8": N.HT_FP8_E4M3, "fp32": N.HT_FP32}[precision]
+    prec = {"bf16": N.HT_BF16, "fp8": N.HT_FP8_E4M3, "fp32": N.HT_FP32, "fp16": N.HT_FP16}[precision]
     pol = api.Policy(chs, ws, bs, head=head, precision=prec, levels=4,
                      arch=N.HT_ARCH_RESNET if resnet else N.HT_ARCH_PLAIN)
     dev = torch.device("cuda", local)
     if prec == N.HT_FP8_E4M3:
         calib = torch.from_numpy(synth.contone_image(256, 256, seed=99)).to(dev)
         pol.calibrate(calib, seed=99)
-    imgs_np, shapes = build_inputs(args, rank)
+    imgs_np, shapes = build_inputs(args, rank, workload)
     cs = [torch.from_numpy(c).to(dev) for c in imgs_np]
     bits = [pol.alloc_bits(c.shape[0], c.shape[1], dev) for c in cs]
     px_per_step = sum(c.numel() for c in cs)
     stream = torch.cuda.current_stream()
+    with_reward = workload == "small"            # BASELINE config 1: the call and the HVS-MSE reward
+    rw_out = torch.empty((len(cs), 4), dtype=torch.float64, device=dev) if with_reward else None
 
     def direct_step():
         pol.halftone_into(cs, bits, mode, seed)
+        if with_reward:
+            api.reward(cs, bits, out=rw_out)
 
     # tensor-core forms: the conv schedule is picked by the library's autotuner on this
     # workload, then the call is captured once into a CUDA graph (ht_plan) and replayed
@@ -328,35 +388,90 @@ def main():
         if world > 1:
             dist.barrier()
 
-
     for _ in range(args.warmup):
         step()
     api.sync()
 
     # ---------------- device-resident timed region (graph replay for the tensor-core forms) ----------------
+    steps = args.steps if full else max(3, min(args.steps, args.sub_steps))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
     api.sync()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
-    ms_step = ms / args.steps
+    ms_step = ms / steps
     value = world * px_per_step / (ms_step * 1e-3) / 1e6
+    clocks = clk.summary()
 
     # ---------------- per-kernel times: the same call, direct launches bracketed by CUDA events ----------------
-    prof_steps = max(1, min(args.steps, 5))
+    prof_steps = max(1, min(steps, 5))
     torch.cuda.synchronize()
     api.profile_begin()
     for _ in range(prof_steps):
         direct_step()
     prof = api.profile_end()
     api.sync()
+    tot_ms = max(1e-9, sum(x[1] for x in prof.values()))
+    kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / tot_ms} for k, v in prof.items()}
+    roof = conv_roofline(prof, precision, chs, px_per_step, prof_steps, clocks, resnet, args)
+    flops_step = (pol.flops_per_px() if hasattr(pol, "flops_per_px") else synth.net_flops_per_px(chs)) * px_per_step
+    whole = None
+    if prec != N.HT_FP32 and not resnet:
+        pk, _ = peaks()
+        ratio = 2.0 if prec == N.HT_FP8_E4M3 else 1.0
+        tf = flops_step / (ms_step * 1e-3) / 1e12
+        whole = {"achieved_tflops": tf, "frac_of_burst": tf / (ratio * pk.get("bf16_tflops", 1900.0)),
+                 "frac_of_sustained": tf / (ratio * pk.get("bf16_tflops_sustained", 1700.0)),
+                 "note": "whole-net flops per step / graph-replay step time (a seconds-long region: the sustained "
+                         "figure applies)"}
+    # HBM-bound passes around the conv stack: algorithmic bytes per pixel, achieved GB/s
+    hbm_bytes = {"k_first_input": 4.0 + 32.0}            # contone read, three-part c / z split write
+    if head != N.HT_HEAD_SOFTMAX:
+        hbm_bytes["k_head_tc"] = 36.0 + 0.25             # 9 partials read, packed levels written
+    pk, _ = peaks()
+    hbm_peak = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    hbm = {}
+    for k, bpp in hbm_bytes.items():
+        if k in prof and prof[k][1] > 0:
+            gbs = bpp * px_per_step * prof_steps / (prof[k][1] * 1e-3) / 1e9
+            hbm[k] = {"bytes_per_px": bpp, "achieved_gbs": gbs, "frac": gbs / hbm_peak}
+    # launches inside the timed region: the replayed graph holds the same launches as one direct call
+    gpu_launches = sum(v[0] for v in prof.values()) * steps // prof_steps
+    timing = (("value: CUDA-graph replay of the call (ht_plan); kernels and roofline: "
+               f"{prof_steps} direct calls, each launch bracketed by CUDA events") if plan is not None
+              else "direct calls")
+    wdesc = desc.format(b=args.batch, h=args.size, w=args.size)
+    rec = {"value": value, "unit": "Mpx/s", "ms_per_step": ms_step, "steps": steps, "warmup": args.warmup,
+           "dtype": {"fp8": "e4m3"}.get(precision, precision),
+           "config": {"workload": wdesc, "images": len(shapes), "pixels_per_step": px_per_step,
+                      "l2": "inputs and activations larger than L2" if px_per_step * 4 > 129e6 else
+                            "inputs smaller than L2; one call's activations (128 B/px per layer) larger than L2"
+                            if px_per_step * 128 > 129e6 else "fits in L2"},
+           "roofline": roof, "whole_step": whole, "kernels": kernels, "gpu_launches": gpu_launches,
+           "clocks": clocks, "timing": timing, "autotune": tune, "hbm_kernels": hbm}
+    if workload == "uneven":
+        rec["config"]["shapes"] = shapes
+    if with_reward:
+        rec["config"]["step"] = "ht_halftone + ht_reward (MSE, SSIM, CSSIM, R of the halftone)"
+
+    if not full:
+        # error against the pure FP64 oracle on a crop of image 0 (probabilities from a direct call)
+        if rank == 0 and not resnet and not args.no_cpu_baseline:
+            b1, probs = pol.halftone([cs[0]], mode=mode, seed=seed, want_prob=True)
+            api.sync()
+            rec["parity"] = crop_parity(imgs_np[0], ws, bs, seed, precision, mode, probs[0].cpu().numpy(), b1[0],
+                                        head)
+        del plan, pol
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        return rec
 
     # ---------------- end-to-end through the C ABI with host buffers ----------------
     host_in = [torch.from_numpy(c).pin_memory() for c in imgs_np]
@@ -375,7 +490,6 @@ def main():
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
-
     ev_start = torch.cuda.Event()
 
     def e2e_run(nsteps):
@@ -418,6 +532,7 @@ def main():
     api.sync()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
     e2e_val = world * px_per_step / (e2e_ms * 1e-3) / 1e6
+    del plans_b, cs_b, bits_b
 
     # ---------------- plain FP32 form of the same net ----------------
     fp32 = None
@@ -438,64 +553,12 @@ def main():
         step()
         torch.cuda.synchronize()
 
-    # ---------------- roofline of the dominant kernel ----------------
-    pk, src = peaks()
-    roof = None
-    kname = {N.HT_BF16: "k_conv_tc_bf16", N.HT_FP8_E4M3: "k_conv_tc_fp8", N.HT_FP32: "k_conv3x3_fp32"}[prec]
-    if kname in prof:
-        launches, tot = prof[kname]
-        per_launch_ms = tot / launches
-        cmid = chs[1]
-        n_mid = len(chs) - 3 if prec != N.HT_FP32 else len(chs) - 2
-        # one launch = one C -> C layer over one image group: layers x pixels / launches
-        flops_launch = 2 * 9 * cmid * cmid * px_per_step * prof_steps * n_mid / launches
-        achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
-        if resnet:
-            # 32-wide layers: 18 432 flop/px against 128 B/px (conv1: read + write bf16) or
-            # 192 B/px (conv2: + the shortcut read), mean 160 B/px -> 115 flop/B, below the
-            # bf16 ridge (~250 flop/B): HBM-bound
-            bytes_launch = 160.0 * px_per_step * prof_steps * n_mid / launches
-            gbs = bytes_launch / (per_launch_ms * 1e-3) / 1e9
-            hbm = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
-            roof = {"bound": "hbm", "kernel": kname, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                    "traffic": None, "per_launch_ms": per_launch_ms, "tensor_tflops": achieved,
-                    "peak_source": f"{src} HBM copy bandwidth"}
-        elif prec == N.HT_FP32:
-            roof = {"bound": "alu", "kernel": kname, "achieved": achieved,
-                    "peak": fp32_alu_peak(clk.summary()), "unit": "TFLOP/s", "traffic": None,
-                    "per_launch_ms": per_launch_ms,
-                    "peak_source": "SM count x 128 FP32 FMA/clk x 2 x median SM clock under load"}
-            roof["frac"] = achieved / roof["peak"]
-        else:
-            peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
-            psrc = f"{src} bf16 dense, sustained"
-            if prec == N.HT_FP8_E4M3:
-                peak *= 2.0
-                psrc = f"{src} bf16 dense sustained x 2 (nominal fp8/bf16 ratio 4.5/2.25)"
-            roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": conv_traffic(args, kname, px_per_step, launches / prof_steps),
-                    "per_launch_ms": per_launch_ms, "peak_source": psrc}
-    tot_ms = max(1e-9, sum(x[1] for x in prof.values()))
-    kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / tot_ms} for k, v in prof.items()}
-    # HBM-bound passes around the conv stack: algorithmic bytes per pixel, achieved GB/s
-    hbm_bytes = {"k_first_input": 4.0 + 16.0}            # contone read, split c / z write
-    if head != N.HT_HEAD_SOFTMAX:
-        hbm_bytes["k_head_tc"] = 36.0 + 0.25             # 9 partials read, packed levels written
-    hbm_peak = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
-    hbm = {}
-    for k, bpp in hbm_bytes.items():
-        if k in prof and prof[k][1] > 0:
-            gbs = bpp * px_per_step * prof_steps / (prof[k][1] * 1e-3) / 1e9
-            hbm[k] = {"bytes_per_px": bpp, "achieved_gbs": gbs, "frac": gbs / hbm_peak}
-    # launches inside the timed region: the replayed graph holds the same launches as one direct call
-    gpu_launches = sum(v[0] for v in prof.values()) * args.steps // prof_steps
-
     # ---------------- CPU oracle baseline on a bounded sample ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
         O.build()
-        quant = {N.HT_BF16: 1, N.HT_FP8_E4M3: 2, N.HT_FP32: 0}[prec]
+        quant = {N.HT_BF16: 1, N.HT_FP8_E4M3: 2, N.HT_FP32: 0, N.HT_FP16: 3}[prec]
         side = 32
         lv = 4 if head == N.HT_HEAD_MULTITONE else 0
         dt, *_ = cpu_oracle_sample(imgs_np[0], ws, bs, side, seed, quant=quant, mode=mode, scales=None, levels=lv,
@@ -531,29 +594,83 @@ def main():
     if rank == 0 and world == 1 and args.torch_fp32_steps > 0 and not resnet:
         torch32 = torch_fp32_form(args.torch_fp32_steps, cs, ws, bs, head == N.HT_HEAD_SOFTMAX, px_per_step)
 
+    rec.update({"config": dict(rec["config"], parallelism=f"replicas x{world}"),
+                "e2e": {"value": e2e_val, "unit": "Mpx/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "ms_per_step": e2e_ms,
+                        "method": "pinned host buffers; per step all inputs H2D and all halftones D2H inside the "
+                                  "timed region, on two copy streams overlapping the neighbouring steps' compute "
+                                  "(two buffer sets, one CUDA-graph plan each)" if plan is not None else
+                                  "pinned host buffers; per step all inputs H2D and all halftones D2H, direct calls"},
+                "fp32_plain": fp32, "torch_fp32": torch32, "cpu_baseline": cpu})
+    if plan is not None:
+        rec["timing"] = rec["timing"].replace("value:", "value and e2e:")
+    del plan, pol
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return rec
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="printer", choices=sorted(list(WORKLOADS) + ["train"]))
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--images", type=int, default=0, help="override: number of images (with --side)")
+    ap.add_argument("--side", type=int, default=0, help="override: square image side (with --images)")
+    ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--torch-fp32-steps", type=int, default=1,
+                    help="timed passes of the plain PyTorch FP32 form (cuDNN, TF32 off); 0 skips it")
+    ap.add_argument("--ref-side", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="headline workload only (no sub-records)")
+    ap.add_argument("--sub-steps", type=int, default=10, help="timed steps of each sub-record")
+    ap.add_argument("--schedule", default="",
+                    help="ROWS,ORDER[,PAIR]: set the conv schedule instead of autotuning (PAIR 1 = CTA-pair 64->64 layers)")
+    ap.add_argument("--ckpt", type=int, default=0, help="train: activation checkpoint stride (recomputation)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "train":
+        return run_train(args)
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    rec = forward_record(args.workload, args, rank, world, local, full=True)
+    configs = None
+    if (rank == 0 and world == 1 and args.workload == "printer" and not args.no_configs and not args.schedule
+            and not (args.images and args.side)):
+        configs = {}
+        for name in SUB_CONFIGS:
+            try:
+                if name == "train":
+                    configs[name] = train_record(args, steps=max(3, min(args.steps, args.sub_steps)), warmup=3,
+                                                 fp32_steps=1 if args.fp32_steps > 0 else 0)
+                else:
+                    configs[name] = forward_record(name, args, rank, world, local, full=False)
+            except Exception as e:      # one failing sub-record must not hide the headline line
+                configs[name] = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
     if rank == 0:
-        wdesc = desc.format(b=args.batch, h=args.size, w=args.size)
-        line = {
-            "metric": "halftone Mpixels/s", "value": value, "unit": "Mpx/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": precision if precision != "fp8" else "e4m3",
-            "data": "synthetic",
-            "config": {"workload": wdesc, "images": len(shapes), "pixels_per_step": px_per_step,
-                       "parallelism": f"replicas x{world}", "l2": "inputs and activations larger than L2"},
-            "e2e": {"value": e2e_val, "unit": "Mpx/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": e2e_ms,
-                    "method": "pinned host buffers; per step all inputs H2D and all halftones D2H inside the "
-                              "timed region, on two copy streams overlapping the neighbouring steps' compute "
-                              "(two buffer sets, one CUDA-graph plan each)"},
-            "roofline": roof, "fp32_plain": fp32, "torch_fp32": torch32, "cpu_baseline": cpu, "kernels": kernels,
-            "gpu_launches": gpu_launches, "clocks": clk.summary(),
-            "timing": ("value and e2e: CUDA-graph replay of the call (ht_plan); kernels and roofline: "
-                       f"{prof_steps} direct calls, each launch bracketed by CUDA events") if plan is not None
-                      else "direct calls",
-            "autotune": tune, "hbm_kernels": hbm,
-        }
-        if args.workload == "uneven":
-            line["config"]["shapes"] = shapes
+        line = {"metric": "halftone Mpixels/s", "value": rec["value"], "unit": "Mpx/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"],
+                "data": "synthetic"}
+        line.update({k: v for k, v in rec.items() if k not in ("value", "unit", "ms_per_step", "steps", "warmup",
+                                                                 "dtype")})
+        if configs is not None:
+            line["configs"] = configs
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -642,51 +759,47 @@ def torch_fp32_form(steps, cs, ws, bs, softmax_head, px_per_step):
             torch.cuda.empty_cache()
 
 
-def conv_traffic(args, kname, px_per_step, launches_per_step):
-    """DRAM bytes per launch of the conv kernel, from the committed ncu summary when its
-    recorded source hash matches the current kernel source (else null)."""
+def conv_traffic(kname, px_per_launch):
+    """DRAM bytes per launch of the conv kernel, from the committed ncu summary of one
+    launch at the benchmark's size, while its recorded source hash matches the current
+    kernel source (else null)."""
     import re
     src = os.path.join(ROOT, "paper_2304_12152_gb300", "csrc", "conv_tc.cu")
-    summ = os.path.join(ROOT, "profiles", "k_conv_tc_bf16_2048.md")
+    summ = os.path.join(ROOT, "profiles", f"{kname}_2048x2048_traffic.md")
     try:
         h = code_hash(src)
         txt = open(summ).read()
     except OSError:
         return None
     m = re.search(r"code_sha256:\s*([0-9a-f]{64})", txt)
-    b = re.search(r"dram_bytes_per_px_per_layer:\s*([0-9.]+)", txt)
-    if not m or not b or m.group(1) != h or kname != "k_conv_tc_bf16":
+    b = re.search(r"dram_bytes_per_px:\s*([0-9.]+)", txt)
+    if not m or not b or m.group(1) != h:
         return None
-    # one launch = one 64 -> 64 layer over one image (six layers per image)
-    return float(b.group(1)) * px_per_step * 6.0 / launches_per_step
+    return float(b.group(1)) * px_per_launch
 
 
-def run_train(args):
+def train_record(args, steps, warmup, fp32_steps, rank=0, world=1, local=0):
     """Training step (Algorithm 1 TRAIN) timing: 16 crops 256x256 + 4 gray patches, S = 4,
     BF16 tensor-core form (FP32 master weights), with the FP32 CUDA-core form beside it."""
     import torch
+    import torch.distributed as dist
     from paper_2304_12152_gb300 import _native as N
     from paper_2304_12152_gb300 import api, synth
-    import torch.distributed as dist
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("nccl")
     chs = synth.NET_WIDE
     ws, bs = synth.he_normal_policy(chs, 3)
     # data parallel: each rank its own 16 crops; gradients averaged with one all-reduce per step
-    crops = [torch.from_numpy(synth.contone_image(256, 256, seed=3, index=rank * 1000 + i)).cuda() for i in range(16)]
+    crops = [torch.from_numpy(synth.contone_image(256, 256, seed=3, index=rank * 1000 + i)).to(dev) for i in range(16)]
     levels = [0.1, 0.25, 0.5, 0.75]
-    gw = torch.empty(sum(chs[i] * chs[i + 1] * 9 for i in range(len(chs) - 1)), device="cuda")
-    gb = torch.empty(sum(chs[1:]), device="cuda")
+    gw = torch.empty(sum(chs[i] * chs[i + 1] * 9 for i in range(len(chs) - 1)), device=dev)
+    gb = torch.empty(sum(chs[1:]), device=dev)
     stream = torch.cuda.current_stream()
 
-    def timed(prec, steps, warmup, profile):
+    def timed(prec, nsteps, nwarm, profile):
         pol = api.Policy(chs, ws, bs, precision=prec)
         tr = api.Trainer(pol, (256, 256), max_crops=16, n_samples=4, n_gray=4, gray_n=256, las_mode=1, n_rad=32,
                          n_ang=16, w_a=0.002, ckpt_stride=args.ckpt if prec == N.HT_BF16 else 0)
-        for _ in range(warmup):
+        for _ in range(nwarm):
             tr.forward(crops, levels, 1)
             tr.backward(gw, gb)
             api.allreduce_grads([gw, gb])
@@ -698,46 +811,75 @@ def run_train(args):
             api.profile_begin()
         with Clocks(local) as clk:
             e0.record(stream)
-            for k in range(steps):
+            for k in range(nsteps):
                 losses = tr.forward(crops, levels, 1 + k)
                 tr.backward(gw, gb)
                 api.allreduce_grads([gw, gb])
             e1.record(stream)
             torch.cuda.synchronize()
         prof = api.profile_end() if profile else {}
-        return max_over_ranks(e0.elapsed_time(e1), world, dev) / steps, losses, prof, clk.summary()
+        out = max_over_ranks(e0.elapsed_time(e1), world, dev) / nsteps, losses, prof, clk.summary()
+        tr.close()
+        pol.close()
+        return out
 
-    ms, losses, prof, clocks = timed(N.HT_BF16, args.steps, args.warmup, True)
+    ms, losses, prof, clocks = timed(N.HT_BF16, steps, warmup, True)
     fp32 = None
-    if args.fp32_steps > 0 and world == 1:
-        ms32, _, _, _ = timed(N.HT_FP32, args.fp32_steps, 1, False)
-        fp32 = {"value": ms32, "unit": "ms", "steps": args.fp32_steps}
-    if rank != 0:
-        dist.barrier()
-        dist.destroy_process_group()
-        return
+    if fp32_steps > 0 and world == 1:
+        ms32, _, _, _ = timed(N.HT_FP32, fp32_steps, 1, False)
+        fp32 = {"value": ms32, "unit": "ms", "steps": fp32_steps}
     # reward window sums and toggle deltas: algorithmic bytes per crop-sample pixel
     # (contone 4 B + 1/8 B bits; toggles: + 7 moment maps written and read, dR written)
-    px_samples = 16 * 4 * 256 * 256 * args.steps
-    hbm_peak = peaks()[0].get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    px_samples = 16 * 4 * 256 * 256 * steps
+    pk, src = peaks()
+    hbm_peak = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
     filt = {}
     for k, bpp in (("k_reward", 4.125), ("k_toggle_delta", 4.125 + 28.0 + 28.0 + 4.125 + 4.0)):
         if k in prof and prof[k][1] > 0:
             gbs = bpp * px_samples / (prof[k][1] * 1e-3) / 1e9
             filt[k] = {"bytes_per_px": bpp, "achieved_gbs": gbs, "frac": gbs / hbm_peak,
                        "note": "ALU-bound stencils (5-6 window sums; toggles ~3.6 kflop/px)"}
-    print(json.dumps({
-        "metric": "training step time", "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+    # tensor work of the step: forward + data gradient + weight gradient of the 64 -> 64 layers
+    # (3 x 73 728 flop/px each, crops and gray patches), over the step time
+    px_step = (16 + 4) * 256 * 256
+    tflops = 3 * 6 * 73728.0 * px_step / (ms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "kernel": "whole step (64 -> 64 layers: forward, data and weight gradients)",
+            "achieved": tflops, "peak": pk.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
+            "frac": tflops / pk.get("bf16_tflops_sustained", 1700.0), "traffic": None,
+            "peak_source": f"{src} bf16 dense, sustained (a multi-millisecond step of many kernels)",
+            "sm_mhz": clocks.get("sm_mhz")}
+    for k, fl in (("k_wgrad_tc", 73728.0), ("k_conv_tc_bf16", 73728.0)):
+        if k in prof and prof[k][0] > 0:
+            per = prof[k][1] / prof[k][0]
+            # per launch: one 64 -> 64 layer over the step's 20 images (forward or data gradient)
+            roof.setdefault("kernels", {})[k] = {
+                "per_launch_ms": per, "achieved": fl * px_step / (per * 1e-3) / 1e12,
+                "frac_of_burst": fl * px_step / (per * 1e-3) / 1e12 / pk.get("bf16_tflops", 1900.0)}
+    return {
+        "metric": "training step time", "value": ms, "unit": "ms", "ms_per_step": ms, "steps": steps,
+        "warmup": warmup, "higher_is_better": False, "dtype": "bf16",
         "config": {"workload": "train: 16 crops 256x256 + 4 gray 256x256 {0.1,0.25,0.5,0.75}, S=4, "
-                               "2->64x7->1, w_s 0.06, w_a 0.002, 32x16-bin anisotropy loss, FP32 master weights"},
+                               "2->64x7->1, w_s 0.06, w_a 0.002, 32x16-bin anisotropy loss, FP32 master weights",
+                   "l2": "the step's activations (~3.5 GB) larger than L2"},
         "losses": {"total": losses[0], "marl": losses[1], "las": losses[2], "mean_R": losses[3]},
-        "fp32_plain": fp32,
+        "fp32_plain": fp32, "roofline": roof,
         "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
         "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clocks,
         "parallelism": f"data parallel x{world}, one gradient all-reduce per step", "hbm_kernels": filt,
-        "ckpt_stride": args.ckpt}), flush=True)
+        "ckpt_stride": args.ckpt}
+
+
+def run_train(args):
+    """--workload train: the training step as its own JSON line."""
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    rec = train_record(args, args.steps, args.warmup, args.fp32_steps, rank, world, local)
+    if rank == 0:
+        print(json.dumps(dict(rec, n_gpus=world, scaling="weak", vs_baseline=None, data="synthetic")), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -460,8 +460,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     if constexpr ((KIND == KIND_HIDDEN || KIND == KIND_FIRST) && !TR && CH == 64) {
                         if (!P.out_fp8) {
                             store_pixel_bias_relu_bf16<F16>(v, P.scale, P.bias, ui.out, ui.H, ui.W, y0 + j, x);
-                            continue;
+                        } else {
+                            store_pixel_bias_relu_e4m3(v, P.scale, P.bias, P.out_inv_scale, ui.out, ui.H, ui.W, y0 + j,
+                                                       x);
                         }
+                        continue;
                     }
 #pragma unroll
                     for (int n = 0; n < C::CO; ++n) v[n] = fmaf(v[n], P.scale[n], P.bias[n]);

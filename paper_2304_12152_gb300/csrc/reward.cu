@@ -390,6 +390,83 @@ __global__ void __launch_bounds__(DTX *DTY, 3) k_toggle_delta(const __grid_const
     dR[(size_t)ay * W + ax] = acc / ((float)VH * (float)VW);
 }
 
+// Binary toggle deltas for a fixed window radius R (the paper's 11 x 11 windows: R = 5),
+// the common case of the training step.  The same exact moment-shift update as
+// k_toggle_delta, arranged so that the 121-term window loop runs unrolled and without
+// bounds checks:
+//   - outside the valid region the staged maps read e = 0, sigma = 0, var_c + C2 = 1
+//     (every term there then vanishes and no division sees a zero denominator);
+//   - the MSE part splits into -2 sum_j g_{j-a} e_j (in the loop) and -delta S_a, with
+//     S_a = sum over valid j of g_{j-a}^2 = (sum of g_y^2 over valid rows) x (sum of
+//     g_x^2 over valid columns), the window being a product of 1-D taps;
+//   - the 2-D tap products g_y g_x and w_y w_x come precomputed in the kernel parameters;
+//   - delta w_sg sigma_j (SSIM' - SSIM_j) is summed as sigma_j (SSIM' - SSIM_j), the
+//     factor delta w_s applied once.
+template <int R>
+struct Win2 {
+    float g2[(2 * R + 1) * (2 * R + 1)];
+    float w2[(2 * R + 1) * (2 * R + 1)];
+};
+
+template <int R>
+__global__ void __launch_bounds__(DTX *DTY, 3) k_toggle_delta_r(const __grid_constant__ RwBatch B, const Win wn,
+                                                                 const __grid_constant__ Win2<R> w2)
+{
+    constexpr int SH = DTY + 2 * R, SW = DTX + 2 * R, K = 2 * R + 1;
+    __shared__ float s_m[NMAP][SH][SW];
+    const RwImg &I = B.im[blockIdx.z];
+    const float *__restrict__ c = I.c;
+    const float *__restrict__ maps = I.maps;
+    const int H = I.H, W = I.W;
+    const int VH = H - 2 * R, VW = W - 2 * R;
+    const size_t plane = (size_t)VH * VW;
+    const int ay0 = blockIdx.y * DTY, ax0 = blockIdx.x * DTX;
+    if (ay0 >= H || ax0 >= W) return;
+    const int tid = threadIdx.y * DTX + threadIdx.x;
+    for (int i = tid; i < NMAP * SH * SW; i += DTX * DTY) {
+        const int q = i / (SH * SW), rem = i % (SH * SW);
+        const int yy = rem / SW, xx = rem % SW;
+        const int jy = ay0 - R + yy, jx = ax0 - R + xx;        // image coords of output j
+        float v = q == 3 ? 1.f : 0.f;
+        if (jy >= R && jy < H - R && jx >= R && jx < W - R) v = __ldg(maps + q * plane + (size_t)(jy - R) * VW + (jx - R));
+        s_m[q][yy][xx] = v;
+    }
+    __syncthreads();
+    const int ay = ay0 + threadIdx.y, ax = ax0 + threadIdx.x;
+    if (ay >= H || ax >= W) return;
+    const float ca = c[(size_t)ay * I.cpitch + ax];
+    const float delta = 1.f - 2.f * hbit(I.bits, I.words, ay, ax);
+    float sy = 0.f, sx = 0.f;
+#pragma unroll
+    for (int d = -R; d <= R; ++d) {
+        const float gd = wn.g[d + R] * wn.g[d + R];
+        if (ay + d >= R && ay + d < H - R) sy += gd;
+        if (ax + d >= R && ax + d < W - R) sx += gd;
+    }
+    float ge = 0.f, acc = 0.f;
+#pragma unroll
+    for (int dy = 0; dy < K; ++dy) {
+#pragma unroll
+        for (int dx = 0; dx < K; ++dx) {
+            const int sy_ = threadIdx.y + dy, sx_ = threadIdx.x + dx;
+            const float e = s_m[0][sy_][sx_], muh = s_m[1][sy_][sx_], muc = s_m[2][sy_][sx_];
+            const float varc2 = s_m[3][sy_][sx_], cov = s_m[4][sy_][sx_], sig = s_m[5][sy_][sx_];
+            const float ss = s_m[6][sy_][sx_];
+            ge = fmaf(w2.g2[dy * K + dx], e, ge);
+            const float dw = delta * w2.w2[dy * K + dx];
+            const float muh2 = muh + dw;
+            const float varh2 = fmaf(-muh2, muh2, muh2);
+            const float cov2 = fmaf(dw, ca - muc, cov);
+            const float num = fmaf(2.f * muh2, muc, wn.c1) * fmaf(2.f, cov2, wn.c2);
+            const float den = fmaf(muh2, muh2, fmaf(muc, muc, wn.c1)) * (varh2 + varc2);
+            // the denominator lies in [C1 C2, ~5]: the fast division (2 ulp) is exact enough
+            acc = fmaf(sig, __fdividef(num, den) - ss, acc);
+        }
+    }
+    const float dr = -2.f * ge - delta * (sy * sx) + delta * wn.ws * acc;
+    I.dR[(size_t)ay * W + ax] = dr / ((float)VH * (float)VW);
+}
+
 Win make_win(const ht_reward_opts &o)
 {
     Win wn;
@@ -511,7 +588,17 @@ ht_status ht_toggle_launch(const ht_image *c, const uint32_t *const *bits, const
         } else {
             k_moment_maps<false><<<dim3(gx, gy, cnt), dim3(32, 8), 0, s>>>(B, wn);
             HT_LAUNCH_CHECK();
-            k_toggle_delta<false><<<dim3(tx, ty, cnt), dim3(DTX, DTY), 0, s>>>(B, wn);
+            if (o.radius == 5) {
+                Win2<5> w2;
+                for (int i = 0; i < 11; ++i)
+                    for (int j = 0; j < 11; ++j) {
+                        w2.g2[i * 11 + j] = wn.g[i] * wn.g[j];
+                        w2.w2[i * 11 + j] = wn.w[i] * wn.w[j];
+                    }
+                k_toggle_delta_r<5><<<dim3(tx, ty, cnt), dim3(DTX, DTY), 0, s>>>(B, wn, w2);
+            } else {
+                k_toggle_delta<false><<<dim3(tx, ty, cnt), dim3(DTX, DTY), 0, s>>>(B, wn);
+            }
         }
         ht_prof_stop(s);
         HT_LAUNCH_CHECK();
@@ -644,5 +731,6 @@ void ht_preload_reward()
     cudaFuncGetAttributes(&fa, k_moment_maps<true>);
     cudaFuncGetAttributes(&fa, k_toggle_delta<false>);
     cudaFuncGetAttributes(&fa, k_toggle_delta<true>);
+    cudaFuncGetAttributes(&fa, k_toggle_delta_r<5>);
     cudaFuncGetAttributes(&fa, k_reward_finalize_noalloc);
 }

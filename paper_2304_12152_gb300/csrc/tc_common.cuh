@@ -475,6 +475,46 @@ __device__ __forceinline__ void store_pixel_bias_relu_bf16(const float *v, const
     }
 }
 
+// Epilogue of an e4m3-output layer (FP8 form): v * scale + bias, ReLU, bf16 (the
+// activations' storage rounding), times the next layer's inverse input scale (a power
+// of two: exact), e4m3 with saturation (round to nearest even), 16 channels per chunk.
+// Packed over channel pairs (fma.rn.f32x2, cvt.rn.relu.bf16x2.f32, mul.rn.f32x2,
+// cvt.rn.satfinite.e4m3x2.f32): the same values as the per-channel sequence.
+__device__ __forceinline__ void store_pixel_bias_relu_e4m3(const float *v, const float *scale, const float *bias,
+                                                          float inv_scale, void *out, int H, int W, int y, int x)
+{
+    uint8_t *o = (uint8_t *)out;
+    unsigned long long ii;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(ii) : "f"(inv_scale));
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint16_t e[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int n = 16 * c + 4 * h + 2 * q;
+                unsigned long long vv, ss, bb, rr;
+                asm("mov.b64 %0, {%1, %2};" : "=l"(vv) : "f"(v[n]), "f"(v[n + 1]));
+                asm("mov.b64 %0, {%1, %2};" : "=l"(ss) : "f"(scale[n]), "f"(scale[n + 1]));
+                asm("mov.b64 %0, {%1, %2};" : "=l"(bb) : "f"(bias[n]), "f"(bias[n + 1]));
+                asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rr) : "l"(vv), "l"(ss), "l"(bb));
+                float lo, hi;
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(rr));
+                uint32_t b2;
+                asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(b2) : "f"(hi), "f"(lo));
+                asm("mov.b64 %0, {%1, %2};" : "=l"(vv) : "f"(__uint_as_float(b2 << 16)), "f"(__uint_as_float(b2 & 0xFFFF0000u)));
+                asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rr) : "l"(vv), "l"(ii));
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(rr));
+                asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(e[q]) : "f"(hi), "f"(lo));
+            }
+            w4[h] = (uint32_t)e[0] | ((uint32_t)e[1] << 16);
+        }
+        *reinterpret_cast<uint4 *>(o + (((size_t)c * H + y) * W + x) * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    }
+}
+
 // One image of a batched call.  Every kernel of the tensor-core form walks a
 // flattened index space (conv units, layer-1 tiles, head tiles) over all images
 // of the call and finds its image through the *_begin prefix sums.

@@ -11,7 +11,9 @@ rewards (a jump, not a slope: the estimator's gradient holds the samples fixed).
 eps = 1e-4 moves p by ~1e-5, so that a sample changes only where u lies within ~1e-5 of p;
 the difference quotients at eps and 2 eps must agree, which also catches the rare case
 where one did change (such a weight is skipped; most must remain).  L_AS alone (a gray
-patch, no sampling) is smooth and is checked at eps = 1e-3 for every weight picked."""
+patch, no sampling) is smooth and is checked at eps = 1e-3 for every weight picked.
+Agreement: 5e-3 of the larger of |dL/dw| and 5% of the largest gradient entry (the float32
+evaluation of the loss leaves the difference quotients ~1e-4 of that entry apart)."""
 import numpy as np
 import pytest
 import torch
@@ -56,10 +58,10 @@ def _fd_check(pol, tr, w0, b0, crops, levels, seed, k, eps, consistency):
         fd1 = (at(eps) - at(-eps)) / (2 * eps)
         fd2 = (at(2 * eps) - at(-2 * eps)) / (4 * eps)
         g = float((gb if is_b else gw)[i])
-        if abs(fd1 - fd2) > consistency * max(abs(fd1), 1e-3 * scale):
+        if abs(fd1 - fd2) > consistency * max(abs(fd1), 5e-2 * scale):
             continue                                  # a sample changed inside the stencil
         checked += 1
-        err = abs(fd1 - g) / max(abs(g), 1e-2 * scale)
+        err = abs(fd1 - g) / max(abs(g), 5e-2 * scale)
         worst = max(worst, err)
         assert err <= 5e-3, (is_b, i, fd1, fd2, g)
     pol.set_weights(w0, b0)
