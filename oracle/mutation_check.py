@@ -1,5 +1,5 @@
-"""Mutation check of the oracle's pins (test infrastructure, run by hand; not collected by
-pytest).
+"""Mutation check of the oracle's pins (test infrastructure beside the oracle it checks, run by
+hand; pytest does not collect it).
 
 Plants one plausible mistake at a time in a scratch copy of the repository -- a wrong
 constant, a dropped term, a flipped sign or index, a transposed operand, a misplaced ring
@@ -8,7 +8,7 @@ CPU suite (`-m "not gpu"`).  Every mutation must make some test fail ("killed");
 passes ("SURVIVED") marks a part of the oracle its pins do not fix, unless the mutation
 cannot change any result (an equivalent mutation; the two known ones are listed below).
 
-    python tests/mutation_check.py --scratch /path/to/empty/dir [name-filter ...]
+    python oracle/mutation_check.py --scratch /path/to/empty/dir [name-filter ...]
 
 Each mutation reruns the CPU suite (about 5-10 s); the whole check takes 10-15 minutes.  Run
 it with nothing else busy on the cores: the oracle's OpenMP thread pools spin while they wait,
