@@ -11,9 +11,10 @@ rewards (a jump, not a slope: the estimator's gradient holds the samples fixed).
 eps = 1e-4 moves p by ~1e-5, so that a sample changes only where u lies within ~1e-5 of p;
 the difference quotients at eps and 2 eps must agree, which also catches the rare case
 where one did change (such a weight is skipped; most must remain).  L_AS alone (a gray
-patch, no sampling) is smooth and is checked at eps = 1e-3 for every weight picked.
-Agreement: 5e-3 of the larger of |dL/dw| and 5% of the largest gradient entry (the float32
-evaluation of the loss leaves the difference quotients ~1e-4 of that entry apart)."""
+patch, no sampling) is smooth and is checked at eps = 1e-2 for every weight picked (its
+float32 spectrum leaves ~1e-6 of noise in the loss, too much for a smaller step).
+Agreement: 5e-3 of the larger of |dL/dw| and 5% of the largest gradient entry, beyond the
+quotients' own spread |fd(eps) - fd(2 eps)|, which estimates their error."""
 import numpy as np
 import pytest
 import torch
@@ -61,7 +62,8 @@ def _fd_check(pol, tr, w0, b0, crops, levels, seed, k, eps, consistency):
         if abs(fd1 - fd2) > consistency * max(abs(fd1), 5e-2 * scale):
             continue                                  # a sample changed inside the stencil
         checked += 1
-        err = abs(fd1 - g) / max(abs(g), 5e-2 * scale)
+        # the difference quotients' own spread |fd1 - fd2| estimates their error
+        err = max(0.0, abs(fd1 - g) - abs(fd1 - fd2)) / max(abs(g), 5e-2 * scale)
         worst = max(worst, err)
         assert err <= 5e-3, (is_b, i, fd1, fd2, g)
     pol.set_weights(w0, b0)
@@ -90,6 +92,6 @@ def test_anisotropy_gradient_matches_central_differences():
                      w_a=1.0)
     w0, b0 = _flat(ws, bs)
     tr.forward([], [0.3], 12)
-    checked, worst = _fd_check(pol, tr, w0, b0, [], [0.3], 12, 2, 1e-3, 2e-2)
+    checked, worst = _fd_check(pol, tr, w0, b0, [], [0.3], 12, 2, 1e-2, 2e-2)
     print(f"L_AS: {checked} of 12 weights checked, worst relative error {worst:.2e}")
     assert checked == 12
