@@ -807,8 +807,6 @@ def train_record(args, steps, warmup, fp32_steps, rank=0, world=1, local=0):
         if world > 1:
             dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if profile:
-            api.profile_begin()
         with Clocks(local) as clk:
             e0.record(stream)
             for k in range(nsteps):
@@ -817,8 +815,17 @@ def train_record(args, steps, warmup, fp32_steps, rank=0, world=1, local=0):
                 api.allreduce_grads([gw, gb])
             e1.record(stream)
             torch.cuda.synchronize()
-        prof = api.profile_end() if profile else {}
-        out = max_over_ranks(e0.elapsed_time(e1), world, dev) / nsteps, losses, prof, clk.summary()
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / nsteps
+        prof = {}
+        if profile:
+            # per-kernel times from separate steps (each launch bracketed by CUDA events,
+            # which would otherwise add to the timed steps)
+            api.profile_begin()
+            for k in range(nsteps):
+                tr.forward(crops, levels, 1 + k)
+                tr.backward(gw, gb)
+            prof = api.profile_end()
+        out = ms, losses, prof, clk.summary()
         tr.close()
         pol.close()
         return out
