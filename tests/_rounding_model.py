@@ -28,6 +28,8 @@ the GB300 kernels show.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 import torch
 import torch.nn.functional as F
@@ -38,6 +40,11 @@ import oracle as O
 def _round(t: torch.Tensor, fmt: str) -> torch.Tensor:
     dt = {"bf16": torch.bfloat16, "fp16": torch.float16}[fmt]
     return t.to(dt).to(torch.float32)
+
+
+def _e4m3(t: torch.Tensor) -> torch.Tensor:
+    """E4M3 rounding (nearest even) with saturation at +-448, as float32."""
+    return t.clamp(-448.0, 448.0).to(torch.float8_e4m3fn).to(torch.float32)
 
 
 def _conv_f32(x: torch.Tensor, w: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
@@ -76,8 +83,13 @@ def _conv_trunc(x: torch.Tensor, w: torch.Tensor, b: torch.Tensor, kept: int) ->
 
 
 def forward_p(contone: np.ndarray, ws, bs, noise_seed: int, image: int = 0, fmt: str = "bf16",
-              first: str = "fp32", acc: str = "rn", kept: int = 22) -> np.ndarray:
-    """Sigmoid output [h][w] (float64) of the float32 model."""
+              first: str = "fp32", acc: str = "rn", kept: int = 22, act_scale=None) -> np.ndarray:
+    """Sigmoid output [h][w] (float64) of the float32 model.  fmt "e4m3" (the FP8 form):
+    inner layers' weights as e4m3 codes of w / s_o with s_o = amax_o / 448 per output
+    channel, their inputs (bf16 activations) as e4m3 codes of a / act_scale[l]; the sum of
+    code products in float32, then times act_scale[l] s_o."""
+    if fmt == "e4m3":
+        return _forward_p_e4m3(contone, ws, bs, noise_seed, image, act_scale)
     h, w = contone.shape
     z = O.uniform_map(noise_seed, image, 0, h, w).astype(np.float32)     # exact: 24-bit values
     x = torch.from_numpy(np.stack([contone.astype(np.float32), z]))[None]
@@ -100,5 +112,42 @@ def forward_p(contone: np.ndarray, ws, bs, noise_seed: int, image: int = 0, fmt:
             y = _conv_f32(x, wt, bt)
         if l < L - 1:
             y = _round(torch.relu(y), fmt)
+        x = y
+    return 1.0 / (1.0 + np.exp(-x[0, 0].double().numpy()))
+
+
+def fp8_scales(ws, bs, chs):
+    """Per-layer power-of-two input scales of the FP8 form from an oracle pass on the
+    calibration image (seed 99), the rule the library's calibration follows:
+    2^ceil(log2(amax / 448)) of each hidden layer's output."""
+    from paper_2304_12152_gb300 import synth
+    c = synth.contone_image(64, 64, seed=99)
+    _, _, acts = O.forward(c, ws, bs, noise_seed=99, save_acts=True)
+    sc = [1.0] * (len(chs) - 1)
+    for l in range(1, len(chs) - 2):
+        sc[l] = 2.0 ** math.ceil(math.log2(max(float(np.abs(acts[l - 1]).max()), 1e-6) / 448.0))
+    return sc
+
+
+def _forward_p_e4m3(contone, ws, bs, noise_seed, image, act_scale):
+    h, w = contone.shape
+    z = O.uniform_map(noise_seed, image, 0, h, w).astype(np.float32)
+    x = torch.from_numpy(np.stack([contone.astype(np.float32), z]))[None]
+    L = len(ws)
+    for l in range(L):
+        wt = torch.from_numpy(np.asarray(ws[l], np.float32))
+        bt = torch.from_numpy(np.asarray(bs[l], np.float32))
+        if 0 < l < L - 1:
+            w64 = np.asarray(ws[l], np.float64)
+            amax = np.abs(w64.reshape(w64.shape[0], -1)).max(1)
+            so = np.where(amax > 0, amax / 448.0, 1.0)
+            wcode = _e4m3(torch.from_numpy(w64 / so[:, None, None, None]).float())
+            acode = _e4m3(x / float(act_scale[l]))
+            y = _conv_f32(acode, wcode, torch.zeros_like(bt))
+            y = y * torch.from_numpy((float(act_scale[l]) * so).astype(np.float32))[None, :, None, None] + bt[None, :, None, None]
+        else:
+            y = _conv_f32(x, wt, bt)
+        if l < L - 1:
+            y = _round(torch.relu(y), "bf16")
         x = y
     return 1.0 / (1.0 + np.exp(-x[0, 0].double().numpy()))

@@ -24,7 +24,7 @@ import oracle as O
 from paper_2304_12152_gb300 import _native as N
 from paper_2304_12152_gb300 import api, synth
 
-from _cases import compare_levels, decided_mask, tight_rule
+from _cases import compare_levels, decided_mask, tight_rule, unexplained
 
 pytestmark = pytest.mark.gpu
 
@@ -122,7 +122,9 @@ def test_bf16_wide_net_tiles_and_tails(mode):
         p_x = ref_x[i][0]
         diffs.append((probs[i] - p_q).ravel())
         assert np.abs(probs[i] - p_x).max() < BF16_X_MAX and _p999(probs[i] - p_x) < BF16_X_P999
-        n, bad = compare_levels(lev[i], lev_q, decided_mask(p_q, u, mode))
+        dec = decided_mask(p_q, u, mode)
+        n, bad = compare_levels(lev[i], lev_q, dec)
+        assert unexplained(lev[i], lev_q, probs[i][0], p_q[0], u, dec) == 0
         tot_n += n
         tot_bad += bad
     fails = tight_rule(np.concatenate(diffs), "bf16", 7)

@@ -17,7 +17,7 @@ import oracle as O
 from paper_2304_12152_gb300 import _native as N
 from paper_2304_12152_gb300 import api, synth
 
-from _cases import compare_levels, decided_mask, tight_rule
+from _cases import compare_levels, decided_mask, tight_rule, unexplained
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,9 @@ def test_fp16_wide_net_tiles_and_tails(mode):
         ref, u = O.sample(p_q, h, w, (0, 0, h, w), mode, 1, i)
         dq.append((probs[i] - p_q).ravel())
         dx.append(np.abs(probs[i] - p_x).ravel())
-        n, bad = compare_levels(lev[i], ref, decided_mask(p_q, u, mode))
+        dec = decided_mask(p_q, u, mode)
+        n, bad = compare_levels(lev[i], ref, dec)
+        assert unexplained(lev[i], ref, probs[i][0], p_q[0], u, dec) == 0
         tot_n += n
         tot_bad += bad
     fails = tight_rule(np.concatenate(dq), "fp16", 7)

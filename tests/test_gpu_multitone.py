@@ -11,6 +11,8 @@ import oracle as O
 from paper_2304_12152_gb300 import _native as N
 from paper_2304_12152_gb300 import api, synth
 
+from _cases import tight_rule
+
 pytestmark = pytest.mark.gpu
 
 
@@ -43,10 +45,12 @@ def test_fp32_multitone_head_matches_oracle(L, mode):
 
 def test_bf16_multitone_head_matches_bf16_oracle():
     """Tensor-core form, 8-layer 64-wide net, 4 levels, Bernoulli: vs the BF16-emulating
-    oracle.  Residual mismatches come from activations at bf16 rounding boundaries, which
-    move v by ~5e-4 typically; the level rule compares v (L - 1) - k with u, so a pixel is
-    undecided within (L - 1) |dv| of the boundary, L - 1 times the binary head's band:
-    allowance (L - 1) x the binary head's 1e-3 of decided pixels (measured 2e-3)."""
+    oracle.  v is held to the 7-layer bf16 row of the tight rule (tests/_cases.TIGHT), as
+    the binary head's p.  Residual mismatches come from activations at bf16 rounding
+    boundaries; the level rule compares v (L - 1) - k with u, so a decision can move only
+    where the oracle's margin (|frac - u|, or the distance of v (L - 1) from a level) is
+    within (L - 1) |dv| of the measured dv at that pixel: every mismatch must be explained
+    so, and there are at most (L - 1) x 1e-3 of the decided pixels."""
     chs = synth.NET_WIDE
     ws, bs = synth.he_normal_policy(chs, 33)
     L = 4
@@ -63,13 +67,14 @@ def test_bf16_multitone_head_matches_bf16_oracle():
     dec = _decided(v, L, u)
     mism = int((lev[dec] != ref[dec]).sum())
     assert mism <= max(2, int((L - 1) * 1e-3 * dec.sum())), (mism, int(dec.sum()))
-    dv = np.abs(probs[0][0].cpu().numpy() - v)
-    # bound from the oracle alone: within 1.5x of how far BF16 rounding moves v (quant 1 vs
-    # FP64); early rounding flips make the two BF16 sides independent realisations
-    _, p64, _ = O.forward(img, ws, bs, noise_seed=6, quant=0)
-    eff = np.abs(v - p64[0])
-    assert np.quantile(dv, 0.999) <= 1.5 * np.quantile(eff, 0.999) and dv.max() <= 1.5 * eff.max(), \
-        (np.quantile(dv, 0.999), dv.max(), np.quantile(eff, 0.999), eff.max())
+    dv = probs[0][0].cpu().numpy() - v
+    t = v * (L - 1)
+    _, frac = O.multitone_pair(v, L)
+    band = (L - 1) * np.abs(dv) + 1e-6
+    explained = (np.abs(frac - u) <= band) | (np.abs(t - np.rint(t)) <= band)
+    assert not np.any(dec & (lev != ref) & ~explained)
+    fails = tight_rule(dv, "bf16", 7)
+    assert fails == [], fails
     # levels are the two around v
     v32 = probs[0][0].cpu().numpy()
     k = np.minimum(np.floor(v32 * np.float32(L - 1)), L - 2).astype(np.int64)   # the kernel's FP32 rule

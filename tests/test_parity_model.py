@@ -52,3 +52,18 @@ def test_truncating_model_meets_the_shallow_row(fmt):
     _, p_or, _ = O.forward(img, ws, bs, noise_seed=9, quant=1 if fmt == "bf16" else 3)
     pt = M.forward_p(img, ws, bs, 9, fmt=fmt, acc="trunc", kept=22)
     assert tight_rule(pt - p_or[0], fmt, 2) == []
+
+
+@pytest.mark.parametrize("chs", [(2, 64, 64, 1), (2, 64, 64, 64, 1), synth.NET_WIDE])
+def test_e4m3_model_meets_the_rule(chs):
+    """The FP8 form's float32 model (e4m3 codes of weights and inputs, float32 sums of code
+    products times the scales) against quant 2 of the oracle."""
+    seed = 25
+    ws, bs = synth.he_normal_policy(chs, seed)
+    bs = synth.random_biases(chs, seed + 1)
+    sc = M.fp8_scales(ws, bs, chs)
+    h, w = (112, 144) if len(chs) > 5 else (144, 176)
+    img = synth.contone_image(h, w, seed=seed)
+    _, p_or, _ = O.forward(img, ws, bs, noise_seed=seed, quant=2, act_scale=sc)
+    p8 = M.forward_p(img, ws, bs, seed, fmt="e4m3", act_scale=sc)
+    assert tight_rule(p8 - p_or[0], "e4m3", len(chs) - 2) == []

@@ -41,3 +41,20 @@ def test_decided_fraction_on_realistic_inputs():
     assert 0.999 < frac < 1.0                      # |p - u| <= 1e-4 has probability ~2e-4
     q = rng.dirichlet(np.ones(4), size=(256, 256)).transpose(2, 0, 1)
     assert 0.998 < decided_mask(q, u, 1).mean() < 1.0
+
+
+def test_unexplained_mismatches():
+    """A mismatch counts as explained only where u lies within |p_gpu - p_or| of p_or."""
+    from _cases import unexplained
+    p_or = np.array([[0.30, 0.50, 0.70, 0.90]])
+    p_gpu = np.array([[0.31, 0.50, 0.70, 0.90]])
+    u = np.array([[0.305, 0.2, 0.6, 0.95]])
+    lev_or = (u < p_or).astype(np.uint8)
+    lev_gpu = lev_or.copy()
+    lev_gpu[0, 0] ^= 1                      # u between the two p: explained
+    dec = np.ones_like(u, bool)
+    assert unexplained(lev_gpu, lev_or, p_gpu, p_or, u, dec) == 0
+    lev_gpu[0, 2] ^= 1                      # p equal on both sides: a fault
+    assert unexplained(lev_gpu, lev_or, p_gpu, p_or, u, dec) == 1
+    dec[0, 2] = False
+    assert unexplained(lev_gpu, lev_or, p_gpu, p_or, u, dec) == 0
