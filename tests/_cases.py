@@ -49,6 +49,13 @@ TIGHT = {
     ("e4m3", 2): (1e-6, 0.03, 1e-3, 4e-3),
     ("e4m3", 3): (1e-6, 0.05, 4e-3, 1e-2),
     ("e4m3", 7): (1e-6, 0.10, 3e-2, 6e-2),
+    # the residual policy (32-wide, BF16), keyed by residual blocks: each block rounds its
+    # inner activation and its output (after the shortcut add), so one block adds two rounded
+    # layers; over 16 blocks and an undamped residual stream the flips reach every pixel
+    # and the two sides become independent BF16 realisations (median ~1e-3)
+    ("bf16-res", 1): (1e-6, 0.15, 8e-4, 2e-3),
+    ("bf16-res", 2): (1e-6, 0.40, 3e-3, 5e-3),
+    ("bf16-res", 16): (3e-3, 1.00, 1.5e-2, 2e-2),
 }
 
 

@@ -151,3 +151,26 @@ def _forward_p_e4m3(contone, ws, bs, noise_seed, image, act_scale):
             y = _round(torch.relu(y), "bf16")
         x = y
     return 1.0 / (1.0 + np.exp(-x[0, 0].double().numpy()))
+
+
+def forward_resnet_p(contone: np.ndarray, ws, bs, noise_seed: int, image: int = 0, acc: str = "rn",
+                     kept: int = 22) -> np.ndarray:
+    """The residual policy (stem, blocks y = ReLU(x + conv2(ReLU(conv1(x)))), output layer) in
+    the BF16 form's rounding points -- block weights bf16, every stored activation bf16 (the
+    block output after the shortcut add and the ReLU) -- with float32 sums."""
+    h, w = contone.shape
+    z = O.uniform_map(noise_seed, image, 0, h, w).astype(np.float32)
+    x = torch.from_numpy(np.stack([contone.astype(np.float32), z]))[None]
+    L = len(ws)
+    conv = (lambda a, wt, bt: _conv_trunc(a, wt, bt, kept)) if acc == "trunc" else _conv_f32
+    t = lambda l: (torch.from_numpy(np.asarray(ws[l], np.float32)), torch.from_numpy(np.asarray(bs[l], np.float32)))
+    w0, b0 = t(0)
+    x = _round(torch.relu(_conv_f32(x, w0, b0)), "bf16")
+    for blk in range((L - 2) // 2):
+        w1, b1 = t(1 + 2 * blk)
+        w2, b2 = t(2 + 2 * blk)
+        tt = _round(torch.relu(conv(x, _round(w1, "bf16"), b1)), "bf16")
+        x = _round(torch.relu(conv(tt, _round(w2, "bf16"), b2) + x), "bf16")
+    wl, bl = t(L - 1)
+    y = _conv_f32(x, wl, bl)
+    return 1.0 / (1.0 + np.exp(-y[0, 0].double().numpy()))

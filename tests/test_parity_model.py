@@ -67,3 +67,16 @@ def test_e4m3_model_meets_the_rule(chs):
     _, p_or, _ = O.forward(img, ws, bs, noise_seed=seed, quant=2, act_scale=sc)
     p8 = M.forward_p(img, ws, bs, seed, fmt="e4m3", act_scale=sc)
     assert tight_rule(p8 - p_or[0], "e4m3", len(chs) - 2) == []
+
+
+@pytest.mark.parametrize("nb", [1, 2, 16])
+def test_residual_model_meets_the_rule(nb):
+    """The residual policy's float32 model (round-to-nearest sums) against the oracle's
+    residual forward with the BF16 rounding points."""
+    seed = 43
+    ws, _ = synth.resnet_policy(nb, synth.RESNET_WIDTH, seed)
+    bs = synth.random_biases(synth.resnet_channels(nb, synth.RESNET_WIDTH), seed + 1, scale=0.05)
+    img = synth.contone_image(96, 160, seed=seed)
+    _, p_or = O.forward_resnet(img, ws, bs, 3, 0, quant=1)
+    pm = M.forward_resnet_p(img, ws, bs, 3, 0)
+    assert tight_rule(pm - p_or, "bf16-res", nb) == []
