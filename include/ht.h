@@ -242,19 +242,21 @@ ht_status ht_plan_destroy(ht_plan *plan);
 
 /* ------------------------------------------------------------------------ */
 /* Schedule autotuner (tensor-core forms).  Runs the caller's ht_halftone call */
-/* (outputs are written) under every candidate conv schedule -- rows per work */
-/* unit (TMEM accumulator blocks: 8, 6, 4) x unit order (row bands first,      */
-/* column tiles first) x CTA form of the 64 -> 64 layers (one CTA per 128-    */
-/* pixel tile, M = 128 MMAs; or a CTA pair per 256-pixel tile, M = 256 MMAs   */
-/* of tcgen05 cta_group::2, policies of the 64-wide plain architecture only)  */
-/* -- reps times each after a warm-up, timed with CUDA events on `stream`,    */
-/* and keeps the fastest in the policy (used by later ht_halftone calls and   */
-/* plans).  results: nullable host array of up to max_results entries,        */
-/* *n_results written (12 candidates, or 6 where the pair form does not       */
-/* apply).  Outputs are bit-identical under every schedule (same per-pixel     */
-/* accumulation order).                                                        */
+/* (outputs are written) under every candidate conv schedule -- work units of */
+/* 8, 6 or 4 rows (one TMEM accumulator block per row), or streaming strips   */
+/* of 32, 64 or 128 rows (eight TMEM blocks used as a ring; every input row   */
+/* staged once per strip; 64-wide plain architecture) x unit order (row bands */
+/* first, column tiles first) x CTA form of the 64 -> 64 layers (one CTA per  */
+/* 128-pixel tile, M = 128 MMAs; or, with 8-row units, a CTA pair per 256-    */
+/* pixel tile, M = 256 MMAs of tcgen05 cta_group::2, 64-wide plain            */
+/* architecture only) -- reps times each after a warm-up, timed with CUDA     */
+/* events on `stream`, and keeps the fastest in the policy (used by later     */
+/* ht_halftone calls and plans).  results: nullable host array of up to       */
+/* max_results entries, *n_results written (18 candidates; 6 for the residual */
+/* architecture).  Outputs are bit-identical under every schedule: each output */
+/* pixel accumulates in one TMEM column through the same chain of MMAs.        */
 /* ------------------------------------------------------------------------ */
-#define HT_TUNE_CANDIDATES 12
+#define HT_TUNE_CANDIDATES 18
 typedef struct {
     int rows_per_unit;
     int unit_order;
@@ -262,9 +264,12 @@ typedef struct {
     float ms;                 /* mean time of one call */
 } ht_tune_result;
 
-/* Sets the conv schedule directly (rows_per_unit in [3, 8], unit_order 0 or 1,
- * cta_pair 0 or 1; the pair form is used only where it applies), e.g. one found
- * by an earlier ht_policy_autotune run. */
+/* Sets the conv schedule directly, e.g. one found by an earlier ht_policy_autotune
+ * run: rows_per_unit in [3, 8] (work units) or in [9, 4096] (streaming strips; the
+ * 64-wide plain architecture only, else HT_ERR_INVALID_ARG), unit_order 0 or 1,
+ * cta_pair 0 or 1 (the pair form is used only where it applies: 8-row units of the
+ * 64-wide plain architecture in BF16 or FP8).  A new policy starts at 64-row strips,
+ * column tiles first (64, 1, 0); a residual policy at 8-row units (8, 0, 0). */
 ht_status ht_policy_set_schedule(ht_policy *p, int rows_per_unit, int unit_order, int cta_pair);
 
 ht_status ht_policy_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed,

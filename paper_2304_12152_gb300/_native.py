@@ -59,7 +59,7 @@ class TuneResult(C.Structure):
     _fields_ = [("rows_per_unit", C.c_int), ("unit_order", C.c_int), ("cta_pair", C.c_int), ("ms", C.c_float)]
 
 
-HT_TUNE_CANDIDATES = 12
+HT_TUNE_CANDIDATES = 18
 
 
 class TrainDesc(C.Structure):

@@ -223,6 +223,10 @@ ht_status ht_create_policy(const ht_policy_desc *desc, const float *weights_host
     p->levels = desc->head == HT_HEAD_MULTITONE ? desc->levels : desc->head == HT_HEAD_SOFTMAX ? 4 : 2;
     p->arch = desc->arch;
     p->width = desc->arch == HT_ARCH_RESNET ? 32 : 64;
+    if (desc->arch != HT_ARCH_RESNET) {       // default schedule: 64-row streaming strips, column tiles first
+        p->tune_ru = 64;
+        p->tune_order = 1;
+    }
     p->K = desc->channels[desc->n_layers];
     p->prec = desc->precision;
     cudaGetDevice(&p->device);
@@ -471,7 +475,9 @@ ht_status ht_plan_destroy(ht_plan *plan) { return ht_plan_destroy_impl(plan); }
 ht_status ht_policy_set_schedule(ht_policy *p, int rows_per_unit, int unit_order, int cta_pair)
 {
     HT_CHECK_ARG(p != nullptr, "null policy");
-    HT_CHECK_ARG(rows_per_unit >= 3 && rows_per_unit <= 8, "rows_per_unit must be in [3, 8]");
+    HT_CHECK_ARG(rows_per_unit >= 3 && rows_per_unit <= 4096, "rows_per_unit must be in [3, 4096]");
+    HT_CHECK_ARG(rows_per_unit <= 8 || p->arch != HT_ARCH_RESNET,
+                 "streaming strips (rows_per_unit > 8) need the 64-wide plain architecture");
     HT_CHECK_ARG(unit_order == 0 || unit_order == 1, "unit_order must be 0 or 1");
     HT_CHECK_ARG(cta_pair == 0 || cta_pair == 1, "cta_pair must be 0 or 1");
     p->tune_ru = rows_per_unit;

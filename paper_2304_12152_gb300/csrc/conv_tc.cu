@@ -143,8 +143,17 @@ __device__ __forceinline__ void head_partials9(const float *v, const ConvParams 
 // (block j = output row y0 + j).  Edge input rows use N = 64 / 128.  Every
 // accumulator block is zeroed by the epilogue after it is drained, so all MMAs
 // accumulate.  Per output row: 12-15 MMAs of N = 192 instead of 36 of N = 64.
+//
+// Row-streaming form (STREAM): a unit is a tall strip (P.ru > 8 output rows) of one column
+// tile, so every input row is staged once per strip instead of 1.25 times per 8-row unit.
+// The eight TMEM blocks form a ring: the CTA's G-th output row (G counts the output rows of
+// all its strips so far) accumulates in block G % 8, guarded by that block's bfull / bfree
+// barriers at phase G / 8.  A staged row's window of up to three output rows wraps past
+// block 7 for two rows in eight; there the window is issued as two MMAs per K step (blocks
+// p .. 7 and 0 ..), so that each output row still accumulates in one block through one chain
+// of MMAs, in the same order as in the 8-row units: the two forms give identical bits.
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false>
+template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false, bool STREAM = false>
 __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
 {
     using C = Cfg<FP8, KIND, CH, F16>;
@@ -279,6 +288,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
             const uint64_t b_base = sdesc(smem_u32(s_w), 3 * C::NOUT * 16, 128);
             bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(wbar), 0, s_abort, P.err));
             uint32_t slot = 0, ph = 0, uit = 0;
+            uint32_t g0 = 0;                      // streaming form: output rows of the CTA's strips so far
             int k = 0, nrows = 0;
             bool unit_start = true;
             while (ok) {
@@ -290,7 +300,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     nrows = __shfl_sync(0xffffffffu, mv[1], 0);
                     if (k < 0) break;
                     unit_start = false;
-                    if (C::MMA8 && nrows == RU && P.ru == RU) {
+                    if (C::MMA8 && !STREAM && nrows == RU && P.ru == RU) {
                         // A full unit (the common case) of an e4m3 layer, unrolled: every row's
                         // N range, TMEM block and weight sub-range is a compile-time constant,
                         // so only the barrier checks and the MMAs (6 per row) remain between
@@ -335,32 +345,63 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         continue;
                     }
                 }
-                if (k < nrows) {
-                    ok = mbar_wait_poll_warp(smem_u32(&bfree[k]), uit & 1u, s_abort, P.err);   // block k enters use
+                if (k < nrows) {                                                   // block of row k enters use
+                    if constexpr (STREAM) {
+                        const uint32_t g = g0 + (uint32_t)k;
+                        ok = mbar_wait_poll_warp(smem_u32(&bfree[g % 8u]), (g / 8u) & 1u, s_abort, P.err);
+                    } else {
+                        ok = mbar_wait_poll_warp(smem_u32(&bfree[k]), uit & 1u, s_abort, P.err);
+                    }
                     if (!ok) break;
                 }
                 tc_fence_after();
                 const int jlo = max(0, k - 2), jhi = min(nrows - 1, k);
-                const uint32_t n = (uint32_t)(jhi - jlo + 1) * C::NOUT;
-                const uint32_t idesc = idesc_m128_ab<C::AB>(n);
                 const uint32_t sb = (uint32_t)(2 - k + jlo);                       // first stacked dy block
-                const uint32_t d = tmem_base + (uint32_t)jlo * C::NOUT;
-                const uint64_t a_q = a_base + (uint64_t)((slot * (uint32_t)C::SLOT_BYTES) >> 4);
-                const uint64_t b_q = b_base + (uint64_t)((sb * C::NOUT * 16u) >> 4);
+                const uint32_t a_off = (slot * (uint32_t)C::SLOT_BYTES) >> 4;
+                if constexpr (STREAM) {
+                    // ring block of row jlo; rows past block 7 go to a second MMA at block 0
+                    const uint32_t p = (g0 + (uint32_t)jlo) % 8u;
+                    const uint32_t r = (uint32_t)(jhi - jlo + 1);
+                    const uint32_t r1 = min(r, 8u - p), r2 = r - r1;
+                    const uint32_t idesc1 = idesc_m128_ab<C::AB>(r1 * C::NOUT);
+                    const uint32_t idesc2 = idesc_m128_ab<C::AB>((r2 ? r2 : 1u) * C::NOUT);
+                    const uint64_t a_q = a_base + (uint64_t)a_off;
+                    const uint64_t b_q1 = b_base + (uint64_t)((sb * C::NOUT * 16u) >> 4);
+                    const uint64_t b_q2 = b_base + (uint64_t)(((sb + r1) * C::NOUT * 16u) >> 4);
 #pragma unroll
-                for (int dx = 0; dx < 3; ++dx)
+                    for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-                    for (int ks = 0; ks < C::KSTEPS; ++ks)
-                        mma_ss_el<C::MMA8>(el, d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
-                                        b_q + (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4),
-                                        idesc);
+                        for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                            const uint64_t a_k = a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4);
+                            const uint64_t b_k = (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4);
+                            mma_ss_el<C::MMA8>(el, tmem_base + p * C::NOUT, a_k, b_q1 + b_k, idesc1);
+                            if (r2) mma_ss_el<C::MMA8>(el, tmem_base, a_k, b_q2 + b_k, idesc2);
+                        }
+                } else {
+                    const uint32_t n = (uint32_t)(jhi - jlo + 1) * C::NOUT;
+                    const uint32_t idesc = idesc_m128_ab<C::AB>(n);
+                    const uint32_t d = tmem_base + (uint32_t)jlo * C::NOUT;
+                    const uint64_t a_q = a_base + (uint64_t)a_off;
+                    const uint64_t b_q = b_base + (uint64_t)((sb * C::NOUT * 16u) >> 4);
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                        for (int ks = 0; ks < C::KSTEPS; ++ks)
+                            mma_ss_el<C::MMA8>(el, d, a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4),
+                                            b_q + (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4),
+                                            idesc);
+                }
                 mma_commit_el(el, smem_u32(&empty[slot]));
-                if (k >= 2) mma_commit_el(el, smem_u32(&bfull[k - 2]));     // output row k-2 complete
+                if (k >= 2)                                                 // output row k-2 complete
+                    mma_commit_el(el, smem_u32(&bfull[STREAM ? (g0 + (uint32_t)k - 2u) % 8u : (uint32_t)(k - 2)]));
                 if (++slot == (uint32_t)NSLOT) {
                     slot = 0;
                     ph ^= 1u;
                 }
-                if (k == nrows + 1) {
+                if (STREAM && k == nrows + 1) {
+                    g0 += (uint32_t)nrows;                // the ring continues with the next strip
+                    unit_start = true;
+                } else if (k == nrows + 1) {
                     // Blocks a short unit leaves unused still go through one full/free round per
                     // unit, so that every block's barriers stay in step.  Wait until the epilogue
                     // has released the block from the previous unit before signalling it: a parity
@@ -382,28 +423,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
         }
     } else {
         // ------------------------- epilogue -------------------------
-        // Eight warps: two per TMEM lane quarter; group g drains blocks j = g, g+2, ...
+        // Eight warps: two per TMEM lane quarter; group g drains blocks g, g+2, ...  (8-row
+        // units: block j holds row j; streaming form: block (G0 + j) % 8 holds row j, so a
+        // group still owns the blocks of its parity)
         const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
         const int grp = (warp - 2) >> 2;              // 0 or 1
         const int px = quarter * 32 + lane;           // pixel within the tile
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        const int nblk = STREAM ? 8 : P.ru;
         // accumulators start at zero (TMEM is undefined after allocation)
-        for (int j = grp; j < P.ru; j += 2)
+        for (int j = grp; j < nblk; j += 2)
             for (int c = 0; c < C::NOUT; c += 16) tmem_zero16(lane_base + j * C::NOUT + c);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0)
-            for (int j = grp; j < P.ru; j += 2) mbar_arrive(smem_u32(&bfree[j]));
+            for (int j = grp; j < nblk; j += 2) mbar_arrive(smem_u32(&bfree[j]));
         uint32_t uit = 0;
+        uint32_t g0 = 0;                              // streaming form: the CTA's output rows so far
         bool ok = true;
         for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x, ++uit) {
             const UnitInfo ui = unit_info(P.imgs, P.n_imgs, P.in_buf, u, P.ru, P.order);
             const int y0 = ui.y0, nrows = ui.nrows;
             const int x = ui.x0 + px;
-            for (int j = grp; j < P.ru; j += 2) {
+            const int jbeg = STREAM ? (int)((g0 + (uint32_t)grp) & 1u) : grp;
+            const int jend = STREAM ? nrows : P.ru;
+            const uint32_t g_unit = g0;
+            if (STREAM) g0 += (uint32_t)nrows;
+            for (int j = jbeg; j < jend; j += 2) {
+                const uint32_t blk = STREAM ? (g_unit + (uint32_t)j) % 8u : (uint32_t)j;
+                const uint32_t par = STREAM ? ((g_unit + (uint32_t)j) / 8u) & 1u : uit & 1u;
                 int got = 0;
-                if (lane == 0) got = mbar_wait(smem_u32(&bfull[j]), uit & 1u, s_abort, P.err) ? 1 : 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&bfull[blk]), par, s_abort, P.err) ? 1 : 0;
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
@@ -414,7 +465,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     // 4-logit head: softmax, level draw, 2-bit packing (whole warp, 32 pixels)
                     float v[16];
                     if (j < nrows) {
-                        const uint32_t taddr = lane_base + j * C::NOUT;
+                        const uint32_t taddr = lane_base + blk * C::NOUT;
                         tmem_ld16(taddr, v);
                         tmem_wait_ld();
                         tmem_zero16(taddr);
@@ -422,7 +473,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                     }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&bfree[j]));
+                    if (lane == 0) mbar_arrive(smem_u32(&bfree[blk]));
                     if (j < nrows) {
                         float z[4];
 #pragma unroll
@@ -436,7 +487,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 }
                 float v[C::CO];
                 if (j < nrows) {
-                    const uint32_t taddr = lane_base + j * (uint32_t)C::NOUT;
+                    const uint32_t taddr = lane_base + blk * (uint32_t)C::NOUT;
 #pragma unroll
                     for (int c = 0; c < C::CO; c += 16) tmem_ld16(taddr + c, v + c);
                     tmem_wait_ld();
@@ -445,7 +496,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bfree[j]));
+                if (lane == 0) mbar_arrive(smem_u32(&bfree[blk]));
                 if (j < nrows && x < ui.W) {
                     const size_t o = (size_t)(y0 + j) * ui.W + x;
                     if (TR && P.dgrad) {
@@ -926,13 +977,13 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__r
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false>
+template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false, bool STREAM = false>
 ht_status ensure_attr()
 {
     static bool attr_set = false;
     if (!attr_set) {
-        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND, TR, CH, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg<FP8, KIND, CH, F16>::SMEM));
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND, TR, CH, F16, STREAM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FP8, KIND, CH, F16>::SMEM));
         attr_set = true;
     }
     return HT_OK;
@@ -992,21 +1043,46 @@ ht_status ensure_all_attrs()
         (st = ensure_attr<false, KIND_HEADPART, false, 64, true>()) != HT_OK ||
         (st = ensure_attr<false, KIND_HEAD4, false, 64, true>()) != HT_OK)
         return st;
+    if ((st = ensure_attr<false, KIND_HIDDEN, false, 64, false, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HEADPART, false, 64, false, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_FIRST, false, 64, false, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HEAD4, false, 64, false, true>()) != HT_OK ||
+        (st = ensure_attr<true, KIND_HIDDEN, false, 64, false, true>()) != HT_OK ||
+        (st = ensure_attr<true, KIND_HEADPART, false, 64, false, true>()) != HT_OK ||
+        (st = ensure_attr<true, KIND_FIRST, false, 64, false, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_FIRST, false, 64, true, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HIDDEN, false, 64, true, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HEADPART, false, 64, true, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_HEAD4, false, 64, true, true>()) != HT_OK)
+        return st;
     return HT_OK;
 }
 
-template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false>
-ht_status launch_conv(const ConvParams &P, cudaStream_t s)
+template <bool FP8, int KIND, bool TR, int CH, bool F16, bool STREAM>
+ht_status launch_conv_k(const ConvParams &P, cudaStream_t s)
 {
-    const ht_status st = ensure_attr<FP8, KIND, TR, CH, F16>();
+    const ht_status st = ensure_attr<FP8, KIND, TR, CH, F16, STREAM>();
     if (st != HT_OK) return st;
     const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
     ht_prof_start(KIND == KIND_FIRST ? HTK_FIRST_TC : KIND == KIND_HEAD4 ? HTK_HEAD_TC
                   : FP8 ? HTK_CONV_TC_FP8 : F16 ? HTK_CONV_TC_FP16 : HTK_CONV_TC_BF16, s);
-    k_conv_tc<FP8, KIND, TR, CH, F16><<<grid, NTHREADS, Cfg<FP8, KIND, CH, F16>::SMEM, s>>>(P);
+    k_conv_tc<FP8, KIND, TR, CH, F16, STREAM><<<grid, NTHREADS, Cfg<FP8, KIND, CH, F16>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
+}
+
+// Units of more than RU rows run as streaming strips (inference forms of the 64-wide
+// architecture only); the 8-row form holds at most RU rows per unit.
+template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false>
+ht_status launch_conv(const ConvParams &P, cudaStream_t s)
+{
+    if (P.ru < 1) return HT_ERR_INVALID_ARG;
+    if (P.ru > RU) {
+        if constexpr (!TR && CH == 64) return launch_conv_k<FP8, KIND, false, 64, F16, true>(P, s);
+        return HT_ERR_INVALID_ARG;
+    }
+    return launch_conv_k<FP8, KIND, TR, CH, F16, false>(P, s);
 }
 
 // CTA-pair form: P.n_units counts 256-pixel units (ImgDesc::unit2_begin), P.wpack
@@ -1353,6 +1429,17 @@ void ht_preload_conv_tc()
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, false, 64, true>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEADPART, false, 64, true>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEAD4, false, 64, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, false, 64, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEADPART, false, 64, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, false, 64, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEAD4, false, 64, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_HIDDEN, false, 64, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_HEADPART, false, 64, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_FIRST, false, 64, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, false, 64, true, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, false, 64, true, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEADPART, false, 64, true, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEAD4, false, 64, true, true>);
     cudaFuncGetAttributes(&fa, k_conv_tc2<false, KIND_HIDDEN>);
     cudaFuncGetAttributes(&fa, k_conv_tc2<false, KIND_HEADPART>);
     cudaFuncGetAttributes(&fa, k_conv_tc2<true, KIND_HIDDEN>);
@@ -1470,7 +1557,7 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
 {
     const bool fp8 = (p->prec == HT_FP8_E4M3);
     const bool f16 = (p->prec == HT_FP16);
-    pair = pair && p->d_wpack2 && p->arch != HT_ARCH_RESNET && !f16;
+    pair = pair && p->d_wpack2 && p->arch != HT_ARCH_RESNET && !f16 && ru <= RU;
     const int n_inner = p->L - 2;
     for (const TcGroup &G : groups) {
         const ImgDesc *dt = d_table + G.g0;
@@ -1745,9 +1832,15 @@ ht_status ht_plan_destroy_impl(ht_plan *pl)
 ht_status ht_tc_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, uint64_t seed, uint32_t *const *bits,
                          float *const *prob, int reps, ht_tune_result *out, int max_out, int *n_out, cudaStream_t s)
 {
-    static const int cand[][3] = {{8, 0, 0}, {8, 1, 0}, {6, 0, 0}, {6, 1, 0}, {4, 0, 0}, {4, 1, 0},
-                                  {8, 0, 1}, {8, 1, 1}, {6, 0, 1}, {6, 1, 1}, {4, 0, 1}, {4, 1, 1}};
-    const int nc = p->d_wpack2 && p->arch != HT_ARCH_RESNET ? 12 : 6;
+    // 8-row units (8, 6, 4 rows), streaming strips (32, 64, 128 rows; 64-wide architecture),
+    // CTA pairs (64-wide architecture with a pair weight image)
+    static const int cand[][3] = {{8, 0, 0},  {8, 1, 0},  {6, 0, 0},  {6, 1, 0},  {4, 0, 0}, {4, 1, 0},
+                                  {32, 0, 0}, {32, 1, 0}, {64, 0, 0}, {64, 1, 0}, {128, 0, 0}, {128, 1, 0},
+                                  {8, 0, 1},  {8, 1, 1},  {6, 0, 1},  {6, 1, 1},  {4, 0, 1}, {4, 1, 1}};
+    const bool plain = p->arch != HT_ARCH_RESNET;
+    int idx[18], nc = 0;
+    for (int c = 0; c < 18; ++c)
+        if ((cand[c][0] <= RU || plain) && (!cand[c][2] || (plain && p->d_wpack2))) idx[nc++] = c;
     cudaEvent_t e0, e1;
     HT_CUDA_TRY(cudaEventCreate(&e0));
     HT_CUDA_TRY(cudaEventCreate(&e1));
@@ -1755,7 +1848,8 @@ ht_status ht_tc_autotune(ht_policy *p, const ht_image *imgs, int n, int mode, ui
     float best = 1e30f;
     int bi = 0, k_out = 0;
     ht_status st = HT_OK;
-    for (int c = 0; c < nc && st == HT_OK; ++c) {
+    for (int ci = 0; ci < nc && st == HT_OK; ++ci) {
+        const int c = idx[ci];
         p->tune_ru = cand[c][0];
         p->tune_order = cand[c][1];
         p->tune_pair = cand[c][2];

@@ -127,8 +127,10 @@ struct ht_policy {
     float head4_inv_scale = 1.f;    // FP16 form: the 4-logit head's weights are stored x 2^k (kept in the
                                     // binary16 normal range), its logits multiplied back by 2^-k
     float head_bias = 0.f;
-    // conv schedule of the tensor-core forms (set by ht_policy_autotune): rows per
-    // work unit (TMEM accumulator blocks) and unit order
+    // conv schedule of the tensor-core forms (set by ht_policy_autotune): rows per work
+    // unit (up to 8: one TMEM accumulator block per row; more: a streaming strip over the
+    // TMEM ring) and unit order.  Policies of the 64-wide plain architecture start at
+    // 64-row strips, column tiles first.
     int tune_ru = 8, tune_order = 0;
     int tune_pair = 0;              // 1: 64 -> 64 layers of the inference forms run as CTA pairs (M = 256)
     // CTA-pair weight images of the inner 64 -> 64 layers (two per layer, one per CTA of a pair)

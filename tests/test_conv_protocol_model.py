@@ -251,6 +251,130 @@ def test_model_catches_the_earlier_protocol_bugs(variant):
 
 
 # ---------------------------------------------------------------------------
+# Row-streaming form of the conv pipeline (tall work units, TMEM blocks as a ring).  A
+# unit is a strip of nrows output rows (tens to hundreds); output row G of the CTA (G
+# counts the output rows of all its strips so far) accumulates in block G % 8, guarded by
+# bfull / bfree[G % 8] at phase G // 8.  The MMA of a staged row covers output rows
+# jlo .. jhi starting at block (G0 + jlo) % 8; where that window passes block 7 it is
+# issued as two MMAs (blocks p .. 7, then 0 ..), so every row keeps one block.  Epilogue
+# group g owns the rows with G % 2 == g (the blocks of its parity).
+# ---------------------------------------------------------------------------
+NRING = 8
+
+
+class StreamSim(Sim):
+    def __init__(self, units, rng, variant=None):
+        super().__init__(units, 8, rng, variant)
+        self.blk_row = [-1] * NRING               # global row whose sum the block holds
+        self.row_contrib = {}                     # global row -> staged-row contributions completed
+
+    def mma(self):
+        yield from wait(self.wbar, 0)
+        li, start, k, nrows, g0 = 0, True, 0, 0, 0
+        while True:
+            slot, rnd = li % NSLOT, li // NSLOT
+            yield from wait(self.full[slot], rnd)
+            if start:
+                k, nrows = self.meta[slot]
+                if k < 0:
+                    break
+                start = False
+            if not self.slot_landed[slot] or self.slot_row[slot] != li:
+                raise Violation(f"row {li} read before it landed")
+            if k < nrows:
+                g = g0 + k
+                yield from wait(self.bfree[g % NRING], g // NRING)
+                if self.blk_zeroed[g % NRING] != 4:
+                    raise Violation(f"block {g % NRING} accumulated before its epilogue warps drained it")
+                self.blk_zeroed[g % NRING], self.blk_row[g % NRING] = 0, g
+                self.row_contrib[g] = 0
+            jlo, jhi = max(0, k - 2), min(nrows - 1, k)
+            p, r = (g0 + jlo) % NRING, jhi - jlo + 1
+            r1 = r if self.variant == "stream_no_split" else min(r, NRING - p)
+            parts = [(p, list(range(jlo, jlo + r1)))]
+            if r1 < r:
+                parts.append((0, list(range(jlo + r1, jhi + 1))))
+            for b0, js in parts:
+                if b0 + len(js) > NRING:
+                    raise Violation(f"MMA window of blocks {b0} .. {b0 + len(js) - 1} leaves TMEM")
+                rows = [g0 + j for j in js]
+                for i, gr in enumerate(rows):
+                    if b0 + i != gr % NRING:
+                        raise Violation(f"row {gr} accumulated in block {b0 + i}")
+                self.slot_readers[slot] += 1
+                self.pipe.append(("smma", slot, [(b0 + i, gr) for i, gr in enumerate(rows)]))
+            self.pipe.append(("commit", self.empty[slot]))
+            if k >= 2:
+                self.pipe.append(("commit", self.bfull[(g0 + k - 2) % NRING]))
+            li += 1
+            yield None
+            if k == nrows + 1:
+                g0 += nrows
+                start = True
+            else:
+                k += 1
+        self.pipe.append(("commit", self.drain))
+        yield from wait(self.drain, 0)
+
+    def epilogue(self, grp):
+        for b in range(grp, NRING, 2):            # blocks start zeroed and free
+            self.bfree[b].arrive()
+            yield None
+        g0 = 0
+        for nrows in self.units:
+            for j in range(nrows):
+                g = j if self.variant == "stream_ring_restarts" else g0 + j
+                if g % 2 != grp:
+                    continue
+                yield from wait(self.bfull[g % NRING], g // NRING)
+                if self.blk_row[g % NRING] != g or self.row_contrib.get(g) != 3:
+                    raise Violation(f"row {g} drained before its three staged rows completed")
+                yield None                         # TMEM read and zeroing of this warp's quarter
+                self.blk_zeroed[g % NRING] += 1
+                self.bfree[g % NRING].arrive()
+                yield None
+            g0 += nrows
+
+    def step_pipe(self):
+        if self.pipe[0][0] == "smma":
+            _, slot, blocks = self.pipe.pop(0)
+            for b, gr in blocks:
+                if self.blk_row[b] != gr:
+                    raise Violation(f"MMA for row {gr} landed in block {b}, which holds row {self.blk_row[b]}")
+                self.row_contrib[gr] += 1
+            self.slot_readers[slot] -= 1
+            return
+        super().step_pipe()
+
+
+def _tall_units(rng):
+    """Strips of a CTA: tall ones, image bottoms of any height, tiny images."""
+    n = rng.randint(1, 6)
+    return [rng.choice([rng.randint(1, 5), rng.randint(6, 40), 64]) for _ in range(n)]
+
+
+def test_stream_protocol_holds():
+    rng = random.Random(4242)
+    for trial in range(150):
+        StreamSim(_tall_units(rng), random.Random(rng.random())).run()
+
+
+@pytest.mark.parametrize("variant", ["stream_no_split", "stream_ring_restarts"])
+def test_stream_model_catches_protocol_faults(variant):
+    """A window issued as one MMA where it passes block 7 (it would leave TMEM's 512
+    columns), and an epilogue that restarts the ring at every strip instead of carrying the
+    CTA's row count across strips."""
+    rng = random.Random(99)
+    caught = 0
+    for trial in range(60):
+        try:
+            StreamSim(_tall_units(rng), random.Random(rng.random()), variant).run()
+        except Violation:
+            caught += 1
+    assert caught >= 10, caught
+
+
+# ---------------------------------------------------------------------------
 # Weight-gradient kernel (k_wgrad_tc): an activation-row ring (NSA slots) and a
 # gradient-row ring (NSG slots).  Per unit of nrows gradient rows the MMA warp needs
 # activation rows base .. base + nrows + 1; gradient row j pairs with activation rows

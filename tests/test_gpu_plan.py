@@ -78,7 +78,8 @@ def test_autotune_schedules_are_bit_identical():
     api.sync()
     assert len(res) == N.HT_TUNE_CANDIDATES
     assert sorted((r, o, pr) for r, o, pr, _ in res) == sorted(
-        [(r, o, pr) for pr in (0, 1) for r in (8, 6, 4) for o in (0, 1)])
+        [(r, o, pr) for pr in (0, 1) for r in (8, 6, 4) for o in (0, 1)]
+        + [(r, o, 0) for r in (32, 64, 128) for o in (0, 1)])
     assert all(ms > 0 for *_, ms in res)
     # the last candidate's outputs, and the chosen schedule's later calls, equal the default schedule's
     for a, b in zip(bits, ref):
@@ -96,14 +97,17 @@ def test_autotune_schedules_are_bit_identical():
 def test_many_short_units_every_schedule():
     """Stress of the conv pipeline's per-block barriers: 160 images of 13 x 300 give
     CTAs long runs of units whose last row band is short (5 of 8 rows, and for rows per
-    unit 6 / 4 other remainders), i.e. TMEM blocks left unused unit after unit.  Every
-    schedule must finish without a wait expiring and give the same bits."""
+    unit 6 / 4 other remainders), i.e. TMEM blocks left unused unit after unit; as
+    streaming strips (9 rows and a 4-row rest, or the whole 13-row image) the TMEM ring
+    continues across strips of odd height.  Every schedule must finish without a wait
+    expiring and give the same bits."""
     pol, _, _ = _policy(N.HT_BF16)
     imgs = [torch.from_numpy(synth.contone_image(13, 300, seed=8, index=i)).cuda() for i in range(160)]
     bits = [pol.alloc_bits(13, 300) for _ in imgs]
     ref = None
     for ru, order, pair in [(8, 0, 0), (8, 1, 0), (6, 0, 0), (6, 1, 0), (4, 0, 0), (4, 1, 0), (3, 0, 0), (7, 1, 0),
-                            (8, 0, 1), (8, 1, 1), (6, 0, 1), (4, 1, 1), (3, 0, 1), (7, 1, 1)]:
+                            (8, 0, 1), (8, 1, 1), (6, 0, 1), (4, 1, 1), (3, 0, 1), (7, 1, 1),
+                            (9, 0, 0), (9, 1, 0), (13, 0, 0), (13, 1, 0), (64, 1, 0)]:
         pol.set_schedule(ru, order, pair)
         for _ in range(3):
             pol.halftone_into(imgs, bits, N.HT_MODE_BERNOULLI, 3)
@@ -155,3 +159,56 @@ def test_cta_pair_form_matches_single_cta_form(prec, head):
     for a, b in zip(bits, ref):
         assert torch.equal(a, b)
     pol.set_schedule(8, 0, 0)
+
+
+STREAM_SHAPES = [(300, 200), (37, 515), (129, 131), (1, 1), (517, 140), (64, 256), (33, 129)]
+
+
+@pytest.mark.parametrize("prec,head", [(N.HT_BF16, N.HT_HEAD_SIGMOID), (N.HT_FP8_E4M3, N.HT_HEAD_SIGMOID),
+                                       (N.HT_FP16, N.HT_HEAD_SIGMOID), (N.HT_BF16, N.HT_HEAD_SOFTMAX),
+                                       (N.HT_FP16, N.HT_HEAD_SOFTMAX), (N.HT_BF16, N.HT_HEAD_MULTITONE)])
+def test_streaming_strips_match_row_units(prec, head):
+    """Streaming strips (units of more than 8 rows, the eight TMEM blocks used as a ring,
+    windows that pass the last block issued as two MMAs) accumulate every output pixel in
+    one TMEM column through the same chain of MMAs as 8-row units, so bits and
+    probabilities are equal bit for bit: every layer kind (layer 1, hidden, fused head
+    partials, 4-logit head), strip heights that leave odd remainders and strips taller than
+    the image, both unit orders; a plan captured with strips replays them."""
+    chs = synth.NET_WIDE_K4 if head == N.HT_HEAD_SOFTMAX else synth.NET_WIDE
+    ws, bs = synth.he_normal_policy(chs, 13)
+    bs = synth.random_biases(chs, 14)
+    pol = api.Policy(chs, ws, bs, head=head, precision=prec, levels=4)
+    imgs = [torch.from_numpy(synth.contone_image(h, w, seed=15, index=i)).cuda()
+            for i, (h, w) in enumerate(STREAM_SHAPES)]
+    if prec == N.HT_FP8_E4M3:
+        pol.calibrate(imgs[0], seed=9)
+    for mode in (N.HT_MODE_THRESHOLD, N.HT_MODE_BERNOULLI):
+        pol.set_schedule(8, 0, 0)
+        ref, pref = pol.halftone(imgs, mode=mode, seed=6, want_prob=True)
+        for ru, order in [(9, 0), (16, 1), (33, 0), (64, 1), (128, 0), (4096, 1)]:
+            pol.set_schedule(ru, order, 0)
+            got, pgot = pol.halftone(imgs, mode=mode, seed=6, want_prob=True)
+            api.sync()                     # also raises a device-side wait expiry
+            for i, (a, b) in enumerate(zip(got, ref)):
+                assert torch.equal(a, b), (mode, ru, order, STREAM_SHAPES[i])
+            for i, (a, b) in enumerate(zip(pgot, pref)):
+                assert torch.equal(a, b), (mode, ru, order, STREAM_SHAPES[i])
+    pol.set_schedule(64, 0, 0)
+    bits = [torch.zeros_like(b) for b in ref]
+    plan = api.Plan(pol, imgs, bits, N.HT_MODE_BERNOULLI, 6)
+    plan.launch()
+    api.sync()
+    for a, b in zip(bits, ref):
+        assert torch.equal(a, b)
+    pol.set_schedule(8, 0, 0)
+
+
+def test_streaming_strips_refused_for_the_residual_policy():
+    chs = synth.resnet_channels(2, 32)
+    ws, bs = synth.resnet_policy(2, 32, 3)
+    pol = api.Policy(chs, ws, bs, precision=N.HT_BF16, arch=N.HT_ARCH_RESNET)
+    with pytest.raises(N.HTError):
+        pol.set_schedule(9, 0, 0)
+    with pytest.raises(N.HTError):
+        pol.set_schedule(4097, 0, 0)
+    pol.set_schedule(8, 1, 0)
