@@ -345,6 +345,50 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
                         continue;
                     }
                 }
+                if constexpr (STREAM) {
+                    // Eight staged rows with full windows whose first TMEM block is 0 .. 7,
+                    // unrolled, so that every window's blocks, split point and weight sub-range
+                    // are compile-time constants (the same waits, MMAs and commits in the same
+                    // order as the rolled loop below)
+                    if (k >= 2 && ((g0 + (uint32_t)k - 2u) & 7u) == 0 && k + 7 <= nrows - 1) {
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) {
+                            if (kk > 0) {
+                                ok = mbar_wait_poll_warp(smem_u32(&full[slot]), ph, s_abort, P.err);
+                                if (!ok) break;
+                            }
+                            const uint32_t g = g0 + (uint32_t)(k + kk);         // output row entering use
+                            ok = mbar_wait_poll_warp(smem_u32(&bfree[(kk + 2) & 7]), (g / 8u) & 1u, s_abort, P.err);
+                            if (!ok) break;
+                            tc_fence_after();
+                            constexpr uint32_t r1c[8] = {3, 3, 3, 3, 3, 3, 2, 1};
+                            const uint32_t r1 = r1c[kk], r2 = 3u - r1;
+                            const uint32_t idesc1 = idesc_m128_ab<C::AB>(r1 * C::NOUT);
+                            const uint32_t idesc2 = idesc_m128_ab<C::AB>((r2 ? r2 : 1u) * C::NOUT);
+                            const uint64_t a_q = a_base + (uint64_t)((slot * (uint32_t)C::SLOT_BYTES) >> 4);
+                            const uint64_t b_q2 = b_base + (uint64_t)((r1 * C::NOUT * 16u) >> 4);
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                                for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                                    const uint64_t a_k = a_q + (uint64_t)(((2 * ks * ROW_PX + dx) * 16) >> 4);
+                                    const uint64_t b_k =
+                                        (uint64_t)((((dx * C::NCHUNK + 2 * ks) * 3) * C::NOUT * 16) >> 4);
+                                    mma_ss_el<C::MMA8>(el, tmem_base + (uint32_t)kk * C::NOUT, a_k, b_base + b_k, idesc1);
+                                    if (r2) mma_ss_el<C::MMA8>(el, tmem_base, a_k, b_q2 + b_k, idesc2);
+                                }
+                            mma_commit_el(el, smem_u32(&empty[slot]));
+                            mma_commit_el(el, smem_u32(&bfull[kk]));      // output row k + kk - 2 complete
+                            if (++slot == (uint32_t)NSLOT) {
+                                slot = 0;
+                                ph ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        k += 8;
+                        continue;
+                    }
+                }
                 if (k < nrows) {                                                   // block of row k enters use
                     if constexpr (STREAM) {
                         const uint32_t g = g0 + (uint32_t)k;
@@ -950,28 +994,142 @@ __global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__
 
 // ---------------------------------------------------------------------------
 // 1-logit head from the per-tap partials written by the last conv layer:
-// z(y,x) = b + sum_{dy,dx} d_{dy,dx}(y+dy-1, x+dx-1) (zero outside the image).
+// z(y,x) = b + sum_{dy,dx} d_{dy,dx}(y+dy-1, x+dx-1) (zero outside the image),
+// then the sigmoid (or the multitoning prototype's level), the action and the packed
+// output.  A block is a 128 x 8 tile: warp w takes row y0 + w, lane l the four pixels
+// x0 + 4l .. x0 + 4l + 3.  Where W is a multiple of 4 (and the partials are 16-byte
+// aligned) the four pixels are one aligned Philox group g = 4m: one Philox call gives their
+// four uniforms, and each tap row is one float4 load, its neighbouring columns taken from
+// the adjacent lanes.  Otherwise the pixels are read and drawn one by one.  The taps are
+// summed in the same order either way (dy, then dx), a tap outside the image adding 0.
 // ---------------------------------------------------------------------------
+constexpr int HQ_W = 128;
+
 __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__restrict__ imgs, int n_imgs, int buf,
                                                               float bias, int mode, uint64_t seed, int head, int levels)
 {
-    const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].hd_begin); });
+    const int lane = threadIdx.x, warp = threadIdx.y;           // block (32, 8): one warp per row
+    const int im = find_image(n_imgs, (int)blockIdx.x, [&](int i) { return __ldg(&imgs[i].hq_begin); });
     const ImgDesc *D = imgs + im;
-    const int lt = (int)blockIdx.x - D->hd_begin;
-    const int H = D->H, W = D->W, words = D->words;
+    const int lt = (int)blockIdx.x - __ldg(&D->hq_begin);
+    const int H = __ldg(&D->H), W = __ldg(&D->W);
+    const int hx = (W + HQ_W - 1) / HQ_W;
+    const int x0 = (lt % hx) * HQ_W, y = (lt / hx) * HT_Y + warp;
+    if (y >= H) return;                                          // the whole warp
     const float *__restrict__ part = D->part ? D->part : (const float *)D->act[buf];
-    const int hx = (W + HT_X - 1) / HT_X;
-    const int x0 = (lt % hx) * HT_X, y = (lt / hx) * HT_Y + threadIdx.y, x = x0 + threadIdx.x;
     const size_t plane = (size_t)H * W;
-    float z = bias;
-    if (y < H && x < W) {
+    const int xb = x0 + 4 * lane;
+    const bool vec = (W & 3) == 0 && (((uintptr_t)part) & 15u) == 0;
+    float z[4] = {bias, bias, bias, bias};
+    if (vec) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-            if (yy >= 0 && yy < H && xx >= 0 && xx < W) z += __ldg(part + t * plane + (size_t)yy * W + xx);
+        for (int dy = 0; dy < 3; ++dy) {
+            const int yy = y + dy - 1;
+            if (yy < 0 || yy >= H) continue;                     // uniform over the warp
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const float *row = part + (size_t)(dy * 3 + dx) * plane + (size_t)yy * W;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (xb < W) v = __ldg(reinterpret_cast<const float4 *>(row + xb));
+                if (dx == 0) {
+                    float left = __shfl_up_sync(0xffffffffu, v.w, 1);
+                    if (lane == 0) left = x0 > 0 ? __ldg(row + x0 - 1) : 0.f;
+                    z[0] += left;
+                    z[1] += v.x;
+                    z[2] += v.y;
+                    z[3] += v.z;
+                } else if (dx == 1) {
+                    z[0] += v.x;
+                    z[1] += v.y;
+                    z[2] += v.z;
+                    z[3] += v.w;
+                } else {
+                    float right = __shfl_down_sync(0xffffffffu, v.x, 1);
+                    if (lane == 31) right = x0 + HQ_W < W ? __ldg(row + x0 + HQ_W) : 0.f;
+                    z[0] += v.y;
+                    z[1] += v.z;
+                    z[2] += v.w;
+                    z[3] += right;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int x = xb + c;
+            if (x >= W) continue;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+                if (yy >= 0 && yy < H && xx >= 0 && xx < W) z[c] += __ldg(part + t * plane + (size_t)yy * W + xx);
+            }
         }
     }
-    ht_head_emit(&z, 1, head, mode, seed, D->image, x0, y, H, W, D->bits, words, D->prob, levels);
+    // uniforms of the action draw (Philox stream 1), 0.5 where unused
+    const uint32_t image = __ldg(&D->image);
+    float u[4] = {0.5f, 0.5f, 0.5f, 0.5f};
+    if (mode == HT_MODE_BERNOULLI) {
+        const uint64_t g = (uint64_t)y * (uint64_t)W + (uint64_t)xb;
+        if (vec) {
+            if (xb < W) {
+                const uint4 r = ht_philox4x32_10(make_uint4((uint32_t)(g >> 2), image, 1u, 0u),
+                                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+                u[0] = (float)(r.x >> 8) * (1.0f / 16777216.0f);
+                u[1] = (float)(r.y >> 8) * (1.0f / 16777216.0f);
+                u[2] = (float)(r.z >> 8) * (1.0f / 16777216.0f);
+                u[3] = (float)(r.w >> 8) * (1.0f / 16777216.0f);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (xb + c < W) u[c] = ht_uniform24(seed, image, 1u, g + (uint64_t)c);
+        }
+    }
+    float pv[4];
+    uint32_t code = 0;                                           // this lane's 4 or 8 output bits
+    const int words = __ldg(&D->words);
+    uint32_t *bits = D->bits + (size_t)y * words;
+    if (head == HT_HEAD_SIGMOID) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            pv[c] = 1.f / (1.f + expf(-z[c]));
+            const bool hbit = (xb + c < W) && (mode == HT_MODE_BERNOULLI ? (u[c] < pv[c]) : (pv[c] > 0.5f));
+            code |= (hbit ? 1u : 0u) << c;
+        }
+        // word x0 / 32 + l / 8 holds lanes l .. l + 7 (4 bits each, LSB first)
+        uint32_t wv = code << (4 * (lane & 7));
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 2);
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 4);
+        if ((lane & 7) == 0 && xb < W) bits[(x0 >> 5) + (lane >> 3)] = wv;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float v = 1.f / (1.f + expf(-z[c]));
+            const float t = v * (float)(levels - 1);
+            const int k = min((int)floorf(t), levels - 2);
+            const float frac = t - (float)k;
+            const int lev = k + ((mode == HT_MODE_BERNOULLI ? (u[c] < frac) : (frac > 0.5f)) ? 1 : 0);
+            pv[c] = v;
+            if (xb + c < W) code |= (uint32_t)lev << (2 * c);
+        }
+        // word x0 / 16 + l / 4 holds lanes l .. l + 3 (8 bits each, LSB first)
+        uint32_t wv = code << (8 * (lane & 3));
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 2);
+        if ((lane & 3) == 0 && xb < W) bits[(x0 >> 4) + (lane >> 2)] = wv;
+    }
+    float *prob = D->prob;
+    if (prob) {
+        float *pr = prob + (size_t)y * W;
+        if (vec && (((uintptr_t)prob) & 15u) == 0) {
+            if (xb < W) *reinterpret_cast<float4 *>(pr + xb) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (xb + c < W) pr[xb + c] = pv[c];
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1508,6 +1666,7 @@ namespace {
 struct TcGroup {
     int g0, ng, units, hd, pre;
     int units2;                 // conv units of the CTA-pair form (256-pixel tiles)
+    int hq;                     // 128 x 8 tiles of k_head_partials
 };
 
 // Host side of a call: the image tables (into `tab`, one entry per image, in call
@@ -1540,7 +1699,7 @@ void tc_make_groups(const ht_policy *p, const ht_image *imgs, int n, uint8_t *ws
             D.image = (uint32_t)g1;
             if (p->arch == HT_ARCH_RESNET)   // 32-wide buffers use half of each 128 B/px slot
                 D.part = (float *)(D.act[1] + (size_t)D.H * D.W * 64);
-            set_begins(D, G.units, G.hd, G.pre, ru, &G.units2);
+            set_begins(D, G.units, G.hd, G.pre, ru, &G.units2, &G.hq);
             ++g1;
         }
         G.ng = g1 - g0;
@@ -1622,7 +1781,7 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
                 }
             }
             ht_prof_start(HTK_HEAD_TC, s);
-            k_head_partials<<<G.hd, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, 0, p->head_bias, mode, seed, p->head, p->levels);
+            k_head_partials<<<G.hq, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, 0, p->head_bias, mode, seed, p->head, p->levels);
             ht_prof_stop(s);
             HT_LAUNCH_CHECK();
             continue;
@@ -1664,7 +1823,7 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
         }
         if (p->K == 1) {
             ht_prof_start(HTK_HEAD_TC, s);
-            k_head_partials<<<G.hd, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, cur, p->head_bias, mode, seed, p->head,
+            k_head_partials<<<G.hq, dim3(HT_X, HT_Y), 0, s>>>(dt, ng, cur, p->head_bias, mode, seed, p->head,
                                                               p->levels);
             ht_prof_stop(s);
             HT_LAUNCH_CHECK();

@@ -202,6 +202,7 @@ struct ht_tc_layer {
 };
 ht_status ht_tc_conv(const ht_tc_layer &a, cudaStream_t s);
 ht_status ht_tc_first_input(const void *table, int n_imgs, int n_groups, uint64_t seed, cudaStream_t s);
+// n_tiles: 128 x 8 head tiles of the table (ImgDesc::hq_begin prefix sums)
 ht_status ht_tc_head_partials(const void *table, int n_imgs, int n_tiles, int buf, float bias, int mode,
                               uint64_t seed, cudaStream_t s);
 

@@ -536,6 +536,7 @@ struct ImgDesc {
     int pre_begin;            // first layer-1 input group of 4 pixels (ceil(H * W / 4))
     int xtiles2;              // ceil(W / 256): column tiles of a CTA pair
     int unit2_begin;          // first conv unit of the CTA-pair form (xtiles2 * ceil(H / RU) units per image)
+    int hq_begin;             // first 128 x 8 tile of k_head_partials (ceil(W / 128) * ceil(H / 8))
 };
 
 // largest i with begin(i) <= u (images sorted by their begin offsets)
@@ -590,7 +591,8 @@ __device__ __forceinline__ UnitInfo unit_info(const ImgDesc *imgs, int n_imgs, i
 
 // Work-index layout of one image inside a call's table: conv units, head tiles,
 // layer-1 input groups (prefix sums over the images in table order).
-inline void set_begins(ImgDesc &D, int &units, int &hd, int &pre, int ru = RU, int *units2 = nullptr)
+inline void set_begins(ImgDesc &D, int &units, int &hd, int &pre, int ru = RU, int *units2 = nullptr,
+                       int *hq = nullptr)
 {
     D.xtiles = (D.W + TILE_M - 1) / TILE_M;
     D.unit_begin = units;
@@ -599,6 +601,8 @@ inline void set_begins(ImgDesc &D, int &units, int &hd, int &pre, int ru = RU, i
     D.xtiles2 = (D.W + 2 * TILE_M - 1) / (2 * TILE_M);
     D.unit2_begin = units2 ? *units2 : 0;
     if (units2) *units2 += D.xtiles2 * ((D.H + ru - 1) / ru);
+    D.hq_begin = hq ? *hq : 0;
+    if (hq) *hq += D.xtiles * ((D.H + HT_Y - 1) / HT_Y);
     units += D.xtiles * ((D.H + ru - 1) / ru);
     hd += ((D.W + HT_X - 1) / HT_X) * ((D.H + HT_Y - 1) / HT_Y);
     pre += (int)(((size_t)D.H * D.W + 3) / 4);

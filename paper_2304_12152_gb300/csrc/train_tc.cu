@@ -710,10 +710,10 @@ inline int T_DG(int L, int l) { return 2 * L - 1 + l; }  // data gradient throug
 inline int n_tables(int L) { return 3 * L - 2; }
 
 void build_tables(const ht_policy *p, const ht_train_tc_ws &w, const ht_image *imgs, int nimg,
-                  std::vector<ImgDesc> &all, int &units, int &hd, int &pre)
+                  std::vector<ImgDesc> &all, int &units, int &hd, int &pre, int &hq)
 {
     const int L = p->L, nh = L - 1;
-    units = hd = pre = 0;
+    units = hd = pre = hq = 0;
     std::vector<ImgDesc> D0(nimg);
     for (int i = 0; i < nimg; ++i) {
         ImgDesc D{};
@@ -723,7 +723,7 @@ void build_tables(const ht_policy *p, const ht_train_tc_ws &w, const ht_image *i
         D.W = imgs[i].w;
         D.image = (uint32_t)i;
         D.words = ht_bits_row_words(D.W, HT_HEAD_SIGMOID);
-        set_begins(D, units, hd, pre);
+        set_begins(D, units, hd, pre, RU, nullptr, &hq);
         D0[i] = D;
     }
     all.assign((size_t)n_tables(L) * nimg, ImgDesc{});
@@ -792,8 +792,8 @@ ht_status ht_train_tc_forward(ht_policy *p, ht_train_tc_ws &w, const ht_image *i
 {
     const int L = p->L;
     std::vector<ImgDesc> all;
-    int units, hd, pre;
-    build_tables(p, w, imgs, nimg, all, units, hd, pre);
+    int units, hd, pre, hq;
+    build_tables(p, w, imgs, nimg, all, units, hd, pre, hq);
     w.units = units;
     w.hd = hd;
     HT_CUDA_TRY(cudaMemcpyAsync(w.tables, all.data(), all.size() * sizeof(ImgDesc), cudaMemcpyHostToDevice, s));
@@ -825,7 +825,7 @@ ht_status ht_train_tc_forward(ht_policy *p, ht_train_tc_ws &w, const ht_image *i
         a.seed = seed;
         if ((st = ht_tc_conv(a, s)) != HT_OK) return st;
     }
-    return ht_tc_head_partials(tab(T_HEAD(L)), nimg, hd, 0, p->head_bias, HT_MODE_THRESHOLD, seed, s);
+    return ht_tc_head_partials(tab(T_HEAD(L)), nimg, hq, 0, p->head_bias, HT_MODE_THRESHOLD, seed, s);
 }
 
 ht_status ht_train_tc_backward(ht_policy *p, ht_train_tc_ws &w, int nimg, uint64_t seed, float *grad_w, float *grad_b,

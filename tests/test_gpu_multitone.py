@@ -43,19 +43,21 @@ def test_fp32_multitone_head_matches_oracle(L, mode):
     assert np.abs(probs[0][0].cpu().numpy() - v).max() < 2e-5
 
 
-def test_bf16_multitone_head_matches_bf16_oracle():
+@pytest.mark.parametrize("H,W", [(60, 150), (37, 200)])
+def test_bf16_multitone_head_matches_bf16_oracle(H, W):
     """Tensor-core form, 8-layer 64-wide net, 4 levels, Bernoulli: vs the BF16-emulating
     oracle.  v is held to the 7-layer bf16 row of the tight rule (tests/_cases.TIGHT), as
     the binary head's p.  Residual mismatches come from activations at bf16 rounding
     boundaries; the level rule compares v (L - 1) - k with u, so a decision can move only
     where the oracle's margin (|frac - u|, or the distance of v (L - 1) from a level) is
     within (L - 1) |dv| of the measured dv at that pixel: every mismatch must be explained
-    so, and there are at most (L - 1) x 1e-3 of the decided pixels."""
+    so, and there are at most (L - 1) x 1e-3 of the decided pixels.  Widths 150 (pixels
+    read one by one) and 200 (a multiple of 4: four pixels per lane from one Philox call,
+    and a ragged second 128-pixel tile)."""
     chs = synth.NET_WIDE
     ws, bs = synth.he_normal_policy(chs, 33)
     L = 4
     pol = api.Policy(chs, ws, bs, head=N.HT_HEAD_MULTITONE, precision=N.HT_BF16, levels=L)
-    H, W = 60, 150
     img = synth.contone_image(H, W, seed=34)
     bits, probs = pol.halftone([torch.from_numpy(img).cuda()], mode=N.HT_MODE_BERNOULLI, seed=6, want_prob=True)
     torch.cuda.synchronize()
