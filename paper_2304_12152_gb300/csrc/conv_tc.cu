@@ -959,35 +959,80 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
 // layer-1 sums carry float32-level error, as a float32 convolution would.
 // z comes from Philox4x32-10 with one call per aligned group of 4 indices g.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__ imgs, int n_imgs, uint64_t seed)
+__device__ __forceinline__ void first_input_pixel(float c, float z, uint4 &o0, uint4 &o1)
 {
-    const int gi = blockIdx.x * blockDim.x + threadIdx.x;      // global 4-group index
-    const int im = find_image(n_imgs, gi, [&](int i) { return __ldg(&imgs[i].pre_begin); });
+    float c0, c1, c2, z0, z1, z2;
+    split3_bf16(c, c0, c1, c2);
+    split3_bf16(z, z0, z1, z2);
+    o0 = make_uint4(pack_bf16x2(c0, c0), pack_bf16x2(c1, c0), pack_bf16x2(c1, c2), pack_bf16x2(z0, z0));
+    o1 = make_uint4(pack_bf16x2(z1, z0), pack_bf16x2(z1, z2), 0u, 0u);
+}
+
+// A block covers 256 groups (1 024 pixels).  Where they all belong to one image, the
+// outputs are staged in shared memory and written back with consecutive threads on
+// consecutive pixels; a block that straddles two images writes pixel by pixel.
+__global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__ imgs, int n_imgs, int n_groups,
+                                                     uint64_t seed)
+{
+    __shared__ uint4 s_out[2][1024];
+    const int t = threadIdx.x;
+    const int gb = blockIdx.x * 256;                            // the block's first 4-group
+    const int gi = gb + t;                                      // this thread's 4-group
+    const int im = find_image(n_imgs, gi < n_groups ? gi : n_groups - 1,
+                              [&](int i) { return __ldg(&imgs[i].pre_begin); });
+    const int imb = find_image(n_imgs, gb, [&](int i) { return __ldg(&imgs[i].pre_begin); });
+    const bool one_image = __syncthreads_and(gi >= n_groups || im == imb);
     const ImgDesc *D = imgs + im;
-    const int H = D->H, W = D->W;
-    const uint64_t npx = (uint64_t)H * W;
-    const uint64_t g0 = (uint64_t)(gi - D->pre_begin) * 4;
-    if (g0 >= npx) return;
-    const uint4 r = ht_philox4x32_10(make_uint4((uint32_t)(g0 >> 2), D->image, 0u, 0u),
-                                     make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    const uint32_t lanes[4] = {r.x, r.y, r.z, r.w};
-    float cv[4];
+    const int W = __ldg(&D->W), cpitch = __ldg(&D->cpitch);
+    const uint64_t npx = (uint64_t)__ldg(&D->H) * (uint64_t)W;
+    const uint64_t g0 = (uint64_t)(gi - __ldg(&D->pre_begin)) * 4;
+    const bool active = gi < n_groups && g0 < npx;
+    uint4 o0[4] = {}, o1[4] = {};
+    if (active) {
+        const uint4 r = ht_philox4x32_10(make_uint4((uint32_t)(g0 >> 2), __ldg(&D->image), 0u, 0u),
+                                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+        const uint32_t lanes[4] = {r.x, r.y, r.z, r.w};
+        uint64_t y = g0 / (uint64_t)W;
+        int x = (int)(g0 - y * (uint64_t)W);
+        const float *__restrict__ contone = D->contone;
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        const uint64_t g = g0 + l;
-        cv[l] = g < npx ? __ldg(D->contone + (size_t)(g / W) * D->cpitch + (g % W)) : 0.f;
+        for (int l = 0; l < 4; ++l) {
+            const float c = g0 + l < npx ? __ldg(contone + (size_t)y * cpitch + x) : 0.f;
+            const float z = (float)(lanes[l] >> 8) * (1.0f / 16777216.0f);
+            first_input_pixel(c, z, o0[l], o1[l]);
+            if (++x == W) {
+                x = 0;
+                ++y;
+            }
+        }
     }
     uint4 *out = reinterpret_cast<uint4 *>(D->act[1]);
+    if (one_image) {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        const uint64_t g = g0 + l;
-        if (g >= npx) break;
-        const float z = (float)(lanes[l] >> 8) * (1.0f / 16777216.0f);
-        float c0, c1, c2, z0, z1, z2;
-        split3_bf16(cv[l], c0, c1, c2);
-        split3_bf16(z, z0, z1, z2);
-        out[g] = make_uint4(pack_bf16x2(c0, c0), pack_bf16x2(c1, c0), pack_bf16x2(c1, c2), pack_bf16x2(z0, z0));
-        out[npx + g] = make_uint4(pack_bf16x2(z1, z0), pack_bf16x2(z1, z2), 0u, 0u);
+        for (int l = 0; l < 4; ++l) {
+            s_out[0][4 * t + l] = o0[l];
+            s_out[1][4 * t + l] = o1[l];
+        }
+        __syncthreads();
+        const uint64_t gB = (uint64_t)(gb - __ldg(&imgs[imb].pre_begin)) * 4;   // the block's first pixel
+        const uint64_t npxb = (uint64_t)__ldg(&imgs[imb].H) * (uint64_t)__ldg(&imgs[imb].W);
+        uint4 *outb = reinterpret_cast<uint4 *>(imgs[imb].act[1]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int idx = t + 256 * k;
+            const uint64_t g = gB + (uint64_t)idx;
+            if (gb + idx / 4 < n_groups && g < npxb) {
+                outb[g] = s_out[0][idx];
+                outb[npxb + g] = s_out[1][idx];
+            }
+        }
+    } else if (active) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if (g0 + l >= npx) break;
+            out[g0 + l] = o0[l];
+            out[npx + g0 + l] = o1[l];
+        }
     }
 }
 
@@ -1643,7 +1688,8 @@ ht_status ht_tc_conv(const ht_tc_layer &a, cudaStream_t s)
 ht_status ht_tc_first_input(const void *table, int n_imgs, int n_groups, uint64_t seed, cudaStream_t s)
 {
     ht_prof_start(HTK_FIRST_INPUT, s);
-    k_first_input<<<(n_groups + 255) / 256, 256, 0, s>>>((const ImgDesc *)table, n_imgs, seed);
+    if (n_groups <= 0) return HT_OK;
+    k_first_input<<<(n_groups + 255) / 256, 256, 0, s>>>((const ImgDesc *)table, n_imgs, n_groups, seed);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -1722,7 +1768,7 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
         const ImgDesc *dt = d_table + G.g0;
         const int ng = G.ng;
         ht_prof_start(HTK_FIRST_INPUT, s);
-        k_first_input<<<(G.pre + 255) / 256, 256, 0, s>>>(dt, ng, seed);
+        k_first_input<<<(G.pre + 255) / 256, 256, 0, s>>>(dt, ng, G.pre, seed);
         ht_prof_stop(s);
         HT_LAUNCH_CHECK();
         auto base = [&](ConvParams &P, int in_buf) {
