@@ -1008,10 +1008,14 @@ __global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__
     }
     uint4 *out = reinterpret_cast<uint4 *>(D->act[1]);
     if (one_image) {
+        // 16-byte slot idx is stored at idx ^ ((idx >> 3) & 3): for the writes (idx = 4t + l)
+        // eight consecutive threads then hit eight different slots modulo 8 (no bank
+        // conflict), and the reads (consecutive idx) stay a permutation within 64 bytes
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-            s_out[0][4 * t + l] = o0[l];
-            s_out[1][4 * t + l] = o1[l];
+            const int q = 4 * t + (l ^ ((t >> 1) & 3));
+            s_out[0][q] = o0[l];
+            s_out[1][q] = o1[l];
         }
         __syncthreads();
         const uint64_t gB = (uint64_t)(gb - __ldg(&imgs[imb].pre_begin)) * 4;   // the block's first pixel
@@ -1020,10 +1024,11 @@ __global__ void __launch_bounds__(256) k_first_input(const ImgDesc *__restrict__
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int idx = t + 256 * k;
+            const int q = idx ^ ((idx >> 3) & 3);
             const uint64_t g = gB + (uint64_t)idx;
             if (gb + idx / 4 < n_groups && g < npxb) {
-                outb[g] = s_out[0][idx];
-                outb[npxb + g] = s_out[1][idx];
+                outb[g] = s_out[0][q];
+                outb[npxb + g] = s_out[1][q];
             }
         }
     } else if (active) {
