@@ -59,8 +59,8 @@ struct Kahan {
     }
 };
 
-constexpr int WG_NSA = 6;                       // activation-row ring (+1 mirror slot)
-constexpr int WG_NSG = 3;                       // gradient-row ring
+constexpr int WG_NSA = 8;                       // activation-row ring (+1 mirror slot)
+constexpr int WG_NSG = 4;                       // gradient-row ring
 constexpr int WG_ASLOT = 8 * ROW_PX * 16;       // [chunk][130 px][16 B]
 constexpr int WG_GSLOT = 8 * TILE_M * 16;       // [chunk][128 px][16 B]
 constexpr int WG_NTHREADS = 192;                // producer, MMA issuer, 4 epilogue warps

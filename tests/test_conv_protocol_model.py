@@ -382,7 +382,7 @@ def test_stream_model_catches_protocol_faults(variant):
 # TMEM lanes that are never read back, so that read is not a dependence).  A gradient
 # slot is released by the MMA commit and by the four bias-sum warps (count 5).
 # ---------------------------------------------------------------------------
-WG_NSA, WG_NSG = 6, 3
+WG_NSA, WG_NSG = 8, 4
 
 
 class WgSim:
