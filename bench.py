@@ -433,6 +433,9 @@ def forward_record(workload, args, rank, world, local, full):
                          "figure applies)"}
     # HBM-bound passes around the conv stack: algorithmic bytes per pixel, achieved GB/s
     hbm_bytes = {"k_first_input": 4.0 + 32.0}            # contone read, three-part c / z split write
+    if netname != "resnet" and prec != N.HT_FP32:
+        # layer 1 building its input itself: contone read, 64-channel activation write
+        hbm_bytes["k_first_tc"] = 4.0 + (64.0 if prec == N.HT_FP8_E4M3 else 128.0)
     if head != N.HT_HEAD_SOFTMAX:
         hbm_bytes["k_head_tc"] = 36.0 + 0.25             # 9 partials read, packed levels written
     pk, _ = peaks()

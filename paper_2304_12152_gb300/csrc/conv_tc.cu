@@ -4,7 +4,9 @@
 // padding 1, ReLU between layers, sigmoid / softmax head.
 //
 //  k_first_input  per pixel, c and the noise channel z (Philox stream 0), each
-//                 as an exact sum of three bf16 parts, two 16-byte chunks.
+//                 as an exact sum of three bf16 parts, two 16-byte chunks (the
+//                 training step and the residual policy; the inference forms of
+//                 the 64-wide policy build these chunks inside layer 1).
 //  k_conv_tc      one pipeline, four kinds: layer 1 (2 -> 64, on the split
 //                 input), a hidden 64 -> 64 layer, the last hidden layer with
 //                 the 1-logit head's per-tap partials fused into its epilogue,
@@ -30,7 +32,8 @@
 //
 // Warp roles (320 threads, one persistent CTA per SM): warp 0 = copy producer
 // (and TMEM owner), warp 1 = MMA issuer, warps 2-9 = epilogue (two per TMEM
-// lane quarter).  Every mbarrier wait is bounded (globaltimer); on expiry the
+// lane quarter).  Layer 1 with its input built in the kernel: 480 threads, warps
+// 0 and 10-14 build the staged rows in place of the copy producer.  Every mbarrier wait is bounded (globaltimer); on expiry the
 // kernel records HT_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM
 // and returns.
 #include <stdlib.h>
@@ -153,9 +156,28 @@ __device__ __forceinline__ void head_partials9(const float *v, const ConvParams 
 // p .. 7 and 0 ..), so that each output row still accumulates in one block through one chain
 // of MMAs, in the same order as in the 8-row units: the two forms give identical bits.
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false, bool STREAM = false>
-__global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
+// Layer-1 input of one pixel: c and z each split exactly into three bf16 parts, laid out as
+// the K elements (c0, c0, c1, c0, c1, c2, z0, z0 | z1, z0, z1, z2, 0, 0, 0, 0), two 16-byte
+// chunks (the matching weights are described at k_first_input).
+__device__ __forceinline__ void first_input_pixel(float c, float z, uint4 &o0, uint4 &o1)
 {
+    float c0, c1, c2, z0, z1, z2;
+    split3_bf16(c, c0, c1, c2);
+    split3_bf16(z, z0, z1, z2);
+    o0 = make_uint4(pack_bf16x2(c0, c0), pack_bf16x2(c1, c0), pack_bf16x2(c1, c2), pack_bf16x2(z0, z0));
+    o1 = make_uint4(pack_bf16x2(z1, z0), pack_bf16x2(z1, z2), 0u, 0u);
+}
+
+// Layer 1 with its input built in the kernel (FUSED): warps 0 and 10 .. 14 take the
+// producer's place, one per input-ring slot.
+constexpr int NIN_WARPS = NSLOT;
+constexpr int NTHREADS_FUSED = NTHREADS + (NIN_WARPS - 1) * 32;
+static_assert(NTHREADS_FUSED <= 512, "block size of the layer-1 kernel");
+
+template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false, bool STREAM = false, bool FUSED = false>
+__global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS, 1) k_conv_tc(const ConvParams P)
+{
+    static_assert(!FUSED || (KIND == KIND_FIRST && !TR && CH == 64), "in-kernel input: inference layer 1 only");
     using C = Cfg<FP8, KIND, CH, F16>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -169,6 +191,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool input_warp = FUSED && (warp == 0 || warp >= 10);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NSLOT; ++i) {
@@ -190,7 +213,105 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv_tc(const ConvParams P)
     tc_fence_after();
     const uint32_t tmem_base = *s_tmem;
 
-    if (warp == 0) {
+    if (input_warp) {
+        if constexpr (FUSED) {
+        // -------------------- producer: layer-1 input built here --------------------
+        // NSLOT warps build the staged rows from the contone image and the noise channel,
+        // warp w the rows of ring slot w, so that up to NSLOT rows are in flight: per pixel
+        // the two 16-byte chunks of the layer-1 input (first_input_pixel, the values
+        // k_first_input stores), zero outside the image.  z is Philox4x32-10 of
+        // (g / 4, image, 0, 0), g = y * W + x, lane g % 4: the row's calls (at most 34
+        // groups of 4 pixels) are made once, two per lane at most, and shared through the
+        // warp's part of shared memory.  The contone values of the warp's next row in the
+        // same unit are loaded while it builds this one.
+        const int wi = warp == 0 ? 0 : warp - 9;                     // 0 .. NSLOT - 1 = ring slot
+        uint4 *s_u = (uint4 *)(((uintptr_t)(s_abort + 1) + 15) & ~(uintptr_t)15) + wi * 36;
+        if (warp == 0 && lane == 0) {
+            mbar_arrive_expect_tx(smem_u32(wbar), C::W_BYTES);
+            bulk_g2s(smem_u32(s_w), P.wpack, C::W_BYTES, smem_u32(wbar));
+        }
+        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+        uint32_t li = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < P.n_units && ok; u += gridDim.x) {
+            const UnitInfo ui = unit_info(P.imgs, P.n_imgs, P.in_buf, u, P.ru, P.order);
+            const float *__restrict__ contone = ui.D->contone;
+            const int cpitch = ui.D->cpitch;
+            const uint32_t image = ui.D->image;
+            const int H = ui.H, W = ui.W, x0 = ui.x0, y0 = ui.y0, nrows = ui.nrows;
+            const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, W);       // in-image pixel range
+            float cn[5];                                       // contone, pixels x0 - 1 + lane + 32 q
+            auto load_row = [&](int yy) {
+                const bool in = yy >= 0 && yy < H;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    const int x = x0 - 1 + lane + 32 * q;
+                    cn[q] = (in && x >= lo && x < hi) ? __ldg(contone + (size_t)yy * cpitch + x) : 0.f;
+                }
+            };
+            // first row of this unit that is the warp's
+            int r = (int)((uint32_t)(wi - (int)(li % NSLOT) + NSLOT) % NSLOT);
+            if (r < nrows + 2) load_row(y0 - 1 + r);
+            for (; r < nrows + 2; r += NSLOT) {
+                const uint32_t lr = li + (uint32_t)r;             // this row's index in the CTA's ring sequence
+                const int yy = y0 - 1 + r;
+                const bool row_in = (yy >= 0 && yy < H) && hi > lo;
+                float cv[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) cv[q] = cn[q];
+                if (r + NSLOT < nrows + 2) load_row(yy + NSLOT);
+                const uint64_t G0 = row_in ? ((uint64_t)yy * (uint64_t)W + (uint64_t)lo) >> 2 : 0;
+                if (row_in) {
+                    const uint32_t ng = (uint32_t)((((uint64_t)yy * (uint64_t)W + (uint64_t)(hi - 1)) >> 2) - G0) + 1u;
+                    for (uint32_t t = (uint32_t)lane; t < ng; t += 32)
+                        s_u[t] = ht_philox4x32_10(make_uint4((uint32_t)(G0 + t), image, 0u, 0u), key);
+                }
+                int got = 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&empty[wi]), ((lr / NSLOT) & 1u) ^ 1u, s_abort, P.err) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, got, 0)) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                uint8_t *dst = s_rows + wi * C::SLOT_BYTES;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    const int i = lane + 32 * q;               // pixel x0 - 1 + i of the staged row
+                    if (i < ROW_PX) {
+                        const int x = x0 - 1 + i;
+                        uint4 o0 = make_uint4(0, 0, 0, 0), o1 = make_uint4(0, 0, 0, 0);
+                        if (row_in && x >= lo && x < hi) {
+                            const uint64_t g = (uint64_t)yy * (uint64_t)W + (uint64_t)x;
+                            const uint4 rr = s_u[(g >> 2) - G0];
+                            const uint32_t l = (uint32_t)g & 3u;
+                            const uint32_t w = l == 0 ? rr.x : l == 1 ? rr.y : l == 2 ? rr.z : rr.w;
+                            first_input_pixel(cv[q], (float)(w >> 8) * (1.0f / 16777216.0f), o0, o1);
+                        }
+                        *reinterpret_cast<uint4 *>(dst + (size_t)i * 16) = o0;
+                        *reinterpret_cast<uint4 *>(dst + ((size_t)ROW_PX + i) * 16) = o1;
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    s_meta[wi] = make_int2(r, nrows);
+                    mbar_arrive(smem_u32(&full[wi]));
+                }
+                __syncwarp();                                  // s_u is rewritten for the warp's next row
+            }
+            li += (uint32_t)nrows + 2u;
+        }
+        if (ok && (int)(li % NSLOT) == wi) {
+            // end marker (from the warp of the next row's slot): the MMA warp stops at k = -1
+            if (lane == 0 && mbar_wait(smem_u32(&empty[wi]), ((li / NSLOT) & 1u) ^ 1u, s_abort, P.err)) {
+                s_meta[wi] = make_int2(-1, 0);
+                mbar_arrive(smem_u32(&full[wi]));
+            }
+        }
+        // the weight copy must have landed before the CTA exits
+        if (warp == 0 && lane == 0) mbar_wait(smem_u32(wbar), 0, s_abort, P.err, true);
+        }
+    } else if (warp == 0) {
         // ------------------------- producer -------------------------
         // One input row = NCHUNK contiguous runs of ROW_PX * 16 bytes in HBM (one
         // per channel chunk).  In-image pixels arrive by bulk async copies
@@ -959,15 +1080,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1) k_conv_
 // layer-1 sums carry float32-level error, as a float32 convolution would.
 // z comes from Philox4x32-10 with one call per aligned group of 4 indices g.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void first_input_pixel(float c, float z, uint4 &o0, uint4 &o1)
-{
-    float c0, c1, c2, z0, z1, z2;
-    split3_bf16(c, c0, c1, c2);
-    split3_bf16(z, z0, z1, z2);
-    o0 = make_uint4(pack_bf16x2(c0, c0), pack_bf16x2(c1, c0), pack_bf16x2(c1, c2), pack_bf16x2(z0, z0));
-    o1 = make_uint4(pack_bf16x2(z1, z0), pack_bf16x2(z1, z2), 0u, 0u);
-}
-
 // A block covers 256 groups (1 024 pixels).  Where they all belong to one image, the
 // outputs are staged in shared memory and written back with consecutive threads on
 // consecutive pixels; a block that straddles two images writes pixel by pixel.
@@ -1185,12 +1297,12 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_partials(const ImgDesc *__r
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false, bool STREAM = false>
+template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false, bool STREAM = false, bool FUSED = false>
 ht_status ensure_attr()
 {
     static bool attr_set = false;
     if (!attr_set) {
-        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND, TR, CH, F16, STREAM>,
+        HT_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<FP8, KIND, TR, CH, F16, STREAM, FUSED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FP8, KIND, CH, F16>::SMEM));
         attr_set = true;
     }
@@ -1263,18 +1375,26 @@ ht_status ensure_all_attrs()
         (st = ensure_attr<false, KIND_HEADPART, false, 64, true, true>()) != HT_OK ||
         (st = ensure_attr<false, KIND_HEAD4, false, 64, true, true>()) != HT_OK)
         return st;
+    if ((st = ensure_attr<false, KIND_FIRST, false, 64, false, false, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_FIRST, false, 64, false, true, true>()) != HT_OK ||
+        (st = ensure_attr<true, KIND_FIRST, false, 64, false, false, true>()) != HT_OK ||
+        (st = ensure_attr<true, KIND_FIRST, false, 64, false, true, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_FIRST, false, 64, true, false, true>()) != HT_OK ||
+        (st = ensure_attr<false, KIND_FIRST, false, 64, true, true, true>()) != HT_OK)
+        return st;
     return HT_OK;
 }
 
-template <bool FP8, int KIND, bool TR, int CH, bool F16, bool STREAM>
+template <bool FP8, int KIND, bool TR, int CH, bool F16, bool STREAM, bool FUSED = false>
 ht_status launch_conv_k(const ConvParams &P, cudaStream_t s)
 {
-    const ht_status st = ensure_attr<FP8, KIND, TR, CH, F16, STREAM>();
+    const ht_status st = ensure_attr<FP8, KIND, TR, CH, F16, STREAM, FUSED>();
     if (st != HT_OK) return st;
     const int grid = P.n_units < num_sms() ? P.n_units : num_sms();
     ht_prof_start(KIND == KIND_FIRST ? HTK_FIRST_TC : KIND == KIND_HEAD4 ? HTK_HEAD_TC
                   : FP8 ? HTK_CONV_TC_FP8 : F16 ? HTK_CONV_TC_FP16 : HTK_CONV_TC_BF16, s);
-    k_conv_tc<FP8, KIND, TR, CH, F16, STREAM><<<grid, NTHREADS, Cfg<FP8, KIND, CH, F16>::SMEM, s>>>(P);
+    k_conv_tc<FP8, KIND, TR, CH, F16, STREAM, FUSED>
+        <<<grid, FUSED ? NTHREADS_FUSED : NTHREADS, Cfg<FP8, KIND, CH, F16>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;
@@ -1291,6 +1411,15 @@ ht_status launch_conv(const ConvParams &P, cudaStream_t s)
         return HT_ERR_INVALID_ARG;
     }
     return launch_conv_k<FP8, KIND, TR, CH, F16, false>(P, s);
+}
+
+// Layer 1 of the inference forms with its input built in the kernel (no input pass).
+template <bool FP8, bool F16>
+ht_status launch_first_fused(const ConvParams &P, cudaStream_t s)
+{
+    if (P.ru < 1) return HT_ERR_INVALID_ARG;
+    if (P.ru > RU) return launch_conv_k<FP8, KIND_FIRST, false, 64, F16, true, true>(P, s);
+    return launch_conv_k<FP8, KIND_FIRST, false, 64, F16, false, true>(P, s);
 }
 
 // CTA-pair form: P.n_units counts 256-pixel units (ImgDesc::unit2_begin), P.wpack
@@ -1648,6 +1777,12 @@ void ht_preload_conv_tc()
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HIDDEN, false, 64, true, true>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEADPART, false, 64, true, true>);
     cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_HEAD4, false, 64, true, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, false, 64, false, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, false, 64, false, true, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_FIRST, false, 64, false, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<true, KIND_FIRST, false, 64, false, true, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, false, 64, true, false, true>);
+    cudaFuncGetAttributes(&fa, k_conv_tc<false, KIND_FIRST, false, 64, true, true, true>);
     cudaFuncGetAttributes(&fa, k_conv_tc2<false, KIND_HIDDEN>);
     cudaFuncGetAttributes(&fa, k_conv_tc2<false, KIND_HEADPART>);
     cudaFuncGetAttributes(&fa, k_conv_tc2<true, KIND_HIDDEN>);
@@ -1772,10 +1907,12 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
     for (const TcGroup &G : groups) {
         const ImgDesc *dt = d_table + G.g0;
         const int ng = G.ng;
-        ht_prof_start(HTK_FIRST_INPUT, s);
-        k_first_input<<<(G.pre + 255) / 256, 256, 0, s>>>(dt, ng, G.pre, seed);
-        ht_prof_stop(s);
-        HT_LAUNCH_CHECK();
+        if (p->arch == HT_ARCH_RESNET) {           // the 64-wide layer 1 builds its input itself
+            ht_prof_start(HTK_FIRST_INPUT, s);
+            k_first_input<<<(G.pre + 255) / 256, 256, 0, s>>>(dt, ng, G.pre, seed);
+            ht_prof_stop(s);
+            HT_LAUNCH_CHECK();
+        }
         auto base = [&](ConvParams &P, int in_buf) {
             P.imgs = dt;
             P.n_imgs = ng;
@@ -1790,7 +1927,7 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
         {
             const bool o8 = fp8 && n_inner > 0;
             ConvParams P{};
-            base(P, 1);                            // reads the split input in act[1], writes act[0]
+            base(P, 1);                            // writes act[0] (the residual form reads the split input in act[1])
             P.wpack = p->d_w1pack;
             for (int c = 0; c < 64; ++c) {
                 P.bias[c] = p->h_b[p->b_off[0] + c];
@@ -1799,9 +1936,9 @@ ht_status tc_launch_groups(ht_policy *p, const ImgDesc *d_table, const std::vect
             P.out_inv_scale = o8 ? 1.f / p->act_scale[1] : 1.f;
             P.out_fp8 = o8 ? 1 : 0;
             const ht_status st = p->arch == HT_ARCH_RESNET ? launch_conv<false, KIND_FIRST, false, 32>(P, s)
-                                 : fp8                      ? launch_conv<true, KIND_FIRST>(P, s)
-                                 : f16                      ? launch_conv<false, KIND_FIRST, false, 64, true>(P, s)
-                                                            : launch_conv<false, KIND_FIRST>(P, s);
+                                 : fp8                      ? launch_first_fused<true, false>(P, s)
+                                 : f16                      ? launch_first_fused<false, true>(P, s)
+                                                            : launch_first_fused<false, false>(P, s);
             if (st != HT_OK) return st;
         }
         if (p->arch == HT_ARCH_RESNET) {
