@@ -434,8 +434,9 @@ struct HeadBwdParams {
 };
 
 // Persistent: block b handles tiles b, b + grid, ...; its weight-gradient sums stay
-// in registers across tiles and are written once.
-__global__ void __launch_bounds__(HT_X *HT_Y) k_head_bwd(const HeadBwdParams P)
+// in registers across tiles and are written once.  The data gradient is formed and
+// stored 8 channels (one 16-byte chunk) at a time, so that four blocks fit on an SM.
+__global__ void __launch_bounds__(HT_X *HT_Y, 4) k_head_bwd(const HeadBwdParams P)
 {
     __shared__ float s_dz[HT_Y + 2][HT_X + 2];
     __shared__ __align__(16) __nv_bfloat16 s_a[(HT_Y + 2) * (HT_X + 2) * 64];
@@ -472,15 +473,25 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_head_bwd(const HeadBwdParams P)
 #pragma unroll
             for (int t = 0; t < 9; ++t) d[t] = s_dz[threadIdx.y + 2 - t / 3][threadIdx.x + 2 - t % 3];
             const uint2 m = D->mask[(size_t)y * W + x];
-            float g[64];
+            uint8_t *o = D->act[1];
 #pragma unroll
-            for (int c = 0; c < 64; ++c) {
-                float acc = 0.f;
+            for (int ch = 0; ch < 8; ++ch) {
+                float g[8];
 #pragma unroll
-                for (int t = 0; t < 9; ++t) acc = fmaf(P.w[t * 64 + c], d[t], acc);
-                g[c] = (((c < 32 ? m.x : m.y) >> (c & 31)) & 1u) ? acc : 0.f;
+                for (int e = 0; e < 8; ++e) {
+                    const int c = 8 * ch + e;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) acc = fmaf(P.w[t * 64 + c], d[t], acc);
+                    g[e] = (((c < 32 ? m.x : m.y) >> (c & 31)) & 1u) ? acc : 0.f;
+                }
+                uint4 q;
+                q.x = pack_bf16x2(g[0], g[1]);
+                q.y = pack_bf16x2(g[2], g[3]);
+                q.z = pack_bf16x2(g[4], g[5]);
+                q.w = pack_bf16x2(g[6], g[7]);
+                *reinterpret_cast<uint4 *>(o + (((size_t)ch * H + y) * W + x) * 16) = q;
             }
-            store_pixel(g, D->act[1], 0, 1.f, H, W, y, x);
         }
         // weight and bias gradient sums of this tile: thread (c, dy) keeps the three dx
         // taps and slides along the row (one activation load per pixel); thread 192 sums dz
@@ -556,14 +567,32 @@ __global__ void __launch_bounds__(HT_X *HT_Y) k_first_wgrad(const ImgDesc *__res
             *reinterpret_cast<uint4 *>(&s_g[(size_t)p * 64 + chunk * 8]) = q;
         }
         __syncthreads();
-        for (int py = half * (HT_Y / 2); py < (half + 1) * (HT_Y / 2); ++py)
+        for (int py = half * (HT_Y / 2); py < (half + 1) * (HT_Y / 2); ++py) {
+            // the 3 x 3 input window slides along the row: one new column per pixel
+            const float *r0 = &s_x[ci][py][0], *r1 = &s_x[ci][py + 1][0], *r2 = &s_x[ci][py + 2][0];
+            float a00 = r0[0], a01 = r0[1], a10 = r1[0], a11 = r1[1], a20 = r2[0], a21 = r2[1];
 #pragma unroll 4
             for (int px = 0; px < HT_X; ++px) {
                 const float g = __bfloat162float(s_g[(py * HT_X + px) * 64 + n]);
                 bacc += g;
-#pragma unroll
-                for (int t = 0; t < 9; ++t) wacc[t] = fmaf(g, s_x[ci][py + t / 3][px + t % 3], wacc[t]);
+                const float a02 = r0[px + 2], a12 = r1[px + 2], a22 = r2[px + 2];
+                wacc[0] = fmaf(g, a00, wacc[0]);
+                wacc[1] = fmaf(g, a01, wacc[1]);
+                wacc[2] = fmaf(g, a02, wacc[2]);
+                wacc[3] = fmaf(g, a10, wacc[3]);
+                wacc[4] = fmaf(g, a11, wacc[4]);
+                wacc[5] = fmaf(g, a12, wacc[5]);
+                wacc[6] = fmaf(g, a20, wacc[6]);
+                wacc[7] = fmaf(g, a21, wacc[7]);
+                wacc[8] = fmaf(g, a22, wacc[8]);
+                a00 = a01;
+                a01 = a02;
+                a10 = a11;
+                a11 = a12;
+                a20 = a21;
+                a21 = a22;
             }
+        }
     }
     // combine the two row halves in a fixed order
     __syncthreads();
@@ -851,6 +880,12 @@ ht_status ht_train_tc_backward(ht_policy *p, ht_train_tc_ws &w, int nimg, uint64
         P.n_tiles = w.hd;
         memcpy(P.w, p->h_headw, sizeof(P.w));
         P.partials = wpart;
+        static bool carveout_set = false;           // 4 blocks x 45 KB of shared memory per SM
+        if (!carveout_set) {
+            HT_CUDA_TRY(cudaFuncSetAttribute(k_head_bwd, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared));
+            carveout_set = true;
+        }
         ht_prof_start(HTK_TRAIN, s);
         k_head_bwd<<<nbg, dim3(HT_X, HT_Y), 0, s>>>(P);
         ht_prof_stop(s);
