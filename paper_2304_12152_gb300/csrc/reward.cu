@@ -413,7 +413,10 @@ __global__ void __launch_bounds__(DTX *DTY, 3) k_toggle_delta_r(const __grid_con
                                                                  const __grid_constant__ Win2<R> w2)
 {
     constexpr int SH = DTY + 2 * R, SW = DTX + 2 * R, K = 2 * R + 1;
-    __shared__ float s_m[NMAP][SH][SW];
+    // the seven maps interleaved as two float4 per position, (e, mu_h, mu_c, var_c + C2) and
+    // (cov, sigma, ss, mu_c^2 + C1): two 16-byte loads per window term, consecutive threads
+    // 16 bytes apart (no bank conflicts)
+    __shared__ float4 s_p[SH][SW], s_q[SH][SW];
     const RwImg &I = B.im[blockIdx.z];
     const float *__restrict__ c = I.c;
     const float *__restrict__ maps = I.maps;
@@ -429,7 +432,13 @@ __global__ void __launch_bounds__(DTX *DTY, 3) k_toggle_delta_r(const __grid_con
         const int jy = ay0 - R + yy, jx = ax0 - R + xx;        // image coords of output j
         float v = q == 3 ? 1.f : 0.f;
         if (jy >= R && jy < H - R && jx >= R && jx < W - R) v = __ldg(maps + q * plane + (size_t)(jy - R) * VW + (jx - R));
-        s_m[q][yy][xx] = v;
+        float *dst = q < 4 ? &s_p[yy][xx].x + q : &s_q[yy][xx].x + (q - 4);
+        *dst = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < SH * SW; i += DTX * DTY) {
+        const float muc = s_p[i / SW][i % SW].z;
+        s_q[i / SW][i % SW].w = fmaf(muc, muc, wn.c1);
     }
     __syncthreads();
     const int ay = ay0 + threadIdx.y, ax = ax0 + threadIdx.x;
@@ -444,21 +453,21 @@ __global__ void __launch_bounds__(DTX *DTY, 3) k_toggle_delta_r(const __grid_con
         if (ax + d >= R && ax + d < W - R) sx += gd;
     }
     float ge = 0.f, acc = 0.f;
-#pragma unroll
+#pragma unroll 1
     for (int dy = 0; dy < K; ++dy) {
 #pragma unroll
         for (int dx = 0; dx < K; ++dx) {
             const int sy_ = threadIdx.y + dy, sx_ = threadIdx.x + dx;
-            const float e = s_m[0][sy_][sx_], muh = s_m[1][sy_][sx_], muc = s_m[2][sy_][sx_];
-            const float varc2 = s_m[3][sy_][sx_], cov = s_m[4][sy_][sx_], sig = s_m[5][sy_][sx_];
-            const float ss = s_m[6][sy_][sx_];
+            const float4 mp = s_p[sy_][sx_], mq = s_q[sy_][sx_];
+            const float e = mp.x, muh = mp.y, muc = mp.z, varc2 = mp.w;
+            const float cov = mq.x, sig = mq.y, ss = mq.z, muc2c1 = mq.w;
             ge = fmaf(w2.g2[dy * K + dx], e, ge);
             const float dw = delta * w2.w2[dy * K + dx];
             const float muh2 = muh + dw;
             const float varh2 = fmaf(-muh2, muh2, muh2);
             const float cov2 = fmaf(dw, ca - muc, cov);
             const float num = fmaf(2.f * muh2, muc, wn.c1) * fmaf(2.f, cov2, wn.c2);
-            const float den = fmaf(muh2, muh2, fmaf(muc, muc, wn.c1)) * (varh2 + varc2);
+            const float den = fmaf(muh2, muh2, muc2c1) * (varh2 + varc2);
             // the denominator lies in [C1 C2, ~5]: the fast division (2 ulp) is exact enough
             acc = fmaf(sig, __fdividef(num, den) - ss, acc);
         }
