@@ -371,7 +371,7 @@ def forward_record(workload, args, rank, world, local, full):
             pol.set_schedule(ru, order, pair)
             tune = {"choice": {"rows_per_unit": ru, "unit_order": order, "cta_pair": pair}, "candidates": None}
         else:
-            res = pol.autotune(cs, bits, mode, seed, reps=2)
+            res = pol.autotune(cs, bits, mode, seed, reps=3)
             best = min(res, key=lambda r: r[3])
             tune = {"choice": {"rows_per_unit": best[0], "unit_order": best[1], "cta_pair": best[2]},
                     "candidates": [{"rows_per_unit": r, "unit_order": o, "cta_pair": pr, "ms": ms}

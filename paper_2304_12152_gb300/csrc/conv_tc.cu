@@ -1712,12 +1712,28 @@ size_t ht_tc_ws_bytes(const ht_policy *p, int h, int w)
 }
 
 namespace {
+// Activation workspace of one group of images: HT_WS_BUDGET_GB if set, else a quarter of
+// the device's memory (at least 16 GB), so that large uneven batches run as one group of
+// persistent launches instead of several, each with its own partial last wave.
 size_t ws_budget()
 {
     static size_t b = 0;
     if (!b) {
         const char *e = getenv("HT_WS_BUDGET_GB");
-        const double gb = e ? atof(e) : 16.0;
+        double gb = 16.0;
+        if (e) {
+            gb = atof(e);
+        } else {
+            int dev = 0;
+            size_t total = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess) {
+                cudaDeviceProp prop;
+                if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) total = prop.totalGlobalMem;
+            }
+            cudaGetLastError();
+            const double quarter = (double)total / 4.0 / 1073741824.0;
+            gb = quarter > gb ? quarter : gb;
+        }
         b = (size_t)((gb > 0.5 ? gb : 0.5) * 1073741824.0);
     }
     return b;
