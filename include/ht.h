@@ -18,7 +18,10 @@
  *   - Pointers documented "device" must point into memory of the current CUDA
  *     device; "host" pointers are read before the call returns.  The caller
  *     owns every buffer it passes; the library owns ht_policy / ht_train
- *     objects and the device workspaces inside them.
+ *     objects and the device workspaces inside them.  A tensor-core call
+ *     splits its images into groups whose activations (256 bytes per pixel)
+ *     fit the workspace budget: the environment variable HT_WS_BUDGET_GB if
+ *     set, else a quarter of the device's memory (at least 16 GB).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls are asynchronous on that stream unless stated; argument
  *     errors are detected on the host before any launch and return
