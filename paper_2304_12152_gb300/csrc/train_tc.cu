@@ -158,21 +158,18 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
                     }
                     if (zeroed) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
+                    const uint32_t run = (uint32_t)(hi - lo) * 16u;
                     if (lane == 0) {
                         a_meta[slot] = make_int2(r, ui.nrows);
-                        const uint32_t run = (uint32_t)(hi - lo) * 16u;
-                        if (row_in && hi > lo) {
-                            mbar_arrive_expect_tx(smem_u32(&a_full[slot]), run * 8u * (uint32_t)ncopy);
-                            for (int cp = 0; cp < ncopy; ++cp) {
-                                uint8_t *dst = s_a + (cp ? WG_NSA : slot) * WG_ASLOT;
-                                for (int c = 0; c < 8; ++c)
-                                    bulk_g2s(smem_u32(dst + ((size_t)c * ROW_PX + (lo - (x0 - 1))) * 16),
-                                             ui.in + (((size_t)c * ui.H + yy) * ui.W + lo) * 16, run,
-                                             smem_u32(&a_full[slot]));
-                            }
-                        } else {
-                            mbar_arrive(smem_u32(&a_full[slot]));
-                        }
+                        if (row_in && hi > lo) mbar_arrive_expect_tx(smem_u32(&a_full[slot]), run * 8u * (uint32_t)ncopy);
+                        else mbar_arrive(smem_u32(&a_full[slot]));
+                    }
+                    __syncwarp();
+                    if (row_in && hi > lo && lane < 8 * ncopy) {     // one bulk copy per (copy, chunk)
+                        const int cp = lane >> 3, c = lane & 7;
+                        uint8_t *dst = s_a + (cp ? WG_NSA : slot) * WG_ASLOT;
+                        bulk_g2s(smem_u32(dst + ((size_t)c * ROW_PX + (lo - (x0 - 1))) * 16),
+                                 ui.in + (((size_t)c * ui.H + yy) * ui.W + lo) * 16, run, smem_u32(&a_full[slot]));
                     }
                     a_last[slot] = (int)la;
                     ++la;
@@ -199,15 +196,15 @@ __global__ void __launch_bounds__(WG_NTHREADS, 1) k_wgrad_tc(const WgParams P)
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     }
                     __syncwarp();
+                    const uint32_t run = (uint32_t)nin * 16u;
                     if (lane == 0) {
                         g_meta[slot] = make_int2(r - 2, ui.nrows);
-                        const uint32_t run = (uint32_t)nin * 16u;
                         mbar_arrive_expect_tx(smem_u32(&g_full[slot]), run * 8u);
-                        const uint8_t *g = ui.out;
-                        for (int c = 0; c < 8; ++c)
-                            bulk_g2s(smem_u32(dst + (size_t)c * TILE_M * 16), g + (((size_t)c * ui.H + yy) * ui.W + x0) * 16,
-                                     run, smem_u32(&g_full[slot]));
                     }
+                    __syncwarp();
+                    if (lane < 8)                                    // one bulk copy per chunk
+                        bulk_g2s(smem_u32(dst + (size_t)lane * TILE_M * 16),
+                                 ui.out + (((size_t)lane * ui.H + yy) * ui.W + x0) * 16, run, smem_u32(&g_full[slot]));
                     g_last[slot] = (int)lg;
                     ++lg;
                 }
