@@ -358,18 +358,16 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS, 1) k_conv_t
                 }
                 if (zeroed) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
+                const uint32_t run = (uint32_t)(hi - lo) * 16u;
                 if (lane == 0) {
                     s_meta[slot] = make_int2(r, y1 - y0);
-                    const uint32_t run = (uint32_t)(hi - lo) * 16u;
-                    if (row_in && hi > lo) {
-                        mbar_arrive_expect_tx(smem_u32(&full[slot]), run * C::NCOPY);
-                        for (int c = 0; c < C::NCOPY; ++c)
-                            bulk_g2s(smem_u32(dst + ((size_t)c * ROW_PX + (lo - (x0 - 1))) * 16),
-                                     ui.in + (((size_t)c * ui.H + yy) * ui.W + lo) * 16, run, smem_u32(&full[slot]));
-                    } else {
-                        mbar_arrive(smem_u32(&full[slot]));
-                    }
+                    if (row_in && hi > lo) mbar_arrive_expect_tx(smem_u32(&full[slot]), run * C::NCOPY);
+                    else mbar_arrive(smem_u32(&full[slot]));
                 }
+                __syncwarp();
+                if (row_in && hi > lo && lane < C::NCOPY)        // one bulk copy per chunk, issued together
+                    bulk_g2s(smem_u32(dst + ((size_t)lane * ROW_PX + (lo - (x0 - 1))) * 16),
+                             ui.in + (((size_t)lane * ui.H + yy) * ui.W + lo) * 16, run, smem_u32(&full[slot]));
                 last_issued[slot] = (int)li;
             }
         }
