@@ -30,12 +30,13 @@
 // 8-pixel core matrix), chunks ROW_PX * 16 B apart (LBO).  A one-pixel shift of
 // the A operand is a 16-byte shift of the descriptor start address.
 //
-// Warp roles (320 threads, one persistent CTA per SM): warp 0 = copy producer
+// Warp roles (one persistent CTA per SM): warp 0 = copy producer
 // (and TMEM owner), warp 1 = MMA issuer, warps 2-9 = epilogue (two per TMEM
-// lane quarter).  Layer 1 with its input built in the kernel: 480 threads, warps
-// 0 and 10-14 build the staged rows in place of the copy producer.  Every mbarrier wait is bounded (globaltimer); on expiry the
-// kernel records HT_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM
-// and returns.
+// lane quarter), warp 10 = a second copy producer (the two take the staged rows in
+// turn): 352 threads.  Layer 1 with its input built in the kernel: 480 threads,
+// warps 0 and 10-14 build the staged rows in place of the copy producers.
+// Every mbarrier wait is bounded (globaltimer); on expiry the kernel records
+// HT_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM and returns.
 #include <stdlib.h>
 
 #include <vector>
@@ -49,6 +50,7 @@ namespace {
 #endif
 constexpr int NSLOT = HT_CONV_NSLOT;       // input-row ring depth (lookahead of the copy engine)
 constexpr int NTHREADS = 320;              // producer, MMA issuer, 8 epilogue warps
+constexpr int PROD2_WARP = 10;             // k_conv_tc: second copy producer
 
 // Kernel kinds built from one pipeline: a hidden 64 -> 64 layer, the last
 // hidden layer with the 1-logit head's per-tap partials fused into its
@@ -173,9 +175,11 @@ __device__ __forceinline__ void first_input_pixel(float c, float z, uint4 &o0, u
 constexpr int NIN_WARPS = NSLOT;
 constexpr int NTHREADS_FUSED = NTHREADS + (NIN_WARPS - 1) * 32;
 static_assert(NTHREADS_FUSED <= 512, "block size of the layer-1 kernel");
+constexpr int NTHREADS_CONV = NTHREADS + 32;           // k_conv_tc: + a second copy producer
+static_assert(NSLOT % 2 == 0, "the two copy producers own alternate ring slots");
 
 template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false, bool STREAM = false, bool FUSED = false>
-__global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS, 1) k_conv_tc(const ConvParams P)
+__global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_conv_tc(const ConvParams P)
 {
     static_assert(!FUSED || (KIND == KIND_FIRST && !TR && CH == 64), "in-kernel input: inference layer 1 only");
     using C = Cfg<FP8, KIND, CH, F16>;
@@ -311,16 +315,20 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS, 1) k_conv_t
         // the weight copy must have landed before the CTA exits
         if (warp == 0 && lane == 0) mbar_wait(smem_u32(wbar), 0, s_abort, P.err, true);
         }
-    } else if (warp == 0) {
-        // ------------------------- producer -------------------------
+    } else if (warp == 0 || warp == PROD2_WARP) {
+        // ------------------------- producers -------------------------
         // One input row = NCHUNK contiguous runs of ROW_PX * 16 bytes in HBM (one
-        // per channel chunk).  In-image pixels arrive by bulk async copies
-        // (complete_tx on the slot's barrier); halo pixels outside the image are
-        // zero-filled by the warp with shared stores, made visible to the
-        // tensor core's async proxy by a proxy fence before the barrier arrive.
+        // per channel chunk).  Two warps take the CTA's ring rows in turn, warp 0 the
+        // even ones and PROD2_WARP the odd ones (NSLOT is even, so each slot always has
+        // the same producer): one warp's wait and bookkeeping for a row then overlap the
+        // other's copies, which a single warp left the copy engine idle through.  In-image
+        // pixels arrive by bulk async copies (complete_tx on the slot's barrier); halo
+        // pixels outside the image are zero-filled by the warp with shared stores, made
+        // visible to the tensor core's async proxy by a proxy fence before the arrive.
+        const uint32_t turn = warp == 0 ? 0u : 1u;
         int last_issued[NSLOT];
         for (int i = 0; i < NSLOT; ++i) last_issued[i] = -1;
-        if (lane == 0) {
+        if (warp == 0 && lane == 0) {
             mbar_arrive_expect_tx(smem_u32(wbar), C::W_BYTES);
             bulk_g2s(smem_u32(s_w), P.wpack, C::W_BYTES, smem_u32(wbar));
         }
@@ -331,6 +339,7 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS, 1) k_conv_t
             const int y0 = ui.y0, y1 = ui.y0 + ui.nrows, x0 = ui.x0;
             const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, ui.W);   // in-image pixel range
             for (int r = 0; r < (y1 - y0) + 2; ++r, ++li) {
+                if ((li & 1u) != turn) continue;               // the other producer's row
                 const int slot = (int)(li % NSLOT);
                 const uint32_t ph = (li / NSLOT) & 1u;
                 int got = 0;
@@ -371,8 +380,8 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS, 1) k_conv_t
                 last_issued[slot] = (int)li;
             }
         }
-        if (ok) {
-            // end marker: the MMA warp stops at a row with k = -1
+        if (ok && (li & 1u) == turn) {
+            // end marker (from the warp whose turn it is): the MMA warp stops at a row with k = -1
             const int slot = (int)(li % NSLOT);
             int got = 0;
             if (lane == 0) got = mbar_wait(smem_u32(&empty[slot]), ((li / NSLOT) & 1u) ^ 1u, s_abort, P.err) ? 1 : 0;
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS, 1) k_conv_t
             for (int s2 = 0; s2 < NSLOT; ++s2)
                 if (last_issued[s2] >= 0)
                     mbar_wait(smem_u32(&full[s2]), ((uint32_t)last_issued[s2] / NSLOT) & 1u, s_abort, P.err, true);
-            mbar_wait(smem_u32(wbar), 0, s_abort, P.err, true);
+            if (warp == 0) mbar_wait(smem_u32(wbar), 0, s_abort, P.err, true);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -1392,7 +1401,7 @@ ht_status launch_conv_k(const ConvParams &P, cudaStream_t s)
     ht_prof_start(KIND == KIND_FIRST ? HTK_FIRST_TC : KIND == KIND_HEAD4 ? HTK_HEAD_TC
                   : FP8 ? HTK_CONV_TC_FP8 : F16 ? HTK_CONV_TC_FP16 : HTK_CONV_TC_BF16, s);
     k_conv_tc<FP8, KIND, TR, CH, F16, STREAM, FUSED>
-        <<<grid, FUSED ? NTHREADS_FUSED : NTHREADS, Cfg<FP8, KIND, CH, F16>::SMEM, s>>>(P);
+        <<<grid, FUSED ? NTHREADS_FUSED : NTHREADS_CONV, Cfg<FP8, KIND, CH, F16>::SMEM, s>>>(P);
     ht_prof_stop(s);
     HT_LAUNCH_CHECK();
     return HT_OK;

@@ -2,9 +2,11 @@
 interleavings.  compute-sanitizer is closed on the GPU pool, so the pipeline's ordering
 argument is checked here instead, on a faithful model of its synchronisation:
 
-* a producer that stages each unit's nrows + 2 input rows in a ring of NSLOT slots
-  (wait `empty`, write the row record, copies landing asynchronously on `full`), then an
-  end-of-work marker, then a drain that waits for its own newest copy in every slot;
+* one or two producer warps that stage each unit's nrows + 2 input rows in a ring of NSLOT
+  slots, the two warps taking the ring rows in turn (NSLOT is even, so a slot always has
+  the same producer): wait `empty`, write the row record, copies landing asynchronously on
+  `full`; then the end-of-work marker (from the warp whose turn it is), then a drain that
+  waits for the warp's own newest copy in each of its slots;
 * the MMA issuer: waits `full` for each row, reads the record at a unit's start, waits the
   accumulator-release barrier `bfree[k]` before block k's first MMA, queues the row's MMAs
   and commits (`empty` for the slot, `bfull[k - 2]` for the completed block), and gives the
@@ -59,8 +61,8 @@ def wait(bar, phase):
 class Sim:
     """One CTA's conv pipeline over a list of units (output rows per unit), scheduled at random."""
 
-    def __init__(self, units, ru, rng, variant=None):
-        self.units, self.ru, self.rng, self.variant = units, ru, rng, variant
+    def __init__(self, units, ru, rng, variant=None, nprod=1):
+        self.units, self.ru, self.rng, self.variant, self.nprod = units, ru, rng, variant, nprod
         self.full = [Bar(f"full[{s}]", 1) for s in range(NSLOT)]
         self.empty = [Bar(f"empty[{s}]", 1) for s in range(NSLOT)]
         self.wbar, self.drain = Bar("wbar", 1), Bar("drain", 1)
@@ -79,11 +81,18 @@ class Sim:
         # other roles run as far ahead as the barriers allow
         self.speed = {k: rng.choice([1.0, 0.2, 0.03]) for k in ("epilogue", "#pipe", "#copy")}
 
-    def producer(self):
+    def _mine(self, p, li):
+        # the "shared_turns" fault: both warps stage every row
+        return self.variant == "shared_turns" or li % self.nprod == p
+
+    def producer(self, p=0):
         li = 0
         last = [-1] * NSLOT
         for nrows in self.units:
             for r in range(nrows + 2):
+                if not self._mine(p, li):               # the other warp's turn
+                    li += 1
+                    continue
                 slot, rnd = li % NSLOT, li // NSLOT
                 yield from wait(self.empty[slot], rnd - 1)
                 if self.slot_readers[slot]:
@@ -98,14 +107,15 @@ class Sim:
                 last[slot] = li
                 li += 1
                 yield None
-        slot, rnd = li % NSLOT, li // NSLOT              # end-of-work marker
-        yield from wait(self.empty[slot], rnd - 1)
-        self.meta[slot] = (-1, 0)
-        self.slot_row[slot], self.slot_landed[slot] = li, True
-        self.full[slot].arrive()
-        if self.variant != "marker_not_recorded":
-            last[slot] = li
-        for s in range(NSLOT):                            # drain: own newest phase of every slot
+        if self._mine(p, li):
+            slot, rnd = li % NSLOT, li // NSLOT          # end-of-work marker
+            yield from wait(self.empty[slot], rnd - 1)
+            self.meta[slot] = (-1, 0)
+            self.slot_row[slot], self.slot_landed[slot] = li, True
+            self.full[slot].arrive()
+            if self.variant != "marker_not_recorded":
+                last[slot] = li
+        for s in range(NSLOT):                            # drain: own newest phase of each of its slots
             if last[s] >= 0:
                 yield from wait(self.full[s], last[s] // NSLOT)
 
@@ -115,13 +125,13 @@ class Sim:
         while True:
             slot, rnd = li % NSLOT, li // NSLOT
             yield from wait(self.full[slot], rnd)
+            if not self.slot_landed[slot] or self.slot_row[slot] != li:
+                raise Violation(f"row {li} read before it landed")
             if start:
                 k, nrows = self.meta[slot]
                 if k < 0:
                     break
                 start = False
-            if not self.slot_landed[slot] or self.slot_row[slot] != li:
-                raise Violation(f"row {li} read before it landed")
             if k < nrows:
                 yield from wait(self.bfree[k], uit)
                 if self.blk_zeroed[k] != 4:
@@ -184,7 +194,8 @@ class Sim:
         self.full[slot].arrive()
 
     def _procs(self):
-        procs = {"producer": self.producer(), "mma": self.mma()}
+        procs = {f"producer{p}": self.producer(p) for p in range(self.nprod)}
+        procs["mma"] = self.mma()
         for g in range(2):
             for q in range(4):
                 procs[f"epilogue{g}.{q}"] = self.epilogue(g)
@@ -224,12 +235,25 @@ def _units(rng, ru):
     return [ru if rng.random() < 0.4 else rng.randint(1, ru) for _ in range(n)]
 
 
+@pytest.mark.parametrize("nprod", [1, 2])
 @pytest.mark.parametrize("ru", [3, 4, 5, 6, 7, 8])
-def test_conv_pipeline_protocol_holds(ru):
+def test_conv_pipeline_protocol_holds(ru, nprod):
     rng = random.Random(1000 + ru)
     for trial in range(60):
         units = _units(rng, ru)
-        Sim(units, ru, random.Random(rng.random())).run()
+        Sim(units, ru, random.Random(rng.random()), nprod=nprod).run()
+
+
+def test_model_catches_two_producers_staging_the_same_rows():
+    """Two producer warps that do not take turns: both stage every row into its slot."""
+    rng = random.Random(17)
+    caught = 0
+    for trial in range(40):
+        try:
+            Sim(_units(rng, 8), 8, random.Random(rng.random()), "shared_turns", nprod=2).run()
+        except (Violation, AssertionError):
+            caught += 1
+    assert caught >= 20, caught
 
 
 @pytest.mark.parametrize("variant", ["skip_unused_wait", "marker_not_recorded"])
@@ -263,8 +287,8 @@ NRING = 8
 
 
 class StreamSim(Sim):
-    def __init__(self, units, rng, variant=None):
-        super().__init__(units, 8, rng, variant)
+    def __init__(self, units, rng, variant=None, nprod=2):
+        super().__init__(units, 8, rng, variant, nprod)
         self.blk_row = [-1] * NRING               # global row whose sum the block holds
         self.row_contrib = {}                     # global row -> staged-row contributions completed
 
@@ -274,13 +298,13 @@ class StreamSim(Sim):
         while True:
             slot, rnd = li % NSLOT, li // NSLOT
             yield from wait(self.full[slot], rnd)
+            if not self.slot_landed[slot] or self.slot_row[slot] != li:
+                raise Violation(f"row {li} read before it landed")
             if start:
                 k, nrows = self.meta[slot]
                 if k < 0:
                     break
                 start = False
-            if not self.slot_landed[slot] or self.slot_row[slot] != li:
-                raise Violation(f"row {li} read before it landed")
             if k < nrows:
                 g = g0 + k
                 yield from wait(self.bfree[g % NRING], g // NRING)
@@ -353,10 +377,11 @@ def _tall_units(rng):
     return [rng.choice([rng.randint(1, 5), rng.randint(6, 40), 64]) for _ in range(n)]
 
 
-def test_stream_protocol_holds():
+@pytest.mark.parametrize("nprod", [1, 2])
+def test_stream_protocol_holds(nprod):
     rng = random.Random(4242)
     for trial in range(150):
-        StreamSim(_tall_units(rng), random.Random(rng.random())).run()
+        StreamSim(_tall_units(rng), random.Random(rng.random()), nprod=nprod).run()
 
 
 @pytest.mark.parametrize("variant", ["stream_no_split", "stream_ring_restarts"])
