@@ -33,8 +33,8 @@
 // Warp roles (one persistent CTA per SM): warp 0 = copy producer
 // (and TMEM owner), warp 1 = MMA issuer, warps 2-9 = epilogue (two per TMEM
 // lane quarter), warp 10 = a second copy producer (the two take the staged rows in
-// turn): 352 threads.  Layer 1 with its input built in the kernel: 480 threads,
-// warps 0 and 10-14 build the staged rows in place of the copy producers.
+// turn): 352 threads.  Layer 1 with its input built in the kernel: 544 threads,
+// warps 0 and 10-16 build the staged rows in place of the copy producers.
 // Every mbarrier wait is bounded (globaltimer); on expiry the kernel records
 // HT_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM and returns.
 #include <stdlib.h>
@@ -47,6 +47,9 @@ namespace {
 
 #ifndef HT_CONV_NSLOT
 #define HT_CONV_NSLOT 6
+#endif
+#ifndef HT_FUSED_NIN
+#define HT_FUSED_NIN 8                     // layer-1 input warps = its ring depth (even)
 #endif
 constexpr int NSLOT = HT_CONV_NSLOT;       // input-row ring depth (lookahead of the copy engine)
 constexpr int NTHREADS = 320;              // producer, MMA issuer, 8 epilogue warps
@@ -85,7 +88,9 @@ struct Cfg {
     static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;
     static constexpr int W_BYTES = 3 * NCHUNK * 3 * NOUT * 16; // [dx][chunk][3 dy][NOUT n][16 B]
     static constexpr int KSTEPS = NCHUNK / 2;                  // MMAs per dx (K = 16 / 32 per MMA)
-    static constexpr int SMEM = W_BYTES + NSLOT * SLOT_BYTES + 1024 /*align*/ + 4096 /*barriers*/;
+    static constexpr int NS = FIRST ? HT_FUSED_NIN : NSLOT;   // ring depth (layer 1: one input warp per slot)
+    static constexpr int SMEM = W_BYTES + NS * SLOT_BYTES + 1024 /*align*/ + 4096 /*barriers*/ + (FIRST ? NS * 576 : 0);
+    static_assert(NS % 2 == 0, "ring depth");
 };
 
 struct ConvParams {
@@ -170,11 +175,12 @@ __device__ __forceinline__ void first_input_pixel(float c, float z, uint4 &o0, u
     o1 = make_uint4(pack_bf16x2(z1, z0), pack_bf16x2(z1, z2), 0u, 0u);
 }
 
-// Layer 1 with its input built in the kernel (FUSED): warps 0 and 10 .. 14 take the
-// producer's place, one per input-ring slot.
-constexpr int NIN_WARPS = NSLOT;
+// Layer 1 with its input built in the kernel (FUSED): warps 0 and 10 .. 8 + NIN_WARPS take
+// the producers' place, one per input-ring slot (the kind's ring depth, Cfg::NS).  Eight
+// warps (96 registers, no spills) built the rows 15% faster than six (124 registers).
+constexpr int NIN_WARPS = HT_FUSED_NIN;
 constexpr int NTHREADS_FUSED = NTHREADS + (NIN_WARPS - 1) * 32;
-static_assert(NTHREADS_FUSED <= 512, "block size of the layer-1 kernel");
+static_assert(NTHREADS_FUSED <= 576, "block size of the layer-1 kernel");
 constexpr int NTHREADS_CONV = NTHREADS + 32;           // k_conv_tc: + a second copy producer
 static_assert(NSLOT % 2 == 0, "the two copy producers own alternate ring slots");
 
@@ -182,23 +188,24 @@ template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false, bo
 __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_conv_tc(const ConvParams P)
 {
     static_assert(!FUSED || (KIND == KIND_FIRST && !TR && CH == 64), "in-kernel input: inference layer 1 only");
+    static_assert(!FUSED || Cfg<FP8, KIND, CH, F16>::NS == NIN_WARPS, "one input warp per ring slot");
     using C = Cfg<FP8, KIND, CH, F16>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *s_w = smem;
     uint8_t *s_rows = smem + C::W_BYTES;
-    uint64_t *bars = (uint64_t *)(s_rows + NSLOT * C::SLOT_BYTES);
-    uint64_t *full = bars, *empty = bars + NSLOT, *wbar = bars + 2 * NSLOT, *bfull = wbar + 1, *bfree = bfull + RU,
+    uint64_t *bars = (uint64_t *)(s_rows + C::NS * C::SLOT_BYTES);
+    uint64_t *full = bars, *empty = bars + C::NS, *wbar = bars + 2 * C::NS, *bfull = wbar + 1, *bfree = bfull + RU,
              *drain = bfree + RU;
     int2 *s_meta = (int2 *)(drain + 1);                         // (k, nrows) of the row in each slot
-    uint32_t *s_tmem = (uint32_t *)(s_meta + NSLOT);
+    uint32_t *s_tmem = (uint32_t *)(s_meta + C::NS);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool input_warp = FUSED && (warp == 0 || warp >= 10);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSLOT; ++i) {
+        for (int i = 0; i < C::NS; ++i) {
             mbar_init(smem_u32(&full[i]), 1);
             mbar_init(smem_u32(&empty[i]), 1);
         }
@@ -220,15 +227,15 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
     if (input_warp) {
         if constexpr (FUSED) {
         // -------------------- producer: layer-1 input built here --------------------
-        // NSLOT warps build the staged rows from the contone image and the noise channel,
-        // warp w the rows of ring slot w, so that up to NSLOT rows are in flight: per pixel
+        // NIN_WARPS (= C::NS) warps build the staged rows from the contone image and the noise
+        // channel, warp w the rows of ring slot w, so that up to C::NS rows are in flight: per pixel
         // the two 16-byte chunks of the layer-1 input (first_input_pixel, the values
         // k_first_input stores), zero outside the image.  z is Philox4x32-10 of
         // (g / 4, image, 0, 0), g = y * W + x, lane g % 4: the row's calls (at most 34
         // groups of 4 pixels) are made once, two per lane at most, and shared through the
         // warp's part of shared memory.  The contone values of the warp's next row in the
         // same unit are loaded while it builds this one.
-        const int wi = warp == 0 ? 0 : warp - 9;                     // 0 .. NSLOT - 1 = ring slot
+        const int wi = warp == 0 ? 0 : warp - 9;                     // 0 .. C::NS - 1 = ring slot
         uint4 *s_u = (uint4 *)(((uintptr_t)(s_abort + 1) + 15) & ~(uintptr_t)15) + wi * 36;
         if (warp == 0 && lane == 0) {
             mbar_arrive_expect_tx(smem_u32(wbar), C::W_BYTES);
@@ -254,16 +261,16 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
                 }
             };
             // first row of this unit that is the warp's
-            int r = (int)((uint32_t)(wi - (int)(li % NSLOT) + NSLOT) % NSLOT);
+            int r = (int)((uint32_t)(wi - (int)(li % C::NS) + C::NS) % C::NS);
             if (r < nrows + 2) load_row(y0 - 1 + r);
-            for (; r < nrows + 2; r += NSLOT) {
+            for (; r < nrows + 2; r += C::NS) {
                 const uint32_t lr = li + (uint32_t)r;             // this row's index in the CTA's ring sequence
                 const int yy = y0 - 1 + r;
                 const bool row_in = (yy >= 0 && yy < H) && hi > lo;
                 float cv[5];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) cv[q] = cn[q];
-                if (r + NSLOT < nrows + 2) load_row(yy + NSLOT);
+                if (r + C::NS < nrows + 2) load_row(yy + C::NS);
                 const uint64_t G0 = row_in ? ((uint64_t)yy * (uint64_t)W + (uint64_t)lo) >> 2 : 0;
                 if (row_in) {
                     const uint32_t ng = (uint32_t)((((uint64_t)yy * (uint64_t)W + (uint64_t)(hi - 1)) >> 2) - G0) + 1u;
@@ -271,13 +278,17 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
                         s_u[t] = ht_philox4x32_10(make_uint4((uint32_t)(G0 + t), image, 0u, 0u), key);
                 }
                 int got = 0;
-                if (lane == 0) got = mbar_wait(smem_u32(&empty[wi]), ((lr / NSLOT) & 1u) ^ 1u, s_abort, P.err) ? 1 : 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&empty[wi]), ((lr / C::NS) & 1u) ^ 1u, s_abort, P.err) ? 1 : 0;
                 if (!__shfl_sync(0xffffffffu, got, 0)) {
                     ok = false;
                     break;
                 }
                 __syncwarp();
                 uint8_t *dst = s_rows + wi * C::SLOT_BYTES;
+                // z of pixel x is word g % 4 of the row's Philox group g / 4 - G0, g = yy * W + x:
+                // 32-bit word (x - lo) + r0 of s_u, r0 = (yy * W + lo) % 4
+                const uint32_t *s_u32 = reinterpret_cast<const uint32_t *>(s_u);
+                const uint32_t r0 = (uint32_t)(((uint64_t)yy * (uint64_t)W + (uint64_t)lo) & 3u);
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
                     const int i = lane + 32 * q;               // pixel x0 - 1 + i of the staged row
@@ -285,10 +296,7 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
                         const int x = x0 - 1 + i;
                         uint4 o0 = make_uint4(0, 0, 0, 0), o1 = make_uint4(0, 0, 0, 0);
                         if (row_in && x >= lo && x < hi) {
-                            const uint64_t g = (uint64_t)yy * (uint64_t)W + (uint64_t)x;
-                            const uint4 rr = s_u[(g >> 2) - G0];
-                            const uint32_t l = (uint32_t)g & 3u;
-                            const uint32_t w = l == 0 ? rr.x : l == 1 ? rr.y : l == 2 ? rr.z : rr.w;
+                            const uint32_t w = s_u32[(uint32_t)(x - lo) + r0];
                             first_input_pixel(cv[q], (float)(w >> 8) * (1.0f / 16777216.0f), o0, o1);
                         }
                         *reinterpret_cast<uint4 *>(dst + (size_t)i * 16) = o0;
@@ -305,9 +313,9 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
             }
             li += (uint32_t)nrows + 2u;
         }
-        if (ok && (int)(li % NSLOT) == wi) {
+        if (ok && (int)(li % C::NS) == wi) {
             // end marker (from the warp of the next row's slot): the MMA warp stops at k = -1
-            if (lane == 0 && mbar_wait(smem_u32(&empty[wi]), ((li / NSLOT) & 1u) ^ 1u, s_abort, P.err)) {
+            if (lane == 0 && mbar_wait(smem_u32(&empty[wi]), ((li / C::NS) & 1u) ^ 1u, s_abort, P.err)) {
                 s_meta[wi] = make_int2(-1, 0);
                 mbar_arrive(smem_u32(&full[wi]));
             }
@@ -319,15 +327,15 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
         // ------------------------- producers -------------------------
         // One input row = NCHUNK contiguous runs of ROW_PX * 16 bytes in HBM (one
         // per channel chunk).  Two warps take the CTA's ring rows in turn, warp 0 the
-        // even ones and PROD2_WARP the odd ones (NSLOT is even, so each slot always has
+        // even ones and PROD2_WARP the odd ones (C::NS is even, so each slot always has
         // the same producer): one warp's wait and bookkeeping for a row then overlap the
         // other's copies, which a single warp left the copy engine idle through.  In-image
         // pixels arrive by bulk async copies (complete_tx on the slot's barrier); halo
         // pixels outside the image are zero-filled by the warp with shared stores, made
         // visible to the tensor core's async proxy by a proxy fence before the arrive.
         const uint32_t turn = warp == 0 ? 0u : 1u;
-        int last_issued[NSLOT];
-        for (int i = 0; i < NSLOT; ++i) last_issued[i] = -1;
+        int last_issued[C::NS];
+        for (int i = 0; i < C::NS; ++i) last_issued[i] = -1;
         if (warp == 0 && lane == 0) {
             mbar_arrive_expect_tx(smem_u32(wbar), C::W_BYTES);
             bulk_g2s(smem_u32(s_w), P.wpack, C::W_BYTES, smem_u32(wbar));
@@ -340,8 +348,8 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
             const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, ui.W);   // in-image pixel range
             for (int r = 0; r < (y1 - y0) + 2; ++r, ++li) {
                 if ((li & 1u) != turn) continue;               // the other producer's row
-                const int slot = (int)(li % NSLOT);
-                const uint32_t ph = (li / NSLOT) & 1u;
+                const int slot = (int)(li % C::NS);
+                const uint32_t ph = (li / C::NS) & 1u;
                 int got = 0;
                 if (lane == 0) got = mbar_wait(smem_u32(&empty[slot]), ph ^ 1u, s_abort, P.err) ? 1 : 0;
                 if (!__shfl_sync(0xffffffffu, got, 0)) {
@@ -382,9 +390,9 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
         }
         if (ok && (li & 1u) == turn) {
             // end marker (from the warp whose turn it is): the MMA warp stops at a row with k = -1
-            const int slot = (int)(li % NSLOT);
+            const int slot = (int)(li % C::NS);
             int got = 0;
-            if (lane == 0) got = mbar_wait(smem_u32(&empty[slot]), ((li / NSLOT) & 1u) ^ 1u, s_abort, P.err) ? 1 : 0;
+            if (lane == 0) got = mbar_wait(smem_u32(&empty[slot]), ((li / C::NS) & 1u) ^ 1u, s_abort, P.err) ? 1 : 0;
             if (__shfl_sync(0xffffffffu, got, 0)) {
                 if (lane == 0) {
                     s_meta[slot] = make_int2(-1, 0);
@@ -395,9 +403,9 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
         }
         // drain: every issued copy must have landed before the CTA exits
         if (lane == 0) {
-            for (int s2 = 0; s2 < NSLOT; ++s2)
+            for (int s2 = 0; s2 < C::NS; ++s2)
                 if (last_issued[s2] >= 0)
-                    mbar_wait(smem_u32(&full[s2]), ((uint32_t)last_issued[s2] / NSLOT) & 1u, s_abort, P.err, true);
+                    mbar_wait(smem_u32(&full[s2]), ((uint32_t)last_issued[s2] / C::NS) & 1u, s_abort, P.err, true);
             if (warp == 0) mbar_wait(smem_u32(wbar), 0, s_abort, P.err, true);
         }
         __syncwarp();
@@ -462,7 +470,7 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
                                                     idesc);
                             mma_commit_el(el, smem_u32(&empty[slot]));
                             if (kk >= 2) mma_commit_el(el, smem_u32(&bfull[kk - 2]));
-                            if (++slot == (uint32_t)NSLOT) {
+                            if (++slot == (uint32_t)C::NS) {
                                 slot = 0;
                                 ph ^= 1u;
                             }
@@ -507,7 +515,7 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
                                 }
                             mma_commit_el(el, smem_u32(&empty[slot]));
                             mma_commit_el(el, smem_u32(&bfull[kk]));      // output row k + kk - 2 complete
-                            if (++slot == (uint32_t)NSLOT) {
+                            if (++slot == (uint32_t)C::NS) {
                                 slot = 0;
                                 ph ^= 1u;
                             }
@@ -566,7 +574,7 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
                 mma_commit_el(el, smem_u32(&empty[slot]));
                 if (k >= 2)                                                 // output row k-2 complete
                     mma_commit_el(el, smem_u32(&bfull[STREAM ? (g0 + (uint32_t)k - 2u) % 8u : (uint32_t)(k - 2)]));
-                if (++slot == (uint32_t)NSLOT) {
+                if (++slot == (uint32_t)C::NS) {
                     slot = 0;
                     ph ^= 1u;
                 }
