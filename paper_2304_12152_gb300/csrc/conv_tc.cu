@@ -51,9 +51,15 @@ namespace {
 #ifndef HT_FUSED_NIN
 #define HT_FUSED_NIN 8                     // layer-1 input warps = its ring depth (even)
 #endif
-constexpr int NSLOT = HT_CONV_NSLOT;       // input-row ring depth (lookahead of the copy engine)
+constexpr int NSLOT = HT_CONV_NSLOT;       // CTA-pair form: input-row ring depth (lookahead of the copy engine)
 constexpr int NTHREADS = 320;              // producer, MMA issuer, 8 epilogue warps
-constexpr int PROD2_WARP = 10;             // k_conv_tc: second copy producer
+#ifndef HT_CONV_NPROD
+#define HT_CONV_NPROD 2
+#endif
+#ifndef HT_CONV_NS
+#define HT_CONV_NS 8                       // k_conv_tc: input-row ring depth (a multiple of NPROD)
+#endif
+constexpr int NPROD = HT_CONV_NPROD;       // k_conv_tc: copy producers (warps 0, 10, 11, ...)
 
 // Kernel kinds built from one pipeline: a hidden 64 -> 64 layer, the last
 // hidden layer with the 1-logit head's per-tap partials fused into its
@@ -88,9 +94,9 @@ struct Cfg {
     static constexpr int SLOT_BYTES = NCHUNK * ROW_PX * 16;
     static constexpr int W_BYTES = 3 * NCHUNK * 3 * NOUT * 16; // [dx][chunk][3 dy][NOUT n][16 B]
     static constexpr int KSTEPS = NCHUNK / 2;                  // MMAs per dx (K = 16 / 32 per MMA)
-    static constexpr int NS = FIRST ? HT_FUSED_NIN : NSLOT;   // ring depth (layer 1: one input warp per slot)
+    static constexpr int NS = FIRST ? HT_FUSED_NIN : HT_CONV_NS;   // ring depth (layer 1: one input warp per slot)
     static constexpr int SMEM = W_BYTES + NS * SLOT_BYTES + 1024 /*align*/ + 4096 /*barriers*/ + (FIRST ? NS * 576 : 0);
-    static_assert(NS % 2 == 0, "ring depth");
+    static_assert(NS % HT_CONV_NPROD == 0 && SMEM <= 232448, "ring depth");
 };
 
 struct ConvParams {
@@ -181,8 +187,7 @@ __device__ __forceinline__ void first_input_pixel(float c, float z, uint4 &o0, u
 constexpr int NIN_WARPS = HT_FUSED_NIN;
 constexpr int NTHREADS_FUSED = NTHREADS + (NIN_WARPS - 1) * 32;
 static_assert(NTHREADS_FUSED <= 576, "block size of the layer-1 kernel");
-constexpr int NTHREADS_CONV = NTHREADS + 32;           // k_conv_tc: + a second copy producer
-static_assert(NSLOT % 2 == 0, "the two copy producers own alternate ring slots");
+constexpr int NTHREADS_CONV = NTHREADS + (NPROD - 1) * 32;   // k_conv_tc: + the further copy producers
 
 template <bool FP8, int KIND, bool TR = false, int CH = 64, bool F16 = false, bool STREAM = false, bool FUSED = false>
 __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_conv_tc(const ConvParams P)
@@ -323,17 +328,17 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
         // the weight copy must have landed before the CTA exits
         if (warp == 0 && lane == 0) mbar_wait(smem_u32(wbar), 0, s_abort, P.err, true);
         }
-    } else if (warp == 0 || warp == PROD2_WARP) {
+    } else if (warp == 0 || (warp >= 10 && warp < 9 + NPROD)) {
         // ------------------------- producers -------------------------
         // One input row = NCHUNK contiguous runs of ROW_PX * 16 bytes in HBM (one
-        // per channel chunk).  Two warps take the CTA's ring rows in turn, warp 0 the
-        // even ones and PROD2_WARP the odd ones (C::NS is even, so each slot always has
-        // the same producer): one warp's wait and bookkeeping for a row then overlap the
-        // other's copies, which a single warp left the copy engine idle through.  In-image
+        // per channel chunk).  NPROD warps (0, 10, ...) take the CTA's ring rows in turn,
+        // producer p the rows li = p mod NPROD (the ring depth is a multiple of NPROD, so each
+        // slot always has the same producer): one warp's wait and bookkeeping for a row then
+        // overlap another's copies, which a single warp left the copy engine idle through.  In-image
         // pixels arrive by bulk async copies (complete_tx on the slot's barrier); halo
         // pixels outside the image are zero-filled by the warp with shared stores, made
         // visible to the tensor core's async proxy by a proxy fence before the arrive.
-        const uint32_t turn = warp == 0 ? 0u : 1u;
+        const uint32_t turn = warp == 0 ? 0u : (uint32_t)(warp - 9);
         int last_issued[C::NS];
         for (int i = 0; i < C::NS; ++i) last_issued[i] = -1;
         if (warp == 0 && lane == 0) {
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
             const int y0 = ui.y0, y1 = ui.y0 + ui.nrows, x0 = ui.x0;
             const int lo = max(x0 - 1, 0), hi = min(x0 - 1 + ROW_PX, ui.W);   // in-image pixel range
             for (int r = 0; r < (y1 - y0) + 2; ++r, ++li) {
-                if ((li & 1u) != turn) continue;               // the other producer's row
+                if (li % NPROD != turn) continue;              // another producer's row
                 const int slot = (int)(li % C::NS);
                 const uint32_t ph = (li / C::NS) & 1u;
                 int got = 0;
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(FUSED ? NTHREADS_FUSED : NTHREADS_CONV, 1) k_c
                 last_issued[slot] = (int)li;
             }
         }
-        if (ok && (li & 1u) == turn) {
+        if (ok && li % NPROD == turn) {
             // end marker (from the warp whose turn it is): the MMA warp stops at a row with k = -1
             const int slot = (int)(li % C::NS);
             int got = 0;

@@ -235,13 +235,28 @@ def _units(rng, ru):
     return [ru if rng.random() < 0.4 else rng.randint(1, ru) for _ in range(n)]
 
 
-@pytest.mark.parametrize("nprod", [1, 2])
+@pytest.mark.parametrize("nslot,nprod", [(6, 1), (6, 2), (8, 4)])
 @pytest.mark.parametrize("ru", [3, 4, 5, 6, 7, 8])
-def test_conv_pipeline_protocol_holds(ru, nprod):
+def test_conv_pipeline_protocol_holds(ru, nslot, nprod, monkeypatch):
+    monkeypatch.setattr(__import__(__name__), "NSLOT", nslot)
     rng = random.Random(1000 + ru)
     for trial in range(60):
         units = _units(rng, ru)
         Sim(units, ru, random.Random(rng.random()), nprod=nprod).run()
+
+
+def test_model_catches_producers_not_owning_their_slots(monkeypatch):
+    """Four producers on a ring of 6: a slot then passes between producers, and one can wait
+    on a phase of it two phases ahead of the barrier (its parity is then already complete)."""
+    monkeypatch.setattr(__import__(__name__), "NSLOT", 6)
+    rng = random.Random(23)
+    caught = 0
+    for trial in range(60):
+        try:
+            Sim(_units(rng, 8), 8, random.Random(rng.random()), nprod=4).run()
+        except (Violation, AssertionError):
+            caught += 1
+    assert caught >= 5, caught
 
 
 def test_model_catches_two_producers_staging_the_same_rows():
@@ -377,8 +392,9 @@ def _tall_units(rng):
     return [rng.choice([rng.randint(1, 5), rng.randint(6, 40), 64]) for _ in range(n)]
 
 
-@pytest.mark.parametrize("nprod", [1, 2])
-def test_stream_protocol_holds(nprod):
+@pytest.mark.parametrize("nslot,nprod", [(6, 1), (6, 2), (8, 2), (8, 4)])
+def test_stream_protocol_holds(nslot, nprod, monkeypatch):
+    monkeypatch.setattr(__import__(__name__), "NSLOT", nslot)
     rng = random.Random(4242)
     for trial in range(150):
         StreamSim(_tall_units(rng), random.Random(rng.random()), nprod=nprod).run()
