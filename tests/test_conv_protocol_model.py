@@ -2,9 +2,10 @@
 interleavings.  compute-sanitizer is closed on the GPU pool, so the pipeline's ordering
 argument is checked here instead, on a faithful model of its synchronisation:
 
-* one or two producer warps that stage each unit's nrows + 2 input rows in a ring of NSLOT
-  slots, the two warps taking the ring rows in turn (NSLOT is even, so a slot always has
-  the same producer): wait `empty`, write the row record, copies landing asynchronously on
+* one or more producer warps that stage each unit's nrows + 2 input rows in a ring of NSLOT
+  slots, taking the ring rows in turn (NSLOT is a multiple of their number, so a slot always
+  has the same producer; with as many producers as slots this is the layer-1 kernel whose
+  input warps each build the rows of one slot): wait `empty`, write the row record, copies landing asynchronously on
   `full`; then the end-of-work marker (from the warp whose turn it is), then a drain that
   waits for the warp's own newest copy in each of its slots;
 * the MMA issuer: waits `full` for each row, reads the record at a unit's start, waits the
@@ -235,7 +236,8 @@ def _units(rng, ru):
     return [ru if rng.random() < 0.4 else rng.randint(1, ru) for _ in range(n)]
 
 
-@pytest.mark.parametrize("nslot,nprod", [(6, 1), (6, 2), (8, 4)])
+# (8, 8): the layer-1 kernel that builds its input, one input warp per ring slot
+@pytest.mark.parametrize("nslot,nprod", [(6, 1), (6, 2), (8, 2), (8, 4), (8, 8)])
 @pytest.mark.parametrize("ru", [3, 4, 5, 6, 7, 8])
 def test_conv_pipeline_protocol_holds(ru, nslot, nprod, monkeypatch):
     monkeypatch.setattr(__import__(__name__), "NSLOT", nslot)
@@ -392,7 +394,7 @@ def _tall_units(rng):
     return [rng.choice([rng.randint(1, 5), rng.randint(6, 40), 64]) for _ in range(n)]
 
 
-@pytest.mark.parametrize("nslot,nprod", [(6, 1), (6, 2), (8, 2), (8, 4)])
+@pytest.mark.parametrize("nslot,nprod", [(6, 1), (6, 2), (8, 2), (8, 4), (8, 8)])
 def test_stream_protocol_holds(nslot, nprod, monkeypatch):
     monkeypatch.setattr(__import__(__name__), "NSLOT", nslot)
     rng = random.Random(4242)
